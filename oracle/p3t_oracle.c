@@ -1,0 +1,1027 @@
+/*
+ * p3t_oracle.c -- plain FP64 CPU oracle for the P3T soft step with individual
+ * cut-off radii (Ishigaki et al. 2021).  TEST INFRASTRUCTURE ONLY: loaded by the
+ * tests, the smoke check and the benchmark's CPU-baseline leg, never by the
+ * product path.  Plain C11 + OpenMP, FP64, built with -ffp-contract=off.
+ *
+ * Every function states the passage it follows.  Where the paper is silent or
+ * garbled, the reading used (numbered C1..C11) is stated beside the code it
+ * governs.
+ */
+#include "p3t_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+static double dmax(double a, double b) { return a > b ? a : b; }
+static double dmin(double a, double b) { return a < b ? a : b; }
+
+/* ========================================================================= */
+/* Changeover functions, Sec. 2.1.1.                                          */
+/* The paper prints W(y; gamma) (Eq. cutfuncW) and defines K through          */
+/* W(r) = r * int_r^inf K(s)/s^2 ds, so K = W - y dW/dy.  Carrying out the    */
+/* derivative of the printed middle branch (reading C1: the garbled term is   */
+/* -(10/3) y^7) gives K(y) = S(x), x = (y - gamma)/(1 - gamma), with          */
+/* S(x) = 35x^4 - 84x^5 + 70x^6 - 20x^7, K = 0 below gamma and 1 above 1.      */
+/* ========================================================================= */
+double or_changeover_K(double y, double gamma) {
+  if (y <= gamma) return 0.0;
+  if (y >= 1.0) return 1.0;
+  double x = (y - gamma) / (1.0 - gamma);
+  double x2 = x * x;
+  double x3 = x2 * x;
+  double x4 = x2 * x2;
+  return x4 * (35.0 - 84.0 * x + 70.0 * x2 - 20.0 * x3);
+}
+
+/* dK/dy = S'(x) / (1 - gamma), S'(x) = 140 x^3 (1 - x)^3 (needed for the jerk
+ * of the hard force, Eq. hardforce). */
+double or_changeover_dKdy(double y, double gamma) {
+  if (y <= gamma || y >= 1.0) return 0.0;
+  double x = (y - gamma) / (1.0 - gamma);
+  double u = 1.0 - x;
+  return 140.0 * x * x * x * u * u * u / (1.0 - gamma);
+}
+
+/* ========================================================================= */
+/* Row a1: cut-off and search radii.                                          */
+/* r_Hill,i = (m_i / 3M_*)^(1/3) a_i (Sec. 2.1.1), a_i the osculating         */
+/* semi-major axis; r_out,i = max(R~cut,0 r_Hill,i, R~cut,1 v_ran,i dt)       */
+/* (Eq. routi2); r_search,i = R~s,0 r_out,i + R~s,1 v_ran,i dt (Eq. rsearch). */
+/* v_ran,i: reading C3 -- random velocity u = v - sqrt(G M_* / r) phi_hat,      */
+/* v_ran = sqrt(<|u|^2>) over the particle's radial bin; bins uniform in      */
+/* ln R_cyl between the smallest and largest R_cyl.                          */
+/* ========================================================================= */
+int or_cutoffs(int64_t n, const double *x, const double *y, const double *z,
+               const double *vx, const double *vy, const double *vz,
+               const double *m, const or_params *p, double *r_out,
+               double *r_search, double *v_ran, int32_t *bin) {
+  if (n <= 0) return 0;
+  const double mu = p->G * p->m_star;
+  int64_t nb = p->vran_bins;
+  if (nb <= 0) {
+    nb = n / 1000;
+    if (nb < 1) nb = 1;
+    if (nb > 1024) nb = 1024;
+  }
+  double *R = (double *)malloc(sizeof(double) * n);
+  double *u2 = (double *)malloc(sizeof(double) * n);
+  double *sum = (double *)calloc(nb, sizeof(double));
+  int64_t *cnt = (int64_t *)calloc(nb, sizeof(int64_t));
+  int32_t *b = bin ? bin : (int32_t *)malloc(sizeof(int32_t) * n);
+  double Rmin = INFINITY, Rmax = -INFINITY;
+  for (int64_t i = 0; i < n; ++i) {
+    R[i] = sqrt(x[i] * x[i] + y[i] * y[i]);
+    if (R[i] < Rmin) Rmin = R[i];
+    if (R[i] > Rmax) Rmax = R[i];
+    double r = sqrt(x[i] * x[i] + y[i] * y[i] + z[i] * z[i]);
+    double vk = sqrt(mu / r);
+    double px = 0.0, py = 0.0;
+    if (R[i] > 0.0) { px = -y[i] / R[i]; py = x[i] / R[i]; }
+    double ux = vx[i] - vk * px, uy = vy[i] - vk * py, uz = vz[i];
+    u2[i] = ux * ux + uy * uy + uz * uz;
+  }
+  double lmin = log(Rmin), lmax = log(Rmax);
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t k = 0;
+    if (Rmax > Rmin && R[i] > Rmin) {
+      double t = (log(R[i]) - lmin) / (lmax - lmin);
+      k = (int64_t)floor(t * (double)nb);
+      if (k < 0) k = 0;
+      if (k > nb - 1) k = nb - 1;
+    }
+    b[i] = (int32_t)k;
+    sum[k] += u2[i];
+    cnt[k] += 1;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    double r = sqrt(x[i] * x[i] + y[i] * y[i] + z[i] * z[i]);
+    double v2 = vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i];
+    double alpha = 2.0 / r - v2 / mu; /* 1/a from the vis-viva relation */
+    double a = alpha > 0.0 ? 1.0 / alpha : r;
+    double rhill = cbrt(m[i] / (3.0 * p->m_star)) * a;
+    double vr = sqrt(sum[b[i]] / (double)cnt[b[i]]);
+    if (v_ran) v_ran[i] = vr;
+    double ro = dmax(p->rcut0 * rhill, p->rcut1 * vr * p->dt_soft);
+    r_out[i] = ro;
+    r_search[i] = p->rs0 * ro + p->rs1 * vr * p->dt_soft;
+  }
+  if (!bin) free(b);
+  free(R); free(u2); free(sum); free(cnt);
+  return 0;
+}
+
+/* ========================================================================= */
+/* Direct O(N^2) soft force, Eq. softforce:                                   */
+/*   a_i = -sum_{j != i} G m_j K(r_ij; r_out,ij) r_ij / r_ij^3,               */
+/*   r_out,ij = max(r_out,i, r_out,j) (Eq. rout2).                            */
+/* ========================================================================= */
+int or_direct_soft(int64_t n, const double *x, const double *y, const double *z,
+                   const double *m, const double *r_out, const or_params *p,
+                   double *ax, double *ay, double *az) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double rx = x[i] - x[j], ry = y[i] - y[j], rz = z[i] - z[j];
+      double r2 = rx * rx + ry * ry + rz * rz;
+      double r = sqrt(r2);
+      double ro = dmax(r_out[i], r_out[j]);
+      double K = or_changeover_K(r / ro, p->gamma);
+      if (K == 0.0) continue;
+      double f = p->G * m[j] * K / (r2 * r);
+      sx -= f * rx; sy -= f * ry; sz -= f * rz;
+    }
+    ax[i] = sx; ay[i] = sy; az[i] = sz;
+  }
+  return 0;
+}
+
+/* ========================================================================= */
+/* Rows a2-a4: the Barnes-Hut tree (Sec. 2.1.2 uses FDPS's tree; the discrete */
+/* definitions below are reading C4).                             */
+/*  * root cube: bounding box of the positions, made cubic (side L = largest  */
+/*    extent), corner at the per-axis minimum;                                */
+/*  * each axis quantised to 21 bits, bits interleaved (x highest) into a     */
+/*    63-bit Morton key; particles ordered by (key, caller index);            */
+/*  * a node is a key prefix at level l holding > 0 particles; a node is      */
+/*    split while it holds more than leaf_size particles and l < 21;          */
+/*  * target groups are the leaves.  A node is opened for a group if          */
+/*    (i) side^2 > theta^2 d^2(cube centre, group box)  [Barnes-Hut], or      */
+/*    (ii) dist^2(group box, node box) < max(rsmax_group, rsmax_node)^2       */
+/*    [cut-off reach], with tight boxes of particle positions.  Accepted      */
+/*    nodes add monopole + quadrupole; opened leaves add changeover pairs.    */
+/* ========================================================================= */
+#define OR_BITS 21
+#define OR_QMAX ((int64_t)1 << OR_BITS)
+
+static uint64_t spread3(uint64_t v) {
+  uint64_t r = 0;
+  for (int b = 0; b < OR_BITS; ++b) r |= ((v >> b) & 1ull) << (3 * b);
+  return r;
+}
+
+static int64_t quantise(double v, double lo, double L) {
+  double t = (v - lo) / L;
+  int64_t q = (int64_t)floor(t * (double)OR_QMAX);
+  if (q < 0) q = 0;
+  if (q > OR_QMAX - 1) q = OR_QMAX - 1;
+  return q;
+}
+
+static void root_box(int64_t n, const double *x, const double *y,
+                     const double *z, double box[4]) {
+  double lo[3] = {INFINITY, INFINITY, INFINITY};
+  double hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = 0; i < n; ++i) {
+    lo[0] = dmin(lo[0], x[i]); hi[0] = dmax(hi[0], x[i]);
+    lo[1] = dmin(lo[1], y[i]); hi[1] = dmax(hi[1], y[i]);
+    lo[2] = dmin(lo[2], z[i]); hi[2] = dmax(hi[2], z[i]);
+  }
+  double L = dmax(hi[0] - lo[0], dmax(hi[1] - lo[1], hi[2] - lo[2]));
+  if (!(L > 0.0)) L = 1.0;
+  box[0] = lo[0]; box[1] = lo[1]; box[2] = lo[2]; box[3] = L;
+}
+
+int or_morton_keys(int64_t n, const double *x, const double *y, const double *z,
+                   uint64_t *key, double box_out[4]) {
+  double box[4];
+  root_box(n, x, y, z, box);
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t qx = (uint64_t)quantise(x[i], box[0], box[3]);
+    uint64_t qy = (uint64_t)quantise(y[i], box[1], box[3]);
+    uint64_t qz = (uint64_t)quantise(z[i], box[2], box[3]);
+    key[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+  }
+  if (box_out) memcpy(box_out, box, sizeof(box));
+  return 0;
+}
+
+typedef struct {
+  int level;
+  int64_t first, count;  /* range in the sorted particle order */
+  int64_t child0, nchild; /* children are contiguous in the node array */
+  double M, com[3], Q[6]; /* Q = sum m (3 d_a d_b - d^2 delta_ab): xx yy zz xy xz yz */
+  double lo[3], hi[3];    /* tight box of the particle positions */
+  double rsmax;           /* max r_search over the node's particles */
+  double cen[3], side;    /* the node's cube (dyadic subdivision of the root) */
+} or_node;
+
+typedef struct {
+  int64_t n;
+  int64_t *ord;      /* sorted position -> caller index */
+  uint64_t *key;     /* keys in sorted order */
+  double *x, *y, *z, *m, *ro, *rs; /* sorted copies */
+  int64_t *qx, *qy, *qz;
+  or_node *node;
+  int64_t nnode, cap;
+  double box[4];
+} or_tree;
+
+typedef struct { uint64_t key; int64_t idx; } kv_t;
+static int cmp_kv(const void *a, const void *b) {
+  const kv_t *u = (const kv_t *)a, *v = (const kv_t *)b;
+  if (u->key != v->key) return u->key < v->key ? -1 : 1;
+  return (u->idx > v->idx) - (u->idx < v->idx);
+}
+
+/* Moments of a particle set straight from the definitions: M = sum m,        */
+/* com = sum m x / M, Q_ab = sum m (3 d_a d_b - |d|^2 delta_ab), d = x - com. */
+void or_node_moments(int64_t n, const double *x, const double *y,
+                     const double *z, const double *m, double out[10]) {
+  double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    M += m[i]; sx += m[i] * x[i]; sy += m[i] * y[i]; sz += m[i] * z[i];
+  }
+  double cx = sx / M, cy = sy / M, cz = sz / M;
+  double Q[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t i = 0; i < n; ++i) {
+    double dx = x[i] - cx, dy = y[i] - cy, dz = z[i] - cz;
+    double d2 = dx * dx + dy * dy + dz * dz;
+    Q[0] += m[i] * (3.0 * dx * dx - d2);
+    Q[1] += m[i] * (3.0 * dy * dy - d2);
+    Q[2] += m[i] * (3.0 * dz * dz - d2);
+    Q[3] += m[i] * (3.0 * dx * dy);
+    Q[4] += m[i] * (3.0 * dx * dz);
+    Q[5] += m[i] * (3.0 * dy * dz);
+  }
+  out[0] = M; out[1] = cx; out[2] = cy; out[3] = cz;
+  for (int k = 0; k < 6; ++k) out[4 + k] = Q[k];
+}
+
+/* Field of a monopole + quadrupole at p: the potential of the set is          */
+/* phi = -G [M/r + (r.Q.r)/(2 r^5)], r = p - com, so                            */
+/* a = -grad phi = G [-M r/r^3 + Q.r/r^5 - (5/2)(r.Q.r) r/r^7].                */
+void or_multipole_acc(const double mom[10], double G, double px, double py,
+                      double pz, double acc[3]) {
+  double dx = px - mom[1], dy = py - mom[2], dz = pz - mom[3];
+  double r2 = dx * dx + dy * dy + dz * dz;
+  double r = sqrt(r2);
+  double r3 = r2 * r, r5 = r3 * r2, r7 = r5 * r2;
+  const double *Q = mom + 4;
+  double qx = Q[0] * dx + Q[3] * dy + Q[4] * dz;
+  double qy = Q[3] * dx + Q[1] * dy + Q[5] * dz;
+  double qz = Q[4] * dx + Q[5] * dy + Q[2] * dz;
+  double rqr = dx * qx + dy * qy + dz * qz;
+  double M = mom[0];
+  acc[0] = G * (-M * dx / r3 + qx / r5 - 2.5 * rqr * dx / r7);
+  acc[1] = G * (-M * dy / r3 + qy / r5 - 2.5 * rqr * dy / r7);
+  acc[2] = G * (-M * dz / r3 + qz / r5 - 2.5 * rqr * dz / r7);
+}
+
+static int64_t push_node(or_tree *T) {
+  if (T->nnode == T->cap) {
+    T->cap = T->cap ? 2 * T->cap : 1024;
+    T->node = (or_node *)realloc(T->node, sizeof(or_node) * T->cap);
+  }
+  memset(&T->node[T->nnode], 0, sizeof(or_node));
+  return T->nnode++;
+}
+
+static void fill_node(or_tree *T, or_node *nd) {
+  int64_t f = nd->first, c = nd->count;
+  double mom[10];
+  or_node_moments(c, T->x + f, T->y + f, T->z + f, T->m + f, mom);
+  nd->M = mom[0];
+  for (int k = 0; k < 3; ++k) nd->com[k] = mom[1 + k];
+  for (int k = 0; k < 6; ++k) nd->Q[k] = mom[4 + k];
+  for (int k = 0; k < 3; ++k) { nd->lo[k] = INFINITY; nd->hi[k] = -INFINITY; }
+  nd->rsmax = 0.0;
+  for (int64_t i = f; i < f + c; ++i) {
+    nd->lo[0] = dmin(nd->lo[0], T->x[i]); nd->hi[0] = dmax(nd->hi[0], T->x[i]);
+    nd->lo[1] = dmin(nd->lo[1], T->y[i]); nd->hi[1] = dmax(nd->hi[1], T->y[i]);
+    nd->lo[2] = dmin(nd->lo[2], T->z[i]); nd->hi[2] = dmax(nd->hi[2], T->z[i]);
+    nd->rsmax = dmax(nd->rsmax, T->rs[i]);
+  }
+  /* the node's cube: integer cell coordinates at its level, from any member */
+  int sh = OR_BITS - nd->level;
+  double side = ldexp(T->box[3], -nd->level);
+  nd->side = side;
+  nd->cen[0] = T->box[0] + ((double)(T->qx[f] >> sh) + 0.5) * side;
+  nd->cen[1] = T->box[1] + ((double)(T->qy[f] >> sh) + 0.5) * side;
+  nd->cen[2] = T->box[2] + ((double)(T->qz[f] >> sh) + 0.5) * side;
+}
+
+static void tree_build(or_tree *T, int64_t n, const double *x, const double *y,
+                       const double *z, const double *m, const double *ro,
+                       const double *rs, int leaf) {
+  memset(T, 0, sizeof(*T));
+  T->n = n;
+  uint64_t *key = (uint64_t *)malloc(sizeof(uint64_t) * n);
+  or_morton_keys(n, x, y, z, key, T->box);
+  kv_t *kv = (kv_t *)malloc(sizeof(kv_t) * n);
+  for (int64_t i = 0; i < n; ++i) { kv[i].key = key[i]; kv[i].idx = i; }
+  qsort(kv, n, sizeof(kv_t), cmp_kv);
+  T->ord = (int64_t *)malloc(sizeof(int64_t) * n);
+  T->key = (uint64_t *)malloc(sizeof(uint64_t) * n);
+  T->x = (double *)malloc(sizeof(double) * n);
+  T->y = (double *)malloc(sizeof(double) * n);
+  T->z = (double *)malloc(sizeof(double) * n);
+  T->m = (double *)malloc(sizeof(double) * n);
+  T->ro = (double *)malloc(sizeof(double) * n);
+  T->rs = (double *)malloc(sizeof(double) * n);
+  T->qx = (int64_t *)malloc(sizeof(int64_t) * n);
+  T->qy = (int64_t *)malloc(sizeof(int64_t) * n);
+  T->qz = (int64_t *)malloc(sizeof(int64_t) * n);
+  for (int64_t s = 0; s < n; ++s) {
+    int64_t i = kv[s].idx;
+    T->ord[s] = i; T->key[s] = kv[s].key;
+    T->x[s] = x[i]; T->y[s] = y[i]; T->z[s] = z[i]; T->m[s] = m[i];
+    T->ro[s] = ro[i]; T->rs[s] = rs[i];
+    T->qx[s] = quantise(x[i], T->box[0], T->box[3]);
+    T->qy[s] = quantise(y[i], T->box[1], T->box[3]);
+    T->qz[s] = quantise(z[i], T->box[2], T->box[3]);
+  }
+  free(kv); free(key);
+  /* breadth-first: children of a node are appended contiguously */
+  int64_t r = push_node(T);
+  T->node[r].level = 0; T->node[r].first = 0; T->node[r].count = n;
+  for (int64_t k = 0; k < T->nnode; ++k) {
+    or_node nd = T->node[k];
+    if (nd.count > leaf && nd.level < OR_BITS) {
+      int sh = 3 * (OR_BITS - (nd.level + 1));
+      int64_t c0 = T->nnode, nc = 0;
+      int64_t s = nd.first, e = nd.first + nd.count;
+      while (s < e) {
+        uint64_t d = (T->key[s] >> sh) & 7ull;
+        int64_t t = s;
+        while (t < e && ((T->key[t] >> sh) & 7ull) == d) ++t;
+        int64_t c = push_node(T);
+        T->node[c].level = nd.level + 1; T->node[c].first = s;
+        T->node[c].count = t - s;
+        ++nc;
+        s = t;
+      }
+      T->node[k].child0 = c0; T->node[k].nchild = nc;
+    }
+  }
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t k = 0; k < T->nnode; ++k) fill_node(T, &T->node[k]);
+}
+
+static void tree_free(or_tree *T) {
+  free(T->ord); free(T->key); free(T->x); free(T->y); free(T->z); free(T->m);
+  free(T->ro); free(T->rs); free(T->qx); free(T->qy); free(T->qz);
+  free(T->node);
+}
+
+/* Opening decision for node nd seen from target group g (reading C4). */
+static int mac_open(const or_node *g, const or_node *nd, double theta2) {
+  /* (i) Barnes-Hut: distance from the node's cube centre to the group box */
+  double d2 = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    double d = 0.0;
+    if (nd->cen[a] < g->lo[a]) d = g->lo[a] - nd->cen[a];
+    else if (nd->cen[a] > g->hi[a]) d = nd->cen[a] - g->hi[a];
+    d2 = d2 + d * d;
+  }
+  if (nd->side * nd->side > theta2 * d2) return 1;
+  /* (ii) cut-off reach: box-box distance against the larger search radius */
+  double b2 = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    double d = 0.0;
+    if (nd->lo[a] > g->hi[a]) d = nd->lo[a] - g->hi[a];
+    else if (g->lo[a] > nd->hi[a]) d = g->lo[a] - nd->hi[a];
+    b2 = b2 + d * d;
+  }
+  double rs = dmax(g->rsmax, nd->rsmax);
+  return b2 < rs * rs;
+}
+
+typedef struct {
+  int32_t *ci, *cj;
+  int64_t n, cap;
+} cand_buf;
+
+static void cand_push(cand_buf *b, int32_t i, int32_t j) {
+  if (b->n == b->cap) {
+    b->cap = b->cap ? 2 * b->cap : 256;
+    b->ci = (int32_t *)realloc(b->ci, sizeof(int32_t) * b->cap);
+    b->cj = (int32_t *)realloc(b->cj, sizeof(int32_t) * b->cap);
+  }
+  b->ci[b->n] = i; b->cj[b->n] = j; b->n++;
+}
+
+typedef struct {
+  const or_tree *T;
+  const or_params *p;
+  const or_node *g;
+  const unsigned char *is_target;
+  double (*acc)[3]; /* accumulators of the group's targets (indexed s - first) */
+  uint64_t npp, npn;
+  cand_buf *cb;
+  double theta2;
+} walk_ctx;
+
+static void walk(walk_ctx *w, int64_t k) {
+  const or_tree *T = w->T;
+  const or_node *nd = &T->node[k];
+  const or_node *g = w->g;
+  if (!mac_open(g, nd, w->theta2)) {
+    double mom[10] = {nd->M, nd->com[0], nd->com[1], nd->com[2], nd->Q[0],
+                      nd->Q[1], nd->Q[2], nd->Q[3], nd->Q[4], nd->Q[5]};
+    for (int64_t s = g->first; s < g->first + g->count; ++s) {
+      if (!w->is_target[s]) continue;
+      double a[3];
+      or_multipole_acc(mom, w->p->G, T->x[s], T->y[s], T->z[s], a);
+      double *acc = w->acc[s - g->first];
+      acc[0] += a[0]; acc[1] += a[1]; acc[2] += a[2];
+      w->npn += 1;
+    }
+    return;
+  }
+  if (nd->nchild == 0) {
+    for (int64_t s = g->first; s < g->first + g->count; ++s) {
+      if (!w->is_target[s]) continue;
+      double *acc = w->acc[s - g->first];
+      for (int64_t t = nd->first; t < nd->first + nd->count; ++t) {
+        if (t == s) continue;
+        w->npp += 1;
+        double rx = T->x[s] - T->x[t], ry = T->y[s] - T->y[t], rz = T->z[s] - T->z[t];
+        double r2 = rx * rx + ry * ry + rz * rz;
+        double rs = dmax(T->rs[s], T->rs[t]);
+        if (r2 < rs * rs) cand_push(w->cb, (int32_t)T->ord[s], (int32_t)T->ord[t]);
+        double r = sqrt(r2);
+        double ro = dmax(T->ro[s], T->ro[t]);
+        double K = or_changeover_K(r / ro, w->p->gamma);
+        if (K == 0.0) continue;
+        double f = w->p->G * T->m[t] * K / (r2 * r);
+        acc[0] -= f * rx; acc[1] -= f * ry; acc[2] -= f * rz;
+      }
+    }
+    return;
+  }
+  for (int64_t c = nd->child0; c < nd->child0 + nd->nchild; ++c) walk(w, c);
+}
+
+int or_tree_soft(int64_t n, const double *x, const double *y, const double *z,
+                 const double *m, const double *r_out, const double *r_search,
+                 const or_params *p, int64_t n_targets, const int64_t *targets,
+                 double *ax, double *ay, double *az, uint64_t counts[2],
+                 int64_t cand_cap, int32_t *cand_i, int32_t *cand_j,
+                 int64_t *n_cand, int64_t tree_stats[4]) {
+  if (n <= 0) { if (counts) counts[0] = counts[1] = 0; if (n_cand) *n_cand = 0; return 0; }
+  or_tree T;
+  tree_build(&T, n, x, y, z, m, r_out, r_search, p->leaf_size);
+  unsigned char *is_target = (unsigned char *)calloc(n, 1);
+  int64_t *inv = (int64_t *)malloc(sizeof(int64_t) * n);
+  for (int64_t s = 0; s < n; ++s) inv[T.ord[s]] = s;
+  if (targets) {
+    for (int64_t k = 0; k < n_targets; ++k) is_target[inv[targets[k]]] = 1;
+  } else {
+    memset(is_target, 1, n);
+  }
+  /* leaves in node order are the target groups */
+  int64_t nleaf = 0, maxdepth = 0;
+  for (int64_t k = 0; k < T.nnode; ++k) {
+    if (T.node[k].nchild == 0) ++nleaf;
+    if (T.node[k].level > maxdepth) maxdepth = T.node[k].level;
+  }
+  int64_t *leaves = (int64_t *)malloc(sizeof(int64_t) * nleaf);
+  nleaf = 0;
+  for (int64_t k = 0; k < T.nnode; ++k) if (T.node[k].nchild == 0) leaves[nleaf++] = k;
+  int nth = or_num_threads();
+  cand_buf *cbs = (cand_buf *)calloc(nth, sizeof(cand_buf));
+  uint64_t npp = 0, npn = 0;
+  const double theta2 = p->theta * p->theta;
+#pragma omp parallel reduction(+ : npp, npn)
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    double (*acc)[3] = (double (*)[3])malloc(sizeof(double) * 3 * (p->leaf_size > 0 ? p->leaf_size : 1) + 3 * sizeof(double) * 64);
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t gi = 0; gi < nleaf; ++gi) {
+      const or_node *g = &T.node[leaves[gi]];
+      int any = 0;
+      for (int64_t s = g->first; s < g->first + g->count; ++s) any |= is_target[s];
+      if (!any) continue;
+      /* a leaf at level 21 may exceed leaf_size; grow the accumulator then */
+      double (*a)[3] = acc;
+      double (*big)[3] = NULL;
+      if (g->count > (p->leaf_size > 0 ? p->leaf_size : 1) + 64) {
+        big = (double (*)[3])malloc(sizeof(double) * 3 * g->count);
+        a = big;
+      }
+      memset(a, 0, sizeof(double) * 3 * g->count);
+      walk_ctx w = {&T, p, g, is_target, a, 0, 0, &cbs[tid], theta2};
+      walk(&w, 0);
+      for (int64_t s = g->first; s < g->first + g->count; ++s) {
+        if (!is_target[s]) continue;
+        int64_t i = T.ord[s];
+        ax[i] = a[s - g->first][0]; ay[i] = a[s - g->first][1]; az[i] = a[s - g->first][2];
+      }
+      npp += w.npp; npn += w.npn;
+      free(big);
+    }
+    free(acc);
+  }
+  int64_t nc = 0;
+  for (int t = 0; t < nth; ++t) {
+    for (int64_t k = 0; k < cbs[t].n; ++k) {
+      if (nc < cand_cap && cand_i && cand_j) { cand_i[nc] = cbs[t].ci[k]; cand_j[nc] = cbs[t].cj[k]; }
+      ++nc;
+    }
+    free(cbs[t].ci); free(cbs[t].cj);
+  }
+  free(cbs);
+  if (n_cand) *n_cand = nc;
+  if (counts) { counts[0] = npp; counts[1] = npn; }
+  if (tree_stats) {
+    tree_stats[0] = T.nnode; tree_stats[1] = nleaf; tree_stats[2] = maxdepth;
+    tree_stats[3] = 0;
+    for (int64_t k = 0; k < nleaf; ++k)
+      if (T.node[leaves[k]].count > tree_stats[3]) tree_stats[3] = T.node[leaves[k]].count;
+  }
+  free(leaves); free(is_target); free(inv);
+  tree_free(&T);
+  return 0;
+}
+
+/* ========================================================================= */
+/* Row a5: neighbour predicate, Sec. 2.3.                                    */
+/* Candidates: r_ij < r_search,ij = max(r_search,i, r_search,j) (Eq. rsearch  */
+/* and the individual-cut-off rule after it).  A candidate is dropped when    */
+/* its closest approach under linear motion over [0, dt] exceeds             */
+/* R~s,2 r_out,ij (Eq. rsearch1 with t_min; reading C5: "takes a maximum" is  */
+/* read as the minimum the t_min formula computes), unless                    */
+/* v_ij < R~s,3 a_ij dt/2 with a_ij = G (m_i + m_j) / r_ij^2.                 */
+/* All comparisons on squared FP64 quantities.                               */
+/* ========================================================================= */
+int or_neighbour_pair(int64_t i, int64_t j, const double *x, const double *y,
+                      const double *z, const double *vx, const double *vy,
+                      const double *vz, const double *m, const double *r_out,
+                      const double *r_search, const or_params *p) {
+  double rx = x[i] - x[j], ry = y[i] - y[j], rz = z[i] - z[j];
+  double r2 = rx * rx + ry * ry + rz * rz;
+  double rs = dmax(r_search[i], r_search[j]);
+  if (!(r2 < rs * rs)) return 0;
+  double ux = vx[i] - vx[j], uy = vy[i] - vy[j], uz = vz[i] - vz[j];
+  double v2 = ux * ux + uy * uy + uz * uz;
+  double rv = rx * ux + ry * uy + rz * uz;
+  double t = 0.0;
+  if (v2 > 0.0) {
+    t = -rv / v2;
+    if (t < 0.0) t = 0.0;
+    if (t >= p->dt_soft) t = p->dt_soft;
+  }
+  double dx = rx + ux * t, dy = ry + uy * t, dz = rz + uz * t;
+  double d2 = dx * dx + dy * dy + dz * dz;
+  double lim = p->rs2 * dmax(r_out[i], r_out[j]);
+  if (d2 <= lim * lim) return 1;
+  double a = p->G * (m[i] + m[j]) / r2;
+  double w = p->rs3 * a * p->dt_soft * 0.5;
+  return v2 < w * w;
+}
+
+static int cmp_i32(const void *a, const void *b) {
+  int32_t u = *(const int32_t *)a, v = *(const int32_t *)b;
+  return (u > v) - (u < v);
+}
+
+/* Assemble CSR rows from accepted (i, j) pairs; rows sorted by j, duplicates */
+/* removed.  Returns the number of entries (may exceed nb_cap: then only the  */
+/* offsets are valid and the caller retries with a larger capacity).          */
+static int64_t build_csr(int64_t n, int64_t npair, const int32_t *pi,
+                         const int32_t *pj, int64_t *nb_off, int32_t *nb_idx,
+                         int64_t nb_cap) {
+  int64_t *cnt = (int64_t *)calloc(n + 1, sizeof(int64_t));
+  for (int64_t k = 0; k < npair; ++k) cnt[pi[k]]++;
+  int32_t *tmp = (int32_t *)malloc(sizeof(int32_t) * (npair > 0 ? npair : 1));
+  int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (n + 1));
+  pos[0] = 0;
+  for (int64_t i = 0; i < n; ++i) pos[i + 1] = pos[i] + cnt[i];
+  int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (n + 1));
+  memcpy(fill, pos, sizeof(int64_t) * (n + 1));
+  for (int64_t k = 0; k < npair; ++k) tmp[fill[pi[k]]++] = pj[k];
+  int64_t tot = 0;
+  nb_off[0] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t *row = tmp + pos[i];
+    int64_t len = pos[i + 1] - pos[i];
+    qsort(row, len, sizeof(int32_t), cmp_i32);
+    for (int64_t k = 0; k < len; ++k) {
+      if (k > 0 && row[k] == row[k - 1]) continue;
+      if (tot < nb_cap && nb_idx) nb_idx[tot] = row[k];
+      ++tot;
+    }
+    nb_off[i + 1] = tot;
+  }
+  free(cnt); free(tmp); free(pos); free(fill);
+  return tot;
+}
+
+int64_t or_neighbours_from_candidates(
+    int64_t n, const double *x, const double *y, const double *z,
+    const double *vx, const double *vy, const double *vz, const double *m,
+    const double *r_out, const double *r_search, const or_params *p,
+    int64_t n_cand, const int32_t *cand_i, const int32_t *cand_j,
+    int64_t *nb_off, int32_t *nb_idx, int64_t nb_cap) {
+  int32_t *ki = (int32_t *)malloc(sizeof(int32_t) * (n_cand > 0 ? n_cand : 1));
+  int32_t *kj = (int32_t *)malloc(sizeof(int32_t) * (n_cand > 0 ? n_cand : 1));
+  int64_t nk = 0;
+  for (int64_t k = 0; k < n_cand; ++k) {
+    if (or_neighbour_pair(cand_i[k], cand_j[k], x, y, z, vx, vy, vz, m, r_out,
+                          r_search, p)) {
+      ki[nk] = cand_i[k]; kj[nk] = cand_j[k]; ++nk;
+    }
+  }
+  int64_t tot = build_csr(n, nk, ki, kj, nb_off, nb_idx, nb_cap);
+  free(ki); free(kj);
+  return tot;
+}
+
+int64_t or_neighbours_brute(int64_t n, const double *x, const double *y,
+                            const double *z, const double *vx, const double *vy,
+                            const double *vz, const double *m,
+                            const double *r_out, const double *r_search,
+                            const or_params *p, int64_t *nb_off,
+                            int32_t *nb_idx, int64_t nb_cap) {
+  cand_buf b = {0, 0, 0, 0};
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j)
+      if (j != i && or_neighbour_pair(i, j, x, y, z, vx, vy, vz, m, r_out, r_search, p))
+        cand_push(&b, (int32_t)i, (int32_t)j);
+  int64_t tot = build_csr(n, b.n, b.ci, b.cj, nb_off, nb_idx, nb_cap);
+  free(b.ci); free(b.cj);
+  return tot;
+}
+
+/* ========================================================================= */
+/* Row a6: neighbour clusters, Sec. 2.3 steps i-iii: every particle starts    */
+/* with its own index as cluster index; each particle takes the minimum of    */
+/* its own and its neighbours' indices; repeat until nothing changes.  Then   */
+/* compaction: isolated particles ascending; clusters of >= 2 members ordered */
+/* by label, members ascending.  Returns the size of the largest cluster.     */
+/* ========================================================================= */
+int64_t or_clusters(int64_t n, const int64_t *nb_off, const int32_t *nb_idx,
+                    int32_t *label, int64_t *n_single, int32_t *singles,
+                    int64_t *n_clusters, int64_t *cl_off, int32_t *cl_mem) {
+  for (int64_t i = 0; i < n; ++i) label[i] = (int32_t)i;
+  int changed = 1;
+  while (changed) {
+    changed = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      int32_t l = label[i];
+      for (int64_t k = nb_off[i]; k < nb_off[i + 1]; ++k)
+        if (label[nb_idx[k]] < l) l = label[nb_idx[k]];
+      if (l < label[i]) { label[i] = l; changed = 1; }
+    }
+  }
+  int64_t *size = (int64_t *)calloc(n > 0 ? n : 1, sizeof(int64_t));
+  for (int64_t i = 0; i < n; ++i) size[label[i]]++;
+  int64_t ns = 0, nc = 0, maxsz = n > 0 ? 1 : 0;
+  int64_t *cid = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+  for (int64_t i = 0; i < n; ++i) {
+    if (size[label[i]] == 1) { if (singles) singles[ns] = (int32_t)i; ++ns; }
+    if (label[i] == i && size[i] >= 2) {
+      cid[i] = nc++;
+      if (size[i] > maxsz) maxsz = size[i];
+    }
+  }
+  if (cl_off) {
+    cl_off[0] = 0;
+    int64_t c = 0;
+    for (int64_t i = 0; i < n; ++i)
+      if (label[i] == i && size[i] >= 2) { cl_off[c + 1] = cl_off[c] + size[i]; ++c; }
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (nc > 0 ? nc : 1));
+    for (int64_t k = 0; k < nc; ++k) fill[k] = cl_off[k];
+    for (int64_t i = 0; i < n; ++i)
+      if (size[label[i]] >= 2) cl_mem[fill[cid[label[i]]]++] = (int32_t)i;
+    free(fill);
+  }
+  if (n_single) *n_single = ns;
+  if (n_clusters) *n_clusters = nc;
+  free(size); free(cid);
+  return maxsz;
+}
+
+/* ========================================================================= */
+/* Row a7: soft velocity kick v += a_soft * h, h = dt/2 (procedure steps 3    */
+/* and 8, Eq. HamiltonSol).                                                   */
+/* ========================================================================= */
+void or_kick(int64_t n, double *vx, double *vy, double *vz, const double *ax,
+             const double *ay, const double *az, double h) {
+  for (int64_t i = 0; i < n; ++i) {
+    vx[i] += ax[i] * h; vy[i] += ay[i] * h; vz[i] += az[i] * h;
+  }
+}
+
+/* ========================================================================= */
+/* Row a8: hard force and jerk on member k of a cluster (Eq. hardforce):      */
+/*   a_k = -G M_* x_k / |x_k|^3 - sum_{j != k} G m_j (1 - K(y)) r / r^3,      */
+/* r = x_k - x_j, y = r / r_out,kj (reading C8: all other cluster members).   */
+/* The jerk is the time derivative, including dK/dt = K'(y) (r.v)/(r r_out).  */
+/* ========================================================================= */
+void or_hard_acc_jerk(int64_t nc, const double *x, const double *y,
+                      const double *z, const double *vx, const double *vy,
+                      const double *vz, const double *m, const double *r_out,
+                      const or_params *p, int64_t k, double acc[3],
+                      double jerk[3]) {
+  double ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0;
+  {
+    double r2 = x[k] * x[k] + y[k] * y[k] + z[k] * z[k];
+    double r = sqrt(r2);
+    double r3 = r2 * r;
+    double rv = x[k] * vx[k] + y[k] * vy[k] + z[k] * vz[k];
+    double gm = p->G * p->m_star;
+    ax -= gm * x[k] / r3; ay -= gm * y[k] / r3; az -= gm * z[k] / r3;
+    double c = 3.0 * rv / r2;
+    jx -= gm * (vx[k] - c * x[k]) / r3;
+    jy -= gm * (vy[k] - c * y[k]) / r3;
+    jz -= gm * (vz[k] - c * z[k]) / r3;
+  }
+  for (int64_t j = 0; j < nc; ++j) {
+    if (j == k) continue;
+    double rx = x[k] - x[j], ry = y[k] - y[j], rz = z[k] - z[j];
+    double ux = vx[k] - vx[j], uy = vy[k] - vy[j], uz = vz[k] - vz[j];
+    double r2 = rx * rx + ry * ry + rz * rz;
+    if (r2 == 0.0) continue;
+    double r = sqrt(r2);
+    double ro = dmax(r_out[k], r_out[j]);
+    double yv = r / ro;
+    if (yv >= 1.0) continue;
+    double w = 1.0 - or_changeover_K(yv, p->gamma);
+    double dK = or_changeover_dKdy(yv, p->gamma);
+    double r3 = r2 * r;
+    double rv = rx * ux + ry * uy + rz * uz;
+    double gm = p->G * m[j];
+    ax -= gm * w * rx / r3; ay -= gm * w * ry / r3; az -= gm * w * rz / r3;
+    /* d/dt [w r / r^3] = w v / r^3 - (3 w (r.v)/r^2 + K'(y) (r.v)/(r r_out)) r / r^3 */
+    double c = 3.0 * w * rv / r2 + dK * rv / (r * ro);
+    jx -= gm * (w * ux - c * rx) / r3;
+    jy -= gm * (w * uy - c * ry) / r3;
+    jz -= gm * (w * uz - c * rz) / r3;
+  }
+  acc[0] = ax; acc[1] = ay; acc[2] = az;
+  jerk[0] = jx; jerk[1] = jy; jerk[2] = jz;
+}
+
+/* Block time-step quantisation (reading C7): the largest dt_soft / 2^k not   */
+/* above the desired step, k <= 40, at most twice the previous step, and      */
+/* commensurate with the particle's current time (integer units of           */
+/* dt_soft / 2^40).  Sets *underflow when even dt_soft / 2^40 is too long.     */
+#define OR_KMAX 40
+static int quantise_level(double dt_des, double dt_soft, int prev_level,
+                          int64_t t_int, int *underflow) {
+  int lvl = 0;
+  while (lvl < OR_KMAX && ldexp(dt_soft, -lvl) > dt_des) ++lvl;
+  if (ldexp(dt_soft, -lvl) > dt_des) *underflow = 1;
+  if (lvl < prev_level - 1) lvl = prev_level - 1;
+  while (lvl < OR_KMAX && (t_int & ((((int64_t)1) << (OR_KMAX - lvl)) - 1)) != 0) ++lvl;
+  return lvl;
+}
+
+static double norm3(const double *v) { return sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]); }
+
+/* Fourth-order Hermite with block individual time steps over [0, dt] for one */
+/* cluster (Sec. 2.1.2, Makino 1991; Aarseth time steps).  Reading C7:        */
+/*  predictor  x_p = x + v D + a D^2/2 + j D^3/6, v_p = v + a D + j D^2/2;    */
+/*  corrector  a2 = (-6(a0-a1) - D(4 j0 + 2 j1))/D^2,                        */
+/*             a3 = (12(a0-a1) + 6 D (j0 + j1))/D^3,                          */
+/*             x = x_p + a2 D^4/24 + a3 D^5/120, v = v_p + a2 D^3/6 + a3 D^4/24;*/
+/*  new step   sqrt(eta (|a||a2'| + |j|^2)/(|j||a3| + |a2'|^2)), a2' = a2+D a3;*/
+/*  first step eta0 |a|/|j| (each hard step starts afresh, so every member's   */
+/*  first step of the hard step uses eta0).                                   */
+/* All members are predicted to each block time; the active ones are        */
+/* evaluated from the predicted state and then corrected together.           */
+int or_hermite_cluster(int64_t nc, const int32_t *members, double *X, double *Y,
+                       double *Z, double *VX, double *VY, double *VZ,
+                       const double *M, const double *RO, const or_params *p,
+                       double dt, int64_t *n_steps) {
+  const int64_t T = ((int64_t)1) << OR_KMAX;
+  const double unit = ldexp(dt, -OR_KMAX);
+  double *buf = (double *)malloc(sizeof(double) * nc * 26);
+  double *x = buf, *y = x + nc, *z = y + nc, *vx = z + nc, *vy = vx + nc, *vz = vy + nc;
+  double *px = vz + nc, *py = px + nc, *pz = py + nc, *pvx = pz + nc, *pvy = pvx + nc, *pvz = pvy + nc;
+  double *a = pvz + nc;   /* 3 nc */
+  double *jk = a + 3 * nc; /* 3 nc */
+  double *a1 = jk + 3 * nc, *j1 = a1 + 3 * nc;
+  double *m = j1 + 3 * nc, *ro = m + nc;
+  int64_t *t = (int64_t *)malloc(sizeof(int64_t) * nc);
+  int *lvl = (int *)malloc(sizeof(int) * nc);
+  unsigned char *act = (unsigned char *)malloc(nc);
+  int underflow = 0;
+  for (int64_t k = 0; k < nc; ++k) {
+    int32_t i = members[k];
+    x[k] = X[i]; y[k] = Y[i]; z[k] = Z[i]; vx[k] = VX[i]; vy[k] = VY[i]; vz[k] = VZ[i];
+    m[k] = M[i]; ro[k] = RO[i];
+  }
+  for (int64_t k = 0; k < nc; ++k) {
+    or_hard_acc_jerk(nc, x, y, z, vx, vy, vz, m, ro, p, k, a + 3 * k, jk + 3 * k);
+    double an = norm3(a + 3 * k), jn = norm3(jk + 3 * k);
+    double dtd = jn > 0.0 ? p->eta0 * an / jn : dt;
+    t[k] = 0;
+    lvl[k] = quantise_level(dtd, dt, 0, 0, &underflow);
+  }
+  int64_t steps = 0;
+  for (;;) {
+    int64_t tn = T;
+    for (int64_t k = 0; k < nc; ++k) {
+      int64_t e = t[k] + (T >> lvl[k]);
+      if (e < tn) tn = e;
+    }
+    int64_t tmin = T;
+    for (int64_t k = 0; k < nc; ++k) if (t[k] < tmin) tmin = t[k];
+    if (tmin >= T) break;
+    for (int64_t k = 0; k < nc; ++k) {
+      double D = (double)(tn - t[k]) * unit;
+      double D2 = D * D, D3 = D2 * D;
+      const double *ak = a + 3 * k, *jj = jk + 3 * k;
+      px[k] = x[k] + vx[k] * D + ak[0] * D2 / 2.0 + jj[0] * D3 / 6.0;
+      py[k] = y[k] + vy[k] * D + ak[1] * D2 / 2.0 + jj[1] * D3 / 6.0;
+      pz[k] = z[k] + vz[k] * D + ak[2] * D2 / 2.0 + jj[2] * D3 / 6.0;
+      pvx[k] = vx[k] + ak[0] * D + jj[0] * D2 / 2.0;
+      pvy[k] = vy[k] + ak[1] * D + jj[1] * D2 / 2.0;
+      pvz[k] = vz[k] + ak[2] * D + jj[2] * D2 / 2.0;
+      act[k] = (t[k] + (T >> lvl[k]) == tn);
+    }
+    for (int64_t k = 0; k < nc; ++k)
+      if (act[k]) or_hard_acc_jerk(nc, px, py, pz, pvx, pvy, pvz, m, ro, p, k, a1 + 3 * k, j1 + 3 * k);
+    for (int64_t k = 0; k < nc; ++k) {
+      if (!act[k]) continue;
+      double D = (double)(T >> lvl[k]) * unit;
+      double D2 = D * D, D3 = D2 * D, D4 = D3 * D, D5 = D4 * D;
+      double A2[3], A3[3], A2e[3];
+      for (int c = 0; c < 3; ++c) {
+        double da = a[3 * k + c] - a1[3 * k + c];
+        A2[c] = (-6.0 * da - D * (4.0 * jk[3 * k + c] + 2.0 * j1[3 * k + c])) / D2;
+        A3[c] = (12.0 * da + 6.0 * D * (jk[3 * k + c] + j1[3 * k + c])) / D3;
+        A2e[c] = A2[c] + D * A3[c];
+      }
+      x[k] = px[k] + A2[0] * D4 / 24.0 + A3[0] * D5 / 120.0;
+      y[k] = py[k] + A2[1] * D4 / 24.0 + A3[1] * D5 / 120.0;
+      z[k] = pz[k] + A2[2] * D4 / 24.0 + A3[2] * D5 / 120.0;
+      vx[k] = pvx[k] + A2[0] * D3 / 6.0 + A3[0] * D4 / 24.0;
+      vy[k] = pvy[k] + A2[1] * D3 / 6.0 + A3[1] * D4 / 24.0;
+      vz[k] = pvz[k] + A2[2] * D3 / 6.0 + A3[2] * D4 / 24.0;
+      for (int c = 0; c < 3; ++c) { a[3 * k + c] = a1[3 * k + c]; jk[3 * k + c] = j1[3 * k + c]; }
+      double an = norm3(a + 3 * k), jn = norm3(jk + 3 * k);
+      double a2n = norm3(A2e), a3n = norm3(A3);
+      double num = an * a2n + jn * jn, den = jn * a3n + a2n * a2n;
+      double dtd = den > 0.0 ? sqrt(p->eta * num / den) : dt;
+      t[k] = tn;
+      lvl[k] = quantise_level(dtd, dt, lvl[k], tn, &underflow);
+      ++steps;
+    }
+  }
+  for (int64_t k = 0; k < nc; ++k) {
+    int32_t i = members[k];
+    X[i] = x[k]; Y[i] = y[k]; Z[i] = z[k]; VX[i] = vx[k]; VY[i] = vy[k]; VZ[i] = vz[k];
+  }
+  if (n_steps) *n_steps = steps;
+  free(buf); free(t); free(lvl); free(act);
+  return underflow ? -4 : 0;
+}
+
+/* ========================================================================= */
+/* Row a9: Kepler drift of isolated particles (Sec. 2.1.2: "solving the       */
+/* Kepler equation with Newton-Raphson"; reading C9: mu = G M_*, no indirect  */
+/* term).  Gauss f and g functions written with the change of eccentric      */
+/* anomaly x = E - E0 (elliptic) or hyperbolic anomaly (hyperbolic):          */
+/*   elliptic:  n dt = x - c sin x + s (1 - cos x),                           */
+/*              c = 1 - r0/a, s = r0.v0 / sqrt(mu a);                         */
+/*   hyperbolic (A = -a > 0): n dt = c sinh x + s (cosh x - 1) - x,           */
+/*              c = 1 + r0/A, s = r0.v0 / sqrt(mu A).                         */
+/* Returns -1 for an (unsupported) exactly parabolic orbit.                   */
+/* ========================================================================= */
+static int kepler_one(double *X, double *V, double dt, double mu) {
+  double r0 = sqrt(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
+  double v2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+  double rv = X[0] * V[0] + X[1] * V[1] + X[2] * V[2];
+  double alpha = 2.0 / r0 - v2 / mu;
+  double f, g, fd, gd;
+  if (alpha > 0.0) {
+    double a = 1.0 / alpha;
+    double n = sqrt(mu / (a * a * a));
+    double c = 1.0 - r0 / a, s = rv / sqrt(mu * a);
+    /* strip whole orbits: f and g are periodic in x with period 2 pi */
+    double P = 2.0 * M_PI / n;
+    double k = floor(dt / P);
+    double dtr = dt - k * P;
+    double M = n * dtr;
+    double xk = M;
+    for (int it = 0; it < 100; ++it) {
+      double F = xk - c * sin(xk) + s * (1.0 - cos(xk)) - M;
+      double Fp = 1.0 - c * cos(xk) + s * sin(xk);
+      double dx = F / Fp;
+      xk -= dx;
+      if (fabs(dx) <= 1e-15 * (1.0 + fabs(xk))) break;
+    }
+    double cx = cos(xk), sx = sin(xk);
+    double r = a * (1.0 - c * cx + s * sx);
+    f = 1.0 - (a / r0) * (1.0 - cx);
+    g = dtr - (xk - sx) / n;
+    fd = -sqrt(mu * a) * sx / (r * r0);
+    gd = 1.0 - (a / r) * (1.0 - cx);
+  } else if (alpha < 0.0) {
+    double A = -1.0 / alpha;
+    double n = sqrt(mu / (A * A * A));
+    double c = 1.0 + r0 / A, s = rv / sqrt(mu * A);
+    double M = n * dt;
+    double xk = M * A / r0; /* first Newton iterate from the derivative at 0 */
+    if (xk > 5.0) xk = log(2.0 * M / c + 1.0);
+    for (int it = 0; it < 200; ++it) {
+      double ch = cosh(xk), sh = sinh(xk);
+      double F = c * sh + s * (ch - 1.0) - xk - M;
+      double Fp = c * ch + s * sh - 1.0;
+      double dx = F / Fp;
+      if (dx > 1.0) dx = 1.0;
+      if (dx < -1.0) dx = -1.0;
+      xk -= dx;
+      if (fabs(dx) <= 1e-15 * (1.0 + fabs(xk))) break;
+    }
+    double ch = cosh(xk), sh = sinh(xk);
+    double r = A * (c * ch + s * sh - 1.0);
+    f = 1.0 - (A / r0) * (ch - 1.0);
+    g = dt - (sh - xk) / n;
+    fd = -sqrt(mu * A) * sh / (r * r0);
+    gd = 1.0 - (A / r) * (ch - 1.0);
+  } else {
+    return -1;
+  }
+  double nx[3], nv[3];
+  for (int c = 0; c < 3; ++c) {
+    nx[c] = f * X[c] + g * V[c];
+    nv[c] = fd * X[c] + gd * V[c];
+  }
+  for (int c = 0; c < 3; ++c) { X[c] = nx[c]; V[c] = nv[c]; }
+  return 0;
+}
+
+int or_kepler_drift(int64_t n, const int32_t *idx, double *x, double *y,
+                    double *z, double *vx, double *vy, double *vz, double dt,
+                    double mu) {
+  int err = 0;
+#pragma omp parallel for schedule(static) reduction(| : err)
+  for (int64_t k = 0; k < n; ++k) {
+    int64_t i = idx ? idx[k] : k;
+    double X[3] = {x[i], y[i], z[i]}, V[3] = {vx[i], vy[i], vz[i]};
+    if (kepler_one(X, V, dt, mu) != 0) { err |= 1; continue; }
+    x[i] = X[0]; y[i] = X[1]; z[i] = X[2]; vx[i] = V[0]; vy[i] = V[1]; vz[i] = V[2];
+  }
+  return err ? -1 : 0;
+}
+
+/* Hard part of one soft step (procedure step 5): Hermite for every cluster   */
+/* of >= 2 members, Kepler drift for isolated particles.                      */
+int or_hard_step(int64_t n, double *x, double *y, double *z, double *vx,
+                 double *vy, double *vz, const double *m, const double *r_out,
+                 const or_params *p, double dt, int64_t n_single,
+                 const int32_t *singles, int64_t n_clusters,
+                 const int64_t *cl_off, const int32_t *cl_mem,
+                 int64_t *n_hermite_steps) {
+  (void)n;
+  int err = or_kepler_drift(n_single, singles, x, y, z, vx, vy, vz, dt, p->G * p->m_star);
+  int64_t steps = 0;
+  int herr = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : steps) reduction(| : herr)
+  for (int64_t c = 0; c < n_clusters; ++c) {
+    int64_t ns = 0;
+    int e = or_hermite_cluster(cl_off[c + 1] - cl_off[c], cl_mem + cl_off[c], x, y, z,
+                               vx, vy, vz, m, r_out, p, dt, &ns);
+    if (e) herr |= 1;
+    steps += ns;
+  }
+  if (n_hermite_steps) *n_hermite_steps = steps;
+  if (err) return -1;
+  return herr ? -4 : 0;
+}
+
+/* ========================================================================= */
+/* Row a10: total energy.  H_soft + H_hard (Eqs. soft, hard) with             */
+/* W + (1 - W) = 1 is the Newtonian energy                                    */
+/*   E = sum m v^2 / 2 - sum G M_* m / r - sum_{i<j} G m_i m_j / r_ij.        */
+/* out = {E, kinetic, star potential, pair potential}.                       */
+/* ========================================================================= */
+void or_energy(int64_t n, const double *x, const double *y, const double *z,
+               const double *vx, const double *vy, const double *vz,
+               const double *m, double G, double m_star, double out[4]) {
+  double ek = 0.0, es = 0.0, ep = 0.0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : ek, es, ep)
+  for (int64_t i = 0; i < n; ++i) {
+    ek += 0.5 * m[i] * (vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i]);
+    es -= G * m_star * m[i] / sqrt(x[i] * x[i] + y[i] * y[i] + z[i] * z[i]);
+    double s = 0.0;
+    for (int64_t j = i + 1; j < n; ++j) {
+      double rx = x[i] - x[j], ry = y[i] - y[j], rz = z[i] - z[j];
+      s += m[j] / sqrt(rx * rx + ry * ry + rz * rz);
+    }
+    ep -= G * m[i] * s;
+  }
+  out[0] = ek + es + ep; out[1] = ek; out[2] = es; out[3] = ep;
+}
