@@ -152,18 +152,25 @@ int or_direct_soft(int64_t n, const double *x, const double *y, const double *z,
 
 /* ========================================================================= */
 /* Rows a2-a4: the Barnes-Hut tree (Sec. 2.1.2 uses FDPS's tree; the discrete */
-/* definitions below are reading C4).                             */
+/* definitions below are reading C4).                                         */
 /*  * root cube: bounding box of the positions, made cubic (side L = largest  */
 /*    extent), corner at the per-axis minimum;                                */
-/*  * each axis quantised to 21 bits, bits interleaved (x highest) into a     */
-/*    63-bit Morton key; particles ordered by (key, caller index);            */
+/*  * each axis quantised to q in [0, 2^21) (unit u = L / 2^21), bits          */
+/*    interleaved (x highest) into a 63-bit Morton key; particles ordered by  */
+/*    (key, caller index);                                                    */
 /*  * a node is a key prefix at level l holding > 0 particles; a node is      */
 /*    split while it holds more than leaf_size particles and l < 21;          */
-/*  * target groups are the leaves.  A node is opened for a group if          */
-/*    (i) side^2 > theta^2 d^2(cube centre, group box)  [Barnes-Hut], or      */
-/*    (ii) dist^2(group box, node box) < max(rsmax_group, rsmax_node)^2       */
-/*    [cut-off reach], with tight boxes of particle positions.  Accepted      */
-/*    nodes add monopole + quadrupole; opened leaves add changeover pairs.    */
+/*  * target groups are the leaves.  Opening is decided on the quantised      */
+/*    grid, in exact integer arithmetic:                                      */
+/*    (i) Barnes-Hut: with the node's cell side s and centre c, and the       */
+/*        group's cells [qlo, qhi + 1] (all in half units), open iff          */
+/*        d^2 < ceil((2 s)^2 / theta^2), d the point-box distance;  this is   */
+/*        side^2 > theta^2 d^2 on the grid;                                   */
+/*    (ii) cut-off reach: per axis gap g = max(0, qlo_b - qhi_a - 2, ...)     */
+/*        (a lower bound of the true gap in units of u), R = ceil(rsmax/u)+1  */
+/*        per node; open iff g^2 < max(R_group, R_node)^2.  Every pair closer */
+/*        than max(r_search,i, r_search,j) therefore meets in an opened leaf. */
+/*    Accepted nodes add monopole + quadrupole; opened leaves add pairs.      */
 /* ========================================================================= */
 #define OR_BITS 21
 #define OR_QMAX ((int64_t)1 << OR_BITS)
@@ -217,7 +224,9 @@ typedef struct {
   double M, com[3], Q[6]; /* Q = sum m (3 d_a d_b - d^2 delta_ab): xx yy zz xy xz yz */
   double lo[3], hi[3];    /* tight box of the particle positions */
   double rsmax;           /* max r_search over the node's particles */
-  double cen[3], side;    /* the node's cube (dyadic subdivision of the root) */
+  int64_t qlo[3], qhi[3]; /* quantised tight box (cells) of the particles */
+  int64_t c2[3];          /* cell centre of the node, in half units of u */
+  int64_t R;              /* ceil(rsmax / u) + 1, clamped to 2^23 */
 } or_node;
 
 typedef struct {
@@ -306,13 +315,22 @@ static void fill_node(or_tree *T, or_node *nd) {
     nd->lo[2] = dmin(nd->lo[2], T->z[i]); nd->hi[2] = dmax(nd->hi[2], T->z[i]);
     nd->rsmax = dmax(nd->rsmax, T->rs[i]);
   }
-  /* the node's cube: integer cell coordinates at its level, from any member */
+  /* quantised box, cell centre and search reach on the grid */
+  for (int a = 0; a < 3; ++a) { nd->qlo[a] = OR_QMAX; nd->qhi[a] = -1; }
+  for (int64_t i = f; i < f + c; ++i) {
+    const int64_t q[3] = {T->qx[i], T->qy[i], T->qz[i]};
+    for (int a = 0; a < 3; ++a) {
+      if (q[a] < nd->qlo[a]) nd->qlo[a] = q[a];
+      if (q[a] > nd->qhi[a]) nd->qhi[a] = q[a];
+    }
+  }
   int sh = OR_BITS - nd->level;
-  double side = ldexp(T->box[3], -nd->level);
-  nd->side = side;
-  nd->cen[0] = T->box[0] + ((double)(T->qx[f] >> sh) + 0.5) * side;
-  nd->cen[1] = T->box[1] + ((double)(T->qy[f] >> sh) + 0.5) * side;
-  nd->cen[2] = T->box[2] + ((double)(T->qz[f] >> sh) + 0.5) * side;
+  nd->c2[0] = (2 * (T->qx[f] >> sh) + 1) << sh;
+  nd->c2[1] = (2 * (T->qy[f] >> sh) + 1) << sh;
+  nd->c2[2] = (2 * (T->qz[f] >> sh) + 1) << sh;
+  double u = ldexp(T->box[3], -OR_BITS);
+  double rq = ceil(nd->rsmax / u) + 1.0;
+  nd->R = rq < 8388608.0 ? (int64_t)rq : 8388608;
 }
 
 static void tree_build(or_tree *T, int64_t n, const double *x, const double *y,
@@ -378,27 +396,34 @@ static void tree_free(or_tree *T) {
   free(T->node);
 }
 
+/* Barnes-Hut thresholds per level (reading C4): open iff d^2 < T[l] with    */
+/* T[l] = ceil((2^(22-l))^2 / theta^2) in half units; theta = 0 opens all.    */
+static void bh_thresholds(double theta, int64_t T[OR_BITS + 1]) {
+  const double big = 4611686018427387904.0; /* 2^62 */
+  double th2 = theta * theta;
+  for (int l = 0; l <= OR_BITS; ++l) {
+    double X = th2 > 0.0 ? ldexp(1.0, 2 * (OR_BITS + 1 - l)) / th2 : big;
+    X = ceil(X);
+    T[l] = X < big ? (int64_t)X : (int64_t)4611686018427387904LL;
+  }
+}
+
 /* Opening decision for node nd seen from target group g (reading C4). */
-static int mac_open(const or_node *g, const or_node *nd, double theta2) {
-  /* (i) Barnes-Hut: distance from the node's cube centre to the group box */
-  double d2 = 0.0;
+static int mac_open(const or_node *g, const or_node *nd, const int64_t *bh) {
+  int64_t d2 = 0, g2 = 0;
   for (int a = 0; a < 3; ++a) {
-    double d = 0.0;
-    if (nd->cen[a] < g->lo[a]) d = g->lo[a] - nd->cen[a];
-    else if (nd->cen[a] > g->hi[a]) d = nd->cen[a] - g->hi[a];
-    d2 = d2 + d * d;
+    int64_t lo = 2 * g->qlo[a], hi = 2 * g->qhi[a] + 2, d = 0;
+    if (nd->c2[a] < lo) d = lo - nd->c2[a];
+    else if (nd->c2[a] > hi) d = nd->c2[a] - hi;
+    d2 += d * d;
+    int64_t gap = 0;
+    if (nd->qlo[a] - g->qhi[a] - 2 > gap) gap = nd->qlo[a] - g->qhi[a] - 2;
+    if (g->qlo[a] - nd->qhi[a] - 2 > gap) gap = g->qlo[a] - nd->qhi[a] - 2;
+    g2 += gap * gap;
   }
-  if (nd->side * nd->side > theta2 * d2) return 1;
-  /* (ii) cut-off reach: box-box distance against the larger search radius */
-  double b2 = 0.0;
-  for (int a = 0; a < 3; ++a) {
-    double d = 0.0;
-    if (nd->lo[a] > g->hi[a]) d = nd->lo[a] - g->hi[a];
-    else if (g->lo[a] > nd->hi[a]) d = g->lo[a] - nd->hi[a];
-    b2 = b2 + d * d;
-  }
-  double rs = dmax(g->rsmax, nd->rsmax);
-  return b2 < rs * rs;
+  if (d2 < bh[nd->level]) return 1;
+  int64_t R = g->R > nd->R ? g->R : nd->R;
+  return g2 < R * R;
 }
 
 typedef struct {
@@ -423,14 +448,14 @@ typedef struct {
   double (*acc)[3]; /* accumulators of the group's targets (indexed s - first) */
   uint64_t npp, npn;
   cand_buf *cb;
-  double theta2;
+  const int64_t *bh;
 } walk_ctx;
 
 static void walk(walk_ctx *w, int64_t k) {
   const or_tree *T = w->T;
   const or_node *nd = &T->node[k];
   const or_node *g = w->g;
-  if (!mac_open(g, nd, w->theta2)) {
+  if (!mac_open(g, nd, w->bh)) {
     double mom[10] = {nd->M, nd->com[0], nd->com[1], nd->com[2], nd->Q[0],
                       nd->Q[1], nd->Q[2], nd->Q[3], nd->Q[4], nd->Q[5]};
     for (int64_t s = g->first; s < g->first + g->count; ++s) {
@@ -496,7 +521,8 @@ int or_tree_soft(int64_t n, const double *x, const double *y, const double *z,
   int nth = or_num_threads();
   cand_buf *cbs = (cand_buf *)calloc(nth, sizeof(cand_buf));
   uint64_t npp = 0, npn = 0;
-  const double theta2 = p->theta * p->theta;
+  int64_t bh[OR_BITS + 1];
+  bh_thresholds(p->theta, bh);
 #pragma omp parallel reduction(+ : npp, npn)
   {
     int tid = 0;
@@ -518,7 +544,7 @@ int or_tree_soft(int64_t n, const double *x, const double *y, const double *z,
         a = big;
       }
       memset(a, 0, sizeof(double) * 3 * g->count);
-      walk_ctx w = {&T, p, g, is_target, a, 0, 0, &cbs[tid], theta2};
+      walk_ctx w = {&T, p, g, is_target, a, 0, 0, &cbs[tid], bh};
       walk(&w, 0);
       for (int64_t s = g->first; s < g->first + g->count; ++s) {
         if (!is_target[s]) continue;
