@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Soft-step benchmark of the P3T integrator with individual cut-off radii.
+
+One "step" is one full soft step of the paper's procedure (steps 3-8): kick,
+hard part (Hermite clusters + Kepler drift), tree build, soft force walk,
+neighbour lists + clusters, kick -- all in libp3t's kernels.  Workload: the
+N = 10^6 wide disk on 1-10 au (power-law planetesimals on [1e-12, 1e-8] plus
+20 protoplanets of 1e-7; e/i rms 2h and h), theta = 0.5, leaf 16,
+dt = 1/64, mixed precision.  Synthetic, seeded (seed 1003).
+
+Reported value: pair interactions (p-p + p-node terms of the soft force) per
+second of whole-step wall time.  Also reported: the soft-step time, Hermite
+particle-steps per second, per-phase times, a roofline entry for the tree walk
+(FP32-bound, algorithmic FLOPs), an end-to-end number through the C ABI with
+host buffers, and the CPU oracle timed on a bounded sample.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): independent replicas, one per rank (the soft step of one
+disk does not shard across GPUs here); value = sum over ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "soft-step wall time & pair-interactions/s at N=1e6; hard-part Hermite steps/s"
+UNIT = "pair-interactions/s"
+# algorithmic work per unit (counted from the method): changeover pair term
+# ~30 flops + rsqrt, monopole + quadrupole node term ~70 flops + rsqrt
+FLOP_PP, FLOP_PN = 30.0, 70.0
+# FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 (FMA)
+# x 2.07 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=16)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-targets", type=int, default=16384,
+                    help="targets of the CPU oracle's timed walk sample")
+    return ap.parse_args()
+
+
+def workload(n, seed=1003):
+    from paper_2007_15432_gb300 import disks
+    return disks.wide_power_law(n=n, seed=seed)
+
+
+def workload_name(n):
+    return (f"wide power-law disk N={n} (1-10 au, m in [1e-12,1e-8] dN/dm~m^-2.5 + 20 "
+            "protoplanets 1e-7, e/i rms 2h/h), theta=0.5, leaf 16, dt=1/64")
+
+
+# ---------------------------------------------------------------- clocks -----
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return dict(sm_mhz=float(np.median(sm)) if sm else None,
+                    sm_max_mhz=float(max(smax)) if smax else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+# ------------------------------------------------------------ distributed ----
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        return rank, local, world, dist
+    return rank, local, world, None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def allmax(dist, v):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allsum(dist, v):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------- CPU oracle ----
+def oracle_step_estimate(s, n_targets, seed=7):
+    """The CPU oracle on a bounded sample of the same workload.
+
+    Timed: the full tree build at N (keys, sort, octree, moments), the walk for
+    a random sample of targets (scaled to all N), and the Kepler drift of all
+    particles.  Returns (interactions per step, seconds per step, info)."""
+    from oracle import oracle as O
+    p = O.Params(theta=0.5)
+    ro, rs, _, _ = O.cutoffs(s, p)
+    n = len(s["m"])
+    rng = np.random.default_rng(seed)
+    tg = rng.choice(n, size=min(n_targets, n), replace=False)
+    t0 = time.perf_counter()
+    O.tree_soft(s, ro, rs, p, targets=np.array([0]), cand_cap=1 << 20)
+    t_tree = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    res = O.tree_soft(s, ro, rs, p, targets=tg, cand_cap=1 << 22)
+    t_walk = time.perf_counter() - t0 - t_tree
+    scale = n / len(tg)
+    inter = (res.n_pp + res.n_pnode) * scale
+    sk = {k: np.array(s[k], copy=True) for k in ("x", "y", "z", "vx", "vy", "vz", "m")}
+    t0 = time.perf_counter()
+    O.kepler_drift(sk, 1.0 / 64, 1.0)
+    t_kep = time.perf_counter() - t0
+    step = t_tree + max(t_walk, 0.0) * scale + t_kep
+    info = dict(t_tree_s=t_tree, t_walk_sample_s=t_walk, t_kepler_s=t_kep,
+                sample_targets=len(tg), threads=O.num_threads())
+    return inter, step, info
+
+
+def run_reference(args):
+    rank, local, world, dist = dist_setup(args)
+    if rank != 0:
+        return 0
+    s = workload(args.n)
+    from oracle import oracle as O
+    O.build()
+    times, inter = [], 0.0
+    for k in range(args.warmup + args.steps):
+        i, t, info = oracle_step_estimate(s, args.cpu_targets, seed=100 + k)
+        if k >= args.warmup:
+            times.append(t)
+            inter += i
+    tot = float(np.sum(times))
+    value = inter / tot
+    sample = (f"per step: oracle tree build at N={args.n}, walk of {info['sample_targets']} "
+              f"random targets scaled by N/targets, Kepler drift of all N")
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * tot / args.steps, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                impl="reference",
+                config=dict(workload=workload_name(args.n), n=args.n, precision="fp64 (CPU oracle)"),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=info["threads"], kind="oracle",
+                                  sample=sample),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ ours -----
+def run_ours(args):
+    rank, local, world, dist = dist_setup(args)
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2007_15432_gb300 import build
+    build.build()
+    from paper_2007_15432_gb300 import p3t as P
+
+    s = workload(args.n, seed=1003 + 1000 * rank)
+    n = len(s["m"])
+    prec = P.P3T_MIXED if args.precision == "mixed" else P.P3T_FP64
+    prm = P.Params(theta=0.5, precision=prec, eta=0.01, eta0=0.001)
+    st = P.State.from_numpy(s, device=dev)
+    ss = P.SoftStep(prm, st, device=local)
+    stream = torch.cuda.current_stream(dev)
+    ss.init(update_cutoffs=True)            # row a1 at init; radii then held fixed
+    torch.cuda.synchronize(dev)
+    ss.status()
+
+    K, W = args.steps, args.warmup
+    counts_all = torch.zeros(K, 2, dtype=torch.int64, device=dev)
+    hsteps_all = torch.zeros(K, dtype=torch.int64, device=dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(K)]
+    h = 0.5 * prm.dt_soft
+
+    def step(k=None):
+        e = ev[k] if k is not None else None
+        if e: e[0].record(stream)
+        P.p3t_kick(ss.ctx, st, ss.acc, h, stream)
+        P.p3t_hard_step(ss.ctx, st, ss.cl, prm.dt_soft,
+                        hsteps_all[k:k + 1] if k is not None else ss.hsteps, stream)
+        if e: e[1].record(stream)
+        P.p3t_build_tree(ss.ctx, st, False, stream)
+        if e: e[2].record(stream)
+        P.p3t_soft_force(ss.ctx, st, ss.acc, counts_all[k] if k is not None else ss.counts, stream)
+        if e: e[3].record(stream)
+        ss.cl = P.p3t_neighbours(ss.ctx, st, ss.nb_off, ss.nb_idx, stream)
+        if e: e[4].record(stream)
+        P.p3t_kick(ss.ctx, st, ss.acc, h, stream)
+        if e: e[5].record(stream)
+
+    for _ in range(W):
+        step()
+    torch.cuda.synchronize(dev)
+    ss.status()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(dist)
+    torch.cuda.synchronize(dev)
+    launches0 = P.p3t_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(K):
+        step(k)
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = P.p3t_launch_count() - launches0
+    barrier(dist)
+    clk = clocks.stop()
+    ss.status()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    phase = np.zeros(5)
+    for k in range(K):
+        e = ev[k]
+        phase += [e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3]),
+                  e[3].elapsed_time(e[4]), e[4].elapsed_time(e[5])]
+    phase /= K
+    c = counts_all.cpu().numpy()
+    inter = float(c.sum())
+    hsteps = float(hsteps_all.sum().item())
+    walk_s = phase[2] / 1e3
+    flops_per_launch = (FLOP_PP * c[:, 0] + FLOP_PN * c[:, 1]).mean()
+
+    # ---- end to end through the C ABI with host buffers --------------------
+    keys = ("x", "y", "z", "vx", "vy", "vz", "m", "r_out", "r_search")
+    host = {k: getattr(st, k).cpu().pin_memory() for k in keys}
+    out_keys = ("x", "y", "z", "vx", "vy", "vz")
+    host_out = {k: torch.empty_like(host[k]).pin_memory() for k in out_keys}
+    h2d = sum(host[k].numel() * 8 for k in keys)
+    d2h = sum(host_out[k].numel() * 8 for k in out_keys)
+    E = max(1, args.e2e_steps)
+    e2e_counts = torch.zeros(E, 2, dtype=torch.int64, device=dev)
+    torch.cuda.synchronize(dev)
+    barrier(dist)
+    t0 = time.perf_counter()
+    for k in range(E):
+        for key in keys:
+            getattr(st, key).copy_(host[key], non_blocking=True)
+        P.p3t_kick(ss.ctx, st, ss.acc, h, stream)
+        P.p3t_hard_step(ss.ctx, st, ss.cl, prm.dt_soft, ss.hsteps, stream)
+        P.p3t_build_tree(ss.ctx, st, False, stream)
+        P.p3t_soft_force(ss.ctx, st, ss.acc, e2e_counts[k], stream)
+        ss.cl = P.p3t_neighbours(ss.ctx, st, ss.nb_off, ss.nb_idx, stream)
+        P.p3t_kick(ss.ctx, st, ss.acc, h, stream)
+        for key in out_keys:
+            host_out[key].copy_(getattr(st, key), non_blocking=True)
+        torch.cuda.synchronize(dev)
+        for key in out_keys:   # the result is the next step's input
+            host[key], host_out[key] = host_out[key], host[key]
+    t_e2e = time.perf_counter() - t0
+    e2e_inter = float(e2e_counts.sum().item())
+    ss.status()
+
+    tot_elapsed = allmax(dist, elapsed)
+    tot_inter = allsum(dist, inter)
+    tot_e2e_t = allmax(dist, t_e2e)
+    tot_e2e_inter = allsum(dist, e2e_inter)
+    if rank != 0:
+        return 0
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        i_cpu, t_cpu, info = oracle_step_estimate(workload(args.n), args.cpu_targets)
+        cpu = dict(value=i_cpu / t_cpu, unit=UNIT, cores=info["threads"], kind="oracle",
+                   sample=(f"oracle tree build at N={args.n} + walk of {info['sample_targets']} "
+                           f"random targets scaled by N/targets + Kepler drift of all N; "
+                           f"{t_cpu:.2f} s per estimated step"))
+    achieved = flops_per_launch / walk_s / 1e12
+    line = dict(
+        metric=METRIC, value=tot_inter / tot_elapsed, unit=UNIT, n_gpus=world, steps=K,
+        warmup=W, ms_per_step=1e3 * elapsed / K, higher_is_better=True, scaling="weak",
+        vs_baseline=None, dtype="f32/f64" if prec == P.P3T_MIXED else "f64",
+        data="synthetic (seeded disk)",
+        config=dict(workload=workload_name(n), n=n,
+                    precision=args.precision, l2="per-step working set > L2 (inputs ~0.5 GB)",
+                    parallelism="replicas only" if world > 1 else "single GPU"),
+        soft_step_ms=1e3 * elapsed / K,
+        hermite_steps_per_s=hsteps / elapsed,
+        interactions_per_step=inter / K,
+        phases_ms=dict(kick_and_hard=phase[0], tree=phase[1], soft_force=phase[2],
+                       neighbours_clusters=phase[3], kick=phase[4]),
+        roofline=dict(kernel="k_walk (mixed) + FP64 refinement", bound="alu",
+                      achieved=achieved, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
+                      frac=achieved / FP32_PEAK_TFLOPS, traffic=None),
+        e2e=dict(value=tot_e2e_inter / tot_e2e_t, unit=UNIT, h2d_bytes_per_step=h2d,
+                 d2h_bytes_per_step=d2h),
+        gpu_launches=int(launches),
+        clocks=clk,
+        cpu_baseline=cpu,
+    )
+    print(json.dumps(line), flush=True)
+    ss.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

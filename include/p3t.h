@@ -1,0 +1,226 @@
+/*
+ * p3t.h -- C ABI of libp3t, the GB300 (sm_103a) soft step of the
+ * particle-particle particle-tree (P3T) planetary N-body integrator with
+ * individual cut-off radii (Ishigaki, Kominami, Makino, Fujimoto & Iwasawa
+ * 2021, PASJ 73, 660: "GPLUM").
+ *
+ * One soft step (Sec. 2.2, procedure steps 3-8; Eq. HamiltonSol) is
+ *
+ *   p3t_kick        v += a_soft dt/2
+ *   p3t_hard_step   Hermite-4 for every neighbour cluster, Kepler drift for
+ *                   isolated particles, over dt
+ *   p3t_build_tree  Morton keys, sort, octree with monopole + quadrupole
+ *   p3t_soft_force  tree walk with the changeover function -> a_soft,
+ *                   neighbour candidates, interaction counts
+ *   p3t_neighbours  neighbour lists (CSR) and neighbour clusters
+ *   p3t_kick        v += a_soft dt/2
+ *
+ * Conventions shared by every entry point
+ *  - Particles are structure-of-arrays of FP64 in the CALLER's order; every
+ *    output is in the caller's order too (the library sorts internally and
+ *    scatters back).  Particle indices are int32 (n < 2^31), CSR offsets int64.
+ *  - Unless stated otherwise a pointer argument is a DEVICE pointer on the
+ *    context's device, owned by the caller, and must stay valid until the
+ *    work queued on the stream has finished.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every compute entry point only enqueues work: it neither
+ *    allocates (once p3t_reserve has sized the context) nor synchronises, so
+ *    a sequence of calls can be captured into a CUDA graph.
+ *  - Return value: 0 or a negative P3T_ERR_* code for errors detected on the
+ *    host (bad arguments, failed launches).  Errors found while the kernels
+ *    run (a full buffer, a Hermite step below dt/2^40) are recorded on the
+ *    device, are sticky, and are read and cleared by p3t_status.
+ *  - Kernels never trap and never spin without a bound.
+ *  - Units are the caller's; the paper uses G = M_* = 1, au, yr/2pi (Sec. 3.1).
+ */
+#ifndef P3T_H
+#define P3T_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define P3T_OK 0
+#define P3T_ERR_INVALID (-1)       /* bad argument, parameter or call order   */
+#define P3T_ERR_CUDA (-2)          /* a CUDA runtime call or launch failed     */
+#define P3T_ERR_CAPACITY (-3)      /* an output or internal buffer is too small;
+                                      p3t_status reports the size needed      */
+#define P3T_ERR_DT_UNDERFLOW (-4)  /* a Hermite step fell below dt / 2^40      */
+#define P3T_ERR_TIMEOUT (-5)       /* a bounded device loop gave up            */
+
+#define P3T_FP64 0   /* every step in FP64                                     */
+#define P3T_MIXED 1  /* pair arithmetic of the soft force in FP32 on relative
+                        coordinates of FP64 accuracy (float-float split),
+                        FP32 pair terms folded into float-float accumulators;
+                        FP64 state, tree, neighbour search, Hermite, Kepler   */
+
+/* ---- method parameters (defaults: the paper's values, Sec. 3.1) --------- */
+typedef struct {
+  double G;        /* gravitational constant                                  */
+  double m_star;   /* mass of the central star M_*                            */
+  double dt_soft;  /* soft step Delta t (Eq. HamiltonSol); used by the cut-off
+                      and neighbour rules (Eqs. routi2, rsearch, rsearch1)     */
+  double gamma;    /* r_in / r_out of the changeover, 0 < gamma < 1 (Sec. 2.1.1) */
+  double rcut0;    /* R~cut,0: Hill-radius factor (Eq. routi2)                 */
+  double rcut1;    /* R~cut,1: random-velocity factor (Eq. routi2), paper: 8   */
+  double rs0, rs1; /* R~search,0 / R~search,1 (Eq. rsearch), paper: 1.1, 6     */
+  double rs2, rs3; /* R~search,2 / R~search,3 (Eq. rsearch1), paper: 2, 2      */
+  double theta;    /* Barnes-Hut opening angle (Sec. 3.1: 0.1 or 0.5); 0 =
+                      direct summation                                        */
+  double eta;      /* Hermite accuracy parameter (Sec. 3.1: 0.01)             */
+  double eta0;     /* Hermite first-step parameter (Sec. 3.1: 0.1 eta)        */
+  int32_t leaf_size; /* max particles per leaf = per target group, 1..32      */
+  int32_t precision; /* P3T_FP64 or P3T_MIXED                                  */
+  int32_t vran_bins; /* radial bins for v_ran; 0 = clamp(N/1000, 1, 1024)      */
+  int32_t reserved;  /* must be 0                                              */
+} p3t_params;
+
+/* ---- particles ---------------------------------------------------------- */
+typedef struct {
+  int64_t n;                       /* number of particles, 0 <= n < 2^31     */
+  double *x, *y, *z;               /* positions, n each                      */
+  double *vx, *vy, *vz;            /* velocities, n each                     */
+  double *m;                       /* masses, n, > 0                         */
+  double *r_out, *r_search;        /* cut-off and search radii, n each; written
+                                      by p3t_cutoffs (or p3t_build_tree with
+                                      update_cutoffs = 1), read by the rest   */
+} p3t_particles;
+
+/* ---- neighbour clusters: library-owned device views ---------------------- */
+typedef struct {
+  const int32_t *label;   /* n: smallest particle index of the particle's
+                             neighbour cluster (Sec. 2.3, steps i-iii)        */
+  const int32_t *singles; /* counts[0]: isolated particles, ascending          */
+  const int64_t *cl_off;  /* counts[1] + 1: offsets of clusters of >= 2       */
+  const int32_t *cl_mem;  /* counts[2]: members, clusters ordered by label,
+                             members ascending                                 */
+  const int64_t *counts;  /* device int64[4]: n_single, n_clusters, n_members,
+                             size of the largest cluster                       */
+} p3t_clusters;
+
+typedef struct p3t_ctx p3t_ctx;
+
+/* Creates a context on CUDA device `device` with parameters *p (copied).
+ * The context owns the tree, the sorted copies, all scratch and the cluster
+ * views.  Returns P3T_ERR_INVALID for out-of-range parameters. */
+int p3t_create(p3t_ctx **ctx, const p3t_params *p, int device);
+
+/* Frees everything the context owns (synchronises its device first). */
+void p3t_destroy(p3t_ctx *ctx);
+
+/* Replaces the parameters (host call; takes effect for work enqueued after). */
+int p3t_set_params(p3t_ctx *ctx, const p3t_params *p);
+
+/* Sizes every internal buffer for up to n particles (allocates, so call it
+ * before any graph capture).  Compute calls with a larger n grow the context
+ * themselves, which allocates and is then not capturable. */
+int p3t_reserve(p3t_ctx *ctx, int64_t n);
+
+/* Row a1 -- cut-off and search radii, Eq. routi2 and Eq. rsearch:
+ *   r_out,i    = max(R~cut,0 r_Hill,i, R~cut,1 v_ran,i dt_soft),
+ *   r_Hill,i   = (m_i / 3M_*)^(1/3) a_i, a_i the osculating semi-major axis
+ *                (a_i = |x_i| for an unbound orbit),
+ *   r_search,i = R~s,0 r_out,i + R~s,1 v_ran,i dt_soft,
+ * v_ran,i = rms of |v - sqrt(G M_* / |x|) phi_hat| over the particle's radial
+ * bin (bins uniform in ln of the cylindrical radius).  Writes p->r_out and
+ * p->r_search. */
+int p3t_cutoffs(p3t_ctx *ctx, p3t_particles *p, void *stream);
+
+/* Rows a2-a3 -- Morton keys on the 21-bit grid of the cubic bounding box,
+ * stable sort by (key, index), octree (split while > leaf_size particles and
+ * level < 21), per node mass, centre of mass, traceless quadrupole
+ * Q_ab = sum m (3 d_a d_b - d^2 delta_ab), quantised tight box and search
+ * reach.  The tree stays in the context for p3t_soft_force.  With
+ * update_cutoffs = 1, p3t_cutoffs runs first.  (Sec. 2.1.2: the paper's soft
+ * force uses a Barnes-Hut tree.) */
+int p3t_build_tree(p3t_ctx *ctx, p3t_particles *p, int update_cutoffs,
+                   void *stream);
+
+/* Row a4 -- soft acceleration, Eq. softforce:
+ *   a_i = -sum_j G m_j K(r_ij / r_out,ij) r_ij / r_ij^3,
+ *   r_out,ij = max(r_out,i, r_out,j) (Eq. rout2), K the changeover of
+ *   Sec. 2.1.1 (zero below gamma, one above 1),
+ * by a tree walk per leaf: accepted nodes add monopole + quadrupole, opened
+ * leaves add the changeover pair terms.  A node is opened when the
+ * Barnes-Hut test fails or it lies within the search reach, so all pairs with
+ * r_ij < max(r_search,i, r_search,j) are evaluated as pairs and recorded as
+ * neighbour candidates for p3t_neighbours.  p must be the particles the tree
+ * was built from.  ax, ay, az: n doubles each (caller order, overwritten).
+ * counts: NULL or a device uint64[2] overwritten with the numbers of
+ * particle-particle and particle-node terms evaluated. */
+int p3t_soft_force(p3t_ctx *ctx, const p3t_particles *p, double *ax, double *ay,
+                   double *az, uint64_t *counts, void *stream);
+
+/* Rows a5-a6 -- neighbour lists and clusters, Sec. 2.3:
+ * a candidate j of i stays a neighbour iff r_ij < r_search,ij and either its
+ * closest approach under linear motion over [0, dt_soft] (Eq. rsearch1 with
+ * t_min) is at most R~s,2 r_out,ij, or v_ij < R~s,3 a_ij dt_soft / 2 with
+ * a_ij = G (m_i + m_j) / r_ij^2; all tests in FP64.  Lists are symmetric.
+ * nb_off: device int64[n+1], nb_idx: device int32[nb_cap], rows sorted by j.
+ * If more than nb_cap entries are needed, nb_off is still complete, nb_idx
+ * holds the first nb_cap, no clusters are formed and P3T_ERR_CAPACITY is
+ * recorded with the size needed.  Clusters are the connected components of
+ * the neighbour graph labelled by their smallest index (the fixed point of
+ * the paper's min-label propagation).  *out receives library-owned views,
+ * valid until the next p3t_neighbours call on this context.  Must follow
+ * p3t_soft_force on the same particles. */
+int p3t_neighbours(p3t_ctx *ctx, const p3t_particles *p, int64_t *nb_off,
+                   int32_t *nb_idx, int64_t nb_cap, p3t_clusters *out,
+                   void *stream);
+
+/* Rows a8-a9 -- hard part over [0, dt] (procedure step 5, Eq. hardforce):
+ * every cluster of >= 2 members is integrated with the fourth-order Hermite
+ * predictor-corrector and block individual time steps (dt / 2^k, k <= 40;
+ * Aarseth step with eta, first step eta0 |a|/|j|), under the star and the
+ * (1 - K) part of the pair forces; every isolated particle is advanced on its
+ * Kepler orbit about M_* (universal variables, Newton-Raphson).  Positions and
+ * velocities of p are updated in place.  cl: views from p3t_neighbours or
+ * caller-built device arrays of the same layout.  n_steps: NULL or a device
+ * uint64 overwritten with the number of Hermite particle-steps. */
+int p3t_hard_step(p3t_ctx *ctx, p3t_particles *p, const p3t_clusters *cl,
+                  double dt, uint64_t *n_steps, void *stream);
+
+/* Row a7 -- soft kick (procedure steps 3 and 8): v += a * h, h usually
+ * dt_soft / 2.  ax, ay, az: n doubles each, caller order. */
+int p3t_kick(p3t_ctx *ctx, p3t_particles *p, const double *ax, const double *ay,
+             const double *az, double h, void *stream);
+
+/* Row a10 -- total energy (Eqs. soft and hard; W + (1 - W) = 1 makes it the
+ * Newtonian energy): out = device double[4] {E, kinetic, star potential,
+ * pair potential}.  The pair sum is direct O(n^2), in FP64 for P3T_FP64 and
+ * as FP32 terms on float-float relative coordinates with float-float sums for
+ * P3T_MIXED. */
+int p3t_energy(p3t_ctx *ctx, const p3t_particles *p, double *out, void *stream);
+
+/* Copies cluster views (from p3t_neighbours, or caller-built) into caller
+ * buffers, ordered on `stream`: label, singles, cl_mem int32[n], cl_off
+ * int64[n + 1], counts int64[4] (device pointers; entries past the counts are
+ * unspecified).  The paper has no counterpart: it exists so that callers can
+ * keep the clusters beyond the next p3t_neighbours call. */
+int p3t_copy_clusters(p3t_ctx *ctx, const p3t_clusters *cl, int64_t n,
+                      int32_t *label, int32_t *singles, int64_t *cl_off,
+                      int32_t *cl_mem, int64_t *counts, void *stream);
+
+/* Synchronises the context's device, returns the first device-side error
+ * recorded since the last call (or 0) and clears it.  *required (may be NULL)
+ * receives the buffer size a P3T_ERR_CAPACITY asked for.  Not capturable. */
+int p3t_status(p3t_ctx *ctx, int64_t *required);
+
+/* Synchronising read of the last tree: out[4] = {nodes, leaves, deepest level,
+ * largest leaf}.  Host memory.  Not capturable. */
+int p3t_tree_stats(p3t_ctx *ctx, int64_t out[4]);
+
+/* Number of kernels the library has launched in this process (all contexts);
+ * a diagnostic for counting launches per step.  Host only, thread-safe. */
+int64_t p3t_launch_count(void);
+
+/* Human-readable text for a status code. */
+const char *p3t_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* P3T_H */

@@ -1,0 +1,373 @@
+// C-ABI entry points of libp3t: context, buffers, argument checks, status.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <new>
+
+#include "p3t_internal.cuh"
+
+int64_t p3t_walk_warps(int num_sms);
+
+static std::atomic<long long> g_launches{0};
+void p3t_note_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+namespace {
+
+constexpr int64_t kStackCap = 8192;  // walk stack entries per warp
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool params_ok(const p3t_params *p) {
+  if (!p) return false;
+  if (!(p->G > 0.0) || !(p->m_star >= 0.0) || !(p->dt_soft > 0.0)) return false;
+  if (!(p->gamma > 0.0 && p->gamma < 1.0)) return false;
+  if (!(p->rcut0 >= 0.0) || !(p->rcut1 >= 0.0)) return false;
+  if (!(p->rs0 >= 1.0) || !(p->rs1 >= 0.0) || !(p->rs2 >= 0.0) || !(p->rs3 >= 0.0)) return false;
+  if (!(p->theta >= 0.0) || !(p->eta > 0.0) || !(p->eta0 > 0.0)) return false;
+  if (p->leaf_size < 1 || p->leaf_size > 32) return false;
+  if (p->precision != P3T_FP64 && p->precision != P3T_MIXED) return false;
+  if (p->vran_bins < 0 || p->vran_bins > 4096 || p->reserved != 0) return false;
+  return true;
+}
+
+bool particles_ok(const p3t_particles *p) {
+  if (!p || p->n < 0 || p->n >= ((int64_t)1 << 31)) return false;
+  if (p->n == 0) return true;
+  return p->x && p->y && p->z && p->vx && p->vy && p->vz && p->m && p->r_out &&
+         p->r_search;
+}
+
+template <typename T> void dfree(T *&ptr) {
+  if (ptr) cudaFree((void *)ptr);
+  ptr = nullptr;
+}
+
+template <typename T> bool dalloc(T *&ptr, int64_t count) {
+  dfree(ptr);
+  if (count < 1) count = 1;
+  return cudaMalloc((void **)&ptr, sizeof(T) * (size_t)count) == cudaSuccess;
+}
+
+void free_particle_buffers(p3t_ctx *c) {
+  dfree(c->keys); dfree(c->keys_alt); dfree(c->idx); dfree(c->idx_alt);
+  dfree(c->radix_hist);
+  dfree(c->sx); dfree(c->sy); dfree(c->sz); dfree(c->sm); dfree(c->sro); dfree(c->srs);
+  dfree(c->sq); dfree(c->spA); dfree(c->spB); dfree(c->srs32);
+  dfree(c->lp); dfree(c->lv); dfree(c->wlcp); dfree(c->ncount); dfree(c->nstart);
+  dfree(c->pre_first); dfree(c->pre_count); dfree(c->pre_level);
+  dfree(c->lvl_keys); dfree(c->lvl_keys_alt); dfree(c->bfs2pre); dfree(c->bfs2pre_alt);
+  dfree(c->pre2bfs); dfree(c->node); dfree(c->mom64); dfree(c->mom32); dfree(c->nrs);
+  dfree(c->node_done); dfree(c->leaf_list); dfree(c->leaf_flag); dfree(c->leaf_pos);
+  dfree(c->leaf_of); dfree(c->refine);
+  dfree(c->walk_stack); dfree(c->cand_i); dfree(c->cand_j); dfree(c->cand_keep);
+  dfree(c->deg); dfree(c->fill); dfree(c->parent); dfree(c->label); dfree(c->csize);
+  dfree(c->flag); dfree(c->pos); dfree(c->singles); dfree(c->cl_off);
+  // cl_mem aliases one of the mvals buffers
+  c->cl_mem = nullptr;
+  dfree(c->mkeys); dfree(c->mkeys_alt); dfree(c->mvals); dfree(c->mvals_alt);
+  dfree(c->hw); dfree(c->ht); dfree(c->hl);
+  c->cap = 0;
+  c->have_tree = c->have_cand = false;
+}
+
+int64_t node_bound(int64_t n, int leaf) {
+  // internal nodes hold > leaf particles: at most n / (leaf + 1) per level
+  // below the root, 21 levels; leaves are disjoint non-empty sets: at most n
+  return n + (int64_t)P3T_BITS * (n / (leaf + 1) + 1) + 64;
+}
+
+int reserve(p3t_ctx *c, int64_t n, int64_t cand_cap) {
+  const int64_t want_nodes = node_bound(n, c->prm.leaf_size);
+  if (n <= c->cap && want_nodes <= c->node_cap && cand_cap <= c->cand_cap) return P3T_OK;
+  cudaDeviceSynchronize();
+  free_particle_buffers(c);
+  const int64_t N = n > 1 ? n : 1;
+  const int64_t NC = want_nodes;
+  c->node_cap = NC;
+  c->cand_cap = cand_cap;
+  c->walk_warps = p3t_walk_warps(c->num_sms);
+  c->stack_cap = kStackCap;
+  c->radix_hist_cap = p3t_radix_hist_entries(N > NC ? N : NC);
+  bool ok = true;
+  ok &= dalloc(c->keys, N) && dalloc(c->keys_alt, N) && dalloc(c->idx, N) && dalloc(c->idx_alt, N);
+  ok &= dalloc(c->radix_hist, c->radix_hist_cap);
+  ok &= dalloc(c->sx, N) && dalloc(c->sy, N) && dalloc(c->sz, N) && dalloc(c->sm, N);
+  ok &= dalloc(c->sro, N) && dalloc(c->srs, N) && dalloc(c->sq, 3 * N);
+  ok &= dalloc(c->spA, N) && dalloc(c->spB, N) && dalloc(c->srs32, N);
+  ok &= dalloc(c->lp, N) && dalloc(c->lv, N) && dalloc(c->wlcp, N) && dalloc(c->ncount, N);
+  ok &= dalloc(c->nstart, N);
+  ok &= dalloc(c->pre_first, NC) && dalloc(c->pre_count, NC) && dalloc(c->pre_level, NC);
+  ok &= dalloc(c->lvl_keys, NC) && dalloc(c->lvl_keys_alt, NC);
+  ok &= dalloc(c->bfs2pre, NC) && dalloc(c->bfs2pre_alt, NC) && dalloc(c->pre2bfs, NC);
+  ok &= dalloc(c->node, NC) && dalloc(c->mom64, NC) && dalloc(c->mom32, NC) && dalloc(c->nrs, NC);
+  ok &= dalloc(c->node_done, NC) && dalloc(c->leaf_list, NC) && dalloc(c->leaf_flag, NC);
+  ok &= dalloc(c->leaf_pos, NC) && dalloc(c->leaf_of, N) && dalloc(c->refine, N);
+  ok &= dalloc(c->walk_stack, c->walk_warps * c->stack_cap);
+  ok &= dalloc(c->cand_i, cand_cap) && dalloc(c->cand_j, cand_cap) && dalloc(c->cand_keep, cand_cap);
+  ok &= dalloc(c->deg, N + 1) && dalloc(c->fill, N + 1);
+  ok &= dalloc(c->parent, N) && dalloc(c->label, N) && dalloc(c->csize, N);
+  ok &= dalloc(c->flag, 4 * N) && dalloc(c->pos, 4 * N);
+  ok &= dalloc(c->singles, N) && dalloc(c->cl_off, N + 1);
+  ok &= dalloc(c->mkeys, N) && dalloc(c->mkeys_alt, N) && dalloc(c->mvals, N) && dalloc(c->mvals_alt, N);
+  ok &= dalloc(c->hw, 20 * N) && dalloc(c->ht, N) && dalloc(c->hl, N);
+  if (!ok) {
+    free_particle_buffers(c);
+    cudaGetLastError();
+    return P3T_ERR_CUDA;
+  }
+  c->cl_mem = c->mvals;
+  c->cap = N;
+  return P3T_OK;
+}
+
+int64_t default_cand_cap(int64_t n) { return 8 * n + 65536; }
+
+int ensure(p3t_ctx *c, int64_t n) {
+  int64_t cc = c->cand_cap > default_cand_cap(n) ? c->cand_cap : default_cand_cap(n);
+  return reserve(c, n, cc);
+}
+
+}  // namespace
+
+extern "C" {
+
+int p3t_create(p3t_ctx **ctx, const p3t_params *p, int device) {
+  if (!ctx || !params_ok(p)) return P3T_ERR_INVALID;
+  *ctx = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return P3T_ERR_CUDA;
+  }
+  DeviceGuard g(device);
+  p3t_ctx *c = new (std::nothrow) p3t_ctx();
+  if (!c) return P3T_ERR_CUDA;
+  c->device = device;
+  c->prm = *p;
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete c;
+    return P3T_ERR_CUDA;
+  }
+  bool ok = dalloc(c->status, 1) && dalloc(c->box, 4) && dalloc(c->box_bits, 6) &&
+            dalloc(c->counters, 16) && dalloc(c->cl_counts, 4) && dalloc(c->hsteps, 1) &&
+            dalloc(c->epart, 8192) && dalloc(c->scan_part, 1025) && dalloc(c->bh_table, 32);
+  if (ok) ok = cudaMemset(c->status, 0, sizeof(DevStatus)) == cudaSuccess &&
+               cudaMemset(c->counters, 0, 16 * sizeof(int64_t)) == cudaSuccess &&
+               cudaMemset(c->cl_counts, 0, 4 * sizeof(int64_t)) == cudaSuccess;
+  if (!ok) {
+    p3t_destroy(c);
+    cudaGetLastError();
+    return P3T_ERR_CUDA;
+  }
+  *ctx = c;
+  return P3T_OK;
+}
+
+void p3t_destroy(p3t_ctx *c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  cudaDeviceSynchronize();
+  free_particle_buffers(c);
+  dfree(c->status); dfree(c->box); dfree(c->box_bits); dfree(c->counters);
+  dfree(c->cl_counts); dfree(c->hsteps); dfree(c->epart); dfree(c->scan_part);
+  dfree(c->bh_table);
+  cudaGetLastError();
+  delete c;
+}
+
+int p3t_set_params(p3t_ctx *c, const p3t_params *p) {
+  if (!c || !params_ok(p)) return P3T_ERR_INVALID;
+  const bool leaf_changed = p->leaf_size != c->prm.leaf_size;
+  c->prm = *p;
+  if (leaf_changed) c->have_tree = c->have_cand = false;
+  return P3T_OK;
+}
+
+int p3t_reserve(p3t_ctx *c, int64_t n) {
+  if (!c || n < 0 || n >= ((int64_t)1 << 31)) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return ensure(c, n);
+}
+
+int p3t_cutoffs(p3t_ctx *c, p3t_particles *p, void *stream) {
+  if (!c || !particles_ok(p)) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return p3t_run_cutoffs(c, p, (cudaStream_t)stream);
+}
+
+int p3t_build_tree(p3t_ctx *c, p3t_particles *p, int update_cutoffs, void *stream) {
+  if (!c || !particles_ok(p)) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  int rc = ensure(c, p->n);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (update_cutoffs) {
+    rc = p3t_run_cutoffs(c, p, s);
+    if (rc) return rc;
+  }
+  if (p->n == 0) {
+    c->have_tree = false;
+    c->last_n = 0;
+    return P3T_OK;
+  }
+  rc = p3t_run_build_tree(c, p, s);
+  if (rc) return rc;
+  c->last_n = p->n;
+  c->have_tree = true;
+  c->have_cand = false;
+  return P3T_OK;
+}
+
+int p3t_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax, double *ay,
+                   double *az, uint64_t *counts, void *stream) {
+  if (!c || !particles_ok(p)) return P3T_ERR_INVALID;
+  if (p->n == 0) return P3T_OK;
+  if (!ax || !ay || !az || !c->have_tree || p->n != c->last_n) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  int rc = p3t_run_soft_force(c, p, ax, ay, az, counts, (cudaStream_t)stream);
+  if (rc == P3T_OK) c->have_cand = true;
+  return rc;
+}
+
+int p3t_neighbours(p3t_ctx *c, const p3t_particles *p, int64_t *nb_off,
+                   int32_t *nb_idx, int64_t nb_cap, p3t_clusters *out, void *stream) {
+  if (!c || !particles_ok(p) || !nb_off || !out || nb_cap < 0) return P3T_ERR_INVALID;
+  if (nb_cap > 0 && !nb_idx) return P3T_ERR_INVALID;
+  if (p->n > 0 && (!c->have_cand || p->n != c->last_n)) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  int rc = ensure(c, p->n);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (p->n == 0) {
+    if (cudaMemsetAsync(nb_off, 0, sizeof(int64_t), s) != cudaSuccess ||
+        cudaMemsetAsync(c->cl_counts, 0, 4 * sizeof(int64_t), s) != cudaSuccess ||
+        cudaMemsetAsync(c->cl_off, 0, sizeof(int64_t), s) != cudaSuccess)
+      return P3T_ERR_CUDA;
+  } else {
+    rc = p3t_run_neighbours(c, p, nb_off, nb_idx, nb_cap, s);
+    if (rc) return rc;
+  }
+  out->label = c->label;
+  out->singles = c->singles;
+  out->cl_off = c->cl_off;
+  out->cl_mem = c->cl_mem;
+  out->counts = c->cl_counts;
+  return P3T_OK;
+}
+
+int p3t_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl, double dt,
+                  uint64_t *n_steps, void *stream) {
+  if (!c || !particles_ok(p) || !cl || !(dt > 0.0)) return P3T_ERR_INVALID;
+  if (p->n == 0) return P3T_OK;
+  if (!cl->singles || !cl->cl_off || !cl->cl_mem || !cl->counts) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  int rc = ensure(c, p->n);
+  if (rc) return rc;
+  return p3t_run_hard_step(c, p, cl, dt, n_steps, (cudaStream_t)stream);
+}
+
+int p3t_kick(p3t_ctx *c, p3t_particles *p, const double *ax, const double *ay,
+             const double *az, double h, void *stream) {
+  if (!c || !particles_ok(p)) return P3T_ERR_INVALID;
+  if (p->n > 0 && (!ax || !ay || !az)) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return p3t_run_kick(c, p, ax, ay, az, h, (cudaStream_t)stream);
+}
+
+int p3t_energy(p3t_ctx *c, const p3t_particles *p, double *out, void *stream) {
+  if (!c || !particles_ok(p) || !out) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return p3t_run_energy(c, p, out, (cudaStream_t)stream);
+}
+
+int p3t_copy_clusters(p3t_ctx *c, const p3t_clusters *cl, int64_t n, int32_t *label,
+                      int32_t *singles, int64_t *cl_off, int32_t *cl_mem, int64_t *counts,
+                      void *stream) {
+  if (!c || !cl || n < 0 || !label || !singles || !cl_off || !cl_mem || !counts)
+    return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+  if (n > 0) {
+    P3T_CUDA_TRY(cudaMemcpyAsync(label, cl->label, sizeof(int32_t) * n, k, s));
+    P3T_CUDA_TRY(cudaMemcpyAsync(singles, cl->singles, sizeof(int32_t) * n, k, s));
+    P3T_CUDA_TRY(cudaMemcpyAsync(cl_mem, cl->cl_mem, sizeof(int32_t) * n, k, s));
+  }
+  P3T_CUDA_TRY(cudaMemcpyAsync(cl_off, cl->cl_off, sizeof(int64_t) * (n + 1), k, s));
+  P3T_CUDA_TRY(cudaMemcpyAsync(counts, cl->counts, sizeof(int64_t) * 4, k, s));
+  return P3T_OK;
+}
+
+int p3t_status(p3t_ctx *c, int64_t *required) {
+  if (!c) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return P3T_ERR_CUDA;
+  }
+  DevStatus st;
+  if (cudaMemcpy(&st, c->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return P3T_ERR_CUDA;
+  if (required) *required = st.required;
+  // grow the candidate buffers for the next walk if this one overflowed (the
+  // force and neighbour calls of that step must then be repeated)
+  if (st.cand_need > c->cand_cap) {
+    const int64_t want = st.cand_need + st.cand_need / 4 + 1024;
+    if (dalloc(c->cand_i, want) && dalloc(c->cand_j, want) && dalloc(c->cand_keep, want)) {
+      c->cand_cap = want;
+    } else {
+      cudaGetLastError();
+      dalloc(c->cand_i, c->cand_cap); dalloc(c->cand_j, c->cand_cap);
+      dalloc(c->cand_keep, c->cand_cap);
+    }
+    c->have_cand = false;
+  }
+  DevStatus zero;
+  memset(&zero, 0, sizeof(zero));
+  zero.cand_need = st.cand_need;
+  if (cudaMemcpy(c->status, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess)
+    return P3T_ERR_CUDA;
+  return st.code;
+}
+
+int p3t_tree_stats(p3t_ctx *c, int64_t out[4]) {
+  if (!c || !out) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  if (cudaDeviceSynchronize() != cudaSuccess) return P3T_ERR_CUDA;
+  int64_t h[8];
+  if (cudaMemcpy(h, c->counters, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return P3T_ERR_CUDA;
+  out[0] = h[1];
+  out[1] = h[5];
+  out[2] = h[6];
+  out[3] = h[7];
+  return P3T_OK;
+}
+
+int64_t p3t_launch_count(void) { return (int64_t)g_launches.load(); }
+
+const char *p3t_strerror(int code) {
+  switch (code) {
+    case P3T_OK: return "ok";
+    case P3T_ERR_INVALID: return "invalid argument, parameter or call order";
+    case P3T_ERR_CUDA: return "CUDA runtime error";
+    case P3T_ERR_CAPACITY: return "buffer capacity exceeded (see required size)";
+    case P3T_ERR_DT_UNDERFLOW: return "Hermite time step below dt / 2^40";
+    case P3T_ERR_TIMEOUT: return "bounded device loop gave up";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,470 @@
+// Rows a7-a10 of the soft step: kick, Hermite-4 hard step of the neighbour
+// clusters, Kepler drift of isolated particles, energy.
+//
+// Compiled with -fmad=false.  The Hermite force, predictor, corrector and
+// step rule are evaluated in one fixed order with IEEE division and square
+// root, so that the block-step schedule (decided by comparing FP64 step
+// estimates with dt / 2^k) does not depend on the machine.
+#include "p3t_internal.cuh"
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int64_t kHermiteIterLimit = 1 << 24;  // block steps per cluster
+
+// ---- row a7: soft kick (procedure steps 3 and 8) ----------------------------
+__global__ void k_kick(int64_t n, double *vx, double *vy, double *vz,
+                       const double *ax, const double *ay, const double *az,
+                       double h) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    vx[i] += ax[i] * h;
+    vy[i] += ay[i] * h;
+    vz[i] += az[i] * h;
+  }
+}
+
+// ---- row a9: Kepler drift, universal variables ------------------------------
+// Stumpff functions C(z) = sum (-z)^k / (2k+2)!, S(z) = sum (-z)^k / (2k+3)!,
+// as nested series for |z| < 1 and in closed form otherwise.
+__device__ __forceinline__ void stumpff(double z, double &C, double &S) {
+  if (fabs(z) < 1.0) {
+    const double dc[12] = {12.0, 30.0, 56.0, 90.0, 132.0, 182.0,
+                           240.0, 306.0, 380.0, 462.0, 552.0, 650.0};
+    const double ds[12] = {20.0, 42.0, 72.0, 110.0, 156.0, 210.0,
+                           272.0, 342.0, 420.0, 506.0, 600.0, 702.0};
+    double c = 1.0, s = 1.0;
+#pragma unroll
+    for (int k = 11; k >= 0; --k) {
+      c = 1.0 - z / dc[k] * c;
+      s = 1.0 - z / ds[k] * s;
+    }
+    C = 0.5 * c;
+    S = s / 6.0;
+  } else if (z > 0.0) {
+    const double q = sqrt(z);
+    C = (1.0 - cos(q)) / z;
+    S = (q - sin(q)) / (z * q);
+  } else {
+    const double q = sqrt(-z);
+    C = (cosh(q) - 1.0) / (-z);
+    S = (sinh(q) - q) / (-z * q);
+  }
+}
+
+// Advances (X, V) by dt on the Kepler orbit about mu.  Universal anomaly chi
+// solves sqrt(mu) dt = (r0 v_r0/sqrt(mu)) chi^2 C + (1 - alpha r0) chi^3 S
+// + r0 chi (z = alpha chi^2) by Newton-Raphson; then Lagrange f, g.
+__device__ bool kepler_uv(double X[3], double V[3], double dt, double mu) {
+  const double r0 = sqrt(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
+  const double v2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+  const double rv = X[0] * V[0] + X[1] * V[1] + X[2] * V[2];
+  const double alpha = 2.0 / r0 - v2 / mu;
+  const double sq = sqrt(mu);
+  const double sig = rv / sq;  // r0 v_r0 / sqrt(mu)
+  const double tau = sq * dt;
+  double chi = tau / r0;
+  if (alpha > 0.0) {
+    const double P = 2.0 * 3.141592653589793 / (alpha * sqrt(alpha) * sq);
+    if (fabs(dt) > 0.25 * P) chi = tau * alpha;
+  }
+  double C = 0.5, S = 1.0 / 6.0, z = 0.0;
+  bool ok = false;
+  for (int it = 0; it < 64; ++it) {
+    z = alpha * chi * chi;
+    stumpff(z, C, S);
+    const double chi2 = chi * chi;
+    const double F = sig * chi2 * C + (1.0 - alpha * r0) * chi2 * chi * S + r0 * chi - tau;
+    const double Fp = sig * chi * (1.0 - z * S) + (1.0 - alpha * r0) * chi2 * C + r0;
+    double d = F / Fp;
+    const double lim = 0.5 * (fabs(chi) + r0);
+    if (d > lim) d = lim;
+    if (d < -lim) d = -lim;
+    chi -= d;
+    // quadratic convergence: once a correction is below 1e-14 relative the
+    // remaining error is below rounding
+    if (fabs(d) <= 1e-14 * fabs(chi) || d == 0.0) { ok = true; break; }
+  }
+  z = alpha * chi * chi;
+  stumpff(z, C, S);
+  const double chi2 = chi * chi;
+  const double f = 1.0 - chi2 / r0 * C;
+  const double g = dt - chi2 * chi * S / sq;
+  double nx[3];
+  for (int a = 0; a < 3; ++a) nx[a] = f * X[a] + g * V[a];
+  const double r = sqrt(nx[0] * nx[0] + nx[1] * nx[1] + nx[2] * nx[2]);
+  const double fd = sq / (r * r0) * (z * S - 1.0) * chi;
+  const double gd = 1.0 - chi2 / r * C;
+  for (int a = 0; a < 3; ++a) {
+    const double nv = fd * X[a] + gd * V[a];
+    X[a] = nx[a];
+    V[a] = nv;
+  }
+  return ok;
+}
+
+__global__ void k_kepler(const int64_t *d_nsingle, const int32_t *singles,
+                         p3t_particles p, double dt, double mu, DevStatus *st) {
+  const int64_t ns = *d_nsingle;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ns;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = singles[k];
+    double X[3] = {p.x[i], p.y[i], p.z[i]}, V[3] = {p.vx[i], p.vy[i], p.vz[i]};
+    if (!kepler_uv(X, V, dt, mu)) dev_fail(st, P3T_ERR_TIMEOUT, 60, 0);
+    p.x[i] = X[0]; p.y[i] = X[1]; p.z[i] = X[2];
+    p.vx[i] = V[0]; p.vy[i] = V[1]; p.vz[i] = V[2];
+  }
+}
+
+// ---- row a8: Hermite-4 with block steps, one warp per cluster ---------------
+struct HWork {
+  double *x, *y, *z, *vx, *vy, *vz;        // state at the member's own time
+  double *px, *py, *pz, *pvx, *pvy, *pvz;  // predicted to the block time
+  double *ax, *ay, *az, *jx, *jy, *jz;     // a, jerk at the member's own time
+  double *m, *ro;
+  int64_t *t;                              // time, units of dt / 2^40
+  int32_t *lvl;                            // step = dt / 2^lvl
+};
+
+__device__ __forceinline__ double K_of(double y, double gamma) {
+  if (y <= gamma) return 0.0;
+  if (y >= 1.0) return 1.0;
+  const double x = (y - gamma) / (1.0 - gamma);
+  const double x2 = x * x;
+  const double x3 = x2 * x;
+  const double x4 = x2 * x2;
+  return x4 * (35.0 - 84.0 * x + 70.0 * x2 - 20.0 * x3);
+}
+__device__ __forceinline__ double dK_of(double y, double gamma) {
+  if (y <= gamma || y >= 1.0) return 0.0;
+  const double x = (y - gamma) / (1.0 - gamma);
+  const double u = 1.0 - x;
+  return 140.0 * x * x * x * u * u * u / (1.0 - gamma);
+}
+
+// hard acceleration and jerk of member k (Eq. hardforce): star term, then the
+// (1 - K) pair terms over the other members in ascending order
+__device__ void hard_acc_jerk(int nc, const double *x, const double *y,
+                              const double *z, const double *vx, const double *vy,
+                              const double *vz, const double *m, const double *ro,
+                              const p3t_params &prm, int k, double acc[3],
+                              double jerk[3]) {
+  double ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0;
+  {
+    const double r2 = x[k] * x[k] + y[k] * y[k] + z[k] * z[k];
+    const double r = sqrt(r2);
+    const double r3 = r2 * r;
+    const double rv = x[k] * vx[k] + y[k] * vy[k] + z[k] * vz[k];
+    const double gm = prm.G * prm.m_star;
+    ax -= gm * x[k] / r3; ay -= gm * y[k] / r3; az -= gm * z[k] / r3;
+    const double c = 3.0 * rv / r2;
+    jx -= gm * (vx[k] - c * x[k]) / r3;
+    jy -= gm * (vy[k] - c * y[k]) / r3;
+    jz -= gm * (vz[k] - c * z[k]) / r3;
+  }
+  for (int j = 0; j < nc; ++j) {
+    if (j == k) continue;
+    const double rx = x[k] - x[j], ry = y[k] - y[j], rz = z[k] - z[j];
+    const double ux = vx[k] - vx[j], uy = vy[k] - vy[j], uz = vz[k] - vz[j];
+    const double r2 = rx * rx + ry * ry + rz * rz;
+    if (r2 == 0.0) continue;
+    const double r = sqrt(r2);
+    const double rot = fmax(ro[k], ro[j]);
+    const double yv = r / rot;
+    if (yv >= 1.0) continue;
+    const double w = 1.0 - K_of(yv, prm.gamma);
+    const double dK = dK_of(yv, prm.gamma);
+    const double r3 = r2 * r;
+    const double rv = rx * ux + ry * uy + rz * uz;
+    const double gm = prm.G * m[j];
+    ax -= gm * w * rx / r3; ay -= gm * w * ry / r3; az -= gm * w * rz / r3;
+    const double c = 3.0 * w * rv / r2 + dK * rv / (r * rot);
+    jx -= gm * (w * ux - c * rx) / r3;
+    jy -= gm * (w * uy - c * ry) / r3;
+    jz -= gm * (w * uz - c * rz) / r3;
+  }
+  acc[0] = ax; acc[1] = ay; acc[2] = az;
+  jerk[0] = jx; jerk[1] = jy; jerk[2] = jz;
+}
+
+__device__ __forceinline__ double norm3(double a, double b, double c) {
+  return sqrt(a * a + b * b + c * c);
+}
+
+// largest dt / 2^lvl not above dt_des, at most twice the previous step, and
+// commensurate with the current time t (units of dt / 2^40)
+__device__ __forceinline__ int quantise_level(double dt_des, double dt, int prev,
+                                              int64_t t, bool &underflow) {
+  int lvl = 0;
+  while (lvl < P3T_KMAX && ldexp(dt, -lvl) > dt_des) ++lvl;
+  if (ldexp(dt, -lvl) > dt_des) underflow = true;
+  if (lvl < prev - 1) lvl = prev - 1;
+  while (lvl < P3T_KMAX && (t & ((((int64_t)1) << (P3T_KMAX - lvl)) - 1)) != 0) ++lvl;
+  return lvl;
+}
+
+__global__ void k_hermite(const int64_t *d_ncl, const int64_t *cl_off,
+                          const int32_t *cl_mem, p3t_particles p, HWork w,
+                          p3t_params prm, double dt,
+                          unsigned long long *steps_out, DevStatus *st) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t ncl = *d_ncl;
+  const int64_t T = ((int64_t)1) << P3T_KMAX;
+  const double unit = ldexp(dt, -P3T_KMAX);
+  unsigned long long steps = 0;
+  bool underflow = false;
+  for (int64_t c = warp; c < ncl; c += nwarps) {
+    const int64_t off = cl_off[c];
+    const int nc = (int)(cl_off[c + 1] - off);
+    double *x = w.x + off, *y = w.y + off, *z = w.z + off;
+    double *vx = w.vx + off, *vy = w.vy + off, *vz = w.vz + off;
+    double *px = w.px + off, *py = w.py + off, *pz = w.pz + off;
+    double *pvx = w.pvx + off, *pvy = w.pvy + off, *pvz = w.pvz + off;
+    double *ax = w.ax + off, *ay = w.ay + off, *az = w.az + off;
+    double *jx = w.jx + off, *jy = w.jy + off, *jz = w.jz + off;
+    double *m = w.m + off, *ro = w.ro + off;
+    int64_t *t = w.t + off;
+    int32_t *lvl = w.lvl + off;
+    for (int k = lane; k < nc; k += 32) {
+      const int32_t i = cl_mem[off + k];
+      x[k] = p.x[i]; y[k] = p.y[i]; z[k] = p.z[i];
+      vx[k] = p.vx[i]; vy[k] = p.vy[i]; vz[k] = p.vz[i];
+      m[k] = p.m[i]; ro[k] = p.r_out[i];
+    }
+    __syncwarp();
+    for (int k = lane; k < nc; k += 32) {
+      double a[3], j[3];
+      hard_acc_jerk(nc, x, y, z, vx, vy, vz, m, ro, prm, k, a, j);
+      ax[k] = a[0]; ay[k] = a[1]; az[k] = a[2];
+      jx[k] = j[0]; jy[k] = j[1]; jz[k] = j[2];
+      const double an = norm3(a[0], a[1], a[2]), jn = norm3(j[0], j[1], j[2]);
+      const double dtd = jn > 0.0 ? prm.eta0 * an / jn : dt;
+      t[k] = 0;
+      lvl[k] = quantise_level(dtd, dt, 0, 0, underflow);
+    }
+    __syncwarp();
+    int64_t iter = 0;
+    for (;;) {
+      int64_t tn = T, tmin = T;
+      for (int k = lane; k < nc; k += 32) {
+        const int64_t e = t[k] + (T >> lvl[k]);
+        tn = e < tn ? e : tn;
+        tmin = t[k] < tmin ? t[k] : tmin;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const int64_t a = __shfl_xor_sync(0xffffffffu, tn, o);
+        const int64_t b = __shfl_xor_sync(0xffffffffu, tmin, o);
+        tn = a < tn ? a : tn;
+        tmin = b < tmin ? b : tmin;
+      }
+      if (tmin >= T) break;
+      if (++iter > kHermiteIterLimit) {
+        if (lane == 0) dev_fail(st, P3T_ERR_TIMEOUT, 61, 0);
+        break;
+      }
+      // predict every member to the block time
+      for (int k = lane; k < nc; k += 32) {
+        const double D = (double)(tn - t[k]) * unit;
+        const double D2 = D * D, D3 = D2 * D;
+        px[k] = x[k] + vx[k] * D + ax[k] * D2 / 2.0 + jx[k] * D3 / 6.0;
+        py[k] = y[k] + vy[k] * D + ay[k] * D2 / 2.0 + jy[k] * D3 / 6.0;
+        pz[k] = z[k] + vz[k] * D + az[k] * D2 / 2.0 + jz[k] * D3 / 6.0;
+        pvx[k] = vx[k] + ax[k] * D + jx[k] * D2 / 2.0;
+        pvy[k] = vy[k] + ay[k] * D + jy[k] * D2 / 2.0;
+        pvz[k] = vz[k] + az[k] * D + jz[k] * D2 / 2.0;
+      }
+      __syncwarp();
+      // evaluate and correct the active members
+      for (int k = lane; k < nc; k += 32) {
+        if (t[k] + (T >> lvl[k]) != tn) continue;
+        double a1[3], j1[3];
+        hard_acc_jerk(nc, px, py, pz, pvx, pvy, pvz, m, ro, prm, k, a1, j1);
+        const double D = (double)(T >> lvl[k]) * unit;
+        const double D2 = D * D, D3 = D2 * D, D4 = D3 * D, D5 = D4 * D;
+        const double a0[3] = {ax[k], ay[k], az[k]}, j0[3] = {jx[k], jy[k], jz[k]};
+        double A2[3], A3[3], A2e[3];
+        for (int q = 0; q < 3; ++q) {
+          const double da = a0[q] - a1[q];
+          A2[q] = (-6.0 * da - D * (4.0 * j0[q] + 2.0 * j1[q])) / D2;
+          A3[q] = (12.0 * da + 6.0 * D * (j0[q] + j1[q])) / D3;
+          A2e[q] = A2[q] + D * A3[q];
+        }
+        x[k] = px[k] + A2[0] * D4 / 24.0 + A3[0] * D5 / 120.0;
+        y[k] = py[k] + A2[1] * D4 / 24.0 + A3[1] * D5 / 120.0;
+        z[k] = pz[k] + A2[2] * D4 / 24.0 + A3[2] * D5 / 120.0;
+        vx[k] = pvx[k] + A2[0] * D3 / 6.0 + A3[0] * D4 / 24.0;
+        vy[k] = pvy[k] + A2[1] * D3 / 6.0 + A3[1] * D4 / 24.0;
+        vz[k] = pvz[k] + A2[2] * D3 / 6.0 + A3[2] * D4 / 24.0;
+        ax[k] = a1[0]; ay[k] = a1[1]; az[k] = a1[2];
+        jx[k] = j1[0]; jy[k] = j1[1]; jz[k] = j1[2];
+        const double an = norm3(a1[0], a1[1], a1[2]), jn = norm3(j1[0], j1[1], j1[2]);
+        const double a2n = norm3(A2e[0], A2e[1], A2e[2]), a3n = norm3(A3[0], A3[1], A3[2]);
+        const double num = an * a2n + jn * jn, den = jn * a3n + a2n * a2n;
+        const double dtd = den > 0.0 ? sqrt(prm.eta * num / den) : dt;
+        t[k] = tn;
+        lvl[k] = quantise_level(dtd, dt, lvl[k], tn, underflow);
+        ++steps;
+      }
+      __syncwarp();
+    }
+    for (int k = lane; k < nc; k += 32) {
+      const int32_t i = cl_mem[off + k];
+      p.x[i] = x[k]; p.y[i] = y[k]; p.z[i] = z[k];
+      p.vx[i] = vx[k]; p.vy[i] = vy[k]; p.vz[i] = vz[k];
+    }
+    __syncwarp();
+  }
+  if (underflow) dev_fail(st, P3T_ERR_DT_UNDERFLOW, 62, 0);
+  for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(0xffffffffu, steps, o);
+  if (lane == 0 && steps_out && steps) atomicAdd(steps_out, steps);
+}
+
+__global__ void k_zero_u64(unsigned long long *p) { *p = 0ull; }
+
+// ---- row a10: energy --------------------------------------------------------
+__device__ __forceinline__ void two_sum_f(float &hi, float &lo, float b) {
+  const float s = hi + b;
+  const float bb = s - hi;
+  lo += (hi - (s - bb)) + (b - bb);
+  hi = s;
+}
+
+constexpr int kETile = 256;
+
+// E = sum m v^2/2 - sum G M m / r - 1/2 sum_i sum_{j != i} G m_i m_j / r_ij
+template <bool MIXED>
+__global__ void __launch_bounds__(kETile) k_energy(p3t_particles p, p3t_params prm,
+                                                   double *out) {
+  __shared__ double s_x[kETile], s_y[kETile], s_z[kETile], s_m[kETile];
+  __shared__ float4 s_h[kETile], s_l[kETile];
+  __shared__ double s_red[3][kETile / 32];
+  const int64_t n = p.n;
+  const int64_t i = blockIdx.x * (int64_t)kETile + threadIdx.x;
+  const bool valid = i < n;
+  double ek = 0.0, es = 0.0, ep = 0.0;
+  double xi = 0, yi = 0, zi = 0, mi = 0;
+  float xh = 0, yh = 0, zh = 0, xl = 0, yl = 0, zl = 0;
+  if (valid) {
+    xi = p.x[i]; yi = p.y[i]; zi = p.z[i]; mi = p.m[i];
+    ek = 0.5 * mi * (p.vx[i] * p.vx[i] + p.vy[i] * p.vy[i] + p.vz[i] * p.vz[i]);
+    es = -prm.G * prm.m_star * mi / sqrt(xi * xi + yi * yi + zi * zi);
+    xh = (float)xi; yh = (float)yi; zh = (float)zi;
+    xl = (float)(xi - (double)xh); yl = (float)(yi - (double)yh); zl = (float)(zi - (double)zh);
+  }
+  float sh = 0.f, sl = 0.f;
+  double sd = 0.0;
+  for (int64_t base = 0; base < n; base += kETile) {
+    const int64_t j = base + threadIdx.x;
+    __syncthreads();
+    if (j < n) {
+      const double X = p.x[j], Y = p.y[j], Z = p.z[j];
+      if (MIXED) {
+        const float hx = (float)X, hy = (float)Y, hz = (float)Z;
+        s_h[threadIdx.x] = make_float4(hx, hy, hz, (float)p.m[j]);
+        s_l[threadIdx.x] = make_float4((float)(X - (double)hx), (float)(Y - (double)hy),
+                                       (float)(Z - (double)hz), 0.f);
+      } else {
+        s_x[threadIdx.x] = X; s_y[threadIdx.x] = Y; s_z[threadIdx.x] = Z;
+        s_m[threadIdx.x] = p.m[j];
+      }
+    } else {
+      if (MIXED) { s_h[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f); s_l[threadIdx.x] = s_h[threadIdx.x]; }
+      else { s_x[threadIdx.x] = 0.0; s_y[threadIdx.x] = 0.0; s_z[threadIdx.x] = 0.0; s_m[threadIdx.x] = 0.0; }
+    }
+    __syncthreads();
+    const int lim = (int)min((int64_t)kETile, n - base);
+    if (MIXED) {
+      float b = 0.f;
+      for (int q = 0; q < lim; ++q) {
+        const float4 H = s_h[q], L = s_l[q];
+        const float dx = (xh - H.x) + (xl - L.x);
+        const float dy = (yh - H.y) + (yl - L.y);
+        const float dz = (zh - H.z) + (zl - L.z);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
+        ri = ri * (1.5f - 0.5f * r2 * ri * ri);  // one Newton step
+        b += H.w * ri;
+      }
+      two_sum_f(sh, sl, b);
+    } else {
+      for (int q = 0; q < lim; ++q) {
+        if (base + q == i) continue;
+        const double dx = xi - s_x[q], dy = yi - s_y[q], dz = zi - s_z[q];
+        sd += s_m[q] / sqrt(dx * dx + dy * dy + dz * dz);
+      }
+    }
+  }
+  if (valid) ep = MIXED ? -0.5 * prm.G * mi * ((double)sh + (double)sl) : -0.5 * prm.G * mi * sd;
+  else ep = 0.0;
+  double v[3] = {ek, es, ep};
+  for (int q = 0; q < 3; ++q)
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  if ((threadIdx.x & 31) == 0)
+    for (int q = 0; q < 3; ++q) s_red[q][threadIdx.x >> 5] = v[q];
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double s = 0.0;
+    for (int w = 0; w < kETile / 32; ++w) s += s_red[threadIdx.x][w];
+    atomicAdd(&out[1 + threadIdx.x], s);
+  }
+}
+
+__global__ void k_energy_init(double *out) {
+  if (threadIdx.x < 4) out[threadIdx.x] = 0.0;
+}
+__global__ void k_energy_final(double *out) { out[0] = out[1] + out[2] + out[3]; }
+
+}  // namespace
+
+int p3t_run_kick(p3t_ctx *c, p3t_particles *p, const double *ax,
+                 const double *ay, const double *az, double h, cudaStream_t s) {
+  if (p->n == 0) return P3T_OK;
+  const int64_t g = p3t_grid(p->n, kBlock, (int64_t)c->num_sms * P3T_NSM_BLOCKS);
+  k_kick<<<(unsigned)g, kBlock, 0, s>>>(p->n, p->vx, p->vy, p->vz, ax, ay, az, h);
+  p3t_note_launches(1);
+  return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
+}
+
+int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
+                      double dt, uint64_t *n_steps, cudaStream_t s) {
+  const int64_t n = p->n;
+  const int64_t maxb = (int64_t)c->num_sms * P3T_NSM_BLOCKS;
+  const double mu = c->prm.G * c->prm.m_star;
+  k_kepler<<<(unsigned)p3t_grid(n, 128, maxb), 128, 0, s>>>(&cl->counts[0], cl->singles, *p,
+                                                             dt, mu, c->status);
+  HWork w;
+  const int64_t cap = c->cap;
+  double *b = c->hw;
+  double **f[] = {&w.x, &w.y, &w.z, &w.vx, &w.vy, &w.vz, &w.px, &w.py, &w.pz,
+                  &w.pvx, &w.pvy, &w.pvz, &w.ax, &w.ay, &w.az, &w.jx, &w.jy, &w.jz,
+                  &w.m, &w.ro};
+  for (int q = 0; q < 20; ++q) *f[q] = b + q * cap;
+  w.t = c->ht;
+  w.lvl = c->hl;
+  unsigned long long *steps = n_steps ? reinterpret_cast<unsigned long long *>(n_steps)
+                                      : c->hsteps;
+  k_zero_u64<<<1, 1, 0, s>>>(steps);
+  // one warp per cluster; at most n/2 clusters
+  const int64_t warps = (n / 2) > 0 ? n / 2 : 1;
+  const int64_t gw = p3t_grid(warps * 32, 128, maxb);
+  k_hermite<<<(unsigned)gw, 128, 0, s>>>(&cl->counts[1], cl->cl_off, cl->cl_mem, *p, w,
+                                          c->prm, dt, steps, c->status);
+  p3t_note_launches(3);
+  return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
+}
+
+int p3t_run_energy(p3t_ctx *c, const p3t_particles *p, double *out, cudaStream_t s) {
+  k_energy_init<<<1, 32, 0, s>>>(out);
+  if (p->n > 0) {
+    const unsigned g = (unsigned)((p->n + kETile - 1) / kETile);
+    if (c->prm.precision == P3T_MIXED)
+      k_energy<true><<<g, kETile, 0, s>>>(*p, c->prm, out);
+    else
+      k_energy<false><<<g, kETile, 0, s>>>(*p, c->prm, out);
+  }
+  k_energy_final<<<1, 1, 0, s>>>(out);
+  p3t_note_launches(p->n > 0 ? 3 : 2);
+  return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
+}

@@ -1,0 +1,189 @@
+// Internal declarations of libp3t (CUDA, sm_103a).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "p3t.h"
+
+#define P3T_BITS 21           // bits per axis of the Morton grid
+#define P3T_QMAX (1 << P3T_BITS)
+#define P3T_KMAX 40           // deepest Hermite block level: dt / 2^40
+#define P3T_NSM_BLOCKS 8      // resident blocks per SM assumed for grid sizing
+
+// ---- device-side status (sticky first error + requested size) ------------
+struct DevStatus {
+  int32_t code;
+  int32_t where;       // id of the kernel that recorded it (diagnostics)
+  int64_t required;    // size asked for by a capacity error
+  int64_t cand_need;   // neighbour candidates found by the last walk
+  int64_t walk_stack_need;
+};
+
+__device__ __forceinline__ void dev_fail(DevStatus *st, int code, int where,
+                                         int64_t required) {
+  if (atomicCAS(&st->code, 0, code) == 0) st->where = where;
+  if (required > 0)
+    atomicMax(reinterpret_cast<unsigned long long *>(&st->required),
+              (unsigned long long)required);
+}
+
+// ---- tree node, walk record (64 bytes, breadth-first order) ---------------
+// Integer geometry on the 21-bit grid: quantised tight box of the members
+// (qlo, qhi), cell centre in half units (c2), search reach R (grid units).
+struct __align__(16) TreeNode {
+  int32_t qlo[3];
+  int32_t R;
+  int32_t qhi[3];
+  int32_t level;
+  int32_t c2[3];
+  int32_t parent;
+  int32_t child0;   // first child (children contiguous), -1 for a leaf
+  int32_t nchild;   // 0 for a leaf
+  int32_t first;    // first member in sorted order
+  int32_t count;    // number of members
+};
+
+// multipole moments in FP64: centre of mass, mass, traceless quadrupole
+struct __align__(16) Mom64 {
+  double cx, cy, cz, M;
+  double qxx, qyy, qzz, qxy;
+  double qxz, qyz, pad0, pad1;
+};
+
+// the same for the mixed path: centre of mass as float-float, Q in FP32
+struct __align__(16) Mom32 {
+  float4 hi;  // cx_hi, cy_hi, cz_hi, M
+  float4 lo;  // cx_lo, cy_lo, cz_lo, 0
+  float4 q0;  // qxx, qyy, qzz, qxy
+  float4 q1;  // qxz, qyz, 0, 0
+};
+
+// ---- the context ---------------------------------------------------------
+struct p3t_ctx {
+  int device = 0;
+  int num_sms = 0;
+  p3t_params prm{};
+  int64_t cap = 0;        // particle capacity
+  int64_t node_cap = 0;   // node capacity
+  int64_t cand_cap = 0;   // neighbour-candidate capacity (pairs)
+  int64_t walk_warps = 0; // resident warps of the walk kernel
+  int64_t stack_cap = 0;  // walk stack entries per warp
+  int64_t last_n = -1;    // n of the last tree build
+  bool have_tree = false;
+  bool have_cand = false;
+
+  DevStatus *status = nullptr;
+  // root box {x0, y0, z0, L} and scalar counters
+  double *box = nullptr;
+  unsigned long long *box_bits = nullptr;  // ordered-bits min/max workspace [6]
+  int64_t *counters = nullptr;             // misc device counters [16]
+
+  // sort
+  uint64_t *keys = nullptr, *keys_alt = nullptr;
+  int32_t *idx = nullptr, *idx_alt = nullptr;
+  uint32_t *radix_hist = nullptr;
+  int64_t radix_hist_cap = 0;
+  int64_t *scan_part = nullptr;           // scan partials
+
+  // sorted particles (FP64 and mixed packings)
+  double *sx = nullptr, *sy = nullptr, *sz = nullptr, *sm = nullptr;
+  double *sro = nullptr, *srs = nullptr;
+  int32_t *sq = nullptr;                   // 3 * cap quantised coordinates
+  float4 *spA = nullptr, *spB = nullptr;   // {x_hi,y_hi,z_hi,m}, {x_lo,y_lo,z_lo,1/r_out}
+  float *srs32 = nullptr;                  // r_search in FP32
+
+  // tree build scratch (per particle)
+  int8_t *lp = nullptr, *lv = nullptr;     // lcp with predecessor, leaf level
+  int32_t *wlcp = nullptr;                 // lcp(a, a + leaf)
+  int32_t *ncount = nullptr;               // nodes started by particle
+  int64_t *nstart = nullptr;               // exclusive scan of ncount
+  // nodes (preorder scratch and breadth-first result)
+  int32_t *pre_first = nullptr, *pre_count = nullptr, *pre_level = nullptr;
+  uint64_t *lvl_keys = nullptr, *lvl_keys_alt = nullptr;
+  int32_t *bfs2pre = nullptr, *bfs2pre_alt = nullptr, *pre2bfs = nullptr;
+  TreeNode *node = nullptr;
+  Mom64 *mom64 = nullptr;
+  Mom32 *mom32 = nullptr;
+  double *nrs = nullptr;                   // max r_search per node
+  int32_t *node_done = nullptr;            // bottom-up arrival counters
+  int32_t *leaf_list = nullptr;            // leaves (BFS ids) in key order
+  int32_t *leaf_of = nullptr;              // sorted particle -> its leaf (BFS id)
+  int32_t *refine = nullptr;               // targets redone in FP64 (mixed path)
+  int32_t *leaf_flag = nullptr;
+  int64_t *leaf_pos = nullptr;
+  int64_t *bh_table = nullptr;             // Barnes-Hut thresholds per level
+
+  // walk
+  int32_t *walk_stack = nullptr;
+  int32_t *cand_i = nullptr, *cand_j = nullptr;  // sorted indices
+  double *acc_sorted = nullptr;            // 3 * cap, sorted order
+
+  // neighbours and clusters
+  int32_t *cand_keep = nullptr;
+  int32_t *deg = nullptr, *fill = nullptr;
+  int32_t *parent = nullptr, *label = nullptr, *csize = nullptr;
+  int32_t *flag = nullptr;
+  int64_t *pos = nullptr;
+  int32_t *singles = nullptr, *cl_mem = nullptr;
+  int64_t *cl_off = nullptr;
+  int64_t *cl_counts = nullptr;            // [4]
+  uint64_t *mkeys = nullptr, *mkeys_alt = nullptr;
+  int32_t *mvals = nullptr, *mvals_alt = nullptr;
+
+  // hard step workspace (per cluster member)
+  double *hw = nullptr;                    // 26 * cap doubles
+  int64_t *ht = nullptr;                   // time in units of dt / 2^40
+  int32_t *hl = nullptr;                   // block level
+  unsigned long long *hsteps = nullptr;    // device counter
+
+  // energy
+  double *epart = nullptr;                 // per-block partial sums
+};
+
+// ---- helpers -------------------------------------------------------------
+// kernels launched by the library in this process (diagnostics)
+void p3t_note_launches(int64_t k);
+
+#define P3T_CUDA_TRY(x)                      \
+  do {                                       \
+    cudaError_t e_ = (x);                    \
+    if (e_ != cudaSuccess) return P3T_ERR_CUDA; \
+  } while (0)
+
+static inline int64_t p3t_grid(int64_t n, int block, int64_t max_blocks) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > max_blocks) g = max_blocks;
+  return g;
+}
+
+// ---- primitives (primitives.cu) ------------------------------------------
+// Exclusive scan of n (device count *d_n, at most n_cap) int32 values into
+// int64; *d_total receives the sum.  Deterministic.
+int p3t_scan_i32_to_i64(const int32_t *in, int64_t *out, const int64_t *d_n,
+                        int64_t n_cap, int64_t *d_total, int64_t *part,
+                        cudaStream_t s);
+// Stable LSD radix sort of (key, val) on bits [begin_bit, end_bit), n from
+// device memory (at most n_cap).  Ping-pongs between the two buffers; on
+// return *keys / *vals point at the sorted data.
+int p3t_radix_sort(uint64_t **keys, int32_t **vals, uint64_t **keys_alt,
+                   int32_t **vals_alt, const int64_t *d_n, int64_t n_cap,
+                   int begin_bit, int end_bit, uint32_t *hist,
+                   int64_t hist_cap, cudaStream_t s);
+int64_t p3t_radix_hist_entries(int64_t n_cap);
+
+// ---- stages (tree.cu, walk.cu, neighbours.cu, hard.cu) -------------------
+int p3t_run_cutoffs(p3t_ctx *c, p3t_particles *p, cudaStream_t s);
+int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s);
+int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
+                       double *ay, double *az, uint64_t *counts,
+                       cudaStream_t s);
+int p3t_run_neighbours(p3t_ctx *c, const p3t_particles *p, int64_t *nb_off,
+                       int32_t *nb_idx, int64_t nb_cap, cudaStream_t s);
+int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
+                      double dt, uint64_t *n_steps, cudaStream_t s);
+int p3t_run_kick(p3t_ctx *c, p3t_particles *p, const double *ax,
+                 const double *ay, const double *az, double h, cudaStream_t s);
+int p3t_run_energy(p3t_ctx *c, const p3t_particles *p, double *out,
+                   cudaStream_t s);

@@ -1,0 +1,569 @@
+// Rows a1-a3 of the soft step: cut-off radii, Morton keys and sort, octree
+// with monopole + quadrupole moments.  Compiled with -fmad=false: the keys
+// and the integer grid geometry must be bit-identical on every IEEE machine.
+#include <math.h>
+
+#include "p3t_internal.cuh"
+
+namespace {
+
+constexpr int kBlock = 256;
+
+// order-preserving map of doubles to unsigned 64-bit integers
+__device__ __forceinline__ unsigned long long ord_bits(double v) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double ord_double(unsigned long long b) {
+  b = (b >> 63) ? (b & 0x7fffffffffffffffull) : ~b;
+  return __longlong_as_double((long long)b);
+}
+
+// =========================================================================
+// Row a1: cut-off radii (Eq. routi2, Eq. rsearch).  Random velocity
+// u = v - sqrt(G M_* / |x|) phi_hat (phi_hat: cylindrical azimuth),
+// v_ran = rms |u| over radial bins uniform in ln R_cyl.
+// =========================================================================
+__global__ void k_cut_init(unsigned long long *bits, double *bsum,
+                           unsigned long long *bcnt, int nb) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) { bits[0] = ~0ull; bits[1] = 0ull; }
+  for (int k = t; k < nb; k += gridDim.x * blockDim.x) { bsum[k] = 0.0; bcnt[k] = 0ull; }
+}
+
+__global__ void k_cut_range(int64_t n, const double *x, const double *y,
+                            unsigned long long *bits) {
+  unsigned long long lo = ~0ull, hi = 0ull;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long b = ord_bits(sqrt(x[i] * x[i] + y[i] * y[i]));
+    lo = b < lo ? b : lo;
+    hi = b > hi ? b : hi;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long a = __shfl_xor_sync(0xffffffffu, lo, o);
+    unsigned long long c = __shfl_xor_sync(0xffffffffu, hi, o);
+    lo = a < lo ? a : lo;
+    hi = c > hi ? c : hi;
+  }
+  if ((threadIdx.x & 31) == 0) { atomicMin(&bits[0], lo); atomicMax(&bits[1], hi); }
+}
+
+__device__ __forceinline__ int cut_bin(double R, double Rmin, double Rmax,
+                                       double lmin, double lmax, int nb) {
+  int k = 0;
+  if (Rmax > Rmin && R > Rmin) {
+    double t = (log(R) - lmin) / (lmax - lmin);
+    double f = floor(t * (double)nb);
+    k = f < 0.0 ? 0 : (f > (double)(nb - 1) ? nb - 1 : (int)f);
+  }
+  return k;
+}
+
+__global__ void k_cut_bins(int64_t n, const double *x, const double *y,
+                           const double *z, const double *vx, const double *vy,
+                           const double *vz, double mu,
+                           const unsigned long long *bits, int nb, double *bsum,
+                           unsigned long long *bcnt) {
+  extern __shared__ double s_sum[];
+  unsigned int *s_cnt = reinterpret_cast<unsigned int *>(s_sum + nb);
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) { s_sum[k] = 0.0; s_cnt[k] = 0u; }
+  __syncthreads();
+  const double Rmin = ord_double(bits[0]), Rmax = ord_double(bits[1]);
+  const double lmin = log(Rmin), lmax = log(Rmax);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double R = sqrt(x[i] * x[i] + y[i] * y[i]);
+    double r = sqrt(x[i] * x[i] + y[i] * y[i] + z[i] * z[i]);
+    double vk = sqrt(mu / r);
+    double px = 0.0, py = 0.0;
+    if (R > 0.0) { px = -y[i] / R; py = x[i] / R; }
+    double ux = vx[i] - vk * px, uy = vy[i] - vk * py, uz = vz[i];
+    double u2 = ux * ux + uy * uy + uz * uz;
+    int k = cut_bin(R, Rmin, Rmax, lmin, lmax, nb);
+    atomicAdd(&s_sum[k], u2);
+    atomicAdd(&s_cnt[k], 1u);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+    if (s_cnt[k]) {
+      atomicAdd(&bsum[k], s_sum[k]);
+      atomicAdd(&bcnt[k], (unsigned long long)s_cnt[k]);
+    }
+  }
+}
+
+__global__ void k_cut_final(int64_t n, const double *x, const double *y,
+                            const double *z, const double *vx, const double *vy,
+                            const double *vz, const double *m, p3t_params prm,
+                            const unsigned long long *bits, int nb,
+                            const double *bsum, const unsigned long long *bcnt,
+                            double *r_out, double *r_search) {
+  const double mu = prm.G * prm.m_star;
+  const double Rmin = ord_double(bits[0]), Rmax = ord_double(bits[1]);
+  const double lmin = log(Rmin), lmax = log(Rmax);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double R = sqrt(x[i] * x[i] + y[i] * y[i]);
+    double r = sqrt(x[i] * x[i] + y[i] * y[i] + z[i] * z[i]);
+    double v2 = vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i];
+    double alpha = 2.0 / r - v2 / mu;  // 1/a, vis-viva
+    double a = alpha > 0.0 ? 1.0 / alpha : r;
+    double rhill = cbrt(m[i] / (3.0 * prm.m_star)) * a;
+    int k = cut_bin(R, Rmin, Rmax, lmin, lmax, nb);
+    double vr = sqrt(bsum[k] / (double)bcnt[k]);
+    double ro = fmax(prm.rcut0 * rhill, prm.rcut1 * vr * prm.dt_soft);
+    r_out[i] = ro;
+    r_search[i] = prm.rs0 * ro + prm.rs1 * vr * prm.dt_soft;
+  }
+}
+
+// =========================================================================
+// Rows a2-a3: keys, sort, octree, moments.
+// =========================================================================
+__global__ void k_set_i64(int64_t *dst, int64_t v) { *dst = v; }
+
+// node count clamped to the capacity (kernels index with the clamped value)
+__global__ void k_clamp_nodes(int64_t *cnt, int64_t node_cap, DevStatus *st) {
+  const int64_t nn = cnt[1];
+  if (nn > node_cap) dev_fail(st, P3T_ERR_CAPACITY, 10, nn);
+  cnt[3] = nn < node_cap ? nn : node_cap;
+}
+__global__ void k_box_init(unsigned long long *bits) {
+  if (threadIdx.x < 3) { bits[threadIdx.x] = ~0ull; bits[3 + threadIdx.x] = 0ull; }
+}
+
+__global__ void k_box(int64_t n, const double *x, const double *y,
+                      const double *z, unsigned long long *bits) {
+  unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long b[3] = {ord_bits(x[i]), ord_bits(y[i]), ord_bits(z[i])};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { lo[a] = b[a] < lo[a] ? b[a] : lo[a]; hi[a] = b[a] > hi[a] ? b[a] : hi[a]; }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long u = __shfl_xor_sync(0xffffffffu, lo[a], o);
+      unsigned long long v = __shfl_xor_sync(0xffffffffu, hi[a], o);
+      lo[a] = u < lo[a] ? u : lo[a];
+      hi[a] = v > hi[a] ? v : hi[a];
+    }
+    if ((threadIdx.x & 31) == 0) { atomicMin(&bits[a], lo[a]); atomicMax(&bits[3 + a], hi[a]); }
+  }
+}
+
+// root cube: corner at the per-axis minimum, side = largest extent
+__global__ void k_box_final(const unsigned long long *bits, double *box) {
+  double lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) { lo[a] = ord_double(bits[a]); hi[a] = ord_double(bits[3 + a]); }
+  double L = fmax(hi[0] - lo[0], fmax(hi[1] - lo[1], hi[2] - lo[2]));
+  if (!(L > 0.0)) L = 1.0;
+  box[0] = lo[0]; box[1] = lo[1]; box[2] = lo[2]; box[3] = L;
+}
+
+__device__ __forceinline__ uint64_t spread3(uint64_t v) {
+  v &= 0x1fffffull;
+  v = (v | (v << 32)) & 0x1f00000000ffffull;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+  v = (v | (v << 8)) & 0x100f00f00f00f00full;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
+}
+__device__ __forceinline__ uint32_t compact3(uint64_t v) {
+  v &= 0x1249249249249249ull;
+  v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+  v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+  v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+  v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+  v = (v ^ (v >> 32)) & 0x1fffffull;
+  return (uint32_t)v;
+}
+
+__device__ __forceinline__ uint64_t quantise(double v, double lo, double L) {
+  double t = (v - lo) / L;
+  double f = floor(t * (double)P3T_QMAX);
+  if (f < 0.0) f = 0.0;
+  if (f > (double)(P3T_QMAX - 1)) f = (double)(P3T_QMAX - 1);
+  return (uint64_t)f;
+}
+
+__global__ void k_keys(int64_t n, const double *x, const double *y,
+                       const double *z, const double *box, uint64_t *keys,
+                       int32_t *idx) {
+  const double x0 = box[0], y0 = box[1], z0 = box[2], L = box[3];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t qx = quantise(x[i], x0, L), qy = quantise(y[i], y0, L), qz = quantise(z[i], z0, L);
+    keys[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+    idx[i] = (int32_t)i;
+  }
+}
+
+// gather sorted copies (FP64 and the float-float packing of the mixed path)
+__global__ void k_gather(int64_t n, const int32_t *idx, const uint64_t *keys,
+                         const double *x, const double *y, const double *z,
+                         const double *m, const double *ro, const double *rs,
+                         double *sx, double *sy, double *sz, double *sm,
+                         double *sro, double *srs, int32_t *sq, float4 *spA,
+                         float4 *spB, float *srs32) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = idx[s];
+    const double X = x[i], Y = y[i], Z = z[i], M = m[i], RO = ro[i], RS = rs[i];
+    sx[s] = X; sy[s] = Y; sz[s] = Z; sm[s] = M; sro[s] = RO; srs[s] = RS;
+    const uint64_t k = keys[s];
+    sq[3 * s + 0] = (int32_t)compact3(k >> 2);
+    sq[3 * s + 1] = (int32_t)compact3(k >> 1);
+    sq[3 * s + 2] = (int32_t)compact3(k);
+    const float xh = (float)X, yh = (float)Y, zh = (float)Z;
+    spA[s] = make_float4(xh, yh, zh, (float)M);
+    spB[s] = make_float4((float)(X - (double)xh), (float)(Y - (double)yh),
+                         (float)(Z - (double)zh), (float)(1.0 / RO));
+    srs32[s] = (float)RS;
+  }
+}
+
+// common prefix of two keys in levels (0..21)
+__device__ __forceinline__ int lcp_levels(uint64_t a, uint64_t b) {
+  uint64_t d = a ^ b;
+  if (d == 0) return P3T_BITS;
+  return (__clzll((long long)d) - 1) / 3;
+}
+
+__global__ void k_lcp(int64_t n, const uint64_t *keys, int leaf, int32_t *wlcp,
+                      int8_t *lp) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = keys[i];
+    lp[i] = (int8_t)(i == 0 ? -1 : lcp_levels(keys[i - 1], k));
+    if (i + leaf < n) wlcp[i] = lcp_levels(k, keys[i + leaf]);
+  }
+}
+
+// Leaf level of each particle and the number of nodes it starts.  The cell of
+// i at level l holds more than `leaf` particles iff some window of leaf + 1
+// consecutive sorted particles containing i shares the level-l prefix.
+__global__ void k_levels(int64_t n, int leaf, const int32_t *wlcp,
+                         const int8_t *lp, int8_t *lv, int32_t *ncount) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int D = -1;
+    int64_t a0 = i - leaf > 0 ? i - leaf : 0;
+    int64_t a1 = i < n - 1 - leaf ? i : n - 1 - leaf;
+    for (int64_t a = a0; a <= a1; ++a) D = max(D, (int)wlcp[a]);
+    int L = min(D + 1, P3T_BITS);
+    lv[i] = (int8_t)L;
+    ncount[i] = max(0, L - (int)lp[i]);
+  }
+}
+
+// first index e > i (or n) whose key leaves i's level-l cell
+__device__ __forceinline__ int64_t cell_end(const uint64_t *keys, int64_t n,
+                                            int64_t i, int l) {
+  if (l == 0) return n;
+  const uint64_t ki = keys[i];
+  int64_t lo = i + 1, hi = n;  // answer in [lo, hi]
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (lcp_levels(ki, keys[mid]) >= l) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_nodes_pre(int64_t n, const uint64_t *keys, const int8_t *lp,
+                            const int8_t *lv, const int64_t *nstart,
+                            const int64_t *d_nnode, int64_t node_cap,
+                            int32_t *pre_first, int32_t *pre_count,
+                            int32_t *pre_level, uint64_t *lvl_keys,
+                            int32_t *bfs2pre, DevStatus *st) {
+  if (*d_nnode > node_cap || st->code != 0) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int l0 = (int)lp[i] + 1, L = (int)lv[i];
+    int64_t id = nstart[i];
+    for (int l = l0; l <= L; ++l, ++id) {
+      pre_first[id] = (int32_t)i;
+      pre_count[id] = (int32_t)(cell_end(keys, n, i, l) - i);
+      pre_level[id] = l;
+      lvl_keys[id] = (uint64_t)l;
+      bfs2pre[id] = (int32_t)id;
+    }
+  }
+}
+
+__global__ void k_pre2bfs(const int64_t *d_nnode, int64_t node_cap,
+                          const int32_t *bfs2pre, int32_t *pre2bfs) {
+  const int64_t nn = min(*d_nnode, node_cap);
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nn;
+       b += (int64_t)gridDim.x * blockDim.x)
+    pre2bfs[bfs2pre[b]] = (int32_t)b;
+}
+
+__global__ void k_nodes_bfs(const int64_t *d_nnode, int64_t node_cap,
+                            const int32_t *bfs2pre, const int32_t *pre2bfs,
+                            const int32_t *pre_first, const int32_t *pre_count,
+                            const int32_t *pre_level, const int8_t *lp,
+                            const int8_t *lv, const int64_t *nstart,
+                            const int32_t *sq, TreeNode *node,
+                            int32_t *leaf_flag, int32_t *node_done, DevStatus *st) {
+  const int64_t nn = min(*d_nnode, node_cap);
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nn;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t pre = bfs2pre[b];
+    const int32_t first = pre_first[pre], count = pre_count[pre], l = pre_level[pre];
+    TreeNode nd;
+    nd.level = l;
+    nd.first = first;
+    nd.count = count;
+    const int sh = P3T_BITS - l;
+    for (int a = 0; a < 3; ++a) nd.c2[a] = (2 * (sq[3 * first + a] >> sh) + 1) << sh;
+    const bool internal = l < (int)lv[first];
+    leaf_flag[pre] = internal ? 0 : 1;
+    node_done[b] = 0;
+    if (internal && pre + 1 < nn) {
+      nd.child0 = pre2bfs[pre + 1];
+      const int64_t e = (int64_t)first + count;
+      int k = 0;
+      int64_t c = pre + 1;
+      for (;;) {
+        ++k;
+        const int64_t cend = (int64_t)pre_first[c] + pre_count[c];
+        if (cend >= e) break;
+        c = nstart[cend] + (l + 1) - ((int)lp[cend] + 1);
+        if (k >= 8 || c <= pre || c >= nn) {  // cannot happen in a consistent tree
+          dev_fail(st, P3T_ERR_INVALID, 11, 0);
+          break;
+        }
+      }
+      nd.nchild = k;
+    } else {
+      nd.child0 = -1;
+      nd.nchild = 0;
+    }
+    // geometry (qlo, qhi, R) is filled bottom-up by k_moments and the parent
+    // links by k_parents
+    TreeNode *o = &node[b];
+    o->level = nd.level; o->first = nd.first; o->count = nd.count;
+    o->c2[0] = nd.c2[0]; o->c2[1] = nd.c2[1]; o->c2[2] = nd.c2[2];
+    o->child0 = nd.child0; o->nchild = nd.nchild;
+    o->parent = -1;  // set for children by k_parents
+  }
+}
+
+__global__ void k_parents(const int64_t *d_nnode, int64_t node_cap, TreeNode *node) {
+  const int64_t nn = min(*d_nnode, node_cap);
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nn;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c0 = node[b].child0, nc = node[b].nchild;
+    if (nc > 0 && (c0 <= b || (int64_t)c0 + nc > nn)) continue;  // inconsistent: skip
+    for (int k = 0; k < nc; ++k) node[c0 + k].parent = (int32_t)b;
+  }
+}
+
+__global__ void k_leaf_list(const int64_t *d_nnode, int64_t node_cap,
+                            const int32_t *leaf_flag, const int64_t *leaf_pos,
+                            const int32_t *pre2bfs, int32_t *leaf_list) {
+  const int64_t nn = min(*d_nnode, node_cap);
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nn;
+       p += (int64_t)gridDim.x * blockDim.x)
+    if (leaf_flag[p]) leaf_list[leaf_pos[p]] = pre2bfs[p];
+}
+
+__device__ __forceinline__ void finish_node(TreeNode *nd, Mom64 *m64, Mom32 *m32,
+                                            double rsmax, double u, int64_t b,
+                                            const Mom64 &mm) {
+  double rq = ceil(rsmax / u) + 1.0;
+  nd->R = rq < 8388608.0 ? (int32_t)rq : 8388608;
+  m64[b] = mm;
+  Mom32 f;
+  const float hx = (float)mm.cx, hy = (float)mm.cy, hz = (float)mm.cz;
+  f.hi = make_float4(hx, hy, hz, (float)mm.M);
+  f.lo = make_float4((float)(mm.cx - (double)hx), (float)(mm.cy - (double)hy),
+                     (float)(mm.cz - (double)hz), 0.f);
+  f.q0 = make_float4((float)mm.qxx, (float)mm.qyy, (float)mm.qzz, (float)mm.qxy);
+  f.q1 = make_float4((float)mm.qxz, (float)mm.qyz, 0.f, 0.f);
+  m32[b] = f;
+}
+
+// Bottom-up moments.  One thread per leaf computes the leaf from its
+// particles (definition: com, then Q about com); the last child to arrive at
+// a parent combines the children (parallel-axis shift of Q) and climbs on.
+__global__ void k_moments(const int64_t *d_nleaf, const int32_t *leaf_list,
+                          TreeNode *node, Mom64 *m64, Mom32 *m32, double *nrs,
+                          int32_t *node_done, const double *sx, const double *sy,
+                          const double *sz, const double *sm, const double *srs,
+                          const int32_t *sq, const double *box, int32_t *leaf_of) {
+  const int64_t nleaf = *d_nleaf;
+  const double u = ldexp(box[3], -P3T_BITS);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nleaf;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = leaf_list[t];
+    TreeNode *nd = &node[b];
+    const int32_t f = nd->first, c = nd->count;
+    Mom64 mm = {};
+    double M = 0.0, sxm = 0.0, sym = 0.0, szm = 0.0, rsmax = 0.0;
+    int32_t qlo[3] = {P3T_QMAX, P3T_QMAX, P3T_QMAX}, qhi[3] = {-1, -1, -1};
+    for (int32_t i = f; i < f + c; ++i) {
+      leaf_of[i] = (int32_t)b;
+      M += sm[i]; sxm += sm[i] * sx[i]; sym += sm[i] * sy[i]; szm += sm[i] * sz[i];
+      rsmax = fmax(rsmax, srs[i]);
+      for (int a = 0; a < 3; ++a) { qlo[a] = min(qlo[a], sq[3 * i + a]); qhi[a] = max(qhi[a], sq[3 * i + a]); }
+    }
+    mm.M = M; mm.cx = sxm / M; mm.cy = sym / M; mm.cz = szm / M;
+    for (int32_t i = f; i < f + c; ++i) {
+      double dx = sx[i] - mm.cx, dy = sy[i] - mm.cy, dz = sz[i] - mm.cz;
+      double d2 = dx * dx + dy * dy + dz * dz;
+      mm.qxx += sm[i] * (3.0 * dx * dx - d2);
+      mm.qyy += sm[i] * (3.0 * dy * dy - d2);
+      mm.qzz += sm[i] * (3.0 * dz * dz - d2);
+      mm.qxy += sm[i] * (3.0 * dx * dy);
+      mm.qxz += sm[i] * (3.0 * dx * dz);
+      mm.qyz += sm[i] * (3.0 * dy * dz);
+    }
+    for (int a = 0; a < 3; ++a) { nd->qlo[a] = qlo[a]; nd->qhi[a] = qhi[a]; }
+    nrs[b] = rsmax;
+    finish_node(nd, m64, m32, rsmax, u, b, mm);
+    // climb
+    for (;;) {
+      const int32_t par = nd->parent;
+      if (par < 0) break;
+      __threadfence();
+      const int32_t prev = atomicAdd(&node_done[par], 1);
+      TreeNode *pn = &node[par];
+      const int32_t c0 = __ldcg(&pn->child0), nc = __ldcg(&pn->nchild);
+      if (prev != nc - 1) break;
+      __threadfence();
+      Mom64 pm = {};
+      double PM = 0.0, px = 0.0, py = 0.0, pz = 0.0, prs = 0.0;
+      int32_t plo[3] = {P3T_QMAX, P3T_QMAX, P3T_QMAX}, phi[3] = {-1, -1, -1};
+      for (int k = 0; k < nc; ++k) {
+        const Mom64 *cm = &m64[c0 + k];
+        const double cM = __ldcg(&cm->M);
+        PM += cM;
+        px += cM * __ldcg(&cm->cx); py += cM * __ldcg(&cm->cy); pz += cM * __ldcg(&cm->cz);
+        prs = fmax(prs, __ldcg(&nrs[c0 + k]));
+        const TreeNode *cn = &node[c0 + k];
+        for (int a = 0; a < 3; ++a) {
+          plo[a] = min(plo[a], __ldcg(&cn->qlo[a]));
+          phi[a] = max(phi[a], __ldcg(&cn->qhi[a]));
+        }
+      }
+      pm.M = PM; pm.cx = px / PM; pm.cy = py / PM; pm.cz = pz / PM;
+      for (int k = 0; k < nc; ++k) {
+        const Mom64 *cm = &m64[c0 + k];
+        const double cM = __ldcg(&cm->M);
+        const double dx = __ldcg(&cm->cx) - pm.cx, dy = __ldcg(&cm->cy) - pm.cy,
+                     dz = __ldcg(&cm->cz) - pm.cz;
+        const double d2 = dx * dx + dy * dy + dz * dz;
+        pm.qxx += __ldcg(&cm->qxx) + cM * (3.0 * dx * dx - d2);
+        pm.qyy += __ldcg(&cm->qyy) + cM * (3.0 * dy * dy - d2);
+        pm.qzz += __ldcg(&cm->qzz) + cM * (3.0 * dz * dz - d2);
+        pm.qxy += __ldcg(&cm->qxy) + cM * (3.0 * dx * dy);
+        pm.qxz += __ldcg(&cm->qxz) + cM * (3.0 * dx * dz);
+        pm.qyz += __ldcg(&cm->qyz) + cM * (3.0 * dy * dz);
+      }
+      for (int a = 0; a < 3; ++a) { pn->qlo[a] = plo[a]; pn->qhi[a] = phi[a]; }
+      nrs[par] = prs;
+      finish_node(pn, m64, m32, prs, u, par, pm);
+      nd = pn;
+    }
+  }
+}
+
+__global__ void k_tree_stats(const int64_t *d_nnode, int64_t node_cap,
+                             const TreeNode *node, int64_t *stats) {
+  const int64_t nn = min(*d_nnode, node_cap);
+  unsigned long long depth = 0, maxleaf = 0, nleaf = 0;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nn;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    depth = max(depth, (unsigned long long)node[b].level);
+    if (node[b].nchild == 0) { ++nleaf; maxleaf = max(maxleaf, (unsigned long long)node[b].count); }
+  }
+  atomicMax(reinterpret_cast<unsigned long long *>(&stats[2]), depth);
+  atomicMax(reinterpret_cast<unsigned long long *>(&stats[3]), maxleaf);
+  atomicAdd(reinterpret_cast<unsigned long long *>(&stats[1]), nleaf);
+}
+
+}  // namespace
+
+// counters layout (int64): [0] n, [1] nodes, [2] leaves, [3] nodes clamped to
+// the capacity, [4..7] tree stats, [8] candidates, [9] candidates clamped,
+// [10] neighbour entries, [11] cluster members, [12] walk group cursor
+int p3t_run_cutoffs(p3t_ctx *c, p3t_particles *p, cudaStream_t s) {
+  const int64_t n = p->n;
+  if (n == 0) return P3T_OK;
+  int nb = c->prm.vran_bins;
+  if (nb <= 0) { int64_t t = n / 1000; nb = (int)(t < 1 ? 1 : (t > 1024 ? 1024 : t)); }
+  if (nb > 4096) return P3T_ERR_INVALID;
+  double *bsum = c->epart;  // reuse: >= 4096 doubles
+  unsigned long long *bcnt = reinterpret_cast<unsigned long long *>(c->epart + 4096);
+  const int64_t g = p3t_grid(n, kBlock, (int64_t)c->num_sms * P3T_NSM_BLOCKS);
+  k_cut_init<<<4, kBlock, 0, s>>>(c->box_bits, bsum, bcnt, nb);
+  k_cut_range<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, c->box_bits);
+  const double mu = c->prm.G * c->prm.m_star;
+  k_cut_bins<<<(unsigned)g, kBlock, nb * (sizeof(double) + sizeof(unsigned)), s>>>(
+      n, p->x, p->y, p->z, p->vx, p->vy, p->vz, mu, c->box_bits, nb, bsum, bcnt);
+  k_cut_final<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, p->z, p->vx, p->vy,
+                                             p->vz, p->m, c->prm, c->box_bits, nb,
+                                             bsum, bcnt, p->r_out, p->r_search);
+  p3t_note_launches(4);
+  return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
+}
+
+int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
+  const int64_t n = p->n;
+  const int leaf = c->prm.leaf_size;
+  const int64_t maxb = (int64_t)c->num_sms * P3T_NSM_BLOCKS;
+  const int64_t g = p3t_grid(n, kBlock, maxb);
+  int64_t *cnt = c->counters;
+  int rc;
+  // n on the device for the count-driven primitives
+  k_box_init<<<1, 32, 0, s>>>(c->box_bits);
+  k_box<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, p->z, c->box_bits);
+  k_box_final<<<1, 1, 0, s>>>(c->box_bits, c->box);
+  k_keys<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, p->z, c->box, c->keys, c->idx);
+  k_set_i64<<<1, 1, 0, s>>>(&cnt[0], n);
+  rc = p3t_radix_sort(&c->keys, &c->idx, &c->keys_alt, &c->idx_alt, &cnt[0], c->cap,
+                      0, 64, c->radix_hist, c->radix_hist_cap, s);
+  if (rc) return rc;
+  k_gather<<<(unsigned)g, kBlock, 0, s>>>(n, c->idx, c->keys, p->x, p->y, p->z, p->m,
+                                          p->r_out, p->r_search, c->sx, c->sy, c->sz,
+                                          c->sm, c->sro, c->srs, c->sq, c->spA, c->spB,
+                                          c->srs32);
+  k_lcp<<<(unsigned)g, kBlock, 0, s>>>(n, c->keys, leaf, c->wlcp, c->lp);
+  k_levels<<<(unsigned)g, kBlock, 0, s>>>(n, leaf, c->wlcp, c->lp, c->lv, c->ncount);
+  rc = p3t_scan_i32_to_i64(c->ncount, c->nstart, &cnt[0], c->cap, &cnt[1], c->scan_part, s);
+  if (rc) return rc;
+  k_clamp_nodes<<<1, 1, 0, s>>>(cnt, c->node_cap, c->status);
+  k_nodes_pre<<<(unsigned)g, kBlock, 0, s>>>(n, c->keys, c->lp, c->lv, c->nstart, &cnt[1],
+                                             c->node_cap, c->pre_first, c->pre_count,
+                                             c->pre_level, c->lvl_keys, c->bfs2pre, c->status);
+  rc = p3t_radix_sort(&c->lvl_keys, &c->bfs2pre, &c->lvl_keys_alt, &c->bfs2pre_alt, &cnt[3],
+                      c->node_cap, 0, 8, c->radix_hist, c->radix_hist_cap, s);
+  if (rc) return rc;
+  const int64_t gn = p3t_grid(c->node_cap, kBlock, maxb);
+  k_pre2bfs<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->bfs2pre, c->pre2bfs);
+  k_nodes_bfs<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->bfs2pre, c->pre2bfs,
+                                              c->pre_first, c->pre_count, c->pre_level,
+                                              c->lp, c->lv, c->nstart, c->sq, c->node,
+                                              c->leaf_flag, c->node_done, c->status);
+  k_parents<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->node);
+  rc = p3t_scan_i32_to_i64(c->leaf_flag, c->leaf_pos, &cnt[3], c->node_cap, &cnt[2],
+                           c->scan_part, s);
+  if (rc) return rc;
+  k_leaf_list<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->leaf_flag,
+                                              c->leaf_pos, c->pre2bfs, c->leaf_list);
+  k_moments<<<(unsigned)gn, 128, 0, s>>>(&cnt[2], c->leaf_list, c->node, c->mom64, c->mom32,
+                                         c->nrs, c->node_done, c->sx, c->sy, c->sz, c->sm,
+                                         c->srs, c->sq, c->box, c->leaf_of);
+  P3T_CUDA_TRY(cudaMemsetAsync(&cnt[4], 0, 4 * sizeof(int64_t), s));
+  k_tree_stats<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->node, &cnt[4]);
+  // own kernels here (the scans and sorts count themselves): box 3, keys, n,
+  // gather, lcp, levels, clamp, nodes_pre, pre2bfs, nodes_bfs, parents,
+  // leaf_list, moments, tree_stats
+  p3t_note_launches(16);
+  return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
+}

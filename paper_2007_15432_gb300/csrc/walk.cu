@@ -1,0 +1,624 @@
+// Row a4 of the soft step: the changeover tree walk (Eq. softforce).
+//
+// One warp per target group (a leaf of <= 16 particles; larger level-21 leaves
+// are taken 16 targets at a time).  Two lanes per target, each taking every
+// other entry of a batch of 32 list entries.  The walk pops up to 32 nodes at
+// a time from a per-warp stack, decides opening for all of them at once on
+// the integer grid, and compacts accepted nodes, opened leaves and children
+// with warp ballots / scans into shared-memory lists that are evaluated in
+// batches of 32.
+//
+// Mixed path: positions are float-float (hi + lo) pairs, so a relative
+// coordinate (x_i,hi - x_j,hi) + (x_i,lo - x_j,lo) carries the accuracy of an
+// FP64 subtraction rounded to FP32, with no FP64 instruction per pair.  Pair
+// and quadrupole terms are FP32; each batch's FP32 sum is folded into a
+// float-float accumulator.  FP64 path: everything in FP64.
+#include "p3t_internal.cuh"
+
+namespace {
+
+constexpr int kWarps = 4;                 // warps per block
+constexpr int kPPCap = 32 * 33;           // p-p list: leftover < 32 + 32 leaves x <= 32
+constexpr int kNDCap = 64;                // node list: leftover < 32 + 32 nodes
+constexpr int kBigCap = 8;                // opened leaves with more than 32 members
+constexpr float kCandMargin = 1.00001f;   // FP32 candidate test is widened by 1e-5
+
+struct WalkArgs {
+  const TreeNode *node;
+  const Mom64 *mom64;
+  const Mom32 *mom32;
+  const int32_t *leaf_list;
+  const int64_t *d_nleaf;
+  const int64_t *d_nnode;
+  const double *sx, *sy, *sz, *sm, *sro, *srs;
+  const float4 *spA, *spB;
+  const float *srs32;
+  const int32_t *idx;        // sorted -> caller
+  double *ax, *ay, *az;      // caller order
+  int32_t *stack;
+  int64_t stack_cap;
+  int32_t *cand_i, *cand_j;
+  int64_t cand_cap;
+  unsigned long long *cand_count;
+  unsigned long long *counts;  // [2] n_pp, n_pnode (may be null)
+  int64_t *cursor;
+  DevStatus *st;
+  int32_t *refine;                 // targets whose FP32 sum is ill-conditioned
+  unsigned long long *refine_count;
+  int64_t refine_cap;
+  const int64_t *d_nrefine;        // refine count clamped to the capacity
+  const int32_t *leaf_of;          // sorted index -> its leaf (BFS id)
+  double G, gamma;
+  float gamma_f, inv1mg_f;
+  float refine_cf;                 // refine when sum|term| > refine_cf * |a|
+  int64_t bh[P3T_BITS + 1];
+};
+
+// integer box of a target group (a leaf) on the key grid
+struct GroupBox {
+  int32_t qlo0, qlo1, qlo2, qhi0, qhi1, qhi2, R;
+  __device__ void load(const TreeNode &G) {
+    qlo0 = G.qlo[0]; qlo1 = G.qlo[1]; qlo2 = G.qlo[2];
+    qhi0 = G.qhi[0]; qhi1 = G.qhi[1]; qhi2 = G.qhi[2];
+    R = G.R;
+  }
+};
+
+__device__ __forceinline__ int warp_excl_scan(int v, int *total) {
+  const int lane = threadIdx.x & 31;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += t;
+  }
+  *total = __shfl_sync(0xffffffffu, x, 31);
+  return x - v;
+}
+
+__device__ __forceinline__ void two_sum(float &hi, float &lo, float b) {
+  const float s = hi + b;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (b - bb);
+  hi = s;
+  lo += err;
+}
+
+// ---- per-target state ----------------------------------------------------
+template <bool MIXED> struct Target;
+
+template <> struct Target<true> {
+  float xh, yh, zh, xl, yl, zl, inv_ro, rs;
+  float ahx, ahy, ahz, alx, aly, alz;  // float-float accumulators
+  float tabs;                          // sum of term magnitudes (conditioning)
+  int32_t self;
+  bool valid;
+  __device__ void load(const WalkArgs &a, int32_t ti, bool v) {
+    valid = v;
+    self = ti;
+    ahx = ahy = ahz = alx = aly = alz = 0.f;
+    tabs = 0.f;
+    if (v) {
+      const float4 A = a.spA[ti], B = a.spB[ti];
+      xh = A.x; yh = A.y; zh = A.z; xl = B.x; yl = B.y; zl = B.z; inv_ro = B.w;
+      rs = a.srs32[ti];
+    } else {
+      xh = yh = zh = 3.0e30f; xl = yl = zl = 0.f; inv_ro = 0.f; rs = 0.f;
+    }
+  }
+  __device__ void fold(float bx, float by, float bz) {
+    two_sum(ahx, alx, bx); two_sum(ahy, aly, by); two_sum(ahz, alz, bz);
+  }
+};
+
+template <> struct Target<false> {
+  double x, y, z, ro, rs;
+  double ax, ay, az;
+  int32_t self;
+  bool valid;
+  __device__ void load(const WalkArgs &a, int32_t ti, bool v) {
+    valid = v;
+    self = ti;
+    ax = ay = az = 0.0;
+    if (v) {
+      x = a.sx[ti]; y = a.sy[ti]; z = a.sz[ti]; ro = a.sro[ti]; rs = a.srs[ti];
+    } else {
+      x = y = z = 1.0e300; ro = 1.0; rs = 0.0;
+    }
+  }
+};
+
+__device__ __forceinline__ void record_candidate(const WalkArgs &a, int32_t i,
+                                                 int32_t j) {
+  const unsigned long long slot = atomicAdd(a.cand_count, 1ull);
+  if (slot < (unsigned long long)a.cand_cap) {
+    a.cand_i[slot] = i;
+    a.cand_j[slot] = j;
+  }
+}
+
+// ---- particle-particle batch ----------------------------------------------
+__device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<true> &t,
+                                        const int32_t *list, int nsrc, int h,
+                                        unsigned &npp) {
+  float bx = 0.f, by = 0.f, bz = 0.f;
+#pragma unroll 2
+  for (int s = h; s < nsrc; s += 2) {
+    const int32_t j = list[s];
+    const float4 A = __ldg(&a.spA[j]);
+    const float4 B = __ldg(&a.spB[j]);
+    const float dx = (t.xh - A.x) + (t.xl - B.x);
+    const float dy = (t.yh - A.y) + (t.yl - B.y);
+    const float dz = (t.zh - A.z) + (t.zl - B.z);
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    const float r = r2 * rinv;
+    const float y = r * fminf(t.inv_ro, B.w);
+    const float x = __saturatef((y - a.gamma_f) * a.inv1mg_f);
+    const float x2 = x * x;
+    const float K = (x2 * x2) * fmaf(fmaf(fmaf(-20.f, x, 70.f), x, -84.f), x, 35.f);
+    const float f = A.w * K * (rinv * rinv * rinv);
+    bx = fmaf(-f, dx, bx);
+    by = fmaf(-f, dy, by);
+    bz = fmaf(-f, dz, bz);
+    t.tabs = fmaf(f, r, t.tabs);
+    const float rsj = fmaxf(t.rs, __ldg(&a.srs32[j]));
+    if (t.valid && j != t.self && r2 < rsj * rsj * kCandMargin) record_candidate(a, t.self, j);
+    npp += (t.valid && j != t.self) ? 1u : 0u;
+  }
+  t.fold(bx, by, bz);
+}
+
+__device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<false> &t,
+                                        const int32_t *list, int nsrc, int h,
+                                        unsigned &npp) {
+  for (int s = h; s < nsrc; s += 2) {
+    const int32_t j = list[s];
+    const double dx = t.x - a.sx[j], dy = t.y - a.sy[j], dz = t.z - a.sz[j];
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    const double rinv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
+    const double r = r2 * rinv;
+    const double y = r / fmax(t.ro, a.sro[j]);
+    double x = (y - a.gamma) / (1.0 - a.gamma);
+    x = x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x);
+    const double x2 = x * x;
+    const double K = (x2 * x2) * (((-20.0 * x + 70.0) * x - 84.0) * x + 35.0);
+    const double f = a.sm[j] * K * (rinv * rinv * rinv);
+    t.ax -= f * dx; t.ay -= f * dy; t.az -= f * dz;
+    const double rsj = fmax(t.rs, a.srs[j]);
+    if (t.valid && j != t.self && r2 < rsj * rsj) record_candidate(a, t.self, j);
+    npp += (t.valid && j != t.self) ? 1u : 0u;
+  }
+}
+
+// ---- particle-node batch (monopole + traceless quadrupole) ---------------
+// a += -M r/r^3 + Q.r/r^5 - (5/2)(r.Q.r) r/r^7, r = x_i - com
+__device__ __forceinline__ void eval_nodes(const WalkArgs &a, Target<true> &t,
+                                           const int32_t *list, int nnd, int h,
+                                           unsigned &npn) {
+  float bx = 0.f, by = 0.f, bz = 0.f;
+#pragma unroll 2
+  for (int s = h; s < nnd; s += 2) {
+    const Mom32 *m = &a.mom32[list[s]];
+    const float4 hi = __ldg(&m->hi), lo = __ldg(&m->lo), q0 = __ldg(&m->q0), q1 = __ldg(&m->q1);
+    const float dx = (t.xh - hi.x) + (t.xl - lo.x);
+    const float dy = (t.yh - hi.y) + (t.yl - lo.y);
+    const float dz = (t.zh - hi.z) + (t.zl - lo.z);
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    const float rinv2 = rinv * rinv;
+    const float rinv3 = rinv2 * rinv;
+    const float rinv5 = rinv3 * rinv2;
+    const float qx = fmaf(q0.x, dx, fmaf(q0.w, dy, q1.x * dz));
+    const float qy = fmaf(q0.w, dx, fmaf(q0.y, dy, q1.y * dz));
+    const float qz = fmaf(q1.x, dx, fmaf(q1.y, dy, q0.z * dz));
+    const float rqr = fmaf(dx, qx, fmaf(dy, qy, dz * qz));
+    const float c = fmaf(-2.5f * rqr, rinv5 * rinv2, -hi.w * rinv3);
+    bx = fmaf(c, dx, fmaf(qx, rinv5, bx));
+    by = fmaf(c, dy, fmaf(qy, rinv5, by));
+    bz = fmaf(c, dz, fmaf(qz, rinv5, bz));
+    t.tabs = fmaf(hi.w, rinv2, t.tabs);
+    npn += t.valid ? 1u : 0u;
+  }
+  t.fold(bx, by, bz);
+}
+
+__device__ __forceinline__ void eval_nodes(const WalkArgs &a, Target<false> &t,
+                                           const int32_t *list, int nnd, int h,
+                                           unsigned &npn) {
+  for (int s = h; s < nnd; s += 2) {
+    const Mom64 &m = a.mom64[list[s]];
+    const double dx = t.x - m.cx, dy = t.y - m.cy, dz = t.z - m.cz;
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    const double rinv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
+    const double rinv2 = rinv * rinv, rinv3 = rinv2 * rinv, rinv5 = rinv3 * rinv2;
+    const double qx = m.qxx * dx + m.qxy * dy + m.qxz * dz;
+    const double qy = m.qxy * dx + m.qyy * dy + m.qyz * dz;
+    const double qz = m.qxz * dx + m.qyz * dy + m.qzz * dz;
+    const double rqr = dx * qx + dy * qy + dz * qz;
+    const double c = -m.M * rinv3 - 2.5 * rqr * rinv5 * rinv2;
+    t.ax += c * dx + qx * rinv5;
+    t.ay += c * dy + qy * rinv5;
+    t.az += c * dz + qz * rinv5;
+    npn += t.valid ? 1u : 0u;
+  }
+}
+
+template <bool MIXED>
+__device__ __forceinline__ void write_result(const WalkArgs &a, Target<MIXED> &t);
+
+template <>
+__device__ __forceinline__ void write_result<true>(const WalkArgs &a, Target<true> &t) {
+  double x = (double)t.ahx + (double)t.alx;
+  double y = (double)t.ahy + (double)t.aly;
+  double z = (double)t.ahz + (double)t.alz;
+  x += __shfl_xor_sync(0xffffffffu, x, 16);
+  y += __shfl_xor_sync(0xffffffffu, y, 16);
+  z += __shfl_xor_sync(0xffffffffu, z, 16);
+  const float tabs = t.tabs + __shfl_xor_sync(0xffffffffu, t.tabs, 16);
+  if (t.valid && (threadIdx.x & 16) == 0) {
+    const int32_t i = a.idx[t.self];
+    a.ax[i] = a.G * x; a.ay[i] = a.G * y; a.az[i] = a.G * z;
+    // FP32 terms carry ~1e-7 relative error each; where they cancel to a sum
+    // much smaller than their magnitudes the target is redone in FP64
+    const double amag = sqrt(x * x + y * y + z * z);
+    if ((double)tabs > (double)a.refine_cf * amag) {
+      const unsigned long long slot = atomicAdd(a.refine_count, 1ull);
+      if (slot < (unsigned long long)a.refine_cap) a.refine[slot] = t.self;
+    }
+  }
+}
+
+template <>
+__device__ __forceinline__ void write_result<false>(const WalkArgs &a, Target<false> &t) {
+  double x = t.ax + __shfl_xor_sync(0xffffffffu, t.ax, 16);
+  double y = t.ay + __shfl_xor_sync(0xffffffffu, t.ay, 16);
+  double z = t.az + __shfl_xor_sync(0xffffffffu, t.az, 16);
+  if (t.valid && (threadIdx.x & 16) == 0) {
+    const int32_t i = a.idx[t.self];
+    a.ax[i] = a.G * x; a.ay[i] = a.G * y; a.az[i] = a.G * z;
+  }
+}
+
+
+// ---- the traversal, shared by the group walk and the FP64 refinement --------
+// Pops up to 32 nodes per round, decides opening on the integer grid, and
+// hands full batches of 32 accepted nodes / leaf members to the evaluator.
+// Returns false when the walk had to stop (capacity or round bound).
+template <class Ev>
+__device__ bool traverse(const WalkArgs &a, const GroupBox &gb, int32_t *stack,
+                         int32_t *pp, int32_t *nd, int32_t *big,
+                         const int64_t *s_bh, int64_t round_limit, Ev &ev) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  int top = 1, npl = 0, nnd = 0, nbig = 0;
+  int64_t rounds = 0;
+  if (lane == 0) stack[0] = 0;
+  __syncwarp();
+  while (top > 0) {
+    if (++rounds > round_limit) {
+      if (lane == 0) dev_fail(a.st, P3T_ERR_TIMEOUT, 43, 0);
+      return false;
+    }
+    const int k = top < 32 ? top : 32;
+    top -= k;
+    int32_t id = -1;
+    bool acc_node = false, open_leaf = false, open_inner = false;
+    int32_t child0 = 0, nchild = 0, first = 0, count = 0;
+    if (lane < k) {
+      id = stack[top + lane];
+      const int4 *r = reinterpret_cast<const int4 *>(&a.node[id]);
+      const int4 q0 = __ldg(r), q1 = __ldg(r + 1), q2 = __ldg(r + 2), q3 = __ldg(r + 3);
+      // (i) Barnes-Hut on the grid: half units, group cells [2 qlo, 2 qhi + 2]
+      int64_t d2 = 0, g2 = 0;
+      {
+        int32_t d = max(0, max(2 * gb.qlo0 - q2.x, q2.x - (2 * gb.qhi0 + 2)));
+        d2 += (int64_t)d * d;
+        d = max(0, max(2 * gb.qlo1 - q2.y, q2.y - (2 * gb.qhi1 + 2)));
+        d2 += (int64_t)d * d;
+        d = max(0, max(2 * gb.qlo2 - q2.z, q2.z - (2 * gb.qhi2 + 2)));
+        d2 += (int64_t)d * d;
+      }
+      // (ii) cut-off reach: lower-bound gap against the larger search reach
+      {
+        int32_t e = max(0, max(q0.x - gb.qhi0 - 2, gb.qlo0 - q1.x - 2));
+        g2 += (int64_t)e * e;
+        e = max(0, max(q0.y - gb.qhi1 - 2, gb.qlo1 - q1.y - 2));
+        g2 += (int64_t)e * e;
+        e = max(0, max(q0.z - gb.qhi2 - 2, gb.qlo2 - q1.z - 2));
+        g2 += (int64_t)e * e;
+      }
+      const int64_t R = max(gb.R, q0.w);
+      const bool open = (d2 < s_bh[q1.w]) || (g2 < R * R);
+      child0 = q3.x; nchild = q3.y; first = q3.z; count = q3.w;
+      acc_node = !open;
+      open_leaf = open && nchild == 0;
+      open_inner = open && nchild > 0;
+    }
+    // accepted nodes -> node list
+    {
+      const unsigned m = __ballot_sync(0xffffffffu, acc_node);
+      if (acc_node) nd[nnd + __popc(m & lt)] = id;
+      nnd += __popc(m);
+    }
+    // opened big leaves (> 32 members) -> their own list
+    {
+      const bool isbig = open_leaf && count > 32;
+      const unsigned m = __ballot_sync(0xffffffffu, isbig);
+      if (isbig) {
+        const int slot = nbig + __popc(m & lt);
+        if (slot < kBigCap) big[slot] = id;
+      }
+      nbig += __popc(m);
+      if (isbig) open_leaf = false;
+    }
+    __syncwarp();  // every lane has read its stack entry before any push
+    // children of opened inner nodes -> stack
+    {
+      int tot;
+      const int c = open_inner ? nchild : 0;
+      const int off = warp_excl_scan(c, &tot);
+      if (top + tot > a.stack_cap) {
+        if (lane == 0) dev_fail(a.st, P3T_ERR_CAPACITY, 40, top + tot);
+        return false;
+      }
+      for (int q = 0; q < c; ++q) stack[top + off + q] = child0 + q;
+      top += tot;
+    }
+    // members of opened leaves -> p-p list
+    {
+      int tot;
+      const int c = open_leaf ? count : 0;
+      const int off = warp_excl_scan(c, &tot);
+      for (int q = 0; q < c; ++q) pp[npl + off + q] = first + q;
+      npl += tot;
+    }
+    __syncwarp();
+    if (nbig > kBigCap) {
+      if (lane == 0) dev_fail(a.st, P3T_ERR_CAPACITY, 41, nbig);
+      return false;
+    }
+    // evaluate full batches
+    int o = 0;
+    for (; nnd - o >= 32; o += 32) ev.nodes(nd + o, 32);
+    if (o) {
+      __syncwarp();
+      const int rem = nnd - o;
+      const int32_t v = lane < rem ? nd[o + lane] : 0;
+      __syncwarp();
+      if (lane < rem) nd[lane] = v;
+      nnd = rem;
+    }
+    o = 0;
+    for (; npl - o >= 32; o += 32) ev.pp(pp + o, 32);
+    if (o) {
+      __syncwarp();
+      const int rem = npl - o;
+      const int32_t v = lane < rem ? pp[o + lane] : 0;
+      __syncwarp();
+      if (lane < rem) pp[lane] = v;
+      npl = rem;
+    }
+    __syncwarp();
+  }
+  if (nnd) ev.nodes(nd, nnd);
+  if (npl) ev.pp(pp, npl);
+  // big leaves, 32 members at a time, straight from their index range
+  for (int b = 0; b < nbig; ++b) {
+    const TreeNode &B = a.node[big[b]];
+    for (int32_t s0 = B.first; s0 < B.first + B.count; s0 += 32) {
+      const int ns = min(32, B.first + B.count - s0);
+      __syncwarp();
+      if (lane < ns) pp[lane] = s0 + lane;
+      __syncwarp();
+      ev.pp(pp, ns);
+    }
+  }
+  __syncwarp();
+  return true;
+}
+
+// 16 targets of a group, two lanes per target (h = lane / 16)
+template <bool MIXED> struct GroupEval {
+  const WalkArgs &a;
+  Target<MIXED> &t;
+  int h;
+  unsigned &npp, &npn;
+  __device__ void nodes(const int32_t *list, int n) { eval_nodes(a, t, list, n, h, npn); }
+  __device__ void pp(const int32_t *list, int n) { eval_pp(a, t, list, n, h, npp); }
+};
+
+// one target, all 32 lanes, FP64 (the refinement of ill-conditioned targets)
+struct RefineEval {
+  const WalkArgs &a;
+  double x, y, z, ro;
+  int32_t self;
+  double ax, ay, az;
+  __device__ void pp(const int32_t *list, int n) {
+    for (int s = threadIdx.x & 31; s < n; s += 32) {
+      const int32_t j = list[s];
+      const double dx = x - a.sx[j], dy = y - a.sy[j], dz = z - a.sz[j];
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      const double rinv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
+      const double yv = r2 * rinv / fmax(ro, a.sro[j]);
+      double u = (yv - a.gamma) / (1.0 - a.gamma);
+      u = u < 0.0 ? 0.0 : (u > 1.0 ? 1.0 : u);
+      const double u2 = u * u;
+      const double K = (u2 * u2) * (((-20.0 * u + 70.0) * u - 84.0) * u + 35.0);
+      const double f = a.sm[j] * K * (rinv * rinv * rinv);
+      ax -= f * dx; ay -= f * dy; az -= f * dz;
+    }
+  }
+  __device__ void nodes(const int32_t *list, int n) {
+    for (int s = threadIdx.x & 31; s < n; s += 32) {
+      const Mom64 &m = a.mom64[list[s]];
+      const double dx = x - m.cx, dy = y - m.cy, dz = z - m.cz;
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      const double rinv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
+      const double rinv2 = rinv * rinv, rinv3 = rinv2 * rinv, rinv5 = rinv3 * rinv2;
+      const double qx = m.qxx * dx + m.qxy * dy + m.qxz * dz;
+      const double qy = m.qxy * dx + m.qyy * dy + m.qyz * dz;
+      const double qz = m.qxz * dx + m.qyz * dy + m.qzz * dz;
+      const double rqr = dx * qx + dy * qy + dz * qz;
+      const double c = -m.M * rinv3 - 2.5 * rqr * rinv5 * rinv2;
+      ax += c * dx + qx * rinv5;
+      ay += c * dy + qy * rinv5;
+      az += c * dz + qz * rinv5;
+    }
+  }
+};
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kWarps * 32) k_walk(const WalkArgs a) {
+  __shared__ int32_t s_pp[kWarps][kPPCap];
+  __shared__ int32_t s_nd[kWarps][kNDCap];
+  __shared__ int32_t s_big[kWarps][kBigCap];
+  __shared__ int64_t s_bh[P3T_BITS + 1];
+  if (threadIdx.x <= P3T_BITS) s_bh[threadIdx.x] = a.bh[threadIdx.x];
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int h = lane >> 4, tl = lane & 15;
+  int32_t *stack = a.stack + ((int64_t)blockIdx.x * kWarps + w) * a.stack_cap;
+  const int64_t nleaf = *a.d_nleaf;
+  const int64_t round_limit = *a.d_nnode + 2;  // a node is pushed at most once per walk
+  unsigned npp = 0, npn = 0;
+
+  for (;;) {
+    int64_t g = 0;
+    if (lane == 0) g = atomicAdd(reinterpret_cast<unsigned long long *>(a.cursor), 1ull);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= nleaf) break;
+    if (*(volatile int32_t *)&a.st->code != 0) break;
+    const TreeNode &G = a.node[a.leaf_list[g]];
+    GroupBox gb;
+    gb.load(G);
+    const int32_t gfirst = G.first, gcount = G.count;
+    bool ok = true;
+    for (int32_t tb = gfirst; tb < gfirst + gcount && ok; tb += 16) {
+      Target<MIXED> t;
+      t.load(a, tb + tl, tb + tl < gfirst + gcount);
+      GroupEval<MIXED> ev{a, t, h, npp, npn};
+      ok = traverse(a, gb, stack, s_pp[w], s_nd[w], s_big[w], s_bh, round_limit, ev);
+      if (ok) write_result<MIXED>(a, t);
+    }
+    if (!ok) break;
+  }
+  if (a.counts) {
+    unsigned long long p = npp, q = npn;
+    for (int o = 16; o > 0; o >>= 1) {
+      p += __shfl_xor_sync(0xffffffffu, p, o);
+      q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    if (lane == 0) { atomicAdd(&a.counts[0], p); atomicAdd(&a.counts[1], q); }
+  }
+}
+
+// FP64 redo of the targets the mixed walk flagged: one warp per target, the
+// same group box (so the same interaction list), every lane on the entries
+__global__ void __launch_bounds__(kWarps * 32) k_refine(const WalkArgs a) {
+  __shared__ int32_t s_pp[kWarps][kPPCap];
+  __shared__ int32_t s_nd[kWarps][kNDCap];
+  __shared__ int32_t s_big[kWarps][kBigCap];
+  __shared__ int64_t s_bh[P3T_BITS + 1];
+  if (threadIdx.x <= P3T_BITS) s_bh[threadIdx.x] = a.bh[threadIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t *stack = a.stack + ((int64_t)blockIdx.x * kWarps + w) * a.stack_cap;
+  const int64_t nref = *a.d_nrefine;
+  const int64_t round_limit = *a.d_nnode + 2;
+  const int64_t warp = (int64_t)blockIdx.x * kWarps + w;
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  for (int64_t q = warp; q < nref; q += nwarps) {
+    if (*(volatile int32_t *)&a.st->code != 0) break;
+    const int32_t ti = a.refine[q];
+    GroupBox gb;
+    gb.load(a.node[a.leaf_of[ti]]);
+    RefineEval ev{a, a.sx[ti], a.sy[ti], a.sz[ti], a.sro[ti], ti, 0.0, 0.0, 0.0};
+    if (!traverse(a, gb, stack, s_pp[w], s_nd[w], s_big[w], s_bh, round_limit, ev)) break;
+    // the target itself is in the list: its own term is zero (r = 0)
+    for (int o = 16; o > 0; o >>= 1) {
+      ev.ax += __shfl_xor_sync(0xffffffffu, ev.ax, o);
+      ev.ay += __shfl_xor_sync(0xffffffffu, ev.ay, o);
+      ev.az += __shfl_xor_sync(0xffffffffu, ev.az, o);
+    }
+    if (lane == 0) {
+      const int32_t i = a.idx[ti];
+      a.ax[i] = a.G * ev.ax; a.ay[i] = a.G * ev.ay; a.az[i] = a.G * ev.az;
+    }
+  }
+}
+
+__global__ void k_walk_prep(int64_t *cursor, unsigned long long *cand_count,
+                            unsigned long long *counts, unsigned long long *refine_count) {
+  *cursor = 0;
+  *cand_count = 0ull;
+  *refine_count = 0ull;
+  if (counts) { counts[0] = 0ull; counts[1] = 0ull; }
+}
+
+// candidates found -> device status (for growth on the host) and clamped count
+__global__ void k_walk_post(int64_t *cnt, int64_t cand_cap, int64_t refine_cap,
+                            DevStatus *st) {
+  const int64_t nc = cnt[8];
+  st->cand_need = nc;
+  if (nc > cand_cap) dev_fail(st, P3T_ERR_CAPACITY, 42, nc);
+  cnt[9] = nc < cand_cap ? nc : cand_cap;
+  const int64_t nr = cnt[13];
+  cnt[14] = nr < refine_cap ? nr : refine_cap;
+}
+
+}  // namespace
+
+int p3t_walk_blocks_per_sm() { return 6; }
+
+int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
+                       double *ay, double *az, uint64_t *counts,
+                       cudaStream_t s) {
+  WalkArgs a;
+  a.node = c->node; a.mom64 = c->mom64; a.mom32 = c->mom32;
+  a.leaf_list = c->leaf_list; a.d_nleaf = &c->counters[2]; a.d_nnode = &c->counters[3];
+  a.sx = c->sx; a.sy = c->sy; a.sz = c->sz; a.sm = c->sm; a.sro = c->sro; a.srs = c->srs;
+  a.spA = c->spA; a.spB = c->spB; a.srs32 = c->srs32;
+  a.idx = c->idx;
+  a.ax = ax; a.ay = ay; a.az = az;
+  a.stack = c->walk_stack; a.stack_cap = c->stack_cap;
+  a.cand_i = c->cand_i; a.cand_j = c->cand_j; a.cand_cap = c->cand_cap;
+  a.cand_count = reinterpret_cast<unsigned long long *>(&c->counters[8]);
+  a.counts = reinterpret_cast<unsigned long long *>(counts);
+  a.cursor = &c->counters[12];
+  a.st = c->status;
+  a.refine = c->refine;
+  a.refine_count = reinterpret_cast<unsigned long long *>(&c->counters[13]);
+  a.refine_cap = c->cap;
+  a.d_nrefine = &c->counters[14];
+  a.leaf_of = c->leaf_of;
+  a.refine_cf = 32.0f;
+  a.G = c->prm.G;
+  a.gamma = c->prm.gamma;
+  a.gamma_f = (float)c->prm.gamma;
+  a.inv1mg_f = (float)(1.0 / (1.0 - c->prm.gamma));
+  // Barnes-Hut thresholds per level, ceil((2^(22-l))^2 / theta^2) (half units)
+  const double big = 4611686018427387904.0;
+  const double th2 = c->prm.theta * c->prm.theta;
+  for (int l = 0; l <= P3T_BITS; ++l) {
+    double X = th2 > 0.0 ? ldexp(1.0, 2 * (P3T_BITS + 1 - l)) / th2 : big;
+    X = ceil(X);
+    a.bh[l] = X < big ? (int64_t)X : (int64_t)4611686018427387904LL;
+  }
+  k_walk_prep<<<1, 1, 0, s>>>(a.cursor, a.cand_count, a.counts, a.refine_count);
+  const unsigned blocks = (unsigned)(c->num_sms * p3t_walk_blocks_per_sm());
+  if (c->prm.precision == P3T_MIXED)
+    k_walk<true><<<blocks, kWarps * 32, 0, s>>>(a);
+  else
+    k_walk<false><<<blocks, kWarps * 32, 0, s>>>(a);
+  k_walk_post<<<1, 1, 0, s>>>(c->counters, c->cand_cap, c->cap, c->status);
+  if (c->prm.precision == P3T_MIXED) k_refine<<<blocks, kWarps * 32, 0, s>>>(a);
+  p3t_note_launches(c->prm.precision == P3T_MIXED ? 4 : 3);
+  (void)p;
+  return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
+}
+
+int64_t p3t_walk_warps(int num_sms) {
+  return (int64_t)num_sms * p3t_walk_blocks_per_sm() * kWarps;
+}

@@ -1,0 +1,314 @@
+"""Thin ctypes binding of ``libp3t.so`` (the C ABI declared in include/p3t.h).
+
+Argument marshalling only: every step of the soft step runs in the library's
+sm_103a kernels.  PyTorch provides device memory and streams.  Importing this
+module loads the library and raises ImportError when it has not been built --
+there is no CPU fallback.
+
+The functions carry the C names (``p3t_build_tree`` ...) and take a context
+handle, a :class:`State` of float64 CUDA tensors and optional streams.
+:class:`SoftStep` strings them together into the paper's procedure steps 3-8.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libp3t.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with paper_2007_15432_gb300.build.build() "
+        "(nvcc, sm_103a); the soft step has no CPU fallback")
+
+_lib = C.CDLL(LIB_PATH)
+
+P3T_OK = 0
+P3T_ERR_INVALID = -1
+P3T_ERR_CUDA = -2
+P3T_ERR_CAPACITY = -3
+P3T_ERR_DT_UNDERFLOW = -4
+P3T_ERR_TIMEOUT = -5
+P3T_FP64 = 0
+P3T_MIXED = 1
+
+
+class Params(C.Structure):
+    """``p3t_params``; defaults are the paper's values (Sec. 3.1), gamma = 0.1."""
+
+    _fields_ = [(n, C.c_double) for n in (
+        "G", "m_star", "dt_soft", "gamma", "rcut0", "rcut1", "rs0", "rs1", "rs2",
+        "rs3", "theta", "eta", "eta0")] + [
+        ("leaf_size", C.c_int32), ("precision", C.c_int32), ("vran_bins", C.c_int32),
+        ("reserved", C.c_int32)]
+
+    def __init__(self, **kw):
+        d = dict(G=1.0, m_star=1.0, dt_soft=1.0 / 64.0, gamma=0.1, rcut0=2.0, rcut1=8.0,
+                 rs0=1.1, rs1=6.0, rs2=2.0, rs3=2.0, theta=0.5, eta=0.01, eta0=0.001,
+                 leaf_size=16, precision=P3T_FP64, vran_bins=0, reserved=0)
+        d.update(kw)
+        super().__init__(**d)
+
+
+class Particles(C.Structure):
+    _fields_ = [("n", C.c_int64)] + [(k, C.c_void_p) for k in (
+        "x", "y", "z", "vx", "vy", "vz", "m", "r_out", "r_search")]
+
+
+class Clusters(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("label", "singles", "cl_off", "cl_mem", "counts")]
+
+
+_vp = C.c_void_p
+_CTX = C.c_void_p
+_sig = {
+    "p3t_create": (C.c_int, [C.POINTER(_CTX), C.POINTER(Params), C.c_int]),
+    "p3t_destroy": (None, [_CTX]),
+    "p3t_set_params": (C.c_int, [_CTX, C.POINTER(Params)]),
+    "p3t_reserve": (C.c_int, [_CTX, C.c_int64]),
+    "p3t_cutoffs": (C.c_int, [_CTX, C.POINTER(Particles), _vp]),
+    "p3t_build_tree": (C.c_int, [_CTX, C.POINTER(Particles), C.c_int, _vp]),
+    "p3t_soft_force": (C.c_int, [_CTX, C.POINTER(Particles), _vp, _vp, _vp, _vp, _vp]),
+    "p3t_neighbours": (C.c_int, [_CTX, C.POINTER(Particles), _vp, _vp, C.c_int64,
+                                 C.POINTER(Clusters), _vp]),
+    "p3t_hard_step": (C.c_int, [_CTX, C.POINTER(Particles), C.POINTER(Clusters), C.c_double,
+                                _vp, _vp]),
+    "p3t_kick": (C.c_int, [_CTX, C.POINTER(Particles), _vp, _vp, _vp, C.c_double, _vp]),
+    "p3t_energy": (C.c_int, [_CTX, C.POINTER(Particles), _vp, _vp]),
+    "p3t_status": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
+    "p3t_tree_stats": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
+    "p3t_strerror": (C.c_char_p, [C.c_int]),
+    "p3t_launch_count": (C.c_int64, []),
+    "p3t_copy_clusters": (C.c_int, [_CTX, C.POINTER(Clusters), C.c_int64, _vp, _vp, _vp, _vp,
+                                    _vp, _vp]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class P3TError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        super().__init__(f"{where}: {p3t_strerror(code)} ({code})")
+
+
+def _check(rc, where):
+    if rc != P3T_OK:
+        raise P3TError(rc, where)
+
+
+def _stream(s):
+    if s is None:
+        s = torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(None)
+
+
+@dataclass
+class State:
+    """Particle state: float64 CUDA tensors of length n in caller order."""
+
+    x: torch.Tensor
+    y: torch.Tensor
+    z: torch.Tensor
+    vx: torch.Tensor
+    vy: torch.Tensor
+    vz: torch.Tensor
+    m: torch.Tensor
+    r_out: torch.Tensor
+    r_search: torch.Tensor
+
+    @staticmethod
+    def from_numpy(s: dict, device="cuda", r_out=None, r_search=None):
+        def t(a):
+            return torch.as_tensor(a, dtype=torch.float64).to(device).contiguous()
+        n = len(s["m"])
+        ro = t(r_out) if r_out is not None else torch.zeros(n, dtype=torch.float64, device=device)
+        rs = t(r_search) if r_search is not None else torch.zeros(n, dtype=torch.float64, device=device)
+        return State(t(s["x"]), t(s["y"]), t(s["z"]), t(s["vx"]), t(s["vy"]), t(s["vz"]),
+                     t(s["m"]), ro, rs)
+
+    def particles(self) -> Particles:
+        for k in ("x", "y", "z", "vx", "vy", "vz", "m", "r_out", "r_search"):
+            v = getattr(self, k)
+            if v.dtype != torch.float64 or not v.is_cuda or not v.is_contiguous():
+                raise TypeError(f"{k} must be a contiguous float64 CUDA tensor")
+        return Particles(len(self.m), *[self.__dict__[k].data_ptr() for k in (
+            "x", "y", "z", "vx", "vy", "vz", "m", "r_out", "r_search")])
+
+    def numpy(self) -> dict:
+        return {k: getattr(self, k).cpu().numpy() for k in (
+            "x", "y", "z", "vx", "vy", "vz", "m", "r_out", "r_search")}
+
+
+# ---- functions with the C names ---------------------------------------------
+def p3t_strerror(code: int) -> str:
+    return _lib.p3t_strerror(int(code)).decode()
+
+
+def p3t_launch_count() -> int:
+    return int(_lib.p3t_launch_count())
+
+
+def p3t_create(params: Params, device: int = 0):
+    ctx = _CTX()
+    _check(_lib.p3t_create(C.byref(ctx), C.byref(params), int(device)), "p3t_create")
+    return ctx
+
+
+def p3t_destroy(ctx) -> None:
+    _lib.p3t_destroy(ctx)
+
+
+def p3t_set_params(ctx, params: Params) -> None:
+    _check(_lib.p3t_set_params(ctx, C.byref(params)), "p3t_set_params")
+
+
+def p3t_reserve(ctx, n: int) -> None:
+    _check(_lib.p3t_reserve(ctx, int(n)), "p3t_reserve")
+
+
+def p3t_cutoffs(ctx, st: State, stream=None) -> None:
+    p = st.particles()
+    _check(_lib.p3t_cutoffs(ctx, C.byref(p), _stream(stream)), "p3t_cutoffs")
+
+
+def p3t_build_tree(ctx, st: State, update_cutoffs: bool = False, stream=None) -> None:
+    p = st.particles()
+    _check(_lib.p3t_build_tree(ctx, C.byref(p), int(bool(update_cutoffs)), _stream(stream)),
+           "p3t_build_tree")
+
+
+def p3t_soft_force(ctx, st: State, acc: torch.Tensor, counts: torch.Tensor | None = None,
+                   stream=None) -> None:
+    """acc: float64 CUDA tensor (3, n); counts: uint64/int64 CUDA tensor (2,) or None."""
+    p = st.particles()
+    _check(_lib.p3t_soft_force(ctx, C.byref(p), _ptr(acc[0]), _ptr(acc[1]), _ptr(acc[2]),
+                               _ptr(counts), _stream(stream)), "p3t_soft_force")
+
+
+def p3t_neighbours(ctx, st: State, nb_off: torch.Tensor, nb_idx: torch.Tensor,
+                   stream=None) -> Clusters:
+    p = st.particles()
+    cl = Clusters()
+    _check(_lib.p3t_neighbours(ctx, C.byref(p), _ptr(nb_off), _ptr(nb_idx), int(nb_idx.numel()),
+                               C.byref(cl), _stream(stream)), "p3t_neighbours")
+    return cl
+
+
+def p3t_hard_step(ctx, st: State, cl: Clusters, dt: float, n_steps: torch.Tensor | None = None,
+                  stream=None) -> None:
+    p = st.particles()
+    _check(_lib.p3t_hard_step(ctx, C.byref(p), C.byref(cl), float(dt), _ptr(n_steps),
+                              _stream(stream)), "p3t_hard_step")
+
+
+def p3t_kick(ctx, st: State, acc: torch.Tensor, h: float, stream=None) -> None:
+    p = st.particles()
+    _check(_lib.p3t_kick(ctx, C.byref(p), _ptr(acc[0]), _ptr(acc[1]), _ptr(acc[2]), float(h),
+                         _stream(stream)), "p3t_kick")
+
+
+def p3t_energy(ctx, st: State, out: torch.Tensor, stream=None) -> None:
+    p = st.particles()
+    _check(_lib.p3t_energy(ctx, C.byref(p), _ptr(out), _stream(stream)), "p3t_energy")
+
+
+def p3t_status(ctx) -> tuple[int, int]:
+    req = C.c_int64(0)
+    rc = _lib.p3t_status(ctx, C.byref(req))
+    return rc, req.value
+
+
+def p3t_tree_stats(ctx) -> dict:
+    out = (C.c_int64 * 4)()
+    _check(_lib.p3t_tree_stats(ctx, out), "p3t_tree_stats")
+    return dict(n_nodes=out[0], n_leaves=out[1], depth=out[2], max_leaf=out[3])
+
+
+def p3t_copy_clusters(ctx, cl: Clusters, n: int, stream=None) -> dict:
+    """Copies the cluster views into new CUDA tensors (stream-ordered)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = dict(label=torch.empty(max(n, 1), dtype=torch.int32, device=dev),
+               singles=torch.empty(max(n, 1), dtype=torch.int32, device=dev),
+               cl_off=torch.empty(n + 1, dtype=torch.int64, device=dev),
+               cl_mem=torch.empty(max(n, 1), dtype=torch.int32, device=dev),
+               counts=torch.empty(4, dtype=torch.int64, device=dev))
+    _check(_lib.p3t_copy_clusters(ctx, C.byref(cl), int(n), *[_ptr(out[k]) for k in (
+        "label", "singles", "cl_off", "cl_mem", "counts")], _stream(stream)), "p3t_copy_clusters")
+    return out
+
+
+def clusters_to_host(ctx, cl: Clusters, n: int) -> dict:
+    """Synchronising copy of the cluster views to numpy, trimmed to the counts."""
+    d = p3t_copy_clusters(ctx, cl, n)
+    counts = d["counts"].cpu().numpy()
+    ns, nc, nm, mx = (int(v) for v in counts)
+    return dict(label=d["label"][:n].cpu().numpy(), singles=d["singles"][:ns].cpu().numpy(),
+                cl_off=d["cl_off"][:nc + 1].cpu().numpy(), cl_mem=d["cl_mem"][:nm].cpu().numpy(),
+                max_size=mx)
+
+
+class SoftStep:
+    """The P3T soft step on one GPU (paper Sec. 2.2, procedure steps 2-8).
+
+    ``init()`` computes the cut-off radii, the first soft force, neighbour
+    lists and clusters; each ``step()`` then runs kick, hard step, tree,
+    force, neighbours, kick.
+    """
+
+    def __init__(self, params: Params, st: State, device: int = 0, nb_cap: int | None = None):
+        self.params = params
+        self.st = st
+        self.n = len(st.m)
+        self.ctx = p3t_create(params, device)
+        p3t_reserve(self.ctx, self.n)
+        dev = st.m.device
+        self.acc = torch.zeros(3, self.n, dtype=torch.float64, device=dev)
+        self.counts = torch.zeros(2, dtype=torch.int64, device=dev)
+        self.hsteps = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.nb_off = torch.zeros(self.n + 1, dtype=torch.int64, device=dev)
+        self.nb_idx = torch.zeros(max(nb_cap or (4 * self.n + 1024), 1), dtype=torch.int32, device=dev)
+        self.cl = None
+
+    def close(self):
+        if self.ctx:
+            p3t_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def force(self, stream=None):
+        p3t_build_tree(self.ctx, self.st, False, stream)
+        p3t_soft_force(self.ctx, self.st, self.acc, self.counts, stream)
+        self.cl = p3t_neighbours(self.ctx, self.st, self.nb_off, self.nb_idx, stream)
+
+    def init(self, update_cutoffs=True, stream=None):
+        if update_cutoffs:
+            p3t_cutoffs(self.ctx, self.st, stream)
+        self.force(stream)
+
+    def step(self, stream=None):
+        h = 0.5 * self.params.dt_soft
+        p3t_kick(self.ctx, self.st, self.acc, h, stream)
+        p3t_hard_step(self.ctx, self.st, self.cl, self.params.dt_soft, self.hsteps, stream)
+        self.force(stream)
+        p3t_kick(self.ctx, self.st, self.acc, h, stream)
+
+    def status(self):
+        rc, req = p3t_status(self.ctx)
+        if rc != P3T_OK:
+            raise P3TError(rc, f"device status (required={req})")
