@@ -129,6 +129,31 @@ int p3t_reserve(p3t_ctx *ctx, int64_t n);
  * p->r_search. */
 int p3t_cutoffs(p3t_ctx *ctx, p3t_particles *p, void *stream);
 
+/* Row a1 without a context and without any allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- an application that owns all device memory through its own
+ * pool and forbids other allocations (a plugin host, a framework with a fixed
+ * memory budget), or a latency-critical loop where the synchronisation
+ * cudaMalloc and cudaFree may imply would stall other work.  Such callers
+ * cannot create a context (p3t_create allocates) but can call this.
+ *  - Same results as p3t_cutoffs for the same parameters and particles (the
+ *    radial-bin sums are accumulated in a different order: a few ulp).
+ *  - Runs on the CURRENT CUDA device; all particle pointers must be on it.
+ *    p and *p are host memory; the arrays they point to are device memory
+ *    owned by the caller (inputs x..m are read, r_out and r_search written).
+ *  - Scratch: a fixed 65,552-byte array in device memory that every GPU
+ *    loading the library holds until the process exits; at most 4096 radial
+ *    bins (prm->vran_bins > 4096 returns P3T_ERR_INVALID; the automatic choice
+ *    is at most 1024).  Each call clears what it uses before use.
+ *  - The first call on a device looks up the scratch address on that device
+ *    (a host-side runtime query); make that first call before any stream
+ *    capture.
+ *  - Every call shares the scratch: calls that overlap on the GPU (e.g. on
+ *    two streams with no ordering between them) race and must be avoided.
+ *  - Returns 0, P3T_ERR_INVALID (bad arguments or too many bins) or
+ *    P3T_ERR_CUDA (the lookup or a launch failed). */
+int p3t_cutoffs_noalloc(const p3t_params *prm, p3t_particles *p, void *stream);
+
 /* Rows a2-a3 -- Morton keys on the 21-bit grid of the cubic bounding box,
  * stable sort by (key, index), octree (split while > leaf_size particles and
  * level < 21), per node mass, centre of mass, traceless quadrupole

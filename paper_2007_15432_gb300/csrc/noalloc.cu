@@ -1,0 +1,210 @@
+// p3t_cutoffs_noalloc: the cut-off and search radii (row a1) for callers that
+// cannot allocate device memory.
+//
+// Some callers of this library cannot call cudaMalloc: an application that
+// owns all device memory through its own pool and forbids other allocations
+// (a plugin host, an embedding framework with a fixed memory budget), or a
+// latency-critical loop where the device-wide synchronisation that cudaMalloc
+// and cudaFree may imply would stall other work.  Such callers cannot create a
+// p3t context either, because the context allocates its buffers.  This entry
+// point needs no context and allocates nothing: its only scratch (the radial
+// bin sums and counts and the range of the cylindrical radius) lives in a
+// fixed array in device memory that every GPU loading the library holds until
+// the process exits.
+//
+// The scratch holds at most kMaxBins radial bins.  Every call shares it and
+// it keeps the contents of the last call; each call clears the part it uses
+// before use.  Calls that overlap on the GPU (on different streams without an
+// ordering between them) race on the scratch and must not be issued.
+#include <math.h>
+
+#include <mutex>
+
+#include "p3t_internal.cuh"
+
+namespace {
+
+constexpr int kMaxBins = 4096;           // largest vran_bins this entry point accepts
+constexpr int kScratchWords = 2 + 2 * kMaxBins;  // range bits, bin sums, bin counts
+constexpr int kMaxDevices = 64;
+constexpr int kBlock = 256;
+
+}  // namespace
+
+// 8 + 2 * 4096 * 8 = 65,552 bytes per device
+static __device__ __align__(256) unsigned long long p3t_noalloc_scratch[kScratchWords];
+
+namespace {
+
+std::mutex g_mu;
+void *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the scratch on the current device.  Looked up once per
+// device (the first call on a device does it) with that device current.
+int scratch_address(unsigned long long **out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return P3T_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) return P3T_ERR_INVALID;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_scratch_addr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, p3t_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return P3T_ERR_CUDA;
+    }
+    g_scratch_addr[dev] = p;
+  }
+  *out = static_cast<unsigned long long *>(g_scratch_addr[dev]);
+  return P3T_OK;
+}
+
+__device__ __forceinline__ unsigned long long nz_ord_bits(double v) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double nz_ord_double(unsigned long long b) {
+  b = (b >> 63) ? (b & 0x7fffffffffffffffull) : ~b;
+  return __longlong_as_double((long long)b);
+}
+
+// scratch layout: [0] min and [1] max of R_cyl (ordered bits),
+// [2, 2 + nb) bin sums of |u|^2 (double bits), [2 + kMaxBins, ...) bin counts
+__global__ void nz_clear(unsigned long long *sc, int nb) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) { sc[0] = ~0ull; sc[1] = 0ull; }
+  for (int k = t; k < nb; k += gridDim.x * blockDim.x) {
+    sc[2 + k] = 0ull;  // +0.0
+    sc[2 + kMaxBins + k] = 0ull;
+  }
+}
+
+__global__ void nz_range(int64_t n, const double *x, const double *y,
+                         unsigned long long *sc) {
+  unsigned long long lo = ~0ull, hi = 0ull;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long b = nz_ord_bits(sqrt(x[i] * x[i] + y[i] * y[i]));
+    lo = b < lo ? b : lo;
+    hi = b > hi ? b : hi;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, lo, o);
+    const unsigned long long c = __shfl_xor_sync(0xffffffffu, hi, o);
+    lo = a < lo ? a : lo;
+    hi = c > hi ? c : hi;
+  }
+  if ((threadIdx.x & 31) == 0) { atomicMin(&sc[0], lo); atomicMax(&sc[1], hi); }
+}
+
+__device__ __forceinline__ int nz_bin(double R, double Rmin, double Rmax,
+                                      double lmin, double lmax, int nb) {
+  int k = 0;
+  if (Rmax > Rmin && R > Rmin) {
+    const double t = (log(R) - lmin) / (lmax - lmin);
+    const double f = floor(t * (double)nb);
+    k = f < 0.0 ? 0 : (f > (double)(nb - 1) ? nb - 1 : (int)f);
+  }
+  return k;
+}
+
+// random velocity u = v - sqrt(G M_* / |x|) phi_hat, |u|^2 summed per bin
+__global__ void nz_bins(int64_t n, const double *x, const double *y,
+                        const double *z, const double *vx, const double *vy,
+                        const double *vz, double mu, int nb,
+                        unsigned long long *sc) {
+  extern __shared__ double s_sum[];
+  unsigned int *s_cnt = reinterpret_cast<unsigned int *>(s_sum + nb);
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) { s_sum[k] = 0.0; s_cnt[k] = 0u; }
+  __syncthreads();
+  const double Rmin = nz_ord_double(sc[0]), Rmax = nz_ord_double(sc[1]);
+  const double lmin = log(Rmin), lmax = log(Rmax);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double R = sqrt(x[i] * x[i] + y[i] * y[i]);
+    const double r = sqrt(x[i] * x[i] + y[i] * y[i] + z[i] * z[i]);
+    const double vk = sqrt(mu / r);
+    double px = 0.0, py = 0.0;
+    if (R > 0.0) { px = -y[i] / R; py = x[i] / R; }
+    const double ux = vx[i] - vk * px, uy = vy[i] - vk * py, uz = vz[i];
+    const int k = nz_bin(R, Rmin, Rmax, lmin, lmax, nb);
+    atomicAdd(&s_sum[k], ux * ux + uy * uy + uz * uz);
+    atomicAdd(&s_cnt[k], 1u);
+  }
+  __syncthreads();
+  double *gsum = reinterpret_cast<double *>(sc + 2);
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+    if (s_cnt[k]) {
+      atomicAdd(&gsum[k], s_sum[k]);
+      atomicAdd(&sc[2 + kMaxBins + k], (unsigned long long)s_cnt[k]);
+    }
+  }
+}
+
+// r_out = max(R~cut,0 r_Hill, R~cut,1 v_ran dt), r_search = R~s,0 r_out + R~s,1 v_ran dt
+__global__ void nz_final(int64_t n, const double *x, const double *y,
+                         const double *z, const double *vx, const double *vy,
+                         const double *vz, const double *m, p3t_params prm,
+                         int nb, const unsigned long long *sc, double *r_out,
+                         double *r_search) {
+  const double mu = prm.G * prm.m_star;
+  const double Rmin = nz_ord_double(sc[0]), Rmax = nz_ord_double(sc[1]);
+  const double lmin = log(Rmin), lmax = log(Rmax);
+  const double *gsum = reinterpret_cast<const double *>(sc + 2);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double R = sqrt(x[i] * x[i] + y[i] * y[i]);
+    const double r = sqrt(x[i] * x[i] + y[i] * y[i] + z[i] * z[i]);
+    const double v2 = vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i];
+    const double alpha = 2.0 / r - v2 / mu;
+    const double a = alpha > 0.0 ? 1.0 / alpha : r;
+    const double rhill = cbrt(m[i] / (3.0 * prm.m_star)) * a;
+    const int k = nz_bin(R, Rmin, Rmax, lmin, lmax, nb);
+    const double vr = sqrt(gsum[k] / (double)sc[2 + kMaxBins + k]);
+    const double ro = fmax(prm.rcut0 * rhill, prm.rcut1 * vr * prm.dt_soft);
+    r_out[i] = ro;
+    r_search[i] = prm.rs0 * ro + prm.rs1 * vr * prm.dt_soft;
+  }
+}
+
+}  // namespace
+
+extern "C" int p3t_cutoffs_noalloc(const p3t_params *prm, p3t_particles *p,
+                                   void *stream) {
+  if (!prm || !p || p->n < 0 || p->n >= ((int64_t)1 << 31)) return P3T_ERR_INVALID;
+  if (!(prm->G > 0.0) || !(prm->m_star > 0.0) || !(prm->dt_soft > 0.0)) return P3T_ERR_INVALID;
+  if (prm->vran_bins < 0 || prm->vran_bins > kMaxBins) return P3T_ERR_INVALID;
+  if (p->n == 0) return P3T_OK;
+  if (!p->x || !p->y || !p->z || !p->vx || !p->vy || !p->vz || !p->m || !p->r_out ||
+      !p->r_search)
+    return P3T_ERR_INVALID;
+  unsigned long long *sc = nullptr;
+  int rc = scratch_address(&sc);
+  if (rc != P3T_OK) return rc;
+  const int64_t n = p->n;
+  int nb = prm->vran_bins;
+  if (nb == 0) {
+    const int64_t t = n / 1000;
+    nb = (int)(t < 1 ? 1 : (t > 1024 ? 1024 : t));
+  }
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return P3T_ERR_CUDA;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t g = (n + kBlock - 1) / kBlock;
+  if (g > (int64_t)sms * P3T_NSM_BLOCKS) g = (int64_t)sms * P3T_NSM_BLOCKS;
+  if (g < 1) g = 1;
+  const double mu = prm->G * prm->m_star;
+  nz_clear<<<4, kBlock, 0, s>>>(sc, nb);
+  nz_range<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, sc);
+  nz_bins<<<(unsigned)g, kBlock, nb * (sizeof(double) + sizeof(unsigned)), s>>>(
+      n, p->x, p->y, p->z, p->vx, p->vy, p->vz, mu, nb, sc);
+  nz_final<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, p->z, p->vx, p->vy, p->vz,
+                                          p->m, *prm, nb, sc, p->r_out, p->r_search);
+  return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
+}

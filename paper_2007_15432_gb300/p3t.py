@@ -83,6 +83,7 @@ _sig = {
     "p3t_tree_stats": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
     "p3t_strerror": (C.c_char_p, [C.c_int]),
     "p3t_launch_count": (C.c_int64, []),
+    "p3t_cutoffs_noalloc": (C.c_int, [C.POINTER(Params), C.POINTER(Particles), _vp]),
     "p3t_copy_clusters": (C.c_int, [_CTX, C.POINTER(Clusters), C.c_int64, _vp, _vp, _vp, _vp,
                                     _vp, _vp]),
 }
@@ -180,6 +181,14 @@ def p3t_reserve(ctx, n: int) -> None:
 def p3t_cutoffs(ctx, st: State, stream=None) -> None:
     p = st.particles()
     _check(_lib.p3t_cutoffs(ctx, C.byref(p), _stream(stream)), "p3t_cutoffs")
+
+
+def p3t_cutoffs_noalloc(params: Params, st: State, stream=None) -> None:
+    """Cut-off radii on the current device without a context or any allocation
+    (for callers that cannot allocate device memory; see include/p3t.h)."""
+    p = st.particles()
+    _check(_lib.p3t_cutoffs_noalloc(C.byref(params), C.byref(p), _stream(stream)),
+           "p3t_cutoffs_noalloc")
 
 
 def p3t_build_tree(ctx, st: State, update_cutoffs: bool = False, stream=None) -> None:
