@@ -758,40 +758,51 @@ void or_hard_acc_jerk(int64_t nc, const double *x, const double *y,
                       const double *vz, const double *m, const double *r_out,
                       const or_params *p, int64_t k, double acc[3],
                       double jerk[3]) {
+  /* evaluated with one reciprocal square root per pair and reciprocal
+   * factors (1/r, 1/r_out, 1/(1-gamma)); the formulas are those above */
+  const double i1mg = 1.0 / (1.0 - p->gamma);
   double ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0;
   {
     double r2 = x[k] * x[k] + y[k] * y[k] + z[k] * z[k];
-    double r = sqrt(r2);
-    double r3 = r2 * r;
+    double rinv = 1.0 / sqrt(r2);
+    double rinv2 = rinv * rinv;
+    double f = p->G * p->m_star * (rinv2 * rinv);
     double rv = x[k] * vx[k] + y[k] * vy[k] + z[k] * vz[k];
-    double gm = p->G * p->m_star;
-    ax -= gm * x[k] / r3; ay -= gm * y[k] / r3; az -= gm * z[k] / r3;
-    double c = 3.0 * rv / r2;
-    jx -= gm * (vx[k] - c * x[k]) / r3;
-    jy -= gm * (vy[k] - c * y[k]) / r3;
-    jz -= gm * (vz[k] - c * z[k]) / r3;
+    ax -= f * x[k]; ay -= f * y[k]; az -= f * z[k];
+    double c = 3.0 * rv * rinv2;
+    jx -= f * (vx[k] - c * x[k]);
+    jy -= f * (vy[k] - c * y[k]);
+    jz -= f * (vz[k] - c * z[k]);
   }
+  const double irok = 1.0 / r_out[k];
   for (int64_t j = 0; j < nc; ++j) {
     if (j == k) continue;
     double rx = x[k] - x[j], ry = y[k] - y[j], rz = z[k] - z[j];
     double ux = vx[k] - vx[j], uy = vy[k] - vy[j], uz = vz[k] - vz[j];
     double r2 = rx * rx + ry * ry + rz * rz;
     if (r2 == 0.0) continue;
-    double r = sqrt(r2);
-    double ro = dmax(r_out[k], r_out[j]);
-    double yv = r / ro;
+    double rinv = 1.0 / sqrt(r2);
+    double r = r2 * rinv;
+    double irot = dmin(irok, 1.0 / r_out[j]); /* = 1 / max(r_out,k, r_out,j) */
+    double yv = r * irot;
     if (yv >= 1.0) continue;
-    double w = 1.0 - or_changeover_K(yv, p->gamma);
-    double dK = or_changeover_dKdy(yv, p->gamma);
-    double r3 = r2 * r;
+    double w = 1.0, dK = 0.0;
+    if (yv > p->gamma) {
+      double xs = (yv - p->gamma) * i1mg;
+      double x2 = xs * xs, x3 = x2 * xs, x4 = x2 * x2, u = 1.0 - xs;
+      w = 1.0 - x4 * (35.0 - 84.0 * xs + 70.0 * x2 - 20.0 * x3);
+      dK = 140.0 * x3 * (u * u * u) * i1mg;
+    }
+    double rinv2 = rinv * rinv;
+    double g3 = p->G * m[j] * (rinv2 * rinv);
+    double f = g3 * w;
     double rv = rx * ux + ry * uy + rz * uz;
-    double gm = p->G * m[j];
-    ax -= gm * w * rx / r3; ay -= gm * w * ry / r3; az -= gm * w * rz / r3;
+    ax -= f * rx; ay -= f * ry; az -= f * rz;
     /* d/dt [w r / r^3] = w v / r^3 - (3 w (r.v)/r^2 + K'(y) (r.v)/(r r_out)) r / r^3 */
-    double c = 3.0 * w * rv / r2 + dK * rv / (r * ro);
-    jx -= gm * (w * ux - c * rx) / r3;
-    jy -= gm * (w * uy - c * ry) / r3;
-    jz -= gm * (w * uz - c * rz) / r3;
+    double c = 3.0 * w * rv * rinv2 + dK * rv * rinv * irot;
+    jx -= g3 * (w * ux - c * rx);
+    jy -= g3 * (w * uy - c * ry);
+    jz -= g3 * (w * uz - c * rz);
   }
   acc[0] = ax; acc[1] = ay; acc[2] = az;
   jerk[0] = jx; jerk[1] = jy; jerk[2] = jz;
@@ -868,12 +879,12 @@ int or_hermite_cluster(int64_t nc, const int32_t *members, double *X, double *Y,
       double D = (double)(tn - t[k]) * unit;
       double D2 = D * D, D3 = D2 * D;
       const double *ak = a + 3 * k, *jj = jk + 3 * k;
-      px[k] = x[k] + vx[k] * D + ak[0] * D2 / 2.0 + jj[0] * D3 / 6.0;
-      py[k] = y[k] + vy[k] * D + ak[1] * D2 / 2.0 + jj[1] * D3 / 6.0;
-      pz[k] = z[k] + vz[k] * D + ak[2] * D2 / 2.0 + jj[2] * D3 / 6.0;
-      pvx[k] = vx[k] + ak[0] * D + jj[0] * D2 / 2.0;
-      pvy[k] = vy[k] + ak[1] * D + jj[1] * D2 / 2.0;
-      pvz[k] = vz[k] + ak[2] * D + jj[2] * D2 / 2.0;
+      px[k] = x[k] + vx[k] * D + ak[0] * D2 * 0.5 + jj[0] * D3 * (1.0 / 6.0);
+      py[k] = y[k] + vy[k] * D + ak[1] * D2 * 0.5 + jj[1] * D3 * (1.0 / 6.0);
+      pz[k] = z[k] + vz[k] * D + ak[2] * D2 * 0.5 + jj[2] * D3 * (1.0 / 6.0);
+      pvx[k] = vx[k] + ak[0] * D + jj[0] * D2 * 0.5;
+      pvy[k] = vy[k] + ak[1] * D + jj[1] * D2 * 0.5;
+      pvz[k] = vz[k] + ak[2] * D + jj[2] * D2 * 0.5;
       act[k] = (t[k] + (T >> lvl[k]) == tn);
     }
     for (int64_t k = 0; k < nc; ++k)
@@ -882,19 +893,20 @@ int or_hermite_cluster(int64_t nc, const int32_t *members, double *X, double *Y,
       if (!act[k]) continue;
       double D = (double)(T >> lvl[k]) * unit;
       double D2 = D * D, D3 = D2 * D, D4 = D3 * D, D5 = D4 * D;
+      double iD = 1.0 / D, iD2 = iD * iD, iD3 = iD2 * iD;
       double A2[3], A3[3], A2e[3];
       for (int c = 0; c < 3; ++c) {
         double da = a[3 * k + c] - a1[3 * k + c];
-        A2[c] = (-6.0 * da - D * (4.0 * jk[3 * k + c] + 2.0 * j1[3 * k + c])) / D2;
-        A3[c] = (12.0 * da + 6.0 * D * (jk[3 * k + c] + j1[3 * k + c])) / D3;
+        A2[c] = (-6.0 * da - D * (4.0 * jk[3 * k + c] + 2.0 * j1[3 * k + c])) * iD2;
+        A3[c] = (12.0 * da + 6.0 * D * (jk[3 * k + c] + j1[3 * k + c])) * iD3;
         A2e[c] = A2[c] + D * A3[c];
       }
-      x[k] = px[k] + A2[0] * D4 / 24.0 + A3[0] * D5 / 120.0;
-      y[k] = py[k] + A2[1] * D4 / 24.0 + A3[1] * D5 / 120.0;
-      z[k] = pz[k] + A2[2] * D4 / 24.0 + A3[2] * D5 / 120.0;
-      vx[k] = pvx[k] + A2[0] * D3 / 6.0 + A3[0] * D4 / 24.0;
-      vy[k] = pvy[k] + A2[1] * D3 / 6.0 + A3[1] * D4 / 24.0;
-      vz[k] = pvz[k] + A2[2] * D3 / 6.0 + A3[2] * D4 / 24.0;
+      x[k] = px[k] + A2[0] * D4 * (1.0 / 24.0) + A3[0] * D5 * (1.0 / 120.0);
+      y[k] = py[k] + A2[1] * D4 * (1.0 / 24.0) + A3[1] * D5 * (1.0 / 120.0);
+      z[k] = pz[k] + A2[2] * D4 * (1.0 / 24.0) + A3[2] * D5 * (1.0 / 120.0);
+      vx[k] = pvx[k] + A2[0] * D3 * (1.0 / 6.0) + A3[0] * D4 * (1.0 / 24.0);
+      vy[k] = pvy[k] + A2[1] * D3 * (1.0 / 6.0) + A3[1] * D4 * (1.0 / 24.0);
+      vz[k] = pvz[k] + A2[2] * D3 * (1.0 / 6.0) + A3[2] * D4 * (1.0 / 24.0);
       for (int c = 0; c < 3; ++c) { a[3 * k + c] = a1[3 * k + c]; jk[3 * k + c] = j1[3 * k + c]; }
       double an = norm3(a + 3 * k), jn = norm3(jk + 3 * k);
       double a2n = norm3(A2e), a3n = norm3(A3);
