@@ -346,6 +346,10 @@ int p3t_tree_stats(p3t_ctx *c, int64_t out[4]) {
   if (!c || !out) return P3T_ERR_INVALID;
   DeviceGuard g(c->device);
   if (cudaDeviceSynchronize() != cudaSuccess) return P3T_ERR_CUDA;
+  if (c->have_tree) {
+    if (p3t_run_tree_stats(c, 0) != P3T_OK) return P3T_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return P3T_ERR_CUDA;
+  }
   int64_t h[8];
   if (cudaMemcpy(h, c->counters, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
     return P3T_ERR_CUDA;

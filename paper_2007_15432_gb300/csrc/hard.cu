@@ -29,18 +29,21 @@ __global__ void k_kick(int64_t n, double *vx, double *vy, double *vz,
 // as nested series for |z| < 1 and in closed form otherwise.
 __device__ __forceinline__ void stumpff(double z, double &C, double &S) {
   if (fabs(z) < 1.0) {
-    const double dc[12] = {12.0, 30.0, 56.0, 90.0, 132.0, 182.0,
-                           240.0, 306.0, 380.0, 462.0, 552.0, 650.0};
-    const double ds[12] = {20.0, 42.0, 72.0, 110.0, 156.0, 210.0,
-                           272.0, 342.0, 420.0, 506.0, 600.0, 702.0};
-    double c = 1.0, s = 1.0;
-#pragma unroll
-    for (int k = 11; k >= 0; --k) {
-      c = 1.0 - z / dc[k] * c;
-      s = 1.0 - z / ds[k] * s;
-    }
-    C = 0.5 * c;
-    S = s / 6.0;
+    // Horner in z with coefficients (-1)^k / (2k+2)! and (-1)^k / (2k+3)!
+    // (compile-time constants: no division at run time); |z| < 1 keeps the
+    // truncation below 1e-20
+    constexpr double c0 = 1.0 / 2.0, c1 = -1.0 / 24.0, c2 = 1.0 / 720.0,
+                     c3 = -1.0 / 40320.0, c4 = 1.0 / 3628800.0,
+                     c5 = -1.0 / 479001600.0, c6 = 1.0 / 87178291200.0,
+                     c7 = -1.0 / 20922789888000.0, c8 = 1.0 / 6402373705728000.0,
+                     c9 = -1.0 / 2432902008176640000.0;
+    constexpr double s0 = 1.0 / 6.0, s1 = -1.0 / 120.0, s2 = 1.0 / 5040.0,
+                     s3 = -1.0 / 362880.0, s4 = 1.0 / 39916800.0,
+                     s5 = -1.0 / 6227020800.0, s6 = 1.0 / 1307674368000.0,
+                     s7 = -1.0 / 355687428096000.0, s8 = 1.0 / 121645100408832000.0,
+                     s9 = -1.0 / 51090942171709440000.0;
+    C = c0 + z * (c1 + z * (c2 + z * (c3 + z * (c4 + z * (c5 + z * (c6 + z * (c7 + z * (c8 + z * c9))))))));
+    S = s0 + z * (s1 + z * (s2 + z * (s3 + z * (s4 + z * (s5 + z * (s6 + z * (s7 + z * (s8 + z * s9))))))));
   } else if (z > 0.0) {
     const double q = sqrt(z);
     C = (1.0 - cos(q)) / z;
@@ -59,11 +62,12 @@ __device__ bool kepler_uv(double X[3], double V[3], double dt, double mu) {
   const double r0 = sqrt(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
   const double v2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
   const double rv = X[0] * V[0] + X[1] * V[1] + X[2] * V[2];
-  const double alpha = 2.0 / r0 - v2 / mu;
-  const double sq = sqrt(mu);
-  const double sig = rv / sq;  // r0 v_r0 / sqrt(mu)
+  const double ir0 = 1.0 / r0, imu = 1.0 / mu;
+  const double alpha = 2.0 * ir0 - v2 * imu;
+  const double sq = sqrt(mu), isq = 1.0 / sq;
+  const double sig = rv * isq;  // r0 v_r0 / sqrt(mu)
   const double tau = sq * dt;
-  double chi = tau / r0;
+  double chi = tau * ir0;
   if (alpha > 0.0) {
     const double P = 2.0 * 3.141592653589793 / (alpha * sqrt(alpha) * sq);
     if (fabs(dt) > 0.25 * P) chi = tau * alpha;
@@ -88,13 +92,14 @@ __device__ bool kepler_uv(double X[3], double V[3], double dt, double mu) {
   z = alpha * chi * chi;
   stumpff(z, C, S);
   const double chi2 = chi * chi;
-  const double f = 1.0 - chi2 / r0 * C;
-  const double g = dt - chi2 * chi * S / sq;
+  const double f = 1.0 - chi2 * ir0 * C;
+  const double g = dt - chi2 * chi * S * isq;
   double nx[3];
   for (int a = 0; a < 3; ++a) nx[a] = f * X[a] + g * V[a];
   const double r = sqrt(nx[0] * nx[0] + nx[1] * nx[1] + nx[2] * nx[2]);
-  const double fd = sq / (r * r0) * (z * S - 1.0) * chi;
-  const double gd = 1.0 - chi2 / r * C;
+  const double ir = 1.0 / r;
+  const double fd = sq * ir * ir0 * (z * S - 1.0) * chi;
+  const double gd = 1.0 - chi2 * ir * C;
   for (int a = 0; a < 3; ++a) {
     const double nv = fd * X[a] + gd * V[a];
     X[a] = nx[a];
@@ -126,62 +131,56 @@ struct HWork {
   int32_t *lvl;                            // step = dt / 2^lvl
 };
 
-__device__ __forceinline__ double K_of(double y, double gamma) {
-  if (y <= gamma) return 0.0;
-  if (y >= 1.0) return 1.0;
-  const double x = (y - gamma) / (1.0 - gamma);
-  const double x2 = x * x;
-  const double x3 = x2 * x;
-  const double x4 = x2 * x2;
-  return x4 * (35.0 - 84.0 * x + 70.0 * x2 - 20.0 * x3);
-}
-__device__ __forceinline__ double dK_of(double y, double gamma) {
-  if (y <= gamma || y >= 1.0) return 0.0;
-  const double x = (y - gamma) / (1.0 - gamma);
-  const double u = 1.0 - x;
-  return 140.0 * x * x * x * u * u * u / (1.0 - gamma);
-}
-
 // hard acceleration and jerk of member k (Eq. hardforce): star term, then the
-// (1 - K) pair terms over the other members in ascending order
+// (1 - K) pair terms over the other members in ascending order; one
+// reciprocal square root per pair, 1/max(r_out) taken as min(1/r_out)
 __device__ void hard_acc_jerk(int nc, const double *x, const double *y,
                               const double *z, const double *vx, const double *vy,
                               const double *vz, const double *m, const double *ro,
-                              const p3t_params &prm, int k, double acc[3],
+                              const p3t_params &prm, double i1mg, int k, double acc[3],
                               double jerk[3]) {
   double ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0;
   {
     const double r2 = x[k] * x[k] + y[k] * y[k] + z[k] * z[k];
-    const double r = sqrt(r2);
-    const double r3 = r2 * r;
+    const double rinv = 1.0 / sqrt(r2);
+    const double rinv2 = rinv * rinv;
+    const double f = prm.G * prm.m_star * (rinv2 * rinv);
     const double rv = x[k] * vx[k] + y[k] * vy[k] + z[k] * vz[k];
-    const double gm = prm.G * prm.m_star;
-    ax -= gm * x[k] / r3; ay -= gm * y[k] / r3; az -= gm * z[k] / r3;
-    const double c = 3.0 * rv / r2;
-    jx -= gm * (vx[k] - c * x[k]) / r3;
-    jy -= gm * (vy[k] - c * y[k]) / r3;
-    jz -= gm * (vz[k] - c * z[k]) / r3;
+    ax -= f * x[k]; ay -= f * y[k]; az -= f * z[k];
+    const double c = 3.0 * rv * rinv2;
+    jx -= f * (vx[k] - c * x[k]);
+    jy -= f * (vy[k] - c * y[k]);
+    jz -= f * (vz[k] - c * z[k]);
   }
+  const double irok = 1.0 / ro[k];
   for (int j = 0; j < nc; ++j) {
     if (j == k) continue;
     const double rx = x[k] - x[j], ry = y[k] - y[j], rz = z[k] - z[j];
     const double ux = vx[k] - vx[j], uy = vy[k] - vy[j], uz = vz[k] - vz[j];
     const double r2 = rx * rx + ry * ry + rz * rz;
     if (r2 == 0.0) continue;
-    const double r = sqrt(r2);
-    const double rot = fmax(ro[k], ro[j]);
-    const double yv = r / rot;
+    const double rinv = 1.0 / sqrt(r2);
+    const double r = r2 * rinv;
+    const double irj = 1.0 / ro[j];
+    const double irot = irok < irj ? irok : irj;
+    const double yv = r * irot;
     if (yv >= 1.0) continue;
-    const double w = 1.0 - K_of(yv, prm.gamma);
-    const double dK = dK_of(yv, prm.gamma);
-    const double r3 = r2 * r;
+    double w = 1.0, dK = 0.0;
+    if (yv > prm.gamma) {
+      const double xs = (yv - prm.gamma) * i1mg;
+      const double x2 = xs * xs, x3 = x2 * xs, x4 = x2 * x2, u = 1.0 - xs;
+      w = 1.0 - x4 * (35.0 - 84.0 * xs + 70.0 * x2 - 20.0 * x3);
+      dK = 140.0 * x3 * (u * u * u) * i1mg;
+    }
+    const double rinv2 = rinv * rinv;
+    const double g3 = prm.G * m[j] * (rinv2 * rinv);
+    const double f = g3 * w;
     const double rv = rx * ux + ry * uy + rz * uz;
-    const double gm = prm.G * m[j];
-    ax -= gm * w * rx / r3; ay -= gm * w * ry / r3; az -= gm * w * rz / r3;
-    const double c = 3.0 * w * rv / r2 + dK * rv / (r * rot);
-    jx -= gm * (w * ux - c * rx) / r3;
-    jy -= gm * (w * uy - c * ry) / r3;
-    jz -= gm * (w * uz - c * rz) / r3;
+    ax -= f * rx; ay -= f * ry; az -= f * rz;
+    const double c = 3.0 * w * rv * rinv2 + dK * rv * rinv * irot;
+    jx -= g3 * (w * ux - c * rx);
+    jy -= g3 * (w * uy - c * ry);
+    jz -= g3 * (w * uz - c * rz);
   }
   acc[0] = ax; acc[1] = ay; acc[2] = az;
   jerk[0] = jx; jerk[1] = jy; jerk[2] = jz;
@@ -192,17 +191,170 @@ __device__ __forceinline__ double norm3(double a, double b, double c) {
 }
 
 // largest dt / 2^lvl not above dt_des, at most twice the previous step, and
-// commensurate with the current time t (units of dt / 2^40)
+// commensurate with the current time t (units of dt / 2^40).  The search
+// starts at a lower bound from the binary exponents and t's trailing zeros
+// give the commensurability level directly; the result is the same as
+// stepping lvl up one at a time.
 __device__ __forceinline__ int quantise_level(double dt_des, double dt, int prev,
                                               int64_t t, bool &underflow) {
   int lvl = 0;
+  if (dt_des > 0.0 && dt_des < dt) {
+    int l0 = ilogb(dt) - ilogb(dt_des) - 1;  // dt / 2^l > dt_des for every l <= l0
+    lvl = l0 < 0 ? 0 : (l0 > P3T_KMAX ? P3T_KMAX : l0);
+  }
   while (lvl < P3T_KMAX && ldexp(dt, -lvl) > dt_des) ++lvl;
   if (ldexp(dt, -lvl) > dt_des) underflow = true;
   if (lvl < prev - 1) lvl = prev - 1;
-  while (lvl < P3T_KMAX && (t & ((((int64_t)1) << (P3T_KMAX - lvl)) - 1)) != 0) ++lvl;
-  return lvl;
+  if (t != 0) {
+    const int need = P3T_KMAX - __ffsll((long long)t) + 1;  // 2^(40-lvl) must divide t
+    if (lvl < need) lvl = need;
+  }
+  return lvl > P3T_KMAX ? P3T_KMAX : lvl;
 }
 
+// Block-step integration of one cluster over [0, dt] by a group of NL lanes
+// (NL = 32: a warp per cluster; NL = 4: eight small clusters per warp).
+// Members are taken k = lane, lane + NL, ...; the arithmetic per member does
+// not depend on NL.
+template <int NL>
+__device__ void integrate_cluster(int64_t off, int nc, const int32_t *cl_mem,
+                                  const p3t_particles &p, const HWork &w,
+                                  const p3t_params &prm, double dt, int lane,
+                                  unsigned mask, unsigned long long &steps,
+                                  bool &underflow, DevStatus *st) {
+  const int64_t T = ((int64_t)1) << P3T_KMAX;
+  const double unit = ldexp(dt, -P3T_KMAX);
+  const double i1mg = 1.0 / (1.0 - prm.gamma);
+  double *x = w.x + off, *y = w.y + off, *z = w.z + off;
+  double *vx = w.vx + off, *vy = w.vy + off, *vz = w.vz + off;
+  double *px = w.px + off, *py = w.py + off, *pz = w.pz + off;
+  double *pvx = w.pvx + off, *pvy = w.pvy + off, *pvz = w.pvz + off;
+  double *ax = w.ax + off, *ay = w.ay + off, *az = w.az + off;
+  double *jx = w.jx + off, *jy = w.jy + off, *jz = w.jz + off;
+  double *m = w.m + off, *ro = w.ro + off;
+  int64_t *t = w.t + off;
+  int32_t *lvl = w.lvl + off;
+  for (int k = lane; k < nc; k += NL) {
+    const int32_t i = cl_mem[off + k];
+    x[k] = p.x[i]; y[k] = p.y[i]; z[k] = p.z[i];
+    vx[k] = p.vx[i]; vy[k] = p.vy[i]; vz[k] = p.vz[i];
+    m[k] = p.m[i]; ro[k] = p.r_out[i];
+  }
+  __syncwarp(mask);
+  for (int k = lane; k < nc; k += NL) {
+    double a[3], j[3];
+    hard_acc_jerk(nc, x, y, z, vx, vy, vz, m, ro, prm, i1mg, k, a, j);
+    ax[k] = a[0]; ay[k] = a[1]; az[k] = a[2];
+    jx[k] = j[0]; jy[k] = j[1]; jz[k] = j[2];
+    const double an = norm3(a[0], a[1], a[2]), jn = norm3(j[0], j[1], j[2]);
+    const double dtd = jn > 0.0 ? prm.eta0 * an / jn : dt;
+    t[k] = 0;
+    lvl[k] = quantise_level(dtd, dt, 0, 0, underflow);
+  }
+  __syncwarp(mask);
+  int64_t iter = 0;
+  for (;;) {
+    int64_t tn = T, tmin = T;
+    for (int k = lane; k < nc; k += NL) {
+      const int64_t e = t[k] + (T >> lvl[k]);
+      tn = e < tn ? e : tn;
+      tmin = t[k] < tmin ? t[k] : tmin;
+    }
+#pragma unroll
+    for (int o = NL / 2; o > 0; o >>= 1) {
+      const int64_t a = __shfl_xor_sync(mask, tn, o);
+      const int64_t b = __shfl_xor_sync(mask, tmin, o);
+      tn = a < tn ? a : tn;
+      tmin = b < tmin ? b : tmin;
+    }
+    if (tmin >= T) break;
+    if (++iter > kHermiteIterLimit) {
+      if (lane == 0) dev_fail(st, P3T_ERR_TIMEOUT, 61, 0);
+      break;
+    }
+    // predict every member to the block time
+    for (int k = lane; k < nc; k += NL) {
+      const double D = (double)(tn - t[k]) * unit;
+      const double D2 = D * D, D3 = D2 * D;
+      px[k] = x[k] + vx[k] * D + ax[k] * D2 * 0.5 + jx[k] * D3 * (1.0 / 6.0);
+      py[k] = y[k] + vy[k] * D + ay[k] * D2 * 0.5 + jy[k] * D3 * (1.0 / 6.0);
+      pz[k] = z[k] + vz[k] * D + az[k] * D2 * 0.5 + jz[k] * D3 * (1.0 / 6.0);
+      pvx[k] = vx[k] + ax[k] * D + jx[k] * D2 * 0.5;
+      pvy[k] = vy[k] + ay[k] * D + jy[k] * D2 * 0.5;
+      pvz[k] = vz[k] + az[k] * D + jz[k] * D2 * 0.5;
+    }
+    __syncwarp(mask);
+    // evaluate and correct the active members
+    for (int k = lane; k < nc; k += NL) {
+      if (t[k] + (T >> lvl[k]) != tn) continue;
+      double a1[3], j1[3];
+      hard_acc_jerk(nc, px, py, pz, pvx, pvy, pvz, m, ro, prm, i1mg, k, a1, j1);
+      const double D = (double)(T >> lvl[k]) * unit;
+      const double D2 = D * D, D3 = D2 * D, D4 = D3 * D, D5 = D4 * D;
+      const double iD = 1.0 / D, iD2 = iD * iD, iD3 = iD2 * iD;
+      const double a0[3] = {ax[k], ay[k], az[k]}, j0[3] = {jx[k], jy[k], jz[k]};
+      double A2[3], A3[3], A2e[3];
+      for (int q = 0; q < 3; ++q) {
+        const double da = a0[q] - a1[q];
+        A2[q] = (-6.0 * da - D * (4.0 * j0[q] + 2.0 * j1[q])) * iD2;
+        A3[q] = (12.0 * da + 6.0 * D * (j0[q] + j1[q])) * iD3;
+        A2e[q] = A2[q] + D * A3[q];
+      }
+      x[k] = px[k] + A2[0] * D4 * (1.0 / 24.0) + A3[0] * D5 * (1.0 / 120.0);
+      y[k] = py[k] + A2[1] * D4 * (1.0 / 24.0) + A3[1] * D5 * (1.0 / 120.0);
+      z[k] = pz[k] + A2[2] * D4 * (1.0 / 24.0) + A3[2] * D5 * (1.0 / 120.0);
+      vx[k] = pvx[k] + A2[0] * D3 * (1.0 / 6.0) + A3[0] * D4 * (1.0 / 24.0);
+      vy[k] = pvy[k] + A2[1] * D3 * (1.0 / 6.0) + A3[1] * D4 * (1.0 / 24.0);
+      vz[k] = pvz[k] + A2[2] * D3 * (1.0 / 6.0) + A3[2] * D4 * (1.0 / 24.0);
+      ax[k] = a1[0]; ay[k] = a1[1]; az[k] = a1[2];
+      jx[k] = j1[0]; jy[k] = j1[1]; jz[k] = j1[2];
+      const double an = norm3(a1[0], a1[1], a1[2]), jn = norm3(j1[0], j1[1], j1[2]);
+      const double a2n = norm3(A2e[0], A2e[1], A2e[2]), a3n = norm3(A3[0], A3[1], A3[2]);
+      const double num = an * a2n + jn * jn, den = jn * a3n + a2n * a2n;
+      const double dtd = den > 0.0 ? sqrt(prm.eta * num / den) : dt;
+      t[k] = tn;
+      lvl[k] = quantise_level(dtd, dt, lvl[k], tn, underflow);
+      ++steps;
+    }
+    __syncwarp(mask);
+  }
+  for (int k = lane; k < nc; k += NL) {
+    const int32_t i = cl_mem[off + k];
+    p.x[i] = x[k]; p.y[i] = y[k]; p.z[i] = z[k];
+    p.vx[i] = vx[k]; p.vy[i] = vy[k]; p.vz[i] = vz[k];
+  }
+  __syncwarp(mask);
+}
+
+constexpr int kSmallCluster = 4;  // clusters up to this size: a 4-lane group each
+
+// clusters of <= kSmallCluster members: a group of 4 lanes each, eight per
+// warp (most clusters are pairs: a whole warp per pair would leave 30 of 32
+// FP64 lanes idle, a single thread per pair would serialise its members)
+__global__ void k_hermite_small(const int64_t *d_ncl, const int64_t *cl_off,
+                                const int32_t *cl_mem, p3t_particles p, HWork w,
+                                p3t_params prm, double dt,
+                                unsigned long long *steps_out, DevStatus *st) {
+  const int64_t ncl = *d_ncl;
+  const int lane = threadIdx.x & 3;
+  const unsigned mask = 0xfu << (threadIdx.x & 28);
+  unsigned long long steps = 0;
+  bool underflow = false;
+  const int64_t g0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 2;
+  const int64_t ng = ((int64_t)gridDim.x * blockDim.x) >> 2;
+  for (int64_t c = g0; c < ncl; c += ng) {
+    const int64_t off = cl_off[c];
+    const int nc = (int)(cl_off[c + 1] - off);
+    if (nc > kSmallCluster) continue;
+    integrate_cluster<4>(off, nc, cl_mem, p, w, prm, dt, lane, mask, steps, underflow, st);
+  }
+  if (underflow) dev_fail(st, P3T_ERR_DT_UNDERFLOW, 62, 0);
+  __syncwarp();
+  for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(0xffffffffu, steps, o);
+  if ((threadIdx.x & 31) == 0 && steps_out && steps) atomicAdd(steps_out, steps);
+}
+
+// larger clusters: one warp each
 __global__ void k_hermite(const int64_t *d_ncl, const int64_t *cl_off,
                           const int32_t *cl_mem, p3t_particles p, HWork w,
                           p3t_params prm, double dt,
@@ -211,110 +363,14 @@ __global__ void k_hermite(const int64_t *d_ncl, const int64_t *cl_off,
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t ncl = *d_ncl;
-  const int64_t T = ((int64_t)1) << P3T_KMAX;
-  const double unit = ldexp(dt, -P3T_KMAX);
   unsigned long long steps = 0;
   bool underflow = false;
   for (int64_t c = warp; c < ncl; c += nwarps) {
     const int64_t off = cl_off[c];
     const int nc = (int)(cl_off[c + 1] - off);
-    double *x = w.x + off, *y = w.y + off, *z = w.z + off;
-    double *vx = w.vx + off, *vy = w.vy + off, *vz = w.vz + off;
-    double *px = w.px + off, *py = w.py + off, *pz = w.pz + off;
-    double *pvx = w.pvx + off, *pvy = w.pvy + off, *pvz = w.pvz + off;
-    double *ax = w.ax + off, *ay = w.ay + off, *az = w.az + off;
-    double *jx = w.jx + off, *jy = w.jy + off, *jz = w.jz + off;
-    double *m = w.m + off, *ro = w.ro + off;
-    int64_t *t = w.t + off;
-    int32_t *lvl = w.lvl + off;
-    for (int k = lane; k < nc; k += 32) {
-      const int32_t i = cl_mem[off + k];
-      x[k] = p.x[i]; y[k] = p.y[i]; z[k] = p.z[i];
-      vx[k] = p.vx[i]; vy[k] = p.vy[i]; vz[k] = p.vz[i];
-      m[k] = p.m[i]; ro[k] = p.r_out[i];
-    }
-    __syncwarp();
-    for (int k = lane; k < nc; k += 32) {
-      double a[3], j[3];
-      hard_acc_jerk(nc, x, y, z, vx, vy, vz, m, ro, prm, k, a, j);
-      ax[k] = a[0]; ay[k] = a[1]; az[k] = a[2];
-      jx[k] = j[0]; jy[k] = j[1]; jz[k] = j[2];
-      const double an = norm3(a[0], a[1], a[2]), jn = norm3(j[0], j[1], j[2]);
-      const double dtd = jn > 0.0 ? prm.eta0 * an / jn : dt;
-      t[k] = 0;
-      lvl[k] = quantise_level(dtd, dt, 0, 0, underflow);
-    }
-    __syncwarp();
-    int64_t iter = 0;
-    for (;;) {
-      int64_t tn = T, tmin = T;
-      for (int k = lane; k < nc; k += 32) {
-        const int64_t e = t[k] + (T >> lvl[k]);
-        tn = e < tn ? e : tn;
-        tmin = t[k] < tmin ? t[k] : tmin;
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const int64_t a = __shfl_xor_sync(0xffffffffu, tn, o);
-        const int64_t b = __shfl_xor_sync(0xffffffffu, tmin, o);
-        tn = a < tn ? a : tn;
-        tmin = b < tmin ? b : tmin;
-      }
-      if (tmin >= T) break;
-      if (++iter > kHermiteIterLimit) {
-        if (lane == 0) dev_fail(st, P3T_ERR_TIMEOUT, 61, 0);
-        break;
-      }
-      // predict every member to the block time
-      for (int k = lane; k < nc; k += 32) {
-        const double D = (double)(tn - t[k]) * unit;
-        const double D2 = D * D, D3 = D2 * D;
-        px[k] = x[k] + vx[k] * D + ax[k] * D2 / 2.0 + jx[k] * D3 / 6.0;
-        py[k] = y[k] + vy[k] * D + ay[k] * D2 / 2.0 + jy[k] * D3 / 6.0;
-        pz[k] = z[k] + vz[k] * D + az[k] * D2 / 2.0 + jz[k] * D3 / 6.0;
-        pvx[k] = vx[k] + ax[k] * D + jx[k] * D2 / 2.0;
-        pvy[k] = vy[k] + ay[k] * D + jy[k] * D2 / 2.0;
-        pvz[k] = vz[k] + az[k] * D + jz[k] * D2 / 2.0;
-      }
-      __syncwarp();
-      // evaluate and correct the active members
-      for (int k = lane; k < nc; k += 32) {
-        if (t[k] + (T >> lvl[k]) != tn) continue;
-        double a1[3], j1[3];
-        hard_acc_jerk(nc, px, py, pz, pvx, pvy, pvz, m, ro, prm, k, a1, j1);
-        const double D = (double)(T >> lvl[k]) * unit;
-        const double D2 = D * D, D3 = D2 * D, D4 = D3 * D, D5 = D4 * D;
-        const double a0[3] = {ax[k], ay[k], az[k]}, j0[3] = {jx[k], jy[k], jz[k]};
-        double A2[3], A3[3], A2e[3];
-        for (int q = 0; q < 3; ++q) {
-          const double da = a0[q] - a1[q];
-          A2[q] = (-6.0 * da - D * (4.0 * j0[q] + 2.0 * j1[q])) / D2;
-          A3[q] = (12.0 * da + 6.0 * D * (j0[q] + j1[q])) / D3;
-          A2e[q] = A2[q] + D * A3[q];
-        }
-        x[k] = px[k] + A2[0] * D4 / 24.0 + A3[0] * D5 / 120.0;
-        y[k] = py[k] + A2[1] * D4 / 24.0 + A3[1] * D5 / 120.0;
-        z[k] = pz[k] + A2[2] * D4 / 24.0 + A3[2] * D5 / 120.0;
-        vx[k] = pvx[k] + A2[0] * D3 / 6.0 + A3[0] * D4 / 24.0;
-        vy[k] = pvy[k] + A2[1] * D3 / 6.0 + A3[1] * D4 / 24.0;
-        vz[k] = pvz[k] + A2[2] * D3 / 6.0 + A3[2] * D4 / 24.0;
-        ax[k] = a1[0]; ay[k] = a1[1]; az[k] = a1[2];
-        jx[k] = j1[0]; jy[k] = j1[1]; jz[k] = j1[2];
-        const double an = norm3(a1[0], a1[1], a1[2]), jn = norm3(j1[0], j1[1], j1[2]);
-        const double a2n = norm3(A2e[0], A2e[1], A2e[2]), a3n = norm3(A3[0], A3[1], A3[2]);
-        const double num = an * a2n + jn * jn, den = jn * a3n + a2n * a2n;
-        const double dtd = den > 0.0 ? sqrt(prm.eta * num / den) : dt;
-        t[k] = tn;
-        lvl[k] = quantise_level(dtd, dt, lvl[k], tn, underflow);
-        ++steps;
-      }
-      __syncwarp();
-    }
-    for (int k = lane; k < nc; k += 32) {
-      const int32_t i = cl_mem[off + k];
-      p.x[i] = x[k]; p.y[i] = y[k]; p.z[i] = z[k];
-      p.vx[i] = vx[k]; p.vy[i] = vy[k]; p.vz[i] = vz[k];
-    }
-    __syncwarp();
+    if (nc <= kSmallCluster) continue;
+    integrate_cluster<32>(off, nc, cl_mem, p, w, prm, dt, lane, 0xffffffffu, steps,
+                          underflow, st);
   }
   if (underflow) dev_fail(st, P3T_ERR_DT_UNDERFLOW, 62, 0);
   for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(0xffffffffu, steps, o);
@@ -446,12 +502,14 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
   unsigned long long *steps = n_steps ? reinterpret_cast<unsigned long long *>(n_steps)
                                       : c->hsteps;
   k_zero_u64<<<1, 1, 0, s>>>(steps);
-  // one warp per cluster; at most n/2 clusters
-  const int64_t warps = (n / 2) > 0 ? n / 2 : 1;
-  const int64_t gw = p3t_grid(warps * 32, 128, maxb);
-  k_hermite<<<(unsigned)gw, 128, 0, s>>>(&cl->counts[1], cl->cl_off, cl->cl_mem, *p, w,
-                                          c->prm, dt, steps, c->status);
-  p3t_note_launches(3);
+  // at most n/2 clusters: a thread per small cluster, a warp per large one
+  const int64_t ncl_max = (n / 2) > 0 ? n / 2 : 1;
+  // 32-thread blocks (8 clusters each) spread consecutive clusters over all SMs
+  k_hermite_small<<<(unsigned)p3t_grid(ncl_max * 4, 32, 4 * maxb), 32, 0, s>>>(
+      &cl->counts[1], cl->cl_off, cl->cl_mem, *p, w, c->prm, dt, steps, c->status);
+  k_hermite<<<(unsigned)p3t_grid(ncl_max * 32, 128, maxb), 128, 0, s>>>(
+      &cl->counts[1], cl->cl_off, cl->cl_mem, *p, w, c->prm, dt, steps, c->status);
+  p3t_note_launches(4);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 

@@ -176,6 +176,7 @@ int64_t p3t_radix_hist_entries(int64_t n_cap);
 // ---- stages (tree.cu, walk.cu, neighbours.cu, hard.cu) -------------------
 int p3t_run_cutoffs(p3t_ctx *c, p3t_particles *p, cudaStream_t s);
 int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s);
+int p3t_run_tree_stats(p3t_ctx *c, cudaStream_t s);
 int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
                        double *ay, double *az, uint64_t *counts,
                        cudaStream_t s);

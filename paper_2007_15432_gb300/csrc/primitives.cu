@@ -102,32 +102,39 @@ __global__ void radix_upsweep(const uint64_t *keys, const int64_t *d_n,
   hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of the digit-major histogram (single block)
-__global__ void radix_scan(uint32_t *hist, int64_t entries) {
+// exclusive scan of each digit's row of tile counts (one block per digit);
+// the row total goes to the last slot of the digit's totals
+__global__ void __launch_bounds__(kRadix) radix_row_scan(uint32_t *hist, int ntiles,
+                                                         uint32_t *digit_total) {
   __shared__ int64_t sh[33];
-  const int64_t per = (entries + blockDim.x - 1) / blockDim.x;
-  const int64_t lo = threadIdx.x * per, hi = min(entries, lo + per);
-  int64_t s = 0;
-  for (int64_t i = lo; i < hi; ++i) s += hist[i];
-  int64_t ex;
-  block_excl_scan(s, &ex, sh);
-  for (int64_t i = lo; i < hi; ++i) {
-    uint32_t v = hist[i];
-    hist[i] = (uint32_t)ex;
-    ex += v;
+  uint32_t *row = hist + (int64_t)blockIdx.x * ntiles;
+  int64_t carry = 0;
+  for (int base = 0; base < ntiles; base += kRadix) {
+    const int i = base + threadIdx.x;
+    const int64_t v = i < ntiles ? row[i] : 0;
+    int64_t ex;
+    const int64_t tot = block_excl_scan(v, &ex, sh);
+    if (i < ntiles) row[i] = (uint32_t)(carry + ex);
+    carry += tot;
   }
+  if (threadIdx.x == 0) digit_total[blockIdx.x] = (uint32_t)carry;
 }
 
 __global__ void __launch_bounds__(kSortThreads)
 radix_downsweep(const uint64_t *keys, const int32_t *vals, uint64_t *okeys,
                 int32_t *ovals, const int64_t *d_n, int shift,
-                const uint32_t *hist, int ntiles) {
+                const uint32_t *hist, int ntiles, const uint32_t *digit_total) {
   __shared__ uint32_t s_warp[kSortThreads / 32][kRadix];
   __shared__ uint32_t s_run[kRadix];
   __shared__ uint32_t s_base[kRadix];
+  __shared__ int64_t sh[33];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   s_run[t] = 0;
-  s_base[t] = hist[(int64_t)t * ntiles + blockIdx.x];
+  {
+    int64_t ex;
+    block_excl_scan((int64_t)digit_total[t], &ex, sh);   // digit bases
+    s_base[t] = (uint32_t)ex + hist[(int64_t)t * ntiles + blockIdx.x];
+  }
   const int64_t n = *d_n;
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   const uint32_t lt = (1u << lane) - 1u;
@@ -186,7 +193,7 @@ int p3t_scan_i32_to_i64(const int32_t *in, int64_t *out, const int64_t *d_n,
 int64_t p3t_radix_hist_entries(int64_t n_cap) {
   int64_t ntiles = (n_cap + kSortTile - 1) / kSortTile;
   if (ntiles < 1) ntiles = 1;
-  return ntiles * kRadix;
+  return ntiles * kRadix + kRadix;  // + the digit totals
 }
 
 int p3t_radix_sort(uint64_t **keys, int32_t **vals, uint64_t **keys_alt,
@@ -195,13 +202,14 @@ int p3t_radix_sort(uint64_t **keys, int32_t **vals, uint64_t **keys_alt,
                    int64_t hist_cap, cudaStream_t s) {
   int64_t ntiles = (n_cap + kSortTile - 1) / kSortTile;
   if (ntiles < 1) ntiles = 1;
-  if (ntiles * kRadix > hist_cap) return P3T_ERR_CAPACITY;
+  if (ntiles * kRadix + kRadix > hist_cap) return P3T_ERR_CAPACITY;
+  uint32_t *digit_total = hist + ntiles * kRadix;
   for (int shift = begin_bit; shift < end_bit; shift += kRadixBits) {
     radix_upsweep<<<(unsigned)ntiles, kSortThreads, 0, s>>>(*keys, d_n, shift,
                                                             hist, (int)ntiles);
-    radix_scan<<<1, 1024, 0, s>>>(hist, ntiles * kRadix);
+    radix_row_scan<<<kRadix, kRadix, 0, s>>>(hist, (int)ntiles, digit_total);
     radix_downsweep<<<(unsigned)ntiles, kSortThreads, 0, s>>>(
-        *keys, *vals, *keys_alt, *vals_alt, d_n, shift, hist, (int)ntiles);
+        *keys, *vals, *keys_alt, *vals_alt, d_n, shift, hist, (int)ntiles, digit_total);
     p3t_note_launches(3);
     uint64_t *tk = *keys; *keys = *keys_alt; *keys_alt = tk;
     int32_t *tv = *vals; *vals = *vals_alt; *vals_alt = tv;

@@ -482,9 +482,16 @@ __global__ void k_tree_stats(const int64_t *d_nnode, int64_t node_cap,
     depth = max(depth, (unsigned long long)node[b].level);
     if (node[b].nchild == 0) { ++nleaf; maxleaf = max(maxleaf, (unsigned long long)node[b].count); }
   }
-  atomicMax(reinterpret_cast<unsigned long long *>(&stats[2]), depth);
-  atomicMax(reinterpret_cast<unsigned long long *>(&stats[3]), maxleaf);
-  atomicAdd(reinterpret_cast<unsigned long long *>(&stats[1]), nleaf);
+  for (int o = 16; o > 0; o >>= 1) {
+    depth = max(depth, __shfl_xor_sync(0xffffffffu, depth, o));
+    maxleaf = max(maxleaf, __shfl_xor_sync(0xffffffffu, maxleaf, o));
+    nleaf += __shfl_xor_sync(0xffffffffu, nleaf, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(reinterpret_cast<unsigned long long *>(&stats[2]), depth);
+    atomicMax(reinterpret_cast<unsigned long long *>(&stats[3]), maxleaf);
+    atomicAdd(reinterpret_cast<unsigned long long *>(&stats[1]), nleaf);
+  }
 }
 
 }  // namespace
@@ -559,11 +566,19 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   k_moments<<<(unsigned)gn, 128, 0, s>>>(&cnt[2], c->leaf_list, c->node, c->mom64, c->mom32,
                                          c->nrs, c->node_done, c->sx, c->sy, c->sz, c->sm,
                                          c->srs, c->sq, c->box, c->leaf_of);
-  P3T_CUDA_TRY(cudaMemsetAsync(&cnt[4], 0, 4 * sizeof(int64_t), s));
-  k_tree_stats<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->node, &cnt[4]);
   // own kernels here (the scans and sorts count themselves): box 3, keys, n,
   // gather, lcp, levels, clamp, nodes_pre, pre2bfs, nodes_bfs, parents,
-  // leaf_list, moments, tree_stats
-  p3t_note_launches(16);
+  // leaf_list, moments
+  p3t_note_launches(15);
+  return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
+}
+
+// tree statistics on demand (diagnostics; not part of the step)
+int p3t_run_tree_stats(p3t_ctx *c, cudaStream_t s) {
+  int64_t *cnt = c->counters;
+  P3T_CUDA_TRY(cudaMemsetAsync(&cnt[4], 0, 4 * sizeof(int64_t), s));
+  const int64_t gn = p3t_grid(c->node_cap, kBlock, (int64_t)c->num_sms * P3T_NSM_BLOCKS);
+  k_tree_stats<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->node, &cnt[4]);
+  p3t_note_launches(1);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
