@@ -40,7 +40,8 @@ class OrParams(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "G", "m_star", "dt_soft", "gamma", "rcut0", "rcut1", "rs0", "rs1", "rs2",
         "rs3", "theta", "eta", "eta0")] + [
-        ("leaf_size", C.c_int32), ("precision", C.c_int32), ("vran_bins", C.c_int32)]
+        ("leaf_size", C.c_int32), ("precision", C.c_int32), ("vran_bins", C.c_int32),
+        ("group_size", C.c_int32)]
 
 
 @dataclass
@@ -64,6 +65,7 @@ class Params:
     leaf_size: int = 16
     precision: int = 0
     vran_bins: int = 0
+    group_size: int = 0
 
     def c(self) -> OrParams:
         return OrParams(*[getattr(self, f[0]) for f in OrParams._fields_])

@@ -160,8 +160,10 @@ int or_direct_soft(int64_t n, const double *x, const double *y, const double *z,
 /*    (key, caller index);                                                    */
 /*  * a node is a key prefix at level l holding > 0 particles; a node is      */
 /*    split while it holds more than leaf_size particles and l < 21;          */
-/*  * target groups are the leaves.  Opening is decided on the quantised      */
-/*    grid, in exact integer arithmetic:                                      */
+/*  * target groups: a node is a group iff it holds <= group_size particles  */
+/*    or is a leaf, and it is the root or its parent holds > group_size       */
+/*    (group_size = 0: every leaf is a group).  Opening is decided for the    */
+/*    group's box on the quantised grid, in exact integer arithmetic:         */
 /*    (i) Barnes-Hut: with the node's cell side s and centre c, and the       */
 /*        group's cells [qlo, qhi + 1] (all in half units), open iff          */
 /*        d^2 < ceil((2 s)^2 / theta^2), d the point-box distance;  this is   */
@@ -237,6 +239,7 @@ typedef struct {
   int64_t *qx, *qy, *qz;
   or_node *node;
   int64_t nnode, cap;
+  int64_t *parent;   /* parent node, -1 for the root */
   double box[4];
 } or_tree;
 
@@ -388,12 +391,17 @@ static void tree_build(or_tree *T, int64_t n, const double *x, const double *y,
   }
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t k = 0; k < T->nnode; ++k) fill_node(T, &T->node[k]);
+  T->parent = (int64_t *)malloc(sizeof(int64_t) * T->nnode);
+  T->parent[0] = -1;
+  for (int64_t k = 0; k < T->nnode; ++k)
+    for (int64_t c = T->node[k].child0; c < T->node[k].child0 + T->node[k].nchild; ++c)
+      T->parent[c] = k;
 }
 
 static void tree_free(or_tree *T) {
   free(T->ord); free(T->key); free(T->x); free(T->y); free(T->z); free(T->m);
   free(T->ro); free(T->rs); free(T->qx); free(T->qy); free(T->qz);
-  free(T->node);
+  free(T->node); free(T->parent);
 }
 
 /* Barnes-Hut thresholds per level (reading C4): open iff d^2 < T[l] with    */
@@ -509,15 +517,17 @@ int or_tree_soft(int64_t n, const double *x, const double *y, const double *z,
   } else {
     memset(is_target, 1, n);
   }
-  /* leaves in node order are the target groups */
-  int64_t nleaf = 0, maxdepth = 0;
+  /* target groups (see above), in node order */
+  int64_t nleaf = 0, maxdepth = 0, ngroup = 0;
+  const int64_t gs = p->group_size;
+  int64_t *leaves = (int64_t *)malloc(sizeof(int64_t) * T.nnode);
   for (int64_t k = 0; k < T.nnode; ++k) {
     if (T.node[k].nchild == 0) ++nleaf;
     if (T.node[k].level > maxdepth) maxdepth = T.node[k].level;
+    int small = T.node[k].count <= gs || T.node[k].nchild == 0;
+    int top = k == 0 || T.node[T.parent[k]].count > gs;
+    if (small && top) leaves[ngroup++] = k;
   }
-  int64_t *leaves = (int64_t *)malloc(sizeof(int64_t) * nleaf);
-  nleaf = 0;
-  for (int64_t k = 0; k < T.nnode; ++k) if (T.node[k].nchild == 0) leaves[nleaf++] = k;
   int nth = or_num_threads();
   cand_buf *cbs = (cand_buf *)calloc(nth, sizeof(cand_buf));
   uint64_t npp = 0, npn = 0;
@@ -531,12 +541,12 @@ int or_tree_soft(int64_t n, const double *x, const double *y, const double *z,
 #endif
     double (*acc)[3] = (double (*)[3])malloc(sizeof(double) * 3 * (p->leaf_size > 0 ? p->leaf_size : 1) + 3 * sizeof(double) * 64);
 #pragma omp for schedule(dynamic, 16)
-    for (int64_t gi = 0; gi < nleaf; ++gi) {
+    for (int64_t gi = 0; gi < ngroup; ++gi) {
       const or_node *g = &T.node[leaves[gi]];
       int any = 0;
       for (int64_t s = g->first; s < g->first + g->count; ++s) any |= is_target[s];
       if (!any) continue;
-      /* a leaf at level 21 may exceed leaf_size; grow the accumulator then */
+      /* a group may exceed the preallocated size; grow the accumulator then */
       double (*a)[3] = acc;
       double (*big)[3] = NULL;
       if (g->count > (p->leaf_size > 0 ? p->leaf_size : 1) + 64) {
@@ -570,8 +580,9 @@ int or_tree_soft(int64_t n, const double *x, const double *y, const double *z,
   if (tree_stats) {
     tree_stats[0] = T.nnode; tree_stats[1] = nleaf; tree_stats[2] = maxdepth;
     tree_stats[3] = 0;
-    for (int64_t k = 0; k < nleaf; ++k)
-      if (T.node[leaves[k]].count > tree_stats[3]) tree_stats[3] = T.node[leaves[k]].count;
+    for (int64_t k = 0; k < T.nnode; ++k)
+      if (T.node[k].nchild == 0 && T.node[k].count > tree_stats[3])
+        tree_stats[3] = T.node[k].count;
   }
   free(leaves); free(is_target); free(inv);
   tree_free(&T);
@@ -813,6 +824,9 @@ void or_hard_acc_jerk(int64_t nc, const double *x, const double *y,
 /* commensurate with the particle's current time (integer units of           */
 /* dt_soft / 2^40).  Sets *underflow when even dt_soft / 2^40 is too long.     */
 #define OR_KMAX 40
+/* a cluster whose steps collapse (two bodies passing ever closer: the paper
+ * merges such pairs, Sec. 2.4) is given up after this many block steps */
+#define OR_BLOCK_LIMIT ((int64_t)1 << 24)
 static int quantise_level(double dt_des, double dt_soft, int prev_level,
                           int64_t t_int, int *underflow) {
   int lvl = 0;
@@ -823,7 +837,14 @@ static int quantise_level(double dt_des, double dt_soft, int prev_level,
   return lvl;
 }
 
-static double norm3(const double *v) { return sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]); }
+/* The step estimates only set a power-of-two step, so they are formed in
+ * single precision.  Each derivative is first scaled by an exact power of two
+ * s^k, s = 2^e close to the step, so that every term of the estimate has the
+ * size of an acceleration squared and nothing overflows FP32. */
+static float norm3f(const double *v, int k) {
+  float a = (float)ldexp(v[0], k), b = (float)ldexp(v[1], k), c = (float)ldexp(v[2], k);
+  return sqrtf(a * a + b * b + c * c);
+}
 
 /* Fourth-order Hermite with block individual time steps over [0, dt] for one */
 /* cluster (Sec. 2.1.2, Makino 1991; Aarseth time steps).  Reading C7:        */
@@ -833,7 +854,8 @@ static double norm3(const double *v) { return sqrt(v[0] * v[0] + v[1] * v[1] + v
 /*             x = x_p + a2 D^4/24 + a3 D^5/120, v = v_p + a2 D^3/6 + a3 D^4/24;*/
 /*  new step   sqrt(eta (|a||a2'| + |j|^2)/(|j||a3| + |a2'|^2)), a2' = a2+D a3;*/
 /*  first step eta0 |a|/|j| (each hard step starts afresh, so every member's   */
-/*  first step of the hard step uses eta0).                                   */
+/*  first step of the hard step uses eta0).  Both estimates are formed in FP32  */
+/*  (they are quantised to dt / 2^k); state, forces and corrector are FP64.    */
 /* All members are predicted to each block time; the active ones are        */
 /* evaluated from the predicted state and then corrected together.           */
 int or_hermite_cluster(int64_t nc, const int32_t *members, double *X, double *Y,
@@ -860,13 +882,17 @@ int or_hermite_cluster(int64_t nc, const int32_t *members, double *X, double *Y,
   }
   for (int64_t k = 0; k < nc; ++k) {
     or_hard_acc_jerk(nc, x, y, z, vx, vy, vz, m, ro, p, k, a + 3 * k, jk + 3 * k);
-    double an = norm3(a + 3 * k), jn = norm3(jk + 3 * k);
-    double dtd = jn > 0.0 ? p->eta0 * an / jn : dt;
+    /* eta0 |a| / |j| = (eta0 |a| / |j s|) s, s = 2^e */
+    int e = ilogb(dt);
+    float an = norm3f(a + 3 * k, 0), jn = norm3f(jk + 3 * k, e);
+    double dtd = jn > 0.0f ? ldexp((double)((float)p->eta0 * an / jn), e) : dt;
     t[k] = 0;
     lvl[k] = quantise_level(dtd, dt, 0, 0, &underflow);
   }
-  int64_t steps = 0;
+  int64_t steps = 0, blocks = 0;
+  int timeout = 0;
   for (;;) {
+    if (++blocks > OR_BLOCK_LIMIT) { timeout = 1; break; }
     int64_t tn = T;
     for (int64_t k = 0; k < nc; ++k) {
       int64_t e = t[k] + (T >> lvl[k]);
@@ -908,10 +934,13 @@ int or_hermite_cluster(int64_t nc, const int32_t *members, double *X, double *Y,
       vy[k] = pvy[k] + A2[1] * D3 * (1.0 / 6.0) + A3[1] * D4 * (1.0 / 24.0);
       vz[k] = pvz[k] + A2[2] * D3 * (1.0 / 6.0) + A3[2] * D4 * (1.0 / 24.0);
       for (int c = 0; c < 3; ++c) { a[3 * k + c] = a1[3 * k + c]; jk[3 * k + c] = j1[3 * k + c]; }
-      double an = norm3(a + 3 * k), jn = norm3(jk + 3 * k);
-      double a2n = norm3(A2e), a3n = norm3(A3);
-      double num = an * a2n + jn * jn, den = jn * a3n + a2n * a2n;
-      double dtd = den > 0.0 ? sqrt(p->eta * num / den) : dt;
+      /* Aarseth step with j, a2, a3 scaled by s, s^2, s^3 (s = 2^e ~ D):
+       * dt = sqrt(eta num_s / den_s) s */
+      int e = ilogb(D);
+      float an = norm3f(a + 3 * k, 0), jn = norm3f(jk + 3 * k, e);
+      float a2n = norm3f(A2e, 2 * e), a3n = norm3f(A3, 3 * e);
+      float num = an * a2n + jn * jn, den = jn * a3n + a2n * a2n;
+      double dtd = den > 0.0f ? ldexp((double)sqrtf((float)p->eta * num / den), e) : dt;
       t[k] = tn;
       lvl[k] = quantise_level(dtd, dt, lvl[k], tn, &underflow);
       ++steps;
@@ -923,6 +952,7 @@ int or_hermite_cluster(int64_t nc, const int32_t *members, double *X, double *Y,
   }
   if (n_steps) *n_steps = steps;
   free(buf); free(t); free(lvl); free(act);
+  if (timeout) return -5;
   return underflow ? -4 : 0;
 }
 
@@ -1027,17 +1057,17 @@ int or_hard_step(int64_t n, double *x, double *y, double *z, double *vx,
   int err = or_kepler_drift(n_single, singles, x, y, z, vx, vy, vz, dt, p->G * p->m_star);
   int64_t steps = 0;
   int herr = 0;
-#pragma omp parallel for schedule(dynamic, 1) reduction(+ : steps) reduction(| : herr)
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : steps) reduction(min : herr)
   for (int64_t c = 0; c < n_clusters; ++c) {
     int64_t ns = 0;
     int e = or_hermite_cluster(cl_off[c + 1] - cl_off[c], cl_mem + cl_off[c], x, y, z,
                                vx, vy, vz, m, r_out, p, dt, &ns);
-    if (e) herr |= 1;
+    if (e) herr = e;
     steps += ns;
   }
   if (n_hermite_steps) *n_hermite_steps = steps;
   if (err) return -1;
-  return herr ? -4 : 0;
+  return herr;
 }
 
 /* ========================================================================= */

@@ -32,6 +32,8 @@ typedef struct {
   int32_t leaf_size;    /* maximum particles per leaf / target group             */
   int32_t precision;    /* unused by the oracle (always FP64)                    */
   int32_t vran_bins;    /* radial bins for v_ran; 0 = clamp(N/1000, 1, 1024)     */
+  int32_t group_size;   /* target groups: highest nodes holding <= group_size
+                           particles (0: every leaf is a group)               */
 } or_params;
 
 /* ---- changeover functions (Sec. 2.1.1, Eq. cutfuncW and the K definition) -- */

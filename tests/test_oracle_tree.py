@@ -37,9 +37,10 @@ def test_morton_keys_bitwise(orc):
         assert int(key[i]) == k
 
 
-def test_theta0_tree_equals_direct_sum(orc):
+@pytest.mark.parametrize("group_size", [0, 32, 64])
+def test_theta0_tree_equals_direct_sum(orc, group_size):
     s = _small()
-    p = orc.Params(theta=0.0, leaf_size=16)
+    p = orc.Params(theta=0.0, leaf_size=16, group_size=group_size)
     ro, rs, _, _ = orc.cutoffs(s, p)
     res = orc.tree_soft(s, ro, rs, p)
     ref = orc.direct_soft(s, ro, p)
@@ -119,9 +120,10 @@ def test_quadrupole_moment_definition(orc):
     assert abs(np.trace(got)) < 1e-13
 
 
-def test_theta_half_accuracy_and_counts(orc):
+@pytest.mark.parametrize("group_size", [0, 32])
+def test_theta_half_accuracy_and_counts(orc, group_size):
     s = disks.equal_mass_ring(n=4000, seed=21)
-    p = orc.Params(theta=0.5)
+    p = orc.Params(theta=0.5, group_size=group_size)
     ro, rs, _, _ = orc.cutoffs(s, p)
     res = orc.tree_soft(s, ro, rs, p)
     ref = orc.direct_soft(s, ro, p)
@@ -132,10 +134,10 @@ def test_theta_half_accuracy_and_counts(orc):
     assert res.tree["max_leaf"] <= 16
 
 
-@pytest.mark.parametrize("theta", [0.0, 0.5, 1.0])
-def test_candidates_are_all_pairs_within_search_radius(orc, theta):
+@pytest.mark.parametrize("theta,group_size", [(0.0, 0), (0.5, 0), (1.0, 0), (0.5, 32), (1.0, 64)])
+def test_candidates_are_all_pairs_within_search_radius(orc, theta, group_size):
     s = _small(800, seed=13)
-    p = orc.Params(theta=theta)
+    p = orc.Params(theta=theta, group_size=group_size)
     ro, rs, _, _ = orc.cutoffs(s, p)
     res = orc.tree_soft(s, ro, rs, p)
     got = set(zip(res.cand_i.tolist(), res.cand_j.tolist()))
