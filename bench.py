@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--group-size", type=int, default=32,
+                    help="target group size of the tree walk (0: one group per leaf)")
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-targets", type=int, default=16384,
@@ -159,14 +161,14 @@ def allsum(dist, v):
 
 
 # ------------------------------------------------------------- CPU oracle ----
-def oracle_step_estimate(s, n_targets, seed=7):
+def oracle_step_estimate(s, n_targets, seed=7, group_size=32):
     """The CPU oracle on a bounded sample of the same workload.
 
     Timed: the full tree build at N (keys, sort, octree, moments), the walk for
     a random sample of targets (scaled to all N), and the Kepler drift of all
     particles.  Returns (interactions per step, seconds per step, info)."""
     from oracle import oracle as O
-    p = O.Params(theta=0.5)
+    p = O.Params(theta=0.5, group_size=group_size)
     ro, rs, _, _ = O.cutoffs(s, p)
     n = len(s["m"])
     rng = np.random.default_rng(seed)
@@ -231,7 +233,7 @@ def run_ours(args):
     s = workload(args.n, seed=1003 + 1000 * rank)
     n = len(s["m"])
     prec = P.P3T_MIXED if args.precision == "mixed" else P.P3T_FP64
-    prm = P.Params(theta=0.5, precision=prec, eta=0.01, eta0=0.001)
+    prm = P.Params(theta=0.5, precision=prec, eta=0.01, eta0=0.001, group_size=args.group_size)
     st = P.State.from_numpy(s, device=dev)
     ss = P.SoftStep(prm, st, device=local)
     stream = torch.cuda.current_stream(dev)
@@ -346,7 +348,7 @@ def run_ours(args):
         warmup=W, ms_per_step=1e3 * elapsed / K, higher_is_better=True, scaling="weak",
         vs_baseline=None, dtype="f32/f64" if prec == P.P3T_MIXED else "f64",
         data="synthetic (seeded disk)",
-        config=dict(workload=workload_name(n), n=n,
+        config=dict(workload=workload_name(n), n=n, group_size=args.group_size,
                     precision=args.precision, l2="per-step working set > L2 (inputs ~0.5 GB)",
                     parallelism="replicas only" if world > 1 else "single GPU"),
         soft_step_ms=1e3 * elapsed / K,

@@ -75,7 +75,9 @@ typedef struct {
   int32_t leaf_size; /* max particles per leaf = per target group, 1..32      */
   int32_t precision; /* P3T_FP64 or P3T_MIXED                                  */
   int32_t vran_bins; /* radial bins for v_ran; 0 = clamp(N/1000, 1, 1024)      */
-  int32_t reserved;  /* must be 0                                              */
+  int32_t group_size;/* target groups of the walk: the highest tree nodes holding
+                        <= group_size particles (0: every leaf is a group);
+                        0..64                                                 */
 } p3t_params;
 
 /* ---- particles ---------------------------------------------------------- */
@@ -168,8 +170,9 @@ int p3t_build_tree(p3t_ctx *ctx, p3t_particles *p, int update_cutoffs,
  *   a_i = -sum_j G m_j K(r_ij / r_out,ij) r_ij / r_ij^3,
  *   r_out,ij = max(r_out,i, r_out,j) (Eq. rout2), K the changeover of
  *   Sec. 2.1.1 (zero below gamma, one above 1),
- * by a tree walk per leaf: accepted nodes add monopole + quadrupole, opened
- * leaves add the changeover pair terms.  A node is opened when the
+ * by a tree walk per target group (a node holding <= group_size particles
+ * whose parent holds more, or a leaf): accepted nodes add monopole +
+ * quadrupole, opened leaves add the changeover pair terms.  A node is opened when the
  * Barnes-Hut test fails or it lies within the search reach, so all pairs with
  * r_ij < max(r_search,i, r_search,j) are evaluated as pairs and recorded as
  * neighbour candidates for p3t_neighbours.  p must be the particles the tree

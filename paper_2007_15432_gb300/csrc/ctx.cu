@@ -38,7 +38,8 @@ bool params_ok(const p3t_params *p) {
   if (!(p->theta >= 0.0) || !(p->eta > 0.0) || !(p->eta0 > 0.0)) return false;
   if (p->leaf_size < 1 || p->leaf_size > 32) return false;
   if (p->precision != P3T_FP64 && p->precision != P3T_MIXED) return false;
-  if (p->vran_bins < 0 || p->vran_bins > 4096 || p->reserved != 0) return false;
+  if (p->vran_bins < 0 || p->vran_bins > 4096) return false;
+  if (p->group_size < 0 || p->group_size > 64) return false;
   return true;
 }
 
@@ -71,6 +72,7 @@ void free_particle_buffers(p3t_ctx *c) {
   dfree(c->pre2bfs); dfree(c->node); dfree(c->mom64); dfree(c->mom32); dfree(c->nrs);
   dfree(c->node_done); dfree(c->leaf_list); dfree(c->leaf_flag); dfree(c->leaf_pos);
   dfree(c->leaf_of); dfree(c->refine);
+  dfree(c->group_list); dfree(c->group_flag); dfree(c->group_pos);
   dfree(c->walk_stack); dfree(c->cand_i); dfree(c->cand_j); dfree(c->cand_keep);
   dfree(c->deg); dfree(c->fill); dfree(c->parent); dfree(c->label); dfree(c->csize);
   dfree(c->flag); dfree(c->pos); dfree(c->singles); dfree(c->cl_off);
@@ -114,6 +116,7 @@ int reserve(p3t_ctx *c, int64_t n, int64_t cand_cap) {
   ok &= dalloc(c->node, NC) && dalloc(c->mom64, NC) && dalloc(c->mom32, NC) && dalloc(c->nrs, NC);
   ok &= dalloc(c->node_done, NC) && dalloc(c->leaf_list, NC) && dalloc(c->leaf_flag, NC);
   ok &= dalloc(c->leaf_pos, NC) && dalloc(c->leaf_of, N) && dalloc(c->refine, N);
+  ok &= dalloc(c->group_list, NC) && dalloc(c->group_flag, NC) && dalloc(c->group_pos, NC);
   ok &= dalloc(c->walk_stack, c->walk_warps * c->stack_cap);
   ok &= dalloc(c->cand_i, cand_cap) && dalloc(c->cand_j, cand_cap) && dalloc(c->cand_keep, cand_cap);
   ok &= dalloc(c->deg, N + 1) && dalloc(c->fill, N + 1);
@@ -163,6 +166,10 @@ int p3t_create(p3t_ctx **ctx, const p3t_params *p, int device) {
   bool ok = dalloc(c->status, 1) && dalloc(c->box, 4) && dalloc(c->box_bits, 6) &&
             dalloc(c->counters, 16) && dalloc(c->cl_counts, 4) && dalloc(c->hsteps, 1) &&
             dalloc(c->epart, 8192) && dalloc(c->scan_part, 1025) && dalloc(c->bh_table, 32);
+  for (int q = 0; q < 2 && ok; ++q)
+    ok = cudaStreamCreateWithFlags(&c->aux[q], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_join[q], cudaEventDisableTiming) == cudaSuccess;
+  if (ok) ok = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
   if (ok) ok = cudaMemset(c->status, 0, sizeof(DevStatus)) == cudaSuccess &&
                cudaMemset(c->counters, 0, 16 * sizeof(int64_t)) == cudaSuccess &&
                cudaMemset(c->cl_counts, 0, 4 * sizeof(int64_t)) == cudaSuccess;
@@ -183,13 +190,19 @@ void p3t_destroy(p3t_ctx *c) {
   dfree(c->status); dfree(c->box); dfree(c->box_bits); dfree(c->counters);
   dfree(c->cl_counts); dfree(c->hsteps); dfree(c->epart); dfree(c->scan_part);
   dfree(c->bh_table);
+  for (int q = 0; q < 2; ++q) {
+    if (c->aux[q]) cudaStreamDestroy(c->aux[q]);
+    if (c->ev_join[q]) cudaEventDestroy(c->ev_join[q]);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   cudaGetLastError();
   delete c;
 }
 
 int p3t_set_params(p3t_ctx *c, const p3t_params *p) {
   if (!c || !params_ok(p)) return P3T_ERR_INVALID;
-  const bool leaf_changed = p->leaf_size != c->prm.leaf_size;
+  const bool leaf_changed = p->leaf_size != c->prm.leaf_size ||
+                            p->group_size != c->prm.group_size;
   c->prm = *p;
   if (leaf_changed) c->have_tree = c->have_cand = false;
   return P3T_OK;

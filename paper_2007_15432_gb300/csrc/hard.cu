@@ -67,7 +67,8 @@ __device__ bool kepler_uv(double X[3], double V[3], double dt, double mu) {
   const double sq = sqrt(mu), isq = 1.0 / sq;
   const double sig = rv * isq;  // r0 v_r0 / sqrt(mu)
   const double tau = sq * dt;
-  double chi = tau * ir0;
+  // series of the universal Kepler equation: chi = tau/r0 - sig tau^2/(2 r0^3) + O(tau^3)
+  double chi = tau * ir0 - 0.5 * sig * tau * tau * ir0 * ir0 * ir0;
   if (alpha > 0.0) {
     const double P = 2.0 * 3.141592653589793 / (alpha * sqrt(alpha) * sq);
     if (fabs(dt) > 0.25 * P) chi = tau * alpha;
@@ -85,9 +86,9 @@ __device__ bool kepler_uv(double X[3], double V[3], double dt, double mu) {
     if (d > lim) d = lim;
     if (d < -lim) d = -lim;
     chi -= d;
-    // quadratic convergence: once a correction is below 1e-14 relative the
-    // remaining error is below rounding
-    if (fabs(d) <= 1e-14 * fabs(chi) || d == 0.0) { ok = true; break; }
+    // quadratic convergence: after a correction below 1e-10 relative the
+    // remaining error (~ its square) is below rounding
+    if (fabs(d) <= 1e-10 * fabs(chi) || d == 0.0) { ok = true; break; }
   }
   z = alpha * chi * chi;
   stumpff(z, C, S);
@@ -186,8 +187,12 @@ __device__ void hard_acc_jerk(int nc, const double *x, const double *y,
   jerk[0] = jx; jerk[1] = jy; jerk[2] = jz;
 }
 
-__device__ __forceinline__ double norm3(double a, double b, double c) {
-  return sqrt(a * a + b * b + c * c);
+// The step estimates only choose a power-of-two step: formed in FP32 from
+// components scaled by an exact power of two 2^k (j by s, a2 by s^2, a3 by
+// s^3, s = 2^e close to the step) so that nothing overflows FP32.
+__device__ __forceinline__ float norm3f(double a, double b, double c, int k) {
+  const float x = (float)ldexp(a, k), y = (float)ldexp(b, k), z = (float)ldexp(c, k);
+  return sqrtf(x * x + y * y + z * z);
 }
 
 // largest dt / 2^lvl not above dt_des, at most twice the previous step, and
@@ -246,8 +251,9 @@ __device__ void integrate_cluster(int64_t off, int nc, const int32_t *cl_mem,
     hard_acc_jerk(nc, x, y, z, vx, vy, vz, m, ro, prm, i1mg, k, a, j);
     ax[k] = a[0]; ay[k] = a[1]; az[k] = a[2];
     jx[k] = j[0]; jy[k] = j[1]; jz[k] = j[2];
-    const double an = norm3(a[0], a[1], a[2]), jn = norm3(j[0], j[1], j[2]);
-    const double dtd = jn > 0.0 ? prm.eta0 * an / jn : dt;
+    const int e = ilogb(dt);  // eta0 |a| / |j| = (eta0 |a| / |j s|) s
+    const float an = norm3f(a[0], a[1], a[2], 0), jn = norm3f(j[0], j[1], j[2], e);
+    const double dtd = jn > 0.0f ? ldexp((double)((float)prm.eta0 * an / jn), e) : dt;
     t[k] = 0;
     lvl[k] = quantise_level(dtd, dt, 0, 0, underflow);
   }
@@ -308,10 +314,12 @@ __device__ void integrate_cluster(int64_t off, int nc, const int32_t *cl_mem,
       vz[k] = pvz[k] + A2[2] * D3 * (1.0 / 6.0) + A3[2] * D4 * (1.0 / 24.0);
       ax[k] = a1[0]; ay[k] = a1[1]; az[k] = a1[2];
       jx[k] = j1[0]; jy[k] = j1[1]; jz[k] = j1[2];
-      const double an = norm3(a1[0], a1[1], a1[2]), jn = norm3(j1[0], j1[1], j1[2]);
-      const double a2n = norm3(A2e[0], A2e[1], A2e[2]), a3n = norm3(A3[0], A3[1], A3[2]);
-      const double num = an * a2n + jn * jn, den = jn * a3n + a2n * a2n;
-      const double dtd = den > 0.0 ? sqrt(prm.eta * num / den) : dt;
+      const int e = ilogb(D);  // dt = sqrt(eta num_s / den_s) s
+      const float an = norm3f(a1[0], a1[1], a1[2], 0), jn = norm3f(j1[0], j1[1], j1[2], e);
+      const float a2n = norm3f(A2e[0], A2e[1], A2e[2], 2 * e);
+      const float a3n = norm3f(A3[0], A3[1], A3[2], 3 * e);
+      const float num = an * a2n + jn * jn, den = jn * a3n + a2n * a2n;
+      const double dtd = den > 0.0f ? ldexp((double)sqrtf((float)prm.eta * num / den), e) : dt;
       t[k] = tn;
       lvl[k] = quantise_level(dtd, dt, lvl[k], tn, underflow);
       ++steps;
@@ -488,8 +496,6 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
   const int64_t n = p->n;
   const int64_t maxb = (int64_t)c->num_sms * P3T_NSM_BLOCKS;
   const double mu = c->prm.G * c->prm.m_star;
-  k_kepler<<<(unsigned)p3t_grid(n, 128, maxb), 128, 0, s>>>(&cl->counts[0], cl->singles, *p,
-                                                             dt, mu, c->status);
   HWork w;
   const int64_t cap = c->cap;
   double *b = c->hw;
@@ -502,13 +508,24 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
   unsigned long long *steps = n_steps ? reinterpret_cast<unsigned long long *>(n_steps)
                                       : c->hsteps;
   k_zero_u64<<<1, 1, 0, s>>>(steps);
-  // at most n/2 clusters: a thread per small cluster, a warp per large one
+  // Kepler drift, small clusters and large clusters touch disjoint particles:
+  // run them on three streams forked from and joined back to the caller's
+  P3T_CUDA_TRY(cudaEventRecord(c->ev_fork, s));
+  P3T_CUDA_TRY(cudaStreamWaitEvent(c->aux[0], c->ev_fork, 0));
+  P3T_CUDA_TRY(cudaStreamWaitEvent(c->aux[1], c->ev_fork, 0));
+  // at most n/2 clusters: 4 lanes per small cluster, a warp per large one
   const int64_t ncl_max = (n / 2) > 0 ? n / 2 : 1;
   // 32-thread blocks (8 clusters each) spread consecutive clusters over all SMs
-  k_hermite_small<<<(unsigned)p3t_grid(ncl_max * 4, 32, 4 * maxb), 32, 0, s>>>(
+  k_hermite_small<<<(unsigned)p3t_grid(ncl_max * 4, 32, 4 * maxb), 32, 0, c->aux[0]>>>(
       &cl->counts[1], cl->cl_off, cl->cl_mem, *p, w, c->prm, dt, steps, c->status);
-  k_hermite<<<(unsigned)p3t_grid(ncl_max * 32, 128, maxb), 128, 0, s>>>(
+  k_hermite<<<(unsigned)p3t_grid(ncl_max * 32, 128, maxb), 128, 0, c->aux[1]>>>(
       &cl->counts[1], cl->cl_off, cl->cl_mem, *p, w, c->prm, dt, steps, c->status);
+  k_kepler<<<(unsigned)p3t_grid(n, 128, maxb), 128, 0, s>>>(&cl->counts[0], cl->singles, *p,
+                                                             dt, mu, c->status);
+  P3T_CUDA_TRY(cudaEventRecord(c->ev_join[0], c->aux[0]));
+  P3T_CUDA_TRY(cudaEventRecord(c->ev_join[1], c->aux[1]));
+  P3T_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[0], 0));
+  P3T_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[1], 0));
   p3t_note_launches(4);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }

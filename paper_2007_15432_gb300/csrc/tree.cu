@@ -372,6 +372,37 @@ __global__ void k_leaf_list(const int64_t *d_nnode, int64_t node_cap,
     if (leaf_flag[p]) leaf_list[leaf_pos[p]] = pre2bfs[p];
 }
 
+// target groups: a node holding <= gs particles (or a leaf) whose parent
+// holds more (or the root); flags indexed by preorder id for key order
+__global__ void k_group_flags(const int64_t *d_nnode, int64_t node_cap,
+                              const TreeNode *node, const int32_t *bfs2pre, int gs,
+                              int32_t *group_flag) {
+  const int64_t nn = min(*d_nnode, node_cap);
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nn;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const TreeNode &nd = node[b];
+    const bool small = nd.count <= gs || nd.nchild == 0;
+    const bool top = nd.parent < 0 || node[nd.parent].count > gs;
+    group_flag[bfs2pre[b]] = (small && top) ? 1 : 0;
+  }
+}
+
+// group list in key order, and every member's group
+__global__ void k_group_list(const int64_t *d_nnode, int64_t node_cap,
+                             const int32_t *group_flag, const int64_t *group_pos,
+                             const int32_t *pre2bfs, const TreeNode *node,
+                             int32_t *group_list, int32_t *group_of) {
+  const int64_t nn = min(*d_nnode, node_cap);
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nn;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    if (!group_flag[p]) continue;
+    const int32_t b = pre2bfs[p];
+    group_list[group_pos[p]] = b;
+    const TreeNode &nd = node[b];
+    for (int32_t i = nd.first; i < nd.first + nd.count; ++i) group_of[i] = b;
+  }
+}
+
 __device__ __forceinline__ void finish_node(TreeNode *nd, Mom64 *m64, Mom32 *m32,
                                             double rsmax, double u, int64_t b,
                                             const Mom64 &mm) {
@@ -395,7 +426,7 @@ __global__ void k_moments(const int64_t *d_nleaf, const int32_t *leaf_list,
                           TreeNode *node, Mom64 *m64, Mom32 *m32, double *nrs,
                           int32_t *node_done, const double *sx, const double *sy,
                           const double *sz, const double *sm, const double *srs,
-                          const int32_t *sq, const double *box, int32_t *leaf_of) {
+                          const int32_t *sq, const double *box) {
   const int64_t nleaf = *d_nleaf;
   const double u = ldexp(box[3], -P3T_BITS);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nleaf;
@@ -407,7 +438,6 @@ __global__ void k_moments(const int64_t *d_nleaf, const int32_t *leaf_list,
     double M = 0.0, sxm = 0.0, sym = 0.0, szm = 0.0, rsmax = 0.0;
     int32_t qlo[3] = {P3T_QMAX, P3T_QMAX, P3T_QMAX}, qhi[3] = {-1, -1, -1};
     for (int32_t i = f; i < f + c; ++i) {
-      leaf_of[i] = (int32_t)b;
       M += sm[i]; sxm += sm[i] * sx[i]; sym += sm[i] * sy[i]; szm += sm[i] * sz[i];
       rsmax = fmax(rsmax, srs[i]);
       for (int a = 0; a < 3; ++a) { qlo[a] = min(qlo[a], sq[3 * i + a]); qhi[a] = max(qhi[a], sq[3 * i + a]); }
@@ -565,11 +595,19 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
                                               c->leaf_pos, c->pre2bfs, c->leaf_list);
   k_moments<<<(unsigned)gn, 128, 0, s>>>(&cnt[2], c->leaf_list, c->node, c->mom64, c->mom32,
                                          c->nrs, c->node_done, c->sx, c->sy, c->sz, c->sm,
-                                         c->srs, c->sq, c->box, c->leaf_of);
+                                         c->srs, c->sq, c->box);
+  k_group_flags<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->node, c->bfs2pre,
+                                                c->prm.group_size, c->group_flag);
+  rc = p3t_scan_i32_to_i64(c->group_flag, c->group_pos, &cnt[3], c->node_cap, &cnt[15],
+                           c->scan_part, s);
+  if (rc) return rc;
+  k_group_list<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->group_flag,
+                                               c->group_pos, c->pre2bfs, c->node,
+                                               c->group_list, c->leaf_of);
   // own kernels here (the scans and sorts count themselves): box 3, keys, n,
   // gather, lcp, levels, clamp, nodes_pre, pre2bfs, nodes_bfs, parents,
-  // leaf_list, moments
-  p3t_note_launches(15);
+  // leaf_list, moments, group_flags, group_list
+  p3t_note_launches(17);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 

@@ -1,12 +1,13 @@
 // Row a4 of the soft step: the changeover tree walk (Eq. softforce).
 //
-// One warp per target group (a leaf of <= 16 particles; larger level-21 leaves
-// are taken 16 targets at a time).  Two lanes per target, each taking every
-// other entry of a batch of 32 list entries.  The walk pops up to 32 nodes at
-// a time from a per-warp stack, decides opening for all of them at once on
-// the integer grid, and compacts accepted nodes, opened leaves and children
-// with warp ballots / scans into shared-memory lists that are evaluated in
-// batches of 32.
+// One warp per target group (the highest tree node holding <= group_size
+// particles, or a leaf), one lane per target, 32 targets per walk (larger
+// groups are taken 32 targets at a time).  The walk pops up to 32 nodes at a
+// time from a per-warp stack, decides opening for all of them at once on the
+// integer grid, and compacts accepted nodes, opened leaves and children with
+// warp ballots / scans into shared-memory lists.  Each batch of 32 list
+// entries is staged into shared memory once (one coalesced load per lane)
+// and then read by every lane as a broadcast.
 //
 // Mixed path: positions are float-float (hi + lo) pairs, so a relative
 // coordinate (x_i,hi - x_j,hi) + (x_i,lo - x_j,lo) carries the accuracy of an
@@ -84,7 +85,7 @@ __device__ __forceinline__ void two_sum(float &hi, float &lo, float b) {
   lo += err;
 }
 
-// ---- per-target state ----------------------------------------------------
+// ---- per-target state (one lane per target) ---------------------------------
 template <bool MIXED> struct Target;
 
 template <> struct Target<true> {
@@ -137,16 +138,20 @@ __device__ __forceinline__ void record_candidate(const WalkArgs &a, int32_t i,
   }
 }
 
+// per-warp staging area for one batch of 32 entries
+constexpr int kStageBytes = 32 * 96;
+struct StagePP32 { float4 A[32]; float4 B[32]; float rs[32]; int32_t idx[32]; };
+struct StagePP64 { double x[32], y[32], z[32], m[32], ro[32], rs[32]; int32_t idx[32]; };
+static_assert(sizeof(StagePP32) <= kStageBytes && sizeof(StagePP64) <= kStageBytes &&
+              sizeof(Mom32) * 32 <= kStageBytes && sizeof(Mom64) * 32 <= kStageBytes,
+              "stage area");
+
 // ---- particle-particle batch ----------------------------------------------
-__device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<true> &t,
-                                        const int32_t *list, int nsrc, int h,
+// one changeover pair term in FP32 on float-float relative coordinates
+__device__ __forceinline__ void pp_term(const WalkArgs &a, Target<true> &t,
+                                        const float4 A, const float4 B, float rss,
+                                        int32_t j, float &bx, float &by, float &bz,
                                         unsigned &npp) {
-  float bx = 0.f, by = 0.f, bz = 0.f;
-#pragma unroll 2
-  for (int s = h; s < nsrc; s += 2) {
-    const int32_t j = list[s];
-    const float4 A = __ldg(&a.spA[j]);
-    const float4 B = __ldg(&a.spB[j]);
     const float dx = (t.xh - A.x) + (t.xl - B.x);
     const float dy = (t.yh - A.y) + (t.yl - B.y);
     const float dz = (t.zh - A.z) + (t.zl - B.z);
@@ -162,45 +167,90 @@ __device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<true> &t,
     by = fmaf(-f, dy, by);
     bz = fmaf(-f, dz, bz);
     t.tabs = fmaf(f, r, t.tabs);
-    const float rsj = fmaxf(t.rs, __ldg(&a.srs32[j]));
-    if (t.valid && j != t.self && r2 < rsj * rsj * kCandMargin) record_candidate(a, t.self, j);
-    npp += (t.valid && j != t.self) ? 1u : 0u;
-  }
-  t.fold(bx, by, bz);
+    const float rsj = fmaxf(t.rs, rss);
+    if (r2 < rsj * rsj * kCandMargin && t.valid) {
+      if (j != t.self) record_candidate(a, t.self, j);
+      else --npp;  // the target itself is not a pair
+    }
 }
 
-__device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<false> &t,
-                                        const int32_t *list, int nsrc, int h,
+template <int TPL>
+__device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<true> (&t)[TPL],
+                                        const int32_t *list, int nsrc, void *stage,
                                         unsigned &npp) {
-  for (int s = h; s < nsrc; s += 2) {
-    const int32_t j = list[s];
-    const double dx = t.x - a.sx[j], dy = t.y - a.sy[j], dz = t.z - a.sz[j];
+  StagePP32 &S = *reinterpret_cast<StagePP32 *>(stage);
+  const int lane = threadIdx.x & 31;
+  if (lane < nsrc) {
+    const int32_t j = list[lane];
+    S.A[lane] = __ldg(&a.spA[j]);
+    S.B[lane] = __ldg(&a.spB[j]);
+    S.rs[lane] = __ldg(&a.srs32[j]);
+    S.idx[lane] = j;
+  }
+  __syncwarp();
+  float bx[TPL], by[TPL], bz[TPL];
+#pragma unroll
+  for (int q = 0; q < TPL; ++q) {
+    bx[q] = by[q] = bz[q] = 0.f;
+    npp += t[q].valid ? (unsigned)nsrc : 0u;
+  }
+#pragma unroll 2
+  for (int s = 0; s < nsrc; ++s) {
+    const float4 A = S.A[s];
+    const float4 B = S.B[s];
+    const float rss = S.rs[s];
+    const int32_t j = S.idx[s];
+#pragma unroll
+    for (int q = 0; q < TPL; ++q) pp_term(a, t[q], A, B, rss, j, bx[q], by[q], bz[q], npp);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < TPL; ++q) t[q].fold(bx[q], by[q], bz[q]);
+}
+
+template <int TPL>
+__device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<false> (&tt)[TPL],
+                                        const int32_t *list, int nsrc, void *stage,
+                                        unsigned &npp) {
+  static_assert(TPL == 1, "the FP64 walk takes one target per lane");
+  Target<false> &t = tt[0];
+  StagePP64 &S = *reinterpret_cast<StagePP64 *>(stage);
+  const int lane = threadIdx.x & 31;
+  if (lane < nsrc) {
+    const int32_t j = list[lane];
+    S.x[lane] = a.sx[j]; S.y[lane] = a.sy[j]; S.z[lane] = a.sz[j];
+    S.m[lane] = a.sm[j]; S.ro[lane] = a.sro[j]; S.rs[lane] = a.srs[j];
+    S.idx[lane] = j;
+  }
+  __syncwarp();
+  npp += t.valid ? (unsigned)nsrc : 0u;
+  for (int s = 0; s < nsrc; ++s) {
+    const double dx = t.x - S.x[s], dy = t.y - S.y[s], dz = t.z - S.z[s];
     const double r2 = dx * dx + dy * dy + dz * dz;
     const double rinv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
     const double r = r2 * rinv;
-    const double y = r / fmax(t.ro, a.sro[j]);
+    const double y = r / fmax(t.ro, S.ro[s]);
     double x = (y - a.gamma) / (1.0 - a.gamma);
     x = x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x);
     const double x2 = x * x;
     const double K = (x2 * x2) * (((-20.0 * x + 70.0) * x - 84.0) * x + 35.0);
-    const double f = a.sm[j] * K * (rinv * rinv * rinv);
+    const double f = S.m[s] * K * (rinv * rinv * rinv);
     t.ax -= f * dx; t.ay -= f * dy; t.az -= f * dz;
-    const double rsj = fmax(t.rs, a.srs[j]);
-    if (t.valid && j != t.self && r2 < rsj * rsj) record_candidate(a, t.self, j);
-    npp += (t.valid && j != t.self) ? 1u : 0u;
+    const double rsj = fmax(t.rs, S.rs[s]);
+    if (r2 < rsj * rsj && t.valid) {
+      const int32_t j = S.idx[s];
+      if (j != t.self) record_candidate(a, t.self, j);
+      else --npp;
+    }
   }
+  __syncwarp();
 }
 
 // ---- particle-node batch (monopole + traceless quadrupole) ---------------
 // a += -M r/r^3 + Q.r/r^5 - (5/2)(r.Q.r) r/r^7, r = x_i - com
-__device__ __forceinline__ void eval_nodes(const WalkArgs &a, Target<true> &t,
-                                           const int32_t *list, int nnd, int h,
-                                           unsigned &npn) {
-  float bx = 0.f, by = 0.f, bz = 0.f;
-#pragma unroll 2
-  for (int s = h; s < nnd; s += 2) {
-    const Mom32 *m = &a.mom32[list[s]];
-    const float4 hi = __ldg(&m->hi), lo = __ldg(&m->lo), q0 = __ldg(&m->q0), q1 = __ldg(&m->q1);
+__device__ __forceinline__ void node_term(Target<true> &t, const float4 hi, const float4 lo,
+                                          const float4 q0, const float4 q1, float &bx,
+                                          float &by, float &bz) {
     const float dx = (t.xh - hi.x) + (t.xl - lo.x);
     const float dy = (t.yh - hi.y) + (t.yl - lo.y);
     const float dz = (t.zh - hi.z) + (t.zl - lo.z);
@@ -218,16 +268,50 @@ __device__ __forceinline__ void eval_nodes(const WalkArgs &a, Target<true> &t,
     by = fmaf(c, dy, fmaf(qy, rinv5, by));
     bz = fmaf(c, dz, fmaf(qz, rinv5, bz));
     t.tabs = fmaf(hi.w, rinv2, t.tabs);
-    npn += t.valid ? 1u : 0u;
-  }
-  t.fold(bx, by, bz);
 }
 
-__device__ __forceinline__ void eval_nodes(const WalkArgs &a, Target<false> &t,
-                                           const int32_t *list, int nnd, int h,
+template <int TPL>
+__device__ __forceinline__ void eval_nodes(const WalkArgs &a, Target<true> (&t)[TPL],
+                                           const int32_t *list, int nnd, void *stage,
                                            unsigned &npn) {
-  for (int s = h; s < nnd; s += 2) {
-    const Mom64 &m = a.mom64[list[s]];
+  Mom32 *S = reinterpret_cast<Mom32 *>(stage);
+  const int lane = threadIdx.x & 31;
+  if (lane < nnd) {
+    const Mom32 *m = &a.mom32[list[lane]];
+    S[lane].hi = __ldg(&m->hi); S[lane].lo = __ldg(&m->lo);
+    S[lane].q0 = __ldg(&m->q0); S[lane].q1 = __ldg(&m->q1);
+  }
+  __syncwarp();
+  float bx[TPL], by[TPL], bz[TPL];
+#pragma unroll
+  for (int q = 0; q < TPL; ++q) {
+    bx[q] = by[q] = bz[q] = 0.f;
+    npn += t[q].valid ? (unsigned)nnd : 0u;
+  }
+#pragma unroll 2
+  for (int s = 0; s < nnd; ++s) {
+    const float4 hi = S[s].hi, lo = S[s].lo, q0 = S[s].q0, q1 = S[s].q1;
+#pragma unroll
+    for (int q = 0; q < TPL; ++q) node_term(t[q], hi, lo, q0, q1, bx[q], by[q], bz[q]);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < TPL; ++q) t[q].fold(bx[q], by[q], bz[q]);
+}
+
+template <int TPL>
+__device__ __forceinline__ void eval_nodes(const WalkArgs &a, Target<false> (&tt)[TPL],
+                                           const int32_t *list, int nnd, void *stage,
+                                           unsigned &npn) {
+  static_assert(TPL == 1, "the FP64 walk takes one target per lane");
+  Target<false> &t = tt[0];
+  Mom64 *S = reinterpret_cast<Mom64 *>(stage);
+  const int lane = threadIdx.x & 31;
+  if (lane < nnd) S[lane] = a.mom64[list[lane]];
+  __syncwarp();
+  npn += t.valid ? (unsigned)nnd : 0u;
+  for (int s = 0; s < nnd; ++s) {
+    const Mom64 &m = S[s];
     const double dx = t.x - m.cx, dy = t.y - m.cy, dz = t.z - m.cz;
     const double r2 = dx * dx + dy * dy + dz * dz;
     const double rinv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
@@ -240,8 +324,8 @@ __device__ __forceinline__ void eval_nodes(const WalkArgs &a, Target<false> &t,
     t.ax += c * dx + qx * rinv5;
     t.ay += c * dy + qy * rinv5;
     t.az += c * dz + qz * rinv5;
-    npn += t.valid ? 1u : 0u;
   }
+  __syncwarp();
 }
 
 template <bool MIXED>
@@ -249,37 +333,27 @@ __device__ __forceinline__ void write_result(const WalkArgs &a, Target<MIXED> &t
 
 template <>
 __device__ __forceinline__ void write_result<true>(const WalkArgs &a, Target<true> &t) {
-  double x = (double)t.ahx + (double)t.alx;
-  double y = (double)t.ahy + (double)t.aly;
-  double z = (double)t.ahz + (double)t.alz;
-  x += __shfl_xor_sync(0xffffffffu, x, 16);
-  y += __shfl_xor_sync(0xffffffffu, y, 16);
-  z += __shfl_xor_sync(0xffffffffu, z, 16);
-  const float tabs = t.tabs + __shfl_xor_sync(0xffffffffu, t.tabs, 16);
-  if (t.valid && (threadIdx.x & 16) == 0) {
-    const int32_t i = a.idx[t.self];
-    a.ax[i] = a.G * x; a.ay[i] = a.G * y; a.az[i] = a.G * z;
-    // FP32 terms carry ~1e-7 relative error each; where they cancel to a sum
-    // much smaller than their magnitudes the target is redone in FP64
-    const double amag = sqrt(x * x + y * y + z * z);
-    if ((double)tabs > (double)a.refine_cf * amag) {
-      const unsigned long long slot = atomicAdd(a.refine_count, 1ull);
-      if (slot < (unsigned long long)a.refine_cap) a.refine[slot] = t.self;
-    }
+  if (!t.valid) return;
+  const double x = (double)t.ahx + (double)t.alx;
+  const double y = (double)t.ahy + (double)t.aly;
+  const double z = (double)t.ahz + (double)t.alz;
+  const int32_t i = a.idx[t.self];
+  a.ax[i] = a.G * x; a.ay[i] = a.G * y; a.az[i] = a.G * z;
+  // FP32 terms carry ~1e-7 relative error each; where they cancel to a sum
+  // much smaller than their magnitudes the target is redone in FP64
+  const float amag = sqrtf((float)(x * x + y * y + z * z));
+  if (t.tabs > a.refine_cf * amag) {
+    const unsigned long long slot = atomicAdd(a.refine_count, 1ull);
+    if (slot < (unsigned long long)a.refine_cap) a.refine[slot] = t.self;
   }
 }
 
 template <>
 __device__ __forceinline__ void write_result<false>(const WalkArgs &a, Target<false> &t) {
-  double x = t.ax + __shfl_xor_sync(0xffffffffu, t.ax, 16);
-  double y = t.ay + __shfl_xor_sync(0xffffffffu, t.ay, 16);
-  double z = t.az + __shfl_xor_sync(0xffffffffu, t.az, 16);
-  if (t.valid && (threadIdx.x & 16) == 0) {
-    const int32_t i = a.idx[t.self];
-    a.ax[i] = a.G * x; a.ay[i] = a.G * y; a.az[i] = a.G * z;
-  }
+  if (!t.valid) return;
+  const int32_t i = a.idx[t.self];
+  a.ax[i] = a.G * t.ax; a.ay[i] = a.G * t.ay; a.az[i] = a.G * t.az;
 }
-
 
 // ---- the traversal, shared by the group walk and the FP64 refinement --------
 // Pops up to 32 nodes per round, decides opening on the integer grid, and
@@ -418,14 +492,15 @@ __device__ bool traverse(const WalkArgs &a, const GroupBox &gb, int32_t *stack,
   return true;
 }
 
-// 16 targets of a group, two lanes per target (h = lane / 16)
-template <bool MIXED> struct GroupEval {
+// up to 32 x TPL targets of a group, TPL per lane, batches staged in shared
+// memory (every staged entry is used by all the lane's targets)
+template <bool MIXED, int TPL> struct GroupEval {
   const WalkArgs &a;
-  Target<MIXED> &t;
-  int h;
+  Target<MIXED> (&t)[TPL];
+  void *stage;
   unsigned &npp, &npn;
-  __device__ void nodes(const int32_t *list, int n) { eval_nodes(a, t, list, n, h, npn); }
-  __device__ void pp(const int32_t *list, int n) { eval_pp(a, t, list, n, h, npp); }
+  __device__ void nodes(const int32_t *list, int n) { eval_nodes<TPL>(a, t, list, n, stage, npn); }
+  __device__ void pp(const int32_t *list, int n) { eval_pp<TPL>(a, t, list, n, stage, npp); }
 };
 
 // one target, all 32 lanes, FP64 (the refinement of ill-conditioned targets)
@@ -468,17 +543,17 @@ struct RefineEval {
   }
 };
 
-template <bool MIXED>
+template <bool MIXED, int TPL>
 __global__ void __launch_bounds__(kWarps * 32) k_walk(const WalkArgs a) {
   __shared__ int32_t s_pp[kWarps][kPPCap];
   __shared__ int32_t s_nd[kWarps][kNDCap];
   __shared__ int32_t s_big[kWarps][kBigCap];
+  __shared__ __align__(16) unsigned char s_stage[kWarps][kStageBytes];
   __shared__ int64_t s_bh[P3T_BITS + 1];
   if (threadIdx.x <= P3T_BITS) s_bh[threadIdx.x] = a.bh[threadIdx.x];
   __syncthreads();
 
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int h = lane >> 4, tl = lane & 15;
   int32_t *stack = a.stack + ((int64_t)blockIdx.x * kWarps + w) * a.stack_cap;
   const int64_t nleaf = *a.d_nleaf;
   const int64_t round_limit = *a.d_nnode + 2;  // a node is pushed at most once per walk
@@ -495,12 +570,19 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(const WalkArgs a) {
     gb.load(G);
     const int32_t gfirst = G.first, gcount = G.count;
     bool ok = true;
-    for (int32_t tb = gfirst; tb < gfirst + gcount && ok; tb += 16) {
-      Target<MIXED> t;
-      t.load(a, tb + tl, tb + tl < gfirst + gcount);
-      GroupEval<MIXED> ev{a, t, h, npp, npn};
+    for (int32_t tb = gfirst; tb < gfirst + gcount && ok; tb += 32 * TPL) {
+      Target<MIXED> t[TPL];
+#pragma unroll
+      for (int q = 0; q < TPL; ++q) {
+        const int32_t ti = tb + q * 32 + lane;
+        t[q].load(a, ti, ti < gfirst + gcount);
+      }
+      GroupEval<MIXED, TPL> ev{a, t, s_stage[w], npp, npn};
       ok = traverse(a, gb, stack, s_pp[w], s_nd[w], s_big[w], s_bh, round_limit, ev);
-      if (ok) write_result<MIXED>(a, t);
+      if (ok) {
+#pragma unroll
+        for (int q = 0; q < TPL; ++q) write_result<MIXED>(a, t[q]);
+      }
     }
     if (!ok) break;
   }
@@ -577,7 +659,7 @@ int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
                        cudaStream_t s) {
   WalkArgs a;
   a.node = c->node; a.mom64 = c->mom64; a.mom32 = c->mom32;
-  a.leaf_list = c->leaf_list; a.d_nleaf = &c->counters[2]; a.d_nnode = &c->counters[3];
+  a.leaf_list = c->group_list; a.d_nleaf = &c->counters[15]; a.d_nnode = &c->counters[3];
   a.sx = c->sx; a.sy = c->sy; a.sz = c->sz; a.sm = c->sm; a.sro = c->sro; a.srs = c->srs;
   a.spA = c->spA; a.spB = c->spB; a.srs32 = c->srs32;
   a.idx = c->idx;
@@ -608,10 +690,13 @@ int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
   }
   k_walk_prep<<<1, 1, 0, s>>>(a.cursor, a.cand_count, a.counts, a.refine_count);
   const unsigned blocks = (unsigned)(c->num_sms * p3t_walk_blocks_per_sm());
-  if (c->prm.precision == P3T_MIXED)
-    k_walk<true><<<blocks, kWarps * 32, 0, s>>>(a);
-  else
-    k_walk<false><<<blocks, kWarps * 32, 0, s>>>(a);
+  if (c->prm.precision == P3T_MIXED) {
+    // one target per lane: two per lane (a 64-target group walked once) was
+    // measured slower than two walks of 32 (register pressure, longer chains)
+    k_walk<true, 1><<<blocks, kWarps * 32, 0, s>>>(a);
+  } else {
+    k_walk<false, 1><<<blocks, kWarps * 32, 0, s>>>(a);
+  }
   k_walk_post<<<1, 1, 0, s>>>(c->counters, c->cand_cap, c->cap, c->status);
   if (c->prm.precision == P3T_MIXED) k_refine<<<blocks, kWarps * 32, 0, s>>>(a);
   p3t_note_launches(c->prm.precision == P3T_MIXED ? 4 : 3);

@@ -63,10 +63,12 @@ def test_direct_theta0_config1(P3T, precision):
     P3T.p3t_destroy(ctx)
 
 
-@pytest.mark.parametrize("n,precision", [(20000, 0), (20000, 1), (2999, 0), (2999, 1)])
-def test_tree_theta_half(P3T, n, precision):
+@pytest.mark.parametrize("n,precision,group_size", [
+    (20000, 0, 0), (20000, 1, 0), (2999, 0, 0), (2999, 1, 0),
+    (20000, 0, 32), (20000, 1, 32), (2999, 1, 64), (5000, 0, 64)])
+def test_tree_theta_half(P3T, n, precision, group_size):
     s = disks.equal_mass_ring(n=n, seed=1002 + n)
-    P = P3T.Params(theta=0.5, precision=precision)
+    P = P3T.Params(theta=0.5, precision=precision, group_size=group_size)
     op = oracle_params(P)
     ro, rs, _, _ = O.cutoffs(s, op)
     ref = O.tree_soft(s, ro, rs, op)
@@ -81,10 +83,11 @@ def test_tree_theta_half(P3T, n, precision):
     P3T.p3t_destroy(ctx)
 
 
-def test_wide_power_law_mixed(P3T):
+@pytest.mark.parametrize("group_size", [0, 32])
+def test_wide_power_law_mixed(P3T, group_size):
     """Wide 1-10 au power-law disk with protoplanets (cut-offs spanning decades)."""
     s = disks.wide_power_law(n=30000, seed=1003)
-    P = P3T.Params(theta=0.5, precision=1)
+    P = P3T.Params(theta=0.5, precision=1, group_size=group_size)
     op = oracle_params(P)
     ro, rs, _, _ = O.cutoffs(s, op)
     ref = O.tree_soft(s, ro, rs, op)
@@ -119,10 +122,10 @@ def _neighbours(P3T, ctx, st, n, cap=None):
     return nb_off, nb_idx, cl
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_neighbours_and_clusters_bit_exact(P3T, precision):
+@pytest.mark.parametrize("precision,group_size", [(0, 0), (1, 0), (1, 32)])
+def test_neighbours_and_clusters_bit_exact(P3T, precision, group_size):
     s = disks.equal_mass_narrow(n=4000, seed=1001)
-    P = P3T.Params(theta=0.5, precision=precision)
+    P = P3T.Params(theta=0.5, precision=precision, group_size=group_size)
     op = oracle_params(P)
     ro, rs, _, _ = O.cutoffs(s, op)
     ref = O.tree_soft(s, ro, rs, op)
