@@ -164,7 +164,7 @@ int p3t_create(p3t_ctx **ctx, const p3t_params *p, int device) {
     return P3T_ERR_CUDA;
   }
   bool ok = dalloc(c->status, 1) && dalloc(c->box, 4) && dalloc(c->box_bits, 6) &&
-            dalloc(c->counters, 16) && dalloc(c->cl_counts, 4) && dalloc(c->hsteps, 1) &&
+            dalloc(c->counters, 16) && dalloc(c->cl_counts, 4) && dalloc(c->hsteps, 1) && dalloc(c->hcursor, 1) &&
             dalloc(c->epart, 8192) && dalloc(c->scan_part, 1025) && dalloc(c->bh_table, 32);
   for (int q = 0; q < 2 && ok; ++q)
     ok = cudaStreamCreateWithFlags(&c->aux[q], cudaStreamNonBlocking) == cudaSuccess &&
@@ -188,7 +188,8 @@ void p3t_destroy(p3t_ctx *c) {
   cudaDeviceSynchronize();
   free_particle_buffers(c);
   dfree(c->status); dfree(c->box); dfree(c->box_bits); dfree(c->counters);
-  dfree(c->cl_counts); dfree(c->hsteps); dfree(c->epart); dfree(c->scan_part);
+  dfree(c->cl_counts); dfree(c->hsteps); dfree(c->hcursor); dfree(c->epart);
+  dfree(c->scan_part);
   dfree(c->bh_table);
   for (int q = 0; q < 2; ++q) {
     if (c->aux[q]) cudaStreamDestroy(c->aux[q]);

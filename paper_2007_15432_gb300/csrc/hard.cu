@@ -334,35 +334,254 @@ __device__ void integrate_cluster(int64_t off, int nc, const int32_t *cl_mem,
   __syncwarp(mask);
 }
 
-constexpr int kSmallCluster = 4;  // clusters up to this size: a 4-lane group each
+// ---- clusters of up to kHMax members: one 128-thread block per cluster ------
+// Work items (member components, or (active member, source) terms) are dealt
+// round-robin over the block's four warps, so one cluster keeps the FP64
+// pipes of all four SM sub-partitions busy: on this part a warp instruction
+// of FP64 occupies its sub-partition's pipe for ~64 cycles, and a cluster's
+// block steps are a serial chain.  Each active member's force is the sum, in
+// the fixed order star term first then sources in ascending index, of terms
+// computed in parallel.
+constexpr int kHB = 128;
+constexpr int kHMax = 128;
 
-// clusters of <= kSmallCluster members: a group of 4 lanes each, eight per
-// warp (most clusters are pairs: a whole warp per pair would leave 30 of 32
-// FP64 lanes idle, a single thread per pair would serialise its members)
-__global__ void k_hermite_small(const int64_t *d_ncl, const int64_t *cl_off,
-                                const int32_t *cl_mem, p3t_particles p, HWork w,
-                                p3t_params prm, double dt,
-                                unsigned long long *steps_out, DevStatus *st) {
-  const int64_t ncl = *d_ncl;
-  const int lane = threadIdx.x & 3;
-  const unsigned mask = 0xfu << (threadIdx.x & 28);
-  unsigned long long steps = 0;
-  bool underflow = false;
-  const int64_t g0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 2;
-  const int64_t ng = ((int64_t)gridDim.x * blockDim.x) >> 2;
-  for (int64_t c = g0; c < ncl; c += ng) {
-    const int64_t off = cl_off[c];
-    const int nc = (int)(cl_off[c + 1] - off);
-    if (nc > kSmallCluster) continue;
-    integrate_cluster<4>(off, nc, cl_mem, p, w, prm, dt, lane, mask, steps, underflow, st);
+struct HShared {
+  double x[3][kHMax], v[3][kHMax], a[3][kHMax], j[3][kHMax];
+  double p[3][kHMax], pv[3][kHMax];
+  double a1[3][kHMax], j1[3][kHMax], a2e[3][kHMax], a3[3][kHMax];
+  double m[kHMax], iro[kHMax];
+  double T[kHMax + 1][6];  // one batch: B members x (nc + 1) terms, at most kHMax + 1
+  int64_t t[kHMax];
+  int32_t lvl[kHMax], act[kHMax];
+  int64_t red[2][4];
+  int32_t wcount[4];
+  int64_t cluster;
+  int nact;
+};
+
+// term of source j (j == nc: the star) on member k, from arrays X, V
+__device__ __forceinline__ void hard_term(const HShared &S, const double (*X)[kHMax],
+                                          const double (*V)[kHMax], int nc, int k, int j,
+                                          const p3t_params &prm, double i1mg, double out[6]) {
+  for (int q = 0; q < 6; ++q) out[q] = 0.0;
+  const double xk = X[0][k], yk = X[1][k], zk = X[2][k];
+  const double vxk = V[0][k], vyk = V[1][k], vzk = V[2][k];
+  if (j == nc) {
+    const double r2 = xk * xk + yk * yk + zk * zk;
+    const double rinv = 1.0 / sqrt(r2);
+    const double rinv2 = rinv * rinv;
+    const double f = prm.G * prm.m_star * (rinv2 * rinv);
+    const double rv = xk * vxk + yk * vyk + zk * vzk;
+    out[0] = f * xk; out[1] = f * yk; out[2] = f * zk;
+    const double c = 3.0 * rv * rinv2;
+    out[3] = f * (vxk - c * xk);
+    out[4] = f * (vyk - c * yk);
+    out[5] = f * (vzk - c * zk);
+    return;
   }
-  if (underflow) dev_fail(st, P3T_ERR_DT_UNDERFLOW, 62, 0);
-  __syncwarp();
-  for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(0xffffffffu, steps, o);
-  if ((threadIdx.x & 31) == 0 && steps_out && steps) atomicAdd(steps_out, steps);
+  if (j == k) return;
+  const double rx = xk - X[0][j], ry = yk - X[1][j], rz = zk - X[2][j];
+  const double ux = vxk - V[0][j], uy = vyk - V[1][j], uz = vzk - V[2][j];
+  const double r2 = rx * rx + ry * ry + rz * rz;
+  if (r2 == 0.0) return;
+  const double rinv = 1.0 / sqrt(r2);
+  const double r = r2 * rinv;
+  const double irot = S.iro[k] < S.iro[j] ? S.iro[k] : S.iro[j];
+  const double yv = r * irot;
+  if (yv >= 1.0) return;
+  double w = 1.0, dK = 0.0;
+  if (yv > prm.gamma) {
+    const double xs = (yv - prm.gamma) * i1mg;
+    const double x2 = xs * xs, x3 = x2 * xs, x4 = x2 * x2, u = 1.0 - xs;
+    w = 1.0 - x4 * (35.0 - 84.0 * xs + 70.0 * x2 - 20.0 * x3);
+    dK = 140.0 * x3 * (u * u * u) * i1mg;
+  }
+  const double rinv2 = rinv * rinv;
+  const double g3 = prm.G * S.m[j] * (rinv2 * rinv);
+  const double f = g3 * w;
+  const double rv = rx * ux + ry * uy + rz * uz;
+  out[0] = f * rx; out[1] = f * ry; out[2] = f * rz;
+  const double c = 3.0 * w * rv * rinv2 + dK * rv * rinv * irot;
+  out[3] = g3 * (w * ux - c * rx);
+  out[4] = g3 * (w * uy - c * ry);
+  out[5] = g3 * (w * uz - c * rz);
 }
 
-// larger clusters: one warp each
+// forces on the active members S.act[0..nact) from arrays X, V into a1, j1
+__device__ void block_forces(HShared &S, const double (*X)[kHMax], const double (*V)[kHMax],
+                             int nc, int nact, int item, const p3t_params &prm, double i1mg) {
+  const int per = nc + 1;
+  const int B = kHB / per > 0 ? kHB / per : 1;  // members per batch
+  for (int b0 = 0; b0 < nact; b0 += B) {
+    const int nb = min(B, nact - b0);
+    const int items = nb * per;
+    for (int i = item; i < items; i += kHB) {
+      const int bm = i / per, jj = i - bm * per;
+      hard_term(S, X, V, nc, S.act[b0 + bm], jj, prm, i1mg, S.T[i]);
+    }
+    __syncthreads();
+    for (int i = item; i < nb * 6; i += kHB) {
+      const int bm = i / 6, q = i - bm * 6;
+      const int k = S.act[b0 + bm];
+      const int base = bm * per;
+      double acc = 0.0;
+      acc -= S.T[base + nc][q];
+      for (int jj = 0; jj < nc; ++jj) acc -= S.T[base + jj][q];
+      if (q < 3) S.a1[q][k] = acc; else S.j1[q - 3][k] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int64_t block_min(int64_t v, int64_t *red4) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const int64_t u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u < v ? u : v;
+  }
+  if ((threadIdx.x & 31) == 0) red4[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int64_t r = red4[0];
+  for (int q = 1; q < kHB / 32; ++q) r = red4[q] < r ? red4[q] : r;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kHB) k_hermite_block(
+    const int64_t *d_ncl, const int64_t *cl_off, const int32_t *cl_mem, p3t_particles p,
+    p3t_params prm, double dt, unsigned long long *steps_out, int64_t *cursor,
+    DevStatus *st) {
+  __shared__ HShared S;
+  const int tid = threadIdx.x;
+  const int item = (tid & 31) * (kHB / 32) + (tid >> 5);  // consecutive items -> different warps
+  const int64_t ncl = *d_ncl;
+  const int64_t T = ((int64_t)1) << P3T_KMAX;
+  const double unit = ldexp(dt, -P3T_KMAX);
+  const double i1mg = 1.0 / (1.0 - prm.gamma);
+  unsigned long long steps = 0;
+  bool underflow = false;
+  for (;;) {
+    if (tid == 0) S.cluster = atomicAdd(reinterpret_cast<unsigned long long *>(cursor), 1ull);
+    __syncthreads();
+    const int64_t c = S.cluster;
+    __syncthreads();
+    if (c >= ncl) break;
+    const int64_t off = cl_off[c];
+    const int nc = (int)(cl_off[c + 1] - off);
+    if (nc > kHMax) continue;  // the warp path takes these
+    for (int k = item; k < nc; k += kHB) {
+      const int32_t i = cl_mem[off + k];
+      S.x[0][k] = p.x[i]; S.x[1][k] = p.y[i]; S.x[2][k] = p.z[i];
+      S.v[0][k] = p.vx[i]; S.v[1][k] = p.vy[i]; S.v[2][k] = p.vz[i];
+      S.m[k] = p.m[i];
+      S.iro[k] = 1.0 / p.r_out[i];
+      S.act[k] = k;
+    }
+    __syncthreads();
+    // initial forces of every member, first steps
+    block_forces(S, S.x, S.v, nc, nc, item, prm, i1mg);
+    for (int k = item; k < nc; k += kHB) {
+      for (int q = 0; q < 3; ++q) { S.a[q][k] = S.a1[q][k]; S.j[q][k] = S.j1[q][k]; }
+      const int e = ilogb(dt);
+      const float an = norm3f(S.a[0][k], S.a[1][k], S.a[2][k], 0);
+      const float jn = norm3f(S.j[0][k], S.j[1][k], S.j[2][k], e);
+      const double dtd = jn > 0.0f ? ldexp((double)((float)prm.eta0 * an / jn), e) : dt;
+      S.t[k] = 0;
+      S.lvl[k] = quantise_level(dtd, dt, 0, 0, underflow);
+    }
+    __syncthreads();
+    int64_t iter = 0;
+    for (;;) {
+      int64_t e_min = T, t_min = T;
+      for (int k = tid; k < nc; k += kHB) {
+        const int64_t e = S.t[k] + (T >> S.lvl[k]);
+        e_min = e < e_min ? e : e_min;
+        t_min = S.t[k] < t_min ? S.t[k] : t_min;
+      }
+      const int64_t tn = block_min(e_min, S.red[0]);
+      const int64_t tmin = block_min(t_min, S.red[1]);
+      if (tmin >= T) break;
+      if (++iter > kHermiteIterLimit) {
+        if (tid == 0) dev_fail(st, P3T_ERR_TIMEOUT, 61, 0);
+        break;
+      }
+      // predict every member (component items)
+      for (int i = item; i < nc * 3; i += kHB) {
+        const int k = i / 3, q = i - 3 * k;
+        const double D = (double)(tn - S.t[k]) * unit;
+        const double D2 = D * D, D3 = D2 * D;
+        S.p[q][k] = S.x[q][k] + S.v[q][k] * D + S.a[q][k] * D2 * 0.5 + S.j[q][k] * D3 * (1.0 / 6.0);
+        S.pv[q][k] = S.v[q][k] + S.a[q][k] * D + S.j[q][k] * D2 * 0.5;
+      }
+      // active members in ascending order
+      {
+        const bool on = tid < nc && S.t[tid] + (T >> S.lvl[tid]) == tn;
+        const unsigned bal = __ballot_sync(0xffffffffu, on);
+        if ((tid & 31) == 0) S.wcount[tid >> 5] = __popc(bal);
+        __syncthreads();
+        int base = 0;
+        for (int q = 0; q < (tid >> 5); ++q) base += S.wcount[q];
+        if (on) S.act[base + __popc(bal & ((1u << (tid & 31)) - 1u))] = tid;
+        if (tid == 0) {
+          int tot = 0;
+          for (int q = 0; q < kHB / 32; ++q) tot += S.wcount[q];
+          S.nact = tot;
+        }
+      }
+      // (kHMax == kHB: member k is thread k here)
+      __syncthreads();
+      const int nact = S.nact;
+      block_forces(S, S.p, S.pv, nc, nact, item, prm, i1mg);
+      // correct (component items of the active members)
+      for (int i = item; i < nact * 3; i += kHB) {
+        const int b = i / 3, q = i - 3 * b;
+        const int k = S.act[b];
+        const double D = (double)(T >> S.lvl[k]) * unit;
+        const double D2 = D * D, D3 = D2 * D, D4 = D3 * D, D5 = D4 * D;
+        const double iD = 1.0 / D, iD2 = iD * iD, iD3 = iD2 * iD;
+        const double da = S.a[q][k] - S.a1[q][k];
+        const double j0 = S.j[q][k], j1 = S.j1[q][k];
+        const double A2 = (-6.0 * da - D * (4.0 * j0 + 2.0 * j1)) * iD2;
+        const double A3 = (12.0 * da + 6.0 * D * (j0 + j1)) * iD3;
+        S.a2e[q][k] = A2 + D * A3;
+        S.a3[q][k] = A3;
+        S.x[q][k] = S.p[q][k] + A2 * D4 * (1.0 / 24.0) + A3 * D5 * (1.0 / 120.0);
+        S.v[q][k] = S.pv[q][k] + A2 * D3 * (1.0 / 6.0) + A3 * D4 * (1.0 / 24.0);
+        S.a[q][k] = S.a1[q][k];
+        S.j[q][k] = j1;
+      }
+      __syncthreads();
+      // new steps of the active members
+      for (int b = item; b < nact; b += kHB) {
+        const int k = S.act[b];
+        const double D = (double)(T >> S.lvl[k]) * unit;
+        const int e = ilogb(D);
+        const float an = norm3f(S.a[0][k], S.a[1][k], S.a[2][k], 0);
+        const float jn = norm3f(S.j[0][k], S.j[1][k], S.j[2][k], e);
+        const float a2n = norm3f(S.a2e[0][k], S.a2e[1][k], S.a2e[2][k], 2 * e);
+        const float a3n = norm3f(S.a3[0][k], S.a3[1][k], S.a3[2][k], 3 * e);
+        const float num = an * a2n + jn * jn, den = jn * a3n + a2n * a2n;
+        const double dtd = den > 0.0f ? ldexp((double)sqrtf((float)prm.eta * num / den), e) : dt;
+        S.t[k] = tn;
+        S.lvl[k] = quantise_level(dtd, dt, S.lvl[k], tn, underflow);
+      }
+      if (tid == 0) steps += (unsigned long long)nact;
+      __syncthreads();
+    }
+    for (int k = item; k < nc; k += kHB) {
+      const int32_t i = cl_mem[off + k];
+      p.x[i] = S.x[0][k]; p.y[i] = S.x[1][k]; p.z[i] = S.x[2][k];
+      p.vx[i] = S.v[0][k]; p.vy[i] = S.v[1][k]; p.vz[i] = S.v[2][k];
+    }
+    __syncthreads();
+  }
+  if (underflow) dev_fail(st, P3T_ERR_DT_UNDERFLOW, 62, 0);
+  if (tid == 0 && steps_out && steps) atomicAdd(steps_out, steps);
+}
+
+__global__ void k_zero_i64_one(int64_t *p) { *p = 0; }
+
+// clusters of more than kHMax members (a percolating cluster): one warp each,
+// members over lanes, state in the global workspace
 __global__ void k_hermite(const int64_t *d_ncl, const int64_t *cl_off,
                           const int32_t *cl_mem, p3t_particles p, HWork w,
                           p3t_params prm, double dt,
@@ -376,7 +595,7 @@ __global__ void k_hermite(const int64_t *d_ncl, const int64_t *cl_off,
   for (int64_t c = warp; c < ncl; c += nwarps) {
     const int64_t off = cl_off[c];
     const int nc = (int)(cl_off[c + 1] - off);
-    if (nc <= kSmallCluster) continue;
+    if (nc <= kHMax) continue;
     integrate_cluster<32>(off, nc, cl_mem, p, w, prm, dt, lane, 0xffffffffu, steps,
                           underflow, st);
   }
@@ -513,11 +732,14 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
   P3T_CUDA_TRY(cudaEventRecord(c->ev_fork, s));
   P3T_CUDA_TRY(cudaStreamWaitEvent(c->aux[0], c->ev_fork, 0));
   P3T_CUDA_TRY(cudaStreamWaitEvent(c->aux[1], c->ev_fork, 0));
-  // at most n/2 clusters: 4 lanes per small cluster, a warp per large one
+  // clusters of <= kHMax members: a block each, handed out dynamically (a
+  // long encounter keeps its block while the others move on); larger ones: a
+  // warp each
   const int64_t ncl_max = (n / 2) > 0 ? n / 2 : 1;
-  // 32-thread blocks (8 clusters each) spread consecutive clusters over all SMs
-  k_hermite_small<<<(unsigned)p3t_grid(ncl_max * 4, 32, 4 * maxb), 32, 0, c->aux[0]>>>(
-      &cl->counts[1], cl->cl_off, cl->cl_mem, *p, w, c->prm, dt, steps, c->status);
+  k_zero_i64_one<<<1, 1, 0, c->aux[0]>>>(c->hcursor);
+  k_hermite_block<<<(unsigned)p3t_grid(ncl_max * kHB, kHB, (int64_t)c->num_sms * 4), kHB, 0,
+                    c->aux[0]>>>(&cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, steps,
+                                 c->hcursor, c->status);
   k_hermite<<<(unsigned)p3t_grid(ncl_max * 32, 128, maxb), 128, 0, c->aux[1]>>>(
       &cl->counts[1], cl->cl_off, cl->cl_mem, *p, w, c->prm, dt, steps, c->status);
   k_kepler<<<(unsigned)p3t_grid(n, 128, maxb), 128, 0, s>>>(&cl->counts[0], cl->singles, *p,
@@ -526,7 +748,7 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
   P3T_CUDA_TRY(cudaEventRecord(c->ev_join[1], c->aux[1]));
   P3T_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[0], 0));
   P3T_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[1], 0));
-  p3t_note_launches(4);
+  p3t_note_launches(5);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 

@@ -139,6 +139,7 @@ struct p3t_ctx {
   int64_t *ht = nullptr;                   // time in units of dt / 2^40
   int32_t *hl = nullptr;                   // block level
   unsigned long long *hsteps = nullptr;    // device counter
+  int64_t *hcursor = nullptr;              // cluster cursor of the block kernel
 
   // energy
   double *epart = nullptr;                 // per-block partial sums
