@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--group-size", type=int, default=32,
+    ap.add_argument("--group-size", type=int, default=64,
                     help="target group size of the tree walk (0: one group per leaf)")
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -161,7 +161,7 @@ def allsum(dist, v):
 
 
 # ------------------------------------------------------------- CPU oracle ----
-def oracle_step_estimate(s, n_targets, seed=7, group_size=32):
+def oracle_step_estimate(s, n_targets, seed=7, group_size=64):
     """The CPU oracle on a bounded sample of the same workload.
 
     Timed: the full tree build at N (keys, sort, octree, moments), the walk for
@@ -200,7 +200,8 @@ def run_reference(args):
     O.build()
     times, inter = [], 0.0
     for k in range(args.warmup + args.steps):
-        i, t, info = oracle_step_estimate(s, args.cpu_targets, seed=100 + k)
+        i, t, info = oracle_step_estimate(s, args.cpu_targets, seed=100 + k,
+                                          group_size=args.group_size)
         if k >= args.warmup:
             times.append(t)
             inter += i
@@ -212,7 +213,8 @@ def run_reference(args):
                 warmup=args.warmup, ms_per_step=1e3 * tot / args.steps, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                 impl="reference",
-                config=dict(workload=workload_name(args.n), n=args.n, precision="fp64 (CPU oracle)"),
+                config=dict(workload=workload_name(args.n), n=args.n, group_size=args.group_size,
+                            precision="fp64 (CPU oracle)"),
                 cpu_baseline=dict(value=value, unit=UNIT, cores=info["threads"], kind="oracle",
                                   sample=sample),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
@@ -268,6 +270,8 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     ss.status()
 
+    energy = torch.zeros(2, 4, dtype=torch.float64, device=dev)
+    P.p3t_energy(ss.ctx, st, energy[0], stream)   # row a10, outside the timed region
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -283,6 +287,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     launches = P.p3t_launch_count() - launches0
     barrier(dist)
+    P.p3t_energy(ss.ctx, st, energy[1], stream)
     clk = clocks.stop()
     ss.status()
     elapsed = t_start.elapsed_time(t_end) / 1e3
@@ -296,6 +301,7 @@ def run_ours(args):
     inter = float(c.sum())
     hsteps = float(hsteps_all.sum().item())
     walk_s = phase[2] / 1e3
+    E0, E1 = (float(v) for v in energy[:, 0].cpu())
     flops_per_launch = (FLOP_PP * c[:, 0] + FLOP_PN * c[:, 1]).mean()
 
     # ---- end to end through the C ABI with host buffers --------------------
@@ -337,7 +343,8 @@ def run_ours(args):
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        i_cpu, t_cpu, info = oracle_step_estimate(workload(args.n), args.cpu_targets)
+        i_cpu, t_cpu, info = oracle_step_estimate(workload(args.n), args.cpu_targets,
+                                                   group_size=args.group_size)
         cpu = dict(value=i_cpu / t_cpu, unit=UNIT, cores=info["threads"], kind="oracle",
                    sample=(f"oracle tree build at N={args.n} + walk of {info['sample_targets']} "
                            f"random targets scaled by N/targets + Kepler drift of all N; "
@@ -352,7 +359,9 @@ def run_ours(args):
                     precision=args.precision, l2="per-step working set > L2 (inputs ~0.5 GB)",
                     parallelism="replicas only" if world > 1 else "single GPU"),
         soft_step_ms=1e3 * elapsed / K,
-        hermite_steps_per_s=hsteps / elapsed,
+        hermite_steps_per_s=hsteps / (phase[0] * K / 1e3),   # over the kick + hard phase
+        hermite_steps_per_step=hsteps / K,
+        energy_error=abs(E1 / E0 - 1.0),
         interactions_per_step=inter / K,
         phases_ms=dict(kick_and_hard=phase[0], tree=phase[1], soft_force=phase[2],
                        neighbours_clusters=phase[3], kick=phase[4]),
