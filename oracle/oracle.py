@@ -39,7 +39,7 @@ class OrParams(C.Structure):
 
     _fields_ = [(n, C.c_double) for n in (
         "G", "m_star", "dt_soft", "gamma", "rcut0", "rcut1", "rs0", "rs1", "rs2",
-        "rs3", "theta", "eta", "eta0")] + [
+        "rs3", "theta", "eta", "eta0", "f_radius")] + [
         ("leaf_size", C.c_int32), ("precision", C.c_int32), ("vran_bins", C.c_int32),
         ("group_size", C.c_int32)]
 
@@ -62,6 +62,7 @@ class Params:
     theta: float = 0.5
     eta: float = 0.01
     eta0: float = 0.001
+    f_radius: float = 0.0     # collision radius factor f (Sec. 2.4.1; paper: 1); 0 = off
     leaf_size: int = 16
     precision: int = 0
     vran_bins: int = 0
@@ -112,13 +113,17 @@ def lib():
         L.or_hard_acc_jerk.argtypes = ([C.c_int64] + [_dp] * 8 + [_P, C.c_int64, _dp, _dp])
         L.or_hermite_cluster.restype = C.c_int
         L.or_hermite_cluster.argtypes = ([C.c_int64, _i32p] + [_dp] * 8 + [
-            _P, C.c_double, C.POINTER(C.c_int64)])
+            _vp, _P, C.c_double, C.POINTER(C.c_int64), _vp, C.POINTER(C.c_double)])
         L.or_kepler_drift.restype = C.c_int
         L.or_kepler_drift.argtypes = [C.c_int64, _vp] + [_dp] * 6 + [C.c_double, C.c_double]
         L.or_hard_step.restype = C.c_int
         L.or_hard_step.argtypes = ([C.c_int64] + [_dp] * 8 + [
-            _P, C.c_double, C.c_int64, _i32p, C.c_int64, _i64p, _i32p,
-            C.POINTER(C.c_int64)])
+            _vp, _P, C.c_double, C.c_int64, _i32p, C.c_int64, _i64p, _i32p,
+            C.POINTER(C.c_int64), _i32p, C.POINTER(C.c_double)])
+        L.or_kick_composites.restype = C.c_double
+        L.or_kick_composites.argtypes = [C.c_int64] + [_dp] * 6 + [C.c_double, _dp, _i32p]
+        L.or_merge.restype = C.c_int64
+        L.or_merge.argtypes = [C.c_int64] + [_dp] * 10 + [_i32p, _i32p]
         L.or_energy.argtypes = [C.c_int64] + [_dp] * 7 + [C.c_double, C.c_double, _dp]
         L.or_num_threads.restype = C.c_int
     return _lib
@@ -297,14 +302,28 @@ def hard_acc_jerk(s: dict, r_out, p: Params, k: int):
     return a, j
 
 
-def hermite_cluster(s: dict, r_out, p: Params, members, dt: float):
-    """Integrates the members of one cluster in place; returns (status, steps)."""
+def _vptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def hermite_cluster(s: dict, r_out, p: Params, members, dt: float, r_phys=None,
+                    with_sets: bool = False):
+    """Integrates the members of one cluster in place; returns (status, steps),
+    or (status, steps, roots, e_disp) with ``with_sets`` (row f4: ``roots`` the
+    lowest member of each member's composite, cluster-local; ``e_disp`` the
+    dissipated energy).  ``r_phys`` (physical radii, caller order) switches the
+    collision test on when ``p.f_radius > 0``."""
     mem = np.ascontiguousarray(members, dtype=np.int32)
     ns = C.c_int64(0)
+    ed = C.c_double(0.0)
+    roots = np.empty(len(mem), dtype=np.int32)
+    rp = None if r_phys is None else _f64(r_phys)
     cp = p.c()
     st = lib().or_hermite_cluster(len(mem), mem, s["x"], s["y"], s["z"], s["vx"], s["vy"],
-                                  s["vz"], _f64(s["m"]), _f64(r_out), C.byref(cp), float(dt),
-                                  C.byref(ns))
+                                  s["vz"], _f64(s["m"]), _f64(r_out), _vptr(rp), C.byref(cp),
+                                  float(dt), C.byref(ns), roots.ctypes.data, C.byref(ed))
+    if with_sets:
+        return st, ns.value, roots, ed.value
     return st, ns.value
 
 
@@ -315,16 +334,48 @@ def kepler_drift(s: dict, dt: float, mu: float, idx=None) -> int:
                                  s["z"], s["vx"], s["vy"], s["vz"], float(dt), float(mu))
 
 
-def hard_step(s: dict, r_out, p: Params, cl: Clusters, dt: float):
-    """Rows a8 + a9 in place; returns (status, hermite particle-steps)."""
+def hard_step(s: dict, r_out, p: Params, cl: Clusters, dt: float, r_phys=None,
+              with_sets: bool = False):
+    """Rows a8 + a9 in place; returns (status, hermite particle-steps), or with
+    ``with_sets`` also (comp_root, e_hard): row f4's composites (lowest member's
+    caller index, -1 outside composites) and the collisions' dissipation."""
     ns = C.c_int64(0)
+    eh = C.c_double(0.0)
+    n = len(s["m"])
+    comp = np.empty(n, dtype=np.int32)
+    rp = None if r_phys is None else _f64(r_phys)
     cp = p.c()
-    st = lib().or_hard_step(len(s["m"]), s["x"], s["y"], s["z"], s["vx"], s["vy"], s["vz"],
-                            _f64(s["m"]), _f64(r_out), C.byref(cp), float(dt),
+    st = lib().or_hard_step(n, s["x"], s["y"], s["z"], s["vx"], s["vy"], s["vz"],
+                            _f64(s["m"]), _f64(r_out), _vptr(rp), C.byref(cp), float(dt),
                             len(cl.singles), np.ascontiguousarray(cl.singles, dtype=np.int32),
                             len(cl.cl_off) - 1, np.ascontiguousarray(cl.cl_off, dtype=np.int64),
-                            np.ascontiguousarray(cl.cl_mem, dtype=np.int32), C.byref(ns))
+                            np.ascontiguousarray(cl.cl_mem, dtype=np.int32), C.byref(ns),
+                            comp, C.byref(eh))
+    if with_sets:
+        return st, ns.value, comp, eh.value
     return st, ns.value
+
+
+def kick_composites(s: dict, acc, h: float, comp_root):
+    """Row f4: kick with composite members given their composite's mass-weighted
+    mean soft acceleration; returns the dissipated energy."""
+    n = len(s["m"])
+    return lib().or_kick_composites(n, s["vx"], s["vy"], s["vz"], _f64(acc[:, 0]),
+                                    _f64(acc[:, 1]), _f64(acc[:, 2]), float(h), _f64(s["m"]),
+                                    np.ascontiguousarray(comp_root, dtype=np.int32))
+
+
+def merge(s: dict, r_phys, r_out, r_search, comp_root):
+    """Row f4 (procedure step 9): replaces every composite by one particle.
+    Returns (new state dict, r_phys, r_out, r_search, new_index)."""
+    n = len(s["m"])
+    a = {k: np.array(s[k], dtype=np.float64, copy=True) for k in ("x", "y", "z", "vx", "vy", "vz", "m")}
+    rp, ro, rs = (np.array(v, dtype=np.float64, copy=True) for v in (r_phys, r_out, r_search))
+    ni = np.empty(n, dtype=np.int32)
+    k = lib().or_merge(n, a["x"], a["y"], a["z"], a["vx"], a["vy"], a["vz"], a["m"], rp, ro, rs,
+                       np.ascontiguousarray(comp_root, dtype=np.int32), ni)
+    out = {q: v[:k].copy() for q, v in a.items()}
+    return out, rp[:k].copy(), ro[:k].copy(), rs[:k].copy(), ni
 
 
 def energy(s: dict, G: float = 1.0, m_star: float = 1.0):
@@ -335,21 +386,41 @@ def energy(s: dict, G: float = 1.0, m_star: float = 1.0):
     return out
 
 
-def soft_step(s: dict, r_out, r_search, p: Params, acc, cl: Clusters):
-    """One P3T soft step (procedure steps 3-8) in place on the state dict ``s``.
+def soft_step(s: dict, r_out, r_search, p: Params, acc, cl: Clusters, r_phys=None):
+    """One P3T soft step (procedure steps 3-9) in place on the state dict ``s``.
 
     ``acc`` and ``cl`` are the soft acceleration and the clusters from the
     previous force evaluation.  Returns (acc, clusters, info) of the new
-    evaluation, ready for the next step.
+    evaluation, ready for the next step.  With ``r_phys`` and ``p.f_radius >
+    0`` colliding particles merge (row f4): the arrays of ``s`` are then
+    replaced by shorter ones, and info carries the new ``r_phys``, ``r_out``,
+    ``r_search`` (recomputed for all particles, step 9), ``new_index`` and the
+    dissipated energies ``e_hard``, ``e_soft``.
     """
     kick(s, acc, 0.5 * p.dt_soft)
-    st, hsteps = hard_step(s, r_out, p, cl, p.dt_soft)
+    coll = r_phys is not None and p.f_radius > 0
+    st, hsteps, comp, e_hard = hard_step(s, r_out, p, cl, p.dt_soft, r_phys, with_sets=True)
     res = tree_soft(s, r_out, r_search, p)
     off, idx = neighbours_from_candidates(s, r_out, r_search, p, res.cand_i, res.cand_j)
     ncl = clusters(len(s["m"]), off, idx)
-    kick(s, res.acc, 0.5 * p.dt_soft)
-    return res.acc, ncl, dict(status=st, hermite_steps=hsteps, n_pp=res.n_pp,
-                              n_pnode=res.n_pnode, nb_off=off, nb_idx=idx)
+    info = dict(status=st, hermite_steps=hsteps, n_pp=res.n_pp, n_pnode=res.n_pnode,
+                nb_off=off, nb_idx=idx, e_hard=e_hard, e_soft=0.0, merged=0)
+    if not coll or not (comp >= 0).any():
+        kick(s, res.acc, 0.5 * p.dt_soft)
+        return res.acc, ncl, info
+    info["e_soft"] = kick_composites(s, res.acc, 0.5 * p.dt_soft, comp)
+    n0 = len(s["m"])
+    ns, rp, ro, rs, ni = merge(s, r_phys, r_out, r_search, comp)
+    for k in ns:
+        s[k] = ns[k]
+    ro, rs, _, _ = cutoffs(s, p)
+    res = tree_soft(s, ro, rs, p)
+    off, idx = neighbours_from_candidates(s, ro, rs, p, res.cand_i, res.cand_j)
+    ncl = clusters(len(s["m"]), off, idx)
+    info.update(merged=n0 - len(s["m"]), r_phys=rp, r_out=ro, r_search=rs, new_index=ni,
+                n_pp=info["n_pp"] + res.n_pp, n_pnode=info["n_pnode"] + res.n_pnode,
+                nb_off=off, nb_idx=idx)
+    return res.acc, ncl, info
 
 
 def initial_force(s: dict, r_out, r_search, p: Params):

@@ -846,6 +846,120 @@ static float norm3f(const double *v, int k) {
   return sqrtf(a * a + b * b + c * c);
 }
 
+/* Hard force and jerk of member k when some members form composites (row   */
+/* f4, Sec. 2.4.1): a member's hard force leaves out the other members of    */
+/* its own composite (set[j] == set[k]).  With RP given, *partner receives   */
+/* the lowest-index member j outside k's composite that touches k, i.e.      */
+/*   r_kj < f (R_p,k + R_p,j),                                               */
+/* at the positions the force is evaluated at (or -1).  Otherwise the terms  */
+/* and their order are those of or_hard_acc_jerk.                             */
+static void hard_acc_jerk_sets(int64_t nc, const double *x, const double *y,
+                               const double *z, const double *vx, const double *vy,
+                               const double *vz, const double *m, const double *r_out,
+                               const double *RP, const int64_t *set, const or_params *p,
+                               int64_t k, double acc[3], double jerk[3], int64_t *partner) {
+  const double i1mg = 1.0 / (1.0 - p->gamma);
+  double ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0;
+  if (partner) *partner = -1;
+  {
+    double r2 = x[k] * x[k] + y[k] * y[k] + z[k] * z[k];
+    double rinv = 1.0 / sqrt(r2);
+    double rinv2 = rinv * rinv;
+    double f = p->G * p->m_star * (rinv2 * rinv);
+    double rv = x[k] * vx[k] + y[k] * vy[k] + z[k] * vz[k];
+    ax -= f * x[k]; ay -= f * y[k]; az -= f * z[k];
+    double c = 3.0 * rv * rinv2;
+    jx -= f * (vx[k] - c * x[k]);
+    jy -= f * (vy[k] - c * y[k]);
+    jz -= f * (vz[k] - c * z[k]);
+  }
+  const double irok = 1.0 / r_out[k];
+  for (int64_t j = 0; j < nc; ++j) {
+    if (j == k || set[j] == set[k]) continue;
+    double rx = x[k] - x[j], ry = y[k] - y[j], rz = z[k] - z[j];
+    double ux = vx[k] - vx[j], uy = vy[k] - vy[j], uz = vz[k] - vz[j];
+    double r2 = rx * rx + ry * ry + rz * rz;
+    if (RP && partner && *partner < 0) {
+      double sr = p->f_radius * (RP[k] + RP[j]);
+      if (r2 < sr * sr) *partner = j;
+    }
+    if (r2 == 0.0) continue;
+    double rinv = 1.0 / sqrt(r2);
+    double r = r2 * rinv;
+    double irot = dmin(irok, 1.0 / r_out[j]);
+    double yv = r * irot;
+    if (yv >= 1.0) continue;
+    double w = 1.0, dK = 0.0;
+    if (yv > p->gamma) {
+      double xs = (yv - p->gamma) * i1mg;
+      double x2 = xs * xs, x3 = x2 * xs, x4 = x2 * x2, u = 1.0 - xs;
+      w = 1.0 - x4 * (35.0 - 84.0 * xs + 70.0 * x2 - 20.0 * x3);
+      dK = 140.0 * x3 * (u * u * u) * i1mg;
+    }
+    double rinv2 = rinv * rinv;
+    double g3 = p->G * m[j] * (rinv2 * rinv);
+    double f = g3 * w;
+    double rv = rx * ux + ry * uy + rz * uz;
+    ax -= f * rx; ay -= f * ry; az -= f * rz;
+    double c = 3.0 * w * rv * rinv2 + dK * rv * rinv * irot;
+    jx -= g3 * (w * ux - c * rx);
+    jy -= g3 * (w * uy - c * ry);
+    jz -= g3 * (w * uz - c * rz);
+  }
+  acc[0] = ax; acc[1] = ay; acc[2] = az;
+  jerk[0] = jx; jerk[1] = jy; jerk[2] = jz;
+}
+
+/* The hard acceleration (and jerk) of a composite is the mass-weighted mean  */
+/* of its members' (Sec. 2.4.1): every evaluated member of a composite gets  */
+/* sum_l m_l a_l / sum_l m_l, sums over the composite in ascending order.     */
+static void average_sets(int64_t nc, const int64_t *set, const unsigned char *evald,
+                         const double *m, double *a, double *jk) {
+  for (int64_t r = 0; r < nc; ++r) {
+    if (set[r] != r || !evald[r]) continue;
+    int64_t size = 0;
+    double M = 0.0, A[3] = {0, 0, 0}, J[3] = {0, 0, 0};
+    for (int64_t l = 0; l < nc; ++l) {
+      if (set[l] != r) continue;
+      ++size;
+      M += m[l];
+      for (int c = 0; c < 3; ++c) { A[c] += m[l] * a[3 * l + c]; J[c] += m[l] * jk[3 * l + c]; }
+    }
+    if (size < 2) continue;
+    for (int64_t l = 0; l < nc; ++l) {
+      if (set[l] != r) continue;
+      for (int c = 0; c < 3; ++c) { a[3 * l + c] = A[c] / M; jk[3 * l + c] = J[c] / M; }
+    }
+  }
+}
+
+/* Energy of the members marked in chg as far as a merge can change it:     */
+/* their kinetic and star potential energy plus every pair potential with   */
+/* at least one marked member (each pair once), pairs inside one composite  */
+/* (set) left out.  Changeover functions replaced by unity.                 */
+static double set_energy(int64_t nc, const unsigned char *chg, const int64_t *set,
+                         const double *qx, const double *qy, const double *qz,
+                         const double *qvx, const double *qvy, const double *qvz,
+                         const double *m, const or_params *p) {
+  double E = 0.0;
+  for (int64_t k = 0; k < nc; ++k) {
+    if (!chg[k]) continue;
+    E += 0.5 * m[k] * (qvx[k] * qvx[k] + qvy[k] * qvy[k] + qvz[k] * qvz[k]);
+    E -= p->G * p->m_star * m[k] / sqrt(qx[k] * qx[k] + qy[k] * qy[k] + qz[k] * qz[k]);
+  }
+  for (int64_t k = 0; k < nc; ++k) {
+    if (!chg[k]) continue;
+    for (int64_t l = 0; l < nc; ++l) {
+      if (l == k || (chg[l] && l < k) || set[l] == set[k]) continue;
+      double dx = qx[k] - qx[l], dy = qy[k] - qy[l], dz = qz[k] - qz[l];
+      double r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 == 0.0) continue;
+      E -= p->G * m[k] * m[l] / sqrt(r2);
+    }
+  }
+  return E;
+}
+
 /* Fourth-order Hermite with block individual time steps over [0, dt] for one */
 /* cluster (Sec. 2.1.2, Makino 1991; Aarseth time steps).  Reading C7:        */
 /*  predictor  x_p = x + v D + a D^2/2 + j D^3/6, v_p = v + a D + j D^2/2;    */
@@ -858,30 +972,61 @@ static float norm3f(const double *v, int k) {
 /*  (they are quantised to dt / 2^k); state, forces and corrector are FP64.    */
 /* All members are predicted to each block time; the active ones are        */
 /* evaluated from the predicted state and then corrected together.           */
+/*                                                                           */
+/* Perfect accretion (row f4, Sec. 2.4.1), when RP (physical radii) is given */
+/* and f_radius > 0.  Readings:                                              */
+/*  - detection: at every force evaluation (the initial one and each block   */
+/*    time), each evaluated member k records its lowest-index partner j      */
+/*    outside its composite with r_kj < f (R_p,k + R_p,j);                   */
+/*  - after the correction, the members joined by these pairs (and the       */
+/*    composites they already belong to) become one composite: each member   */
+/*    is taken at the block time t_b (corrected if it was active, predicted  */
+/*    otherwise), all get the centre-of-mass position and velocity, time t_b,*/
+/*    the composite's hard acceleration and jerk (mass-weighted mean, pairs  */
+/*    inside it left out) and a first step eta0 |a|/|j| (the paper's rule    */
+/*    for the first step after a collision); the members stay separate       */
+/*    particles until the merge after the second kick;                       */
+/*  - dissipation (Eq. edisphard with the changeover functions replaced by   */
+/*    unity, neighbours N_i taken as the cluster): the change of the energy  */
+/*    of the affected members (kinetic, star potential, pair potential with  */
+/*    the cluster) from before to after the replacement.                     */
+/* root_out (nc entries, or NULL) receives for each member the lowest member */
+/* of its composite (itself if none); *e_disp the dissipated energy.         */
 int or_hermite_cluster(int64_t nc, const int32_t *members, double *X, double *Y,
                        double *Z, double *VX, double *VY, double *VZ,
-                       const double *M, const double *RO, const or_params *p,
-                       double dt, int64_t *n_steps) {
+                       const double *M, const double *RO, const double *RPall,
+                       const or_params *p, double dt, int64_t *n_steps,
+                       int32_t *root_out, double *e_disp) {
   const int64_t T = ((int64_t)1) << OR_KMAX;
   const double unit = ldexp(dt, -OR_KMAX);
-  double *buf = (double *)malloc(sizeof(double) * nc * 26);
+  const int coll = RPall != NULL && p->f_radius > 0.0;
+  double *buf = (double *)malloc(sizeof(double) * nc * 34);
   double *x = buf, *y = x + nc, *z = y + nc, *vx = z + nc, *vy = vx + nc, *vz = vy + nc;
   double *px = vz + nc, *py = px + nc, *pz = py + nc, *pvx = pz + nc, *pvy = pvx + nc, *pvz = pvy + nc;
   double *a = pvz + nc;   /* 3 nc */
   double *jk = a + 3 * nc; /* 3 nc */
   double *a1 = jk + 3 * nc, *j1 = a1 + 3 * nc;
-  double *m = j1 + 3 * nc, *ro = m + nc;
-  int64_t *t = (int64_t *)malloc(sizeof(int64_t) * nc);
+  double *m = j1 + 3 * nc, *ro = m + nc, *rp = ro + nc;
+  double *qx = rp + nc, *qy = qx + nc, *qz = qy + nc, *qvx = qz + nc, *qvy = qvx + nc,
+         *qvz = qvy + nc; /* state at a collision's block time */
+  int64_t *t = (int64_t *)malloc(sizeof(int64_t) * nc * 4);
+  int64_t *set = t + nc, *oset = set + nc, *partner = oset + nc;
   int *lvl = (int *)malloc(sizeof(int) * nc);
-  unsigned char *act = (unsigned char *)malloc(nc);
+  unsigned char *act = (unsigned char *)malloc(3 * nc);
+  unsigned char *chg = act + nc, *croot = chg + nc;
   int underflow = 0;
+  double edis = 0.0;
   for (int64_t k = 0; k < nc; ++k) {
     int32_t i = members[k];
     x[k] = X[i]; y[k] = Y[i]; z[k] = Z[i]; vx[k] = VX[i]; vy[k] = VY[i]; vz[k] = VZ[i];
-    m[k] = M[i]; ro[k] = RO[i];
+    m[k] = M[i]; ro[k] = RO[i]; rp[k] = coll ? RPall[i] : 0.0;
+    set[k] = k; partner[k] = -1; act[k] = 1;
   }
+  const double *RP = coll ? rp : NULL;
+  for (int64_t k = 0; k < nc; ++k)
+    hard_acc_jerk_sets(nc, x, y, z, vx, vy, vz, m, ro, RP, set, p, k, a + 3 * k, jk + 3 * k,
+                       &partner[k]);
   for (int64_t k = 0; k < nc; ++k) {
-    or_hard_acc_jerk(nc, x, y, z, vx, vy, vz, m, ro, p, k, a + 3 * k, jk + 3 * k);
     /* eta0 |a| / |j| = (eta0 |a| / |j s|) s, s = 2^e */
     int e = ilogb(dt);
     float an = norm3f(a + 3 * k, 0), jn = norm3f(jk + 3 * k, e);
@@ -889,11 +1034,71 @@ int or_hermite_cluster(int64_t nc, const int32_t *members, double *X, double *Y,
     t[k] = 0;
     lvl[k] = quantise_level(dtd, dt, 0, 0, &underflow);
   }
-  int64_t steps = 0, blocks = 0;
+  /* at t = 0 the block-time state is the initial state */
+  memcpy(px, x, sizeof(double) * nc * 6);
+  int64_t steps = 0, blocks = 0, tn = 0;
   int timeout = 0;
   for (;;) {
+    /* ---- collisions found by this evaluation (all members at tn) ---- */
+    int any = 0;
+    for (int64_t k = 0; k < nc; ++k) any |= partner[k] >= 0;
+    if (any) {
+      for (int64_t k = 0; k < nc; ++k) {
+        const int on = act[k];
+        qx[k] = on ? x[k] : px[k]; qy[k] = on ? y[k] : py[k]; qz[k] = on ? z[k] : pz[k];
+        qvx[k] = on ? vx[k] : pvx[k]; qvy[k] = on ? vy[k] : pvy[k]; qvz[k] = on ? vz[k] : pvz[k];
+        oset[k] = set[k];
+      }
+      for (int64_t k = 0; k < nc; ++k) {
+        if (partner[k] < 0) continue;
+        int64_t ra = set[k], rb = set[partner[k]];
+        int64_t lo = ra < rb ? ra : rb, hi = ra < rb ? rb : ra;
+        for (int64_t l = 0; l < nc; ++l) if (set[l] == hi) set[l] = lo;
+      }
+      for (int64_t k = 0; k < nc; ++k) croot[k] = 0;
+      for (int64_t k = 0; k < nc; ++k) if (partner[k] >= 0) croot[set[k]] = 1;
+      for (int64_t k = 0; k < nc; ++k) chg[k] = croot[set[k]];
+      double Eb = set_energy(nc, chg, oset, qx, qy, qz, qvx, qvy, qvz, m, p);
+      for (int64_t r = 0; r < nc; ++r) {
+        if (!croot[r] || set[r] != r) continue;
+        double Ms = 0.0, S[6] = {0, 0, 0, 0, 0, 0};
+        for (int64_t l = 0; l < nc; ++l) {
+          if (set[l] != r) continue;
+          Ms += m[l];
+          S[0] += m[l] * qx[l]; S[1] += m[l] * qy[l]; S[2] += m[l] * qz[l];
+          S[3] += m[l] * qvx[l]; S[4] += m[l] * qvy[l]; S[5] += m[l] * qvz[l];
+        }
+        for (int64_t l = 0; l < nc; ++l) {
+          if (set[l] != r) continue;
+          qx[l] = S[0] / Ms; qy[l] = S[1] / Ms; qz[l] = S[2] / Ms;
+          qvx[l] = S[3] / Ms; qvy[l] = S[4] / Ms; qvz[l] = S[5] / Ms;
+        }
+      }
+      double Ea = set_energy(nc, chg, set, qx, qy, qz, qvx, qvy, qvz, m, p);
+      edis += Eb - Ea;
+      for (int64_t k = 0; k < nc; ++k) {
+        if (!chg[k]) continue;
+        x[k] = qx[k]; y[k] = qy[k]; z[k] = qz[k];
+        vx[k] = qvx[k]; vy[k] = qvy[k]; vz[k] = qvz[k];
+        t[k] = tn;
+      }
+      for (int64_t k = 0; k < nc; ++k)
+        if (chg[k])
+          hard_acc_jerk_sets(nc, qx, qy, qz, qvx, qvy, qvz, m, ro, NULL, set, p, k,
+                             a + 3 * k, jk + 3 * k, NULL);
+      average_sets(nc, set, chg, m, a, jk);
+      for (int64_t k = 0; k < nc; ++k) {
+        if (!chg[k]) continue;
+        int e = ilogb(dt);
+        float an = norm3f(a + 3 * k, 0), jn = norm3f(jk + 3 * k, e);
+        double dtd = jn > 0.0f ? ldexp((double)((float)p->eta0 * an / jn), e) : dt;
+        lvl[k] = quantise_level(dtd, dt, 0, tn, &underflow);
+      }
+      for (int64_t k = 0; k < nc; ++k) partner[k] = -1;
+    }
+    /* ---- next block time ---- */
     if (++blocks > OR_BLOCK_LIMIT) { timeout = 1; break; }
-    int64_t tn = T;
+    tn = T;
     for (int64_t k = 0; k < nc; ++k) {
       int64_t e = t[k] + (T >> lvl[k]);
       if (e < tn) tn = e;
@@ -914,7 +1119,10 @@ int or_hermite_cluster(int64_t nc, const int32_t *members, double *X, double *Y,
       act[k] = (t[k] + (T >> lvl[k]) == tn);
     }
     for (int64_t k = 0; k < nc; ++k)
-      if (act[k]) or_hard_acc_jerk(nc, px, py, pz, pvx, pvy, pvz, m, ro, p, k, a1 + 3 * k, j1 + 3 * k);
+      if (act[k])
+        hard_acc_jerk_sets(nc, px, py, pz, pvx, pvy, pvz, m, ro, RP, set, p, k, a1 + 3 * k,
+                           j1 + 3 * k, &partner[k]);
+    average_sets(nc, set, act, m, a1, j1);
     for (int64_t k = 0; k < nc; ++k) {
       if (!act[k]) continue;
       double D = (double)(T >> lvl[k]) * unit;
@@ -949,8 +1157,10 @@ int or_hermite_cluster(int64_t nc, const int32_t *members, double *X, double *Y,
   for (int64_t k = 0; k < nc; ++k) {
     int32_t i = members[k];
     X[i] = x[k]; Y[i] = y[k]; Z[i] = z[k]; VX[i] = vx[k]; VY[i] = vy[k]; VZ[i] = vz[k];
+    if (root_out) root_out[k] = (int32_t)set[k];
   }
   if (n_steps) *n_steps = steps;
+  if (e_disp) *e_disp = edis;
   free(buf); free(t); free(lvl); free(act);
   if (timeout) return -5;
   return underflow ? -4 : 0;
@@ -1049,25 +1259,136 @@ int or_kepler_drift(int64_t n, const int32_t *idx, double *x, double *y,
 /* of >= 2 members, Kepler drift for isolated particles.                      */
 int or_hard_step(int64_t n, double *x, double *y, double *z, double *vx,
                  double *vy, double *vz, const double *m, const double *r_out,
-                 const or_params *p, double dt, int64_t n_single,
+                 const double *RP, const or_params *p, double dt, int64_t n_single,
                  const int32_t *singles, int64_t n_clusters,
                  const int64_t *cl_off, const int32_t *cl_mem,
-                 int64_t *n_hermite_steps) {
-  (void)n;
+                 int64_t *n_hermite_steps, int32_t *comp_root, double *e_hard) {
   int err = or_kepler_drift(n_single, singles, x, y, z, vx, vy, vz, dt, p->G * p->m_star);
+  if (comp_root)
+    for (int64_t i = 0; i < n; ++i) comp_root[i] = -1;
+  double *ec = (double *)calloc(n_clusters > 0 ? n_clusters : 1, sizeof(double));
   int64_t steps = 0;
   int herr = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : steps) reduction(min : herr)
   for (int64_t c = 0; c < n_clusters; ++c) {
     int64_t ns = 0;
-    int e = or_hermite_cluster(cl_off[c + 1] - cl_off[c], cl_mem + cl_off[c], x, y, z,
-                               vx, vy, vz, m, r_out, p, dt, &ns);
+    const int64_t nc = cl_off[c + 1] - cl_off[c];
+    const int32_t *mem = cl_mem + cl_off[c];
+    int32_t *root = (int32_t *)malloc(sizeof(int32_t) * 2 * nc);
+    int32_t *cnt = root + nc;
+    int e = or_hermite_cluster(nc, mem, x, y, z, vx, vy, vz, m, r_out, RP, p, dt, &ns, root,
+                               &ec[c]);
+    if (comp_root) {
+      /* members of composites of two or more: the caller index of the lowest */
+      for (int64_t k = 0; k < nc; ++k) cnt[k] = 0;
+      for (int64_t k = 0; k < nc; ++k) ++cnt[root[k]];
+      for (int64_t k = 0; k < nc; ++k)
+        if (cnt[root[k]] >= 2) comp_root[mem[k]] = mem[root[k]];
+    }
+    free(root);
     if (e) herr = e;
     steps += ns;
   }
+  double et = 0.0;
+  for (int64_t c = 0; c < n_clusters; ++c) et += ec[c];
+  free(ec);
+  if (e_hard) *e_hard = et;
   if (n_hermite_steps) *n_hermite_steps = steps;
   if (err) return -1;
   return herr;
+}
+
+/* ========================================================================= */
+/* Row f4: second kick of composites and the merge (Sec. 2.4.1).              */
+/* After the soft force of procedure step 7, the members of a composite are  */
+/* kicked with the mass-weighted mean of their soft accelerations,           */
+/*   a_c = sum_l m_l a_l / sum_l m_l (ascending l),                           */
+/* every other particle with its own.  The dissipation is the relative       */
+/* kinetic energy the separate kicks would have given: per composite         */
+/*   sum_l m_l |h (a_l - a_c)|^2 / 2,                                         */
+/* summed over composites in ascending order of their lowest member.         */
+/* comp_root[i]: lowest member of i's composite, or -1.                      */
+/* ========================================================================= */
+static int64_t composite_list(int64_t n, const int32_t *comp_root, int32_t **list) {
+  int64_t nl = 0;
+  for (int64_t i = 0; i < n; ++i) nl += comp_root[i] >= 0;
+  *list = (int32_t *)malloc(sizeof(int32_t) * (nl > 0 ? nl : 1));
+  nl = 0;
+  for (int64_t i = 0; i < n; ++i)
+    if (comp_root[i] >= 0) (*list)[nl++] = (int32_t)i;
+  return nl;
+}
+
+double or_kick_composites(int64_t n, double *vx, double *vy, double *vz,
+                          const double *ax, const double *ay, const double *az,
+                          double h, const double *m, const int32_t *comp_root) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (comp_root[i] >= 0) continue;
+    vx[i] += ax[i] * h; vy[i] += ay[i] * h; vz[i] += az[i] * h;
+  }
+  int32_t *list;
+  int64_t nl = composite_list(n, comp_root, &list);
+  double E = 0.0;
+  for (int64_t q = 0; q < nl; ++q) {
+    const int32_t r = list[q];
+    if (comp_root[r] != r) continue;
+    double M = 0.0, A[3] = {0, 0, 0};
+    for (int64_t u = 0; u < nl; ++u) {
+      const int32_t l = list[u];
+      if (comp_root[l] != r) continue;
+      M += m[l];
+      A[0] += m[l] * ax[l]; A[1] += m[l] * ay[l]; A[2] += m[l] * az[l];
+    }
+    const double ac[3] = {A[0] / M, A[1] / M, A[2] / M};
+    double Es = 0.0;
+    for (int64_t u = 0; u < nl; ++u) {
+      const int32_t l = list[u];
+      if (comp_root[l] != r) continue;
+      vx[l] += ac[0] * h; vy[l] += ac[1] * h; vz[l] += ac[2] * h;
+      const double dx = (ax[l] - ac[0]) * h, dy = (ay[l] - ac[1]) * h, dz = (az[l] - ac[2]) * h;
+      Es += 0.5 * m[l] * (dx * dx + dy * dy + dz * dz);
+    }
+    E += Es;
+  }
+  free(list);
+  return E;
+}
+
+/* Procedure step 9: each composite becomes one particle at its lowest index:*/
+/* mass sum_l m_l, physical radius (sum_l R_l^3)^(1/3) (reading: volume is   */
+/* kept, all bodies having one density), position and velocity those of its */
+/* members (identical after the kick above).  The other members are removed */
+/* and the survivors keep their order: new_index[i] = i's new index or -1.   */
+/* Returns the new particle count.  r_out and r_search are carried along;    */
+/* the caller recomputes them (and the soft force) afterwards.               */
+int64_t or_merge(int64_t n, double *x, double *y, double *z, double *vx, double *vy,
+                 double *vz, double *m, double *rp, double *r_out, double *r_search,
+                 const int32_t *comp_root, int32_t *new_index) {
+  int32_t *list;
+  int64_t nl = composite_list(n, comp_root, &list);
+  for (int64_t q = 0; q < nl; ++q) {
+    const int32_t r = list[q];
+    if (comp_root[r] != r) continue;
+    double M = 0.0, V = 0.0;
+    for (int64_t u = 0; u < nl; ++u) {
+      const int32_t l = list[u];
+      if (comp_root[l] != r) continue;
+      M += m[l];
+      V += rp[l] * rp[l] * rp[l];
+    }
+    m[r] = M;
+    rp[r] = cbrt(V);
+  }
+  free(list);
+  int64_t k = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (comp_root[i] >= 0 && comp_root[i] != i) { new_index[i] = -1; continue; }
+    new_index[i] = (int32_t)k;
+    x[k] = x[i]; y[k] = y[i]; z[k] = z[i]; vx[k] = vx[i]; vy[k] = vy[i]; vz[k] = vz[i];
+    m[k] = m[i]; rp[k] = rp[i]; r_out[k] = r_out[i]; r_search[k] = r_search[i];
+    ++k;
+  }
+  return k;
 }
 
 /* ========================================================================= */

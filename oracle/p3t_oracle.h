@@ -29,6 +29,8 @@ typedef struct {
   double rs0, rs1, rs2, rs3; /* R~search,0..3 (Eqs. rsearch, rsearch1)           */
   double theta;         /* Barnes-Hut opening angle                              */
   double eta, eta0;     /* Hermite accuracy parameters (Sec. 3.1)                */
+  double f_radius;      /* radius enhancement factor f of the collision test     */
+                        /* (Sec. 2.4.1; the paper uses 1); 0: no collisions      */
   int32_t leaf_size;    /* maximum particles per leaf / target group             */
   int32_t precision;    /* unused by the oracle (always FP64)                    */
   int32_t vran_bins;    /* radial bins for v_ran; 0 = clamp(N/1000, 1, 1024)     */
@@ -103,8 +105,9 @@ void or_hard_acc_jerk(int64_t nc, const double *x, const double *y,
                       double jerk[3]);
 int or_hermite_cluster(int64_t nc, const int32_t *members, double *x, double *y,
                        double *z, double *vx, double *vy, double *vz,
-                       const double *m, const double *r_out, const or_params *p,
-                       double dt, int64_t *n_steps);
+                       const double *m, const double *r_out, const double *r_phys,
+                       const or_params *p, double dt, int64_t *n_steps,
+                       int32_t *root_out, double *e_disp);
 
 /* ---- row a9: Kepler drift of isolated particles --------------------------- */
 int or_kepler_drift(int64_t n, const int32_t *idx, double *x, double *y,
@@ -112,12 +115,23 @@ int or_kepler_drift(int64_t n, const int32_t *idx, double *x, double *y,
                     double mu);
 
 /* ---- rows a8+a9 together: the hard part of one soft step ------------------ */
+/* r_phys: physical radii (NULL or f_radius == 0: no collisions); comp_root:   */
+/* n entries (or NULL), lowest member of each particle's composite or -1;     */
+/* e_hard: energy dissipated by the collisions.                               */
 int or_hard_step(int64_t n, double *x, double *y, double *z, double *vx,
                  double *vy, double *vz, const double *m, const double *r_out,
-                 const or_params *p, double dt, int64_t n_single,
-                 const int32_t *singles, int64_t n_clusters,
+                 const double *r_phys, const or_params *p, double dt,
+                 int64_t n_single, const int32_t *singles, int64_t n_clusters,
                  const int64_t *cl_off, const int32_t *cl_mem,
-                 int64_t *n_hermite_steps);
+                 int64_t *n_hermite_steps, int32_t *comp_root, double *e_hard);
+
+/* ---- row f4: composite kick and merge (Sec. 2.4.1, procedure step 9) ------ */
+double or_kick_composites(int64_t n, double *vx, double *vy, double *vz,
+                          const double *ax, const double *ay, const double *az,
+                          double h, const double *m, const int32_t *comp_root);
+int64_t or_merge(int64_t n, double *x, double *y, double *z, double *vx, double *vy,
+                 double *vz, double *m, double *r_phys, double *r_out,
+                 double *r_search, const int32_t *comp_root, int32_t *new_index);
 
 /* ---- row a10: total energy (Eqs. soft + hard with W + (1-W) = 1) ---------- */
 void or_energy(int64_t n, const double *x, const double *y, const double *z,

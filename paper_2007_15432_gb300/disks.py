@@ -147,3 +147,14 @@ def wide_power_law(n=1_000_000, seed=1003, n_proto=20, m1=1e-12, m2=1e-8,
 
 def copy_state(s):
     return {k: np.array(s[k], dtype=np.float64, copy=True) for k in KEYS}
+
+
+AU_CM = 1.495978707e13      # IAU 2012 astronomical unit
+MSUN_G = 1.98847e33         # solar mass (IAU 2015 nominal G M_sun / G)
+
+
+def physical_radius(m, rho_cgs=2.0):
+    """Radius of a uniform sphere of mass m (solar masses) and density
+    rho_cgs (g cm^-3) in au: the paper's bodies have 2 g cm^-3 (Sec. 3.1)."""
+    rho = rho_cgs * AU_CM**3 / MSUN_G
+    return np.cbrt(3.0 * np.asarray(m, dtype=np.float64) / (4.0 * np.pi * rho))
