@@ -72,6 +72,9 @@ typedef struct {
                       direct summation                                        */
   double eta;      /* Hermite accuracy parameter (Sec. 3.1: 0.01)             */
   double eta0;     /* Hermite first-step parameter (Sec. 3.1: 0.1 eta)        */
+  double f_radius; /* collision radius factor f (Sec. 2.4.1: two particles
+                      collide when r_ij < f (R_p,i + R_p,j); the paper uses
+                      1); 0 = no collisions.  Collisions also need r_phys. */
   int32_t leaf_size; /* max particles per leaf = per target group, 1..32      */
   int32_t precision; /* P3T_FP64 or P3T_MIXED                                  */
   int32_t vran_bins; /* radial bins for v_ran; 0 = clamp(N/1000, 1, 1024)      */
@@ -89,6 +92,9 @@ typedef struct {
   double *r_out, *r_search;        /* cut-off and search radii, n each; written
                                       by p3t_cutoffs (or p3t_build_tree with
                                       update_cutoffs = 1), read by the rest   */
+  double *r_phys;                  /* physical radii R_p, n, or NULL (no
+                                      collisions); read by p3t_hard_step,
+                                      written by p3t_merge                    */
 } p3t_particles;
 
 /* ---- neighbour clusters: library-owned device views ---------------------- */
@@ -207,14 +213,40 @@ int p3t_neighbours(p3t_ctx *ctx, const p3t_particles *p, int64_t *nb_off,
  * Kepler orbit about M_* (universal variables, Newton-Raphson).  Positions and
  * velocities of p are updated in place.  cl: views from p3t_neighbours or
  * caller-built device arrays of the same layout.  n_steps: NULL or a device
- * uint64 overwritten with the number of Hermite particle-steps. */
+ * uint64 overwritten with the number of Hermite particle-steps.
+ * Perfect accretion (Sec. 2.4.1), with f_radius > 0 and p->r_phys set: at
+ * every force evaluation of the block steps a member that touches another
+ * (r_ij < f (R_p,i + R_p,j)) joins it in a composite that moves as one body
+ * (centre-of-mass position and velocity, mass-weighted mean hard force, a
+ * fresh eta0 step); the members stay separate particles, recorded in the
+ * context for the second p3t_kick and p3t_merge, which must follow before
+ * the next p3t_hard_step. */
 int p3t_hard_step(p3t_ctx *ctx, p3t_particles *p, const p3t_clusters *cl,
                   double dt, uint64_t *n_steps, void *stream);
 
 /* Row a7 -- soft kick (procedure steps 3 and 8): v += a * h, h usually
- * dt_soft / 2.  ax, ay, az: n doubles each, caller order. */
+ * dt_soft / 2.  ax, ay, az: n doubles each, caller order.  Members of a
+ * composite formed by the last p3t_hard_step (f_radius > 0) are kicked with
+ * the composite's mass-weighted mean acceleration (Sec. 2.4.1). */
 int p3t_kick(p3t_ctx *ctx, p3t_particles *p, const double *ax, const double *ay,
              const double *az, double h, void *stream);
+
+/* Procedure step 9 for collisions (Sec. 2.4.1; row f4 beyond the soft step):
+ * replaces every composite formed by the last p3t_hard_step by one particle
+ * at the lowest index of its members, with mass sum m_l, physical radius
+ * (sum R_l^3)^(1/3) (one density for all bodies) and the members' common
+ * position and velocity (call after the second p3t_kick).  The other members
+ * are removed from the ten particle arrays, the survivors keep their order,
+ * and p->n is set to the new count.  new_index: NULL or device int32[old n],
+ * each particle's new index or -1.  e_disp: NULL or host double[2], the
+ * energy dissipated since the last merge {in the hard part (Eq. edisphard,
+ * changeover functions replaced by unity, the cluster standing for the
+ * neighbour lists), by the averaged kick (E_disp,Soft)}.  n_merged: NULL or
+ * host, number of particles removed.  Synchronises `stream`; not capturable.
+ * After a merge the caller recomputes the cut-off radii, the tree, the soft
+ * force and the neighbours (procedure step 9). */
+int p3t_merge(p3t_ctx *ctx, p3t_particles *p, int32_t *new_index, double *e_disp,
+              int64_t *n_merged, void *stream);
 
 /* Row a10 -- total energy (Eqs. soft and hard; W + (1 - W) = 1 makes it the
  * Newtonian energy): out = device double[4] {E, kinetic, star potential,

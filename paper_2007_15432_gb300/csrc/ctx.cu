@@ -40,6 +40,7 @@ bool params_ok(const p3t_params *p) {
   if (p->precision != P3T_FP64 && p->precision != P3T_MIXED) return false;
   if (p->vran_bins < 0 || p->vran_bins > 4096) return false;
   if (p->group_size < 0 || p->group_size > 64) return false;
+  if (!(p->f_radius >= 0.0)) return false;
   return true;
 }
 
@@ -80,6 +81,8 @@ void free_particle_buffers(p3t_ctx *c) {
   c->cl_mem = nullptr;
   dfree(c->mkeys); dfree(c->mkeys_alt); dfree(c->mvals); dfree(c->mvals_alt);
   dfree(c->hw); dfree(c->ht); dfree(c->hl);
+  dfree(c->coll_ent); dfree(c->coll_rec); dfree(c->coll_rec_e); dfree(c->coll_esoft);
+  dfree(c->coll_slot);
   c->cap = 0;
   c->have_tree = c->have_cand = false;
 }
@@ -124,7 +127,14 @@ int reserve(p3t_ctx *c, int64_t n, int64_t cand_cap) {
   ok &= dalloc(c->flag, 4 * N) && dalloc(c->pos, 4 * N);
   ok &= dalloc(c->singles, N) && dalloc(c->cl_off, N + 1);
   ok &= dalloc(c->mkeys, N) && dalloc(c->mkeys_alt, N) && dalloc(c->mvals, N) && dalloc(c->mvals_alt, N);
-  ok &= dalloc(c->hw, 20 * N) && dalloc(c->ht, N) && dalloc(c->hl, N);
+  ok &= dalloc(c->hw, 33 * N) && dalloc(c->ht, N) && dalloc(c->hl, 6 * N);
+  ok &= dalloc(c->coll_ent, N) && dalloc(c->coll_rec, N / 2 + 1) && dalloc(c->coll_rec_e, N / 2 + 1);
+  ok &= dalloc(c->coll_esoft, N) && dalloc(c->coll_slot, N);
+  // no composites: every slot -1, empty list (composites pending from a
+  // smaller context are dropped with it)
+  if (ok) ok = cudaMemset(c->coll_slot, 0xff, sizeof(int32_t) * N) == cudaSuccess &&
+               cudaMemset(c->coll_ctr, 0, sizeof(unsigned long long)) == cudaSuccess &&
+               cudaDeviceSynchronize() == cudaSuccess;
   if (!ok) {
     free_particle_buffers(c);
     cudaGetLastError();
@@ -164,14 +174,16 @@ int p3t_create(p3t_ctx **ctx, const p3t_params *p, int device) {
     return P3T_ERR_CUDA;
   }
   bool ok = dalloc(c->status, 1) && dalloc(c->box, 4) && dalloc(c->box_bits, 6) &&
-            dalloc(c->counters, 16) && dalloc(c->cl_counts, 4) && dalloc(c->hsteps, 1) && dalloc(c->hcursor, 1) &&
+            dalloc(c->counters, 24) && dalloc(c->cl_counts, 4) && dalloc(c->hsteps, 1) && dalloc(c->hcursor, 2) &&
+            dalloc(c->coll_ctr, 1) &&
             dalloc(c->epart, 8192) && dalloc(c->scan_part, 1025) && dalloc(c->bh_table, 32);
   for (int q = 0; q < 2 && ok; ++q)
     ok = cudaStreamCreateWithFlags(&c->aux[q], cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->ev_join[q], cudaEventDisableTiming) == cudaSuccess;
   if (ok) ok = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
   if (ok) ok = cudaMemset(c->status, 0, sizeof(DevStatus)) == cudaSuccess &&
-               cudaMemset(c->counters, 0, 16 * sizeof(int64_t)) == cudaSuccess &&
+               cudaMemset(c->counters, 0, 24 * sizeof(int64_t)) == cudaSuccess &&
+               cudaMemset(c->coll_ctr, 0, sizeof(unsigned long long)) == cudaSuccess &&
                cudaMemset(c->cl_counts, 0, 4 * sizeof(int64_t)) == cudaSuccess;
   if (!ok) {
     p3t_destroy(c);
@@ -189,6 +201,7 @@ void p3t_destroy(p3t_ctx *c) {
   free_particle_buffers(c);
   dfree(c->status); dfree(c->box); dfree(c->box_bits); dfree(c->counters);
   dfree(c->cl_counts); dfree(c->hsteps); dfree(c->hcursor); dfree(c->epart);
+  dfree(c->coll_ctr);
   dfree(c->scan_part);
   dfree(c->bh_table);
   for (int q = 0; q < 2; ++q) {
@@ -298,6 +311,17 @@ int p3t_kick(p3t_ctx *c, p3t_particles *p, const double *ax, const double *ay,
   if (p->n > 0 && (!ax || !ay || !az)) return P3T_ERR_INVALID;
   DeviceGuard g(c->device);
   return p3t_run_kick(c, p, ax, ay, az, h, (cudaStream_t)stream);
+}
+
+int p3t_merge(p3t_ctx *c, p3t_particles *p, int32_t *new_index, double *e_disp,
+              int64_t *n_merged, void *stream) {
+  if (!c || !particles_ok(p)) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  if (p->n > c->cap) return P3T_ERR_INVALID;
+  const int64_t n0 = p->n;
+  int rc = p3t_run_merge(c, p, new_index, e_disp, n_merged, (cudaStream_t)stream);
+  if (rc == P3T_OK && p->n != n0) c->have_tree = c->have_cand = false;
+  return rc;
 }
 
 int p3t_energy(p3t_ctx *c, const p3t_particles *p, double *out, void *stream) {

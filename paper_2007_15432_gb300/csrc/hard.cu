@@ -13,14 +13,44 @@ constexpr int kBlock = 256;
 constexpr int64_t kHermiteIterLimit = 1 << 24;  // block steps per cluster
 
 // ---- row a7: soft kick (procedure steps 3 and 8) ----------------------------
+// Members of a composite formed by the last hard step (row f4, Sec. 2.4.1;
+// slot[i] >= 0, its entry in ent) are kicked with the composite's mass-
+// weighted mean acceleration sum_l m_l a_l / sum_l m_l (ascending l); the
+// composite's lowest member records the dissipation sum_l m_l |h (a_l -
+// a_c)|^2 / 2 at its entry.
 __global__ void k_kick(int64_t n, double *vx, double *vy, double *vz,
                        const double *ax, const double *ay, const double *az,
-                       double h) {
+                       double h, const int32_t *slot, const int4 *ent, const double *m,
+                       double *esoft) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    vx[i] += ax[i] * h;
-    vy[i] += ay[i] * h;
-    vz[i] += az[i] * h;
+    const int32_t s = slot ? slot[i] : -1;
+    if (s < 0) {
+      vx[i] += ax[i] * h;
+      vy[i] += ay[i] * h;
+      vz[i] += az[i] * h;
+      continue;
+    }
+    const int4 e = ent[s];
+    double M = 0.0, A[3] = {0.0, 0.0, 0.0};
+    for (int l = e.z; l < e.w; ++l) {
+      const int q = ent[l].x;
+      M += m[q];
+      A[0] += m[q] * ax[q]; A[1] += m[q] * ay[q]; A[2] += m[q] * az[q];
+    }
+    const double ac[3] = {A[0] / M, A[1] / M, A[2] / M};
+    vx[i] += ac[0] * h;
+    vy[i] += ac[1] * h;
+    vz[i] += ac[2] * h;
+    if (e.x == e.y) {
+      double Es = 0.0;
+      for (int l = e.z; l < e.w; ++l) {
+        const int q = ent[l].x;
+        const double dx = (ax[q] - ac[0]) * h, dy = (ay[q] - ac[1]) * h, dz = (az[q] - ac[2]) * h;
+        Es += 0.5 * m[q] * (dx * dx + dy * dy + dz * dz);
+      }
+      esoft[s] = Es;
+    }
   }
 }
 
@@ -122,70 +152,124 @@ __global__ void k_kepler(const int64_t *d_nsingle, const int32_t *singles,
   }
 }
 
-// ---- row a8: Hermite-4 with block steps, one warp per cluster ---------------
-struct HWork {
-  double *x, *y, *z, *vx, *vy, *vz;        // state at the member's own time
-  double *px, *py, *pz, *pvx, *pvy, *pvz;  // predicted to the block time
-  double *ax, *ay, *az, *jx, *jy, *jz;     // a, jerk at the member's own time
-  double *m, *ro;
-  int64_t *t;                              // time, units of dt / 2^40
-  int32_t *lvl;                            // step = dt / 2^lvl
+// ---- row a8 (+ f4): Hermite-4 with block steps, one 128-thread block per ----
+// cluster.  Work items (member components, or (active member, source) terms)
+// are dealt round-robin over the block's four warps, so one cluster keeps the
+// FP64 pipes of all four SM sub-partitions busy: on this part a warp
+// instruction of FP64 occupies its sub-partition's pipe for ~64 cycles, and a
+// cluster's block steps are a serial chain.  Each active member's force is
+// the sum, in the fixed order star term first then sources in ascending
+// index, of terms computed in parallel (clusters of up to kHMax members,
+// state in shared memory) or by one thread per member (larger clusters,
+// state in a global workspace).
+//
+// Perfect accretion (row f4, Sec. 2.4.1; on when f_radius > 0 and physical
+// radii are given): at every force evaluation each evaluated member records
+// the lowest-index member outside its composite that it touches, r < f (R_k
+// + R_j).  After the correction the touching members (with the composites
+// they belong to) become one composite: centre-of-mass position and velocity
+// at the block time, hard force and jerk the mass-weighted mean over the
+// composite with its inner pairs left out, a first step eta0 |a| / |j|.  The
+// dissipated energy is the change of the affected members' kinetic, star and
+// pair energy (changeover functions replaced by unity, the cluster standing
+// for the neighbours).  One thread does this bookkeeping in a fixed order;
+// collisions are rare.
+constexpr int kHB = 128;
+constexpr int kHMax = 128;
+constexpr int32_t kNone = 0x7fffffff;  // no collision partner
+
+struct HSmall {  // a cluster of <= kHMax members
+  double x[3][kHMax], v[3][kHMax], a[3][kHMax], j[3][kHMax];
+  double p[3][kHMax], pv[3][kHMax];
+  double a1[3][kHMax], j1[3][kHMax], a2e[3][kHMax], a3[3][kHMax];
+  double m[kHMax], iro[kHMax], rp[kHMax];
+  double T[kHMax + 1][6];  // one batch: B members x (nc + 1) terms, at most kHMax + 1
+  int64_t t[kHMax];
+  int32_t lvl[kHMax], act[kHMax], set[kHMax], nset[kHMax], partner[kHMax], chg[kHMax];
 };
 
-// hard acceleration and jerk of member k (Eq. hardforce): star term, then the
-// (1 - K) pair terms over the other members in ascending order; one
-// reciprocal square root per pair, 1/max(r_out) taken as min(1/r_out)
-__device__ void hard_acc_jerk(int nc, const double *x, const double *y,
-                              const double *z, const double *vx, const double *vy,
-                              const double *vz, const double *m, const double *ro,
-                              const p3t_params &prm, double i1mg, int k, double acc[3],
-                              double jerk[3]) {
-  double ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0;
-  {
-    const double r2 = x[k] * x[k] + y[k] * y[k] + z[k] * z[k];
-    const double rinv = 1.0 / sqrt(r2);
-    const double rinv2 = rinv * rinv;
-    const double f = prm.G * prm.m_star * (rinv2 * rinv);
-    const double rv = x[k] * vx[k] + y[k] * vy[k] + z[k] * vz[k];
-    ax -= f * x[k]; ay -= f * y[k]; az -= f * z[k];
-    const double c = 3.0 * rv * rinv2;
-    jx -= f * (vx[k] - c * x[k]);
-    jy -= f * (vy[k] - c * y[k]);
-    jz -= f * (vz[k] - c * z[k]);
-  }
-  const double irok = 1.0 / ro[k];
-  for (int j = 0; j < nc; ++j) {
-    if (j == k) continue;
-    const double rx = x[k] - x[j], ry = y[k] - y[j], rz = z[k] - z[j];
-    const double ux = vx[k] - vx[j], uy = vy[k] - vy[j], uz = vz[k] - vz[j];
-    const double r2 = rx * rx + ry * ry + rz * rz;
-    if (r2 == 0.0) continue;
-    const double rinv = 1.0 / sqrt(r2);
-    const double r = r2 * rinv;
-    const double irj = 1.0 / ro[j];
-    const double irot = irok < irj ? irok : irj;
-    const double yv = r * irot;
-    if (yv >= 1.0) continue;
-    double w = 1.0, dK = 0.0;
-    if (yv > prm.gamma) {
-      const double xs = (yv - prm.gamma) * i1mg;
-      const double x2 = xs * xs, x3 = x2 * xs, x4 = x2 * x2, u = 1.0 - xs;
-      w = 1.0 - x4 * (35.0 - 84.0 * xs + 70.0 * x2 - 20.0 * x3);
-      dK = 140.0 * x3 * (u * u * u) * i1mg;
-    }
-    const double rinv2 = rinv * rinv;
-    const double g3 = prm.G * m[j] * (rinv2 * rinv);
-    const double f = g3 * w;
-    const double rv = rx * ux + ry * uy + rz * uz;
-    ax -= f * rx; ay -= f * ry; az -= f * rz;
-    const double c = 3.0 * w * rv * rinv2 + dK * rv * rinv * irot;
-    jx -= g3 * (w * ux - c * rx);
-    jy -= g3 * (w * uy - c * ry);
-    jz -= g3 * (w * uz - c * rz);
-  }
-  acc[0] = ax; acc[1] = ay; acc[2] = az;
-  jerk[0] = jx; jerk[1] = jy; jerk[2] = jz;
-}
+static_assert(sizeof(HSmall) <= 48 * 1024, "HSmall must fit the default dynamic shared memory");
+
+struct HCtl {  // per-block control, shared memory
+  int64_t red[2][4];
+  int32_t wcount[4];
+  int64_t cluster;
+  int nact, any, ncomp;
+  double edisp;
+};
+
+struct SmallView {
+  HSmall *S;
+  static constexpr bool kBig = false;
+  __device__ double &x(int q, int k) const { return S->x[q][k]; }
+  __device__ double &v(int q, int k) const { return S->v[q][k]; }
+  __device__ double &a(int q, int k) const { return S->a[q][k]; }
+  __device__ double &j(int q, int k) const { return S->j[q][k]; }
+  __device__ double &p(int q, int k) const { return S->p[q][k]; }
+  __device__ double &pv(int q, int k) const { return S->pv[q][k]; }
+  __device__ double &a1(int q, int k) const { return S->a1[q][k]; }
+  __device__ double &j1(int q, int k) const { return S->j1[q][k]; }
+  __device__ double &a2e(int q, int k) const { return S->a2e[q][k]; }
+  __device__ double &a3(int q, int k) const { return S->a3[q][k]; }
+  __device__ double &m(int k) const { return S->m[k]; }
+  __device__ double &iro(int k) const { return S->iro[k]; }
+  __device__ double &rp(int k) const { return S->rp[k]; }
+  __device__ int64_t &t(int k) const { return S->t[k]; }
+  __device__ int32_t &lvl(int k) const { return S->lvl[k]; }
+  __device__ int32_t &act(int k) const { return S->act[k]; }
+  __device__ int32_t &set(int k) const { return S->set[k]; }
+  __device__ int32_t &nset(int k) const { return S->nset[k]; }
+  __device__ int32_t &partner(int k) const { return S->partner[k]; }
+  __device__ int32_t &chg(int k) const { return S->chg[k]; }
+};
+
+// global workspace of the large clusters: 33 double, 1 int64 and 6 int32
+// arrays of cap entries, a cluster's members at its member offset
+struct HBig {
+  double *d;
+  int64_t *t;
+  int32_t *i;
+  int64_t cap;
+};
+struct BigView {
+  double *d;
+  int64_t *tt;
+  int32_t *ii;
+  int64_t cap, off;
+  static constexpr bool kBig = true;
+  __device__ double &D(int arr, int k) const { return d[arr * cap + off + k]; }
+  __device__ int32_t &I(int arr, int k) const { return ii[arr * cap + off + k]; }
+  __device__ double &x(int q, int k) const { return D(q, k); }
+  __device__ double &v(int q, int k) const { return D(3 + q, k); }
+  __device__ double &a(int q, int k) const { return D(6 + q, k); }
+  __device__ double &j(int q, int k) const { return D(9 + q, k); }
+  __device__ double &p(int q, int k) const { return D(12 + q, k); }
+  __device__ double &pv(int q, int k) const { return D(15 + q, k); }
+  __device__ double &a1(int q, int k) const { return D(18 + q, k); }
+  __device__ double &j1(int q, int k) const { return D(21 + q, k); }
+  __device__ double &a2e(int q, int k) const { return D(24 + q, k); }
+  __device__ double &a3(int q, int k) const { return D(27 + q, k); }
+  __device__ double &m(int k) const { return D(30, k); }
+  __device__ double &iro(int k) const { return D(31, k); }
+  __device__ double &rp(int k) const { return D(32, k); }
+  __device__ int64_t &t(int k) const { return tt[off + k]; }
+  __device__ int32_t &lvl(int k) const { return I(0, k); }
+  __device__ int32_t &act(int k) const { return I(1, k); }
+  __device__ int32_t &set(int k) const { return I(2, k); }
+  __device__ int32_t &nset(int k) const { return I(3, k); }
+  __device__ int32_t &partner(int k) const { return I(4, k); }
+  __device__ int32_t &chg(int k) const { return I(5, k); }
+};
+
+// composites handed to the kick and the merge (row f4)
+struct CollOut {
+  unsigned long long *ctr;  // (records << 32) | entries
+  int4 *ent;                // {particle, lowest member of its composite, lo, hi}
+  int4 *rec;                // {cluster label, first entry, entries, 0}
+  double *rec_e;            // energy dissipated in the cluster
+  int32_t *slot;            // particle -> its entry, or -1
+  int64_t ent_cap, rec_cap;
+};
 
 // The step estimates only choose a power-of-two step: formed in FP32 from
 // components scaled by an exact power of two 2^k (j by s, a2 by s^2, a3 by
@@ -217,155 +301,30 @@ __device__ __forceinline__ int quantise_level(double dt_des, double dt, int prev
   return lvl > P3T_KMAX ? P3T_KMAX : lvl;
 }
 
-// Block-step integration of one cluster over [0, dt] by a group of NL lanes
-// (NL = 32: a warp per cluster; NL = 4: eight small clusters per warp).
-// Members are taken k = lane, lane + NL, ...; the arithmetic per member does
-// not depend on NL.
-template <int NL>
-__device__ void integrate_cluster(int64_t off, int nc, const int32_t *cl_mem,
-                                  const p3t_particles &p, const HWork &w,
-                                  const p3t_params &prm, double dt, int lane,
-                                  unsigned mask, unsigned long long &steps,
-                                  bool &underflow, DevStatus *st) {
-  const int64_t T = ((int64_t)1) << P3T_KMAX;
-  const double unit = ldexp(dt, -P3T_KMAX);
-  const double i1mg = 1.0 / (1.0 - prm.gamma);
-  double *x = w.x + off, *y = w.y + off, *z = w.z + off;
-  double *vx = w.vx + off, *vy = w.vy + off, *vz = w.vz + off;
-  double *px = w.px + off, *py = w.py + off, *pz = w.pz + off;
-  double *pvx = w.pvx + off, *pvy = w.pvy + off, *pvz = w.pvz + off;
-  double *ax = w.ax + off, *ay = w.ay + off, *az = w.az + off;
-  double *jx = w.jx + off, *jy = w.jy + off, *jz = w.jz + off;
-  double *m = w.m + off, *ro = w.ro + off;
-  int64_t *t = w.t + off;
-  int32_t *lvl = w.lvl + off;
-  for (int k = lane; k < nc; k += NL) {
-    const int32_t i = cl_mem[off + k];
-    x[k] = p.x[i]; y[k] = p.y[i]; z[k] = p.z[i];
-    vx[k] = p.vx[i]; vy[k] = p.vy[i]; vz[k] = p.vz[i];
-    m[k] = p.m[i]; ro[k] = p.r_out[i];
-  }
-  __syncwarp(mask);
-  for (int k = lane; k < nc; k += NL) {
-    double a[3], j[3];
-    hard_acc_jerk(nc, x, y, z, vx, vy, vz, m, ro, prm, i1mg, k, a, j);
-    ax[k] = a[0]; ay[k] = a[1]; az[k] = a[2];
-    jx[k] = j[0]; jy[k] = j[1]; jz[k] = j[2];
-    const int e = ilogb(dt);  // eta0 |a| / |j| = (eta0 |a| / |j s|) s
-    const float an = norm3f(a[0], a[1], a[2], 0), jn = norm3f(j[0], j[1], j[2], e);
-    const double dtd = jn > 0.0f ? ldexp((double)((float)prm.eta0 * an / jn), e) : dt;
-    t[k] = 0;
-    lvl[k] = quantise_level(dtd, dt, 0, 0, underflow);
-  }
-  __syncwarp(mask);
-  int64_t iter = 0;
-  for (;;) {
-    int64_t tn = T, tmin = T;
-    for (int k = lane; k < nc; k += NL) {
-      const int64_t e = t[k] + (T >> lvl[k]);
-      tn = e < tn ? e : tn;
-      tmin = t[k] < tmin ? t[k] : tmin;
-    }
-#pragma unroll
-    for (int o = NL / 2; o > 0; o >>= 1) {
-      const int64_t a = __shfl_xor_sync(mask, tn, o);
-      const int64_t b = __shfl_xor_sync(mask, tmin, o);
-      tn = a < tn ? a : tn;
-      tmin = b < tmin ? b : tmin;
-    }
-    if (tmin >= T) break;
-    if (++iter > kHermiteIterLimit) {
-      if (lane == 0) dev_fail(st, P3T_ERR_TIMEOUT, 61, 0);
-      break;
-    }
-    // predict every member to the block time
-    for (int k = lane; k < nc; k += NL) {
-      const double D = (double)(tn - t[k]) * unit;
-      const double D2 = D * D, D3 = D2 * D;
-      px[k] = x[k] + vx[k] * D + ax[k] * D2 * 0.5 + jx[k] * D3 * (1.0 / 6.0);
-      py[k] = y[k] + vy[k] * D + ay[k] * D2 * 0.5 + jy[k] * D3 * (1.0 / 6.0);
-      pz[k] = z[k] + vz[k] * D + az[k] * D2 * 0.5 + jz[k] * D3 * (1.0 / 6.0);
-      pvx[k] = vx[k] + ax[k] * D + jx[k] * D2 * 0.5;
-      pvy[k] = vy[k] + ay[k] * D + jy[k] * D2 * 0.5;
-      pvz[k] = vz[k] + az[k] * D + jz[k] * D2 * 0.5;
-    }
-    __syncwarp(mask);
-    // evaluate and correct the active members
-    for (int k = lane; k < nc; k += NL) {
-      if (t[k] + (T >> lvl[k]) != tn) continue;
-      double a1[3], j1[3];
-      hard_acc_jerk(nc, px, py, pz, pvx, pvy, pvz, m, ro, prm, i1mg, k, a1, j1);
-      const double D = (double)(T >> lvl[k]) * unit;
-      const double D2 = D * D, D3 = D2 * D, D4 = D3 * D, D5 = D4 * D;
-      const double iD = 1.0 / D, iD2 = iD * iD, iD3 = iD2 * iD;
-      const double a0[3] = {ax[k], ay[k], az[k]}, j0[3] = {jx[k], jy[k], jz[k]};
-      double A2[3], A3[3], A2e[3];
-      for (int q = 0; q < 3; ++q) {
-        const double da = a0[q] - a1[q];
-        A2[q] = (-6.0 * da - D * (4.0 * j0[q] + 2.0 * j1[q])) * iD2;
-        A3[q] = (12.0 * da + 6.0 * D * (j0[q] + j1[q])) * iD3;
-        A2e[q] = A2[q] + D * A3[q];
-      }
-      x[k] = px[k] + A2[0] * D4 * (1.0 / 24.0) + A3[0] * D5 * (1.0 / 120.0);
-      y[k] = py[k] + A2[1] * D4 * (1.0 / 24.0) + A3[1] * D5 * (1.0 / 120.0);
-      z[k] = pz[k] + A2[2] * D4 * (1.0 / 24.0) + A3[2] * D5 * (1.0 / 120.0);
-      vx[k] = pvx[k] + A2[0] * D3 * (1.0 / 6.0) + A3[0] * D4 * (1.0 / 24.0);
-      vy[k] = pvy[k] + A2[1] * D3 * (1.0 / 6.0) + A3[1] * D4 * (1.0 / 24.0);
-      vz[k] = pvz[k] + A2[2] * D3 * (1.0 / 6.0) + A3[2] * D4 * (1.0 / 24.0);
-      ax[k] = a1[0]; ay[k] = a1[1]; az[k] = a1[2];
-      jx[k] = j1[0]; jy[k] = j1[1]; jz[k] = j1[2];
-      const int e = ilogb(D);  // dt = sqrt(eta num_s / den_s) s
-      const float an = norm3f(a1[0], a1[1], a1[2], 0), jn = norm3f(j1[0], j1[1], j1[2], e);
-      const float a2n = norm3f(A2e[0], A2e[1], A2e[2], 2 * e);
-      const float a3n = norm3f(A3[0], A3[1], A3[2], 3 * e);
-      const float num = an * a2n + jn * jn, den = jn * a3n + a2n * a2n;
-      const double dtd = den > 0.0f ? ldexp((double)sqrtf((float)prm.eta * num / den), e) : dt;
-      t[k] = tn;
-      lvl[k] = quantise_level(dtd, dt, lvl[k], tn, underflow);
-      ++steps;
-    }
-    __syncwarp(mask);
-  }
-  for (int k = lane; k < nc; k += NL) {
-    const int32_t i = cl_mem[off + k];
-    p.x[i] = x[k]; p.y[i] = y[k]; p.z[i] = z[k];
-    p.vx[i] = vx[k]; p.vy[i] = vy[k]; p.vz[i] = vz[k];
-  }
-  __syncwarp(mask);
+// first step eta0 |a| / |j| = (eta0 |a| / |j s|) s, s = 2^e
+template <class V>
+__device__ __forceinline__ int first_level(const V &S, int k, const p3t_params &prm, double dt,
+                                           int64_t t, bool &underflow) {
+  const int e = ilogb(dt);
+  const float an = norm3f(S.a(0, k), S.a(1, k), S.a(2, k), 0);
+  const float jn = norm3f(S.j(0, k), S.j(1, k), S.j(2, k), e);
+  const double dtd = jn > 0.0f ? ldexp((double)((float)prm.eta0 * an / jn), e) : dt;
+  return quantise_level(dtd, dt, 0, t, underflow);
 }
 
-// ---- clusters of up to kHMax members: one 128-thread block per cluster ------
-// Work items (member components, or (active member, source) terms) are dealt
-// round-robin over the block's four warps, so one cluster keeps the FP64
-// pipes of all four SM sub-partitions busy: on this part a warp instruction
-// of FP64 occupies its sub-partition's pipe for ~64 cycles, and a cluster's
-// block steps are a serial chain.  Each active member's force is the sum, in
-// the fixed order star term first then sources in ascending index, of terms
-// computed in parallel.
-constexpr int kHB = 128;
-constexpr int kHMax = 128;
-
-struct HShared {
-  double x[3][kHMax], v[3][kHMax], a[3][kHMax], j[3][kHMax];
-  double p[3][kHMax], pv[3][kHMax];
-  double a1[3][kHMax], j1[3][kHMax], a2e[3][kHMax], a3[3][kHMax];
-  double m[kHMax], iro[kHMax];
-  double T[kHMax + 1][6];  // one batch: B members x (nc + 1) terms, at most kHMax + 1
-  int64_t t[kHMax];
-  int32_t lvl[kHMax], act[kHMax];
-  int64_t red[2][4];
-  int32_t wcount[4];
-  int64_t cluster;
-  int nact;
-};
-
-// term of source j (j == nc: the star) on member k, from arrays X, V
-__device__ __forceinline__ void hard_term(const HShared &S, const double (*X)[kHMax],
-                                          const double (*V)[kHMax], int nc, int k, int j,
-                                          const p3t_params &prm, double i1mg, double out[6]) {
+// term of source j (j == nc: the star) on member k at the block-time state
+// (p, pv): the (1 - K) pair force and its jerk (Eq. hardforce), one
+// reciprocal square root per pair, 1/max(r_out) taken as min(1/r_out).
+// Members of k's own composite are left out; with `detect`, hit reports
+// contact r < f (R_k + R_j).
+template <class V>
+__device__ __forceinline__ void hard_term(const V &S, int nc, int k, int j,
+                                          const p3t_params &prm, double i1mg, bool detect,
+                                          double out[6], bool &hit) {
   for (int q = 0; q < 6; ++q) out[q] = 0.0;
-  const double xk = X[0][k], yk = X[1][k], zk = X[2][k];
-  const double vxk = V[0][k], vyk = V[1][k], vzk = V[2][k];
+  hit = false;
+  const double xk = S.p(0, k), yk = S.p(1, k), zk = S.p(2, k);
+  const double vxk = S.pv(0, k), vyk = S.pv(1, k), vzk = S.pv(2, k);
   if (j == nc) {
     const double r2 = xk * xk + yk * yk + zk * zk;
     const double rinv = 1.0 / sqrt(r2);
@@ -379,14 +338,18 @@ __device__ __forceinline__ void hard_term(const HShared &S, const double (*X)[kH
     out[5] = f * (vzk - c * zk);
     return;
   }
-  if (j == k) return;
-  const double rx = xk - X[0][j], ry = yk - X[1][j], rz = zk - X[2][j];
-  const double ux = vxk - V[0][j], uy = vyk - V[1][j], uz = vzk - V[2][j];
+  if (j == k || S.set(j) == S.set(k)) return;
+  const double rx = xk - S.p(0, j), ry = yk - S.p(1, j), rz = zk - S.p(2, j);
+  const double ux = vxk - S.pv(0, j), uy = vyk - S.pv(1, j), uz = vzk - S.pv(2, j);
   const double r2 = rx * rx + ry * ry + rz * rz;
+  if (detect) {
+    const double sr = prm.f_radius * (S.rp(k) + S.rp(j));
+    hit = r2 < sr * sr;
+  }
   if (r2 == 0.0) return;
   const double rinv = 1.0 / sqrt(r2);
   const double r = r2 * rinv;
-  const double irot = S.iro[k] < S.iro[j] ? S.iro[k] : S.iro[j];
+  const double irot = S.iro(k) < S.iro(j) ? S.iro(k) : S.iro(j);
   const double yv = r * irot;
   if (yv >= 1.0) return;
   double w = 1.0, dK = 0.0;
@@ -397,7 +360,7 @@ __device__ __forceinline__ void hard_term(const HShared &S, const double (*X)[kH
     dK = 140.0 * x3 * (u * u * u) * i1mg;
   }
   const double rinv2 = rinv * rinv;
-  const double g3 = prm.G * S.m[j] * (rinv2 * rinv);
+  const double g3 = prm.G * S.m(j) * (rinv2 * rinv);
   const double f = g3 * w;
   const double rv = rx * ux + ry * uy + rz * uz;
   out[0] = f * rx; out[1] = f * ry; out[2] = f * rz;
@@ -407,27 +370,94 @@ __device__ __forceinline__ void hard_term(const HShared &S, const double (*X)[kH
   out[5] = g3 * (w * uz - c * rz);
 }
 
-// forces on the active members S.act[0..nact) from arrays X, V into a1, j1
-__device__ void block_forces(HShared &S, const double (*X)[kHMax], const double (*V)[kHMax],
-                             int nc, int nact, int item, const p3t_params &prm, double i1mg) {
-  const int per = nc + 1;
-  const int B = kHB / per > 0 ? kHB / per : 1;  // members per batch
-  for (int b0 = 0; b0 < nact; b0 += B) {
-    const int nb = min(B, nact - b0);
-    const int items = nb * per;
-    for (int i = item; i < items; i += kHB) {
-      const int bm = i / per, jj = i - bm * per;
-      hard_term(S, X, V, nc, S.act[b0 + bm], jj, prm, i1mg, S.T[i]);
+// the members with pred(k), ascending, into act[0..); returns their number
+template <class V, class Pred>
+__device__ int build_list(const V &S, HCtl &C, int nc, Pred pred) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int base = 0;
+  for (int c0 = 0; c0 < nc; c0 += kHB) {
+    const int k = c0 + tid;
+    const bool on = k < nc && pred(k);
+    const unsigned bal = __ballot_sync(0xffffffffu, on);
+    if (lane == 0) C.wcount[warp] = __popc(bal);
+    __syncthreads();
+    int off = base, tot = 0;
+    for (int q = 0; q < kHB / 32; ++q) {
+      if (q < warp) off += C.wcount[q];
+      tot += C.wcount[q];
+    }
+    if (on) S.act(off + __popc(bal & ((1u << lane) - 1u))) = k;
+    base += tot;
+    __syncthreads();
+  }
+  return base;
+}
+
+// forces on the listed members act[0..nact) from (p, pv) into (a1, j1); with
+// `detect`, each one's lowest touching partner into partner[]; then the
+// composites' mean force
+template <class V>
+__device__ void block_forces(const V &S, HCtl &C, HSmall *Sm, int nc, int nact, int item,
+                             const p3t_params &prm, double i1mg, bool detect) {
+  if constexpr (!V::kBig) {
+    const int per = nc + 1;
+    const int B = kHB / per > 0 ? kHB / per : 1;  // members per batch
+    for (int b0 = 0; b0 < nact; b0 += B) {
+      const int nb = min(B, nact - b0);
+      const int items = nb * per;
+      for (int i = item; i < items; i += kHB) {
+        const int bm = i / per, jj = i - bm * per;
+        const int k = S.act(b0 + bm);
+        bool hit;
+        hard_term(S, nc, k, jj, prm, i1mg, detect, Sm->T[i], hit);
+        if (hit) atomicMin(&S.partner(k), jj);
+      }
+      __syncthreads();
+      for (int i = item; i < nb * 6; i += kHB) {
+        const int bm = i / 6, q = i - bm * 6;
+        const int k = S.act(b0 + bm);
+        const int base = bm * per;
+        double acc = 0.0;
+        acc -= Sm->T[base + nc][q];
+        for (int jj = 0; jj < nc; ++jj) acc -= Sm->T[base + jj][q];
+        if (q < 3) S.a1(q, k) = acc; else S.j1(q - 3, k) = acc;
+      }
+      __syncthreads();
+    }
+  } else {
+    for (int b = threadIdx.x; b < nact; b += kHB) {
+      const int k = S.act(b);
+      double acc[6], out[6];
+      bool hit;
+      hard_term(S, nc, k, nc, prm, i1mg, false, out, hit);
+      for (int q = 0; q < 6; ++q) acc[q] = 0.0 - out[q];
+      for (int jj = 0; jj < nc; ++jj) {
+        hard_term(S, nc, k, jj, prm, i1mg, detect, out, hit);
+        for (int q = 0; q < 6; ++q) acc[q] -= out[q];
+        if (hit && S.partner(k) == kNone) S.partner(k) = jj;
+      }
+      for (int q = 0; q < 3; ++q) { S.a1(q, k) = acc[q]; S.j1(q, k) = acc[3 + q]; }
     }
     __syncthreads();
-    for (int i = item; i < nb * 6; i += kHB) {
-      const int bm = i / 6, q = i - bm * 6;
-      const int k = S.act[b0 + bm];
-      const int base = bm * per;
-      double acc = 0.0;
-      acc -= S.T[base + nc][q];
-      for (int jj = 0; jj < nc; ++jj) acc -= S.T[base + jj][q];
-      if (q < 3) S.a1[q][k] = acc; else S.j1[q - 3][k] = acc;
+  }
+  if (C.ncomp) {
+    // composite force: sum_l m_l a_l / sum_l m_l, ascending l (sets of >= 2)
+    for (int b = item; b < nact; b += kHB) {
+      const int r = S.act(b);
+      if (S.set(r) != r) continue;
+      int size = 0;
+      double M = 0.0, A[3] = {0, 0, 0}, J[3] = {0, 0, 0};
+      for (int l = 0; l < nc; ++l) {
+        if (S.set(l) != r) continue;
+        ++size;
+        M += S.m(l);
+        for (int q = 0; q < 3; ++q) { A[q] += S.m(l) * S.a1(q, l); J[q] += S.m(l) * S.j1(q, l); }
+      }
+      if (size < 2) continue;
+      for (int l = 0; l < nc; ++l) {
+        if (S.set(l) != r) continue;
+        for (int q = 0; q < 3; ++q) { S.a1(q, l) = A[q] / M; S.j1(q, l) = J[q] / M; }
+      }
     }
     __syncthreads();
   }
@@ -446,163 +476,283 @@ __device__ __forceinline__ int64_t block_min(int64_t v, int64_t *red4) {
   return r;
 }
 
-__global__ void __launch_bounds__(kHB) k_hermite_block(
-    const int64_t *d_ncl, const int64_t *cl_off, const int32_t *cl_mem, p3t_particles p,
-    p3t_params prm, double dt, unsigned long long *steps_out, int64_t *cursor,
-    DevStatus *st) {
-  __shared__ HShared S;
+// energy of the members with chg & 1 as far as replacing them can change it:
+// kinetic and star energy, and the pair energy of every pair with one end
+// among them (once), pairs in one set left out; state (p, pv)
+template <class V>
+__device__ double set_energy(const V &S, int nc, bool new_sets, const p3t_params &prm) {
+  double E = 0.0;
+  for (int k = 0; k < nc; ++k) {
+    if (!(S.chg(k) & 1)) continue;
+    const double vx = S.pv(0, k), vy = S.pv(1, k), vz = S.pv(2, k);
+    const double x = S.p(0, k), y = S.p(1, k), z = S.p(2, k);
+    E += 0.5 * S.m(k) * (vx * vx + vy * vy + vz * vz);
+    E -= prm.G * prm.m_star * S.m(k) / sqrt(x * x + y * y + z * z);
+  }
+  for (int k = 0; k < nc; ++k) {
+    if (!(S.chg(k) & 1)) continue;
+    const int sk = new_sets ? S.set(k) : S.nset(k);
+    for (int l = 0; l < nc; ++l) {
+      const int sl = new_sets ? S.set(l) : S.nset(l);
+      if (l == k || ((S.chg(l) & 1) && l < k) || sl == sk) continue;
+      const double dx = S.p(0, k) - S.p(0, l), dy = S.p(1, k) - S.p(1, l),
+                   dz = S.p(2, k) - S.p(2, l);
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 == 0.0) continue;
+      E -= prm.G * S.m(k) * S.m(l) / sqrt(r2);
+    }
+  }
+  return E;
+}
+
+// one thread: joins the touching members into composites at block time tn.
+// On entry (p, pv) hold every member's state at tn; nset holds the sets
+// before, set receives the sets after.
+template <class V>
+__device__ void collide_serial(const V &S, HCtl &C, int nc, int64_t tn, const p3t_params &prm) {
+  for (int k = 0; k < nc; ++k) S.nset(k) = S.set(k);
+  for (int k = 0; k < nc; ++k) {
+    if (S.partner(k) == kNone) continue;
+    const int ra = S.set(k), rb = S.set(S.partner(k));
+    const int lo = ra < rb ? ra : rb, hi = ra < rb ? rb : ra;
+    for (int l = 0; l < nc; ++l)
+      if (S.set(l) == hi) S.set(l) = lo;
+  }
+  for (int k = 0; k < nc; ++k) S.chg(k) = 0;
+  for (int k = 0; k < nc; ++k)
+    if (S.partner(k) != kNone) S.chg(S.set(k)) = 2;
+  for (int k = 0; k < nc; ++k)
+    if (S.chg(S.set(k)) & 2) S.chg(k) |= 1;
+  const double Eb = set_energy(S, nc, false, prm);  // sets before (nset)
+  for (int r = 0; r < nc; ++r) {
+    if (!(S.chg(r) & 1) || S.set(r) != r) continue;
+    double Ms = 0.0, Q[6] = {0, 0, 0, 0, 0, 0};
+    for (int l = 0; l < nc; ++l) {
+      if (S.set(l) != r) continue;
+      Ms += S.m(l);
+      for (int q = 0; q < 3; ++q) { Q[q] += S.m(l) * S.p(q, l); Q[3 + q] += S.m(l) * S.pv(q, l); }
+    }
+    for (int l = 0; l < nc; ++l) {
+      if (S.set(l) != r) continue;
+      for (int q = 0; q < 3; ++q) { S.p(q, l) = Q[q] / Ms; S.pv(q, l) = Q[3 + q] / Ms; }
+    }
+  }
+  const double Ea = set_energy(S, nc, true, prm);
+  C.edisp += Eb - Ea;
+  for (int k = 0; k < nc; ++k) {
+    if (!(S.chg(k) & 1)) continue;
+    for (int q = 0; q < 3; ++q) { S.x(q, k) = S.p(q, k); S.v(q, k) = S.pv(q, k); }
+    S.t(k) = tn;
+  }
+  C.ncomp = 1;
+}
+
+// one thread: the cluster's composites (sets of >= 2) to the global list
+template <class V>
+__device__ void emit_composites(const V &S, const HCtl &C, int nc, int64_t off,
+                                const int32_t *cl_mem, const CollOut &co, DevStatus *st) {
+  int ne = 0;
+  for (int r = 0; r < nc; ++r) {
+    if (S.set(r) != r) continue;
+    int size = 0;
+    for (int l = 0; l < nc; ++l) size += S.set(l) == r;
+    if (size >= 2) ne += size;
+  }
+  if (ne == 0) return;
+  const unsigned long long old =
+      atomicAdd(co.ctr, (1ull << 32) | (unsigned long long)ne);
+  const int64_t rec = (int64_t)(old >> 32), e0 = (int64_t)(old & 0xffffffffull);
+  if (rec >= co.rec_cap || e0 + ne > co.ent_cap) {
+    dev_fail(st, P3T_ERR_CAPACITY, 63, e0 + ne);
+    return;
+  }
+  co.rec[rec] = make_int4(cl_mem[off], (int)e0, ne, 0);
+  co.rec_e[rec] = C.edisp;
+  int e = (int)e0;
+  for (int r = 0; r < nc; ++r) {
+    if (S.set(r) != r) continue;
+    int size = 0;
+    for (int l = 0; l < nc; ++l) size += S.set(l) == r;
+    if (size < 2) continue;
+    const int lo = e, hi = e + size;
+    for (int l = 0; l < nc; ++l) {
+      if (S.set(l) != r) continue;
+      const int32_t i = cl_mem[off + l];
+      co.ent[e] = make_int4(i, cl_mem[off + r], lo, hi);
+      co.slot[i] = e;
+      ++e;
+    }
+  }
+}
+
+// block-step integration of one cluster (the whole block takes part)
+template <class V>
+__device__ void integrate_cluster(const V &S, HCtl &C, HSmall *Sm, int64_t off, int nc,
+                                  const int32_t *cl_mem, const p3t_particles &p,
+                                  const p3t_params &prm, double dt, bool coll,
+                                  const CollOut &co, unsigned long long &steps,
+                                  bool &underflow, DevStatus *st) {
   const int tid = threadIdx.x;
   const int item = (tid & 31) * (kHB / 32) + (tid >> 5);  // consecutive items -> different warps
-  const int64_t ncl = *d_ncl;
   const int64_t T = ((int64_t)1) << P3T_KMAX;
   const double unit = ldexp(dt, -P3T_KMAX);
   const double i1mg = 1.0 / (1.0 - prm.gamma);
+  for (int k = item; k < nc; k += kHB) {
+    const int32_t i = cl_mem[off + k];
+    S.x(0, k) = p.x[i]; S.x(1, k) = p.y[i]; S.x(2, k) = p.z[i];
+    S.v(0, k) = p.vx[i]; S.v(1, k) = p.vy[i]; S.v(2, k) = p.vz[i];
+    for (int q = 0; q < 3; ++q) { S.p(q, k) = S.x(q, k); S.pv(q, k) = S.v(q, k); }
+    S.m(k) = p.m[i];
+    S.iro(k) = 1.0 / p.r_out[i];
+    S.rp(k) = coll ? p.r_phys[i] : 0.0;
+    S.set(k) = k;
+    S.partner(k) = kNone;
+  }
+  if (tid == 0) { C.any = 0; C.ncomp = 0; C.edisp = 0.0; }
+  __syncthreads();
+  // initial forces of every member (the block-time state is the initial
+  // state), first steps
+  int nact = build_list(S, C, nc, [](int) { return true; });
+  block_forces(S, C, Sm, nc, nact, item, prm, i1mg, coll);
+  for (int k = item; k < nc; k += kHB) {
+    for (int q = 0; q < 3; ++q) { S.a(q, k) = S.a1(q, k); S.j(q, k) = S.j1(q, k); }
+    S.t(k) = 0;
+    S.lvl(k) = first_level(S, k, prm, dt, 0, underflow);
+    if (S.partner(k) != kNone) C.any = 1;
+  }
+  __syncthreads();
+  int64_t tn = 0, iter = 0;
+  for (;;) {
+    if (C.any) {
+      // collisions found by the last evaluation: every member's state at tn
+      for (int k = item; k < nc; k += kHB)
+        if (S.t(k) == tn)
+          for (int q = 0; q < 3; ++q) { S.p(q, k) = S.x(q, k); S.pv(q, k) = S.v(q, k); }
+      __syncthreads();
+      if (tid == 0) collide_serial(S, C, nc, tn, prm);
+      __syncthreads();
+      nact = build_list(S, C, nc, [&](int k) { return (S.chg(k) & 1) != 0; });
+      block_forces(S, C, Sm, nc, nact, item, prm, i1mg, false);
+      for (int b = item; b < nact; b += kHB) {
+        const int k = S.act(b);
+        for (int q = 0; q < 3; ++q) { S.a(q, k) = S.a1(q, k); S.j(q, k) = S.j1(q, k); }
+        S.lvl(k) = first_level(S, k, prm, dt, tn, underflow);
+      }
+      for (int k = item; k < nc; k += kHB) S.partner(k) = kNone;
+      __syncthreads();
+      if (tid == 0) C.any = 0;
+      __syncthreads();
+    }
+    int64_t e_min = T, t_min = T;
+    for (int k = tid; k < nc; k += kHB) {
+      const int64_t e = S.t(k) + (T >> S.lvl(k));
+      e_min = e < e_min ? e : e_min;
+      t_min = S.t(k) < t_min ? S.t(k) : t_min;
+    }
+    tn = block_min(e_min, C.red[0]);
+    const int64_t tmin = block_min(t_min, C.red[1]);
+    if (tmin >= T) break;
+    if (++iter > kHermiteIterLimit) {
+      if (tid == 0) dev_fail(st, P3T_ERR_TIMEOUT, 61, 0);
+      break;
+    }
+    // predict every member (component items)
+    for (int i = item; i < nc * 3; i += kHB) {
+      const int k = i / 3, q = i - 3 * k;
+      const double D = (double)(tn - S.t(k)) * unit;
+      const double D2 = D * D, D3 = D2 * D;
+      S.p(q, k) = S.x(q, k) + S.v(q, k) * D + S.a(q, k) * D2 * 0.5 + S.j(q, k) * D3 * (1.0 / 6.0);
+      S.pv(q, k) = S.v(q, k) + S.a(q, k) * D + S.j(q, k) * D2 * 0.5;
+    }
+    __syncthreads();
+    nact = build_list(S, C, nc, [&](int k) { return S.t(k) + (T >> S.lvl(k)) == tn; });
+    block_forces(S, C, Sm, nc, nact, item, prm, i1mg, coll);
+    // correct (component items of the active members)
+    for (int i = item; i < nact * 3; i += kHB) {
+      const int b = i / 3, q = i - 3 * b;
+      const int k = S.act(b);
+      const double D = (double)(T >> S.lvl(k)) * unit;
+      const double D2 = D * D, D3 = D2 * D, D4 = D3 * D, D5 = D4 * D;
+      const double iD = 1.0 / D, iD2 = iD * iD, iD3 = iD2 * iD;
+      const double da = S.a(q, k) - S.a1(q, k);
+      const double j0 = S.j(q, k), j1 = S.j1(q, k);
+      const double A2 = (-6.0 * da - D * (4.0 * j0 + 2.0 * j1)) * iD2;
+      const double A3 = (12.0 * da + 6.0 * D * (j0 + j1)) * iD3;
+      S.a2e(q, k) = A2 + D * A3;
+      S.a3(q, k) = A3;
+      S.x(q, k) = S.p(q, k) + A2 * D4 * (1.0 / 24.0) + A3 * D5 * (1.0 / 120.0);
+      S.v(q, k) = S.pv(q, k) + A2 * D3 * (1.0 / 6.0) + A3 * D4 * (1.0 / 24.0);
+      S.a(q, k) = S.a1(q, k);
+      S.j(q, k) = j1;
+    }
+    __syncthreads();
+    // new steps of the active members
+    for (int b = item; b < nact; b += kHB) {
+      const int k = S.act(b);
+      const double D = (double)(T >> S.lvl(k)) * unit;
+      const int e = ilogb(D);  // dt = sqrt(eta num_s / den_s) s
+      const float an = norm3f(S.a(0, k), S.a(1, k), S.a(2, k), 0);
+      const float jn = norm3f(S.j(0, k), S.j(1, k), S.j(2, k), e);
+      const float a2n = norm3f(S.a2e(0, k), S.a2e(1, k), S.a2e(2, k), 2 * e);
+      const float a3n = norm3f(S.a3(0, k), S.a3(1, k), S.a3(2, k), 3 * e);
+      const float num = an * a2n + jn * jn, den = jn * a3n + a2n * a2n;
+      const double dtd = den > 0.0f ? ldexp((double)sqrtf((float)prm.eta * num / den), e) : dt;
+      S.t(k) = tn;
+      S.lvl(k) = quantise_level(dtd, dt, S.lvl(k), tn, underflow);
+      if (S.partner(k) != kNone) C.any = 1;
+    }
+    if (tid == 0) steps += (unsigned long long)nact;
+    __syncthreads();
+  }
+  for (int k = item; k < nc; k += kHB) {
+    const int32_t i = cl_mem[off + k];
+    p.x[i] = S.x(0, k); p.y[i] = S.x(1, k); p.z[i] = S.x(2, k);
+    p.vx[i] = S.v(0, k); p.vy[i] = S.v(1, k); p.vz[i] = S.v(2, k);
+  }
+  if (tid == 0 && C.ncomp) emit_composites(S, C, nc, off, cl_mem, co, st);
+  __syncthreads();
+}
+
+// clusters of <= kHMax members (BIG = false) or more (BIG = true); one block
+// per cluster, clusters handed out dynamically (a long encounter keeps its
+// block while the others move on)
+template <bool BIG>
+__global__ void __launch_bounds__(kHB) k_hermite_block(
+    const int64_t *d_ncl, const int64_t *cl_off, const int32_t *cl_mem, p3t_particles p,
+    p3t_params prm, double dt, unsigned long long *steps_out, int64_t *cursor, HBig big,
+    CollOut co, DevStatus *st) {
+  __shared__ HCtl C;
+  extern __shared__ __align__(16) unsigned char hsm[];
+  HSmall *Sm = reinterpret_cast<HSmall *>(hsm);
+  const int tid = threadIdx.x;
+  const int64_t ncl = *d_ncl;
+  const bool coll = prm.f_radius > 0.0 && p.r_phys != nullptr;
   unsigned long long steps = 0;
   bool underflow = false;
   for (;;) {
-    if (tid == 0) S.cluster = atomicAdd(reinterpret_cast<unsigned long long *>(cursor), 1ull);
+    if (tid == 0) C.cluster = atomicAdd(reinterpret_cast<unsigned long long *>(cursor), 1ull);
     __syncthreads();
-    const int64_t c = S.cluster;
+    const int64_t c = C.cluster;
     __syncthreads();
     if (c >= ncl) break;
     const int64_t off = cl_off[c];
     const int nc = (int)(cl_off[c + 1] - off);
-    if (nc > kHMax) continue;  // the warp path takes these
-    for (int k = item; k < nc; k += kHB) {
-      const int32_t i = cl_mem[off + k];
-      S.x[0][k] = p.x[i]; S.x[1][k] = p.y[i]; S.x[2][k] = p.z[i];
-      S.v[0][k] = p.vx[i]; S.v[1][k] = p.vy[i]; S.v[2][k] = p.vz[i];
-      S.m[k] = p.m[i];
-      S.iro[k] = 1.0 / p.r_out[i];
-      S.act[k] = k;
+    if ((nc > kHMax) != BIG) continue;
+    if constexpr (BIG) {
+      const BigView S{big.d, big.t, big.i, big.cap, off};
+      integrate_cluster(S, C, nullptr, off, nc, cl_mem, p, prm, dt, coll, co, steps,
+                        underflow, st);
+    } else {
+      const SmallView S{Sm};
+      integrate_cluster(S, C, Sm, off, nc, cl_mem, p, prm, dt, coll, co, steps, underflow,
+                        st);
     }
-    __syncthreads();
-    // initial forces of every member, first steps
-    block_forces(S, S.x, S.v, nc, nc, item, prm, i1mg);
-    for (int k = item; k < nc; k += kHB) {
-      for (int q = 0; q < 3; ++q) { S.a[q][k] = S.a1[q][k]; S.j[q][k] = S.j1[q][k]; }
-      const int e = ilogb(dt);
-      const float an = norm3f(S.a[0][k], S.a[1][k], S.a[2][k], 0);
-      const float jn = norm3f(S.j[0][k], S.j[1][k], S.j[2][k], e);
-      const double dtd = jn > 0.0f ? ldexp((double)((float)prm.eta0 * an / jn), e) : dt;
-      S.t[k] = 0;
-      S.lvl[k] = quantise_level(dtd, dt, 0, 0, underflow);
-    }
-    __syncthreads();
-    int64_t iter = 0;
-    for (;;) {
-      int64_t e_min = T, t_min = T;
-      for (int k = tid; k < nc; k += kHB) {
-        const int64_t e = S.t[k] + (T >> S.lvl[k]);
-        e_min = e < e_min ? e : e_min;
-        t_min = S.t[k] < t_min ? S.t[k] : t_min;
-      }
-      const int64_t tn = block_min(e_min, S.red[0]);
-      const int64_t tmin = block_min(t_min, S.red[1]);
-      if (tmin >= T) break;
-      if (++iter > kHermiteIterLimit) {
-        if (tid == 0) dev_fail(st, P3T_ERR_TIMEOUT, 61, 0);
-        break;
-      }
-      // predict every member (component items)
-      for (int i = item; i < nc * 3; i += kHB) {
-        const int k = i / 3, q = i - 3 * k;
-        const double D = (double)(tn - S.t[k]) * unit;
-        const double D2 = D * D, D3 = D2 * D;
-        S.p[q][k] = S.x[q][k] + S.v[q][k] * D + S.a[q][k] * D2 * 0.5 + S.j[q][k] * D3 * (1.0 / 6.0);
-        S.pv[q][k] = S.v[q][k] + S.a[q][k] * D + S.j[q][k] * D2 * 0.5;
-      }
-      // active members in ascending order
-      {
-        const bool on = tid < nc && S.t[tid] + (T >> S.lvl[tid]) == tn;
-        const unsigned bal = __ballot_sync(0xffffffffu, on);
-        if ((tid & 31) == 0) S.wcount[tid >> 5] = __popc(bal);
-        __syncthreads();
-        int base = 0;
-        for (int q = 0; q < (tid >> 5); ++q) base += S.wcount[q];
-        if (on) S.act[base + __popc(bal & ((1u << (tid & 31)) - 1u))] = tid;
-        if (tid == 0) {
-          int tot = 0;
-          for (int q = 0; q < kHB / 32; ++q) tot += S.wcount[q];
-          S.nact = tot;
-        }
-      }
-      // (kHMax == kHB: member k is thread k here)
-      __syncthreads();
-      const int nact = S.nact;
-      block_forces(S, S.p, S.pv, nc, nact, item, prm, i1mg);
-      // correct (component items of the active members)
-      for (int i = item; i < nact * 3; i += kHB) {
-        const int b = i / 3, q = i - 3 * b;
-        const int k = S.act[b];
-        const double D = (double)(T >> S.lvl[k]) * unit;
-        const double D2 = D * D, D3 = D2 * D, D4 = D3 * D, D5 = D4 * D;
-        const double iD = 1.0 / D, iD2 = iD * iD, iD3 = iD2 * iD;
-        const double da = S.a[q][k] - S.a1[q][k];
-        const double j0 = S.j[q][k], j1 = S.j1[q][k];
-        const double A2 = (-6.0 * da - D * (4.0 * j0 + 2.0 * j1)) * iD2;
-        const double A3 = (12.0 * da + 6.0 * D * (j0 + j1)) * iD3;
-        S.a2e[q][k] = A2 + D * A3;
-        S.a3[q][k] = A3;
-        S.x[q][k] = S.p[q][k] + A2 * D4 * (1.0 / 24.0) + A3 * D5 * (1.0 / 120.0);
-        S.v[q][k] = S.pv[q][k] + A2 * D3 * (1.0 / 6.0) + A3 * D4 * (1.0 / 24.0);
-        S.a[q][k] = S.a1[q][k];
-        S.j[q][k] = j1;
-      }
-      __syncthreads();
-      // new steps of the active members
-      for (int b = item; b < nact; b += kHB) {
-        const int k = S.act[b];
-        const double D = (double)(T >> S.lvl[k]) * unit;
-        const int e = ilogb(D);
-        const float an = norm3f(S.a[0][k], S.a[1][k], S.a[2][k], 0);
-        const float jn = norm3f(S.j[0][k], S.j[1][k], S.j[2][k], e);
-        const float a2n = norm3f(S.a2e[0][k], S.a2e[1][k], S.a2e[2][k], 2 * e);
-        const float a3n = norm3f(S.a3[0][k], S.a3[1][k], S.a3[2][k], 3 * e);
-        const float num = an * a2n + jn * jn, den = jn * a3n + a2n * a2n;
-        const double dtd = den > 0.0f ? ldexp((double)sqrtf((float)prm.eta * num / den), e) : dt;
-        S.t[k] = tn;
-        S.lvl[k] = quantise_level(dtd, dt, S.lvl[k], tn, underflow);
-      }
-      if (tid == 0) steps += (unsigned long long)nact;
-      __syncthreads();
-    }
-    for (int k = item; k < nc; k += kHB) {
-      const int32_t i = cl_mem[off + k];
-      p.x[i] = S.x[0][k]; p.y[i] = S.x[1][k]; p.z[i] = S.x[2][k];
-      p.vx[i] = S.v[0][k]; p.vy[i] = S.v[1][k]; p.vz[i] = S.v[2][k];
-    }
-    __syncthreads();
   }
   if (underflow) dev_fail(st, P3T_ERR_DT_UNDERFLOW, 62, 0);
   if (tid == 0 && steps_out && steps) atomicAdd(steps_out, steps);
 }
 
-__global__ void k_zero_i64_one(int64_t *p) { *p = 0; }
-
-// clusters of more than kHMax members (a percolating cluster): one warp each,
-// members over lanes, state in the global workspace
-__global__ void k_hermite(const int64_t *d_ncl, const int64_t *cl_off,
-                          const int32_t *cl_mem, p3t_particles p, HWork w,
-                          p3t_params prm, double dt,
-                          unsigned long long *steps_out, DevStatus *st) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t ncl = *d_ncl;
-  unsigned long long steps = 0;
-  bool underflow = false;
-  for (int64_t c = warp; c < ncl; c += nwarps) {
-    const int64_t off = cl_off[c];
-    const int nc = (int)(cl_off[c + 1] - off);
-    if (nc <= kHMax) continue;
-    integrate_cluster<32>(off, nc, cl_mem, p, w, prm, dt, lane, 0xffffffffu, steps,
-                          underflow, st);
-  }
-  if (underflow) dev_fail(st, P3T_ERR_DT_UNDERFLOW, 62, 0);
-  for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(0xffffffffu, steps, o);
-  if (lane == 0 && steps_out && steps) atomicAdd(steps_out, steps);
-}
+__global__ void k_zero_i64_two(int64_t *p) { p[0] = 0; p[1] = 0; }
 
 __global__ void k_zero_u64(unsigned long long *p) { *p = 0ull; }
 
@@ -699,13 +849,109 @@ __global__ void k_energy_init(double *out) {
 }
 __global__ void k_energy_final(double *out) { out[0] = out[1] + out[2] + out[3]; }
 
+
+// ---- row f4: the merge after the second kick (procedure step 9) ------------
+// One block: every composite's lowest member gets the summed mass and the
+// radius of the summed volume; the dissipation totals are summed in a fixed
+// order (clusters by label, composites by lowest member) so that they do not
+// depend on the order the hard step appended them in.
+__global__ void k_merge_sets(const int4 *ent, int64_t ne, const int4 *rec, const double *rec_e,
+                             int64_t nrec, const double *esoft, double *m, double *rp,
+                             double *sorted_h, double *sorted_s, double *out) {
+  for (int64_t s = threadIdx.x; s < ne; s += blockDim.x) {
+    const int4 e = ent[s];
+    if (e.x != e.y) continue;
+    double M = 0.0, V = 0.0;
+    for (int l = e.z; l < e.w; ++l) {
+      const int q = ent[l].x;
+      M += m[q];
+      if (rp) V += rp[q] * rp[q] * rp[q];
+    }
+    m[e.x] = M;
+    if (rp) rp[e.x] = cbrt(V);
+    int64_t rank = 0;
+    for (int64_t u = 0; u < ne; ++u) rank += ent[u].x == ent[u].y && ent[u].y < e.y;
+    sorted_s[rank] = esoft[s];
+  }
+  for (int64_t r = threadIdx.x; r < nrec; r += blockDim.x) {
+    int64_t rank = 0;
+    for (int64_t u = 0; u < nrec; ++u) rank += rec[u].x < rec[r].x;
+    sorted_h[rank] = rec_e[r];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t nsets = 0;
+    for (int64_t u = 0; u < ne; ++u) nsets += ent[u].x == ent[u].y;
+    double eh = 0.0, es = 0.0;
+    for (int64_t r = 0; r < nrec; ++r) eh += sorted_h[r];
+    for (int64_t q = 0; q < nsets; ++q) es += sorted_s[q];
+    out[0] = eh;
+    out[1] = es;
+  }
+}
+
+__global__ void k_merge_keep(int64_t n, const int32_t *slot, const int4 *ent, int32_t *keep) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t s = slot[i];
+    keep[i] = (s < 0 || ent[s].x == ent[s].y) ? 1 : 0;
+  }
+}
+
+// survivors to their new places in the scratch arrays (10 arrays of n)
+__global__ void k_merge_gather(int64_t n, const int32_t *keep, const int64_t *pos,
+                               p3t_particles p, double *scr, int32_t *new_index) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (!keep[i]) {
+      new_index[i] = -1;
+      continue;
+    }
+    const int64_t d = pos[i];
+    new_index[i] = (int32_t)d;
+    scr[d] = p.x[i]; scr[n + d] = p.y[i]; scr[2 * n + d] = p.z[i];
+    scr[3 * n + d] = p.vx[i]; scr[4 * n + d] = p.vy[i]; scr[5 * n + d] = p.vz[i];
+    scr[6 * n + d] = p.m[i]; scr[7 * n + d] = p.r_out[i]; scr[8 * n + d] = p.r_search[i];
+    if (p.r_phys) scr[9 * n + d] = p.r_phys[i];
+  }
+}
+
+__global__ void k_merge_reset(const int4 *ent, int64_t ne, int32_t *slot,
+                              unsigned long long *ctr) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ne;
+       s += (int64_t)gridDim.x * blockDim.x)
+    slot[ent[s].x] = -1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *ctr = 0ull;
+}
+
+__global__ void k_iota(int64_t n, int32_t *a) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = (int32_t)i;
+}
+
+CollOut coll_out(p3t_ctx *c) {
+  CollOut co;
+  co.ctr = c->coll_ctr;
+  co.ent = c->coll_ent;
+  co.rec = c->coll_rec;
+  co.rec_e = c->coll_rec_e;
+  co.slot = c->coll_slot;
+  co.ent_cap = c->cap;
+  co.rec_cap = c->cap / 2 + 1;
+  return co;
+}
+
 }  // namespace
 
 int p3t_run_kick(p3t_ctx *c, p3t_particles *p, const double *ax,
                  const double *ay, const double *az, double h, cudaStream_t s) {
   if (p->n == 0) return P3T_OK;
   const int64_t g = p3t_grid(p->n, kBlock, (int64_t)c->num_sms * P3T_NSM_BLOCKS);
-  k_kick<<<(unsigned)g, kBlock, 0, s>>>(p->n, p->vx, p->vy, p->vz, ax, ay, az, h);
+  const bool coll = c->prm.f_radius > 0.0;
+  k_kick<<<(unsigned)g, kBlock, 0, s>>>(p->n, p->vx, p->vy, p->vz, ax, ay, az, h,
+                                        coll ? c->coll_slot : nullptr, c->coll_ent, p->m,
+                                        c->coll_esoft);
   p3t_note_launches(1);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
@@ -715,33 +961,26 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
   const int64_t n = p->n;
   const int64_t maxb = (int64_t)c->num_sms * P3T_NSM_BLOCKS;
   const double mu = c->prm.G * c->prm.m_star;
-  HWork w;
-  const int64_t cap = c->cap;
-  double *b = c->hw;
-  double **f[] = {&w.x, &w.y, &w.z, &w.vx, &w.vy, &w.vz, &w.px, &w.py, &w.pz,
-                  &w.pvx, &w.pvy, &w.pvz, &w.ax, &w.ay, &w.az, &w.jx, &w.jy, &w.jz,
-                  &w.m, &w.ro};
-  for (int q = 0; q < 20; ++q) *f[q] = b + q * cap;
-  w.t = c->ht;
-  w.lvl = c->hl;
+  HBig big{c->hw, c->ht, c->hl, c->cap};
+  const CollOut co = coll_out(c);
   unsigned long long *steps = n_steps ? reinterpret_cast<unsigned long long *>(n_steps)
                                       : c->hsteps;
   k_zero_u64<<<1, 1, 0, s>>>(steps);
+  k_zero_i64_two<<<1, 1, 0, s>>>(c->hcursor);
   // Kepler drift, small clusters and large clusters touch disjoint particles:
   // run them on three streams forked from and joined back to the caller's
   P3T_CUDA_TRY(cudaEventRecord(c->ev_fork, s));
   P3T_CUDA_TRY(cudaStreamWaitEvent(c->aux[0], c->ev_fork, 0));
   P3T_CUDA_TRY(cudaStreamWaitEvent(c->aux[1], c->ev_fork, 0));
-  // clusters of <= kHMax members: a block each, handed out dynamically (a
-  // long encounter keeps its block while the others move on); larger ones: a
-  // warp each
   const int64_t ncl_max = (n / 2) > 0 ? n / 2 : 1;
-  k_zero_i64_one<<<1, 1, 0, c->aux[0]>>>(c->hcursor);
-  k_hermite_block<<<(unsigned)p3t_grid(ncl_max * kHB, kHB, (int64_t)c->num_sms * 4), kHB, 0,
-                    c->aux[0]>>>(&cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, steps,
-                                 c->hcursor, c->status);
-  k_hermite<<<(unsigned)p3t_grid(ncl_max * 32, 128, maxb), 128, 0, c->aux[1]>>>(
-      &cl->counts[1], cl->cl_off, cl->cl_mem, *p, w, c->prm, dt, steps, c->status);
+  const int64_t nbig = c->num_sms < 32 ? c->num_sms : 32;
+  k_hermite_block<false><<<(unsigned)p3t_grid(ncl_max * kHB, kHB, (int64_t)c->num_sms * 4), kHB,
+                           sizeof(HSmall), c->aux[0]>>>(&cl->counts[1], cl->cl_off, cl->cl_mem,
+                                                        *p, c->prm, dt, steps, c->hcursor, big,
+                                                        co, c->status);
+  k_hermite_block<true><<<(unsigned)p3t_grid(ncl_max, 1, nbig), kHB, 0, c->aux[1]>>>(
+      &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, steps, c->hcursor + 1, big, co,
+      c->status);
   k_kepler<<<(unsigned)p3t_grid(n, 128, maxb), 128, 0, s>>>(&cl->counts[0], cl->singles, *p,
                                                              dt, mu, c->status);
   P3T_CUDA_TRY(cudaEventRecord(c->ev_join[0], c->aux[0]));
@@ -749,6 +988,63 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
   P3T_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[0], 0));
   P3T_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[1], 0));
   p3t_note_launches(5);
+  return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
+}
+
+// Procedure step 9 for composites (row f4).  Synchronises the stream: the
+// caller needs the new particle count on the host.
+int p3t_run_merge(p3t_ctx *c, p3t_particles *p, int32_t *new_index, double *e_disp,
+                  int64_t *n_merged, cudaStream_t s) {
+  const int64_t n = p->n;
+  const int64_t maxb = (int64_t)c->num_sms * P3T_NSM_BLOCKS;
+  unsigned long long ctr = 0;
+  P3T_CUDA_TRY(cudaMemcpyAsync(&ctr, c->coll_ctr, sizeof(ctr), cudaMemcpyDeviceToHost, s));
+  P3T_CUDA_TRY(cudaStreamSynchronize(s));
+  int64_t nrec = (int64_t)(ctr >> 32), ne = (int64_t)(ctr & 0xffffffffull);
+  const CollOut co = coll_out(c);
+  if (nrec > co.rec_cap) nrec = co.rec_cap;  // a capacity error is already recorded
+  if (ne > co.ent_cap) ne = co.ent_cap;
+  if (nrec == 0 || ne == 0 || n == 0) {
+    if (e_disp) e_disp[0] = e_disp[1] = 0.0;
+    if (n_merged) *n_merged = 0;
+    if (new_index && n > 0) {
+      k_iota<<<(unsigned)p3t_grid(n, kBlock, maxb), kBlock, 0, s>>>(n, new_index);
+      p3t_note_launches(1);
+    }
+    return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
+  }
+  double *scr = c->hw;              // 10 n for the gather
+  double *sorted_h = c->hw + 10 * c->cap, *sorted_s = sorted_h + c->cap;
+  double *out = c->epart;
+  int32_t *keep = c->flag;
+  int64_t *pos = c->pos;
+  int32_t *ni = new_index ? new_index : c->flag + c->cap;
+  int64_t *d_n = c->counters + 16, *d_total = c->counters + 17;
+  P3T_CUDA_TRY(cudaMemcpyAsync(d_n, &n, sizeof(n), cudaMemcpyHostToDevice, s));
+  k_merge_sets<<<1, 1024, 0, s>>>(co.ent, ne, co.rec, co.rec_e, nrec, c->coll_esoft, p->m,
+                                  p->r_phys, sorted_h, sorted_s, out);
+  const unsigned g = (unsigned)p3t_grid(n, kBlock, maxb);
+  k_merge_keep<<<g, kBlock, 0, s>>>(n, c->coll_slot, co.ent, keep);
+  int rc = p3t_scan_i32_to_i64(keep, pos, d_n, n, d_total, c->scan_part, s);
+  if (rc) return rc;
+  k_merge_gather<<<g, kBlock, 0, s>>>(n, keep, pos, *p, scr, ni);
+  double *dst[10] = {p->x, p->y, p->z, p->vx, p->vy, p->vz, p->m, p->r_out, p->r_search,
+                     p->r_phys};
+  for (int q = 0; q < 10; ++q)
+    if (dst[q])
+      P3T_CUDA_TRY(cudaMemcpyAsync(dst[q], scr + q * n, sizeof(double) * n,
+                                   cudaMemcpyDeviceToDevice, s));
+  k_merge_reset<<<(unsigned)p3t_grid(ne, kBlock, maxb), kBlock, 0, s>>>(co.ent, ne, c->coll_slot,
+                                                                        c->coll_ctr);
+  p3t_note_launches(5);
+  double eo[2];
+  int64_t total = 0;
+  P3T_CUDA_TRY(cudaMemcpyAsync(eo, out, sizeof(eo), cudaMemcpyDeviceToHost, s));
+  P3T_CUDA_TRY(cudaMemcpyAsync(&total, d_total, sizeof(total), cudaMemcpyDeviceToHost, s));
+  P3T_CUDA_TRY(cudaStreamSynchronize(s));
+  if (e_disp) { e_disp[0] = eo[0]; e_disp[1] = eo[1]; }
+  if (n_merged) *n_merged = n - total;
+  p->n = total;
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 

@@ -77,7 +77,7 @@ struct p3t_ctx {
   // root box {x0, y0, z0, L} and scalar counters
   double *box = nullptr;
   unsigned long long *box_bits = nullptr;  // ordered-bits min/max workspace [6]
-  int64_t *counters = nullptr;             // misc device counters [16]
+  int64_t *counters = nullptr;             // misc device counters [24]
 
   // sort
   uint64_t *keys = nullptr, *keys_alt = nullptr;
@@ -134,12 +134,20 @@ struct p3t_ctx {
   uint64_t *mkeys = nullptr, *mkeys_alt = nullptr;
   int32_t *mvals = nullptr, *mvals_alt = nullptr;
 
-  // hard step workspace (per cluster member)
-  double *hw = nullptr;                    // 26 * cap doubles
+  // hard step workspace (per cluster member, clusters of more than 128)
+  double *hw = nullptr;                    // 33 * cap doubles
   int64_t *ht = nullptr;                   // time in units of dt / 2^40
-  int32_t *hl = nullptr;                   // block level
+  int32_t *hl = nullptr;                   // 6 * cap: level, list, sets, partner, flags
   unsigned long long *hsteps = nullptr;    // device counter
-  int64_t *hcursor = nullptr;              // cluster cursor of the block kernel
+  int64_t *hcursor = nullptr;              // [2] cluster cursors of the two Hermite kernels
+
+  // composites of colliding particles, from the hard step to the merge
+  unsigned long long *coll_ctr = nullptr;  // (records << 32) | entries
+  int4 *coll_ent = nullptr;                // cap entries {particle, lowest member, lo, hi}
+  int4 *coll_rec = nullptr;                // cap / 2 + 1 records {label, first, count, 0}
+  double *coll_rec_e = nullptr;            // dissipation per record
+  double *coll_esoft = nullptr;            // kick dissipation per entry
+  int32_t *coll_slot = nullptr;            // particle -> entry or -1 (cap)
 
   // energy
   double *epart = nullptr;                 // per-block partial sums
@@ -196,3 +204,5 @@ int p3t_run_kick(p3t_ctx *c, p3t_particles *p, const double *ax,
                  const double *ay, const double *az, double h, cudaStream_t s);
 int p3t_run_energy(p3t_ctx *c, const p3t_particles *p, double *out,
                    cudaStream_t s);
+int p3t_run_merge(p3t_ctx *c, p3t_particles *p, int32_t *new_index, double *e_disp,
+                  int64_t *n_merged, cudaStream_t s);

@@ -158,3 +158,31 @@ def physical_radius(m, rho_cgs=2.0):
     rho_cgs (g cm^-3) in au: the paper's bodies have 2 g cm^-3 (Sec. 3.1)."""
     rho = rho_cgs * AU_CM**3 / MSUN_G
     return np.cbrt(3.0 * np.asarray(m, dtype=np.float64) / (4.0 * np.pi * rho))
+
+
+def planted_impacts(s, pairs, sep=2e-4, speed=0.05):
+    """Sets each (i, j) of `pairs` on a head-on course: j placed `sep` au
+    radially outward of i, closing at `speed` (so the pair touches within a
+    soft step of 1/64 when sep < speed / 64).  Modifies s in place."""
+    for i, j in pairs:
+        r = np.array([s["x"][i], s["y"][i], s["z"][i]])
+        d = r / np.linalg.norm(r) * sep
+        for q, k in enumerate(("x", "y", "z")):
+            s[k][j] = s[k][i] + d[q]
+        for q, k in enumerate(("vx", "vy", "vz")):
+            s[k][j] = s[k][i] - speed * d[q] / sep
+    return s
+
+
+def clump(n, seed, a=1.0, size=2e-4, m=1e-9, v_disp=1e-3):
+    """n bodies inside a cube of side `size` around (a, 0, 0) on the local
+    circular velocity plus a Gaussian dispersion `v_disp` per axis: a dense
+    group that forms one large neighbour cluster."""
+    rng = np.random.default_rng(seed)
+    x = a + rng.uniform(-0.5, 0.5, n) * size
+    y = rng.uniform(-0.5, 0.5, n) * size
+    z = rng.uniform(-0.5, 0.5, n) * size
+    vk = 1.0 / np.sqrt(a)
+    return {"x": x, "y": y, "z": z, "vx": rng.normal(0, v_disp, n),
+            "vy": vk + rng.normal(0, v_disp, n), "vz": rng.normal(0, v_disp, n),
+            "m": np.full(n, m)}

@@ -7,7 +7,7 @@ there is no CPU fallback.
 
 The functions carry the C names (``p3t_build_tree`` ...) and take a context
 handle, a :class:`State` of float64 CUDA tensors and optional streams.
-:class:`SoftStep` strings them together into the paper's procedure steps 3-8.
+:class:`SoftStep` strings them together into the paper's procedure steps 3-9.
 """
 from __future__ import annotations
 
@@ -42,21 +42,21 @@ class Params(C.Structure):
 
     _fields_ = [(n, C.c_double) for n in (
         "G", "m_star", "dt_soft", "gamma", "rcut0", "rcut1", "rs0", "rs1", "rs2",
-        "rs3", "theta", "eta", "eta0")] + [
+        "rs3", "theta", "eta", "eta0", "f_radius")] + [
         ("leaf_size", C.c_int32), ("precision", C.c_int32), ("vran_bins", C.c_int32),
         ("group_size", C.c_int32)]
 
     def __init__(self, **kw):
         d = dict(G=1.0, m_star=1.0, dt_soft=1.0 / 64.0, gamma=0.1, rcut0=2.0, rcut1=8.0,
                  rs0=1.1, rs1=6.0, rs2=2.0, rs3=2.0, theta=0.5, eta=0.01, eta0=0.001,
-                 leaf_size=16, precision=P3T_FP64, vran_bins=0, group_size=0)
+                 f_radius=0.0, leaf_size=16, precision=P3T_FP64, vran_bins=0, group_size=0)
         d.update(kw)
         super().__init__(**d)
 
 
 class Particles(C.Structure):
     _fields_ = [("n", C.c_int64)] + [(k, C.c_void_p) for k in (
-        "x", "y", "z", "vx", "vy", "vz", "m", "r_out", "r_search")]
+        "x", "y", "z", "vx", "vy", "vz", "m", "r_out", "r_search", "r_phys")]
 
 
 class Clusters(C.Structure):
@@ -79,6 +79,8 @@ _sig = {
                                 _vp, _vp]),
     "p3t_kick": (C.c_int, [_CTX, C.POINTER(Particles), _vp, _vp, _vp, C.c_double, _vp]),
     "p3t_energy": (C.c_int, [_CTX, C.POINTER(Particles), _vp, _vp]),
+    "p3t_merge": (C.c_int, [_CTX, C.POINTER(Particles), _vp, C.POINTER(C.c_double),
+                            C.POINTER(C.c_int64), _vp]),
     "p3t_status": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
     "p3t_tree_stats": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
     "p3t_strerror": (C.c_char_p, [C.c_int]),
@@ -114,9 +116,13 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(None)
 
 
+_KEYS = ("x", "y", "z", "vx", "vy", "vz", "m", "r_out", "r_search")
+
+
 @dataclass
 class State:
-    """Particle state: float64 CUDA tensors of length n in caller order."""
+    """Particle state: float64 CUDA tensors of length n in caller order;
+    r_phys (physical radii) is optional and enables collisions."""
 
     x: torch.Tensor
     y: torch.Tensor
@@ -127,28 +133,37 @@ class State:
     m: torch.Tensor
     r_out: torch.Tensor
     r_search: torch.Tensor
+    r_phys: torch.Tensor | None = None
 
     @staticmethod
-    def from_numpy(s: dict, device="cuda", r_out=None, r_search=None):
+    def from_numpy(s: dict, device="cuda", r_out=None, r_search=None, r_phys=None):
         def t(a):
             return torch.as_tensor(a, dtype=torch.float64).to(device).contiguous()
         n = len(s["m"])
         ro = t(r_out) if r_out is not None else torch.zeros(n, dtype=torch.float64, device=device)
         rs = t(r_search) if r_search is not None else torch.zeros(n, dtype=torch.float64, device=device)
         return State(t(s["x"]), t(s["y"]), t(s["z"]), t(s["vx"]), t(s["vy"]), t(s["vz"]),
-                     t(s["m"]), ro, rs)
+                     t(s["m"]), ro, rs, t(r_phys) if r_phys is not None else None)
+
+    def _arrays(self):
+        return _KEYS + (("r_phys",) if self.r_phys is not None else ())
 
     def particles(self) -> Particles:
-        for k in ("x", "y", "z", "vx", "vy", "vz", "m", "r_out", "r_search"):
+        n = len(self.m)
+        for k in self._arrays():
             v = getattr(self, k)
-            if v.dtype != torch.float64 or not v.is_cuda or not v.is_contiguous():
-                raise TypeError(f"{k} must be a contiguous float64 CUDA tensor")
-        return Particles(len(self.m), *[self.__dict__[k].data_ptr() for k in (
-            "x", "y", "z", "vx", "vy", "vz", "m", "r_out", "r_search")])
+            if v.dtype != torch.float64 or not v.is_cuda or not v.is_contiguous() or len(v) != n:
+                raise TypeError(f"{k} must be a contiguous float64 CUDA tensor of length {n}")
+        return Particles(n, *[getattr(self, k).data_ptr() for k in _KEYS],
+                         self.r_phys.data_ptr() if self.r_phys is not None else None)
+
+    def truncate(self, n: int) -> None:
+        """Keeps the first n particles (views of the same storage)."""
+        for k in self._arrays():
+            setattr(self, k, getattr(self, k)[:n])
 
     def numpy(self) -> dict:
-        return {k: getattr(self, k).cpu().numpy() for k in (
-            "x", "y", "z", "vx", "vy", "vz", "m", "r_out", "r_search")}
+        return {k: getattr(self, k).cpu().numpy() for k in self._arrays()}
 
 
 # ---- functions with the C names ---------------------------------------------
@@ -232,6 +247,20 @@ def p3t_energy(ctx, st: State, out: torch.Tensor, stream=None) -> None:
     _check(_lib.p3t_energy(ctx, C.byref(p), _ptr(out), _stream(stream)), "p3t_energy")
 
 
+def p3t_merge(ctx, st: State, new_index: torch.Tensor | None = None, stream=None):
+    """Procedure step 9 for collisions: merges the composites of the last hard
+    step, shortens the tensors of ``st`` to the new count in place and returns
+    (particles removed, hard dissipation, kick dissipation).  Synchronises."""
+    p = st.particles()
+    e = (C.c_double * 2)()
+    nm = C.c_int64(0)
+    _check(_lib.p3t_merge(ctx, C.byref(p), _ptr(new_index), e, C.byref(nm), _stream(stream)),
+           "p3t_merge")
+    if nm.value:
+        st.truncate(int(p.n))
+    return nm.value, e[0], e[1]
+
+
 def p3t_status(ctx) -> tuple[int, int]:
     req = C.c_int64(0)
     rc = _lib.p3t_status(ctx, C.byref(req))
@@ -268,11 +297,14 @@ def clusters_to_host(ctx, cl: Clusters, n: int) -> dict:
 
 
 class SoftStep:
-    """The P3T soft step on one GPU (paper Sec. 2.2, procedure steps 2-8).
+    """The P3T soft step on one GPU (paper Sec. 2.2, procedure steps 2-9).
 
     ``init()`` computes the cut-off radii, the first soft force, neighbour
     lists and clusters; each ``step()`` then runs kick, hard step, tree,
-    force, neighbours, kick.
+    force, neighbours, kick and, with collisions on (``f_radius > 0`` and
+    ``st.r_phys``), the merge followed by new cut-off radii, force and
+    neighbours when particles merged.  ``e_disp`` accumulates the dissipated
+    energy {hard part, kick}.
     """
 
     def __init__(self, params: Params, st: State, device: int = 0, nb_cap: int | None = None):
@@ -288,6 +320,8 @@ class SoftStep:
         self.nb_off = torch.zeros(self.n + 1, dtype=torch.int64, device=dev)
         self.nb_idx = torch.zeros(max(nb_cap or (4 * self.n + 1024), 1), dtype=torch.int32, device=dev)
         self.cl = None
+        self.e_disp = [0.0, 0.0]
+        self.merged = 0
 
     def close(self):
         if self.ctx:
@@ -310,12 +344,31 @@ class SoftStep:
             p3t_cutoffs(self.ctx, self.st, stream)
         self.force(stream)
 
+    @property
+    def collisions(self) -> bool:
+        return self.params.f_radius > 0.0 and self.st.r_phys is not None
+
+    def merge(self, stream=None) -> int:
+        """Procedure step 9: merge, then new cut-off radii, force, neighbours."""
+        nm, eh, es = p3t_merge(self.ctx, self.st, None, stream)
+        self.e_disp[0] += eh
+        self.e_disp[1] += es
+        if nm:
+            self.merged += nm
+            self.n = len(self.st.m)
+            self.acc = self.acc[:, :self.n]
+            p3t_cutoffs(self.ctx, self.st, stream)
+            self.force(stream)
+        return nm
+
     def step(self, stream=None):
         h = 0.5 * self.params.dt_soft
         p3t_kick(self.ctx, self.st, self.acc, h, stream)
         p3t_hard_step(self.ctx, self.st, self.cl, self.params.dt_soft, self.hsteps, stream)
         self.force(stream)
         p3t_kick(self.ctx, self.st, self.acc, h, stream)
+        if self.collisions:
+            self.merge(stream)
 
     def status(self):
         rc, req = p3t_status(self.ctx)

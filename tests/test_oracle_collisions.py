@@ -184,17 +184,8 @@ def test_merge_sums_mass_and_volume_and_compacts(orc):
 
 
 def _disk_with_impacts():
-    """The planted narrow disk with two pairs set on head-on courses (closing
-    at 0.05 from 2e-4 au apart, so they touch within one soft step)."""
-    s = disks.equal_mass_narrow()
-    for i, j in ((100, 101), (500, 501)):
-        r = np.array([s["x"][i], s["y"][i], s["z"][i]])
-        d = r / np.linalg.norm(r) * 2e-4
-        for q, k in enumerate(("x", "y", "z")):
-            s[k][j] = s[k][i] + d[q]
-        for q, k in enumerate(("vx", "vy", "vz")):
-            s[k][j] = s[k][i] - 0.05 * d[q] / 2e-4
-    return s
+    """The planted narrow disk with two pairs on head-on courses."""
+    return disks.planted_impacts(disks.equal_mass_narrow(), [(100, 101), (500, 501)])
 
 
 def test_soft_step_energy_balance_with_collisions(orc):
