@@ -1,12 +1,15 @@
 #!/usr/bin/env python3
 """Soft-step benchmark of the P3T integrator with individual cut-off radii.
 
-One "step" is one full soft step of the paper's procedure (steps 3-8): kick,
-hard part (Hermite clusters + Kepler drift), tree build, soft force walk,
-neighbour lists + clusters, kick -- all in libp3t's kernels.  Workload: the
-N = 10^6 wide disk on 1-10 au (power-law planetesimals on [1e-12, 1e-8] plus
-20 protoplanets of 1e-7; e/i rms 2h and h), theta = 0.5, leaf 16,
-dt = 1/64, mixed precision.  Synthetic, seeded (seed 1003).
+One "step" is one full soft step of the paper's procedure (steps 3-9): kick,
+hard part (Hermite clusters with perfect-accretion collisions + Kepler
+drift), tree build, soft force walk, neighbour lists + clusters, kick, and
+when bodies collided the merge with new cut-off radii, force and neighbours
+-- all in libp3t's kernels.  Workload: the N = 10^6 wide disk on 1-10 au
+(power-law planetesimals on [1e-12, 1e-8] plus 20 protoplanets of 1e-7; e/i
+rms 2h and h; density 2 g/cm^3, radius factor f = 1), theta = 0.5, leaf 16,
+target groups of up to 64, dt = 1/64, mixed precision.  Synthetic, seeded
+(seed 1003).
 
 Reported value: pair interactions (p-p + p-node terms of the soft force) per
 second of whole-step wall time.  Also reported: the soft-step time, Hermite
@@ -53,6 +56,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--group-size", type=int, default=64,
                     help="target group size of the tree walk (0: one group per leaf)")
+    ap.add_argument("--f-radius", type=float, default=1.0,
+                    help="collision radius factor f (0: no collisions)")
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-targets", type=int, default=16384,
@@ -235,22 +240,28 @@ def run_ours(args):
     s = workload(args.n, seed=1003 + 1000 * rank)
     n = len(s["m"])
     prec = P.P3T_MIXED if args.precision == "mixed" else P.P3T_FP64
-    prm = P.Params(theta=0.5, precision=prec, eta=0.01, eta0=0.001, group_size=args.group_size)
-    st = P.State.from_numpy(s, device=dev)
+    prm = P.Params(theta=0.5, precision=prec, eta=0.01, eta0=0.001, group_size=args.group_size,
+                   f_radius=args.f_radius)
+    from paper_2007_15432_gb300 import disks
+    st = P.State.from_numpy(s, device=dev, r_phys=disks.physical_radius(s["m"]))
     ss = P.SoftStep(prm, st, device=local)
     stream = torch.cuda.current_stream(dev)
-    ss.init(update_cutoffs=True)            # row a1 at init; radii then held fixed
+    ss.init(update_cutoffs=True)            # row a1 at init, then after merges
     torch.cuda.synchronize(dev)
     ss.status()
 
     K, W = args.steps, args.warmup
-    counts_all = torch.zeros(K, 2, dtype=torch.int64, device=dev)
+    counts_all = torch.zeros(K, 2, 2, dtype=torch.int64, device=dev)
     hsteps_all = torch.zeros(K, dtype=torch.int64, device=dev)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(K)]
     h = 0.5 * prm.dt_soft
+    scratch_counts = torch.zeros(2, 2, dtype=torch.int64, device=dev)
+    e_disp = [0.0, 0.0]
+    merged = [0]
 
-    def step(k=None):
+    def step(k=None, counts=None):
         e = ev[k] if k is not None else None
+        cnt = counts if counts is not None else (counts_all[k] if k is not None else scratch_counts)
         if e: e[0].record(stream)
         P.p3t_kick(ss.ctx, st, ss.acc, h, stream)
         P.p3t_hard_step(ss.ctx, st, ss.cl, prm.dt_soft,
@@ -258,20 +269,39 @@ def run_ours(args):
         if e: e[1].record(stream)
         P.p3t_build_tree(ss.ctx, st, False, stream)
         if e: e[2].record(stream)
-        P.p3t_soft_force(ss.ctx, st, ss.acc, counts_all[k] if k is not None else ss.counts, stream)
+        P.p3t_soft_force(ss.ctx, st, ss.acc, cnt[0], stream)
         if e: e[3].record(stream)
         ss.cl = P.p3t_neighbours(ss.ctx, st, ss.nb_off, ss.nb_idx, stream)
         if e: e[4].record(stream)
         P.p3t_kick(ss.ctx, st, ss.acc, h, stream)
         if e: e[5].record(stream)
+        if ss.collisions:
+            # procedure step 9: merge (synchronises), then new radii and force
+            nm, eh, es = P.p3t_merge(ss.ctx, st, None, stream)
+            e_disp[0] += eh
+            e_disp[1] += es
+            if nm:
+                merged[0] += nm
+                ss.n = len(st.m)
+                ss.acc = ss.acc[:, :ss.n]
+                P.p3t_cutoffs(ss.ctx, st, stream)
+                P.p3t_build_tree(ss.ctx, st, False, stream)
+                P.p3t_soft_force(ss.ctx, st, ss.acc, cnt[1], stream)
+                ss.cl = P.p3t_neighbours(ss.ctx, st, ss.nb_off, ss.nb_idx, stream)
+        if e: e[6].record(stream)
 
     for _ in range(W):
         step()
     torch.cuda.synchronize(dev)
     ss.status()
+    n_start = len(st.m)
+    m_start = float(st.m.sum().item())
 
     energy = torch.zeros(2, 4, dtype=torch.float64, device=dev)
     P.p3t_energy(ss.ctx, st, energy[0], stream)   # row a10, outside the timed region
+    e_disp[0] = e_disp[1] = 0.0
+    merged[0] = 0
+    counts_all.zero_()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -291,47 +321,46 @@ def run_ours(args):
     clk = clocks.stop()
     ss.status()
     elapsed = t_start.elapsed_time(t_end) / 1e3
-    phase = np.zeros(5)
+    phase = np.zeros(6)
     for k in range(K):
         e = ev[k]
-        phase += [e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3]),
-                  e[3].elapsed_time(e[4]), e[4].elapsed_time(e[5])]
+        phase += [e[q].elapsed_time(e[q + 1]) for q in range(6)]
     phase /= K
-    c = counts_all.cpu().numpy()
+    c = counts_all.cpu().numpy()               # [step, first / after-merge force, pp / pnode]
     inter = float(c.sum())
     hsteps = float(hsteps_all.sum().item())
     walk_s = phase[2] / 1e3
     E0, E1 = (float(v) for v in energy[:, 0].cpu())
-    flops_per_launch = (FLOP_PP * c[:, 0] + FLOP_PN * c[:, 1]).mean()
+    flops_per_launch = (FLOP_PP * c[:, 0, 0] + FLOP_PN * c[:, 0, 1]).mean()
 
     # ---- end to end through the C ABI with host buffers --------------------
-    keys = ("x", "y", "z", "vx", "vy", "vz", "m", "r_out", "r_search")
+    keys = ("x", "y", "z", "vx", "vy", "vz", "m", "r_out", "r_search", "r_phys")
+    n0 = len(st.m)
     host = {k: getattr(st, k).cpu().pin_memory() for k in keys}
-    out_keys = ("x", "y", "z", "vx", "vy", "vz")
-    host_out = {k: torch.empty_like(host[k]).pin_memory() for k in out_keys}
-    h2d = sum(host[k].numel() * 8 for k in keys)
-    d2h = sum(host_out[k].numel() * 8 for k in out_keys)
+    host_out = {k: torch.empty_like(host[k]).pin_memory() for k in keys}
     E = max(1, args.e2e_steps)
-    e2e_counts = torch.zeros(E, 2, dtype=torch.int64, device=dev)
+    e2e_counts = torch.zeros(E, 2, 2, dtype=torch.int64, device=dev)
+    h2d = d2h = 0
     torch.cuda.synchronize(dev)
     barrier(dist)
     t0 = time.perf_counter()
     for k in range(E):
+        n = len(st.m)
         for key in keys:
-            getattr(st, key).copy_(host[key], non_blocking=True)
-        P.p3t_kick(ss.ctx, st, ss.acc, h, stream)
-        P.p3t_hard_step(ss.ctx, st, ss.cl, prm.dt_soft, ss.hsteps, stream)
-        P.p3t_build_tree(ss.ctx, st, False, stream)
-        P.p3t_soft_force(ss.ctx, st, ss.acc, e2e_counts[k], stream)
-        ss.cl = P.p3t_neighbours(ss.ctx, st, ss.nb_off, ss.nb_idx, stream)
-        P.p3t_kick(ss.ctx, st, ss.acc, h, stream)
-        for key in out_keys:
-            host_out[key].copy_(getattr(st, key), non_blocking=True)
+            getattr(st, key).copy_(host[key][:n], non_blocking=True)
+        h2d += 8 * n * len(keys)
+        step(None, counts=e2e_counts[k])
+        n = len(st.m)
+        for key in keys:
+            host_out[key][:n].copy_(getattr(st, key), non_blocking=True)
+        d2h += 8 * n * len(keys)
         torch.cuda.synchronize(dev)
-        for key in out_keys:   # the result is the next step's input
+        for key in keys:   # the result is the next step's input
             host[key], host_out[key] = host_out[key], host[key]
     t_e2e = time.perf_counter() - t0
     e2e_inter = float(e2e_counts.sum().item())
+    h2d //= E
+    d2h //= E
     ss.status()
 
     tot_elapsed = allmax(dist, elapsed)
@@ -355,16 +384,21 @@ def run_ours(args):
         warmup=W, ms_per_step=1e3 * elapsed / K, higher_is_better=True, scaling="weak",
         vs_baseline=None, dtype="f32/f64" if prec == P.P3T_MIXED else "f64",
         data="synthetic (seeded disk)",
-        config=dict(workload=workload_name(n), n=n, group_size=args.group_size,
+        config=dict(workload=workload_name(args.n), n=args.n, group_size=args.group_size,
+                    f_radius=args.f_radius, density_g_cm3=2.0,
                     precision=args.precision, l2="per-step working set > L2 (inputs ~0.5 GB)",
                     parallelism="replicas only" if world > 1 else "single GPU"),
         soft_step_ms=1e3 * elapsed / K,
         hermite_steps_per_s=hsteps / (phase[0] * K / 1e3),   # over the kick + hard phase
         hermite_steps_per_step=hsteps / K,
-        energy_error=abs(E1 / E0 - 1.0),
+        energy_error=abs((E1 + e_disp[0] + e_disp[1]) / E0 - 1.0),
+        energy_dissipated=e_disp[0] + e_disp[1],
+        collisions=dict(merged=merged[0], n_start=n_start, n_end=len(st.m),
+                        mass_error=abs(float(st.m.sum().item()) / m_start - 1.0)),
         interactions_per_step=inter / K,
         phases_ms=dict(kick_and_hard=phase[0], tree=phase[1], soft_force=phase[2],
-                       neighbours_clusters=phase[3], kick=phase[4]),
+                       neighbours_clusters=phase[3], kick=phase[4],
+                       merge_and_recompute=phase[5]),
         roofline=dict(kernel="k_walk (mixed) + FP64 refinement", bound="alu",
                       achieved=achieved, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
                       frac=achieved / FP32_PEAK_TFLOPS, traffic=None),

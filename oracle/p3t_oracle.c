@@ -155,9 +155,11 @@ int or_direct_soft(int64_t n, const double *x, const double *y, const double *z,
 /* definitions below are reading C4).                                         */
 /*  * root cube: bounding box of the positions, made cubic (side L = largest  */
 /*    extent), corner at the per-axis minimum;                                */
-/*  * each axis quantised to q in [0, 2^21) (unit u = L / 2^21), bits          */
-/*    interleaved (x highest) into a 63-bit Morton key; particles ordered by  */
-/*    (key, caller index);                                                    */
+/*  * each axis quantised to q = floor((v - lo) S) in [0, 2^21), with the    */
+/*    scale S = 2^21 / L formed once (unit u = L / 2^21); bits interleaved    */
+/*    (x highest) into a 63-bit Morton key; particles ordered by (key,        */
+/*    caller index).  q is the cell of v up to ~1e-9 u, well inside the two- */
+/*    cell margin of the reach test below;                                    */
 /*  * a node is a key prefix at level l holding > 0 particles; a node is      */
 /*    split while it holds more than leaf_size particles and l < 21;          */
 /*  * target groups: a node is a group iff it holds <= group_size particles  */
@@ -183,9 +185,8 @@ static uint64_t spread3(uint64_t v) {
   return r;
 }
 
-static int64_t quantise(double v, double lo, double L) {
-  double t = (v - lo) / L;
-  int64_t q = (int64_t)floor(t * (double)OR_QMAX);
+static int64_t quantise(double v, double lo, double S) {
+  int64_t q = (int64_t)floor((v - lo) * S);
   if (q < 0) q = 0;
   if (q > OR_QMAX - 1) q = OR_QMAX - 1;
   return q;
@@ -209,10 +210,11 @@ int or_morton_keys(int64_t n, const double *x, const double *y, const double *z,
                    uint64_t *key, double box_out[4]) {
   double box[4];
   root_box(n, x, y, z, box);
+  const double S = (double)OR_QMAX / box[3];
   for (int64_t i = 0; i < n; ++i) {
-    uint64_t qx = (uint64_t)quantise(x[i], box[0], box[3]);
-    uint64_t qy = (uint64_t)quantise(y[i], box[1], box[3]);
-    uint64_t qz = (uint64_t)quantise(z[i], box[2], box[3]);
+    uint64_t qx = (uint64_t)quantise(x[i], box[0], S);
+    uint64_t qy = (uint64_t)quantise(y[i], box[1], S);
+    uint64_t qz = (uint64_t)quantise(z[i], box[2], S);
     key[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
   }
   if (box_out) memcpy(box_out, box, sizeof(box));
@@ -362,9 +364,9 @@ static void tree_build(or_tree *T, int64_t n, const double *x, const double *y,
     T->ord[s] = i; T->key[s] = kv[s].key;
     T->x[s] = x[i]; T->y[s] = y[i]; T->z[s] = z[i]; T->m[s] = m[i];
     T->ro[s] = ro[i]; T->rs[s] = rs[i];
-    T->qx[s] = quantise(x[i], T->box[0], T->box[3]);
-    T->qy[s] = quantise(y[i], T->box[1], T->box[3]);
-    T->qz[s] = quantise(z[i], T->box[2], T->box[3]);
+    T->qx[s] = quantise(x[i], T->box[0], (double)OR_QMAX / T->box[3]);
+    T->qy[s] = quantise(y[i], T->box[1], (double)OR_QMAX / T->box[3]);
+    T->qz[s] = quantise(z[i], T->box[2], (double)OR_QMAX / T->box[3]);
   }
   free(kv); free(key);
   /* breadth-first: children of a node are appended contiguously */

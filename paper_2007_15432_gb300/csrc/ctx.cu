@@ -173,8 +173,8 @@ int p3t_create(p3t_ctx **ctx, const p3t_params *p, int device) {
     delete c;
     return P3T_ERR_CUDA;
   }
-  bool ok = dalloc(c->status, 1) && dalloc(c->box, 4) && dalloc(c->box_bits, 6) &&
-            dalloc(c->counters, 24) && dalloc(c->cl_counts, 4) && dalloc(c->hsteps, 1) && dalloc(c->hcursor, 2) &&
+  bool ok = dalloc(c->status, 1) && dalloc(c->box, 5) && dalloc(c->box_bits, 6) &&
+            dalloc(c->counters, 24) && dalloc(c->cl_counts, 4) && dalloc(c->hsteps, 1) && dalloc(c->hcursor, 3) &&
             dalloc(c->coll_ctr, 1) &&
             dalloc(c->epart, 8192) && dalloc(c->scan_part, 1025) && dalloc(c->bh_table, 32);
   for (int q = 0; q < 2 && ok; ++q)

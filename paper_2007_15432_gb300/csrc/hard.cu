@@ -56,24 +56,36 @@ __global__ void k_kick(int64_t n, double *vx, double *vy, double *vz,
 
 // ---- row a9: Kepler drift, universal variables ------------------------------
 // Stumpff functions C(z) = sum (-z)^k / (2k+2)!, S(z) = sum (-z)^k / (2k+3)!,
-// as nested series for |z| < 1 and in closed form otherwise.
+// as nested series for |z| < 1 (6 terms below |z| = 1e-2, 10 terms above;
+// truncation below 1e-20 either way) and in closed form otherwise.
 __device__ __forceinline__ void stumpff(double z, double &C, double &S) {
-  if (fabs(z) < 1.0) {
-    // Horner in z with coefficients (-1)^k / (2k+2)! and (-1)^k / (2k+3)!
-    // (compile-time constants: no division at run time); |z| < 1 keeps the
-    // truncation below 1e-20
-    constexpr double c0 = 1.0 / 2.0, c1 = -1.0 / 24.0, c2 = 1.0 / 720.0,
-                     c3 = -1.0 / 40320.0, c4 = 1.0 / 3628800.0,
-                     c5 = -1.0 / 479001600.0, c6 = 1.0 / 87178291200.0,
-                     c7 = -1.0 / 20922789888000.0, c8 = 1.0 / 6402373705728000.0,
-                     c9 = -1.0 / 2432902008176640000.0;
-    constexpr double s0 = 1.0 / 6.0, s1 = -1.0 / 120.0, s2 = 1.0 / 5040.0,
-                     s3 = -1.0 / 362880.0, s4 = 1.0 / 39916800.0,
-                     s5 = -1.0 / 6227020800.0, s6 = 1.0 / 1307674368000.0,
-                     s7 = -1.0 / 355687428096000.0, s8 = 1.0 / 121645100408832000.0,
-                     s9 = -1.0 / 51090942171709440000.0;
-    C = c0 + z * (c1 + z * (c2 + z * (c3 + z * (c4 + z * (c5 + z * (c6 + z * (c7 + z * (c8 + z * c9))))))));
-    S = s0 + z * (s1 + z * (s2 + z * (s3 + z * (s4 + z * (s5 + z * (s6 + z * (s7 + z * (s8 + z * s9))))))));
+  constexpr double c0 = 1.0 / 2.0, c1 = -1.0 / 24.0, c2 = 1.0 / 720.0,
+                   c3 = -1.0 / 40320.0, c4 = 1.0 / 3628800.0,
+                   c5 = -1.0 / 479001600.0, c6 = 1.0 / 87178291200.0,
+                   c7 = -1.0 / 20922789888000.0, c8 = 1.0 / 6402373705728000.0,
+                   c9 = -1.0 / 2432902008176640000.0;
+  constexpr double s0 = 1.0 / 6.0, s1 = -1.0 / 120.0, s2 = 1.0 / 5040.0,
+                   s3 = -1.0 / 362880.0, s4 = 1.0 / 39916800.0,
+                   s5 = -1.0 / 6227020800.0, s6 = 1.0 / 1307674368000.0,
+                   s7 = -1.0 / 355687428096000.0, s8 = 1.0 / 121645100408832000.0,
+                   s9 = -1.0 / 51090942171709440000.0;
+  const double az = fabs(z);
+  if (az < 1e-2) {
+    double c = __fma_rn(z, c5, c4), s = __fma_rn(z, s5, s4);
+    c = __fma_rn(z, c, c3); s = __fma_rn(z, s, s3);
+    c = __fma_rn(z, c, c2); s = __fma_rn(z, s, s2);
+    c = __fma_rn(z, c, c1); s = __fma_rn(z, s, s1);
+    C = __fma_rn(z, c, c0); S = __fma_rn(z, s, s0);
+  } else if (az < 1.0) {
+    double c = __fma_rn(z, c9, c8), s = __fma_rn(z, s9, s8);
+    c = __fma_rn(z, c, c7); s = __fma_rn(z, s, s7);
+    c = __fma_rn(z, c, c6); s = __fma_rn(z, s, s6);
+    c = __fma_rn(z, c, c5); s = __fma_rn(z, s, s5);
+    c = __fma_rn(z, c, c4); s = __fma_rn(z, s, s4);
+    c = __fma_rn(z, c, c3); s = __fma_rn(z, s, s3);
+    c = __fma_rn(z, c, c2); s = __fma_rn(z, s, s2);
+    c = __fma_rn(z, c, c1); s = __fma_rn(z, s, s1);
+    C = __fma_rn(z, c, c0); S = __fma_rn(z, s, s0);
   } else if (z > 0.0) {
     const double q = sqrt(z);
     C = (1.0 - cos(q)) / z;
@@ -85,54 +97,68 @@ __device__ __forceinline__ void stumpff(double z, double &C, double &S) {
   }
 }
 
+// Per-call constants of the drift: mu, sqrt(mu), 1 / sqrt(mu), 1 / mu.
+struct KepConst {
+  double mu, sq, isq, imu;
+};
+
 // Advances (X, V) by dt on the Kepler orbit about mu.  Universal anomaly chi
-// solves sqrt(mu) dt = (r0 v_r0/sqrt(mu)) chi^2 C + (1 - alpha r0) chi^3 S
-// + r0 chi (z = alpha chi^2) by Newton-Raphson; then Lagrange f, g.
-__device__ bool kepler_uv(double X[3], double V[3], double dt, double mu) {
+// solves F(chi) = sig chi^2 C + (1 - alpha r0) chi^3 S + r0 chi - sqrt(mu) dt
+// = 0 (z = alpha chi^2, sig = r0 v_r0 / sqrt(mu)) by Newton-Raphson from the
+// third-order series inversion of F; F'(chi) = r(chi) and F''(chi) = sig (1 -
+// z C) + (1 - alpha r0) chi (1 - z S).  A Newton step d leaves an error of
+// about |F'' / (2 F')| d^2, so the iteration stops once 16 times that bound
+// is below 2^-53 |chi| (or |d| <= 1e-10 |chi|).  Then Lagrange f, g.
+__device__ bool kepler_uv(double X[3], double V[3], double dt, const KepConst &K) {
   const double r0 = sqrt(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
   const double v2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
   const double rv = X[0] * V[0] + X[1] * V[1] + X[2] * V[2];
-  const double ir0 = 1.0 / r0, imu = 1.0 / mu;
-  const double alpha = 2.0 * ir0 - v2 * imu;
-  const double sq = sqrt(mu), isq = 1.0 / sq;
-  const double sig = rv * isq;  // r0 v_r0 / sqrt(mu)
-  const double tau = sq * dt;
-  // series of the universal Kepler equation: chi = tau/r0 - sig tau^2/(2 r0^3) + O(tau^3)
-  double chi = tau * ir0 - 0.5 * sig * tau * tau * ir0 * ir0 * ir0;
-  if (alpha > 0.0) {
-    const double P = 2.0 * 3.141592653589793 / (alpha * sqrt(alpha) * sq);
-    if (fabs(dt) > 0.25 * P) chi = tau * alpha;
-  }
+  const double ir0 = 1.0 / r0;
+  const double alpha = 2.0 * ir0 - v2 * K.imu;
+  const double sig = rv * K.isq;  // r0 v_r0 / sqrt(mu)
+  const double tau = K.sq * dt;
+  const double bet = 1.0 - alpha * r0;
+  // inversion of tau = r0 chi + sig chi^2 / 2 + bet chi^3 / 6 + O(chi^4)
+  const double x1 = tau * ir0, ir02 = ir0 * ir0;
+  double chi = x1 * (1.0 - 0.5 * sig * x1 * ir0 +
+                     (0.5 * sig * sig * ir02 - bet * ir0 * (1.0 / 6.0)) * x1 * x1);
+  // beyond a quarter period (16 dt^2 alpha^3 mu > (2 pi)^2) start from the mean motion
+  if (alpha > 0.0 && 16.0 * dt * dt * alpha * alpha * alpha * K.mu > 4.0 * 9.869604401089358)
+    chi = tau * alpha;
   double C = 0.5, S = 1.0 / 6.0, z = 0.0;
   bool ok = false;
   for (int it = 0; it < 64; ++it) {
     z = alpha * chi * chi;
     stumpff(z, C, S);
     const double chi2 = chi * chi;
-    const double F = sig * chi2 * C + (1.0 - alpha * r0) * chi2 * chi * S + r0 * chi - tau;
-    const double Fp = sig * chi * (1.0 - z * S) + (1.0 - alpha * r0) * chi2 * C + r0;
+    const double F = __fma_rn(sig * chi2, C, __fma_rn(bet * chi2 * chi, S, __fma_rn(r0, chi, -tau)));
+    const double Fp = __fma_rn(sig * chi, __fma_rn(-z, S, 1.0), __fma_rn(bet * chi2, C, r0));
+    const double Fpp = __fma_rn(sig, __fma_rn(-z, C, 1.0), bet * chi * __fma_rn(-z, S, 1.0));
     double d = F / Fp;
     const double lim = 0.5 * (fabs(chi) + r0);
     if (d > lim) d = lim;
     if (d < -lim) d = -lim;
     chi -= d;
-    // quadratic convergence: after a correction below 1e-10 relative the
-    // remaining error (~ its square) is below rounding
-    if (fabs(d) <= 1e-10 * fabs(chi) || d == 0.0) { ok = true; break; }
+    const double rest = 0.5 * fabs(Fpp / Fp) * d * d;
+    if (16.0 * rest <= 1.1102230246251565e-16 * fabs(chi) || fabs(d) <= 1e-10 * fabs(chi) ||
+        d == 0.0) {
+      ok = true;
+      break;
+    }
   }
   z = alpha * chi * chi;
   stumpff(z, C, S);
   const double chi2 = chi * chi;
   const double f = 1.0 - chi2 * ir0 * C;
-  const double g = dt - chi2 * chi * S * isq;
+  const double g = dt - chi2 * chi * S * K.isq;
   double nx[3];
-  for (int a = 0; a < 3; ++a) nx[a] = f * X[a] + g * V[a];
+  for (int a = 0; a < 3; ++a) nx[a] = __fma_rn(f, X[a], g * V[a]);
   const double r = sqrt(nx[0] * nx[0] + nx[1] * nx[1] + nx[2] * nx[2]);
   const double ir = 1.0 / r;
-  const double fd = sq * ir * ir0 * (z * S - 1.0) * chi;
+  const double fd = K.sq * ir * ir0 * (z * S - 1.0) * chi;
   const double gd = 1.0 - chi2 * ir * C;
   for (int a = 0; a < 3; ++a) {
-    const double nv = fd * X[a] + gd * V[a];
+    const double nv = __fma_rn(fd, X[a], gd * V[a]);
     X[a] = nx[a];
     V[a] = nv;
   }
@@ -140,28 +166,28 @@ __device__ bool kepler_uv(double X[3], double V[3], double dt, double mu) {
 }
 
 __global__ void k_kepler(const int64_t *d_nsingle, const int32_t *singles,
-                         p3t_particles p, double dt, double mu, DevStatus *st) {
+                         p3t_particles p, double dt, KepConst K, DevStatus *st) {
   const int64_t ns = *d_nsingle;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ns;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int32_t i = singles[k];
     double X[3] = {p.x[i], p.y[i], p.z[i]}, V[3] = {p.vx[i], p.vy[i], p.vz[i]};
-    if (!kepler_uv(X, V, dt, mu)) dev_fail(st, P3T_ERR_TIMEOUT, 60, 0);
+    if (!kepler_uv(X, V, dt, K)) dev_fail(st, P3T_ERR_TIMEOUT, 60, 0);
     p.x[i] = X[0]; p.y[i] = X[1]; p.z[i] = X[2];
     p.vx[i] = V[0]; p.vy[i] = V[1]; p.vz[i] = V[2];
   }
 }
 
-// ---- row a8 (+ f4): Hermite-4 with block steps, one 128-thread block per ----
-// cluster.  Work items (member components, or (active member, source) terms)
-// are dealt round-robin over the block's four warps, so one cluster keeps the
-// FP64 pipes of all four SM sub-partitions busy: on this part a warp
-// instruction of FP64 occupies its sub-partition's pipe for ~64 cycles, and a
-// cluster's block steps are a serial chain.  Each active member's force is
-// the sum, in the fixed order star term first then sources in ascending
-// index, of terms computed in parallel (clusters of up to kHMax members,
-// state in shared memory) or by one thread per member (larger clusters,
-// state in a global workspace).
+// ---- row a8 (+ f4): Hermite-4 with block steps, one block per cluster ------
+// Clusters of up to 32 members (nearly all) run one warp each, so that the
+// FP64 instructions of their few work items are not spread over idle lanes
+// of several warps; clusters of 33 to 128 members run one 128-thread block
+// each, their work items (member components, or (active member, source)
+// terms) dealt round-robin over the four warps so that one long cluster keeps
+// the FP64 pipes of all four SM sub-partitions busy.  Each active member's
+// force is the sum, in the fixed order star term first then sources in
+// ascending index, of terms computed in parallel (state in shared memory) or,
+// above 128 members, by one thread per member (state in a global workspace).
 //
 // Perfect accretion (row f4, Sec. 2.4.1; on when f_radius > 0 and physical
 // radii are given): at every force evaluation each evaluated member records
@@ -174,21 +200,22 @@ __global__ void k_kepler(const int64_t *d_nsingle, const int32_t *singles,
 // pair energy (changeover functions replaced by unity, the cluster standing
 // for the neighbours).  One thread does this bookkeeping in a fixed order;
 // collisions are rare.
-constexpr int kHB = 128;
-constexpr int kHMax = 128;
+constexpr int kHMax = 128;  // largest cluster kept in shared memory
 constexpr int32_t kNone = 0x7fffffff;  // no collision partner
 
-struct HSmall {  // a cluster of <= kHMax members
-  double x[3][kHMax], v[3][kHMax], a[3][kHMax], j[3][kHMax];
-  double p[3][kHMax], pv[3][kHMax];
-  double a1[3][kHMax], j1[3][kHMax], a2e[3][kHMax], a3[3][kHMax];
-  double m[kHMax], iro[kHMax], rp[kHMax];
-  double T[kHMax + 1][6];  // one batch: B members x (nc + 1) terms, at most kHMax + 1
-  int64_t t[kHMax];
-  int32_t lvl[kHMax], act[kHMax], set[kHMax], nset[kHMax], partner[kHMax], chg[kHMax];
+template <int KM>
+struct HSmall {  // a cluster of <= KM members
+  double x[3][KM], v[3][KM], a[3][KM], j[3][KM];
+  double p[3][KM], pv[3][KM];
+  double a1[3][KM], j1[3][KM], a2e[3][KM], a3[3][KM];
+  double m[KM], iro[KM], rp[KM];
+  double T[KM + 1][6];  // one batch: B members x (nc + 1) terms, at most KM + 1
+  int64_t t[KM];
+  int32_t lvl[KM], act[KM], set[KM], nset[KM], partner[KM], chg[KM];
 };
 
-static_assert(sizeof(HSmall) <= 48 * 1024, "HSmall must fit the default dynamic shared memory");
+static_assert(sizeof(HSmall<kHMax>) <= 48 * 1024,
+              "HSmall must fit the default dynamic shared memory");
 
 struct HCtl {  // per-block control, shared memory
   int64_t red[2][4];
@@ -198,8 +225,9 @@ struct HCtl {  // per-block control, shared memory
   double edisp;
 };
 
+template <int KM>
 struct SmallView {
-  HSmall *S;
+  HSmall<KM> *S;
   static constexpr bool kBig = false;
   __device__ double &x(int q, int k) const { return S->x[q][k]; }
   __device__ double &v(int q, int k) const { return S->v[q][k]; }
@@ -371,18 +399,18 @@ __device__ __forceinline__ void hard_term(const V &S, int nc, int k, int j,
 }
 
 // the members with pred(k), ascending, into act[0..); returns their number
-template <class V, class Pred>
+template <int NT, class V, class Pred>
 __device__ int build_list(const V &S, HCtl &C, int nc, Pred pred) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int base = 0;
-  for (int c0 = 0; c0 < nc; c0 += kHB) {
+  for (int c0 = 0; c0 < nc; c0 += NT) {
     const int k = c0 + tid;
     const bool on = k < nc && pred(k);
     const unsigned bal = __ballot_sync(0xffffffffu, on);
     if (lane == 0) C.wcount[warp] = __popc(bal);
     __syncthreads();
     int off = base, tot = 0;
-    for (int q = 0; q < kHB / 32; ++q) {
+    for (int q = 0; q < NT / 32; ++q) {
       if (q < warp) off += C.wcount[q];
       tot += C.wcount[q];
     }
@@ -396,36 +424,36 @@ __device__ int build_list(const V &S, HCtl &C, int nc, Pred pred) {
 // forces on the listed members act[0..nact) from (p, pv) into (a1, j1); with
 // `detect`, each one's lowest touching partner into partner[]; then the
 // composites' mean force
-template <class V>
-__device__ void block_forces(const V &S, HCtl &C, HSmall *Sm, int nc, int nact, int item,
+template <int NT, class V>
+__device__ void block_forces(const V &S, HCtl &C, double (*Tb)[6], int nc, int nact, int item,
                              const p3t_params &prm, double i1mg, bool detect) {
   if constexpr (!V::kBig) {
     const int per = nc + 1;
-    const int B = kHB / per > 0 ? kHB / per : 1;  // members per batch
+    const int B = NT / per > 0 ? NT / per : 1;  // members per batch
     for (int b0 = 0; b0 < nact; b0 += B) {
       const int nb = min(B, nact - b0);
       const int items = nb * per;
-      for (int i = item; i < items; i += kHB) {
+      for (int i = item; i < items; i += NT) {
         const int bm = i / per, jj = i - bm * per;
         const int k = S.act(b0 + bm);
         bool hit;
-        hard_term(S, nc, k, jj, prm, i1mg, detect, Sm->T[i], hit);
+        hard_term(S, nc, k, jj, prm, i1mg, detect, Tb[i], hit);
         if (hit) atomicMin(&S.partner(k), jj);
       }
       __syncthreads();
-      for (int i = item; i < nb * 6; i += kHB) {
+      for (int i = item; i < nb * 6; i += NT) {
         const int bm = i / 6, q = i - bm * 6;
         const int k = S.act(b0 + bm);
         const int base = bm * per;
         double acc = 0.0;
-        acc -= Sm->T[base + nc][q];
-        for (int jj = 0; jj < nc; ++jj) acc -= Sm->T[base + jj][q];
+        acc -= Tb[base + nc][q];
+        for (int jj = 0; jj < nc; ++jj) acc -= Tb[base + jj][q];
         if (q < 3) S.a1(q, k) = acc; else S.j1(q - 3, k) = acc;
       }
       __syncthreads();
     }
   } else {
-    for (int b = threadIdx.x; b < nact; b += kHB) {
+    for (int b = threadIdx.x; b < nact; b += NT) {
       const int k = S.act(b);
       double acc[6], out[6];
       bool hit;
@@ -442,7 +470,7 @@ __device__ void block_forces(const V &S, HCtl &C, HSmall *Sm, int nc, int nact, 
   }
   if (C.ncomp) {
     // composite force: sum_l m_l a_l / sum_l m_l, ascending l (sets of >= 2)
-    for (int b = item; b < nact; b += kHB) {
+    for (int b = item; b < nact; b += NT) {
       const int r = S.act(b);
       if (S.set(r) != r) continue;
       int size = 0;
@@ -463,6 +491,7 @@ __device__ void block_forces(const V &S, HCtl &C, HSmall *Sm, int nc, int nact, 
   }
 }
 
+template <int NT>
 __device__ __forceinline__ int64_t block_min(int64_t v, int64_t *red4) {
   for (int o = 16; o > 0; o >>= 1) {
     const int64_t u = __shfl_xor_sync(0xffffffffu, v, o);
@@ -471,7 +500,7 @@ __device__ __forceinline__ int64_t block_min(int64_t v, int64_t *red4) {
   if ((threadIdx.x & 31) == 0) red4[threadIdx.x >> 5] = v;
   __syncthreads();
   int64_t r = red4[0];
-  for (int q = 1; q < kHB / 32; ++q) r = red4[q] < r ? red4[q] : r;
+  for (int q = 1; q < NT / 32; ++q) r = red4[q] < r ? red4[q] : r;
   __syncthreads();
   return r;
 }
@@ -586,18 +615,18 @@ __device__ void emit_composites(const V &S, const HCtl &C, int nc, int64_t off,
 }
 
 // block-step integration of one cluster (the whole block takes part)
-template <class V>
-__device__ void integrate_cluster(const V &S, HCtl &C, HSmall *Sm, int64_t off, int nc,
+template <int NT, class V>
+__device__ void integrate_cluster(const V &S, HCtl &C, double (*Tb)[6], int64_t off, int nc,
                                   const int32_t *cl_mem, const p3t_particles &p,
                                   const p3t_params &prm, double dt, bool coll,
                                   const CollOut &co, unsigned long long &steps,
                                   bool &underflow, DevStatus *st) {
   const int tid = threadIdx.x;
-  const int item = (tid & 31) * (kHB / 32) + (tid >> 5);  // consecutive items -> different warps
+  const int item = (tid & 31) * (NT / 32) + (tid >> 5);  // consecutive items -> different warps
   const int64_t T = ((int64_t)1) << P3T_KMAX;
   const double unit = ldexp(dt, -P3T_KMAX);
   const double i1mg = 1.0 / (1.0 - prm.gamma);
-  for (int k = item; k < nc; k += kHB) {
+  for (int k = item; k < nc; k += NT) {
     const int32_t i = cl_mem[off + k];
     S.x(0, k) = p.x[i]; S.x(1, k) = p.y[i]; S.x(2, k) = p.z[i];
     S.v(0, k) = p.vx[i]; S.v(1, k) = p.vy[i]; S.v(2, k) = p.vz[i];
@@ -612,9 +641,9 @@ __device__ void integrate_cluster(const V &S, HCtl &C, HSmall *Sm, int64_t off, 
   __syncthreads();
   // initial forces of every member (the block-time state is the initial
   // state), first steps
-  int nact = build_list(S, C, nc, [](int) { return true; });
-  block_forces(S, C, Sm, nc, nact, item, prm, i1mg, coll);
-  for (int k = item; k < nc; k += kHB) {
+  int nact = build_list<NT>(S, C, nc, [](int) { return true; });
+  block_forces<NT>(S, C, Tb, nc, nact, item, prm, i1mg, coll);
+  for (int k = item; k < nc; k += NT) {
     for (int q = 0; q < 3; ++q) { S.a(q, k) = S.a1(q, k); S.j(q, k) = S.j1(q, k); }
     S.t(k) = 0;
     S.lvl(k) = first_level(S, k, prm, dt, 0, underflow);
@@ -625,39 +654,39 @@ __device__ void integrate_cluster(const V &S, HCtl &C, HSmall *Sm, int64_t off, 
   for (;;) {
     if (C.any) {
       // collisions found by the last evaluation: every member's state at tn
-      for (int k = item; k < nc; k += kHB)
+      for (int k = item; k < nc; k += NT)
         if (S.t(k) == tn)
           for (int q = 0; q < 3; ++q) { S.p(q, k) = S.x(q, k); S.pv(q, k) = S.v(q, k); }
       __syncthreads();
       if (tid == 0) collide_serial(S, C, nc, tn, prm);
       __syncthreads();
-      nact = build_list(S, C, nc, [&](int k) { return (S.chg(k) & 1) != 0; });
-      block_forces(S, C, Sm, nc, nact, item, prm, i1mg, false);
-      for (int b = item; b < nact; b += kHB) {
+      nact = build_list<NT>(S, C, nc, [&](int k) { return (S.chg(k) & 1) != 0; });
+      block_forces<NT>(S, C, Tb, nc, nact, item, prm, i1mg, false);
+      for (int b = item; b < nact; b += NT) {
         const int k = S.act(b);
         for (int q = 0; q < 3; ++q) { S.a(q, k) = S.a1(q, k); S.j(q, k) = S.j1(q, k); }
         S.lvl(k) = first_level(S, k, prm, dt, tn, underflow);
       }
-      for (int k = item; k < nc; k += kHB) S.partner(k) = kNone;
+      for (int k = item; k < nc; k += NT) S.partner(k) = kNone;
       __syncthreads();
       if (tid == 0) C.any = 0;
       __syncthreads();
     }
     int64_t e_min = T, t_min = T;
-    for (int k = tid; k < nc; k += kHB) {
+    for (int k = tid; k < nc; k += NT) {
       const int64_t e = S.t(k) + (T >> S.lvl(k));
       e_min = e < e_min ? e : e_min;
       t_min = S.t(k) < t_min ? S.t(k) : t_min;
     }
-    tn = block_min(e_min, C.red[0]);
-    const int64_t tmin = block_min(t_min, C.red[1]);
+    tn = block_min<NT>(e_min, C.red[0]);
+    const int64_t tmin = block_min<NT>(t_min, C.red[1]);
     if (tmin >= T) break;
     if (++iter > kHermiteIterLimit) {
       if (tid == 0) dev_fail(st, P3T_ERR_TIMEOUT, 61, 0);
       break;
     }
     // predict every member (component items)
-    for (int i = item; i < nc * 3; i += kHB) {
+    for (int i = item; i < nc * 3; i += NT) {
       const int k = i / 3, q = i - 3 * k;
       const double D = (double)(tn - S.t(k)) * unit;
       const double D2 = D * D, D3 = D2 * D;
@@ -665,10 +694,10 @@ __device__ void integrate_cluster(const V &S, HCtl &C, HSmall *Sm, int64_t off, 
       S.pv(q, k) = S.v(q, k) + S.a(q, k) * D + S.j(q, k) * D2 * 0.5;
     }
     __syncthreads();
-    nact = build_list(S, C, nc, [&](int k) { return S.t(k) + (T >> S.lvl(k)) == tn; });
-    block_forces(S, C, Sm, nc, nact, item, prm, i1mg, coll);
+    nact = build_list<NT>(S, C, nc, [&](int k) { return S.t(k) + (T >> S.lvl(k)) == tn; });
+    block_forces<NT>(S, C, Tb, nc, nact, item, prm, i1mg, coll);
     // correct (component items of the active members)
-    for (int i = item; i < nact * 3; i += kHB) {
+    for (int i = item; i < nact * 3; i += NT) {
       const int b = i / 3, q = i - 3 * b;
       const int k = S.act(b);
       const double D = (double)(T >> S.lvl(k)) * unit;
@@ -687,7 +716,7 @@ __device__ void integrate_cluster(const V &S, HCtl &C, HSmall *Sm, int64_t off, 
     }
     __syncthreads();
     // new steps of the active members
-    for (int b = item; b < nact; b += kHB) {
+    for (int b = item; b < nact; b += NT) {
       const int k = S.act(b);
       const double D = (double)(T >> S.lvl(k)) * unit;
       const int e = ilogb(D);  // dt = sqrt(eta num_s / den_s) s
@@ -704,7 +733,7 @@ __device__ void integrate_cluster(const V &S, HCtl &C, HSmall *Sm, int64_t off, 
     if (tid == 0) steps += (unsigned long long)nact;
     __syncthreads();
   }
-  for (int k = item; k < nc; k += kHB) {
+  for (int k = item; k < nc; k += NT) {
     const int32_t i = cl_mem[off + k];
     p.x[i] = S.x(0, k); p.y[i] = S.x(1, k); p.z[i] = S.x(2, k);
     p.vx[i] = S.v(0, k); p.vy[i] = S.v(1, k); p.vz[i] = S.v(2, k);
@@ -713,17 +742,18 @@ __device__ void integrate_cluster(const V &S, HCtl &C, HSmall *Sm, int64_t off, 
   __syncthreads();
 }
 
-// clusters of <= kHMax members (BIG = false) or more (BIG = true); one block
+// clusters of nc_lo..nc_hi members; NT threads per block; state in shared
+// memory for up to KM members or (BIG) in the global workspace.  One block
 // per cluster, clusters handed out dynamically (a long encounter keeps its
-// block while the others move on)
-template <bool BIG>
-__global__ void __launch_bounds__(kHB) k_hermite_block(
+// block while the others move on).
+template <int NT, int KM, bool BIG>
+__global__ void __launch_bounds__(NT) k_hermite_block(
     const int64_t *d_ncl, const int64_t *cl_off, const int32_t *cl_mem, p3t_particles p,
-    p3t_params prm, double dt, unsigned long long *steps_out, int64_t *cursor, HBig big,
-    CollOut co, DevStatus *st) {
+    p3t_params prm, double dt, int nc_lo, int nc_hi, unsigned long long *steps_out,
+    int64_t *cursor, HBig big, CollOut co, DevStatus *st) {
   __shared__ HCtl C;
   extern __shared__ __align__(16) unsigned char hsm[];
-  HSmall *Sm = reinterpret_cast<HSmall *>(hsm);
+  HSmall<KM> *Sm = reinterpret_cast<HSmall<KM> *>(hsm);
   const int tid = threadIdx.x;
   const int64_t ncl = *d_ncl;
   const bool coll = prm.f_radius > 0.0 && p.r_phys != nullptr;
@@ -737,22 +767,22 @@ __global__ void __launch_bounds__(kHB) k_hermite_block(
     if (c >= ncl) break;
     const int64_t off = cl_off[c];
     const int nc = (int)(cl_off[c + 1] - off);
-    if ((nc > kHMax) != BIG) continue;
+    if (nc < nc_lo || nc > nc_hi) continue;
     if constexpr (BIG) {
       const BigView S{big.d, big.t, big.i, big.cap, off};
-      integrate_cluster(S, C, nullptr, off, nc, cl_mem, p, prm, dt, coll, co, steps,
-                        underflow, st);
+      integrate_cluster<NT>(S, C, nullptr, off, nc, cl_mem, p, prm, dt, coll, co, steps,
+                            underflow, st);
     } else {
-      const SmallView S{Sm};
-      integrate_cluster(S, C, Sm, off, nc, cl_mem, p, prm, dt, coll, co, steps, underflow,
-                        st);
+      const SmallView<KM> S{Sm};
+      integrate_cluster<NT>(S, C, Sm->T, off, nc, cl_mem, p, prm, dt, coll, co, steps,
+                            underflow, st);
     }
   }
   if (underflow) dev_fail(st, P3T_ERR_DT_UNDERFLOW, 62, 0);
   if (tid == 0 && steps_out && steps) atomicAdd(steps_out, steps);
 }
 
-__global__ void k_zero_i64_two(int64_t *p) { p[0] = 0; p[1] = 0; }
+__global__ void k_zero_i64_three(int64_t *p) { p[0] = 0; p[1] = 0; p[2] = 0; }
 
 __global__ void k_zero_u64(unsigned long long *p) { *p = 0ull; }
 
@@ -966,7 +996,7 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
   unsigned long long *steps = n_steps ? reinterpret_cast<unsigned long long *>(n_steps)
                                       : c->hsteps;
   k_zero_u64<<<1, 1, 0, s>>>(steps);
-  k_zero_i64_two<<<1, 1, 0, s>>>(c->hcursor);
+  k_zero_i64_three<<<1, 1, 0, s>>>(c->hcursor);
   // Kepler drift, small clusters and large clusters touch disjoint particles:
   // run them on three streams forked from and joined back to the caller's
   P3T_CUDA_TRY(cudaEventRecord(c->ev_fork, s));
@@ -974,20 +1004,31 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
   P3T_CUDA_TRY(cudaStreamWaitEvent(c->aux[1], c->ev_fork, 0));
   const int64_t ncl_max = (n / 2) > 0 ? n / 2 : 1;
   const int64_t nbig = c->num_sms < 32 ? c->num_sms : 32;
-  k_hermite_block<false><<<(unsigned)p3t_grid(ncl_max * kHB, kHB, (int64_t)c->num_sms * 4), kHB,
-                           sizeof(HSmall), c->aux[0]>>>(&cl->counts[1], cl->cl_off, cl->cl_mem,
-                                                        *p, c->prm, dt, steps, c->hcursor, big,
-                                                        co, c->status);
-  k_hermite_block<true><<<(unsigned)p3t_grid(ncl_max, 1, nbig), kHB, 0, c->aux[1]>>>(
-      &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, steps, c->hcursor + 1, big, co,
+  // clusters of 2..32 members: a warp each (stream aux[0]); 33..128: a
+  // 128-thread block each, then > 128 (stream aux[1])
+  k_hermite_block<32, 32, false><<<(unsigned)p3t_grid(ncl_max * 32, 32, (int64_t)c->num_sms * 16),
+                                   32, sizeof(HSmall<32>), c->aux[0]>>>(
+      &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, 2, 32, steps, c->hcursor, big, co,
       c->status);
+  k_hermite_block<128, kHMax, false><<<(unsigned)p3t_grid(ncl_max * 128, 128, (int64_t)c->num_sms * 2),
+                                       128, sizeof(HSmall<kHMax>), c->aux[1]>>>(
+      &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, 33, kHMax, steps, c->hcursor + 1,
+      big, co, c->status);
+  k_hermite_block<128, 1, true><<<(unsigned)p3t_grid(ncl_max, 1, nbig), 128, 0, c->aux[1]>>>(
+      &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, kHMax + 1, 0x7fffffff, steps,
+      c->hcursor + 2, big, co, c->status);
+  KepConst kc;
+  kc.mu = mu;
+  kc.sq = sqrt(mu);
+  kc.isq = 1.0 / kc.sq;
+  kc.imu = 1.0 / mu;
   k_kepler<<<(unsigned)p3t_grid(n, 128, maxb), 128, 0, s>>>(&cl->counts[0], cl->singles, *p,
-                                                             dt, mu, c->status);
+                                                             dt, kc, c->status);
   P3T_CUDA_TRY(cudaEventRecord(c->ev_join[0], c->aux[0]));
   P3T_CUDA_TRY(cudaEventRecord(c->ev_join[1], c->aux[1]));
   P3T_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[0], 0));
   P3T_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[1], 0));
-  p3t_note_launches(5);
+  p3t_note_launches(6);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 

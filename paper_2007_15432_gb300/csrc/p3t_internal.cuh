@@ -139,7 +139,7 @@ struct p3t_ctx {
   int64_t *ht = nullptr;                   // time in units of dt / 2^40
   int32_t *hl = nullptr;                   // 6 * cap: level, list, sets, partner, flags
   unsigned long long *hsteps = nullptr;    // device counter
-  int64_t *hcursor = nullptr;              // [2] cluster cursors of the two Hermite kernels
+  int64_t *hcursor = nullptr;              // [3] cluster cursors of the three Hermite kernels
 
   // composites of colliding particles, from the hard step to the merge
   unsigned long long *coll_ctr = nullptr;  // (records << 32) | entries

@@ -84,7 +84,7 @@ __global__ void scan_apply_kernel(const int32_t *in, int64_t *out,
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
+constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 
 __global__ void radix_upsweep(const uint64_t *keys, const int64_t *d_n,
@@ -94,9 +94,12 @@ __global__ void radix_upsweep(const uint64_t *keys, const int64_t *d_n,
   __syncthreads();
   const int64_t n = *d_n;
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  const int lane = threadIdx.x & 31;
   for (int k = 0; k < kSortItems; ++k) {
-    int64_t e = base + k * kSortThreads + threadIdx.x;
-    if (e < n) atomicAdd(&h[(keys[e] >> shift) & (kRadix - 1)], 1u);
+    const int64_t e = base + k * kSortThreads + threadIdx.x;
+    const uint32_t d = e < n ? (uint32_t)((keys[e] >> shift) & (kRadix - 1)) : kRadix;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);  // one atomic per digit and warp
+    if (d < kRadix && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
   }
   __syncthreads();
   hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
@@ -120,38 +123,49 @@ __global__ void __launch_bounds__(kRadix) radix_row_scan(uint32_t *hist, int nti
   if (threadIdx.x == 0) digit_total[blockIdx.x] = (uint32_t)carry;
 }
 
+// Stable scatter of one tile: the tile's elements are ranked by (digit,
+// position), placed digit-ordered in shared memory, then written out so that
+// consecutive threads write consecutive addresses of one digit's run.
 __global__ void __launch_bounds__(kSortThreads)
 radix_downsweep(const uint64_t *keys, const int32_t *vals, uint64_t *okeys,
                 int32_t *ovals, const int64_t *d_n, int shift,
                 const uint32_t *hist, int ntiles, const uint32_t *digit_total) {
   __shared__ uint32_t s_warp[kSortThreads / 32][kRadix];
   __shared__ uint32_t s_run[kRadix];
-  __shared__ uint32_t s_base[kRadix];
+  __shared__ uint32_t s_gbase[kRadix];  // first output index of the tile's digit d
+  __shared__ uint32_t s_lbase[kRadix];  // first tile position of digit d
   __shared__ int64_t sh[33];
+  __shared__ uint64_t s_key[kSortTile];
+  __shared__ int32_t s_val[kSortTile];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   s_run[t] = 0;
   {
     int64_t ex;
     block_excl_scan((int64_t)digit_total[t], &ex, sh);   // digit bases
-    s_base[t] = (uint32_t)ex + hist[(int64_t)t * ntiles + blockIdx.x];
+    s_gbase[t] = (uint32_t)ex + hist[(int64_t)t * ntiles + blockIdx.x];
   }
   const int64_t n = *d_n;
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   const uint32_t lt = (1u << lane) - 1u;
+  uint64_t key[kSortItems];
+  int32_t val[kSortItems];
+  uint32_t dig[kSortItems], rk[kSortItems];
+#pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
 #pragma unroll
     for (int k = 0; k < kSortThreads / 32; ++k) s_warp[k][t] = 0;
     __syncthreads();
     const int64_t e = base + r * kSortThreads + t;
     const bool valid = e < n;
-    uint64_t key = 0;
-    int32_t val = 0;
+    key[r] = 0;
+    val[r] = 0;
     uint32_t d = kRadix;  // invalid lanes form their own group
     if (valid) {
-      key = keys[e];
-      val = vals[e];
-      d = (uint32_t)((key >> shift) & (kRadix - 1));
+      key[r] = keys[e];
+      val[r] = vals[e];
+      d = (uint32_t)((key[r] >> shift) & (kRadix - 1));
     }
+    dig[r] = d;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     if (valid && lane == __ffs(peers) - 1) s_warp[w][d] = __popc(peers);
     __syncthreads();
@@ -166,12 +180,30 @@ radix_downsweep(const uint64_t *keys, const int32_t *vals, uint64_t *okeys,
       s_run[t] = run;
     }
     __syncthreads();
-    if (valid) {
-      const uint32_t dst = s_base[d] + s_warp[w][d] + __popc(peers & lt);
-      okeys[dst] = key;
-      ovals[dst] = val;
-    }
+    rk[r] = valid ? s_warp[w][d] + __popc(peers & lt) : 0;  // rank within the tile's digit
     __syncthreads();
+  }
+  {
+    int64_t ex;
+    block_excl_scan((int64_t)s_run[t], &ex, sh);
+    s_lbase[t] = (uint32_t)ex;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r)
+    if (dig[r] < kRadix) {
+      const uint32_t pos = s_lbase[dig[r]] + rk[r];
+      s_key[pos] = key[r];
+      s_val[pos] = val[r];
+    }
+  __syncthreads();
+  const int64_t tn = n - base < kSortTile ? n - base : kSortTile;
+  for (int i = t; i < tn; i += kSortThreads) {
+    const uint64_t k = s_key[i];
+    const uint32_t d = (uint32_t)((k >> shift) & (kRadix - 1));
+    const uint32_t dst = s_gbase[d] + ((uint32_t)i - s_lbase[d]);
+    okeys[dst] = k;
+    ovals[dst] = s_val[i];
   }
 }
 

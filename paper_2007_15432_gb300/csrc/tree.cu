@@ -133,8 +133,11 @@ __global__ void k_box_init(unsigned long long *bits) {
   if (threadIdx.x < 3) { bits[threadIdx.x] = ~0ull; bits[3 + threadIdx.x] = 0ull; }
 }
 
+// min / max of the positions: warp and block reductions, then six atomics
+// per block (launched with a few blocks per SM)
 __global__ void k_box(int64_t n, const double *x, const double *y,
                       const double *z, unsigned long long *bits) {
+  __shared__ unsigned long long red[6][kBlock / 32];
   unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -150,7 +153,15 @@ __global__ void k_box(int64_t n, const double *x, const double *y,
       lo[a] = u < lo[a] ? u : lo[a];
       hi[a] = v > hi[a] ? v : hi[a];
     }
-    if ((threadIdx.x & 31) == 0) { atomicMin(&bits[a], lo[a]); atomicMax(&bits[3 + a], hi[a]); }
+    if ((threadIdx.x & 31) == 0) { red[a][threadIdx.x >> 5] = lo[a]; red[3 + a][threadIdx.x >> 5] = hi[a]; }
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int a = threadIdx.x;
+    unsigned long long r = red[a][0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      r = a < 3 ? (red[a][w] < r ? red[a][w] : r) : (red[a][w] > r ? red[a][w] : r);
+    if (a < 3) atomicMin(&bits[a], r); else atomicMax(&bits[a], r);
   }
 }
 
@@ -161,6 +172,7 @@ __global__ void k_box_final(const unsigned long long *bits, double *box) {
   double L = fmax(hi[0] - lo[0], fmax(hi[1] - lo[1], hi[2] - lo[2]));
   if (!(L > 0.0)) L = 1.0;
   box[0] = lo[0]; box[1] = lo[1]; box[2] = lo[2]; box[3] = L;
+  box[4] = (double)P3T_QMAX / L;  // quantisation scale S
 }
 
 __device__ __forceinline__ uint64_t spread3(uint64_t v) {
@@ -182,9 +194,9 @@ __device__ __forceinline__ uint32_t compact3(uint64_t v) {
   return (uint32_t)v;
 }
 
-__device__ __forceinline__ uint64_t quantise(double v, double lo, double L) {
-  double t = (v - lo) / L;
-  double f = floor(t * (double)P3T_QMAX);
+// cell index floor((v - lo) S), S = 2^21 / L formed once per build
+__device__ __forceinline__ uint64_t quantise(double v, double lo, double S) {
+  double f = floor((v - lo) * S);
   if (f < 0.0) f = 0.0;
   if (f > (double)(P3T_QMAX - 1)) f = (double)(P3T_QMAX - 1);
   return (uint64_t)f;
@@ -193,10 +205,10 @@ __device__ __forceinline__ uint64_t quantise(double v, double lo, double L) {
 __global__ void k_keys(int64_t n, const double *x, const double *y,
                        const double *z, const double *box, uint64_t *keys,
                        int32_t *idx) {
-  const double x0 = box[0], y0 = box[1], z0 = box[2], L = box[3];
+  const double x0 = box[0], y0 = box[1], z0 = box[2], S = box[4];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t qx = quantise(x[i], x0, L), qy = quantise(y[i], y0, L), qz = quantise(z[i], z0, L);
+    uint64_t qx = quantise(x[i], x0, S), qy = quantise(y[i], y0, S), qz = quantise(z[i], z0, S);
     keys[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
     idx[i] = (int32_t)i;
   }
@@ -221,7 +233,7 @@ __global__ void k_gather(int64_t n, const int32_t *idx, const uint64_t *keys,
     const float xh = (float)X, yh = (float)Y, zh = (float)Z;
     spA[s] = make_float4(xh, yh, zh, (float)M);
     spB[s] = make_float4((float)(X - (double)xh), (float)(Y - (double)yh),
-                         (float)(Z - (double)zh), (float)(1.0 / RO));
+                         (float)(Z - (double)zh), 1.0f / (float)RO);  // FP32 path only
     srs32[s] = (float)RS;
   }
 }
@@ -419,87 +431,112 @@ __device__ __forceinline__ void finish_node(TreeNode *nd, Mom64 *m64, Mom32 *m32
   m32[b] = f;
 }
 
-// Bottom-up moments.  One thread per leaf computes the leaf from its
-// particles (definition: com, then Q about com); the last child to arrive at
-// a parent combines the children (parallel-axis shift of Q) and climbs on.
-__global__ void k_moments(const int64_t *d_nleaf, const int32_t *leaf_list,
-                          TreeNode *node, Mom64 *m64, Mom32 *m32, double *nrs,
-                          int32_t *node_done, const double *sx, const double *sy,
-                          const double *sz, const double *sm, const double *srs,
-                          const int32_t *sq, const double *box) {
+// Moments, one thread per node, level by level with no atomics: first every
+// leaf from its members, then the internal nodes of one level per launch,
+// deepest level first, from their (finished) children.  (A warp instruction
+// of FP64 occupies a sub-partition's pipe for ~64 cycles however few of its
+// lanes are active, so every lane carries a node of its own.)  A leaf's
+// members are summed about a reference point r (its first member): M, D =
+// sum m d, S_ab = sum m d_a d_b with d = x - r; then com = r + D / M and the
+// traceless quadrupole about the com, Q_ab = 3 C_ab - delta_ab tr C with C_ab
+// = S_ab - M e_a e_b, e = D / M (the definition sum m (3 d'_a d'_b - d'^2
+// delta_ab), d' = x - com, expanded).  An internal node sums its children with
+// the parallel-axis shift of Q.
+__global__ void k_moments_leaf(
+    const int64_t *d_nleaf, const int32_t *leaf_list, TreeNode *node, Mom64 *m64, Mom32 *m32,
+    double *nrs, const double *sx, const double *sy, const double *sz, const double *sm,
+    const double *srs, const int32_t *sq, const double *box) {
   const int64_t nleaf = *d_nleaf;
   const double u = ldexp(box[3], -P3T_BITS);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nleaf;
        t += (int64_t)gridDim.x * blockDim.x) {
-    int64_t b = leaf_list[t];
+    const int64_t b = leaf_list[t];
     TreeNode *nd = &node[b];
     const int32_t f = nd->first, c = nd->count;
+    const double rx = sx[f], ry = sy[f], rz = sz[f];
+    double M = 0.0, D[3] = {0, 0, 0}, S[6] = {0, 0, 0, 0, 0, 0}, rs = 0.0;
+    int32_t lo[3] = {P3T_QMAX, P3T_QMAX, P3T_QMAX}, hi[3] = {-1, -1, -1};
+    for (int32_t i = f; i < f + c; ++i) {
+      const double m = sm[i], dx = sx[i] - rx, dy = sy[i] - ry, dz = sz[i] - rz;
+      const double mx = m * dx, my = m * dy, mz = m * dz;
+      M += m; D[0] += mx; D[1] += my; D[2] += mz;
+      S[0] = __fma_rn(mx, dx, S[0]); S[1] = __fma_rn(my, dy, S[1]); S[2] = __fma_rn(mz, dz, S[2]);
+      S[3] = __fma_rn(mx, dy, S[3]); S[4] = __fma_rn(mx, dz, S[4]); S[5] = __fma_rn(my, dz, S[5]);
+      rs = fmax(rs, srs[i]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) { lo[a] = min(lo[a], sq[3 * i + a]); hi[a] = max(hi[a], sq[3 * i + a]); }
+    }
     Mom64 mm = {};
-    double M = 0.0, sxm = 0.0, sym = 0.0, szm = 0.0, rsmax = 0.0;
-    int32_t qlo[3] = {P3T_QMAX, P3T_QMAX, P3T_QMAX}, qhi[3] = {-1, -1, -1};
-    for (int32_t i = f; i < f + c; ++i) {
-      M += sm[i]; sxm += sm[i] * sx[i]; sym += sm[i] * sy[i]; szm += sm[i] * sz[i];
-      rsmax = fmax(rsmax, srs[i]);
-      for (int a = 0; a < 3; ++a) { qlo[a] = min(qlo[a], sq[3 * i + a]); qhi[a] = max(qhi[a], sq[3 * i + a]); }
+    const double iM = 1.0 / M;
+    const double e[3] = {D[0] * iM, D[1] * iM, D[2] * iM};
+    mm.M = M; mm.cx = rx + e[0]; mm.cy = ry + e[1]; mm.cz = rz + e[2];
+    const double Cxx = S[0] - M * e[0] * e[0], Cyy = S[1] - M * e[1] * e[1],
+                 Czz = S[2] - M * e[2] * e[2];
+    const double tr = Cxx + Cyy + Czz;
+    mm.qxx = 3.0 * Cxx - tr; mm.qyy = 3.0 * Cyy - tr; mm.qzz = 3.0 * Czz - tr;
+    mm.qxy = 3.0 * (S[3] - M * e[0] * e[1]);
+    mm.qxz = 3.0 * (S[4] - M * e[0] * e[2]);
+    mm.qyz = 3.0 * (S[5] - M * e[1] * e[2]);
+    for (int a = 0; a < 3; ++a) { nd->qlo[a] = lo[a]; nd->qhi[a] = hi[a]; }
+    nrs[b] = rs;
+    finish_node(nd, m64, m32, rs, u, b, mm);
+  }
+}
+
+// first breadth-first id at level >= l (levels ascend in breadth-first order)
+__device__ __forceinline__ int64_t level_begin(const TreeNode *node, int64_t nn, int l) {
+  int64_t lo = 0, hi = nn;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (node[mid].level < l) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_moments_level(int level, const int64_t *d_nnode, int64_t node_cap,
+                                TreeNode *node, Mom64 *m64, Mom32 *m32, double *nrs,
+                                const double *box) {
+  __shared__ int64_t range[2];
+  const int64_t nn = min(*d_nnode, node_cap);
+  if (threadIdx.x < 2) range[threadIdx.x] = level_begin(node, nn, level + (int)threadIdx.x);
+  __syncthreads();
+  const int64_t b0 = range[0], b1 = range[1];
+  if (b0 >= b1) return;
+  const double u = ldexp(box[3], -P3T_BITS);
+  for (int64_t b = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < b1;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    TreeNode *pn = &node[b];
+    const int32_t c0 = pn->child0, nch = pn->nchild;
+    if (nch == 0) continue;  // a leaf: done already
+    double PM = 0.0, P[3] = {0, 0, 0}, prs = 0.0;
+    int32_t plo[3] = {P3T_QMAX, P3T_QMAX, P3T_QMAX}, phi[3] = {-1, -1, -1};
+    for (int k = 0; k < nch; ++k) {
+      const Mom64 &cm = m64[c0 + k];
+      PM += cm.M;
+      P[0] = __fma_rn(cm.M, cm.cx, P[0]);
+      P[1] = __fma_rn(cm.M, cm.cy, P[1]);
+      P[2] = __fma_rn(cm.M, cm.cz, P[2]);
+      prs = fmax(prs, nrs[c0 + k]);
+      const TreeNode &cn = node[c0 + k];
+      for (int a = 0; a < 3; ++a) { plo[a] = min(plo[a], cn.qlo[a]); phi[a] = max(phi[a], cn.qhi[a]); }
     }
-    mm.M = M; mm.cx = sxm / M; mm.cy = sym / M; mm.cz = szm / M;
-    for (int32_t i = f; i < f + c; ++i) {
-      double dx = sx[i] - mm.cx, dy = sy[i] - mm.cy, dz = sz[i] - mm.cz;
-      double d2 = dx * dx + dy * dy + dz * dz;
-      mm.qxx += sm[i] * (3.0 * dx * dx - d2);
-      mm.qyy += sm[i] * (3.0 * dy * dy - d2);
-      mm.qzz += sm[i] * (3.0 * dz * dz - d2);
-      mm.qxy += sm[i] * (3.0 * dx * dy);
-      mm.qxz += sm[i] * (3.0 * dx * dz);
-      mm.qyz += sm[i] * (3.0 * dy * dz);
+    Mom64 pm = {};
+    const double iM = 1.0 / PM;
+    pm.M = PM; pm.cx = P[0] * iM; pm.cy = P[1] * iM; pm.cz = P[2] * iM;
+    for (int k = 0; k < nch; ++k) {
+      const Mom64 &cm = m64[c0 + k];
+      const double dx = cm.cx - pm.cx, dy = cm.cy - pm.cy, dz = cm.cz - pm.cz;
+      const double d2 = dx * dx + dy * dy + dz * dz;
+      pm.qxx += cm.qxx + cm.M * (3.0 * dx * dx - d2);
+      pm.qyy += cm.qyy + cm.M * (3.0 * dy * dy - d2);
+      pm.qzz += cm.qzz + cm.M * (3.0 * dz * dz - d2);
+      pm.qxy += cm.qxy + cm.M * (3.0 * dx * dy);
+      pm.qxz += cm.qxz + cm.M * (3.0 * dx * dz);
+      pm.qyz += cm.qyz + cm.M * (3.0 * dy * dz);
     }
-    for (int a = 0; a < 3; ++a) { nd->qlo[a] = qlo[a]; nd->qhi[a] = qhi[a]; }
-    nrs[b] = rsmax;
-    finish_node(nd, m64, m32, rsmax, u, b, mm);
-    // climb
-    for (;;) {
-      const int32_t par = nd->parent;
-      if (par < 0) break;
-      __threadfence();
-      const int32_t prev = atomicAdd(&node_done[par], 1);
-      TreeNode *pn = &node[par];
-      const int32_t c0 = __ldcg(&pn->child0), nc = __ldcg(&pn->nchild);
-      if (prev != nc - 1) break;
-      __threadfence();
-      Mom64 pm = {};
-      double PM = 0.0, px = 0.0, py = 0.0, pz = 0.0, prs = 0.0;
-      int32_t plo[3] = {P3T_QMAX, P3T_QMAX, P3T_QMAX}, phi[3] = {-1, -1, -1};
-      for (int k = 0; k < nc; ++k) {
-        const Mom64 *cm = &m64[c0 + k];
-        const double cM = __ldcg(&cm->M);
-        PM += cM;
-        px += cM * __ldcg(&cm->cx); py += cM * __ldcg(&cm->cy); pz += cM * __ldcg(&cm->cz);
-        prs = fmax(prs, __ldcg(&nrs[c0 + k]));
-        const TreeNode *cn = &node[c0 + k];
-        for (int a = 0; a < 3; ++a) {
-          plo[a] = min(plo[a], __ldcg(&cn->qlo[a]));
-          phi[a] = max(phi[a], __ldcg(&cn->qhi[a]));
-        }
-      }
-      pm.M = PM; pm.cx = px / PM; pm.cy = py / PM; pm.cz = pz / PM;
-      for (int k = 0; k < nc; ++k) {
-        const Mom64 *cm = &m64[c0 + k];
-        const double cM = __ldcg(&cm->M);
-        const double dx = __ldcg(&cm->cx) - pm.cx, dy = __ldcg(&cm->cy) - pm.cy,
-                     dz = __ldcg(&cm->cz) - pm.cz;
-        const double d2 = dx * dx + dy * dy + dz * dz;
-        pm.qxx += __ldcg(&cm->qxx) + cM * (3.0 * dx * dx - d2);
-        pm.qyy += __ldcg(&cm->qyy) + cM * (3.0 * dy * dy - d2);
-        pm.qzz += __ldcg(&cm->qzz) + cM * (3.0 * dz * dz - d2);
-        pm.qxy += __ldcg(&cm->qxy) + cM * (3.0 * dx * dy);
-        pm.qxz += __ldcg(&cm->qxz) + cM * (3.0 * dx * dz);
-        pm.qyz += __ldcg(&cm->qyz) + cM * (3.0 * dy * dz);
-      }
-      for (int a = 0; a < 3; ++a) { pn->qlo[a] = plo[a]; pn->qhi[a] = phi[a]; }
-      nrs[par] = prs;
-      finish_node(pn, m64, m32, prs, u, par, pm);
-      nd = pn;
-    }
+    for (int a = 0; a < 3; ++a) { pn->qlo[a] = plo[a]; pn->qhi[a] = phi[a]; }
+    nrs[b] = prs;
+    finish_node(pn, m64, m32, prs, u, b, pm);
   }
 }
 
@@ -559,7 +596,8 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   int rc;
   // n on the device for the count-driven primitives
   k_box_init<<<1, 32, 0, s>>>(c->box_bits);
-  k_box<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, p->z, c->box_bits);
+  k_box<<<(unsigned)p3t_grid(n, kBlock, (int64_t)c->num_sms * 2), kBlock, 0, s>>>(
+      n, p->x, p->y, p->z, c->box_bits);
   k_box_final<<<1, 1, 0, s>>>(c->box_bits, c->box);
   k_keys<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, p->z, c->box, c->keys, c->idx);
   k_set_i64<<<1, 1, 0, s>>>(&cnt[0], n);
@@ -593,9 +631,13 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   if (rc) return rc;
   k_leaf_list<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->leaf_flag,
                                               c->leaf_pos, c->pre2bfs, c->leaf_list);
-  k_moments<<<(unsigned)gn, 128, 0, s>>>(&cnt[2], c->leaf_list, c->node, c->mom64, c->mom32,
-                                         c->nrs, c->node_done, c->sx, c->sy, c->sz, c->sm,
-                                         c->srs, c->sq, c->box);
+  k_moments_leaf<<<(unsigned)p3t_grid(c->node_cap, 128, maxb), 128, 0, s>>>(
+      &cnt[2], c->leaf_list, c->node, c->mom64, c->mom32, c->nrs, c->sx, c->sy, c->sz, c->sm,
+      c->srs, c->sq, c->box);
+  // internal nodes have levels 0..20: one launch per level, deepest first
+  for (int l = P3T_BITS - 1; l >= 0; --l)
+    k_moments_level<<<(unsigned)p3t_grid(c->node_cap, 128, (int64_t)c->num_sms * 2), 128, 0,
+                      s>>>(l, &cnt[3], c->node_cap, c->node, c->mom64, c->mom32, c->nrs, c->box);
   k_group_flags<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->node, c->bfs2pre,
                                                 c->prm.group_size, c->group_flag);
   rc = p3t_scan_i32_to_i64(c->group_flag, c->group_pos, &cnt[3], c->node_cap, &cnt[15],
@@ -606,8 +648,8 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
                                                c->group_list, c->leaf_of);
   // own kernels here (the scans and sorts count themselves): box 3, keys, n,
   // gather, lcp, levels, clamp, nodes_pre, pre2bfs, nodes_bfs, parents,
-  // leaf_list, moments, group_flags, group_list
-  p3t_note_launches(17);
+  // leaf_list, moments (1 + 21 levels), group_flags, group_list
+  p3t_note_launches(16 + 1 + P3T_BITS);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 

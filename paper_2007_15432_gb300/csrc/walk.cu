@@ -1,8 +1,10 @@
 // Row a4 of the soft step: the changeover tree walk (Eq. softforce).
 //
 // One warp per target group (the highest tree node holding <= group_size
-// particles, or a leaf), one lane per target, 32 targets per walk (larger
-// groups are taken 32 targets at a time).  The walk pops up to 32 nodes at a
+// particles, or a leaf), 32 targets per walk (larger groups are taken 32
+// targets at a time).  A walk of k < 32 targets gives each target r =
+// floor(32 / k) lanes, each of which takes every r-th entry of a batch; the
+// r partial sums are added at the end, so that lanes are not left idle.  The walk pops up to 32 nodes at a
 // time from a per-warp stack, decides opening for all of them at once on the
 // integer grid, and compacts accepted nodes, opened leaves and children with
 // warp ballots / scans into shared-memory lists.  Each batch of 32 list
@@ -93,10 +95,13 @@ template <> struct Target<true> {
   float ahx, ahy, ahz, alx, aly, alz;  // float-float accumulators
   float tabs;                          // sum of term magnitudes (conditioning)
   int32_t self;
+  int rep, nrep;                       // this lane's replica of the target, replicas
   bool valid;
-  __device__ void load(const WalkArgs &a, int32_t ti, bool v) {
+  __device__ void load(const WalkArgs &a, int32_t ti, bool v, int r, int nr) {
     valid = v;
     self = ti;
+    rep = r;
+    nrep = nr;
     ahx = ahy = ahz = alx = aly = alz = 0.f;
     tabs = 0.f;
     if (v) {
@@ -110,21 +115,52 @@ template <> struct Target<true> {
   __device__ void fold(float bx, float by, float bz) {
     two_sum(ahx, alx, bx); two_sum(ahy, aly, by); two_sum(ahz, alz, bz);
   }
+  // adds the partial sums of the other replicas (lanes lane + q k) into the
+  // first; nrep and k are warp-uniform
+  __device__ void reduce(int k) {
+    const int lane = threadIdx.x & 31;
+    for (int q = 1; q < nrep; ++q) {
+      const int src = lane < k ? lane + q * k : lane;
+      const float hx = __shfl_sync(0xffffffffu, ahx, src), lx = __shfl_sync(0xffffffffu, alx, src);
+      const float hy = __shfl_sync(0xffffffffu, ahy, src), ly = __shfl_sync(0xffffffffu, aly, src);
+      const float hz = __shfl_sync(0xffffffffu, ahz, src), lz = __shfl_sync(0xffffffffu, alz, src);
+      const float tb = __shfl_sync(0xffffffffu, tabs, src);
+      if (lane < k) {
+        two_sum(ahx, alx, hx); alx += lx;
+        two_sum(ahy, aly, hy); aly += ly;
+        two_sum(ahz, alz, hz); alz += lz;
+        tabs += tb;
+      }
+    }
+  }
 };
 
 template <> struct Target<false> {
   double x, y, z, ro, rs;
   double ax, ay, az;
   int32_t self;
+  int rep, nrep;
   bool valid;
-  __device__ void load(const WalkArgs &a, int32_t ti, bool v) {
+  __device__ void load(const WalkArgs &a, int32_t ti, bool v, int r, int nr) {
     valid = v;
     self = ti;
+    rep = r;
+    nrep = nr;
     ax = ay = az = 0.0;
     if (v) {
       x = a.sx[ti]; y = a.sy[ti]; z = a.sz[ti]; ro = a.sro[ti]; rs = a.srs[ti];
     } else {
       x = y = z = 1.0e300; ro = 1.0; rs = 0.0;
+    }
+  }
+  __device__ void reduce(int k) {
+    const int lane = threadIdx.x & 31;
+    for (int q = 1; q < nrep; ++q) {
+      const int src = lane < k ? lane + q * k : lane;
+      const double x2 = __shfl_sync(0xffffffffu, ax, src);
+      const double y2 = __shfl_sync(0xffffffffu, ay, src);
+      const double z2 = __shfl_sync(0xffffffffu, az, src);
+      if (lane < k) { ax += x2; ay += y2; az += z2; }
     }
   }
 };
@@ -174,10 +210,8 @@ __device__ __forceinline__ void pp_term(const WalkArgs &a, Target<true> &t,
     }
 }
 
-template <int TPL>
-__device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<true> (&t)[TPL],
-                                        const int32_t *list, int nsrc, void *stage,
-                                        unsigned &npp) {
+__device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<true> &t, const int32_t *list,
+                                        int nsrc, void *stage, unsigned &npp) {
   StagePP32 &S = *reinterpret_cast<StagePP32 *>(stage);
   const int lane = threadIdx.x & 31;
   if (lane < nsrc) {
@@ -188,32 +222,17 @@ __device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<true> (&t)[TPL
     S.idx[lane] = j;
   }
   __syncwarp();
-  float bx[TPL], by[TPL], bz[TPL];
-#pragma unroll
-  for (int q = 0; q < TPL; ++q) {
-    bx[q] = by[q] = bz[q] = 0.f;
-    npp += t[q].valid ? (unsigned)nsrc : 0u;
-  }
+  float bx = 0.f, by = 0.f, bz = 0.f;
+  npp += (t.valid && t.rep == 0) ? (unsigned)nsrc : 0u;
 #pragma unroll 2
-  for (int s = 0; s < nsrc; ++s) {
-    const float4 A = S.A[s];
-    const float4 B = S.B[s];
-    const float rss = S.rs[s];
-    const int32_t j = S.idx[s];
-#pragma unroll
-    for (int q = 0; q < TPL; ++q) pp_term(a, t[q], A, B, rss, j, bx[q], by[q], bz[q], npp);
-  }
+  for (int s = t.rep; s < nsrc; s += t.nrep)
+    pp_term(a, t, S.A[s], S.B[s], S.rs[s], S.idx[s], bx, by, bz, npp);
   __syncwarp();
-#pragma unroll
-  for (int q = 0; q < TPL; ++q) t[q].fold(bx[q], by[q], bz[q]);
+  t.fold(bx, by, bz);
 }
 
-template <int TPL>
-__device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<false> (&tt)[TPL],
-                                        const int32_t *list, int nsrc, void *stage,
-                                        unsigned &npp) {
-  static_assert(TPL == 1, "the FP64 walk takes one target per lane");
-  Target<false> &t = tt[0];
+__device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<false> &t, const int32_t *list,
+                                        int nsrc, void *stage, unsigned &npp) {
   StagePP64 &S = *reinterpret_cast<StagePP64 *>(stage);
   const int lane = threadIdx.x & 31;
   if (lane < nsrc) {
@@ -223,8 +242,8 @@ __device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<false> (&tt)[T
     S.idx[lane] = j;
   }
   __syncwarp();
-  npp += t.valid ? (unsigned)nsrc : 0u;
-  for (int s = 0; s < nsrc; ++s) {
+  npp += (t.valid && t.rep == 0) ? (unsigned)nsrc : 0u;
+  for (int s = t.rep; s < nsrc; s += t.nrep) {
     const double dx = t.x - S.x[s], dy = t.y - S.y[s], dz = t.z - S.z[s];
     const double r2 = dx * dx + dy * dy + dz * dz;
     const double rinv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
@@ -270,8 +289,7 @@ __device__ __forceinline__ void node_term(Target<true> &t, const float4 hi, cons
     t.tabs = fmaf(hi.w, rinv2, t.tabs);
 }
 
-template <int TPL>
-__device__ __forceinline__ void eval_nodes(const WalkArgs &a, Target<true> (&t)[TPL],
+__device__ __forceinline__ void eval_nodes(const WalkArgs &a, Target<true> &t,
                                            const int32_t *list, int nnd, void *stage,
                                            unsigned &npn) {
   Mom32 *S = reinterpret_cast<Mom32 *>(stage);
@@ -282,35 +300,23 @@ __device__ __forceinline__ void eval_nodes(const WalkArgs &a, Target<true> (&t)[
     S[lane].q0 = __ldg(&m->q0); S[lane].q1 = __ldg(&m->q1);
   }
   __syncwarp();
-  float bx[TPL], by[TPL], bz[TPL];
-#pragma unroll
-  for (int q = 0; q < TPL; ++q) {
-    bx[q] = by[q] = bz[q] = 0.f;
-    npn += t[q].valid ? (unsigned)nnd : 0u;
-  }
+  float bx = 0.f, by = 0.f, bz = 0.f;
+  npn += (t.valid && t.rep == 0) ? (unsigned)nnd : 0u;
 #pragma unroll 2
-  for (int s = 0; s < nnd; ++s) {
-    const float4 hi = S[s].hi, lo = S[s].lo, q0 = S[s].q0, q1 = S[s].q1;
-#pragma unroll
-    for (int q = 0; q < TPL; ++q) node_term(t[q], hi, lo, q0, q1, bx[q], by[q], bz[q]);
-  }
+  for (int s = t.rep; s < nnd; s += t.nrep) node_term(t, S[s].hi, S[s].lo, S[s].q0, S[s].q1, bx, by, bz);
   __syncwarp();
-#pragma unroll
-  for (int q = 0; q < TPL; ++q) t[q].fold(bx[q], by[q], bz[q]);
+  t.fold(bx, by, bz);
 }
 
-template <int TPL>
-__device__ __forceinline__ void eval_nodes(const WalkArgs &a, Target<false> (&tt)[TPL],
+__device__ __forceinline__ void eval_nodes(const WalkArgs &a, Target<false> &t,
                                            const int32_t *list, int nnd, void *stage,
                                            unsigned &npn) {
-  static_assert(TPL == 1, "the FP64 walk takes one target per lane");
-  Target<false> &t = tt[0];
   Mom64 *S = reinterpret_cast<Mom64 *>(stage);
   const int lane = threadIdx.x & 31;
   if (lane < nnd) S[lane] = a.mom64[list[lane]];
   __syncwarp();
-  npn += t.valid ? (unsigned)nnd : 0u;
-  for (int s = 0; s < nnd; ++s) {
+  npn += (t.valid && t.rep == 0) ? (unsigned)nnd : 0u;
+  for (int s = t.rep; s < nnd; s += t.nrep) {
     const Mom64 &m = S[s];
     const double dx = t.x - m.cx, dy = t.y - m.cy, dz = t.z - m.cz;
     const double r2 = dx * dx + dy * dy + dz * dz;
@@ -333,7 +339,7 @@ __device__ __forceinline__ void write_result(const WalkArgs &a, Target<MIXED> &t
 
 template <>
 __device__ __forceinline__ void write_result<true>(const WalkArgs &a, Target<true> &t) {
-  if (!t.valid) return;
+  if (!t.valid || t.rep != 0) return;
   const double x = (double)t.ahx + (double)t.alx;
   const double y = (double)t.ahy + (double)t.aly;
   const double z = (double)t.ahz + (double)t.alz;
@@ -350,7 +356,7 @@ __device__ __forceinline__ void write_result<true>(const WalkArgs &a, Target<tru
 
 template <>
 __device__ __forceinline__ void write_result<false>(const WalkArgs &a, Target<false> &t) {
-  if (!t.valid) return;
+  if (!t.valid || t.rep != 0) return;
   const int32_t i = a.idx[t.self];
   a.ax[i] = a.G * t.ax; a.ay[i] = a.G * t.ay; a.az[i] = a.G * t.az;
 }
@@ -492,15 +498,15 @@ __device__ bool traverse(const WalkArgs &a, const GroupBox &gb, int32_t *stack,
   return true;
 }
 
-// up to 32 x TPL targets of a group, TPL per lane, batches staged in shared
-// memory (every staged entry is used by all the lane's targets)
-template <bool MIXED, int TPL> struct GroupEval {
+// up to 32 targets of a group (each on nrep lanes), batches staged in shared
+// memory
+template <bool MIXED> struct GroupEval {
   const WalkArgs &a;
-  Target<MIXED> (&t)[TPL];
+  Target<MIXED> &t;
   void *stage;
   unsigned &npp, &npn;
-  __device__ void nodes(const int32_t *list, int n) { eval_nodes<TPL>(a, t, list, n, stage, npn); }
-  __device__ void pp(const int32_t *list, int n) { eval_pp<TPL>(a, t, list, n, stage, npp); }
+  __device__ void nodes(const int32_t *list, int n) { eval_nodes(a, t, list, n, stage, npn); }
+  __device__ void pp(const int32_t *list, int n) { eval_pp(a, t, list, n, stage, npp); }
 };
 
 // one target, all 32 lanes, FP64 (the refinement of ill-conditioned targets)
@@ -543,7 +549,7 @@ struct RefineEval {
   }
 };
 
-template <bool MIXED, int TPL>
+template <bool MIXED>
 __global__ void __launch_bounds__(kWarps * 32) k_walk(const WalkArgs a) {
   __shared__ int32_t s_pp[kWarps][kPPCap];
   __shared__ int32_t s_nd[kWarps][kNDCap];
@@ -570,29 +576,32 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(const WalkArgs a) {
     gb.load(G);
     const int32_t gfirst = G.first, gcount = G.count;
     bool ok = true;
-    for (int32_t tb = gfirst; tb < gfirst + gcount && ok; tb += 32 * TPL) {
-      Target<MIXED> t[TPL];
-#pragma unroll
-      for (int q = 0; q < TPL; ++q) {
-        const int32_t ti = tb + q * 32 + lane;
-        t[q].load(a, ti, ti < gfirst + gcount);
-      }
-      GroupEval<MIXED, TPL> ev{a, t, s_stage[w], npp, npn};
+    for (int32_t tb = gfirst; tb < gfirst + gcount && ok; tb += 32) {
+      const int k = min(32, gfirst + gcount - tb);
+      const int nrep = 32 / k, rep = lane / k;
+      Target<MIXED> t;
+      t.load(a, tb + (lane - rep * k), rep < nrep, rep < nrep ? rep : 0, nrep);
+      GroupEval<MIXED> ev{a, t, s_stage[w], npp, npn};
       ok = traverse(a, gb, stack, s_pp[w], s_nd[w], s_big[w], s_bh, round_limit, ev);
       if (ok) {
-#pragma unroll
-        for (int q = 0; q < TPL; ++q) write_result<MIXED>(a, t[q]);
+        t.reduce(k);
+        write_result<MIXED>(a, t);
       }
     }
     if (!ok) break;
   }
   if (a.counts) {
-    unsigned long long p = npp, q = npn;
+    // a replica lane that met its target's own entry holds npp below zero:
+    // the warp sum is taken modulo 2^32, where a warp's true count fits
+    unsigned p = npp, q = npn;
     for (int o = 16; o > 0; o >>= 1) {
       p += __shfl_xor_sync(0xffffffffu, p, o);
       q += __shfl_xor_sync(0xffffffffu, q, o);
     }
-    if (lane == 0) { atomicAdd(&a.counts[0], p); atomicAdd(&a.counts[1], q); }
+    if (lane == 0) {
+      atomicAdd(&a.counts[0], (unsigned long long)p);
+      atomicAdd(&a.counts[1], (unsigned long long)q);
+    }
   }
 }
 
@@ -691,11 +700,12 @@ int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
   k_walk_prep<<<1, 1, 0, s>>>(a.cursor, a.cand_count, a.counts, a.refine_count);
   const unsigned blocks = (unsigned)(c->num_sms * p3t_walk_blocks_per_sm());
   if (c->prm.precision == P3T_MIXED) {
-    // one target per lane: two per lane (a 64-target group walked once) was
-    // measured slower than two walks of 32 (register pressure, longer chains)
-    k_walk<true, 1><<<blocks, kWarps * 32, 0, s>>>(a);
+    // one target per lane (or several lanes per target): two targets per
+    // lane (a 64-target group walked once) was measured slower than two
+    // walks of 32 (register pressure, longer chains)
+    k_walk<true><<<blocks, kWarps * 32, 0, s>>>(a);
   } else {
-    k_walk<false, 1><<<blocks, kWarps * 32, 0, s>>>(a);
+    k_walk<false><<<blocks, kWarps * 32, 0, s>>>(a);
   }
   k_walk_post<<<1, 1, 0, s>>>(c->counters, c->cand_cap, c->cap, c->status);
   if (c->prm.precision == P3T_MIXED) k_refine<<<blocks, kWarps * 32, 0, s>>>(a);

@@ -25,11 +25,17 @@ def test_morton_keys_bitwise(orc):
     lo = np.array([s["x"].min(), s["y"].min(), s["z"].min()])
     L = max(s["x"].max() - lo[0], s["y"].max() - lo[1], s["z"].max() - lo[2])
     assert np.allclose(box, [*lo, L], rtol=0, atol=0)
+    S = 2.0**21 / L
     for i in range(40):
         q = []
         for a, c in enumerate(("x", "y", "z")):
-            t = int(np.floor((s[c][i] - lo[a]) / L * 2**21))
+            t = int(np.floor((s[c][i] - lo[a]) * S))
             q.append(min(max(t, 0), 2**21 - 1))
+            # the position lies in its cell [q u, (q + 1) u) up to far less
+            # than the two-cell margin of the cut-off reach test
+            u = L / 2**21
+            off = (s[c][i] - lo[a]) / u - q[-1]
+            assert -1e-6 < off < 1 + 1e-6
         k = 0
         for b in range(20, -1, -1):          # most significant level first
             for a in range(3):
