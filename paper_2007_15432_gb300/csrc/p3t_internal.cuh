@@ -91,7 +91,7 @@ struct p3t_ctx {
   double *sro = nullptr, *srs = nullptr;
   int32_t *sq = nullptr;                   // 3 * cap quantised coordinates
   float4 *spA = nullptr, *spB = nullptr;   // {x_hi,y_hi,z_hi,m}, {x_lo,y_lo,z_lo,1/r_out}
-  float *srs32 = nullptr;                  // r_search in FP32
+  float *srs32 = nullptr;                  // r_search^2 x 1.00001 in FP32 (walk's candidate test)
 
   // tree build scratch (per particle)
   int8_t *lp = nullptr, *lv = nullptr;     // lcp with predecessor, leaf level

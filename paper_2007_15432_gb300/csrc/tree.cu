@@ -234,7 +234,7 @@ __global__ void k_gather(int64_t n, const int32_t *idx, const uint64_t *keys,
     spA[s] = make_float4(xh, yh, zh, (float)M);
     spB[s] = make_float4((float)(X - (double)xh), (float)(Y - (double)yh),
                          (float)(Z - (double)zh), 1.0f / (float)RO);  // FP32 path only
-    srs32[s] = (float)RS;
+    srs32[s] = (float)(RS * RS) * 1.00001f;  // walk's candidate test: r^2 vs r_search^2, widened
   }
 }
 

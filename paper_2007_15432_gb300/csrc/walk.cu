@@ -24,7 +24,8 @@ constexpr int kWarps = 4;                 // warps per block
 constexpr int kPPCap = 32 * 33;           // p-p list: leftover < 32 + 32 leaves x <= 32
 constexpr int kNDCap = 64;                // node list: leftover < 32 + 32 nodes
 constexpr int kBigCap = 8;                // opened leaves with more than 32 members
-constexpr float kCandMargin = 1.00001f;   // FP32 candidate test is widened by 1e-5
+// the FP32 candidate test r^2 < r_search^2 is widened by a factor 1.00001
+// (applied to the squared radii in the gather); the exact FP64 test follows
 
 struct WalkArgs {
   const TreeNode *node;
@@ -52,7 +53,7 @@ struct WalkArgs {
   const int64_t *d_nrefine;        // refine count clamped to the capacity
   const int32_t *leaf_of;          // sorted index -> its leaf (BFS id)
   double G, gamma;
-  float gamma_f, inv1mg_f;
+  float inv1mg_f, mgi_f;           // 1 / (1 - gamma), -gamma / (1 - gamma)
   float refine_cf;                 // refine when sum|term| > refine_cf * |a|
   int64_t bh[P3T_BITS + 1];
 };
@@ -91,7 +92,7 @@ __device__ __forceinline__ void two_sum(float &hi, float &lo, float b) {
 template <bool MIXED> struct Target;
 
 template <> struct Target<true> {
-  float xh, yh, zh, xl, yl, zl, inv_ro, rs;
+  float xh, yh, zh, xl, yl, zl, inv_ro, rs2;  // rs2: r_search^2 with the FP32 margin
   float ahx, ahy, ahz, alx, aly, alz;  // float-float accumulators
   float tabs;                          // sum of term magnitudes (conditioning)
   int32_t self;
@@ -107,9 +108,9 @@ template <> struct Target<true> {
     if (v) {
       const float4 A = a.spA[ti], B = a.spB[ti];
       xh = A.x; yh = A.y; zh = A.z; xl = B.x; yl = B.y; zl = B.z; inv_ro = B.w;
-      rs = a.srs32[ti];
-    } else {
-      xh = yh = zh = 3.0e30f; xl = yl = zl = 0.f; inv_ro = 0.f; rs = 0.f;
+      rs2 = a.srs32[ti];
+    } else {  // far away: no force, no candidate
+      xh = yh = zh = 3.0e30f; xl = yl = zl = 0.f; inv_ro = 0.f; rs2 = 0.f;
     }
   }
   __device__ void fold(float bx, float by, float bz) {
@@ -183,28 +184,33 @@ static_assert(sizeof(StagePP32) <= kStageBytes && sizeof(StagePP64) <= kStageByt
               "stage area");
 
 // ---- particle-particle batch ----------------------------------------------
-// one changeover pair term in FP32 on float-float relative coordinates
+// one changeover pair term in FP32 on float-float relative coordinates.  r^2
+// is kept above 1e-30 for the reciprocal square root: a coincident pair (the
+// target itself) has y = 0 < gamma, K = 0 and so adds nothing, and f is
+// formed as ((m K) r^-1) r^-2 so that no factor overflows.  The candidate test
+// compares r^2 with max(r_search^2) (squared and widened in the gather);
+// far-away dummy targets never pass it.
 __device__ __forceinline__ void pp_term(const WalkArgs &a, Target<true> &t,
-                                        const float4 A, const float4 B, float rss,
-                                        int32_t j, float &bx, float &by, float &bz,
+                                        const float4 A, const float4 B, float rs2s,
+                                        const int32_t *idx, float &bx, float &by, float &bz,
                                         unsigned &npp) {
     const float dx = (t.xh - A.x) + (t.xl - B.x);
     const float dy = (t.yh - A.y) + (t.yl - B.y);
     const float dz = (t.zh - A.z) + (t.zl - B.z);
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
     const float r = r2 * rinv;
     const float y = r * fminf(t.inv_ro, B.w);
-    const float x = __saturatef((y - a.gamma_f) * a.inv1mg_f);
+    const float x = __saturatef(fmaf(y, a.inv1mg_f, a.mgi_f));
     const float x2 = x * x;
     const float K = (x2 * x2) * fmaf(fmaf(fmaf(-20.f, x, 70.f), x, -84.f), x, 35.f);
-    const float f = A.w * K * (rinv * rinv * rinv);
+    const float f = ((A.w * K) * rinv) * (rinv * rinv);
     bx = fmaf(-f, dx, bx);
     by = fmaf(-f, dy, by);
     bz = fmaf(-f, dz, bz);
     t.tabs = fmaf(f, r, t.tabs);
-    const float rsj = fmaxf(t.rs, rss);
-    if (r2 < rsj * rsj * kCandMargin && t.valid) {
+    if (r2 < fmaxf(t.rs2, rs2s)) {
+      const int32_t j = *idx;
       if (j != t.self) record_candidate(a, t.self, j);
       else --npp;  // the target itself is not a pair
     }
@@ -226,7 +232,7 @@ __device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<true> &t, cons
   npp += (t.valid && t.rep == 0) ? (unsigned)nsrc : 0u;
 #pragma unroll 2
   for (int s = t.rep; s < nsrc; s += t.nrep)
-    pp_term(a, t, S.A[s], S.B[s], S.rs[s], S.idx[s], bx, by, bz, npp);
+    pp_term(a, t, S.A[s], S.B[s], S.rs[s], &S.idx[s], bx, by, bz, npp);
   __syncwarp();
   t.fold(bx, by, bz);
 }
@@ -274,7 +280,7 @@ __device__ __forceinline__ void node_term(Target<true> &t, const float4 hi, cons
     const float dy = (t.yh - hi.y) + (t.yl - lo.y);
     const float dz = (t.zh - hi.z) + (t.zl - lo.z);
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
     const float rinv2 = rinv * rinv;
     const float rinv3 = rinv2 * rinv;
     const float rinv5 = rinv3 * rinv2;
@@ -661,7 +667,8 @@ __global__ void k_walk_post(int64_t *cnt, int64_t cand_cap, int64_t refine_cap,
 
 }  // namespace
 
-int p3t_walk_blocks_per_sm() { return 6; }
+// 7 blocks of 4 warps: 72 registers and 30.5 KB of shared memory a block fit 7
+int p3t_walk_blocks_per_sm() { return 7; }
 
 int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
                        double *ay, double *az, uint64_t *counts,
@@ -687,8 +694,8 @@ int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
   a.refine_cf = 32.0f;
   a.G = c->prm.G;
   a.gamma = c->prm.gamma;
-  a.gamma_f = (float)c->prm.gamma;
   a.inv1mg_f = (float)(1.0 / (1.0 - c->prm.gamma));
+  a.mgi_f = (float)(-c->prm.gamma / (1.0 - c->prm.gamma));
   // Barnes-Hut thresholds per level, ceil((2^(22-l))^2 / theta^2) (half units)
   const double big = 4611686018427387904.0;
   const double th2 = c->prm.theta * c->prm.theta;
