@@ -173,6 +173,7 @@ int p3t_create(p3t_ctx **ctx, const p3t_params *p, int device) {
     delete c;
     return P3T_ERR_CUDA;
   }
+  c->coop_blocks = p3t_moments_coop_blocks(c->num_sms);
   bool ok = dalloc(c->status, 1) && dalloc(c->box, 5) && dalloc(c->box_bits, 6) &&
             dalloc(c->counters, 24) && dalloc(c->cl_counts, 4) && dalloc(c->hsteps, 1) && dalloc(c->hcursor, 3) &&
             dalloc(c->coll_ctr, 1) &&

@@ -342,42 +342,36 @@ __device__ __forceinline__ int first_level(const V &S, int k, const p3t_params &
 
 // term of source j (j == nc: the star) on member k at the block-time state
 // (p, pv): the (1 - K) pair force and its jerk (Eq. hardforce), one
-// reciprocal square root per pair, 1/max(r_out) taken as min(1/r_out).
-// Members of k's own composite are left out; with `detect`, hit reports
-// contact r < f (R_k + R_j).
+// reciprocal square root per pair, 1/max(r_out) taken as min(1/r_out).  The
+// star is a source at the origin, at rest, of mass M_*, with 1/r_out = 0 (so
+// y = 0: no changeover): the same instructions then give exactly the star
+// term -G M_* x / |x|^3 and its jerk, with no divergent path.  Members of k's
+// own composite are left out; with `detect`, hit reports contact r < f (R_k +
+// R_j) with another member.
 template <class V>
 __device__ __forceinline__ void hard_term(const V &S, int nc, int k, int j,
                                           const p3t_params &prm, double i1mg, bool detect,
                                           double out[6], bool &hit) {
   for (int q = 0; q < 6; ++q) out[q] = 0.0;
   hit = false;
+  const bool star = j == nc;
+  if (!star && (j == k || S.set(j) == S.set(k))) return;
+  const int js = star ? k : j;  // an index that can be read
   const double xk = S.p(0, k), yk = S.p(1, k), zk = S.p(2, k);
   const double vxk = S.pv(0, k), vyk = S.pv(1, k), vzk = S.pv(2, k);
-  if (j == nc) {
-    const double r2 = xk * xk + yk * yk + zk * zk;
-    const double rinv = 1.0 / sqrt(r2);
-    const double rinv2 = rinv * rinv;
-    const double f = prm.G * prm.m_star * (rinv2 * rinv);
-    const double rv = xk * vxk + yk * vyk + zk * vzk;
-    out[0] = f * xk; out[1] = f * yk; out[2] = f * zk;
-    const double c = 3.0 * rv * rinv2;
-    out[3] = f * (vxk - c * xk);
-    out[4] = f * (vyk - c * yk);
-    out[5] = f * (vzk - c * zk);
-    return;
-  }
-  if (j == k || S.set(j) == S.set(k)) return;
-  const double rx = xk - S.p(0, j), ry = yk - S.p(1, j), rz = zk - S.p(2, j);
-  const double ux = vxk - S.pv(0, j), uy = vyk - S.pv(1, j), uz = vzk - S.pv(2, j);
+  const double rx = xk - (star ? 0.0 : S.p(0, js)), ry = yk - (star ? 0.0 : S.p(1, js)),
+               rz = zk - (star ? 0.0 : S.p(2, js));
+  const double ux = vxk - (star ? 0.0 : S.pv(0, js)), uy = vyk - (star ? 0.0 : S.pv(1, js)),
+               uz = vzk - (star ? 0.0 : S.pv(2, js));
   const double r2 = rx * rx + ry * ry + rz * rz;
-  if (detect) {
-    const double sr = prm.f_radius * (S.rp(k) + S.rp(j));
+  if (detect && !star) {
+    const double sr = prm.f_radius * (S.rp(k) + S.rp(js));
     hit = r2 < sr * sr;
   }
   if (r2 == 0.0) return;
   const double rinv = 1.0 / sqrt(r2);
   const double r = r2 * rinv;
-  const double irot = S.iro(k) < S.iro(j) ? S.iro(k) : S.iro(j);
+  const double irot = star ? 0.0 : (S.iro(k) < S.iro(js) ? S.iro(k) : S.iro(js));
   const double yv = r * irot;
   if (yv >= 1.0) return;
   double w = 1.0, dK = 0.0;
@@ -388,7 +382,7 @@ __device__ __forceinline__ void hard_term(const V &S, int nc, int k, int j,
     dK = 140.0 * x3 * (u * u * u) * i1mg;
   }
   const double rinv2 = rinv * rinv;
-  const double g3 = prm.G * S.m(j) * (rinv2 * rinv);
+  const double g3 = prm.G * (star ? prm.m_star : S.m(js)) * (rinv2 * rinv);
   const double f = g3 * w;
   const double rv = rx * ux + ry * uy + rz * uz;
   out[0] = f * rx; out[1] = f * ry; out[2] = f * rz;
@@ -625,6 +619,7 @@ __device__ void integrate_cluster(const V &S, HCtl &C, double (*Tb)[6], int64_t 
   const int item = (tid & 31) * (NT / 32) + (tid >> 5);  // consecutive items -> different warps
   const int64_t T = ((int64_t)1) << P3T_KMAX;
   const double unit = ldexp(dt, -P3T_KMAX);
+  const double idt = 1.0 / dt;
   const double i1mg = 1.0 / (1.0 - prm.gamma);
   for (int k = item; k < nc; k += NT) {
     const int32_t i = cl_mem[off + k];
@@ -702,7 +697,9 @@ __device__ void integrate_cluster(const V &S, HCtl &C, double (*Tb)[6], int64_t 
       const int k = S.act(b);
       const double D = (double)(T >> S.lvl(k)) * unit;
       const double D2 = D * D, D3 = D2 * D, D4 = D3 * D, D5 = D4 * D;
-      const double iD = 1.0 / D, iD2 = iD * iD, iD3 = iD2 * iD;
+      // 1 / D = 2^lvl (1 / dt) exactly (D = dt 2^-lvl): a product, not a division
+      const double iD = idt * __longlong_as_double((long long)(1023 + S.lvl(k)) << 52);
+      const double iD2 = iD * iD, iD3 = iD2 * iD;
       const double da = S.a(q, k) - S.a1(q, k);
       const double j0 = S.j(q, k), j1 = S.j1(q, k);
       const double A2 = (-6.0 * da - D * (4.0 * j0 + 2.0 * j1)) * iD2;

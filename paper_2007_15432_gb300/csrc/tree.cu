@@ -3,7 +3,11 @@
 // and the integer grid geometry must be bit-identical on every IEEE machine.
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include "p3t_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -493,50 +497,58 @@ __device__ __forceinline__ int64_t level_begin(const TreeNode *node, int64_t nn,
   return lo;
 }
 
-__global__ void k_moments_level(int level, const int64_t *d_nnode, int64_t node_cap,
-                                TreeNode *node, Mom64 *m64, Mom32 *m32, double *nrs,
-                                const double *box) {
+// The internal nodes, deepest level first, in one cooperative launch: the
+// blocks take a level's nodes and wait at a grid barrier before the next
+// non-empty level (levels ascend in breadth-first order; internal nodes have
+// levels 0..20).
+__global__ void k_moments_levels(const int64_t *d_nnode, int64_t node_cap, TreeNode *node,
+                                 Mom64 *m64, Mom32 *m32, double *nrs, const double *box) {
+  cg::grid_group grid = cg::this_grid();
   __shared__ int64_t range[2];
   const int64_t nn = min(*d_nnode, node_cap);
-  if (threadIdx.x < 2) range[threadIdx.x] = level_begin(node, nn, level + (int)threadIdx.x);
-  __syncthreads();
-  const int64_t b0 = range[0], b1 = range[1];
-  if (b0 >= b1) return;
   const double u = ldexp(box[3], -P3T_BITS);
-  for (int64_t b = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < b1;
-       b += (int64_t)gridDim.x * blockDim.x) {
-    TreeNode *pn = &node[b];
-    const int32_t c0 = pn->child0, nch = pn->nchild;
-    if (nch == 0) continue;  // a leaf: done already
-    double PM = 0.0, P[3] = {0, 0, 0}, prs = 0.0;
-    int32_t plo[3] = {P3T_QMAX, P3T_QMAX, P3T_QMAX}, phi[3] = {-1, -1, -1};
-    for (int k = 0; k < nch; ++k) {
-      const Mom64 &cm = m64[c0 + k];
-      PM += cm.M;
-      P[0] = __fma_rn(cm.M, cm.cx, P[0]);
-      P[1] = __fma_rn(cm.M, cm.cy, P[1]);
-      P[2] = __fma_rn(cm.M, cm.cz, P[2]);
-      prs = fmax(prs, nrs[c0 + k]);
-      const TreeNode &cn = node[c0 + k];
-      for (int a = 0; a < 3; ++a) { plo[a] = min(plo[a], cn.qlo[a]); phi[a] = max(phi[a], cn.qhi[a]); }
+  for (int level = P3T_BITS - 1; level >= 0; --level) {
+    __syncthreads();
+    if (threadIdx.x < 2) range[threadIdx.x] = level_begin(node, nn, level + (int)threadIdx.x);
+    __syncthreads();
+    const int64_t b0 = range[0], b1 = range[1];
+    if (b0 >= b1) continue;  // the same for every block: no barrier needed
+    for (int64_t b = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < b1;
+         b += (int64_t)gridDim.x * blockDim.x) {
+      TreeNode *pn = &node[b];
+      const int32_t c0 = pn->child0, nch = pn->nchild;
+      if (nch == 0) continue;  // a leaf: done already
+      double PM = 0.0, P[3] = {0, 0, 0}, prs = 0.0;
+      int32_t plo[3] = {P3T_QMAX, P3T_QMAX, P3T_QMAX}, phi[3] = {-1, -1, -1};
+      for (int k = 0; k < nch; ++k) {
+        const Mom64 &cm = m64[c0 + k];
+        PM += cm.M;
+        P[0] = __fma_rn(cm.M, cm.cx, P[0]);
+        P[1] = __fma_rn(cm.M, cm.cy, P[1]);
+        P[2] = __fma_rn(cm.M, cm.cz, P[2]);
+        prs = fmax(prs, nrs[c0 + k]);
+        const TreeNode &cn = node[c0 + k];
+        for (int a = 0; a < 3; ++a) { plo[a] = min(plo[a], cn.qlo[a]); phi[a] = max(phi[a], cn.qhi[a]); }
+      }
+      Mom64 pm = {};
+      const double iM = 1.0 / PM;
+      pm.M = PM; pm.cx = P[0] * iM; pm.cy = P[1] * iM; pm.cz = P[2] * iM;
+      for (int k = 0; k < nch; ++k) {
+        const Mom64 &cm = m64[c0 + k];
+        const double dx = cm.cx - pm.cx, dy = cm.cy - pm.cy, dz = cm.cz - pm.cz;
+        const double d2 = dx * dx + dy * dy + dz * dz;
+        pm.qxx += cm.qxx + cm.M * (3.0 * dx * dx - d2);
+        pm.qyy += cm.qyy + cm.M * (3.0 * dy * dy - d2);
+        pm.qzz += cm.qzz + cm.M * (3.0 * dz * dz - d2);
+        pm.qxy += cm.qxy + cm.M * (3.0 * dx * dy);
+        pm.qxz += cm.qxz + cm.M * (3.0 * dx * dz);
+        pm.qyz += cm.qyz + cm.M * (3.0 * dy * dz);
+      }
+      for (int a = 0; a < 3; ++a) { pn->qlo[a] = plo[a]; pn->qhi[a] = phi[a]; }
+      nrs[b] = prs;
+      finish_node(pn, m64, m32, prs, u, b, pm);
     }
-    Mom64 pm = {};
-    const double iM = 1.0 / PM;
-    pm.M = PM; pm.cx = P[0] * iM; pm.cy = P[1] * iM; pm.cz = P[2] * iM;
-    for (int k = 0; k < nch; ++k) {
-      const Mom64 &cm = m64[c0 + k];
-      const double dx = cm.cx - pm.cx, dy = cm.cy - pm.cy, dz = cm.cz - pm.cz;
-      const double d2 = dx * dx + dy * dy + dz * dz;
-      pm.qxx += cm.qxx + cm.M * (3.0 * dx * dx - d2);
-      pm.qyy += cm.qyy + cm.M * (3.0 * dy * dy - d2);
-      pm.qzz += cm.qzz + cm.M * (3.0 * dz * dz - d2);
-      pm.qxy += cm.qxy + cm.M * (3.0 * dx * dy);
-      pm.qxz += cm.qxz + cm.M * (3.0 * dx * dz);
-      pm.qyz += cm.qyz + cm.M * (3.0 * dy * dz);
-    }
-    for (int a = 0; a < 3; ++a) { pn->qlo[a] = plo[a]; pn->qhi[a] = phi[a]; }
-    nrs[b] = prs;
-    finish_node(pn, m64, m32, prs, u, b, pm);
+    grid.sync();
   }
 }
 
@@ -634,10 +646,20 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   k_moments_leaf<<<(unsigned)p3t_grid(c->node_cap, 128, maxb), 128, 0, s>>>(
       &cnt[2], c->leaf_list, c->node, c->mom64, c->mom32, c->nrs, c->sx, c->sy, c->sz, c->sm,
       c->srs, c->sq, c->box);
-  // internal nodes have levels 0..20: one launch per level, deepest first
-  for (int l = P3T_BITS - 1; l >= 0; --l)
-    k_moments_level<<<(unsigned)p3t_grid(c->node_cap, 128, (int64_t)c->num_sms * 2), 128, 0,
-                      s>>>(l, &cnt[3], c->node_cap, c->node, c->mom64, c->mom32, c->nrs, c->box);
+  {
+    // internal nodes, level by level in one cooperative launch (every block
+    // resident: a few blocks per SM of a small kernel)
+    const int64_t *a0 = &cnt[3];
+    int64_t a1 = c->node_cap;
+    TreeNode *a2 = c->node;
+    Mom64 *a3 = c->mom64;
+    Mom32 *a4 = c->mom32;
+    double *a5 = c->nrs;
+    const double *a6 = c->box;
+    void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6};
+    P3T_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_moments_levels,
+                                             dim3((unsigned)c->coop_blocks), dim3(128), args, 0, s));
+  }
   k_group_flags<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->node, c->bfs2pre,
                                                 c->prm.group_size, c->group_flag);
   rc = p3t_scan_i32_to_i64(c->group_flag, c->group_pos, &cnt[3], c->node_cap, &cnt[15],
@@ -648,9 +670,21 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
                                                c->group_list, c->leaf_of);
   // own kernels here (the scans and sorts count themselves): box 3, keys, n,
   // gather, lcp, levels, clamp, nodes_pre, pre2bfs, nodes_bfs, parents,
-  // leaf_list, moments (1 + 21 levels), group_flags, group_list
-  p3t_note_launches(16 + 1 + P3T_BITS);
+  // leaf_list, moments (leaves, levels), group_flags, group_list
+  p3t_note_launches(18);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
+}
+
+// blocks of k_moments_levels that are resident at once (cooperative launch)
+int p3t_moments_coop_blocks(int num_sms) {
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_moments_levels, 128, 0) != cudaSuccess) {
+    cudaGetLastError();
+    per = 1;
+  }
+  if (per > 4) per = 4;
+  if (per < 1) per = 1;
+  return per * num_sms;
 }
 
 // tree statistics on demand (diagnostics; not part of the step)
