@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-targets", type=int, default=16384,
                     help="targets of the CPU oracle's timed walk sample")
+    ap.add_argument("--cutoff-sweep", action="store_true",
+                    help="compare the cut-off schemes (shared / individual / individual with "
+                         "random velocity) over R~cut,0 on the mass-spectrum ring; one JSON "
+                         "line per configuration")
     return ap.parse_args()
 
 
@@ -413,8 +417,100 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------- cut-off schemes -----
+def run_cutoff_sweep(args):
+    """Shared vs individual vs individual + random-velocity cut-off (Sec.
+    2.1.1-2.1.3, Eqs. rout1, routi, routi2): mean neighbour count, largest
+    neighbour cluster and soft-step time (with its phases and interaction
+    count) against R~cut,0, on seeded stand-ins for the paper's mass-spectrum
+    snapshot (N = 377,740 on 0.9-1.1 au, power-law masses on [1e-12,
+    4.25e-9]): "cold" (e/i rms 2h/h per particle) and "warm" (e/i rms
+    1e-3 / 5e-4, where the random-velocity term sets most radii).  Perfect
+    accretion as in the paper's runs (f = 1, 2 g/cm^3).  Steps are timed only
+    while the largest cluster has at most 600 members: a cluster's block step
+    costs its size squared on one block."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    from paper_2007_15432_gb300 import build, disks
+    build.build()
+    from paper_2007_15432_gb300 import p3t as P
+    n = 377_740
+    rings = {"cold": disks.mass_spectrum_ring(n), "warm": disks.mass_spectrum_ring(n, e_rms=1e-3,
+                                                                                 i_rms=5e-4)}
+    names = {P.P3T_CUT_SHARED: "shared", P.P3T_CUT_HILL: "individual",
+             P.P3T_CUT_HILL_VRAN: "individual+random-velocity"}
+    for ring, s0 in rings.items():
+        for mode in (P.P3T_CUT_SHARED, P.P3T_CUT_HILL, P.P3T_CUT_HILL_VRAN):
+            for rc in (0.5, 1.0, 2.0, 3.0):
+                prm = P.Params(theta=0.5, precision=P.P3T_MIXED, eta=0.01, eta0=0.001,
+                               group_size=64, rcut0=rc, cutoff_mode=mode, f_radius=1.0)
+                st = P.State.from_numpy(s0, device=dev, r_phys=disks.physical_radius(s0["m"]))
+                ss = P.SoftStep(prm, st, device=0, nb_cap=64 * n)
+                ok = False
+                for _ in range(3):   # grow the candidate buffer when it overflowed
+                    ss.init(update_cutoffs=True)
+                    code, _ = P.p3t_status(ss.ctx)
+                    if code == 0:
+                        ok = True
+                        break
+                line = dict(study="cutoff schemes", ring=ring, scheme=names[mode], rcut0=rc, n=n)
+                if not ok:
+                    line["error"] = P.p3t_strerror(code)
+                    print(json.dumps(line), flush=True)
+                    ss.close()
+                    continue
+                cl = P.clusters_to_host(ss.ctx, ss.cl, n)
+                line.update(mean_neighbours=int(ss.nb_off[n].item()) / n,
+                            largest_cluster=int(cl["max_size"]), clusters=int(len(cl["cl_off"]) - 1),
+                            mean_r_out=float(st.r_out.mean().item()))
+                if cl["max_size"] <= 600:
+                    K, h = 4, 0.5 * prm.dt_soft
+                    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+                    ph = np.zeros(5)
+                    merged = 0
+                    counts = torch.zeros(2, dtype=torch.int64, device=dev)
+                    inter = 0
+                    for k in range(K + 2):
+                        timed = k >= 2
+                        ev[0].record(stream)
+                        P.p3t_kick(ss.ctx, st, ss.acc, h, stream)
+                        P.p3t_hard_step(ss.ctx, st, ss.cl, prm.dt_soft, ss.hsteps, stream)
+                        ev[1].record(stream)
+                        P.p3t_build_tree(ss.ctx, st, False, stream)
+                        ev[2].record(stream)
+                        P.p3t_soft_force(ss.ctx, st, ss.acc, counts, stream)
+                        ev[3].record(stream)
+                        ss.cl = P.p3t_neighbours(ss.ctx, st, ss.nb_off, ss.nb_idx, stream)
+                        P.p3t_kick(ss.ctx, st, ss.acc, h, stream)
+                        ev[4].record(stream)
+                        if timed:
+                            inter += int(counts.sum().item())
+                        nm = ss.merge(stream)      # procedure step 9 (synchronises)
+                        ev[5].record(stream)
+                        torch.cuda.synchronize(dev)
+                        if timed:
+                            ph += [ev[q].elapsed_time(ev[q + 1]) for q in range(5)]
+                            merged += nm
+                    ss.status()
+                    ph /= K
+                    line.update(ms_per_step=float(ph.sum()), interactions_per_step=inter / K,
+                                merged=merged,
+                                phases_ms=dict(kick_and_hard=ph[0], tree=ph[1], soft_force=ph[2],
+                                               neighbours_and_kick=ph[3], merge_and_recompute=ph[4]))
+                else:
+                    line["ms_per_step"] = None
+                    line["note"] = "steps not timed: largest cluster above 600 members"
+                print(json.dumps(line), flush=True)
+                ss.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.cutoff_sweep:
+        return run_cutoff_sweep(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

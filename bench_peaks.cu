@@ -1,5 +1,7 @@
 // Device peak probe for the roofline denominators: FP32 FFMA, FP64 DFMA, FP64
-// DADD and FP32 rsqrt throughput from independent dependency chains.
+// DADD and FP32 rsqrt throughput from independent dependency chains, and the
+// latency of one dependent FMA chain in a single block (1 or 4 warps, 1, 8 or
+// 32 active lanes a warp).
 // Each thread runs 8 independent chains; one store per thread at the end (in bounds: out has grid*block elems).
 #include <cstdio>
 #include <cuda_runtime.h>
@@ -32,6 +34,14 @@ __global__ void rsqrt_chain(float* out, int iters) {
   }
   out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3;
 }
+// one dependent FMA per iteration; lanes >= active return at once (out has
+// >= blockDim.x elements)
+template <typename T> __global__ void latency_chain(T* out, int iters, int active, T a, T b) {
+  if ((int)(threadIdx.x & 31) >= active) return;
+  T x = (T)threadIdx.x;
+  for (int i = 0; i < iters; ++i) x = x * a + b;
+  out[threadIdx.x] = x;
+}
 int main() {
   int dev = 0; cudaDeviceProp p; cudaGetDeviceProperties(&p, dev);
   printf("device %s SMs %d clock? cc %d.%d\n", p.name, p.multiProcessorCount, p.major, p.minor);
@@ -48,6 +58,17 @@ int main() {
     int itr = 1024; cudaEventRecord(e0); rsqrt_chain<<<blocks, threads>>>(of, itr); cudaEventRecord(e1); cudaEventSynchronize(e1); cudaEventElapsedTime(&ms, e0, e1);
     fl = 4.0 * 16 * (double)itr * n; printf("FP32 rsqrt(+add): %.3f Gop/s (%.3f ms)\n", fl / ms / 1e6, ms);
   }
+  const int itl = 200000;
+  for (int warps = 1; warps <= 4; warps *= 4)
+    for (int act : {1, 8, 32}) {
+      float m64 = 0.f, m32 = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0); latency_chain<double><<<1, 32 * warps>>>(od, itl, act, 0.999999, 1e-9); cudaEventRecord(e1); cudaEventSynchronize(e1); cudaEventElapsedTime(&m64, e0, e1);
+        cudaEventRecord(e0); latency_chain<float><<<1, 32 * warps>>>(of, itl, act, 0.999f, 1e-3f); cudaEventRecord(e1); cudaEventSynchronize(e1); cudaEventElapsedTime(&m32, e0, e1);
+      }
+      printf("dependent FMA, %d warp(s), %2d active lanes: FP64 %.2f ns, FP32 %.2f ns\n", warps, act,
+             m64 * 1e6 / itl, m32 * 1e6 / itl);
+    }
   cudaError_t err = cudaDeviceSynchronize(); printf("status %s\n", cudaGetErrorString(err));
   return err == cudaSuccess ? 0 : 1;
 }

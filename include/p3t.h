@@ -57,6 +57,11 @@ extern "C" {
                         FP32 pair terms folded into float-float accumulators;
                         FP64 state, tree, neighbour search, Hermite, Kepler   */
 
+/* cut-off radius schemes (Sec. 2.1.1-2.1.3), p3t_params.cutoff_mode */
+#define P3T_CUT_HILL_VRAN 0  /* Hill radius and random velocity (Eq. routi2)   */
+#define P3T_CUT_HILL 1       /* Hill radius only (Eq. routi)                   */
+#define P3T_CUT_SHARED 2     /* one shared radius (Eq. rout1)                  */
+
 /* ---- method parameters (defaults: the paper's values, Sec. 3.1) --------- */
 typedef struct {
   double G;        /* gravitational constant                                  */
@@ -81,6 +86,12 @@ typedef struct {
   int32_t group_size;/* target groups of the walk: the highest tree nodes holding
                         <= group_size particles (0: every leaf is a group);
                         0..64                                                 */
+  int32_t cutoff_mode;/* P3T_CUT_HILL_VRAN (default): r_out,i = max(R~cut,0
+                        r_Hill,i, R~cut,1 v_ran,i dt) (Eq. routi2);
+                        P3T_CUT_HILL: R~cut,0 r_Hill,i (Eq. routi);
+                        P3T_CUT_SHARED: every particle gets the largest
+                        Eq. routi radius and the largest search radius
+                        (Eq. rout1, the "shared cut-off")                     */
 } p3t_params;
 
 /* ---- particles ---------------------------------------------------------- */
@@ -158,7 +169,9 @@ int p3t_cutoffs(p3t_ctx *ctx, p3t_particles *p, void *stream);
  *    capture.
  *  - Every call shares the scratch: calls that overlap on the GPU (e.g. on
  *    two streams with no ordering between them) race and must be avoided.
- *  - Returns 0, P3T_ERR_INVALID (bad arguments or too many bins) or
+ *  - cutoff_mode P3T_CUT_HILL_VRAN or P3T_CUT_HILL only; the shared radius
+ *    (a maximum over all particles) returns P3T_ERR_INVALID.
+ *  - Returns 0, P3T_ERR_INVALID (bad arguments, too many bins, shared mode) or
  *    P3T_ERR_CUDA (the lookup or a launch failed). */
 int p3t_cutoffs_noalloc(const p3t_params *prm, p3t_particles *p, void *stream);
 

@@ -41,7 +41,7 @@ class OrParams(C.Structure):
         "G", "m_star", "dt_soft", "gamma", "rcut0", "rcut1", "rs0", "rs1", "rs2",
         "rs3", "theta", "eta", "eta0", "f_radius")] + [
         ("leaf_size", C.c_int32), ("precision", C.c_int32), ("vran_bins", C.c_int32),
-        ("group_size", C.c_int32)]
+        ("group_size", C.c_int32), ("cutoff_mode", C.c_int32)]
 
 
 @dataclass
@@ -67,6 +67,7 @@ class Params:
     precision: int = 0
     vran_bins: int = 0
     group_size: int = 0
+    cutoff_mode: int = 0      # 0: Hill + v_ran (Eq. routi2), 1: Hill (routi), 2: shared (rout1)
 
     def c(self) -> OrParams:
         return OrParams(*[getattr(self, f[0]) for f in OrParams._fields_])

@@ -114,9 +114,18 @@ int or_cutoffs(int64_t n, const double *x, const double *y, const double *z,
     double rhill = cbrt(m[i] / (3.0 * p->m_star)) * a;
     double vr = sqrt(sum[b[i]] / (double)cnt[b[i]]);
     if (v_ran) v_ran[i] = vr;
-    double ro = dmax(p->rcut0 * rhill, p->rcut1 * vr * p->dt_soft);
+    /* Eq. routi2 (mode 0) or Eq. routi (modes 1, 2); Eq. rsearch */
+    double ro = p->cutoff_mode == 0 ? dmax(p->rcut0 * rhill, p->rcut1 * vr * p->dt_soft)
+                                    : p->rcut0 * rhill;
     r_out[i] = ro;
     r_search[i] = p->rs0 * ro + p->rs1 * vr * p->dt_soft;
+  }
+  if (p->cutoff_mode == 2) {
+    /* shared cut-off (Eq. rout1): every particle gets the largest r_out, and
+     * the largest search radius (Sec. 2.3) */
+    double mo = 0.0, ms = 0.0;
+    for (int64_t i = 0; i < n; ++i) { mo = dmax(mo, r_out[i]); ms = dmax(ms, r_search[i]); }
+    for (int64_t i = 0; i < n; ++i) { r_out[i] = mo; r_search[i] = ms; }
   }
   if (!bin) free(b);
   free(R); free(u2); free(sum); free(cnt);

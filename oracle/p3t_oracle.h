@@ -36,6 +36,9 @@ typedef struct {
   int32_t vran_bins;    /* radial bins for v_ran; 0 = clamp(N/1000, 1, 1024)     */
   int32_t group_size;   /* target groups: highest nodes holding <= group_size
                            particles (0: every leaf is a group)               */
+  int32_t cutoff_mode;  /* 0: Hill + random velocity, individual (Eq. routi2) */
+                        /* 1: Hill only, individual (Eq. routi)               */
+                        /* 2: shared, max over particles of Eq. routi (rout1) */
 } or_params;
 
 /* ---- changeover functions (Sec. 2.1.1, Eq. cutfuncW and the K definition) -- */

@@ -41,6 +41,7 @@ bool params_ok(const p3t_params *p) {
   if (p->vran_bins < 0 || p->vran_bins > 4096) return false;
   if (p->group_size < 0 || p->group_size > 64) return false;
   if (!(p->f_radius >= 0.0)) return false;
+  if (p->cutoff_mode < P3T_CUT_HILL_VRAN || p->cutoff_mode > P3T_CUT_SHARED) return false;
   return true;
 }
 

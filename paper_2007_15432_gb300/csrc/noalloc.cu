@@ -163,7 +163,9 @@ __global__ void nz_final(int64_t n, const double *x, const double *y,
     const double rhill = cbrt(m[i] / (3.0 * prm.m_star)) * a;
     const int k = nz_bin(R, Rmin, Rmax, lmin, lmax, nb);
     const double vr = sqrt(gsum[k] / (double)sc[2 + kMaxBins + k]);
-    const double ro = fmax(prm.rcut0 * rhill, prm.rcut1 * vr * prm.dt_soft);
+    const double ro = prm.cutoff_mode == P3T_CUT_HILL_VRAN
+                          ? fmax(prm.rcut0 * rhill, prm.rcut1 * vr * prm.dt_soft)
+                          : prm.rcut0 * rhill;
     r_out[i] = ro;
     r_search[i] = prm.rs0 * ro + prm.rs1 * vr * prm.dt_soft;
   }
@@ -176,6 +178,9 @@ extern "C" int p3t_cutoffs_noalloc(const p3t_params *prm, p3t_particles *p,
   if (!prm || !p || p->n < 0 || p->n >= ((int64_t)1 << 31)) return P3T_ERR_INVALID;
   if (!(prm->G > 0.0) || !(prm->m_star > 0.0) || !(prm->dt_soft > 0.0)) return P3T_ERR_INVALID;
   if (prm->vran_bins < 0 || prm->vran_bins > kMaxBins) return P3T_ERR_INVALID;
+  // the shared radius needs a maximum over all particles: not offered here
+  if (prm->cutoff_mode != P3T_CUT_HILL_VRAN && prm->cutoff_mode != P3T_CUT_HILL)
+    return P3T_ERR_INVALID;
   if (p->n == 0) return P3T_OK;
   if (!p->x || !p->y || !p->z || !p->vx || !p->vy || !p->vz || !p->m || !p->r_out ||
       !p->r_search)

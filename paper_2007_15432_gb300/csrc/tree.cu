@@ -31,7 +31,7 @@ __device__ __forceinline__ double ord_double(unsigned long long b) {
 __global__ void k_cut_init(unsigned long long *bits, double *bsum,
                            unsigned long long *bcnt, int nb) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t == 0) { bits[0] = ~0ull; bits[1] = 0ull; }
+  if (t == 0) { bits[0] = ~0ull; bits[1] = 0ull; bits[2] = 0ull; bits[3] = 0ull; }
   for (int k = t; k < nb; k += gridDim.x * blockDim.x) { bsum[k] = 0.0; bcnt[k] = 0ull; }
 }
 
@@ -100,7 +100,7 @@ __global__ void k_cut_bins(int64_t n, const double *x, const double *y,
 __global__ void k_cut_final(int64_t n, const double *x, const double *y,
                             const double *z, const double *vx, const double *vy,
                             const double *vz, const double *m, p3t_params prm,
-                            const unsigned long long *bits, int nb,
+                            unsigned long long *bits, int nb,
                             const double *bsum, const unsigned long long *bcnt,
                             double *r_out, double *r_search) {
   const double mu = prm.G * prm.m_star;
@@ -116,9 +116,31 @@ __global__ void k_cut_final(int64_t n, const double *x, const double *y,
     double rhill = cbrt(m[i] / (3.0 * prm.m_star)) * a;
     int k = cut_bin(R, Rmin, Rmax, lmin, lmax, nb);
     double vr = sqrt(bsum[k] / (double)bcnt[k]);
-    double ro = fmax(prm.rcut0 * rhill, prm.rcut1 * vr * prm.dt_soft);
+    // Eq. routi2 (P3T_CUT_HILL_VRAN) or Eq. routi (the other two); Eq. rsearch
+    const double ro = prm.cutoff_mode == P3T_CUT_HILL_VRAN
+                          ? fmax(prm.rcut0 * rhill, prm.rcut1 * vr * prm.dt_soft)
+                          : prm.rcut0 * rhill;
+    const double rs = prm.rs0 * ro + prm.rs1 * vr * prm.dt_soft;
     r_out[i] = ro;
-    r_search[i] = prm.rs0 * ro + prm.rs1 * vr * prm.dt_soft;
+    r_search[i] = rs;
+    if (prm.cutoff_mode == P3T_CUT_SHARED) {
+      // non-negative doubles order like their bit patterns
+      atomicMax(&bits[2], (unsigned long long)__double_as_longlong(ro));
+      atomicMax(&bits[3], (unsigned long long)__double_as_longlong(rs));
+    }
+  }
+}
+
+// shared cut-off (Eq. rout1): every particle gets the largest r_out and the
+// largest search radius
+__global__ void k_cut_shared(int64_t n, const unsigned long long *bits, double *r_out,
+                             double *r_search) {
+  const double ro = __longlong_as_double((long long)bits[2]);
+  const double rs = __longlong_as_double((long long)bits[3]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    r_out[i] = ro;
+    r_search[i] = rs;
   }
 }
 
@@ -595,7 +617,9 @@ int p3t_run_cutoffs(p3t_ctx *c, p3t_particles *p, cudaStream_t s) {
   k_cut_final<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, p->z, p->vx, p->vy,
                                              p->vz, p->m, c->prm, c->box_bits, nb,
                                              bsum, bcnt, p->r_out, p->r_search);
-  p3t_note_launches(4);
+  if (c->prm.cutoff_mode == P3T_CUT_SHARED)
+    k_cut_shared<<<(unsigned)g, kBlock, 0, s>>>(n, c->box_bits, p->r_out, p->r_search);
+  p3t_note_launches(c->prm.cutoff_mode == P3T_CUT_SHARED ? 5 : 4);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 

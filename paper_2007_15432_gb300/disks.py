@@ -186,3 +186,15 @@ def clump(n, seed, a=1.0, size=2e-4, m=1e-9, v_disp=1e-3):
     return {"x": x, "y": y, "z": z, "vx": rng.normal(0, v_disp, n),
             "vy": vk + rng.normal(0, v_disp, n), "vz": rng.normal(0, v_disp, n),
             "m": np.full(n, m)}
+
+
+def mass_spectrum_ring(n=377_740, seed=1005, m1=1e-12, m2=4.25e-9, e_rms=None, i_rms=None):
+    """Stand-in for the paper's mass-spectrum snapshot (Sec. 3.2.2: N =
+    377,740 on the 0.9-1.1 au ring, masses 2e21 to 8.46e24 g, mean 5.3e21 g):
+    power-law masses on [m1, m2] (mean ~3e-12 for slope 2.5), e/i rms 2h/h per
+    particle, or the given rms values for every particle."""
+    rng = np.random.default_rng(seed)
+    m = power_law_masses(rng, n, m1, m2)
+    h = np.cbrt(m / 3.0)
+    return disk(n, 0.9, 1.1, 2.0 * h if e_rms is None else e_rms,
+                h if i_rms is None else i_rms, m, seed + 1)

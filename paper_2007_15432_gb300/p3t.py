@@ -35,6 +35,9 @@ P3T_ERR_DT_UNDERFLOW = -4
 P3T_ERR_TIMEOUT = -5
 P3T_FP64 = 0
 P3T_MIXED = 1
+P3T_CUT_HILL_VRAN = 0
+P3T_CUT_HILL = 1
+P3T_CUT_SHARED = 2
 
 
 class Params(C.Structure):
@@ -44,12 +47,13 @@ class Params(C.Structure):
         "G", "m_star", "dt_soft", "gamma", "rcut0", "rcut1", "rs0", "rs1", "rs2",
         "rs3", "theta", "eta", "eta0", "f_radius")] + [
         ("leaf_size", C.c_int32), ("precision", C.c_int32), ("vran_bins", C.c_int32),
-        ("group_size", C.c_int32)]
+        ("group_size", C.c_int32), ("cutoff_mode", C.c_int32)]
 
     def __init__(self, **kw):
         d = dict(G=1.0, m_star=1.0, dt_soft=1.0 / 64.0, gamma=0.1, rcut0=2.0, rcut1=8.0,
                  rs0=1.1, rs1=6.0, rs2=2.0, rs3=2.0, theta=0.5, eta=0.01, eta0=0.001,
-                 f_radius=0.0, leaf_size=16, precision=P3T_FP64, vran_bins=0, group_size=0)
+                 f_radius=0.0, leaf_size=16, precision=P3T_FP64, vran_bins=0, group_size=0,
+                 cutoff_mode=P3T_CUT_HILL_VRAN)
         d.update(kw)
         super().__init__(**d)
 

@@ -19,6 +19,6 @@ def oracle_params(P, **kw):
     from oracle import oracle as O
     d = {k: getattr(P, k) for k in ("G", "m_star", "dt_soft", "gamma", "rcut0", "rcut1", "rs0",
                                     "rs1", "rs2", "rs3", "theta", "eta", "eta0", "f_radius", "leaf_size",
-                                    "precision", "vran_bins", "group_size")}
+                                    "precision", "vran_bins", "group_size", "cutoff_mode")}
     d.update(kw)
     return O.Params(**d)

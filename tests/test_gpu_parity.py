@@ -100,9 +100,10 @@ def test_wide_power_law_mixed(P3T, group_size):
         P3T.p3t_destroy(ctx)
 
 
-def test_cutoffs_match_oracle(P3T):
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_cutoffs_match_oracle(P3T, mode):
     for s in (disks.equal_mass_narrow(n=5000, seed=3), disks.wide_power_law(n=20000, seed=4)):
-        P = P3T.Params()
+        P = P3T.Params(cutoff_mode=mode)
         op = oracle_params(P)
         ro, rs, _, b = O.cutoffs(s, op)
         st, ctx = _setup(P3T, s, P)

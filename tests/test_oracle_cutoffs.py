@@ -64,3 +64,29 @@ def test_random_velocity_term_dominates_when_hot(orc):
     edges = np.exp(np.linspace(np.log(R.min()), np.log(R.max()), 4))
     ref = np.clip(np.searchsorted(edges, R, side="right") - 1, 0, 2)
     assert np.mean(ref == b) > 0.999
+
+
+def test_hill_only_mode_is_the_hill_term(orc):
+    """Eq. routi (mode 1) is Eq. routi2 without the random-velocity term, and
+    on circular orbits it is R~cut,0 (m / 3 M_*)^(1/3) r."""
+    s = disks.wide_power_law(n=3000, seed=12, n_proto=0)
+    p1 = orc.Params(cutoff_mode=1, rcut0=1.7)
+    p0 = orc.Params(cutoff_mode=0, rcut0=1.7, rcut1=0.0)
+    ro1, rs1, _, _ = orc.cutoffs(s, p1)
+    ro0, rs0, _, _ = orc.cutoffs(s, p0)
+    assert np.array_equal(ro1, ro0) and np.array_equal(rs1, rs0)
+    a = np.array([1.0, 2.5, 7.0])
+    z = np.zeros(3)
+    c = disks.elements_to_state(a, z, z, z, z, np.array([0.3, 1.0, 4.0]))
+    c["m"] = np.array([1e-9, 3e-8, 1e-12])
+    ro, _, _, _ = orc.cutoffs(c, p1)
+    assert np.allclose(ro, 1.7 * np.cbrt(c["m"] / 3.0) * a, rtol=1e-13, atol=0)
+
+
+def test_shared_mode_is_the_largest_individual_radius(orc):
+    """Eq. rout1: one radius for every pair, the largest of Eq. routi; the
+    search radius likewise the largest one (Sec. 2.3)."""
+    s = disks.wide_power_law(n=3000, seed=13, n_proto=3)
+    ro1, rs1, _, _ = orc.cutoffs(s, orc.Params(cutoff_mode=1))
+    ro2, rs2, _, _ = orc.cutoffs(s, orc.Params(cutoff_mode=2))
+    assert np.all(ro2 == ro1.max()) and np.all(rs2 == rs1.max())
