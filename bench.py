@@ -44,6 +44,10 @@ FLOP_PP, FLOP_PN = 30.0, 70.0
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 (FMA)
 # x 2.07 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) of one k_walk launch on the N = 10^6 wide disk,
+# group size 64, from a single-pass ncu capture of this kernel
+# (dram__bytes_read.sum 78.40 MB + dram__bytes_write.sum 16.98 MB)
+WALK_TRAFFIC_1E6 = 95.38e6
 
 
 def parse():
@@ -62,6 +66,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-targets", type=int, default=16384,
                     help="targets of the CPU oracle's timed walk sample")
+    ap.add_argument("--ensemble", action="store_true",
+                    help="the batched ensemble of 256 independent disks: one CUDA graph per "
+                         "step vs the same disks stepped one after another")
     ap.add_argument("--cutoff-sweep", action="store_true",
                     help="compare the cut-off schemes (shared / individual / individual with "
                          "random velocity) over R~cut,0 on the mass-spectrum ring; one JSON "
@@ -405,7 +412,9 @@ def run_ours(args):
                        merge_and_recompute=phase[5]),
         roofline=dict(kernel="k_walk (mixed) + FP64 refinement", bound="alu",
                       achieved=achieved, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
-                      frac=achieved / FP32_PEAK_TFLOPS, traffic=None),
+                      frac=achieved / FP32_PEAK_TFLOPS,
+                      traffic=WALK_TRAFFIC_1E6 if (args.n == 1_000_000 and args.group_size == 64)
+                      else None, traffic_kernel="k_walk"),
         e2e=dict(value=tot_e2e_inter / tot_e2e_t, unit=UNIT, h2d_bytes_per_step=h2d,
                  d2h_bytes_per_step=d2h),
         gpu_launches=int(launches),
@@ -507,8 +516,79 @@ def run_cutoff_sweep(args):
     return 0
 
 
+# ------------------------------------------------------------- ensemble ------
+def run_ensemble(args):
+    """256 independent disks (sizes round(exp U(ln 512, ln 16384)), seeds
+    4000 + d; even disks equal-mass rings, odd disks power-law wide disks), no
+    collisions.  Group sizes per disk-size class from the autotuner.  One
+    ensemble soft step = one replay of a captured CUDA graph (disks forked
+    over 16 streams); compared with the same kernels issued disk after disk
+    on one stream.  Value: pair interactions of all disks per second."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_2007_15432_gb300 import build, disks
+    build.build()
+    from paper_2007_15432_gb300 import ensemble as EN
+    from paper_2007_15432_gb300 import p3t as P
+    ds = disks.ensemble_disks()
+    base = P.Params(theta=0.5, precision=P.P3T_MIXED, eta=0.01, eta0=0.001)
+    t0 = time.perf_counter()
+    tune = EN.autotune(ds, base)
+    t_tune = time.perf_counter() - t0
+    params = []
+    for d in ds:
+        p = P.Params(**{f[0]: getattr(base, f[0]) for f in P.Params._fields_})
+        p.group_size = tune[EN.size_class(len(d["m"]))]
+        params.append(p)
+
+    def timed(run, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        inter = 0
+        e0.record()
+        for _ in range(k):
+            run()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / 1e3
+
+    K, W = args.steps, args.warmup
+    ens = EN.Ensemble(ds, params)
+    ens.init()
+    ens.capture()
+    for _ in range(W):
+        ens.step_graph()
+    torch.cuda.synchronize(dev)
+    t_graph = timed(ens.step_graph, K)
+    ens.status()
+    inter = ens.interactions()
+    ens.close()
+    seq = EN.Ensemble(ds, params)
+    seq.init()
+    for _ in range(W):
+        seq.step_sequential()
+    torch.cuda.synchronize(dev)
+    t_seq = timed(seq.step_sequential, K)
+    seq.status()
+    inter_seq = seq.interactions()
+    seq.close()
+    line = dict(metric="ensemble soft step: pair-interactions/s of all disks", study="ensemble",
+                value=inter / (t_graph / K), unit=UNIT, n_gpus=1, steps=K, warmup=W,
+                ms_per_step=1e3 * t_graph / K, higher_is_better=True,
+                sequential=dict(value=inter_seq / (t_seq / K), ms_per_step=1e3 * t_seq / K),
+                speedup=(t_seq / K) / (t_graph / K), dtype="f32/f64", data="synthetic (seeded disks)",
+                config=dict(workload="ensemble of 256 disks, sizes round(exp U(ln 512, ln 16384))",
+                            n_total=int(sum(len(d["m"]) for d in ds)), streams=16,
+                            group_size_by_log2_n={str(k): v for k, v in sorted(tune.items())},
+                            autotune_s=t_tune))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.ensemble:
+        return run_ensemble(args)
     if args.cutoff_sweep:
         return run_cutoff_sweep(args)
     if args.impl == "reference":

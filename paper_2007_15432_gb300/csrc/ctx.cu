@@ -8,7 +8,7 @@
 
 #include "p3t_internal.cuh"
 
-int64_t p3t_walk_warps(int num_sms);
+int64_t p3t_walk_warps(int num_sms, int64_t n);
 
 static std::atomic<long long> g_launches{0};
 void p3t_note_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -103,7 +103,7 @@ int reserve(p3t_ctx *c, int64_t n, int64_t cand_cap) {
   const int64_t NC = want_nodes;
   c->node_cap = NC;
   c->cand_cap = cand_cap;
-  c->walk_warps = p3t_walk_warps(c->num_sms);
+  c->walk_warps = p3t_walk_warps(c->num_sms, N);
   c->stack_cap = kStackCap;
   c->radix_hist_cap = p3t_radix_hist_entries(N > NC ? N : NC);
   bool ok = true;
@@ -174,9 +174,8 @@ int p3t_create(p3t_ctx **ctx, const p3t_params *p, int device) {
     delete c;
     return P3T_ERR_CUDA;
   }
-  c->coop_blocks = p3t_moments_coop_blocks(c->num_sms);
   bool ok = dalloc(c->status, 1) && dalloc(c->box, 5) && dalloc(c->box_bits, 6) &&
-            dalloc(c->counters, 24) && dalloc(c->cl_counts, 4) && dalloc(c->hsteps, 1) && dalloc(c->hcursor, 3) &&
+            dalloc(c->counters, 64) && dalloc(c->cl_counts, 4) && dalloc(c->hsteps, 1) && dalloc(c->hcursor, 3) &&
             dalloc(c->coll_ctr, 1) &&
             dalloc(c->epart, 8192) && dalloc(c->scan_part, 1025) && dalloc(c->bh_table, 32);
   for (int q = 0; q < 2 && ok; ++q)
@@ -184,7 +183,7 @@ int p3t_create(p3t_ctx **ctx, const p3t_params *p, int device) {
          cudaEventCreateWithFlags(&c->ev_join[q], cudaEventDisableTiming) == cudaSuccess;
   if (ok) ok = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
   if (ok) ok = cudaMemset(c->status, 0, sizeof(DevStatus)) == cudaSuccess &&
-               cudaMemset(c->counters, 0, 24 * sizeof(int64_t)) == cudaSuccess &&
+               cudaMemset(c->counters, 0, 64 * sizeof(int64_t)) == cudaSuccess &&
                cudaMemset(c->coll_ctr, 0, sizeof(unsigned long long)) == cudaSuccess &&
                cudaMemset(c->cl_counts, 0, 4 * sizeof(int64_t)) == cudaSuccess;
   if (!ok) {
@@ -233,6 +232,8 @@ int p3t_reserve(p3t_ctx *c, int64_t n) {
 int p3t_cutoffs(p3t_ctx *c, p3t_particles *p, void *stream) {
   if (!c || !particles_ok(p)) return P3T_ERR_INVALID;
   DeviceGuard g(c->device);
+  int rc = ensure(c, p->n);
+  if (rc) return rc;
   return p3t_run_cutoffs(c, p, (cudaStream_t)stream);
 }
 
@@ -329,6 +330,8 @@ int p3t_merge(p3t_ctx *c, p3t_particles *p, int32_t *new_index, double *e_disp,
 int p3t_energy(p3t_ctx *c, const p3t_particles *p, double *out, void *stream) {
   if (!c || !particles_ok(p) || !out) return P3T_ERR_INVALID;
   DeviceGuard g(c->device);
+  int rc = ensure(c, p->n);
+  if (rc) return rc;
   return p3t_run_energy(c, p, out, (cudaStream_t)stream);
 }
 

@@ -796,7 +796,7 @@ constexpr int kETile = 256;
 // E = sum m v^2/2 - sum G M m / r - 1/2 sum_i sum_{j != i} G m_i m_j / r_ij
 template <bool MIXED>
 __global__ void __launch_bounds__(kETile) k_energy(p3t_particles p, p3t_params prm,
-                                                   double *out) {
+                                                   double *part) {
   __shared__ double s_x[kETile], s_y[kETile], s_z[kETile], s_m[kETile];
   __shared__ float4 s_h[kETile], s_l[kETile];
   __shared__ double s_red[3][kETile / 32];
@@ -864,17 +864,30 @@ __global__ void __launch_bounds__(kETile) k_energy(p3t_particles p, p3t_params p
   if ((threadIdx.x & 31) == 0)
     for (int q = 0; q < 3; ++q) s_red[q][threadIdx.x >> 5] = v[q];
   __syncthreads();
-  if (threadIdx.x < 3) {
+  if (threadIdx.x < 3) {  // per-block partials, added in block order afterwards
     double s = 0.0;
     for (int w = 0; w < kETile / 32; ++w) s += s_red[threadIdx.x][w];
-    atomicAdd(&out[1 + threadIdx.x], s);
+    part[3 * (int64_t)blockIdx.x + threadIdx.x] = s;
   }
 }
 
-__global__ void k_energy_init(double *out) {
-  if (threadIdx.x < 4) out[threadIdx.x] = 0.0;
+// the three sums over the block partials in block order (one warp each, a
+// fixed lane-strided order and shuffle tree): the same result on every run
+__global__ void k_energy_final(const double *part, int64_t nblocks, double *out) {
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ double sum[3];
+  if (q < 3) {
+    double s = 0.0;
+    for (int64_t b = lane; b < nblocks; b += 32) s += part[3 * b + q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) sum[q] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    out[1] = sum[0]; out[2] = sum[1]; out[3] = sum[2];
+    out[0] = sum[0] + sum[1] + sum[2];
+  }
 }
-__global__ void k_energy_final(double *out) { out[0] = out[1] + out[2] + out[3]; }
 
 
 // ---- row f4: the merge after the second kick (procedure step 9) ------------
@@ -1087,15 +1100,15 @@ int p3t_run_merge(p3t_ctx *c, p3t_particles *p, int32_t *new_index, double *e_di
 }
 
 int p3t_run_energy(p3t_ctx *c, const p3t_particles *p, double *out, cudaStream_t s) {
-  k_energy_init<<<1, 32, 0, s>>>(out);
+  const int64_t g = (p->n + kETile - 1) / kETile;
+  double *part = c->hw;  // 3 g <= 33 cap doubles
   if (p->n > 0) {
-    const unsigned g = (unsigned)((p->n + kETile - 1) / kETile);
     if (c->prm.precision == P3T_MIXED)
-      k_energy<true><<<g, kETile, 0, s>>>(*p, c->prm, out);
+      k_energy<true><<<(unsigned)g, kETile, 0, s>>>(*p, c->prm, part);
     else
-      k_energy<false><<<g, kETile, 0, s>>>(*p, c->prm, out);
+      k_energy<false><<<(unsigned)g, kETile, 0, s>>>(*p, c->prm, part);
   }
-  k_energy_final<<<1, 1, 0, s>>>(out);
-  p3t_note_launches(p->n > 0 ? 3 : 2);
+  k_energy_final<<<1, 96, 0, s>>>(part, g, out);
+  p3t_note_launches(p->n > 0 ? 2 : 1);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }

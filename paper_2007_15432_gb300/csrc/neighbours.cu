@@ -210,9 +210,11 @@ int p3t_run_neighbours(p3t_ctx *c, const p3t_particles *p, int64_t *nb_off,
                                               c->cl_off, c->mkeys, c->mvals, c->cl_counts);
   // filter, check, fill, sort_rows, zero, uf_init, uf_union, uf_label, flags, scatter
   p3t_note_launches(10);
-  // members ordered by (label, index): stable sort of the ascending member list
-  int bits = 8;
-  while (bits < 32 && ((int64_t)1 << bits) < n) bits += 8;
+  // members ordered by (label, index): stable sort of the ascending member list;
+  // an even number of 8-bit passes leaves the result in the buffer it started
+  // in, so the cluster views keep their addresses from step to step (a step
+  // captured in a CUDA graph reads the previous step's clusters there)
+  const int bits = n <= 65536 ? 16 : 32;
   uint64_t *k0 = c->mkeys, *k1 = c->mkeys_alt;
   int32_t *v0 = c->mvals, *v1 = c->mvals_alt;
   rc = p3t_radix_sort(&k0, &v0, &k1, &v1, &cnt[11], c->cap, 0, bits, c->radix_hist,

@@ -68,7 +68,6 @@ struct p3t_ctx {
   int64_t node_cap = 0;   // node capacity
   int64_t cand_cap = 0;   // neighbour-candidate capacity (pairs)
   int64_t walk_warps = 0; // resident warps of the walk kernel
-  int64_t coop_blocks = 1; // blocks of the cooperative moments kernel
   int64_t stack_cap = 0;  // walk stack entries per warp
   int64_t last_n = -1;    // n of the last tree build
   bool have_tree = false;
@@ -78,7 +77,7 @@ struct p3t_ctx {
   // root box {x0, y0, z0, L} and scalar counters
   double *box = nullptr;
   unsigned long long *box_bits = nullptr;  // ordered-bits min/max workspace [6]
-  int64_t *counters = nullptr;             // misc device counters [24]
+  int64_t *counters = nullptr;             // misc device counters [64] (32..53: tree level offsets)
 
   // sort
   uint64_t *keys = nullptr, *keys_alt = nullptr;
@@ -194,7 +193,6 @@ int64_t p3t_radix_hist_entries(int64_t n_cap);
 int p3t_run_cutoffs(p3t_ctx *c, p3t_particles *p, cudaStream_t s);
 int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s);
 int p3t_run_tree_stats(p3t_ctx *c, cudaStream_t s);
-int p3t_moments_coop_blocks(int num_sms);
 int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
                        double *ay, double *az, uint64_t *counts,
                        cudaStream_t s);

@@ -3,11 +3,7 @@
 // and the integer grid geometry must be bit-identical on every IEEE machine.
 #include <math.h>
 
-#include <cooperative_groups.h>
-
 #include "p3t_internal.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace {
 
@@ -64,15 +60,12 @@ __device__ __forceinline__ int cut_bin(double R, double Rmin, double Rmax,
   return k;
 }
 
-__global__ void k_cut_bins(int64_t n, const double *x, const double *y,
-                           const double *z, const double *vx, const double *vy,
-                           const double *vz, double mu,
-                           const unsigned long long *bits, int nb, double *bsum,
-                           unsigned long long *bcnt) {
-  extern __shared__ double s_sum[];
-  unsigned int *s_cnt = reinterpret_cast<unsigned int *>(s_sum + nb);
-  for (int k = threadIdx.x; k < nb; k += blockDim.x) { s_sum[k] = 0.0; s_cnt[k] = 0u; }
-  __syncthreads();
+// |u|^2 and the radial bin of every particle; bin counts (integer atomics);
+// (bin, index) pairs for a stable sort by bin
+__global__ void k_cut_u2(int64_t n, const double *x, const double *y, const double *z,
+                         const double *vx, const double *vy, const double *vz, double mu,
+                         const unsigned long long *bits, int nb, double *u2, uint64_t *key,
+                         int32_t *idx, unsigned long long *bcnt) {
   const double Rmin = ord_double(bits[0]), Rmax = ord_double(bits[1]);
   const double lmin = log(Rmin), lmax = log(Rmax);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -83,17 +76,34 @@ __global__ void k_cut_bins(int64_t n, const double *x, const double *y,
     double px = 0.0, py = 0.0;
     if (R > 0.0) { px = -y[i] / R; py = x[i] / R; }
     double ux = vx[i] - vk * px, uy = vy[i] - vk * py, uz = vz[i];
-    double u2 = ux * ux + uy * uy + uz * uz;
-    int k = cut_bin(R, Rmin, Rmax, lmin, lmax, nb);
-    atomicAdd(&s_sum[k], u2);
-    atomicAdd(&s_cnt[k], 1u);
+    u2[i] = ux * ux + uy * uy + uz * uz;
+    const int k = cut_bin(R, Rmin, Rmax, lmin, lmax, nb);
+    key[i] = (uint64_t)k;
+    idx[i] = (int32_t)i;
+    atomicAdd(&bcnt[k], 1ull);
   }
-  __syncthreads();
-  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-    if (s_cnt[k]) {
-      atomicAdd(&bsum[k], s_sum[k]);
-      atomicAdd(&bcnt[k], (unsigned long long)s_cnt[k]);
-    }
+}
+
+// exclusive offsets of the bins (one thread: at most 4096 bins)
+__global__ void k_cut_offsets(int nb, const unsigned long long *bcnt, int64_t *boff) {
+  int64_t o = 0;
+  for (int k = 0; k < nb; ++k) { boff[k] = o; o += (int64_t)bcnt[k]; }
+  boff[nb] = o;
+}
+
+// sum of |u|^2 over each bin, one warp per bin over its members in index
+// order (a fixed lane-strided order and a fixed shuffle tree: the same sum
+// on every run)
+__global__ void k_cut_binsum(int nb, const int64_t *boff, const int32_t *sorted_idx,
+                             const double *u2, double *bsum) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t k = w0; k < nb; k += nw) {
+    double sum = 0.0;
+    for (int64_t j = boff[k] + lane; j < boff[k + 1]; j += 32) sum += u2[sorted_idx[j]];
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) bsum[k] = sum;
   }
 }
 
@@ -519,22 +529,24 @@ __device__ __forceinline__ int64_t level_begin(const TreeNode *node, int64_t nn,
   return lo;
 }
 
-// The internal nodes, deepest level first, in one cooperative launch: the
-// blocks take a level's nodes and wait at a grid barrier before the next
-// non-empty level (levels ascend in breadth-first order; internal nodes have
-// levels 0..20).
-__global__ void k_moments_levels(const int64_t *d_nnode, int64_t node_cap, TreeNode *node,
-                                 Mom64 *m64, Mom32 *m32, double *nrs, const double *box) {
-  cg::grid_group grid = cg::this_grid();
-  __shared__ int64_t range[2];
+// first breadth-first id of every level 0..21 and the node count (levels
+// ascend in breadth-first order): one thread per level
+__global__ void k_level_offsets(const int64_t *d_nnode, int64_t node_cap, const TreeNode *node,
+                                int64_t *lvl_start) {
   const int64_t nn = min(*d_nnode, node_cap);
+  const int l = threadIdx.x;
+  if (l <= P3T_BITS + 1) lvl_start[l] = l == P3T_BITS + 1 ? nn : level_begin(node, nn, l);
+}
+
+// The internal nodes of one level (levels 0..20), one thread per node, from
+// their finished children; launched level by level, deepest first.  (A grid
+// barrier between levels in one cooperative launch was measured slower than
+// the launches: its waits dominated.)
+__global__ void k_moments_level(int level, const int64_t *lvl_start, TreeNode *node,
+                                Mom64 *m64, Mom32 *m32, double *nrs, const double *box) {
   const double u = ldexp(box[3], -P3T_BITS);
-  for (int level = P3T_BITS - 1; level >= 0; --level) {
-    __syncthreads();
-    if (threadIdx.x < 2) range[threadIdx.x] = level_begin(node, nn, level + (int)threadIdx.x);
-    __syncthreads();
-    const int64_t b0 = range[0], b1 = range[1];
-    if (b0 >= b1) continue;  // the same for every block: no barrier needed
+  {
+    const int64_t b0 = lvl_start[level], b1 = lvl_start[level + 1];
     for (int64_t b = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < b1;
          b += (int64_t)gridDim.x * blockDim.x) {
       TreeNode *pn = &node[b];
@@ -570,7 +582,6 @@ __global__ void k_moments_levels(const int64_t *d_nnode, int64_t node_cap, TreeN
       nrs[b] = prs;
       finish_node(pn, m64, m32, prs, u, b, pm);
     }
-    grid.sync();
   }
 }
 
@@ -612,14 +623,27 @@ int p3t_run_cutoffs(p3t_ctx *c, p3t_particles *p, cudaStream_t s) {
   k_cut_init<<<4, kBlock, 0, s>>>(c->box_bits, bsum, bcnt, nb);
   k_cut_range<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, c->box_bits);
   const double mu = c->prm.G * c->prm.m_star;
-  k_cut_bins<<<(unsigned)g, kBlock, nb * (sizeof(double) + sizeof(unsigned)), s>>>(
-      n, p->x, p->y, p->z, p->vx, p->vy, p->vz, mu, c->box_bits, nb, bsum, bcnt);
+  // per-bin sums in a fixed order (particles grouped by bin with the stable
+  // radix sort, then one warp per bin): the radii do not depend on timing
+  double *u2 = c->hw;
+  int64_t *boff = c->pos;
+  int64_t *d_n = &c->counters[18];
+  k_set_i64<<<1, 1, 0, s>>>(d_n, n);
+  k_cut_u2<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, p->z, p->vx, p->vy, p->vz, mu,
+                                          c->box_bits, nb, u2, c->keys, c->idx, bcnt);
+  int rc = p3t_radix_sort(&c->keys, &c->idx, &c->keys_alt, &c->idx_alt, d_n, c->cap, 0, 16,
+                          c->radix_hist, c->radix_hist_cap, s);
+  if (rc) return rc;
+  k_cut_offsets<<<1, 1, 0, s>>>(nb, bcnt, boff);
+  k_cut_binsum<<<(unsigned)p3t_grid((int64_t)nb * 32, kBlock, (int64_t)c->num_sms * 4), kBlock, 0,
+                 s>>>(nb, boff, c->idx, u2, bsum);
   k_cut_final<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, p->z, p->vx, p->vy,
                                              p->vz, p->m, c->prm, c->box_bits, nb,
                                              bsum, bcnt, p->r_out, p->r_search);
   if (c->prm.cutoff_mode == P3T_CUT_SHARED)
     k_cut_shared<<<(unsigned)g, kBlock, 0, s>>>(n, c->box_bits, p->r_out, p->r_search);
-  p3t_note_launches(c->prm.cutoff_mode == P3T_CUT_SHARED ? 5 : 4);
+  // init, range, n, u2, offsets, bin sums, final (+ shared); the sort counts itself
+  p3t_note_launches(c->prm.cutoff_mode == P3T_CUT_SHARED ? 8 : 7);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 
@@ -671,18 +695,13 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
       &cnt[2], c->leaf_list, c->node, c->mom64, c->mom32, c->nrs, c->sx, c->sy, c->sz, c->sm,
       c->srs, c->sq, c->box);
   {
-    // internal nodes, level by level in one cooperative launch (every block
-    // resident: a few blocks per SM of a small kernel)
-    const int64_t *a0 = &cnt[3];
-    int64_t a1 = c->node_cap;
-    TreeNode *a2 = c->node;
-    Mom64 *a3 = c->mom64;
-    Mom32 *a4 = c->mom32;
-    double *a5 = c->nrs;
-    const double *a6 = c->box;
-    void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6};
-    P3T_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_moments_levels,
-                                             dim3((unsigned)c->coop_blocks), dim3(128), args, 0, s));
+    // internal nodes, level by level, deepest first
+    int64_t *lvl_start = c->counters + 32;  // [P3T_BITS + 2]
+    k_level_offsets<<<1, 32, 0, s>>>(&cnt[3], c->node_cap, c->node, lvl_start);
+    const unsigned gl = (unsigned)p3t_grid(c->node_cap, 128, (int64_t)c->num_sms * 2);
+    for (int l = P3T_BITS - 1; l >= 0; --l)
+      k_moments_level<<<gl, 128, 0, s>>>(l, lvl_start, c->node, c->mom64, c->mom32, c->nrs,
+                                         c->box);
   }
   k_group_flags<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->node, c->bfs2pre,
                                                 c->prm.group_size, c->group_flag);
@@ -694,21 +713,10 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
                                                c->group_list, c->leaf_of);
   // own kernels here (the scans and sorts count themselves): box 3, keys, n,
   // gather, lcp, levels, clamp, nodes_pre, pre2bfs, nodes_bfs, parents,
-  // leaf_list, moments (leaves, levels), group_flags, group_list
-  p3t_note_launches(18);
+  // leaf_list, moments (leaves, level offsets, 21 levels), group_flags,
+  // group_list
+  p3t_note_launches(18 + P3T_BITS);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
-}
-
-// blocks of k_moments_levels that are resident at once (cooperative launch)
-int p3t_moments_coop_blocks(int num_sms) {
-  int per = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_moments_levels, 128, 0) != cudaSuccess) {
-    cudaGetLastError();
-    per = 1;
-  }
-  if (per > 4) per = 4;
-  if (per < 1) per = 1;
-  return per * num_sms;
 }
 
 // tree statistics on demand (diagnostics; not part of the step)

@@ -705,7 +705,7 @@ int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
     a.bh[l] = X < big ? (int64_t)X : (int64_t)4611686018427387904LL;
   }
   k_walk_prep<<<1, 1, 0, s>>>(a.cursor, a.cand_count, a.counts, a.refine_count);
-  const unsigned blocks = (unsigned)(c->num_sms * p3t_walk_blocks_per_sm());
+  const unsigned blocks = (unsigned)(c->walk_warps / kWarps);
   if (c->prm.precision == P3T_MIXED) {
     // one target per lane (or several lanes per target): two targets per
     // lane (a 64-target group walked once) was measured slower than two
@@ -721,6 +721,12 @@ int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 
-int64_t p3t_walk_warps(int num_sms) {
-  return (int64_t)num_sms * p3t_walk_blocks_per_sm() * kWarps;
+// persistent walk warps for a context of up to n particles: 7 blocks per SM,
+// fewer for small systems (a block for every 256 particles: a group walk
+// takes a warp, and a group holds tens of particles)
+int64_t p3t_walk_warps(int num_sms, int64_t n) {
+  int64_t blocks = (int64_t)num_sms * p3t_walk_blocks_per_sm();
+  const int64_t want = n / 256 + 1;
+  if (want < blocks) blocks = want;
+  return blocks * kWarps;
 }

@@ -198,3 +198,24 @@ def mass_spectrum_ring(n=377_740, seed=1005, m1=1e-12, m2=4.25e-9, e_rms=None, i
     h = np.cbrt(m / 3.0)
     return disk(n, 0.9, 1.1, 2.0 * h if e_rms is None else e_rms,
                 h if i_rms is None else i_rms, m, seed + 1)
+
+
+def ensemble_sizes(n_disks=256, seed=4000, n_min=512, n_max=16384):
+    """Disk sizes round(exp U(ln n_min, ln n_max))."""
+    rng = np.random.default_rng(seed)
+    return np.round(np.exp(rng.uniform(np.log(n_min), np.log(n_max), n_disks))).astype(np.int64)
+
+
+def ensemble_disks(n_disks=256, seed=4000):
+    """The ensemble workload: disk d has the size above and seed 4000 + d;
+    even d: equal masses 1e-6 / n_d on 0.95-1.05 au, e/i rms 0.01/0.005;
+    odd d: power-law masses on [1e-12, 1e-8] on 1-10 au with e/i rms 2h/h
+    (the wide disk without protoplanets)."""
+    out = []
+    for d, n in enumerate(ensemble_sizes(n_disks, seed)):
+        n = int(n)
+        if d % 2 == 0:
+            out.append(disk(n, 0.95, 1.05, 0.01, 0.005, 1e-6 / n, seed + d))
+        else:
+            out.append(wide_power_law(n=n, seed=seed + d, n_proto=0))
+    return out

@@ -52,3 +52,11 @@ def test_binding_imports_and_mirrors_names():
     from paper_2007_15432_gb300 import p3t
     for n in _declared():
         assert hasattr(p3t, n), n
+
+
+def test_ensemble_descriptor_table():
+    """Row f1 host logic: disks laid end to end in the shared arrays."""
+    from paper_2007_15432_gb300 import ensemble as EN
+    t = EN.descriptor_table([5, 0, 3, 7])
+    assert t.tolist() == [[0, 5], [5, 0], [5, 3], [8, 7]]
+    assert EN.size_class(512) == 9 and EN.size_class(16383) == 13

@@ -332,3 +332,27 @@ def test_coincident_particles_level21_leaf(P3T):
         assert counts[0] == ref.n_pp and counts[1] == ref.n_pnode
         assert rel_err(acc, ref.acc).max() <= bar
         P3T.p3t_destroy(ctx)
+
+
+def test_runs_are_bit_reproducible(P3T):
+    """Two fresh contexts on the same input give the same bits: cut-off radii
+    (bin sums in a fixed order), three soft steps and the energy (block
+    partials added in a fixed order)."""
+    s = disks.wide_power_law(n=30000, seed=21, n_proto=4)
+    out = []
+    for _ in range(2):
+        P = P3T.Params(theta=0.5, precision=1, group_size=64)
+        st = P3T.State.from_numpy(s)
+        ss = P3T.SoftStep(P, st)
+        ss.init(update_cutoffs=True)
+        for _ in range(3):
+            ss.step()
+        e = torch.zeros(4, dtype=torch.float64, device="cuda")
+        P3T.p3t_energy(ss.ctx, st, e)
+        ss.status()
+        g = st.numpy()
+        g["E"] = e.cpu().numpy()
+        out.append(g)
+        ss.close()
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), k
