@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-targets", type=int, default=16384,
                     help="targets of the CPU oracle's timed walk sample")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time one gradient of the 32-step soft KDK rollout at N=1e4")
+    ap.add_argument("--adjoint-n", type=int, default=10_000)
     ap.add_argument("--ensemble", action="store_true",
                     help="the batched ensemble of 256 independent disks: one CUDA graph per "
                          "step vs the same disks stepped one after another")
@@ -585,8 +588,96 @@ def run_ensemble(args):
     return 0
 
 
+def run_adjoint(args):
+    """The differentiation workload: N = 1e4 equal-mass ring on 0.95-1.05 au
+    (m = 1e-10, seed 1006), 32 soft kick-drift-kick steps (every particle on
+    its Kepler orbit, direct changeover soft force, cut-off radii frozen at
+    the initial state), checkpoint every 8 steps, FP32 pair arithmetic with
+    FP64 state.  One step = one gradient of L = sum |x_N - x_target|^2 with
+    respect to x_0, v_0 and m (forward sweep + checkpointed reverse sweep);
+    x_target = x_N + seeded offsets of rms 1e-4 au.  Value: pair terms of
+    the forward forces, the recomputed forces and the VJPs per second."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_2007_15432_gb300 import build, disks
+    build.build()
+    from paper_2007_15432_gb300 import adjoint as AD
+    from paper_2007_15432_gb300 import p3t as P
+    n, steps, ck = args.adjoint_n, 32, 8
+    s = disks.adjoint_disk(n)
+    X0 = torch.tensor(np.stack([s["x"], s["y"], s["z"]]), device=dev)
+    V0 = torch.tensor(np.stack([s["vx"], s["vy"], s["vz"]]), device=dev)
+    M = torch.tensor(s["m"], device=dev)
+    RO = AD.cutoffs(P.Params(), X0, V0, M)
+    run = AD.SoftKDK(P.Params(precision=P.P3T_MIXED), n, steps, ck)
+    TGT = run.forward(X0, V0, M, RO)[0] + torch.tensor(disks.target_offsets(n), device=dev)
+
+    def grad():
+        x0, v0, m = X0.clone().requires_grad_(True), V0.clone().requires_grad_(True), \
+            M.clone().requires_grad_(True)
+        xN, _ = AD.soft_kdk(x0, v0, m, RO, run)
+        ((xN - TGT) ** 2).sum().backward()
+        return x0.grad, v0.grad, m.grad
+
+    K, W = args.steps, args.warmup
+    for _ in range(W):
+        grad()
+    torch.cuda.synchronize(dev)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record()
+    for _ in range(K):
+        grad()
+    e[1].record()
+    torch.cuda.synchronize(dev)
+    t = e[0].elapsed_time(e[1]) / 1e3 / K
+    # phases of one gradient
+    e[0].record()
+    xN, vN, tape = run.forward(X0, V0, M, RO)
+    e[1].record()
+    run.backward(tape, 2.0 * (xN - TGT), torch.zeros_like(vN))
+    e[2].record()
+    lp = torch.zeros(3, n, dtype=torch.float64, device=dev)
+    lxx = torch.zeros(3, n, dtype=torch.float64, device=dev)
+    gm = torch.zeros(n, dtype=torch.float64, device=dev)
+    st = run._state(X0.contiguous(), V0.contiguous(), M, RO)
+    e[3].record()
+    for _ in range(10):
+        P.p3t_soft_force_vjp(run.ctx, st, 1.0, lp, lxx, gm)
+    e4 = torch.cuda.Event(enable_timing=True)
+    e4.record()
+    torch.cuda.synchronize(dev)
+    run.status()
+    t_fwd, t_bwd = e[0].elapsed_time(e[1]) / 1e3, e[1].elapsed_time(e[2]) / 1e3
+    t_vjp = e[3].elapsed_time(e4) / 1e3 / 10
+    segs = (steps + ck - 1) // ck
+    forces = 2 * (steps + segs)            # forward sweep + recomputation
+    vjps = steps + 1
+    pairs = float(n) * (n - 1)
+    # FP32 work of one VJP pair term (float-float difference 9, r2 5, rsqrt,
+    # y and the changeover polynomial ~14, phi/psi 7, w 6, the four sums 14)
+    flop_vjp = 55.0
+    line = dict(metric="adjoint of 32 soft KDK steps at N=1e4: gradient time and pair terms/s",
+                study="adjoint", value=(forces + vjps) * pairs / t, unit=UNIT, n_gpus=1, steps=K,
+                warmup=W, ms_per_step=1e3 * t, higher_is_better=True,
+                phases_ms=dict(forward=1e3 * t_fwd, backward=1e3 * t_bwd, soft_vjp=1e3 * t_vjp),
+                roofline=dict(kernel="k_soft_vjp<FP32>", bound="alu",
+                              achieved=flop_vjp * pairs / t_vjp / 1e12, peak=FP32_PEAK_TFLOPS,
+                              unit="TFLOP/s", frac=flop_vjp * pairs / t_vjp / 1e12 / FP32_PEAK_TFLOPS,
+                              traffic=None),
+                dtype="f32 pair terms / f64 state", data="synthetic (seeded ring)",
+                config=dict(workload=f"equal-mass ring N={n}, 0.95-1.05 au, m=1e-10, 32 KDK steps, "
+                            "checkpoint 8", n=n, steps_per_gradient=steps, checkpoint=ck,
+                            forces_per_gradient=forces, vjps_per_gradient=vjps))
+    run.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.adjoint:
+        return run_adjoint(args)
     if args.ensemble:
         return run_ensemble(args)
     if args.cutoff_sweep:

@@ -261,6 +261,44 @@ int p3t_kick(p3t_ctx *ctx, p3t_particles *p, const double *ax, const double *ay,
 int p3t_merge(p3t_ctx *ctx, p3t_particles *p, int32_t *new_index, double *e_disp,
               int64_t *n_merged, void *stream);
 
+/* Row a6 at theta = 0 (and the forward force of the row-f2 adjoint) -- the
+ * soft force of Eq. softforce summed directly over all pairs, which is what
+ * the tree walk gives at theta = 0:
+ *   a_i = -G sum_{j != i} m_j K(r_ij / r_out,ij) r_ij / r_ij^3,
+ * r_out,ij = max(r_out,i, r_out,j); the central star is not included (it is
+ * in the hard part's Kepler drift).  ax, ay, az: device, n each, caller
+ * order, OVERWRITTEN.  P3T_FP64: FP64 arithmetic; P3T_MIXED: float-float
+ * positions, FP32 pair terms, float-float sums.  Deterministic (fixed
+ * summation order).  O(n^2): for small n and for the adjoint. */
+int p3t_soft_force_direct(p3t_ctx *ctx, const p3t_particles *p, double *ax, double *ay,
+                          double *az, void *stream);
+
+/* Row f2 (adjoint of the soft kick-drift-kick; the paper has no counterpart:
+ * a gradient of a trajectory with respect to its initial state) -- the
+ * vector-Jacobian product of the soft force of Eq. softforce with the cut-off
+ * radii held fixed, taken for the direct sum over all pairs (the force the
+ * tree approximates; exact at theta = 0):
+ *   g_k += h G sum_j J(r_kj) (m_k lam_j - m_j lam_k),
+ *   gm_k += h G sum_j phi_kj lam_j . r_kj,
+ * J = phi I + psi r r^T the derivative of F(r) = K(|r|/r_out) r / |r|^3,
+ * phi = K / r^3, psi = K'(y) / (r_out r^4) - 3 K / r^5.  That is, with
+ * lam the adjoint of the velocity after a kick v += h a, the contributions
+ * of that kick to the adjoints of the positions (gx, gy, gz) and masses (gm),
+ * ADDED to what the arrays hold.  lx, ly, lz, gx..gm: device, n each, caller
+ * order.  Arithmetic as p3t_soft_force_direct (FP64, or FP32 pair terms with
+ * P3T_MIXED); deterministic.  O(n^2). */
+int p3t_soft_force_vjp(p3t_ctx *ctx, const p3t_particles *p, double h, const double *lx,
+                       const double *ly, const double *lz, double *gx, double *gy, double *gz,
+                       double *gm, void *stream);
+
+/* Row f2 -- the adjoint of the Kepler drift of every particle of p by dt
+ * (row a9's map, mu = G M_*): on entry lx..lvz hold the adjoint of the state
+ * after the drift, on return the adjoint of the state before it (Phi^T lam,
+ * Phi the state-transition matrix at the state p holds, which is the state
+ * BEFORE the drift).  Device arrays, n each, caller order. */
+int p3t_kepler_vjp(p3t_ctx *ctx, const p3t_particles *p, double dt, double *lx, double *ly,
+                   double *lz, double *lvx, double *lvy, double *lvz, void *stream);
+
 /* Row a10 -- total energy (Eqs. soft and hard; W + (1 - W) = 1 makes it the
  * Newtonian energy): out = device double[4] {E, kinetic, star potential,
  * pair potential}.  The pair sum is direct O(n^2), in FP64 for P3T_FP64 and

@@ -20,7 +20,7 @@ OBJDIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libp3t.so")
 
 SOURCES = ["primitives.cu", "tree.cu", "walk.cu", "neighbours.cu", "hard.cu", "ctx.cu",
-           "noalloc.cu"]
+           "noalloc.cu", "adjoint.cu", "direct.cu"]
 NO_FMA = {"tree.cu", "neighbours.cu", "hard.cu", "ctx.cu", "noalloc.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -205,6 +205,7 @@ void p3t_destroy(p3t_ctx *c) {
   dfree(c->coll_ctr);
   dfree(c->scan_part);
   dfree(c->bh_table);
+  dfree(c->dpart);
   for (int q = 0; q < 2; ++q) {
     if (c->aux[q]) cudaStreamDestroy(c->aux[q]);
     if (c->ev_join[q]) cudaEventDestroy(c->ev_join[q]);
@@ -325,6 +326,45 @@ int p3t_merge(p3t_ctx *c, p3t_particles *p, int32_t *new_index, double *e_disp,
   int rc = p3t_run_merge(c, p, new_index, e_disp, n_merged, (cudaStream_t)stream);
   if (rc == P3T_OK && p->n != n0) c->have_tree = c->have_cand = false;
   return rc;
+}
+
+// the all-pairs kernels' partial sums: one allocation of fixed size, made on
+// the first call (so a graph captured after one eager call allocates nothing)
+static int direct_scratch(p3t_ctx *c) {
+  if (c->dpart) return P3T_OK;
+  const int64_t want = p3t_direct_part_doubles(c);
+  if (!dalloc(c->dpart, want)) return P3T_ERR_CUDA;
+  c->dpart_cap = want;
+  return P3T_OK;
+}
+
+int p3t_soft_force_direct(p3t_ctx *c, const p3t_particles *p, double *ax, double *ay,
+                          double *az, void *stream) {
+  if (!c || !particles_ok(p)) return P3T_ERR_INVALID;
+  if (p->n > 0 && (!ax || !ay || !az)) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  int rc = direct_scratch(c);
+  if (rc) return rc;
+  return p3t_run_soft_force_direct(c, p, ax, ay, az, (cudaStream_t)stream);
+}
+
+int p3t_soft_force_vjp(p3t_ctx *c, const p3t_particles *p, double h, const double *lx,
+                       const double *ly, const double *lz, double *gx, double *gy, double *gz,
+                       double *gm, void *stream) {
+  if (!c || !particles_ok(p)) return P3T_ERR_INVALID;
+  if (p->n > 0 && (!lx || !ly || !lz || !gx || !gy || !gz || !gm)) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  int rc = direct_scratch(c);
+  if (rc) return rc;
+  return p3t_run_soft_force_vjp(c, p, h, lx, ly, lz, gx, gy, gz, gm, (cudaStream_t)stream);
+}
+
+int p3t_kepler_vjp(p3t_ctx *c, const p3t_particles *p, double dt, double *lx, double *ly,
+                   double *lz, double *lvx, double *lvy, double *lvz, void *stream) {
+  if (!c || !particles_ok(p)) return P3T_ERR_INVALID;
+  if (p->n > 0 && (!lx || !ly || !lz || !lvx || !lvy || !lvz)) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return p3t_run_kepler_vjp(c, p, dt, lx, ly, lz, lvx, lvy, lvz, (cudaStream_t)stream);
 }
 
 int p3t_energy(p3t_ctx *c, const p3t_particles *p, double *out, void *stream) {

@@ -1,0 +1,325 @@
+// All-pairs sums of the soft force of Eq. softforce (the tree at theta = 0)
+// and of its vector-Jacobian product (row f2), cut-off radii held fixed:
+//   a_k = -G sum_j m_j K(r_kj / r_out,kj) r_kj / r_kj^3,
+//   g_k += s sum_j J(r_kj) (m_k lam_j - m_j lam_k),  gm_k += s sum_j phi_kj lam_j . r_kj,
+// J = phi I + psi r r^T, phi = K / r^3, psi = K'(y) / (r_out r^4) - 3 K / r^5.
+//
+// Layout: a block is 8 warps over 64 targets (two per lane); the warps take
+// interleaved 32-source chunks of the block's source range and stage each
+// chunk in their own shared-memory slots as packed 4-vectors (one broadcast
+// load per vector, shared by the lane's two targets).  A grid column
+// (blockIdx.y) is one split of the sources; each block writes its per-target
+// sums to part[(split * C + c) * n + k] after adding its 8 warps in order,
+// and k_direct_sum adds the splits in order: the result does not depend on
+// scheduling.
+//
+// Precision: FP64 throughout, or (MIXED) float-float positions whose
+// difference (hi_k - hi_j) + (lo_k - lo_j) carries the relative coordinate
+// to about 2^-24 of itself, FP32 pair terms summed in FP32 over a 32-source
+// chunk and the chunk sums kept as float-float (TwoSum), so that no FP64
+// instruction runs inside the pair loop.
+#include <math.h>
+
+#include "p3t_internal.cuh"
+
+namespace {
+
+constexpr int kDW = 8;          // warps per block
+constexpr int kDT = 2;          // targets per lane
+constexpr int kDTB = 32 * kDT;  // targets per block
+
+template <typename T>
+struct alignas(4 * sizeof(T)) Q4 {
+  T x, y, z, w;
+};
+
+template <bool MIXED>
+struct DT {
+  using T = double;
+};
+template <>
+struct DT<true> {
+  using T = float;
+};
+
+__device__ __forceinline__ float rsq(float a) { return rsqrtf(a); }
+__device__ __forceinline__ double rsq(double a) { return 1.0 / sqrt(a); }
+
+// hi + lo += p without losing the rounding error of the addition (TwoSum)
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float p) {
+  const float s = hi + p;
+  const float b = s - hi;
+  lo += (hi - (s - b)) + (p - b);
+  hi = s;
+}
+
+// one pair term: k the target (its mass, 1/r_out and adjoint), j the source
+template <typename T, bool VJP>
+__device__ __forceinline__ void pair_term(T rx, T ry, T rz, const Q4<T> &A, T iroj,
+                                          const Q4<T> &L, T mk, T irok, T lxk, T lyk, T lzk,
+                                          T g, T i1mg, T *acc) {
+  const T r2 = rx * rx + ry * ry + rz * rz;
+  if (r2 == (T)0) return;  // the target itself
+  const T ir = rsq(r2);
+  const T irout = irok < iroj ? irok : iroj;  // 1 / max(r_out,k, r_out,j)
+  const T yv = r2 * ir * irout;
+  if (yv <= g) return;  // K = K' = 0
+  T K = 1, dKr = 0;     // K(y) and K'(y) / r_out
+  if (yv < (T)1) {
+    const T u = (yv - g) * i1mg, u2 = u * u, u3 = u2 * u;
+    K = u2 * u2 * ((T)35 - (T)84 * u + (T)70 * u2 - (T)20 * u3);
+    if constexpr (VJP) {
+      const T v = (T)1 - u;
+      dKr = (T)140 * u3 * (v * v * v) * i1mg * irout;
+    }
+  }
+  const T ir2 = ir * ir;
+  const T phi = K * ir2 * ir;
+  if constexpr (!VJP) {
+    const T w = A.w * phi;  // m_j K / r^3
+    acc[0] += w * rx;
+    acc[1] += w * ry;
+    acc[2] += w * rz;
+  } else {
+    const T psi = ir2 * ir2 * (dKr - (T)3 * K * ir);
+    const T wx = mk * L.x - A.w * lxk, wy = mk * L.y - A.w * lyk, wz = mk * L.z - A.w * lzk;
+    const T prw = psi * (rx * wx + ry * wy + rz * wz);
+    acc[0] += phi * wx + prw * rx;
+    acc[1] += phi * wy + prw * ry;
+    acc[2] += phi * wz + prw * rz;
+    acc[3] += phi * (L.x * rx + L.y * ry + L.z * rz);
+  }
+}
+
+// outputs: with one split, the block writes out_c[k] = (add ? out_c[k] : 0)
+// + scale * sum itself; with several, the sums go to part
+struct DOut {
+  double *o[4];
+  double scale;
+  int add;
+};
+
+template <bool MIXED, bool VJP>
+__global__ void __launch_bounds__(kDW * 32, MIXED ? 3 : 1)
+    k_direct(int64_t n, int64_t chunk, const double *x, const double *y, const double *z,
+             const double *m, const double *ro, const double *lx, const double *ly,
+             const double *lz, double gamma, double *part, DOut out) {
+  using T = typename DT<MIXED>::T;
+  constexpr int NC = VJP ? 4 : 3;
+  __shared__ Q4<T> sA[kDW][32];                     // x_hi, y_hi, z_hi, m
+  __shared__ Q4<T> sB[kDW][32];                     // x_lo, y_lo, z_lo, 1 / r_out
+  __shared__ Q4<T> sL[VJP ? kDW : 1][VJP ? 32 : 1];  // lam
+  __shared__ double red[kDW][NC][kDTB];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const T g = (T)gamma, i1mg = (T)(1.0 / (1.0 - gamma));
+
+  T txh[kDT], tyh[kDT], tzh[kDT], txl[kDT], tyl[kDT], tzl[kDT];
+  T tm[kDT], tiro[kDT], tlx[kDT], tly[kDT], tlz[kDT];
+#pragma unroll
+  for (int t = 0; t < kDT; ++t) {
+    const int64_t k = (int64_t)blockIdx.x * kDTB + t * 32 + lane;
+    txh[t] = tyh[t] = tzh[t] = txl[t] = tyl[t] = tzl[t] = 0;
+    tm[t] = tiro[t] = tlx[t] = tly[t] = tlz[t] = 0;  // 1/r_out = 0: no pair term
+    if (k < n) {
+      txh[t] = (T)x[k]; tyh[t] = (T)y[k]; tzh[t] = (T)z[k];
+      if constexpr (MIXED) {
+        txl[t] = (T)(x[k] - (double)txh[t]);
+        tyl[t] = (T)(y[k] - (double)tyh[t]);
+        tzl[t] = (T)(z[k] - (double)tzh[t]);
+      }
+      tm[t] = (T)m[k];
+      tiro[t] = (T)(1.0 / ro[k]);
+      if constexpr (VJP) {
+        tlx[t] = (T)lx[k]; tly[t] = (T)ly[k]; tlz[t] = (T)lz[k];
+      }
+    }
+  }
+  float fh[kDT][NC], fl[kDT][NC];  // MIXED running sums (float-float)
+  double dd[kDT][NC];              // FP64 running sums
+#pragma unroll
+  for (int t = 0; t < kDT; ++t)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) fh[t][c] = fl[t][c] = 0.0f, dd[t][c] = 0.0;
+
+  const int64_t s_lo = (int64_t)blockIdx.y * chunk;
+  const int64_t s_hi = min(n, s_lo + chunk);
+  for (int64_t cb = s_lo + (int64_t)warp * 32; cb < s_hi; cb += kDW * 32) {
+    const int lim = (int)min((int64_t)32, s_hi - cb);
+    __syncwarp();
+    if (lane < lim) {
+      const int64_t j = cb + lane;
+      Q4<T> A, B;
+      A.x = (T)x[j]; A.y = (T)y[j]; A.z = (T)z[j]; A.w = (T)m[j];
+      B.x = B.y = B.z = 0;
+      if constexpr (MIXED) {
+        B.x = (T)(x[j] - (double)A.x);
+        B.y = (T)(y[j] - (double)A.y);
+        B.z = (T)(z[j] - (double)A.z);
+      }
+      B.w = (T)(1.0 / ro[j]);
+      sA[warp][lane] = A;
+      sB[warp][lane] = B;
+      if constexpr (VJP) {
+        Q4<T> L;
+        L.x = (T)lx[j]; L.y = (T)ly[j]; L.z = (T)lz[j]; L.w = 0;
+        sL[warp][lane] = L;
+      }
+    }
+    __syncwarp();
+    T acc[kDT][NC];
+#pragma unroll
+    for (int t = 0; t < kDT; ++t)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[t][c] = 0;
+    for (int q = 0; q < lim; ++q) {
+      const Q4<T> A = sA[warp][q], B = sB[warp][q];
+      Q4<T> L{0, 0, 0, 0};
+      if constexpr (VJP) L = sL[warp][q];
+#pragma unroll
+      for (int t = 0; t < kDT; ++t) {
+        T rx = txh[t] - A.x, ry = tyh[t] - A.y, rz = tzh[t] - A.z;
+        if constexpr (MIXED) {
+          rx += txl[t] - B.x;
+          ry += tyl[t] - B.y;
+          rz += tzl[t] - B.z;
+        }
+        pair_term<T, VJP>(rx, ry, rz, A, B.w, L, tm[t], tiro[t], tlx[t], tly[t], tlz[t], g, i1mg,
+                          acc[t]);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kDT; ++t)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        if constexpr (MIXED) two_sum_acc(fh[t][c], fl[t][c], acc[t][c]);
+        else dd[t][c] += acc[t][c];
+      }
+  }
+#pragma unroll
+  for (int t = 0; t < kDT; ++t)
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      red[warp][c][t * 32 + lane] =
+          MIXED ? (double)fh[t][c] + (double)fl[t][c] : dd[t][c];
+  __syncthreads();
+  for (int e = threadIdx.x; e < NC * kDTB; e += kDW * 32) {
+    const int c = e / kDTB, tt = e - c * kDTB;
+    const int64_t k = (int64_t)blockIdx.x * kDTB + tt;
+    if (k >= n) continue;
+    double s = 0.0;
+    for (int w = 0; w < kDW; ++w) s += red[w][c][tt];
+    if (gridDim.y == 1) {
+      double *o = c == 0 ? out.o[0] : (c == 1 ? out.o[1] : (c == 2 ? out.o[2] : out.o[3]));
+      o[k] = (out.add ? o[k] : 0.0) + out.scale * s;
+    } else {
+      part[((int64_t)blockIdx.y * NC + c) * n + k] = s;
+    }
+  }
+}
+
+// out_c[k] = (add ? out_c[k] : 0) + scale * sum over splits of part (in order)
+__global__ void k_direct_sum(int64_t n, int nsplit, int nc, const double *part, double scale,
+                             int add, double *o0, double *o1, double *o2, double *o3) {
+  double *out[4] = {o0, o1, o2, o3};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (c >= nc) break;
+      double a = 0.0;
+      for (int s = 0; s < nsplit; ++s) a += part[((int64_t)s * nc + c) * n + k];
+      out[c][k] = (add ? out[c][k] : 0.0) + scale * a;
+    }
+  }
+}
+
+// Work split: blocks of 64 targets x one source split.  With fewer than 8
+// waves of target tiles alone, the sources are split so that the grid is at
+// least 8 waves of resident blocks (the last, partial wave then costs at most
+// an eighth); every split keeps at least 256 sources (a chunk per warp).
+// With ns >= 2 splits, (ns - 1) n < 8 slots 64, so the partial sums, C ns n
+// doubles, fit in 4 * 2 * 8 * slots * 64 (direct_part_doubles).
+template <bool MIXED, bool VJP>
+int blocks_per_sm() {
+  static int b = 0;
+  if (b == 0) {
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_direct<MIXED, VJP>, kDW * 32, 0) !=
+            cudaSuccess || v < 1)
+      v = 1;
+    b = v;
+  }
+  return b;
+}
+
+int max_blocks_per_sm() {
+  int b = blocks_per_sm<true, true>();
+  b = b > blocks_per_sm<true, false>() ? b : blocks_per_sm<true, false>();
+  b = b > blocks_per_sm<false, true>() ? b : blocks_per_sm<false, true>();
+  b = b > blocks_per_sm<false, false>() ? b : blocks_per_sm<false, false>();
+  return b;
+}
+
+struct Split {
+  int64_t tiles, chunk;
+  int nsplit;
+};
+Split split_for(const p3t_ctx *c, int64_t n, int bps) {
+  Split s;
+  s.tiles = (n + kDTB - 1) / kDTB;
+  const int64_t slots = (int64_t)c->num_sms * bps;
+  int64_t ns = 1;
+  if (s.tiles < 8 * slots) ns = (8 * slots + s.tiles - 1) / s.tiles;
+  const int64_t ns_max = (n + kDW * 32 - 1) / (kDW * 32);
+  ns = ns > ns_max ? ns_max : ns;
+  ns = ns < 1 ? 1 : ns;
+  s.chunk = (n + ns - 1) / ns;
+  s.chunk = (s.chunk + 31) / 32 * 32;
+  s.nsplit = (int)((n + s.chunk - 1) / s.chunk);
+  return s;
+}
+
+template <bool MIXED, bool VJP>
+int launch_direct(p3t_ctx *c, const p3t_particles *p, const double *lx, const double *ly,
+                  const double *lz, DOut out, cudaStream_t s) {
+  constexpr int NC = VJP ? 4 : 3;
+  const int64_t n = p->n;
+  const Split sp = split_for(c, n, blocks_per_sm<MIXED, VJP>());
+  if (sp.nsplit > 1 && (int64_t)NC * sp.nsplit * n > c->dpart_cap) return P3T_ERR_CAPACITY;
+  const dim3 grid((unsigned)sp.tiles, (unsigned)sp.nsplit);
+  k_direct<MIXED, VJP><<<grid, kDW * 32, 0, s>>>(n, sp.chunk, p->x, p->y, p->z, p->m, p->r_out,
+                                                lx, ly, lz, c->prm.gamma, c->dpart, out);
+  int launches = 1;
+  if (sp.nsplit > 1) {
+    k_direct_sum<<<(unsigned)p3t_grid(n, 256, (int64_t)c->num_sms * 4), 256, 0, s>>>(
+        n, sp.nsplit, NC, c->dpart, out.scale, out.add, out.o[0], out.o[1], out.o[2], out.o[3]);
+    ++launches;
+  }
+  p3t_note_launches(launches);
+  return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
+}
+
+}  // namespace
+
+int64_t p3t_direct_part_doubles(const p3t_ctx *c) {
+  return (int64_t)4 * 2 * 8 * c->num_sms * max_blocks_per_sm() * kDTB;
+}
+
+int p3t_run_soft_force_direct(p3t_ctx *c, const p3t_particles *p, double *ax, double *ay,
+                              double *az, cudaStream_t s) {
+  if (p->n == 0) return P3T_OK;
+  const DOut out{{ax, ay, az, nullptr}, -c->prm.G, 0};
+  return c->prm.precision == P3T_MIXED ? launch_direct<true, false>(c, p, nullptr, nullptr,
+                                                                    nullptr, out, s)
+                                       : launch_direct<false, false>(c, p, nullptr, nullptr,
+                                                                     nullptr, out, s);
+}
+
+int p3t_run_soft_force_vjp(p3t_ctx *c, const p3t_particles *p, double h, const double *lx,
+                           const double *ly, const double *lz, double *gx, double *gy,
+                           double *gz, double *gm, cudaStream_t s) {
+  if (p->n == 0) return P3T_OK;
+  const DOut out{{gx, gy, gz, gm}, h * c->prm.G, 1};
+  return c->prm.precision == P3T_MIXED ? launch_direct<true, true>(c, p, lx, ly, lz, out, s)
+                                       : launch_direct<false, true>(c, p, lx, ly, lz, out, s);
+}

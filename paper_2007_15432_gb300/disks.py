@@ -219,3 +219,15 @@ def ensemble_disks(n_disks=256, seed=4000):
         else:
             out.append(wide_power_law(n=n, seed=seed + d, n_proto=0))
     return out
+
+
+def adjoint_disk(n=10_000, seed=1006, m=1e-10):
+    """The differentiation workload: N equal-mass planetesimals on 0.95-1.05 au,
+    e/i rms 0.01/0.005."""
+    return disk(n, 0.95, 1.05, 0.01, 0.005, m, seed)
+
+
+def target_offsets(n, seed=1007, scale=1e-4):
+    """(3, n) Gaussian offsets of rms ``scale`` au per coordinate: the target of
+    the differentiation loss is the final position plus these."""
+    return np.random.default_rng(seed).normal(0.0, scale, (3, n))

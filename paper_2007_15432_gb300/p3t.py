@@ -85,6 +85,9 @@ _sig = {
     "p3t_energy": (C.c_int, [_CTX, C.POINTER(Particles), _vp, _vp]),
     "p3t_merge": (C.c_int, [_CTX, C.POINTER(Particles), _vp, C.POINTER(C.c_double),
                             C.POINTER(C.c_int64), _vp]),
+    "p3t_soft_force_direct": (C.c_int, [_CTX, C.POINTER(Particles), _vp, _vp, _vp, _vp]),
+    "p3t_soft_force_vjp": (C.c_int, [_CTX, C.POINTER(Particles), C.c_double] + [_vp] * 8),
+    "p3t_kepler_vjp": (C.c_int, [_CTX, C.POINTER(Particles), C.c_double] + [_vp] * 7),
     "p3t_status": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
     "p3t_tree_stats": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
     "p3t_strerror": (C.c_char_p, [C.c_int]),
@@ -263,6 +266,33 @@ def p3t_merge(ctx, st: State, new_index: torch.Tensor | None = None, stream=None
     if nm.value:
         st.truncate(int(p.n))
     return nm.value, e[0], e[1]
+
+
+def p3t_soft_force_direct(ctx, st: State, acc: torch.Tensor, stream=None) -> None:
+    """The soft force summed over all pairs (the tree at theta = 0); acc: (3, n)."""
+    p = st.particles()
+    _check(_lib.p3t_soft_force_direct(ctx, C.byref(p), _ptr(acc[0]), _ptr(acc[1]), _ptr(acc[2]),
+                                      _stream(stream)), "p3t_soft_force_direct")
+
+
+def p3t_soft_force_vjp(ctx, st: State, h: float, lam: torch.Tensor, gx: torch.Tensor,
+                       gm: torch.Tensor, stream=None) -> None:
+    """Adds h * lam^T da/dx (into gx, shape (3, n)) and h * lam^T da/dm (into
+    gm) for the soft force at the state st; lam: (3, n)."""
+    p = st.particles()
+    _check(_lib.p3t_soft_force_vjp(ctx, C.byref(p), float(h), _ptr(lam[0]), _ptr(lam[1]),
+                                   _ptr(lam[2]), _ptr(gx[0]), _ptr(gx[1]), _ptr(gx[2]), _ptr(gm),
+                                   _stream(stream)), "p3t_soft_force_vjp")
+
+
+def p3t_kepler_vjp(ctx, st: State, dt: float, lam_x: torch.Tensor, lam_v: torch.Tensor,
+                   stream=None) -> None:
+    """In place: the adjoints (lam_x, lam_v), each (3, n), of the state after a
+    Kepler drift by dt become those of the state st before it."""
+    p = st.particles()
+    _check(_lib.p3t_kepler_vjp(ctx, C.byref(p), float(dt), _ptr(lam_x[0]), _ptr(lam_x[1]),
+                               _ptr(lam_x[2]), _ptr(lam_v[0]), _ptr(lam_v[1]), _ptr(lam_v[2]),
+                               _stream(stream)), "p3t_kepler_vjp")
 
 
 def p3t_status(ctx) -> tuple[int, int]:
