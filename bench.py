@@ -651,7 +651,7 @@ def run_adjoint(args):
     t_fwd, t_bwd = e[0].elapsed_time(e[1]) / 1e3, e[1].elapsed_time(e[2]) / 1e3
     t_vjp = e[3].elapsed_time(e4) / 1e3 / 10
     segs = (steps + ck - 1) // ck
-    forces = 2 * (steps + segs)            # forward sweep + recomputation
+    forces = (steps + 1) + (steps + segs)  # forward sweep + recomputation
     vjps = steps + 1
     pairs = float(n) * (n - 1)
     # FP32 work of one VJP pair term (float-float difference 9, r2 5, rsqrt,

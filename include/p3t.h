@@ -237,6 +237,14 @@ int p3t_neighbours(p3t_ctx *ctx, const p3t_particles *p, int64_t *nb_off,
 int p3t_hard_step(p3t_ctx *ctx, p3t_particles *p, const p3t_clusters *cl,
                   double dt, uint64_t *n_steps, void *stream);
 
+/* Row a9 for every particle -- the Kepler drift of p3t_hard_step applied to
+ * all particles of p by dt (mu = G M_*), with no cluster integrated: the
+ * drift of a rollout whose particles are all treated as isolated (the
+ * row-f2 adjoint's forward map).  Positions and velocities updated in place;
+ * a drift whose Newton iteration does not converge is reported as
+ * P3T_ERR_TIMEOUT by p3t_status. */
+int p3t_kepler_drift(p3t_ctx *ctx, p3t_particles *p, double dt, void *stream);
+
 /* Row a7 -- soft kick (procedure steps 3 and 8): v += a * h, h usually
  * dt_soft / 2.  ax, ay, az: n doubles each, caller order.  Members of a
  * composite formed by the last p3t_hard_step (f_radius > 0) are kicked with

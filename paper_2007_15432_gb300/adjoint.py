@@ -21,8 +21,6 @@ Positions and velocities are (3, n) float64 CUDA tensors (rows x, y, z).
 """
 from __future__ import annotations
 
-import ctypes as C
-
 import torch
 
 from . import p3t as P
@@ -50,16 +48,6 @@ class SoftKDK:
         f64 = dict(dtype=torch.float64, device=self.dev)
         self.acc = torch.zeros(3, self.n, **f64)
         self._rs = torch.zeros(self.n, **f64)
-        # every particle is a single: the hard step is the Kepler drift
-        i32 = dict(dtype=torch.int32, device=self.dev)
-        self._cl_t = dict(label=torch.arange(self.n, **i32),
-                          singles=torch.arange(max(self.n, 1), **i32),
-                          cl_off=torch.zeros(1, dtype=torch.int64, device=self.dev),
-                          cl_mem=torch.zeros(1, **i32),
-                          counts=torch.tensor([self.n, 0, 0, 0], dtype=torch.int64,
-                                              device=self.dev))
-        self.cl = P.Clusters(*[C.c_void_p(self._cl_t[k].data_ptr()) for k in (
-            "label", "singles", "cl_off", "cl_mem", "counts")])
 
     def close(self):
         if self.ctx:
@@ -79,17 +67,19 @@ class SoftKDK:
     def _force(self, st: P.State):
         P.p3t_soft_force_direct(self.ctx, st, self.acc)
 
-    def _run(self, X, V, m, r_out, k0: int, k1: int, keep=None):
+    def _run(self, X, V, m, r_out, k0: int, k1: int, keep=None, have_force=False):
         """Steps k0..k1-1 in place on (X, V); with ``keep`` a list, appends
-        (x_k, v'_k) (positions and velocities after the first kick) per step."""
+        (x_k, v'_k) (positions and velocities after the first kick) per step.
+        ``have_force``: self.acc already holds the force at X."""
         h = 0.5 * self.params.dt_soft
         st = self._state(X, V, m, r_out)
-        self._force(st)
+        if not have_force:
+            self._force(st)
         for _ in range(k0, k1):
             P.p3t_kick(self.ctx, st, self.acc, h)
             if keep is not None:
                 keep.append((X.clone(), V.clone()))
-            P.p3t_hard_step(self.ctx, st, self.cl, self.params.dt_soft)
+            P.p3t_kepler_drift(self.ctx, st, self.params.dt_soft)
             self._force(st)
             P.p3t_kick(self.ctx, st, self.acc, h)
 
@@ -105,7 +95,8 @@ class SoftKDK:
         cps = []
         for k0 in range(0, self.steps, self.checkpoint):
             cps.append((k0, X.clone(), V.clone()))
-            self._run(X, V, m, r_out, k0, min(self.steps, k0 + self.checkpoint))
+            self._run(X, V, m, r_out, k0, min(self.steps, k0 + self.checkpoint),
+                      have_force=k0 > 0)
         return X, V, dict(checkpoints=cps, m=m, r_out=r_out, xN=X.clone(), vN=V.clone())
 
     def backward(self, tape, lam_x, lam_v):

@@ -4,7 +4,8 @@ Each CUDA source is compiled to an object in parallel, then linked into a
 shared library with the CUDA runtime linked statically.  Sources whose
 arithmetic must be bit-identical on every IEEE machine (keys and grid
 geometry, the neighbour predicate, the Hermite block steps) are compiled with
-``-fmad=false``; the tree walk keeps FMA contraction.
+``-fmad=false``; the tree walk keeps FMA contraction; the all-pairs kernels
+flush FP32 subnormals.
 """
 from __future__ import annotations
 
@@ -22,6 +23,9 @@ LIB = os.path.join(HERE, "libp3t.so")
 SOURCES = ["primitives.cu", "tree.cu", "walk.cu", "neighbours.cu", "hard.cu", "ctx.cu",
            "noalloc.cu", "adjoint.cu", "direct.cu"]
 NO_FMA = {"tree.cu", "neighbours.cu", "hard.cu", "ctx.cu", "noalloc.cu"}
+# FP32 subnormals flushed to zero (the all-pairs kernels' FP32 operands are
+# far from 2^-126; rsqrtf then needs no subnormal handling)
+FTZ = {"direct.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -51,6 +55,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
                "-I", INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
         if src in NO_FMA:
             cmd.insert(len(ARCH) + 1, "-fmad=false")
+        if src in FTZ:
+            cmd.insert(len(ARCH) + 1, "-ftz=true")
         if verbose:
             cmd.insert(len(ARCH) + 1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

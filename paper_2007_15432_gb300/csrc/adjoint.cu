@@ -64,39 +64,67 @@ __device__ __forceinline__ D6 dfun(const D6 &a, double f, double df) {
   return r;
 }
 
+// 1 / n! as a double (exact product of the integers up to 18!, then one
+// rounding per factor)
+__host__ __device__ constexpr double inv_fact(int n) {
+  double f = 1.0;
+  for (int i = 2; i <= n; ++i) f *= (double)i;
+  return 1.0 / f;
+}
+
 // Stumpff functions C(z) = (1 - cos sqrt z) / z, S(z) = (sqrt z - sin sqrt z) /
-// z^(3/2) (and their hyperbolic forms for z < 0); for |z| < 1 their series
-// C = sum (-z)^k / (2k+2)!, S = sum (-z)^k / (2k+3)!, 12 terms (truncation
-// below 1e-26)
-__device__ void stumpff_d(const D6 &z, D6 &C, D6 &S) {
-  if (fabs(z.v) < 1.0) {
-    double cc[12], ss[12];
-    double f = 2.0;  // (2k + 2)!
-    for (int k = 0; k < 12; ++k) {
-      if (k > 0) f *= (double)(2 * k + 1) * (double)(2 * k + 2);
-      const double sign = (k & 1) ? -1.0 : 1.0;
-      cc[k] = sign / f;
-      ss[k] = sign / (f * (double)(2 * k + 3));
+// z^(3/2) (hyperbolic forms for z < 0) and their derivatives C', S' as plain
+// numbers.  |z| < 1: the series C = sum (-z)^k / (2k+2)!, S = sum (-z)^k /
+// (2k+3)! and their term-by-term derivatives, NT terms; otherwise the closed
+// forms with C' = (1 - z S - 2C) / (2z), S' = (C - 3S) / (2z).
+template <int NT>
+__device__ __forceinline__ void stumpff_series(double z, double &C, double &S, double &dC,
+                                               double &dS) {
+  const double mz = -z;
+  double c = inv_fact(2 * NT), s_ = inv_fact(2 * NT + 1);
+  double dc_ = (double)(NT - 1) * c, ds_ = (double)(NT - 1) * s_;
+#pragma unroll
+  for (int k = NT - 2; k >= 0; --k) {
+    c = fma(mz, c, inv_fact(2 * k + 2));
+    s_ = fma(mz, s_, inv_fact(2 * k + 3));
+    if (k >= 1) {
+      dc_ = fma(mz, dc_, (double)k * inv_fact(2 * k + 2));
+      ds_ = fma(mz, ds_, (double)k * inv_fact(2 * k + 3));
     }
-    D6 c = dc(cc[11]), s = dc(ss[11]);
-    for (int k = 10; k >= 0; --k) {
-      c = dc(cc[k]) + z * c;
-      s = dc(ss[k]) + z * s;
-    }
-    C = c;
-    S = s;
-  } else if (z.v > 0.0) {
-    const D6 q = dsqrt(z);
-    const D6 cq = dfun(q, cos(q.v), -sin(q.v)), sq = dfun(q, sin(q.v), cos(q.v));
-    C = (dc(1.0) - cq) / z;
-    S = (q - sq) / (z * q);
-  } else {
-    const D6 mz = dc(0.0) - z;
-    const D6 q = dsqrt(mz);
-    const D6 chq = dfun(q, cosh(q.v), sinh(q.v)), shq = dfun(q, sinh(q.v), cosh(q.v));
-    C = (chq - dc(1.0)) / mz;
-    S = (shq - q) / (mz * q);
   }
+  C = c;
+  S = s_;
+  dC = -dc_;
+  dS = -ds_;
+}
+
+__device__ void stumpff4(double z, double &C, double &S, double &dC, double &dS) {
+  if (fabs(z) < 0.01) {
+    stumpff_series<6>(z, C, S, dC, dS);  // truncation below |z|^6 / 14! ~ 1e-23
+  } else if (fabs(z) < 1.0) {
+    stumpff_series<12>(z, C, S, dC, dS);  // below 1 / 26! ~ 2.5e-27
+  } else {
+    if (z > 0.0) {
+      const double q = sqrt(z);
+      C = (1.0 - cos(q)) / z;
+      S = (q - sin(q)) / (z * q);
+    } else {
+      const double q = sqrt(-z);
+      C = (cosh(q) - 1.0) / (-z);
+      S = (sinh(q) - q) / (-z * q);
+    }
+    const double i2z = 0.5 / z;
+    dC = (1.0 - z * S - 2.0 * C) * i2z;
+    dS = (C - 3.0 * S) * i2z;
+  }
+}
+
+// C and S of a dual argument: values at z.v, derivatives by the chain rule
+__device__ __forceinline__ void stumpff_d(const D6 &z, D6 &C, D6 &S) {
+  double c, s_, dc_, ds_;
+  stumpff4(z.v, c, s_, dc_, ds_);
+  C = dfun(z, c, dc_);
+  S = dfun(z, s_, ds_);
 }
 
 // the universal anomaly (values only), Newton from the series inversion
@@ -108,12 +136,11 @@ __device__ double chi_solve(double r0, double sig, double bet, double alpha, dou
   if (alpha > 0.0 && 16.0 * dt * dt * alpha * alpha * alpha * mu > 4.0 * 9.869604401089358)
     chi = tau * alpha;
   for (int it = 0; it < 64; ++it) {
-    const D6 zd = dc(alpha * chi * chi);
-    D6 C, S;
-    stumpff_d(zd, C, S);
-    const double z = zd.v, chi2 = chi * chi;
-    const double F = sig * chi2 * C.v + bet * chi2 * chi * S.v + r0 * chi - tau;
-    const double Fp = sig * chi * (1.0 - z * S.v) + bet * chi2 * C.v + r0;
+    const double z = alpha * chi * chi, chi2 = chi * chi;
+    double C, S, dC, dS;
+    stumpff4(z, C, S, dC, dS);
+    const double F = sig * chi2 * C + bet * chi2 * chi * S + r0 * chi - tau;
+    const double Fp = sig * chi * (1.0 - z * S) + bet * chi2 * C + r0;
     double d = F / Fp;
     const double lim = 0.5 * (fabs(chi) + r0);
     d = d > lim ? lim : (d < -lim ? -lim : d);

@@ -205,7 +205,7 @@ void p3t_destroy(p3t_ctx *c) {
   dfree(c->coll_ctr);
   dfree(c->scan_part);
   dfree(c->bh_table);
-  dfree(c->dpart);
+  dfree(c->dpart); dfree(c->dcnt);
   for (int q = 0; q < 2; ++q) {
     if (c->aux[q]) cudaStreamDestroy(c->aux[q]);
     if (c->ev_join[q]) cudaEventDestroy(c->ev_join[q]);
@@ -328,14 +328,25 @@ int p3t_merge(p3t_ctx *c, p3t_particles *p, int32_t *new_index, double *e_disp,
   return rc;
 }
 
-// the all-pairs kernels' partial sums: one allocation of fixed size, made on
-// the first call (so a graph captured after one eager call allocates nothing)
-static int direct_scratch(p3t_ctx *c) {
+// the all-pairs kernels' scratch: the packed particles in hw (sized by
+// ensure) and the partial sums, one allocation of fixed size made on the
+// first call (a graph captured after one eager call allocates nothing)
+static int direct_scratch(p3t_ctx *c, int64_t n) {
+  int rc = ensure(c, n);  // hw holds the packed particles
+  if (rc) return rc;
   if (c->dpart) return P3T_OK;
-  const int64_t want = p3t_direct_part_doubles(c);
-  if (!dalloc(c->dpart, want)) return P3T_ERR_CUDA;
+  const int64_t want = p3t_direct_part_doubles(c), tiles = p3t_direct_tile_counters(c);
+  if (!dalloc(c->dpart, want) || !dalloc(c->dcnt, tiles)) return P3T_ERR_CUDA;
+  if (cudaMemset(c->dcnt, 0, sizeof(int32_t) * tiles) != cudaSuccess) return P3T_ERR_CUDA;
   c->dpart_cap = want;
+  c->dcnt_cap = tiles;
   return P3T_OK;
+}
+
+int p3t_kepler_drift(p3t_ctx *c, p3t_particles *p, double dt, void *stream) {
+  if (!c || !particles_ok(p)) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  return p3t_run_kepler_drift(c, p, dt, (cudaStream_t)stream);
 }
 
 int p3t_soft_force_direct(p3t_ctx *c, const p3t_particles *p, double *ax, double *ay,
@@ -343,7 +354,7 @@ int p3t_soft_force_direct(p3t_ctx *c, const p3t_particles *p, double *ax, double
   if (!c || !particles_ok(p)) return P3T_ERR_INVALID;
   if (p->n > 0 && (!ax || !ay || !az)) return P3T_ERR_INVALID;
   DeviceGuard g(c->device);
-  int rc = direct_scratch(c);
+  int rc = direct_scratch(c, p->n);
   if (rc) return rc;
   return p3t_run_soft_force_direct(c, p, ax, ay, az, (cudaStream_t)stream);
 }
@@ -354,7 +365,7 @@ int p3t_soft_force_vjp(p3t_ctx *c, const p3t_particles *p, double h, const doubl
   if (!c || !particles_ok(p)) return P3T_ERR_INVALID;
   if (p->n > 0 && (!lx || !ly || !lz || !gx || !gy || !gz || !gm)) return P3T_ERR_INVALID;
   DeviceGuard g(c->device);
-  int rc = direct_scratch(c);
+  int rc = direct_scratch(c, p->n);
   if (rc) return rc;
   return p3t_run_soft_force_vjp(c, p, h, lx, ly, lz, gx, gy, gz, gm, (cudaStream_t)stream);
 }

@@ -4,14 +4,15 @@
 //   g_k += s sum_j J(r_kj) (m_k lam_j - m_j lam_k),  gm_k += s sum_j phi_kj lam_j . r_kj,
 // J = phi I + psi r r^T, phi = K / r^3, psi = K'(y) / (r_out r^4) - 3 K / r^5.
 //
-// Layout: a block is 8 warps over 64 targets (two per lane); the warps take
-// interleaved 32-source chunks of the block's source range and stage each
-// chunk in their own shared-memory slots as packed 4-vectors (one broadcast
-// load per vector, shared by the lane's two targets).  A grid column
-// (blockIdx.y) is one split of the sources; each block writes its per-target
-// sums to part[(split * C + c) * n + k] after adding its 8 warps in order,
-// and k_direct_sum adds the splits in order: the result does not depend on
-// scheduling.
+// Layout: k_direct_pack writes every particle once as packed 4-vectors in
+// the pair arithmetic's type; a block is 8 warps over 64 targets (two per
+// lane); each warp takes one eighth of the block's source range and stages
+// it 32 sources at a time in its own shared-memory slots (one broadcast load
+// per 4-vector, shared by the lane's two targets).  A grid column
+// (blockIdx.y) is one split of the sources; each block adds its 8 warps in
+// order and writes its per-target sums to part[(split * C + c) * n + k];
+// the last block of a target tile to finish adds the splits in order: the
+// result does not depend on scheduling.
 //
 // Precision: FP64 throughout, or (MIXED) float-float positions whose
 // difference (hi_k - hi_j) + (lo_k - lo_j) carries the relative coordinate
@@ -27,6 +28,9 @@ namespace {
 constexpr int kDW = 8;          // warps per block
 constexpr int kDT = 2;          // targets per lane
 constexpr int kDTB = 32 * kDT;  // targets per block
+#ifndef P3T_DIRECT_MINB_MIXED
+#define P3T_DIRECT_MINB_MIXED 3  // resident blocks per SM asked of the FP32 kernels
+#endif
 
 template <typename T>
 struct alignas(4 * sizeof(T)) Q4 {
@@ -59,11 +63,12 @@ __device__ __forceinline__ void pair_term(T rx, T ry, T rz, const Q4<T> &A, T ir
                                           const Q4<T> &L, T mk, T irok, T lxk, T lyk, T lzk,
                                           T g, T i1mg, T *acc) {
   const T r2 = rx * rx + ry * ry + rz * rz;
-  if (r2 == (T)0) return;  // the target itself
   const T ir = rsq(r2);
   const T irout = irok < iroj ? irok : iroj;  // 1 / max(r_out,k, r_out,j)
   const T yv = r2 * ir * irout;
-  if (yv <= g) return;  // K = K' = 0
+  // y <= gamma: K = K' = 0.  The target itself (r2 = 0) gives 0 * inf = NaN
+  // and leaves here too.
+  if (!(yv > g)) return;
   T K = 1, dKr = 0;     // K(y) and K'(y) / r_out
   if (yv < (T)1) {
     const T u = (yv - g) * i1mg, u2 = u * u, u3 = u2 * u;
@@ -99,11 +104,44 @@ struct DOut {
   int add;
 };
 
+// Packs every particle once per call: A = (x_hi, y_hi, z_hi, m), B = (x_lo,
+// y_lo, z_lo, 1 / r_out), L = (lam, 0), in the pair arithmetic's type (the
+// lo parts are zero in FP64), so that no conversion or FP64 division is
+// repeated per block.
 template <bool MIXED, bool VJP>
-__global__ void __launch_bounds__(kDW * 32, MIXED ? 3 : 1)
-    k_direct(int64_t n, int64_t chunk, const double *x, const double *y, const double *z,
-             const double *m, const double *ro, const double *lx, const double *ly,
-             const double *lz, double gamma, double *part, DOut out) {
+__global__ void k_direct_pack(int64_t n, const double *x, const double *y, const double *z,
+                              const double *m, const double *ro, const double *lx,
+                              const double *ly, const double *lz,
+                              Q4<typename DT<MIXED>::T> *A, Q4<typename DT<MIXED>::T> *B,
+                              Q4<typename DT<MIXED>::T> *L) {
+  using T = typename DT<MIXED>::T;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    Q4<T> a, b;
+    a.x = (T)x[j]; a.y = (T)y[j]; a.z = (T)z[j]; a.w = (T)m[j];
+    b.x = b.y = b.z = 0;
+    if constexpr (MIXED) {
+      b.x = (T)(x[j] - (double)a.x);
+      b.y = (T)(y[j] - (double)a.y);
+      b.z = (T)(z[j] - (double)a.z);
+    }
+    b.w = (T)(1.0 / ro[j]);
+    A[j] = a;
+    B[j] = b;
+    if constexpr (VJP) {
+      Q4<T> l;
+      l.x = (T)lx[j]; l.y = (T)ly[j]; l.z = (T)lz[j]; l.w = 0;
+      L[j] = l;
+    }
+  }
+}
+
+template <bool MIXED, bool VJP>
+__global__ void __launch_bounds__(kDW * 32, MIXED ? P3T_DIRECT_MINB_MIXED : 1)
+    k_direct(int64_t n, int64_t chunk, const Q4<typename DT<MIXED>::T> *__restrict__ PA,
+             const Q4<typename DT<MIXED>::T> *__restrict__ PB,
+             const Q4<typename DT<MIXED>::T> *__restrict__ PL, double gamma, double *part,
+             int32_t *tile_cnt, DOut out) {
   using T = typename DT<MIXED>::T;
   constexpr int NC = VJP ? 4 : 3;
   __shared__ Q4<T> sA[kDW][32];                     // x_hi, y_hi, z_hi, m
@@ -121,16 +159,12 @@ __global__ void __launch_bounds__(kDW * 32, MIXED ? 3 : 1)
     txh[t] = tyh[t] = tzh[t] = txl[t] = tyl[t] = tzl[t] = 0;
     tm[t] = tiro[t] = tlx[t] = tly[t] = tlz[t] = 0;  // 1/r_out = 0: no pair term
     if (k < n) {
-      txh[t] = (T)x[k]; tyh[t] = (T)y[k]; tzh[t] = (T)z[k];
-      if constexpr (MIXED) {
-        txl[t] = (T)(x[k] - (double)txh[t]);
-        tyl[t] = (T)(y[k] - (double)tyh[t]);
-        tzl[t] = (T)(z[k] - (double)tzh[t]);
-      }
-      tm[t] = (T)m[k];
-      tiro[t] = (T)(1.0 / ro[k]);
+      const Q4<T> a = PA[k], b = PB[k];
+      txh[t] = a.x; tyh[t] = a.y; tzh[t] = a.z; tm[t] = a.w;
+      txl[t] = b.x; tyl[t] = b.y; tzl[t] = b.z; tiro[t] = b.w;
       if constexpr (VJP) {
-        tlx[t] = (T)lx[k]; tly[t] = (T)ly[k]; tlz[t] = (T)lz[k];
+        const Q4<T> l = PL[k];
+        tlx[t] = l.x; tly[t] = l.y; tlz[t] = l.z;
       }
     }
   }
@@ -141,29 +175,20 @@ __global__ void __launch_bounds__(kDW * 32, MIXED ? 3 : 1)
 #pragma unroll
     for (int c = 0; c < NC; ++c) fh[t][c] = fl[t][c] = 0.0f, dd[t][c] = 0.0;
 
-  const int64_t s_lo = (int64_t)blockIdx.y * chunk;
-  const int64_t s_hi = min(n, s_lo + chunk);
-  for (int64_t cb = s_lo + (int64_t)warp * 32; cb < s_hi; cb += kDW * 32) {
+  // the split's sources, cut into 8 contiguous, equal (to one source) warp
+  // ranges, walked in chunks of 32
+  const int64_t b_lo = (int64_t)blockIdx.y * chunk;
+  const int64_t b_len = max((int64_t)0, min(n, b_lo + chunk) - b_lo);
+  const int64_t s_lo = b_lo + b_len * warp / kDW;
+  const int64_t s_hi = b_lo + b_len * (warp + 1) / kDW;
+  for (int64_t cb = s_lo; cb < s_hi; cb += 32) {
     const int lim = (int)min((int64_t)32, s_hi - cb);
     __syncwarp();
     if (lane < lim) {
       const int64_t j = cb + lane;
-      Q4<T> A, B;
-      A.x = (T)x[j]; A.y = (T)y[j]; A.z = (T)z[j]; A.w = (T)m[j];
-      B.x = B.y = B.z = 0;
-      if constexpr (MIXED) {
-        B.x = (T)(x[j] - (double)A.x);
-        B.y = (T)(y[j] - (double)A.y);
-        B.z = (T)(z[j] - (double)A.z);
-      }
-      B.w = (T)(1.0 / ro[j]);
-      sA[warp][lane] = A;
-      sB[warp][lane] = B;
-      if constexpr (VJP) {
-        Q4<T> L;
-        L.x = (T)lx[j]; L.y = (T)ly[j]; L.z = (T)lz[j]; L.w = 0;
-        sL[warp][lane] = L;
-      }
+      sA[warp][lane] = PA[j];
+      sB[warp][lane] = PB[j];
+      if constexpr (VJP) sL[warp][lane] = PL[j];
     }
     __syncwarp();
     T acc[kDT][NC];
@@ -171,6 +196,7 @@ __global__ void __launch_bounds__(kDW * 32, MIXED ? 3 : 1)
     for (int t = 0; t < kDT; ++t)
 #pragma unroll
       for (int c = 0; c < NC; ++c) acc[t][c] = 0;
+#pragma unroll 4
     for (int q = 0; q < lim; ++q) {
       const Q4<T> A = sA[warp][q], B = sB[warp][q];
       Q4<T> L{0, 0, 0, 0};
@@ -215,22 +241,28 @@ __global__ void __launch_bounds__(kDW * 32, MIXED ? 3 : 1)
       part[((int64_t)blockIdx.y * NC + c) * n + k] = s;
     }
   }
-}
-
-// out_c[k] = (add ? out_c[k] : 0) + scale * sum over splits of part (in order)
-__global__ void k_direct_sum(int64_t n, int nsplit, int nc, const double *part, double scale,
-                             int add, double *o0, double *o1, double *o2, double *o3) {
-  double *out[4] = {o0, o1, o2, o3};
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      if (c >= nc) break;
-      double a = 0.0;
-      for (int s = 0; s < nsplit; ++s) a += part[((int64_t)s * nc + c) * n + k];
-      out[c][k] = (add ? out[c][k] : 0.0) + scale * a;
-    }
+  if (gridDim.y == 1) return;
+  // several splits: the last block of this target tile to arrive adds the
+  // splits' sums in split order (the result does not depend on which block
+  // that is) and resets the tile's counter for the next call
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&tile_cnt[blockIdx.x], 1) == (int)gridDim.y - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int e = threadIdx.x; e < NC * kDTB; e += kDW * 32) {
+    const int c = e / kDTB, tt = e - c * kDTB;
+    const int64_t k = (int64_t)blockIdx.x * kDTB + tt;
+    if (k >= n) continue;
+    double s = 0.0;
+#pragma unroll 8
+    for (int q = 0; q < (int)gridDim.y; ++q) s += __ldcg(&part[((int64_t)q * NC + c) * n + k]);
+    double *o = c == 0 ? out.o[0] : (c == 1 ? out.o[1] : (c == 2 ? out.o[2] : out.o[3]));
+    o[k] = (out.add ? o[k] : 0.0) + out.scale * s;
   }
+  if (threadIdx.x == 0) tile_cnt[blockIdx.x] = 0;
 }
 
 // Work split: blocks of 64 targets x one source split.  With fewer than 8
@@ -286,16 +318,16 @@ int launch_direct(p3t_ctx *c, const p3t_particles *p, const double *lx, const do
   const int64_t n = p->n;
   const Split sp = split_for(c, n, blocks_per_sm<MIXED, VJP>());
   if (sp.nsplit > 1 && (int64_t)NC * sp.nsplit * n > c->dpart_cap) return P3T_ERR_CAPACITY;
+  using T = typename DT<MIXED>::T;
+  Q4<T> *A = reinterpret_cast<Q4<T> *>(c->hw);  // 3 n packed 4-vectors <= 96 n bytes
+  Q4<T> *B = A + n, *L = B + n;
+  k_direct_pack<MIXED, VJP><<<(unsigned)p3t_grid(n, 256, (int64_t)c->num_sms * 4), 256, 0, s>>>(
+      n, p->x, p->y, p->z, p->m, p->r_out, lx, ly, lz, A, B, L);
+  if (sp.nsplit > 1 && sp.tiles > c->dcnt_cap) return P3T_ERR_CAPACITY;
   const dim3 grid((unsigned)sp.tiles, (unsigned)sp.nsplit);
-  k_direct<MIXED, VJP><<<grid, kDW * 32, 0, s>>>(n, sp.chunk, p->x, p->y, p->z, p->m, p->r_out,
-                                                lx, ly, lz, c->prm.gamma, c->dpart, out);
-  int launches = 1;
-  if (sp.nsplit > 1) {
-    k_direct_sum<<<(unsigned)p3t_grid(n, 256, (int64_t)c->num_sms * 4), 256, 0, s>>>(
-        n, sp.nsplit, NC, c->dpart, out.scale, out.add, out.o[0], out.o[1], out.o[2], out.o[3]);
-    ++launches;
-  }
-  p3t_note_launches(launches);
+  k_direct<MIXED, VJP><<<grid, kDW * 32, 0, s>>>(n, sp.chunk, A, B, L, c->prm.gamma, c->dpart,
+                                                c->dcnt, out);
+  p3t_note_launches(2);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 
@@ -303,6 +335,11 @@ int launch_direct(p3t_ctx *c, const p3t_particles *p, const double *lx, const do
 
 int64_t p3t_direct_part_doubles(const p3t_ctx *c) {
   return (int64_t)4 * 2 * 8 * c->num_sms * max_blocks_per_sm() * kDTB;
+}
+
+// with several splits there are fewer than 8 slots target tiles
+int64_t p3t_direct_tile_counters(const p3t_ctx *c) {
+  return (int64_t)8 * c->num_sms * max_blocks_per_sm();
 }
 
 int p3t_run_soft_force_direct(p3t_ctx *c, const p3t_particles *p, double *ax, double *ay,

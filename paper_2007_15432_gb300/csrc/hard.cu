@@ -178,6 +178,17 @@ __global__ void k_kepler(const int64_t *d_nsingle, const int32_t *singles,
   }
 }
 
+// every particle of p (p3t_kepler_drift)
+__global__ void k_kepler_all(p3t_particles p, double dt, KepConst K, DevStatus *st) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double X[3] = {p.x[i], p.y[i], p.z[i]}, V[3] = {p.vx[i], p.vy[i], p.vz[i]};
+    if (!kepler_uv(X, V, dt, K)) dev_fail(st, P3T_ERR_TIMEOUT, 60, 0);
+    p.x[i] = X[0]; p.y[i] = X[1]; p.z[i] = X[2];
+    p.vx[i] = V[0]; p.vy[i] = V[1]; p.vz[i] = V[2];
+  }
+}
+
 // ---- row a8 (+ f4): Hermite-4 with block steps, one block per cluster ------
 // Clusters of up to 32 members (nearly all) run one warp each, so that the
 // FP64 instructions of their few work items are not spread over idle lanes
@@ -1039,6 +1050,19 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
   P3T_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[0], 0));
   P3T_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[1], 0));
   p3t_note_launches(6);
+  return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
+}
+
+int p3t_run_kepler_drift(p3t_ctx *c, p3t_particles *p, double dt, cudaStream_t s) {
+  if (p->n == 0) return P3T_OK;
+  KepConst kc;
+  kc.mu = c->prm.G * c->prm.m_star;
+  kc.sq = sqrt(kc.mu);
+  kc.isq = 1.0 / kc.sq;
+  kc.imu = 1.0 / kc.mu;
+  k_kepler_all<<<(unsigned)p3t_grid(p->n, 128, (int64_t)c->num_sms * P3T_NSM_BLOCKS), 128, 0,
+                 s>>>(*p, dt, kc, c->status);
+  p3t_note_launches(1);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 

@@ -70,6 +70,8 @@ struct p3t_ctx {
   int64_t walk_warps = 0; // resident warps of the walk kernel
   double *dpart = nullptr; // partial sums of the all-pairs kernels (allocated
   int64_t dpart_cap = 0;   //   on their first call; size independent of n)
+  int32_t *dcnt = nullptr; // their per-tile arrival counters (zero between calls)
+  int64_t dcnt_cap = 0;
   int64_t stack_cap = 0;  // walk stack entries per warp
   int64_t last_n = -1;    // n of the last tree build
   bool have_tree = false;
@@ -209,6 +211,8 @@ int p3t_run_energy(p3t_ctx *c, const p3t_particles *p, double *out,
 int p3t_run_merge(p3t_ctx *c, p3t_particles *p, int32_t *new_index, double *e_disp,
                   int64_t *n_merged, cudaStream_t s);
 int64_t p3t_direct_part_doubles(const p3t_ctx *c);
+int64_t p3t_direct_tile_counters(const p3t_ctx *c);
+int p3t_run_kepler_drift(p3t_ctx *c, p3t_particles *p, double dt, cudaStream_t s);
 int p3t_run_soft_force_direct(p3t_ctx *c, const p3t_particles *p, double *ax, double *ay,
                               double *az, cudaStream_t s);
 int p3t_run_soft_force_vjp(p3t_ctx *c, const p3t_particles *p, double h, const double *lx,

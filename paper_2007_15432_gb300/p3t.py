@@ -81,6 +81,7 @@ _sig = {
                                  C.POINTER(Clusters), _vp]),
     "p3t_hard_step": (C.c_int, [_CTX, C.POINTER(Particles), C.POINTER(Clusters), C.c_double,
                                 _vp, _vp]),
+    "p3t_kepler_drift": (C.c_int, [_CTX, C.POINTER(Particles), C.c_double, _vp]),
     "p3t_kick": (C.c_int, [_CTX, C.POINTER(Particles), _vp, _vp, _vp, C.c_double, _vp]),
     "p3t_energy": (C.c_int, [_CTX, C.POINTER(Particles), _vp, _vp]),
     "p3t_merge": (C.c_int, [_CTX, C.POINTER(Particles), _vp, C.POINTER(C.c_double),
@@ -241,6 +242,13 @@ def p3t_hard_step(ctx, st: State, cl: Clusters, dt: float, n_steps: torch.Tensor
     p = st.particles()
     _check(_lib.p3t_hard_step(ctx, C.byref(p), C.byref(cl), float(dt), _ptr(n_steps),
                               _stream(stream)), "p3t_hard_step")
+
+
+def p3t_kepler_drift(ctx, st: State, dt: float, stream=None) -> None:
+    """Every particle on its Kepler orbit about the star by dt (row a9 for all)."""
+    p = st.particles()
+    _check(_lib.p3t_kepler_drift(ctx, C.byref(p), float(dt), _stream(stream)),
+           "p3t_kepler_drift")
 
 
 def p3t_kick(ctx, st: State, acc: torch.Tensor, h: float, stream=None) -> None:

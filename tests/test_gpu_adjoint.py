@@ -141,6 +141,39 @@ def test_kepler_vjp_matches_oracle(mods, dt):
     assert np.array_equal(X.cpu().numpy(), x) and np.array_equal(V.cpu().numpy(), v)
 
 
+def test_kepler_drift_all_matches_oracle_and_hard_step(mods):
+    """p3t_kepler_drift: row a9's drift for every particle, the same bits as
+    p3t_hard_step with every particle single, and the oracle's drift."""
+    AD, P = mods
+    from oracle import oracle as O
+    s = disks.disk(3000, 0.5, 2.0, 0.3, 0.1, 1e-10, 23)
+    dt = 0.3
+    ref = {k: s[k].copy() for k in s}
+    O.kepler_drift(ref, dt, 1.0)
+    st = P.State.from_numpy(s, device="cuda")
+    st2 = P.State.from_numpy(s, device="cuda")
+    n = len(s["m"])
+    ctx = P.p3t_create(P.Params(), 0)
+    try:
+        P.p3t_kepler_drift(ctx, st, dt)
+        i32 = dict(dtype=torch.int32, device="cuda")
+        t = dict(label=torch.arange(n, **i32), singles=torch.arange(n, **i32),
+                 cl_off=torch.zeros(1, dtype=torch.int64, device="cuda"),
+                 cl_mem=torch.zeros(1, **i32),
+                 counts=torch.tensor([n, 0, 0, 0], dtype=torch.int64, device="cuda"))
+        cl = P.Clusters(*[t[k].data_ptr() for k in ("label", "singles", "cl_off", "cl_mem",
+                                                    "counts")])
+        P.p3t_hard_step(ctx, st2, cl, dt)
+        torch.cuda.synchronize()
+        assert P.p3t_status(ctx)[0] == 0
+    finally:
+        P.p3t_destroy(ctx)
+    a, b = st.numpy(), st2.numpy()
+    for k in ("x", "y", "z", "vx", "vy", "vz"):
+        assert np.array_equal(a[k], b[k])
+        assert np.max(np.abs(a[k] - ref[k])) <= 1e-12
+
+
 @pytest.mark.parametrize("steps,checkpoint", [(12, 5), (6, 8)])
 def test_rollout_gradient_matches_oracle(mods, steps, checkpoint):
     AD, P = mods
@@ -168,7 +201,7 @@ def test_rollout_gradient_matches_oracle(mods, steps, checkpoint):
         run.status()
     finally:
         run.close()
-    assert abs(float(loss) - float(L)) <= 1e-9 * float(L)
+    assert abs(float(loss.detach()) - float(L)) <= 1e-9 * float(L)
     for g, e in ((X0.grad, egx.numpy().T), (V0.grad, egv.numpy().T), (M.grad, egm.numpy())):
         g = g.cpu().numpy()
         assert np.max(np.abs(g - e)) <= 1e-9 * np.max(np.abs(e))

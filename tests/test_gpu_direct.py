@@ -28,9 +28,13 @@ def _direct(P3T, s, P, ro, rs):
     try:
         acc = torch.full((3, len(s["m"])), np.nan, dtype=torch.float64, device="cuda")
         P3T.p3t_soft_force_direct(ctx, st, acc)
+        # a second call in the same context (split counters reset) gives the same bits
+        acc2 = torch.full((3, len(s["m"])), np.nan, dtype=torch.float64, device="cuda")
+        P3T.p3t_soft_force_direct(ctx, st, acc2)
         torch.cuda.synchronize()
         rc, req = P3T.p3t_status(ctx)
         assert rc == 0, (rc, req)
+        assert torch.equal(acc, acc2)
         return acc.cpu().numpy().T
     finally:
         P3T.p3t_destroy(ctx)
