@@ -413,7 +413,7 @@ def run_ours(args):
         phases_ms=dict(kick_and_hard=phase[0], tree=phase[1], soft_force=phase[2],
                        neighbours_clusters=phase[3], kick=phase[4],
                        merge_and_recompute=phase[5]),
-        roofline=dict(kernel="k_walk (mixed) + FP64 refinement", bound="alu",
+        roofline=dict(kernel="k_walk (mixed) + float-float refinement", bound="alu",
                       achieved=achieved, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
                       frac=achieved / FP32_PEAK_TFLOPS,
                       traffic=WALK_TRAFFIC_1E6 if (args.n == 1_000_000 and args.group_size == 64)

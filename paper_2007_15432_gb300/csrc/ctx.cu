@@ -67,7 +67,7 @@ void free_particle_buffers(p3t_ctx *c) {
   dfree(c->keys); dfree(c->keys_alt); dfree(c->idx); dfree(c->idx_alt);
   dfree(c->radix_hist);
   dfree(c->sx); dfree(c->sy); dfree(c->sz); dfree(c->sm); dfree(c->sro); dfree(c->srs);
-  dfree(c->sq); dfree(c->spA); dfree(c->spB); dfree(c->srs32);
+  dfree(c->sq); dfree(c->spA); dfree(c->spB); dfree(c->srs32); dfree(c->sml);
   dfree(c->lp); dfree(c->lv); dfree(c->wlcp); dfree(c->ncount); dfree(c->nstart);
   dfree(c->pre_first); dfree(c->pre_count); dfree(c->pre_level);
   dfree(c->lvl_keys); dfree(c->lvl_keys_alt); dfree(c->bfs2pre); dfree(c->bfs2pre_alt);
@@ -111,7 +111,8 @@ int reserve(p3t_ctx *c, int64_t n, int64_t cand_cap) {
   ok &= dalloc(c->radix_hist, c->radix_hist_cap);
   ok &= dalloc(c->sx, N) && dalloc(c->sy, N) && dalloc(c->sz, N) && dalloc(c->sm, N);
   ok &= dalloc(c->sro, N) && dalloc(c->srs, N) && dalloc(c->sq, 3 * N);
-  ok &= dalloc(c->spA, N) && dalloc(c->spB, N) && dalloc(c->srs32, N);
+  ok &= dalloc(c->spA, N) && dalloc(c->spB, N) && dalloc(c->srs32, N) &&
+        dalloc(c->sml, N);
   ok &= dalloc(c->lp, N) && dalloc(c->lv, N) && dalloc(c->wlcp, N) && dalloc(c->ncount, N);
   ok &= dalloc(c->nstart, N);
   ok &= dalloc(c->pre_first, NC) && dalloc(c->pre_count, NC) && dalloc(c->pre_level, NC);

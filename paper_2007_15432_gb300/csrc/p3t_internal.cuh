@@ -54,7 +54,7 @@ struct __align__(16) Mom64 {
 // the same for the mixed path: centre of mass as float-float, Q in FP32
 struct __align__(16) Mom32 {
   float4 hi;  // cx_hi, cy_hi, cz_hi, M
-  float4 lo;  // cx_lo, cy_lo, cz_lo, 0
+  float4 lo;  // cx_lo, cy_lo, cz_lo, M - (float)M
   float4 q0;  // qxx, qyy, qzz, qxy
   float4 q1;  // qxz, qyz, 0, 0
 };
@@ -96,6 +96,7 @@ struct p3t_ctx {
   int32_t *sq = nullptr;                   // 3 * cap quantised coordinates
   float4 *spA = nullptr, *spB = nullptr;   // {x_hi,y_hi,z_hi,m}, {x_lo,y_lo,z_lo,1/r_out}
   float *srs32 = nullptr;                  // r_search^2 x 1.00001 in FP32 (walk's candidate test)
+  float *sml = nullptr;                    // m - (float)m: the mass as float-float with spA.w
 
   // tree build scratch (per particle)
   int8_t *lp = nullptr, *lv = nullptr;     // lcp with predecessor, leaf level

@@ -256,7 +256,7 @@ __global__ void k_gather(int64_t n, const int32_t *idx, const uint64_t *keys,
                          const double *m, const double *ro, const double *rs,
                          double *sx, double *sy, double *sz, double *sm,
                          double *sro, double *srs, int32_t *sq, float4 *spA,
-                         float4 *spB, float *srs32) {
+                         float4 *spB, float *srs32, float *sml) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
        s += (int64_t)gridDim.x * blockDim.x) {
     const int32_t i = idx[s];
@@ -267,7 +267,9 @@ __global__ void k_gather(int64_t n, const int32_t *idx, const uint64_t *keys,
     sq[3 * s + 1] = (int32_t)compact3(k >> 1);
     sq[3 * s + 2] = (int32_t)compact3(k);
     const float xh = (float)X, yh = (float)Y, zh = (float)Z;
-    spA[s] = make_float4(xh, yh, zh, (float)M);
+    const float mh = (float)M;
+    spA[s] = make_float4(xh, yh, zh, mh);
+    sml[s] = (float)(M - (double)mh);
     spB[s] = make_float4((float)(X - (double)xh), (float)(Y - (double)yh),
                          (float)(Z - (double)zh), 1.0f / (float)RO);  // FP32 path only
     srs32[s] = (float)(RS * RS) * 1.00001f;  // walk's candidate test: r^2 vs r_search^2, widened
@@ -459,9 +461,10 @@ __device__ __forceinline__ void finish_node(TreeNode *nd, Mom64 *m64, Mom32 *m32
   m64[b] = mm;
   Mom32 f;
   const float hx = (float)mm.cx, hy = (float)mm.cy, hz = (float)mm.cz;
-  f.hi = make_float4(hx, hy, hz, (float)mm.M);
+  const float mh = (float)mm.M;
+  f.hi = make_float4(hx, hy, hz, mh);
   f.lo = make_float4((float)(mm.cx - (double)hx), (float)(mm.cy - (double)hy),
-                     (float)(mm.cz - (double)hz), 0.f);
+                     (float)(mm.cz - (double)hz), (float)(mm.M - (double)mh));
   f.q0 = make_float4((float)mm.qxx, (float)mm.qyy, (float)mm.qzz, (float)mm.qxy);
   f.q1 = make_float4((float)mm.qxz, (float)mm.qyz, 0.f, 0.f);
   m32[b] = f;
@@ -667,7 +670,7 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   k_gather<<<(unsigned)g, kBlock, 0, s>>>(n, c->idx, c->keys, p->x, p->y, p->z, p->m,
                                           p->r_out, p->r_search, c->sx, c->sy, c->sz,
                                           c->sm, c->sro, c->srs, c->sq, c->spA, c->spB,
-                                          c->srs32);
+                                          c->srs32, c->sml);
   k_lcp<<<(unsigned)g, kBlock, 0, s>>>(n, c->keys, leaf, c->wlcp, c->lp);
   k_levels<<<(unsigned)g, kBlock, 0, s>>>(n, leaf, c->wlcp, c->lp, c->lv, c->ncount);
   rc = p3t_scan_i32_to_i64(c->ncount, c->nstart, &cnt[0], c->cap, &cnt[1], c->scan_part, s);

@@ -37,6 +37,7 @@ struct WalkArgs {
   const double *sx, *sy, *sz, *sm, *sro, *srs;
   const float4 *spA, *spB;
   const float *srs32;
+  const float *sml;          // mass lo parts (float-float masses with spA.w)
   const int32_t *idx;        // sorted -> caller
   double *ax, *ay, *az;      // caller order
   int32_t *stack;
@@ -515,42 +516,105 @@ template <bool MIXED> struct GroupEval {
   __device__ void pp(const int32_t *list, int n) { eval_pp(a, t, list, n, stage, npp); }
 };
 
-// one target, all 32 lanes, FP64 (the refinement of ill-conditioned targets)
+// ---- float-float arithmetic (pairs hi + lo of floats, ~2^-44 relative) ------
+// Dekker's and Knuth's error-free transformations with fmaf for the product
+// error: FP32 instructions only, which on this part cost 1/64 of an FP64 one.
+struct FF {
+  float h, l;
+};
+__device__ __forceinline__ FF ff_fast(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  const float e = (a.h - (s - bb)) + (b.h - bb) + (a.l + b.l);
+  return ff_fast(s, e);
+}
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+  return ff_fast(p, e);
+}
+__device__ __forceinline__ FF ff_mulf(FF a, float b) {
+  const float p = a.h * b;
+  const float e = fmaf(a.l, b, fmaf(a.h, b, -p));
+  return ff_fast(p, e);
+}
+// 1 / sqrt(r2): the FP32 estimate and one Newton step y (3 - r2 y^2) / 2 with
+// the residual 1 - r2 y^2 formed in float-float
+__device__ __forceinline__ FF ff_rsqrt(FF r2) {
+  const float y = rsqrtf(r2.h);
+  const float p = y * y;
+  const FF yy{p, fmaf(y, y, -p)};
+  const FF t = ff_mul(r2, yy);
+  const float d = ((1.0f - t.h) - t.l);
+  return ff_fast(y, 0.5f * y * d);
+}
+__device__ __forceinline__ FF ff_shfl_xor(FF a, int o) {
+  return {__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o)};
+}
+
+// one target, all 32 lanes, float-float (the refinement of ill-conditioned
+// targets): relative coordinates, r^2, 1/r, masses, monopoles and the sums in
+// float-float (terms to ~1e-13 of themselves); the changeover factor K and
+// the quadrupole correction in FP32 (exact K = 1 beyond r_out)
 struct RefineEval {
   const WalkArgs &a;
-  double x, y, z, ro;
-  int32_t self;
-  double ax, ay, az;
+  float xh, yh, zh, xl, yl, zl, inv_ro;
+  FF ax, ay, az;
+  __device__ void term(FF dx, FF dy, FF dz, FF m, float k_inv_ro, bool pp, const float4 q0,
+                       const float4 q1) {
+    const FF r2 = ff_add(ff_add(ff_mul(dx, dx), ff_mul(dy, dy)), ff_mul(dz, dz));
+    if (r2.h == 0.0f) return;  // the target itself
+    const FF ri = ff_rsqrt(r2);
+    const FF ri3 = ff_mul(ff_mul(ri, ri), ri);
+    float K = 1.0f;
+    if (pp) {
+      const float y = r2.h * ri.h * k_inv_ro;
+      const float x = __saturatef(fmaf(y, a.inv1mg_f, a.mgi_f));
+      const float x2 = x * x;
+      K = (x2 * x2) * fmaf(fmaf(fmaf(-20.f, x, 70.f), x, -84.f), x, 35.f);
+      if (K == 0.0f) return;
+    }
+    const FF f = ff_mul(ff_mulf(m, K), ri3);  // m K / r^3
+    ax = ff_add(ax, ff_mul(f, {-dx.h, -dx.l}));
+    ay = ff_add(ay, ff_mul(f, {-dy.h, -dy.l}));
+    az = ff_add(az, ff_mul(f, {-dz.h, -dz.l}));
+    if (!pp) {  // Q.r / r^5 - (5/2) (r.Q.r) r / r^7 in FP32
+      const float ddx = dx.h, ddy = dy.h, ddz = dz.h, rinv = ri.h;
+      const float rinv2 = rinv * rinv, rinv5 = rinv2 * rinv2 * rinv;
+      const float qx = fmaf(q0.x, ddx, fmaf(q0.w, ddy, q1.x * ddz));
+      const float qy = fmaf(q0.w, ddx, fmaf(q0.y, ddy, q1.y * ddz));
+      const float qz = fmaf(q1.x, ddx, fmaf(q1.y, ddy, q0.z * ddz));
+      const float rqr = fmaf(ddx, qx, fmaf(ddy, qy, ddz * qz));
+      const float c = -2.5f * rqr * rinv5 * rinv2;
+      ax = ff_add(ax, ff_fast(fmaf(c, ddx, qx * rinv5), 0.0f));
+      ay = ff_add(ay, ff_fast(fmaf(c, ddy, qy * rinv5), 0.0f));
+      az = ff_add(az, ff_fast(fmaf(c, ddz, qz * rinv5), 0.0f));
+    }
+  }
   __device__ void pp(const int32_t *list, int n) {
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int s = threadIdx.x & 31; s < n; s += 32) {
       const int32_t j = list[s];
-      const double dx = x - a.sx[j], dy = y - a.sy[j], dz = z - a.sz[j];
-      const double r2 = dx * dx + dy * dy + dz * dz;
-      const double rinv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
-      const double yv = r2 * rinv / fmax(ro, a.sro[j]);
-      double u = (yv - a.gamma) / (1.0 - a.gamma);
-      u = u < 0.0 ? 0.0 : (u > 1.0 ? 1.0 : u);
-      const double u2 = u * u;
-      const double K = (u2 * u2) * (((-20.0 * u + 70.0) * u - 84.0) * u + 35.0);
-      const double f = a.sm[j] * K * (rinv * rinv * rinv);
-      ax -= f * dx; ay -= f * dy; az -= f * dz;
+      const float4 A = __ldg(&a.spA[j]), B = __ldg(&a.spB[j]);
+      const FF dx = ff_add({xh, xl}, {-A.x, -B.x});
+      const FF dy = ff_add({yh, yl}, {-A.y, -B.y});
+      const FF dz = ff_add({zh, zl}, {-A.z, -B.z});
+      term(dx, dy, dz, ff_fast(A.w, __ldg(&a.sml[j])), fminf(inv_ro, B.w), true, z4, z4);
     }
   }
   __device__ void nodes(const int32_t *list, int n) {
     for (int s = threadIdx.x & 31; s < n; s += 32) {
-      const Mom64 &m = a.mom64[list[s]];
-      const double dx = x - m.cx, dy = y - m.cy, dz = z - m.cz;
-      const double r2 = dx * dx + dy * dy + dz * dz;
-      const double rinv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
-      const double rinv2 = rinv * rinv, rinv3 = rinv2 * rinv, rinv5 = rinv3 * rinv2;
-      const double qx = m.qxx * dx + m.qxy * dy + m.qxz * dz;
-      const double qy = m.qxy * dx + m.qyy * dy + m.qyz * dz;
-      const double qz = m.qxz * dx + m.qyz * dy + m.qzz * dz;
-      const double rqr = dx * qx + dy * qy + dz * qz;
-      const double c = -m.M * rinv3 - 2.5 * rqr * rinv5 * rinv2;
-      ax += c * dx + qx * rinv5;
-      ay += c * dy + qy * rinv5;
-      az += c * dz + qz * rinv5;
+      const Mom32 *m = &a.mom32[list[s]];
+      const float4 hi = __ldg(&m->hi), lo = __ldg(&m->lo);
+      const FF dx = ff_add({xh, xl}, {-hi.x, -lo.x});
+      const FF dy = ff_add({yh, yl}, {-hi.y, -lo.y});
+      const FF dz = ff_add({zh, zl}, {-hi.z, -lo.z});
+      term(dx, dy, dz, ff_fast(hi.w, lo.w), 0.0f, false, __ldg(&m->q0), __ldg(&m->q1));
     }
   }
 };
@@ -611,8 +675,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(const WalkArgs a) {
   }
 }
 
-// FP64 redo of the targets the mixed walk flagged: one warp per target, the
-// same group box (so the same interaction list), every lane on the entries
+// Float-float redo of the targets the mixed walk flagged: one warp per
+// target, the same group box (so the same interaction list), every lane on
+// the entries
 __global__ void __launch_bounds__(kWarps * 32) k_refine(const WalkArgs a) {
   __shared__ int32_t s_pp[kWarps][kPPCap];
   __shared__ int32_t s_nd[kWarps][kNDCap];
@@ -631,17 +696,20 @@ __global__ void __launch_bounds__(kWarps * 32) k_refine(const WalkArgs a) {
     const int32_t ti = a.refine[q];
     GroupBox gb;
     gb.load(a.node[a.leaf_of[ti]]);
-    RefineEval ev{a, a.sx[ti], a.sy[ti], a.sz[ti], a.sro[ti], ti, 0.0, 0.0, 0.0};
+    const float4 A = a.spA[ti], B = a.spB[ti];
+    RefineEval ev{a, A.x, A.y, A.z, B.x, B.y, B.z, B.w, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     if (!traverse(a, gb, stack, s_pp[w], s_nd[w], s_big[w], s_bh, round_limit, ev)) break;
-    // the target itself is in the list: its own term is zero (r = 0)
+    // the target itself is in the list: its own term is skipped (r = 0)
     for (int o = 16; o > 0; o >>= 1) {
-      ev.ax += __shfl_xor_sync(0xffffffffu, ev.ax, o);
-      ev.ay += __shfl_xor_sync(0xffffffffu, ev.ay, o);
-      ev.az += __shfl_xor_sync(0xffffffffu, ev.az, o);
+      ev.ax = ff_add(ev.ax, ff_shfl_xor(ev.ax, o));
+      ev.ay = ff_add(ev.ay, ff_shfl_xor(ev.ay, o));
+      ev.az = ff_add(ev.az, ff_shfl_xor(ev.az, o));
     }
     if (lane == 0) {
       const int32_t i = a.idx[ti];
-      a.ax[i] = a.G * ev.ax; a.ay[i] = a.G * ev.ay; a.az[i] = a.G * ev.az;
+      a.ax[i] = a.G * ((double)ev.ax.h + (double)ev.ax.l);
+      a.ay[i] = a.G * ((double)ev.ay.h + (double)ev.ay.l);
+      a.az[i] = a.G * ((double)ev.az.h + (double)ev.az.l);
     }
   }
 }
@@ -677,7 +745,7 @@ int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
   a.node = c->node; a.mom64 = c->mom64; a.mom32 = c->mom32;
   a.leaf_list = c->group_list; a.d_nleaf = &c->counters[15]; a.d_nnode = &c->counters[3];
   a.sx = c->sx; a.sy = c->sy; a.sz = c->sz; a.sm = c->sm; a.sro = c->sro; a.srs = c->srs;
-  a.spA = c->spA; a.spB = c->spB; a.srs32 = c->srs32;
+  a.spA = c->spA; a.spB = c->spB; a.srs32 = c->srs32; a.sml = c->sml;
   a.idx = c->idx;
   a.ax = ax; a.ay = ay; a.az = az;
   a.stack = c->walk_stack; a.stack_cap = c->stack_cap;
