@@ -217,29 +217,82 @@ __device__ __forceinline__ void pp_term(const WalkArgs &a, Target<true> &t,
     }
 }
 
+// The targets' bounding box of one walk (float), the largest max(r_search^2,
+// r_out^2) of its targets (widened like the candidate test) and the largest
+// coordinate magnitude; per warp, in shared memory.
+struct FarBox {
+  float lo[3], hi[3], R2, amax;
+};
+
+// A source is far from every target of the walk when its distance to the
+// box, less a margin that covers the FP32 rounding of the coordinates, is
+// beyond max(r_search, r_out) of the source and of every target: then K = 1
+// for every pair (y >= 1) and no pair is a neighbour candidate.
+__device__ __forceinline__ bool far_from(const FarBox &b, const float4 A, const float4 B,
+                                         float rs2s) {
+  const float x = A.x + B.x, y = A.y + B.y, z = A.z + B.z;
+  const float m = 9.5367431640625e-7f *  // 2^-20 of the coordinates' scale
+                  (b.amax + fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z))));
+  const float gx = fmaxf(fmaxf(b.lo[0] - x, x - b.hi[0]) - m, 0.f);
+  const float gy = fmaxf(fmaxf(b.lo[1] - y, y - b.hi[1]) - m, 0.f);
+  const float gz = fmaxf(fmaxf(b.lo[2] - z, z - b.hi[2]) - m, 0.f);
+  const float d2 = gx * gx + gy * gy + gz * gz;
+  const float ro = 1.0f / B.w;  // B.w = 1 / r_out
+  const float R2 = fmaxf(b.R2, fmaxf(rs2s, ro * ro * 1.00001f));
+  return d2 > 0.f && d2 >= R2;
+}
+
+// a pair term with K = 1 and no candidate test (the source is far, see above):
+// the same operations as pp_term's K = 1 case, so the same bits
+__device__ __forceinline__ void pp_term_far(Target<true> &t, const float4 A, const float4 B,
+                                            float &bx, float &by, float &bz) {
+    const float dx = (t.xh - A.x) + (t.xl - B.x);
+    const float dy = (t.yh - A.y) + (t.yl - B.y);
+    const float dz = (t.zh - A.z) + (t.zl - B.z);
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float f = (A.w * rinv) * (rinv * rinv);
+    bx = fmaf(-f, dx, bx);
+    by = fmaf(-f, dy, by);
+    bz = fmaf(-f, dz, bz);
+    t.tabs = fmaf(f, r, t.tabs);
+}
+
 __device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<true> &t, const int32_t *list,
-                                        int nsrc, void *stage, unsigned &npp) {
+                                        int nsrc, void *stage, const FarBox &box,
+                                        unsigned &npp) {
   StagePP32 &S = *reinterpret_cast<StagePP32 *>(stage);
   const int lane = threadIdx.x & 31;
+  bool near = false;
   if (lane < nsrc) {
     const int32_t j = list[lane];
-    S.A[lane] = __ldg(&a.spA[j]);
-    S.B[lane] = __ldg(&a.spB[j]);
-    S.rs[lane] = __ldg(&a.srs32[j]);
+    const float4 A = __ldg(&a.spA[j]), B = __ldg(&a.spB[j]);
+    const float rs = __ldg(&a.srs32[j]);
+    S.A[lane] = A;
+    S.B[lane] = B;
+    S.rs[lane] = rs;
     S.idx[lane] = j;
+    near = !far_from(box, A, B, rs);
   }
+  const bool any_near = __any_sync(0xffffffffu, near);
   __syncwarp();
   float bx = 0.f, by = 0.f, bz = 0.f;
   npp += (t.valid && t.rep == 0) ? (unsigned)nsrc : 0u;
+  if (any_near) {
 #pragma unroll 2
-  for (int s = t.rep; s < nsrc; s += t.nrep)
-    pp_term(a, t, S.A[s], S.B[s], S.rs[s], &S.idx[s], bx, by, bz, npp);
+    for (int s = t.rep; s < nsrc; s += t.nrep)
+      pp_term(a, t, S.A[s], S.B[s], S.rs[s], &S.idx[s], bx, by, bz, npp);
+  } else {
+#pragma unroll 2
+    for (int s = t.rep; s < nsrc; s += t.nrep) pp_term_far(t, S.A[s], S.B[s], bx, by, bz);
+  }
   __syncwarp();
   t.fold(bx, by, bz);
 }
 
 __device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<false> &t, const int32_t *list,
-                                        int nsrc, void *stage, unsigned &npp) {
+                                        int nsrc, void *stage, const FarBox &, unsigned &npp) {
   StagePP64 &S = *reinterpret_cast<StagePP64 *>(stage);
   const int lane = threadIdx.x & 31;
   if (lane < nsrc) {
@@ -511,10 +564,40 @@ template <bool MIXED> struct GroupEval {
   const WalkArgs &a;
   Target<MIXED> &t;
   void *stage;
+  const FarBox &box;
   unsigned &npp, &npn;
   __device__ void nodes(const int32_t *list, int n) { eval_nodes(a, t, list, n, stage, npn); }
-  __device__ void pp(const int32_t *list, int n) { eval_pp(a, t, list, n, stage, npp); }
+  __device__ void pp(const int32_t *list, int n) { eval_pp(a, t, list, n, stage, box, npp); }
 };
+
+// the walk's FarBox from its (valid) targets, written by lane 0
+__device__ __forceinline__ void far_box(const Target<true> &t, FarBox &b) {
+  const float x = t.xh + t.xl, y = t.yh + t.yl, z = t.zh + t.zl;
+  const float inf = __int_as_float(0x7f800000);
+  float lo0 = t.valid ? x : inf, lo1 = t.valid ? y : inf, lo2 = t.valid ? z : inf;
+  float hi0 = t.valid ? x : -inf, hi1 = t.valid ? y : -inf, hi2 = t.valid ? z : -inf;
+  const float ro = 1.0f / t.inv_ro;
+  float R2 = t.valid ? fmaxf(t.rs2, ro * ro * 1.00001f) : 0.f;
+  float am = t.valid ? fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z))) : 0.f;
+  for (int o = 16; o > 0; o >>= 1) {
+    lo0 = fminf(lo0, __shfl_xor_sync(0xffffffffu, lo0, o));
+    lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, o));
+    lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, o));
+    hi0 = fmaxf(hi0, __shfl_xor_sync(0xffffffffu, hi0, o));
+    hi1 = fmaxf(hi1, __shfl_xor_sync(0xffffffffu, hi1, o));
+    hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, o));
+    R2 = fmaxf(R2, __shfl_xor_sync(0xffffffffu, R2, o));
+    am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+  }
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) {
+    b.lo[0] = lo0; b.lo[1] = lo1; b.lo[2] = lo2;
+    b.hi[0] = hi0; b.hi[1] = hi1; b.hi[2] = hi2;
+    b.R2 = R2;
+    b.amax = am;
+  }
+  __syncwarp();
+}
 
 // ---- float-float arithmetic (pairs hi + lo of floats, ~2^-44 relative) ------
 // Dekker's and Knuth's error-free transformations with fmaf for the product
@@ -626,6 +709,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(const WalkArgs a) {
   __shared__ int32_t s_big[kWarps][kBigCap];
   __shared__ __align__(16) unsigned char s_stage[kWarps][kStageBytes];
   __shared__ int64_t s_bh[P3T_BITS + 1];
+  __shared__ FarBox s_box[kWarps];
   if (threadIdx.x <= P3T_BITS) s_bh[threadIdx.x] = a.bh[threadIdx.x];
   __syncthreads();
 
@@ -651,7 +735,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(const WalkArgs a) {
       const int nrep = 32 / k, rep = lane / k;
       Target<MIXED> t;
       t.load(a, tb + (lane - rep * k), rep < nrep, rep < nrep ? rep : 0, nrep);
-      GroupEval<MIXED> ev{a, t, s_stage[w], npp, npn};
+      if constexpr (MIXED) far_box(t, s_box[w]);
+      GroupEval<MIXED> ev{a, t, s_stage[w], s_box[w], npp, npn};
       ok = traverse(a, gb, stack, s_pp[w], s_nd[w], s_big[w], s_bh, round_limit, ev);
       if (ok) {
         t.reduce(k);
