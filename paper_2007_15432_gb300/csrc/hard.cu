@@ -56,8 +56,9 @@ __global__ void k_kick(int64_t n, double *vx, double *vy, double *vz,
 
 // ---- row a9: Kepler drift, universal variables ------------------------------
 // Stumpff functions C(z) = sum (-z)^k / (2k+2)!, S(z) = sum (-z)^k / (2k+3)!,
-// as nested series for |z| < 1 (6 terms below |z| = 1e-2, 10 terms above;
-// truncation below 1e-20 either way) and in closed form otherwise.
+// as nested series for |z| < 1 (4 terms below |z| = 1e-3, 6 below 1e-2, 10
+// above; truncation below 1e-19 of the result in each band) and in closed
+// form otherwise.
 __device__ __forceinline__ void stumpff(double z, double &C, double &S) {
   constexpr double c0 = 1.0 / 2.0, c1 = -1.0 / 24.0, c2 = 1.0 / 720.0,
                    c3 = -1.0 / 40320.0, c4 = 1.0 / 3628800.0,
@@ -70,7 +71,11 @@ __device__ __forceinline__ void stumpff(double z, double &C, double &S) {
                    s7 = -1.0 / 355687428096000.0, s8 = 1.0 / 121645100408832000.0,
                    s9 = -1.0 / 51090942171709440000.0;
   const double az = fabs(z);
-  if (az < 1e-2) {
+  if (az < 1e-3) {
+    double c = __fma_rn(z, c3, c2), s = __fma_rn(z, s3, s2);
+    c = __fma_rn(z, c, c1); s = __fma_rn(z, s, s1);
+    C = __fma_rn(z, c, c0); S = __fma_rn(z, s, s0);
+  } else if (az < 1e-2) {
     double c = __fma_rn(z, c5, c4), s = __fma_rn(z, s5, s4);
     c = __fma_rn(z, c, c3); s = __fma_rn(z, s, s3);
     c = __fma_rn(z, c, c2); s = __fma_rn(z, s, s2);
@@ -102,6 +107,20 @@ struct KepConst {
   double mu, sq, isq, imu;
 };
 
+// 1 / sqrt(x), x > 0: the FP32 estimate refined by two Newton-Raphson steps
+// y <- y (3 - x y^2) / 2 in FP64 (the error squares at each step, from ~2^-23
+// to below FP64 rounding), instead of a rounded square root and a division.
+// Outside the FP32 normal range the rounded forms are used.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  const float xf = (float)x;
+  if (!(xf > 1e-36f && xf < 1e36f)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf(xf);
+  const double hx = 0.5 * x;
+  y = y * __fma_rn(-hx * y, y, 1.5);
+  y = y * __fma_rn(-hx * y, y, 1.5);
+  return y;
+}
+
 // Advances (X, V) by dt on the Kepler orbit about mu.  Universal anomaly chi
 // solves F(chi) = sig chi^2 C + (1 - alpha r0) chi^3 S + r0 chi - sqrt(mu) dt
 // = 0 (z = alpha chi^2, sig = r0 v_r0 / sqrt(mu)) by Newton-Raphson from the
@@ -110,18 +129,19 @@ struct KepConst {
 // about |F'' / (2 F')| d^2, so the iteration stops once 16 times that bound
 // is below 2^-53 |chi| (or |d| <= 1e-10 |chi|).  Then Lagrange f, g.
 __device__ bool kepler_uv(double X[3], double V[3], double dt, const KepConst &K) {
-  const double r0 = sqrt(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
-  const double v2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
-  const double rv = X[0] * V[0] + X[1] * V[1] + X[2] * V[2];
-  const double ir0 = 1.0 / r0;
-  const double alpha = 2.0 * ir0 - v2 * K.imu;
+  const double r02 = __fma_rn(X[0], X[0], __fma_rn(X[1], X[1], X[2] * X[2]));
+  const double v2 = __fma_rn(V[0], V[0], __fma_rn(V[1], V[1], V[2] * V[2]));
+  const double rv = __fma_rn(X[0], V[0], __fma_rn(X[1], V[1], X[2] * V[2]));
+  const double ir0 = rsqrt_nr(r02);
+  const double r0 = r02 * ir0;
+  const double alpha = __fma_rn(-v2, K.imu, 2.0 * ir0);
   const double sig = rv * K.isq;  // r0 v_r0 / sqrt(mu)
   const double tau = K.sq * dt;
-  const double bet = 1.0 - alpha * r0;
+  const double bet = __fma_rn(-alpha, r0, 1.0);
   // inversion of tau = r0 chi + sig chi^2 / 2 + bet chi^3 / 6 + O(chi^4)
-  const double x1 = tau * ir0, ir02 = ir0 * ir0;
-  double chi = x1 * (1.0 - 0.5 * sig * x1 * ir0 +
-                     (0.5 * sig * sig * ir02 - bet * ir0 * (1.0 / 6.0)) * x1 * x1);
+  const double x1 = tau * ir0, hs = 0.5 * sig * ir0;
+  double chi = x1 * __fma_rn(__fma_rn(hs, hs + hs, -bet * ir0 * (1.0 / 6.0) * ir0), x1 * x1,
+                             __fma_rn(-hs, x1, 1.0));
   // beyond a quarter period (16 dt^2 alpha^3 mu > (2 pi)^2) start from the mean motion
   if (alpha > 0.0 && 16.0 * dt * dt * alpha * alpha * alpha * K.mu > 4.0 * 9.869604401089358)
     chi = tau * alpha;
@@ -134,12 +154,13 @@ __device__ bool kepler_uv(double X[3], double V[3], double dt, const KepConst &K
     const double F = __fma_rn(sig * chi2, C, __fma_rn(bet * chi2 * chi, S, __fma_rn(r0, chi, -tau)));
     const double Fp = __fma_rn(sig * chi, __fma_rn(-z, S, 1.0), __fma_rn(bet * chi2, C, r0));
     const double Fpp = __fma_rn(sig, __fma_rn(-z, C, 1.0), bet * chi * __fma_rn(-z, S, 1.0));
-    double d = F / Fp;
+    const double iFp = 1.0 / Fp;
+    double d = F * iFp;
     const double lim = 0.5 * (fabs(chi) + r0);
     if (d > lim) d = lim;
     if (d < -lim) d = -lim;
     chi -= d;
-    const double rest = 0.5 * fabs(Fpp / Fp) * d * d;
+    const double rest = 0.5 * fabs(Fpp * iFp) * d * d;
     if (16.0 * rest <= 1.1102230246251565e-16 * fabs(chi) || fabs(d) <= 1e-10 * fabs(chi) ||
         d == 0.0) {
       ok = true;
@@ -149,14 +170,13 @@ __device__ bool kepler_uv(double X[3], double V[3], double dt, const KepConst &K
   z = alpha * chi * chi;
   stumpff(z, C, S);
   const double chi2 = chi * chi;
-  const double f = 1.0 - chi2 * ir0 * C;
-  const double g = dt - chi2 * chi * S * K.isq;
+  const double f = __fma_rn(-chi2 * ir0, C, 1.0);
+  const double g = __fma_rn(-chi2 * chi, S * K.isq, dt);
   double nx[3];
   for (int a = 0; a < 3; ++a) nx[a] = __fma_rn(f, X[a], g * V[a]);
-  const double r = sqrt(nx[0] * nx[0] + nx[1] * nx[1] + nx[2] * nx[2]);
-  const double ir = 1.0 / r;
-  const double fd = K.sq * ir * ir0 * (z * S - 1.0) * chi;
-  const double gd = 1.0 - chi2 * ir * C;
+  const double ir = rsqrt_nr(__fma_rn(nx[0], nx[0], __fma_rn(nx[1], nx[1], nx[2] * nx[2])));
+  const double fd = K.sq * ir * ir0 * __fma_rn(z, S, -1.0) * chi;
+  const double gd = __fma_rn(-chi2 * ir, C, 1.0);
   for (int a = 0; a < 3; ++a) {
     const double nv = __fma_rn(fd, X[a], gd * V[a]);
     X[a] = nx[a];
