@@ -83,7 +83,8 @@ void free_particle_buffers(p3t_ctx *c) {
   dfree(c->mkeys); dfree(c->mkeys_alt); dfree(c->mvals); dfree(c->mvals_alt);
   dfree(c->hw); dfree(c->ht); dfree(c->hl);
   dfree(c->coll_ent); dfree(c->coll_rec); dfree(c->coll_rec_e); dfree(c->coll_esoft);
-  dfree(c->coll_slot);
+  dfree(c->coll_slot); dfree(c->scan_state);
+  c->scan_words = 0;
   c->cap = 0;
   c->have_tree = c->have_cand = false;
 }
@@ -132,6 +133,10 @@ int reserve(p3t_ctx *c, int64_t n, int64_t cand_cap) {
   ok &= dalloc(c->hw, 33 * N) && dalloc(c->ht, N) && dalloc(c->hl, 6 * N);
   ok &= dalloc(c->coll_ent, N) && dalloc(c->coll_rec, N / 2 + 1) && dalloc(c->coll_rec_e, N / 2 + 1);
   ok &= dalloc(c->coll_esoft, N) && dalloc(c->coll_slot, N);
+  c->scan_words = p3t_scan_state_words(N > NC ? N : NC);
+  ok &= dalloc(c->scan_state, c->scan_words);
+  if (ok) ok = cudaMemset(c->scan_state, 0, sizeof(unsigned long long) * c->scan_words) ==
+               cudaSuccess;
   // no composites: every slot -1, empty list (composites pending from a
   // smaller context are dropped with it)
   if (ok) ok = cudaMemset(c->coll_slot, 0xff, sizeof(int32_t) * N) == cudaSuccess &&
@@ -178,7 +183,7 @@ int p3t_create(p3t_ctx **ctx, const p3t_params *p, int device) {
   bool ok = dalloc(c->status, 1) && dalloc(c->box, 5) && dalloc(c->box_bits, 6) &&
             dalloc(c->counters, 64) && dalloc(c->cl_counts, 4) && dalloc(c->hsteps, 1) && dalloc(c->hcursor, 3) &&
             dalloc(c->coll_ctr, 1) &&
-            dalloc(c->epart, 8192) && dalloc(c->scan_part, 1025) && dalloc(c->bh_table, 32);
+            dalloc(c->epart, 8192) && dalloc(c->bh_table, 32);
   for (int q = 0; q < 2 && ok; ++q)
     ok = cudaStreamCreateWithFlags(&c->aux[q], cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->ev_join[q], cudaEventDisableTiming) == cudaSuccess;
@@ -204,7 +209,6 @@ void p3t_destroy(p3t_ctx *c) {
   dfree(c->status); dfree(c->box); dfree(c->box_bits); dfree(c->counters);
   dfree(c->cl_counts); dfree(c->hsteps); dfree(c->hcursor); dfree(c->epart);
   dfree(c->coll_ctr);
-  dfree(c->scan_part);
   dfree(c->bh_table);
   dfree(c->dpart); dfree(c->dcnt);
   for (int q = 0; q < 2; ++q) {

@@ -1120,7 +1120,7 @@ int p3t_run_merge(p3t_ctx *c, p3t_particles *p, int32_t *new_index, double *e_di
                                   p->r_phys, sorted_h, sorted_s, out);
   const unsigned g = (unsigned)p3t_grid(n, kBlock, maxb);
   k_merge_keep<<<g, kBlock, 0, s>>>(n, c->coll_slot, co.ent, keep);
-  int rc = p3t_scan_i32_to_i64(keep, pos, d_n, n, d_total, c->scan_part, s);
+  int rc = p3t_scan_i32_to_i64(keep, pos, d_n, n, d_total, c->scan_state, c->scan_words, c->status, s);
   if (rc) return rc;
   k_merge_gather<<<g, kBlock, 0, s>>>(n, keep, pos, *p, scr, ni);
   double *dst[10] = {p->x, p->y, p->z, p->vx, p->vy, p->vz, p->m, p->r_out, p->r_search,

@@ -68,6 +68,8 @@ struct p3t_ctx {
   int64_t node_cap = 0;   // node capacity
   int64_t cand_cap = 0;   // neighbour-candidate capacity (pairs)
   int64_t walk_warps = 0; // resident warps of the walk kernel
+  unsigned long long *scan_state = nullptr;  // the single-pass scan's tile words
+  int64_t scan_words = 0;
   double *dpart = nullptr; // partial sums of the all-pairs kernels (allocated
   int64_t dpart_cap = 0;   //   on their first call; size independent of n)
   int32_t *dcnt = nullptr; // their per-tile arrival counters (zero between calls)
@@ -88,7 +90,6 @@ struct p3t_ctx {
   int32_t *idx = nullptr, *idx_alt = nullptr;
   uint32_t *radix_hist = nullptr;
   int64_t radix_hist_cap = 0;
-  int64_t *scan_part = nullptr;           // scan partials
 
   // sorted particles (FP64 and mixed packings)
   double *sx = nullptr, *sy = nullptr, *sz = nullptr, *sm = nullptr;
@@ -180,11 +181,14 @@ static inline int64_t p3t_grid(int64_t n, int block, int64_t max_blocks) {
 }
 
 // ---- primitives (primitives.cu) ------------------------------------------
-// Exclusive scan of n (device count *d_n, at most n_cap) int32 values into
-// int64; *d_total receives the sum.  Deterministic.
+// Exclusive scan of n (device count *d_n, at most n_cap) non-negative int32
+// values into int64; *d_total receives the sum.  Deterministic (one pass,
+// decoupled look-back).  state: p3t_scan_state_words(n_cap) words, zero
+// before the first call (the scan leaves them zero).
+int64_t p3t_scan_state_words(int64_t n_cap);
 int p3t_scan_i32_to_i64(const int32_t *in, int64_t *out, const int64_t *d_n,
-                        int64_t n_cap, int64_t *d_total, int64_t *part,
-                        cudaStream_t s);
+                        int64_t n_cap, int64_t *d_total, unsigned long long *state,
+                        int64_t state_words, DevStatus *st, cudaStream_t s);
 // Stable LSD radix sort of (key, val) on bits [begin_bit, end_bit), n from
 // device memory (at most n_cap).  Ping-pongs between the two buffers; on
 // return *keys / *vals point at the sorted data.

@@ -5,9 +5,6 @@
 
 namespace {
 
-constexpr int kScanBlock = 1024;
-constexpr int kScanMaxBlocks = 1024;
-
 __device__ __forceinline__ int64_t warp_incl_scan(int64_t v) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -37,46 +34,130 @@ __device__ int64_t block_excl_scan(int64_t v, int64_t *excl, int64_t *sh) {
   return tot;
 }
 
-__global__ void scan_reduce_kernel(const int32_t *in, const int64_t *d_n,
-                                   int64_t *part) {
-  __shared__ int64_t sh[33];
-  const int64_t n = *d_n;
-  const int64_t G = gridDim.x;
-  const int64_t chunk = (n + G - 1) / G;
-  const int64_t lo = blockIdx.x * chunk;
-  const int64_t hi = min(n, lo + chunk);
-  int64_t s = 0;
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += in[i];
-  int64_t ex;
-  int64_t tot = block_excl_scan(s, &ex, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = tot;
-}
+// ---- single-pass exclusive scan (decoupled look-back) -----------------------
+// Each block takes the next tile number from a counter in state[0] (so every
+// smaller tile belongs to a block that has started and will finish without
+// waiting on this one), scans its tile, publishes the tile's sum, adds its
+// predecessors' sums by looking back (a warp reads 32 predecessor words at a
+// time and stops at the nearest one that holds an inclusive prefix), and
+// publishes its own inclusive prefix.  A word holds a flag in bits 63-62 (1:
+// the tile's own sum, 2: inclusive prefix) and the value in bits 61-0
+// (non-negative inputs).  The last block to finish (counter state[1]) clears
+// the words it used and both counters, so that the next call starts clean
+// with no host involvement.  A bounded number of polls: a predecessor that
+// never publishes is reported (P3T_ERR_TIMEOUT) and counted as zero.
+constexpr int kScanThreads = 512;
+constexpr int kScanPer = 8;
+constexpr int kScanTile = kScanThreads * kScanPer;
+constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagInc = 2ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+constexpr int kScanPollLimit = 1 << 22;
 
-__global__ void scan_partials_kernel(int64_t *part, int G, int64_t *d_total) {
+__global__ void __launch_bounds__(kScanThreads)
+scan_onepass(const int32_t *in, int64_t *out, const int64_t *d_n, int64_t *d_total,
+             unsigned long long *state, DevStatus *st) {
   __shared__ int64_t sh[33];
-  int64_t v = threadIdx.x < G ? part[threadIdx.x] : 0;
-  int64_t ex;
-  int64_t tot = block_excl_scan(v, &ex, sh);
-  if (threadIdx.x < G) part[threadIdx.x] = ex;
-  if (threadIdx.x == 0 && d_total) *d_total = tot;
-}
-
-__global__ void scan_apply_kernel(const int32_t *in, int64_t *out,
-                                  const int64_t *d_n, const int64_t *part) {
-  __shared__ int64_t sh[33];
+  // the tile: first its int32 inputs, then its int64 outputs (staged so that
+  // both the loads and the stores are coalesced)
+  __shared__ __align__(16) int64_t s_buf[kScanTile];
+  int32_t *s_in = reinterpret_cast<int32_t *>(s_buf);
+  __shared__ unsigned long long s_tile;
+  __shared__ int64_t s_prefix;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (t == 0) s_tile = atomicAdd(&state[0], 1ull);
+  __syncthreads();
+  const int64_t tile = (int64_t)s_tile;
   const int64_t n = *d_n;
-  const int64_t G = gridDim.x;
-  const int64_t chunk = (n + G - 1) / G;
-  const int64_t lo = blockIdx.x * chunk;
-  const int64_t hi = min(n, lo + chunk);
-  int64_t carry = part[blockIdx.x];
-  for (int64_t base = lo; base < hi; base += blockDim.x) {
-    int64_t i = base + threadIdx.x;
-    int64_t v = i < hi ? in[i] : 0;
+  const int64_t base = tile * kScanTile;
+  unsigned long long *ts = state + 2;
+  if (base < n) {
+    for (int i = 0; i < kScanPer; ++i) {
+      const int64_t e = base + (int64_t)i * kScanThreads + t;
+      s_in[i * kScanThreads + t] = e < n ? in[e] : 0;
+    }
+    __syncthreads();
+    int32_t v[kScanPer];
+    int64_t sum = 0;
+    {
+      const int4 a = reinterpret_cast<const int4 *>(s_in)[2 * t];
+      const int4 b = reinterpret_cast<const int4 *>(s_in)[2 * t + 1];
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+      v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    }
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) sum += v[i];
     int64_t ex;
-    int64_t tot = block_excl_scan(v, &ex, sh);
-    if (i < hi) out[i] = carry + ex;
-    carry += tot;
+    const int64_t agg = block_excl_scan(sum, &ex, sh);
+    if (warp == 0) {
+      int64_t prefix = 0;
+      if (tile == 0) {
+        if (lane == 0) {
+          __threadfence();
+          __stcg(&ts[0], kFlagInc | (unsigned long long)agg);
+        }
+      } else {
+        if (lane == 0) {
+          __threadfence();
+          __stcg(&ts[tile], kFlagAgg | (unsigned long long)agg);
+        }
+        int64_t p = tile - 1;  // the window's first (nearest) predecessor
+        int polls = 0;
+        for (;;) {
+          const int64_t q = p - lane;
+          unsigned long long w = q >= 0 ? __ldcv(&ts[q]) : kFlagInc;
+          while (__any_sync(0xffffffffu, (w >> 62) == 0)) {
+            if (++polls > kScanPollLimit) {
+              if (lane == 0) dev_fail(st, P3T_ERR_TIMEOUT, 70, 0);
+              w = (w >> 62) == 0 ? kFlagAgg : w;  // count the silent tile as zero
+              break;
+            }
+            __nanosleep(64);
+            if ((w >> 62) == 0) w = __ldcv(&ts[q]);
+          }
+          const unsigned inc = __ballot_sync(0xffffffffu, (w >> 62) == 2);
+          const int last = inc ? __ffs(inc) - 1 : 31;  // nearest inclusive prefix
+          int64_t val = lane <= last ? (int64_t)(w & kValMask) : 0;
+          for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+          prefix += val;
+          if (inc) break;
+          p -= 32;
+        }
+        if (lane == 0) {
+          __threadfence();
+          __stcg(&ts[tile], kFlagInc | (unsigned long long)(prefix + agg));
+        }
+      }
+      if (lane == 0) s_prefix = prefix;
+    }
+    __syncthreads();  // every thread has read its inputs: s_buf now holds outputs
+    int64_t run = s_prefix + ex;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+      s_buf[t * kScanPer + i] = run;
+      run += v[i];
+    }
+    __syncthreads();
+    for (int i = 0; i < kScanPer; ++i) {
+      const int64_t e = base + (int64_t)i * kScanThreads + t;
+      if (e < n) out[e] = s_buf[i * kScanThreads + t];
+    }
+    if (t == 0 && base + kScanTile >= n && d_total) *d_total = s_prefix + agg;
+  } else if (t == 0 && tile == 0 && d_total) {
+    *d_total = 0;  // n = 0
+  }
+  // the last block out resets the tile words and the counters
+  __shared__ bool s_last;
+  __syncthreads();
+  if (t == 0) {
+    __threadfence();
+    s_last = atomicAdd(&state[1], 1ull) == (unsigned long long)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    const int64_t used = (n + kScanTile - 1) / kScanTile;
+    for (int64_t k = t; k < used; k += kScanThreads) ts[k] = 0ull;
+    if (t == 0) { state[0] = 0ull; state[1] = 0ull; }
   }
 }
 
@@ -209,16 +290,18 @@ radix_downsweep(const uint64_t *keys, const int32_t *vals, uint64_t *okeys,
 
 }  // namespace
 
+int64_t p3t_scan_state_words(int64_t n_cap) {
+  return 2 + (n_cap + kScanTile - 1) / kScanTile;
+}
+
 int p3t_scan_i32_to_i64(const int32_t *in, int64_t *out, const int64_t *d_n,
-                        int64_t n_cap, int64_t *d_total, int64_t *part,
-                        cudaStream_t s) {
-  int G = (int)((n_cap + 4 * kScanBlock - 1) / (4 * kScanBlock));
+                        int64_t n_cap, int64_t *d_total, unsigned long long *state,
+                        int64_t state_words, DevStatus *st, cudaStream_t s) {
+  int64_t G = (n_cap + kScanTile - 1) / kScanTile;
   if (G < 1) G = 1;
-  if (G > kScanMaxBlocks) G = kScanMaxBlocks;
-  scan_reduce_kernel<<<G, kScanBlock, 0, s>>>(in, d_n, part);
-  scan_partials_kernel<<<1, kScanBlock, 0, s>>>(part, G, d_total);
-  scan_apply_kernel<<<G, kScanBlock, 0, s>>>(in, out, d_n, part);
-  p3t_note_launches(3);
+  if (G + 2 > state_words) return P3T_ERR_CAPACITY;
+  scan_onepass<<<(unsigned)G, kScanThreads, 0, s>>>(in, out, d_n, d_total, state, st);
+  p3t_note_launches(1);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 

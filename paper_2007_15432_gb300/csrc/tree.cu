@@ -673,7 +673,7 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
                                           c->srs32, c->sml);
   k_lcp<<<(unsigned)g, kBlock, 0, s>>>(n, c->keys, leaf, c->wlcp, c->lp);
   k_levels<<<(unsigned)g, kBlock, 0, s>>>(n, leaf, c->wlcp, c->lp, c->lv, c->ncount);
-  rc = p3t_scan_i32_to_i64(c->ncount, c->nstart, &cnt[0], c->cap, &cnt[1], c->scan_part, s);
+  rc = p3t_scan_i32_to_i64(c->ncount, c->nstart, &cnt[0], c->cap, &cnt[1], c->scan_state, c->scan_words, c->status, s);
   if (rc) return rc;
   k_clamp_nodes<<<1, 1, 0, s>>>(cnt, c->node_cap, c->status);
   k_nodes_pre<<<(unsigned)g, kBlock, 0, s>>>(n, c->keys, c->lp, c->lv, c->nstart, &cnt[1],
@@ -690,7 +690,7 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
                                               c->leaf_flag, c->node_done, c->status);
   k_parents<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->node);
   rc = p3t_scan_i32_to_i64(c->leaf_flag, c->leaf_pos, &cnt[3], c->node_cap, &cnt[2],
-                           c->scan_part, s);
+                           c->scan_state, c->scan_words, c->status, s);
   if (rc) return rc;
   k_leaf_list<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->leaf_flag,
                                               c->leaf_pos, c->pre2bfs, c->leaf_list);
@@ -709,7 +709,7 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   k_group_flags<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->node, c->bfs2pre,
                                                 c->prm.group_size, c->group_flag);
   rc = p3t_scan_i32_to_i64(c->group_flag, c->group_pos, &cnt[3], c->node_cap, &cnt[15],
-                           c->scan_part, s);
+                           c->scan_state, c->scan_words, c->status, s);
   if (rc) return rc;
   k_group_list<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->group_flag,
                                                c->group_pos, c->pre2bfs, c->node,
