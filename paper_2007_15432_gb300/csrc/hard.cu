@@ -330,11 +330,28 @@ struct CollOut {
   int64_t ent_cap, rec_cap;
 };
 
+// x 2^k and ilogb(x) read from and written to the exponent field with integer
+// operations when x (and the result) are normal -- the same values as ldexp
+// and ilogb, without an FP64 instruction (one costs 64 cycles of a
+// sub-partition's FP64 pipe on this part) -- and by ldexp / ilogb otherwise.
+__device__ __forceinline__ double ldexp_fast(double x, int k) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e > 0 && e < 0x7ff && e + k > 0 && e + k < 0x7ff)
+    return __longlong_as_double(b + ((long long)k << 52));
+  return ldexp(x, k);
+}
+__device__ __forceinline__ int ilogb_fast(double x) {
+  const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+  return (e > 0 && e < 0x7ff) ? e - 1023 : ilogb(x);
+}
+
 // The step estimates only choose a power-of-two step: formed in FP32 from
 // components scaled by an exact power of two 2^k (j by s, a2 by s^2, a3 by
 // s^3, s = 2^e close to the step) so that nothing overflows FP32.
 __device__ __forceinline__ float norm3f(double a, double b, double c, int k) {
-  const float x = (float)ldexp(a, k), y = (float)ldexp(b, k), z = (float)ldexp(c, k);
+  const float x = (float)ldexp_fast(a, k), y = (float)ldexp_fast(b, k),
+              z = (float)ldexp_fast(c, k);
   return sqrtf(x * x + y * y + z * z);
 }
 
@@ -346,12 +363,27 @@ __device__ __forceinline__ float norm3f(double a, double b, double c, int k) {
 __device__ __forceinline__ int quantise_level(double dt_des, double dt, int prev,
                                               int64_t t, bool &underflow) {
   int lvl = 0;
-  if (dt_des > 0.0 && dt_des < dt) {
-    int l0 = ilogb(dt) - ilogb(dt_des) - 1;  // dt / 2^l > dt_des for every l <= l0
-    lvl = l0 < 0 ? 0 : (l0 > P3T_KMAX ? P3T_KMAX : l0);
+  const long long bd = __double_as_longlong(dt), bs = __double_as_longlong(dt_des);
+  const int edt = (int)((bd >> 52) & 0x7ff);
+  if (bd > 0 && edt > P3T_KMAX && edt < 0x7ff &&
+      (bs & 0x7fffffffffffffffLL) <= 0x7ff0000000000000LL) {
+    // dt positive and normal down to dt / 2^KMAX, dt_des not NaN: as integers
+    // the bit patterns order like the values (negative dt_des, -0 included,
+    // below every positive one), and dt / 2^l is dt's pattern less l << 52
+    if (bs > 0 && bs < bd) {
+      int l0 = ilogb_fast(dt) - ilogb_fast(dt_des) - 1;  // dt / 2^l > dt_des for l <= l0
+      lvl = l0 < 0 ? 0 : (l0 > P3T_KMAX ? P3T_KMAX : l0);
+    }
+    while (lvl < P3T_KMAX && bd - ((long long)lvl << 52) > bs) ++lvl;
+    if (bd - ((long long)lvl << 52) > bs) underflow = true;
+  } else {
+    if (dt_des > 0.0 && dt_des < dt) {
+      int l0 = ilogb(dt) - ilogb(dt_des) - 1;
+      lvl = l0 < 0 ? 0 : (l0 > P3T_KMAX ? P3T_KMAX : l0);
+    }
+    while (lvl < P3T_KMAX && ldexp(dt, -lvl) > dt_des) ++lvl;
+    if (ldexp(dt, -lvl) > dt_des) underflow = true;
   }
-  while (lvl < P3T_KMAX && ldexp(dt, -lvl) > dt_des) ++lvl;
-  if (ldexp(dt, -lvl) > dt_des) underflow = true;
   if (lvl < prev - 1) lvl = prev - 1;
   if (t != 0) {
     const int need = P3T_KMAX - __ffsll((long long)t) + 1;  // 2^(40-lvl) must divide t
@@ -364,10 +396,10 @@ __device__ __forceinline__ int quantise_level(double dt_des, double dt, int prev
 template <class V>
 __device__ __forceinline__ int first_level(const V &S, int k, const p3t_params &prm, double dt,
                                            int64_t t, bool &underflow) {
-  const int e = ilogb(dt);
+  const int e = ilogb_fast(dt);
   const float an = norm3f(S.a(0, k), S.a(1, k), S.a(2, k), 0);
   const float jn = norm3f(S.j(0, k), S.j(1, k), S.j(2, k), e);
-  const double dtd = jn > 0.0f ? ldexp((double)((float)prm.eta0 * an / jn), e) : dt;
+  const double dtd = jn > 0.0f ? ldexp_fast((double)((float)prm.eta0 * an / jn), e) : dt;
   return quantise_level(dtd, dt, 0, t, underflow);
 }
 
@@ -516,18 +548,36 @@ __device__ void block_forces(const V &S, HCtl &C, double (*Tb)[6], int nc, int n
   }
 }
 
+// minimum over the warp of a value in [0, 2^63): the minimum of the high
+// words, then of the low words among the lanes that hold it (two warp
+// reductions instead of five dependent shuffle steps)
+__device__ __forceinline__ int64_t warp_min64(int64_t v) {
+  const unsigned hi = (unsigned)((unsigned long long)v >> 32), lo = (unsigned)v;
+  const unsigned hmin = __reduce_min_sync(0xffffffffu, hi);
+  const unsigned lmin = __reduce_min_sync(0xffffffffu, hi == hmin ? lo : 0xffffffffu);
+  return (int64_t)(((unsigned long long)hmin << 32) | lmin);
+}
+
+// the block minima of two non-negative values (one warp: no shared memory)
 template <int NT>
-__device__ __forceinline__ int64_t block_min(int64_t v, int64_t *red4) {
-  for (int o = 16; o > 0; o >>= 1) {
-    const int64_t u = __shfl_xor_sync(0xffffffffu, v, o);
-    v = u < v ? u : v;
+__device__ __forceinline__ void block_min2(int64_t &a, int64_t &b, int64_t (*red)[4]) {
+  a = warp_min64(a);
+  b = warp_min64(b);
+  if constexpr (NT > 32) {
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = a;
+      red[1][threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    int64_t ra = red[0][0], rb = red[1][0];
+    for (int q = 1; q < NT / 32; ++q) {
+      ra = red[0][q] < ra ? red[0][q] : ra;
+      rb = red[1][q] < rb ? red[1][q] : rb;
+    }
+    __syncthreads();
+    a = ra;
+    b = rb;
   }
-  if ((threadIdx.x & 31) == 0) red4[threadIdx.x >> 5] = v;
-  __syncthreads();
-  int64_t r = red4[0];
-  for (int q = 1; q < NT / 32; ++q) r = red4[q] < r ? red4[q] : r;
-  __syncthreads();
-  return r;
 }
 
 // energy of the members with chg & 1 as far as replacing them can change it:
@@ -704,8 +754,9 @@ __device__ void integrate_cluster(const V &S, HCtl &C, double (*Tb)[6], int64_t 
       e_min = e < e_min ? e : e_min;
       t_min = S.t(k) < t_min ? S.t(k) : t_min;
     }
-    tn = block_min<NT>(e_min, C.red[0]);
-    const int64_t tmin = block_min<NT>(t_min, C.red[1]);
+    block_min2<NT>(e_min, t_min, C.red);
+    tn = e_min;
+    const int64_t tmin = t_min;
     if (tmin >= T) break;
     if (++iter > kHermiteIterLimit) {
       if (tid == 0) dev_fail(st, P3T_ERR_TIMEOUT, 61, 0);
@@ -747,13 +798,14 @@ __device__ void integrate_cluster(const V &S, HCtl &C, double (*Tb)[6], int64_t 
     for (int b = item; b < nact; b += NT) {
       const int k = S.act(b);
       const double D = (double)(T >> S.lvl(k)) * unit;
-      const int e = ilogb(D);  // dt = sqrt(eta num_s / den_s) s
+      const int e = ilogb_fast(D);  // dt = sqrt(eta num_s / den_s) s
       const float an = norm3f(S.a(0, k), S.a(1, k), S.a(2, k), 0);
       const float jn = norm3f(S.j(0, k), S.j(1, k), S.j(2, k), e);
       const float a2n = norm3f(S.a2e(0, k), S.a2e(1, k), S.a2e(2, k), 2 * e);
       const float a3n = norm3f(S.a3(0, k), S.a3(1, k), S.a3(2, k), 3 * e);
       const float num = an * a2n + jn * jn, den = jn * a3n + a2n * a2n;
-      const double dtd = den > 0.0f ? ldexp((double)sqrtf((float)prm.eta * num / den), e) : dt;
+      const double dtd =
+          den > 0.0f ? ldexp_fast((double)sqrtf((float)prm.eta * num / den), e) : dt;
       S.t(k) = tn;
       S.lvl(k) = quantise_level(dtd, dt, S.lvl(k), tn, underflow);
       if (S.partner(k) != kNone) C.any = 1;
