@@ -785,23 +785,23 @@ void or_hard_acc_jerk(int64_t nc, const double *x, const double *y,
   const double i1mg = 1.0 / (1.0 - p->gamma);
   double ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0;
   {
-    double r2 = x[k] * x[k] + y[k] * y[k] + z[k] * z[k];
+    double r2 = fma(x[k], x[k], fma(y[k], y[k], z[k] * z[k]));
     double rinv = 1.0 / sqrt(r2);
     double rinv2 = rinv * rinv;
     double f = p->G * p->m_star * (rinv2 * rinv);
-    double rv = x[k] * vx[k] + y[k] * vy[k] + z[k] * vz[k];
+    double rv = fma(x[k], vx[k], fma(y[k], vy[k], z[k] * vz[k]));
     ax -= f * x[k]; ay -= f * y[k]; az -= f * z[k];
     double c = 3.0 * rv * rinv2;
-    jx -= f * (vx[k] - c * x[k]);
-    jy -= f * (vy[k] - c * y[k]);
-    jz -= f * (vz[k] - c * z[k]);
+    jx -= f * fma(-c, x[k], vx[k]);
+    jy -= f * fma(-c, y[k], vy[k]);
+    jz -= f * fma(-c, z[k], vz[k]);
   }
   const double irok = 1.0 / r_out[k];
   for (int64_t j = 0; j < nc; ++j) {
     if (j == k) continue;
     double rx = x[k] - x[j], ry = y[k] - y[j], rz = z[k] - z[j];
     double ux = vx[k] - vx[j], uy = vy[k] - vy[j], uz = vz[k] - vz[j];
-    double r2 = rx * rx + ry * ry + rz * rz;
+    double r2 = fma(rx, rx, fma(ry, ry, rz * rz));
     if (r2 == 0.0) continue;
     double rinv = 1.0 / sqrt(r2);
     double r = r2 * rinv;
@@ -818,13 +818,13 @@ void or_hard_acc_jerk(int64_t nc, const double *x, const double *y,
     double rinv2 = rinv * rinv;
     double g3 = p->G * m[j] * (rinv2 * rinv);
     double f = g3 * w;
-    double rv = rx * ux + ry * uy + rz * uz;
+    double rv = fma(rx, ux, fma(ry, uy, rz * uz));
     ax -= f * rx; ay -= f * ry; az -= f * rz;
     /* d/dt [w r / r^3] = w v / r^3 - (3 w (r.v)/r^2 + K'(y) (r.v)/(r r_out)) r / r^3 */
-    double c = 3.0 * w * rv * rinv2 + dK * rv * rinv * irot;
-    jx -= g3 * (w * ux - c * rx);
-    jy -= g3 * (w * uy - c * ry);
-    jz -= g3 * (w * uz - c * rz);
+    double c = fma(dK * rv * rinv, irot, 3.0 * w * rv * rinv2);
+    jx -= g3 * fma(-c, rx, w * ux);
+    jy -= g3 * fma(-c, ry, w * uy);
+    jz -= g3 * fma(-c, rz, w * uz);
   }
   acc[0] = ax; acc[1] = ay; acc[2] = az;
   jerk[0] = jx; jerk[1] = jy; jerk[2] = jz;
@@ -873,23 +873,23 @@ static void hard_acc_jerk_sets(int64_t nc, const double *x, const double *y,
   double ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0;
   if (partner) *partner = -1;
   {
-    double r2 = x[k] * x[k] + y[k] * y[k] + z[k] * z[k];
+    double r2 = fma(x[k], x[k], fma(y[k], y[k], z[k] * z[k]));
     double rinv = 1.0 / sqrt(r2);
     double rinv2 = rinv * rinv;
     double f = p->G * p->m_star * (rinv2 * rinv);
-    double rv = x[k] * vx[k] + y[k] * vy[k] + z[k] * vz[k];
+    double rv = fma(x[k], vx[k], fma(y[k], vy[k], z[k] * vz[k]));
     ax -= f * x[k]; ay -= f * y[k]; az -= f * z[k];
     double c = 3.0 * rv * rinv2;
-    jx -= f * (vx[k] - c * x[k]);
-    jy -= f * (vy[k] - c * y[k]);
-    jz -= f * (vz[k] - c * z[k]);
+    jx -= f * fma(-c, x[k], vx[k]);
+    jy -= f * fma(-c, y[k], vy[k]);
+    jz -= f * fma(-c, z[k], vz[k]);
   }
   const double irok = 1.0 / r_out[k];
   for (int64_t j = 0; j < nc; ++j) {
     if (j == k || set[j] == set[k]) continue;
     double rx = x[k] - x[j], ry = y[k] - y[j], rz = z[k] - z[j];
     double ux = vx[k] - vx[j], uy = vy[k] - vy[j], uz = vz[k] - vz[j];
-    double r2 = rx * rx + ry * ry + rz * rz;
+    double r2 = fma(rx, rx, fma(ry, ry, rz * rz));
     if (RP && partner && *partner < 0) {
       double sr = p->f_radius * (RP[k] + RP[j]);
       if (r2 < sr * sr) *partner = j;
@@ -910,12 +910,12 @@ static void hard_acc_jerk_sets(int64_t nc, const double *x, const double *y,
     double rinv2 = rinv * rinv;
     double g3 = p->G * m[j] * (rinv2 * rinv);
     double f = g3 * w;
-    double rv = rx * ux + ry * uy + rz * uz;
+    double rv = fma(rx, ux, fma(ry, uy, rz * uz));
     ax -= f * rx; ay -= f * ry; az -= f * rz;
-    double c = 3.0 * w * rv * rinv2 + dK * rv * rinv * irot;
-    jx -= g3 * (w * ux - c * rx);
-    jy -= g3 * (w * uy - c * ry);
-    jz -= g3 * (w * uz - c * rz);
+    double c = fma(dK * rv * rinv, irot, 3.0 * w * rv * rinv2);
+    jx -= g3 * fma(-c, rx, w * ux);
+    jy -= g3 * fma(-c, ry, w * uy);
+    jz -= g3 * fma(-c, rz, w * uz);
   }
   acc[0] = ax; acc[1] = ay; acc[2] = az;
   jerk[0] = jx; jerk[1] = jy; jerk[2] = jz;
@@ -974,6 +974,8 @@ static double set_energy(int64_t nc, const unsigned char *chg, const int64_t *se
 /* Fourth-order Hermite with block individual time steps over [0, dt] for one */
 /* cluster (Sec. 2.1.2, Makino 1991; Aarseth time steps).  Reading C7:        */
 /*  predictor  x_p = x + v D + a D^2/2 + j D^3/6, v_p = v + a D + j D^2/2;    */
+/*             (Horner form with fused multiply-adds, as are the corrector's */
+/*             sums and the pair term's dot products)                        */
 /*  corrector  a2 = (-6(a0-a1) - D(4 j0 + 2 j1))/D^2,                        */
 /*             a3 = (12(a0-a1) + 6 D (j0 + j1))/D^3,                          */
 /*             x = x_p + a2 D^4/24 + a3 D^5/120, v = v_p + a2 D^3/6 + a3 D^4/24;*/
@@ -1119,14 +1121,15 @@ int or_hermite_cluster(int64_t nc, const int32_t *members, double *X, double *Y,
     if (tmin >= T) break;
     for (int64_t k = 0; k < nc; ++k) {
       double D = (double)(tn - t[k]) * unit;
-      double D2 = D * D, D3 = D2 * D;
       const double *ak = a + 3 * k, *jj = jk + 3 * k;
-      px[k] = x[k] + vx[k] * D + ak[0] * D2 * 0.5 + jj[0] * D3 * (1.0 / 6.0);
-      py[k] = y[k] + vy[k] * D + ak[1] * D2 * 0.5 + jj[1] * D3 * (1.0 / 6.0);
-      pz[k] = z[k] + vz[k] * D + ak[2] * D2 * 0.5 + jj[2] * D3 * (1.0 / 6.0);
-      pvx[k] = vx[k] + ak[0] * D + jj[0] * D2 * 0.5;
-      pvy[k] = vy[k] + ak[1] * D + jj[1] * D2 * 0.5;
-      pvz[k] = vz[k] + ak[2] * D + jj[2] * D2 * 0.5;
+      /* Horner form with fused multiply-adds: x + D (v + D (a/2 + D j/6)),
+       * v + D (a + D j/2) */
+      px[k] = fma(fma(fma(jj[0] * (1.0 / 6.0), D, ak[0] * 0.5), D, vx[k]), D, x[k]);
+      py[k] = fma(fma(fma(jj[1] * (1.0 / 6.0), D, ak[1] * 0.5), D, vy[k]), D, y[k]);
+      pz[k] = fma(fma(fma(jj[2] * (1.0 / 6.0), D, ak[2] * 0.5), D, vz[k]), D, z[k]);
+      pvx[k] = fma(fma(jj[0] * 0.5, D, ak[0]), D, vx[k]);
+      pvy[k] = fma(fma(jj[1] * 0.5, D, ak[1]), D, vy[k]);
+      pvz[k] = fma(fma(jj[2] * 0.5, D, ak[2]), D, vz[k]);
       act[k] = (t[k] + (T >> lvl[k]) == tn);
     }
     for (int64_t k = 0; k < nc; ++k)
@@ -1142,16 +1145,18 @@ int or_hermite_cluster(int64_t nc, const int32_t *members, double *X, double *Y,
       double A2[3], A3[3], A2e[3];
       for (int c = 0; c < 3; ++c) {
         double da = a[3 * k + c] - a1[3 * k + c];
-        A2[c] = (-6.0 * da - D * (4.0 * jk[3 * k + c] + 2.0 * j1[3 * k + c])) * iD2;
-        A3[c] = (12.0 * da + 6.0 * D * (jk[3 * k + c] + j1[3 * k + c])) * iD3;
-        A2e[c] = A2[c] + D * A3[c];
+        A2[c] = fma(-D, fma(2.0, j1[3 * k + c], 4.0 * jk[3 * k + c]), -6.0 * da) * iD2;
+        A3[c] = fma(6.0 * D, jk[3 * k + c] + j1[3 * k + c], 12.0 * da) * iD3;
+        A2e[c] = fma(D, A3[c], A2[c]);
       }
-      x[k] = px[k] + A2[0] * D4 * (1.0 / 24.0) + A3[0] * D5 * (1.0 / 120.0);
-      y[k] = py[k] + A2[1] * D4 * (1.0 / 24.0) + A3[1] * D5 * (1.0 / 120.0);
-      z[k] = pz[k] + A2[2] * D4 * (1.0 / 24.0) + A3[2] * D5 * (1.0 / 120.0);
-      vx[k] = pvx[k] + A2[0] * D3 * (1.0 / 6.0) + A3[0] * D4 * (1.0 / 24.0);
-      vy[k] = pvy[k] + A2[1] * D3 * (1.0 / 6.0) + A3[1] * D4 * (1.0 / 24.0);
-      vz[k] = pvz[k] + A2[2] * D3 * (1.0 / 6.0) + A3[2] * D4 * (1.0 / 24.0);
+      /* x_p + a2 D^4/24 + a3 D^5/120, v_p + a2 D^3/6 + a3 D^4/24, fused */
+      const double c3 = D3 * (1.0 / 6.0), c4 = D4 * (1.0 / 24.0), c5 = D5 * (1.0 / 120.0);
+      x[k] = fma(A3[0], c5, fma(A2[0], c4, px[k]));
+      y[k] = fma(A3[1], c5, fma(A2[1], c4, py[k]));
+      z[k] = fma(A3[2], c5, fma(A2[2], c4, pz[k]));
+      vx[k] = fma(A3[0], c4, fma(A2[0], c3, pvx[k]));
+      vy[k] = fma(A3[1], c4, fma(A2[1], c3, pvy[k]));
+      vz[k] = fma(A3[2], c4, fma(A2[2], c3, pvz[k]));
       for (int c = 0; c < 3; ++c) { a[3 * k + c] = a1[3 * k + c]; jk[3 * k + c] = j1[3 * k + c]; }
       /* Aarseth step with j, a2, a3 scaled by s, s^2, s^3 (s = 2^e ~ D):
        * dt = sqrt(eta num_s / den_s) s */

@@ -426,7 +426,7 @@ __device__ __forceinline__ void hard_term(const V &S, int nc, int k, int j,
                rz = zk - (star ? 0.0 : S.p(2, js));
   const double ux = vxk - (star ? 0.0 : S.pv(0, js)), uy = vyk - (star ? 0.0 : S.pv(1, js)),
                uz = vzk - (star ? 0.0 : S.pv(2, js));
-  const double r2 = rx * rx + ry * ry + rz * rz;
+  const double r2 = __fma_rn(rx, rx, __fma_rn(ry, ry, rz * rz));
   if (detect && !star) {
     const double sr = prm.f_radius * (S.rp(k) + S.rp(js));
     hit = r2 < sr * sr;
@@ -447,12 +447,12 @@ __device__ __forceinline__ void hard_term(const V &S, int nc, int k, int j,
   const double rinv2 = rinv * rinv;
   const double g3 = prm.G * (star ? prm.m_star : S.m(js)) * (rinv2 * rinv);
   const double f = g3 * w;
-  const double rv = rx * ux + ry * uy + rz * uz;
+  const double rv = __fma_rn(rx, ux, __fma_rn(ry, uy, rz * uz));
   out[0] = f * rx; out[1] = f * ry; out[2] = f * rz;
-  const double c = 3.0 * w * rv * rinv2 + dK * rv * rinv * irot;
-  out[3] = g3 * (w * ux - c * rx);
-  out[4] = g3 * (w * uy - c * ry);
-  out[5] = g3 * (w * uz - c * rz);
+  const double c = __fma_rn(dK * rv * rinv, irot, 3.0 * w * rv * rinv2);
+  out[3] = g3 * __fma_rn(-c, rx, w * ux);
+  out[4] = g3 * __fma_rn(-c, ry, w * uy);
+  out[5] = g3 * __fma_rn(-c, rz, w * uz);
 }
 
 // the members with pred(k), ascending, into act[0..); returns their number
@@ -766,9 +766,10 @@ __device__ void integrate_cluster(const V &S, HCtl &C, double (*Tb)[6], int64_t 
     for (int i = item; i < nc * 3; i += NT) {
       const int k = i / 3, q = i - 3 * k;
       const double D = (double)(tn - S.t(k)) * unit;
-      const double D2 = D * D, D3 = D2 * D;
-      S.p(q, k) = S.x(q, k) + S.v(q, k) * D + S.a(q, k) * D2 * 0.5 + S.j(q, k) * D3 * (1.0 / 6.0);
-      S.pv(q, k) = S.v(q, k) + S.a(q, k) * D + S.j(q, k) * D2 * 0.5;
+      const double jq = S.j(q, k), aq = S.a(q, k), vq = S.v(q, k);
+      // Horner form, fused: x + D (v + D (a/2 + D j/6)), v + D (a + D j/2)
+      S.p(q, k) = __fma_rn(__fma_rn(__fma_rn(jq * (1.0 / 6.0), D, aq * 0.5), D, vq), D, S.x(q, k));
+      S.pv(q, k) = __fma_rn(__fma_rn(jq * 0.5, D, aq), D, vq);
     }
     __syncthreads();
     nact = build_list<NT>(S, C, nc, [&](int k) { return S.t(k) + (T >> S.lvl(k)) == tn; });
@@ -784,12 +785,13 @@ __device__ void integrate_cluster(const V &S, HCtl &C, double (*Tb)[6], int64_t 
       const double iD2 = iD * iD, iD3 = iD2 * iD;
       const double da = S.a(q, k) - S.a1(q, k);
       const double j0 = S.j(q, k), j1 = S.j1(q, k);
-      const double A2 = (-6.0 * da - D * (4.0 * j0 + 2.0 * j1)) * iD2;
-      const double A3 = (12.0 * da + 6.0 * D * (j0 + j1)) * iD3;
-      S.a2e(q, k) = A2 + D * A3;
+      const double A2 = __fma_rn(-D, __fma_rn(2.0, j1, 4.0 * j0), -6.0 * da) * iD2;
+      const double A3 = __fma_rn(6.0 * D, j0 + j1, 12.0 * da) * iD3;
+      S.a2e(q, k) = __fma_rn(D, A3, A2);
       S.a3(q, k) = A3;
-      S.x(q, k) = S.p(q, k) + A2 * D4 * (1.0 / 24.0) + A3 * D5 * (1.0 / 120.0);
-      S.v(q, k) = S.pv(q, k) + A2 * D3 * (1.0 / 6.0) + A3 * D4 * (1.0 / 24.0);
+      const double c3 = D3 * (1.0 / 6.0), c4 = D4 * (1.0 / 24.0), c5 = D5 * (1.0 / 120.0);
+      S.x(q, k) = __fma_rn(A3, c5, __fma_rn(A2, c4, S.p(q, k)));
+      S.v(q, k) = __fma_rn(A3, c4, __fma_rn(A2, c3, S.pv(q, k)));
       S.a(q, k) = S.a1(q, k);
       S.j(q, k) = j1;
     }
