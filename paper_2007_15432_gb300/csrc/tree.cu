@@ -545,45 +545,99 @@ __global__ void k_level_offsets(const int64_t *d_nnode, int64_t node_cap, const 
 // their finished children; launched level by level, deepest first.  (A grid
 // barrier between levels in one cooperative launch was measured slower than
 // the launches: its waits dominated.)
-__global__ void k_moments_level(int level, const int64_t *lvl_start, TreeNode *node,
-                                Mom64 *m64, Mom32 *m32, double *nrs, const double *box) {
-  const double u = ldexp(box[3], -P3T_BITS);
-  {
-    const int64_t b0 = lvl_start[level], b1 = lvl_start[level + 1];
-    for (int64_t b = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < b1;
-         b += (int64_t)gridDim.x * blockDim.x) {
-      TreeNode *pn = &node[b];
-      const int32_t c0 = pn->child0, nch = pn->nchild;
-      if (nch == 0) continue;  // a leaf: done already
-      double PM = 0.0, P[3] = {0, 0, 0}, prs = 0.0;
-      int32_t plo[3] = {P3T_QMAX, P3T_QMAX, P3T_QMAX}, phi[3] = {-1, -1, -1};
-      for (int k = 0; k < nch; ++k) {
-        const Mom64 &cm = m64[c0 + k];
-        PM += cm.M;
-        P[0] = __fma_rn(cm.M, cm.cx, P[0]);
-        P[1] = __fma_rn(cm.M, cm.cy, P[1]);
-        P[2] = __fma_rn(cm.M, cm.cz, P[2]);
-        prs = fmax(prs, nrs[c0 + k]);
-        const TreeNode &cn = node[c0 + k];
-        for (int a = 0; a < 3; ++a) { plo[a] = min(plo[a], cn.qlo[a]); phi[a] = max(phi[a], cn.qhi[a]); }
+// Internal nodes of one level from their finished children.  Every level is
+// small enough that its time is the latency of one warp's FP64 instruction
+// stream (one FP64 warp instruction per 64 cycles of a sub-partition), so a
+// node's children are spread over L lanes (L = 8, 4, 2 or 1, the largest that
+// keeps the level within about one warp per sub-partition), each lane summing
+// the children k = sub, sub + L, ..., and the L partial sums are added by
+// shuffles.  The loop runs in warp-uniform chunks so that every lane reaches
+// every shuffle; groups past the level's end or at leaves contribute nothing.
+__device__ __forceinline__ double shfl_down_group(double v, int o) {
+  return __shfl_xor_sync(0xffffffffu, v, o);
+}
+
+__device__ void moments_level(int level, const int64_t *lvl_start, TreeNode *node, Mom64 *m64,
+                              Mom32 *m32, double *nrs, double u, int64_t warp_target) {
+  const int64_t b0 = lvl_start[level], b1 = lvl_start[level + 1];
+  const int64_t nn = b1 - b0;
+  if (nn <= 0) return;
+  int L = 8;
+  while (L > 1 && nn * L > 32 * warp_target) L >>= 1;
+  const int lane = threadIdx.x & 31, sub = lane & (L - 1);
+  const int per_warp = 32 / L;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t wb = warp * per_warp; wb < nn; wb += nwarps * per_warp) {
+    const int64_t gi = wb + lane / L;
+    const bool valid = gi < nn;
+    const int64_t b = b0 + (valid ? gi : 0);
+    TreeNode *pn = &node[b];
+    const int32_t c0 = valid ? pn->child0 : 0, nch = valid ? pn->nchild : 0;
+    double PM = 0.0, P[3] = {0, 0, 0}, prs = 0.0;
+    int32_t plo[3] = {P3T_QMAX, P3T_QMAX, P3T_QMAX}, phi[3] = {-1, -1, -1};
+    for (int k = sub; k < nch; k += L) {
+      const Mom64 &cm = m64[c0 + k];
+      PM += cm.M;
+      P[0] = __fma_rn(cm.M, cm.cx, P[0]);
+      P[1] = __fma_rn(cm.M, cm.cy, P[1]);
+      P[2] = __fma_rn(cm.M, cm.cz, P[2]);
+      prs = fmax(prs, nrs[c0 + k]);
+      const TreeNode &cn = node[c0 + k];
+      for (int a = 0; a < 3; ++a) { plo[a] = min(plo[a], cn.qlo[a]); phi[a] = max(phi[a], cn.qhi[a]); }
+    }
+    for (int o = L >> 1; o > 0; o >>= 1) {
+      PM += shfl_down_group(PM, o);
+      for (int a = 0; a < 3; ++a) {
+        P[a] += shfl_down_group(P[a], o);
+        plo[a] = min(plo[a], __shfl_xor_sync(0xffffffffu, plo[a], o));
+        phi[a] = max(phi[a], __shfl_xor_sync(0xffffffffu, phi[a], o));
       }
-      Mom64 pm = {};
+      prs = fmax(prs, shfl_down_group(prs, o));
+    }
+    Mom64 pm = {};
+    if (nch > 0) {
       const double iM = 1.0 / PM;
       pm.M = PM; pm.cx = P[0] * iM; pm.cy = P[1] * iM; pm.cz = P[2] * iM;
-      for (int k = 0; k < nch; ++k) {
-        const Mom64 &cm = m64[c0 + k];
-        const double dx = cm.cx - pm.cx, dy = cm.cy - pm.cy, dz = cm.cz - pm.cz;
-        const double d2 = dx * dx + dy * dy + dz * dz;
-        pm.qxx += cm.qxx + cm.M * (3.0 * dx * dx - d2);
-        pm.qyy += cm.qyy + cm.M * (3.0 * dy * dy - d2);
-        pm.qzz += cm.qzz + cm.M * (3.0 * dz * dz - d2);
-        pm.qxy += cm.qxy + cm.M * (3.0 * dx * dy);
-        pm.qxz += cm.qxz + cm.M * (3.0 * dx * dz);
-        pm.qyz += cm.qyz + cm.M * (3.0 * dy * dz);
-      }
+    }
+    double Q[6] = {0, 0, 0, 0, 0, 0};  // xx, yy, zz, xy, xz, yz
+    for (int k = sub; k < nch; k += L) {
+      const Mom64 &cm = m64[c0 + k];
+      const double dx = cm.cx - pm.cx, dy = cm.cy - pm.cy, dz = cm.cz - pm.cz;
+      const double d2 = __fma_rn(dx, dx, __fma_rn(dy, dy, dz * dz));
+      const double tx = 3.0 * dx, ty = 3.0 * dy;
+      Q[0] += __fma_rn(cm.M, __fma_rn(tx, dx, -d2), cm.qxx);
+      Q[1] += __fma_rn(cm.M, __fma_rn(ty, dy, -d2), cm.qyy);
+      Q[2] += __fma_rn(cm.M, __fma_rn(3.0 * dz, dz, -d2), cm.qzz);
+      Q[3] += __fma_rn(cm.M, tx * dy, cm.qxy);
+      Q[4] += __fma_rn(cm.M, tx * dz, cm.qxz);
+      Q[5] += __fma_rn(cm.M, ty * dz, cm.qyz);
+    }
+    for (int o = L >> 1; o > 0; o >>= 1)
+      for (int q = 0; q < 6; ++q) Q[q] += shfl_down_group(Q[q], o);
+    if (valid && nch > 0 && sub == 0) {
+      pm.qxx = Q[0]; pm.qyy = Q[1]; pm.qzz = Q[2]; pm.qxy = Q[3]; pm.qxz = Q[4]; pm.qyz = Q[5];
       for (int a = 0; a < 3; ++a) { pn->qlo[a] = plo[a]; pn->qhi[a] = phi[a]; }
       nrs[b] = prs;
       finish_node(pn, m64, m32, prs, u, b, pm);
+    }
+  }
+}
+
+// levels kDeepLevel and deeper share one single-block launch
+constexpr int kDeepLevel = 12;
+
+// levels level_hi down to level_lo; several levels only with a single block
+// (a block barrier between levels)
+__global__ void k_moments_level(int level_hi, int level_lo, const int64_t *lvl_start,
+                                TreeNode *node, Mom64 *m64, Mom32 *m32, double *nrs,
+                                const double *box, int64_t warp_target) {
+  const double u = ldexp(box[3], -P3T_BITS);
+  for (int l = level_hi; l >= level_lo; --l) {
+    moments_level(l, lvl_start, node, m64, m32, nrs, u, warp_target);
+    if (l > level_lo) {
+      __threadfence_block();
+      __syncthreads();
     }
   }
 }
@@ -701,10 +755,14 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
     // internal nodes, level by level, deepest first
     int64_t *lvl_start = c->counters + 32;  // [P3T_BITS + 2]
     k_level_offsets<<<1, 32, 0, s>>>(&cnt[3], c->node_cap, c->node, lvl_start);
-    const unsigned gl = (unsigned)p3t_grid(c->node_cap, 128, (int64_t)c->num_sms * 2);
-    for (int l = P3T_BITS - 1; l >= 0; --l)
-      k_moments_level<<<gl, 128, 0, s>>>(l, lvl_start, c->node, c->mom64, c->mom32, c->nrs,
-                                         c->box);
+    // the deep levels (empty or nearly so in a disk) in one single-block
+    // launch, then one launch a level at about one warp per sub-partition
+    k_moments_level<<<1, 128, 0, s>>>(P3T_BITS - 1, kDeepLevel, lvl_start, c->node, c->mom64,
+                                      c->mom32, c->nrs, c->box, 4);
+    const int64_t wt = (int64_t)c->num_sms * 4;
+    for (int l = kDeepLevel - 1; l >= 0; --l)
+      k_moments_level<<<(unsigned)c->num_sms, 128, 0, s>>>(l, l, lvl_start, c->node, c->mom64,
+                                                           c->mom32, c->nrs, c->box, wt);
   }
   k_group_flags<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->node, c->bfs2pre,
                                                 c->prm.group_size, c->group_flag);
@@ -718,7 +776,7 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   // gather, lcp, levels, clamp, nodes_pre, pre2bfs, nodes_bfs, parents,
   // leaf_list, moments (leaves, level offsets, 21 levels), group_flags,
   // group_list
-  p3t_note_launches(18 + P3T_BITS);
+  p3t_note_launches(18 + 1 + kDeepLevel);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 
