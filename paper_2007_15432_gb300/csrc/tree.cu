@@ -60,12 +60,12 @@ __device__ __forceinline__ int cut_bin(double R, double Rmin, double Rmax,
   return k;
 }
 
-// |u|^2 and the radial bin of every particle; bin counts (integer atomics);
-// (bin, index) pairs for a stable sort by bin
+// |u|^2 and the radial bin of every particle (kept for k_cut_final); bin
+// counts (integer atomics); (bin, index) pairs for a stable sort by bin
 __global__ void k_cut_u2(int64_t n, const double *x, const double *y, const double *z,
                          const double *vx, const double *vy, const double *vz, double mu,
                          const unsigned long long *bits, int nb, double *u2, uint64_t *key,
-                         int32_t *idx, unsigned long long *bcnt) {
+                         int32_t *idx, int32_t *bin, unsigned long long *bcnt) {
   const double Rmin = ord_double(bits[0]), Rmax = ord_double(bits[1]);
   const double lmin = log(Rmin), lmax = log(Rmax);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -80,6 +80,7 @@ __global__ void k_cut_u2(int64_t n, const double *x, const double *y, const doub
     const int k = cut_bin(R, Rmin, Rmax, lmin, lmax, nb);
     key[i] = (uint64_t)k;
     idx[i] = (int32_t)i;
+    bin[i] = k;
     atomicAdd(&bcnt[k], 1ull);
   }
 }
@@ -91,11 +92,11 @@ __global__ void k_cut_offsets(int nb, const unsigned long long *bcnt, int64_t *b
   boff[nb] = o;
 }
 
-// sum of |u|^2 over each bin, one warp per bin over its members in index
-// order (a fixed lane-strided order and a fixed shuffle tree: the same sum
-// on every run)
+// v_ran of each bin, sqrt(sum |u|^2 / count), the sum by one warp per bin
+// over its members in index order (a fixed lane-strided order and a fixed
+// shuffle tree: the same sum on every run)
 __global__ void k_cut_binsum(int nb, const int64_t *boff, const int32_t *sorted_idx,
-                             const double *u2, double *bsum) {
+                             const double *u2, double *bvr) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -103,29 +104,24 @@ __global__ void k_cut_binsum(int nb, const int64_t *boff, const int32_t *sorted_
     double sum = 0.0;
     for (int64_t j = boff[k] + lane; j < boff[k + 1]; j += 32) sum += u2[sorted_idx[j]];
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) bsum[k] = sum;
+    if (lane == 0) bvr[k] = sqrt(sum / (double)(boff[k + 1] - boff[k]));
   }
 }
 
 __global__ void k_cut_final(int64_t n, const double *x, const double *y,
                             const double *z, const double *vx, const double *vy,
                             const double *vz, const double *m, p3t_params prm,
-                            unsigned long long *bits, int nb,
-                            const double *bsum, const unsigned long long *bcnt,
-                            double *r_out, double *r_search) {
+                            unsigned long long *bits, const int32_t *bin,
+                            const double *bvr, double *r_out, double *r_search) {
   const double mu = prm.G * prm.m_star;
-  const double Rmin = ord_double(bits[0]), Rmax = ord_double(bits[1]);
-  const double lmin = log(Rmin), lmax = log(Rmax);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double R = sqrt(x[i] * x[i] + y[i] * y[i]);
     double r = sqrt(x[i] * x[i] + y[i] * y[i] + z[i] * z[i]);
     double v2 = vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i];
     double alpha = 2.0 / r - v2 / mu;  // 1/a, vis-viva
     double a = alpha > 0.0 ? 1.0 / alpha : r;
     double rhill = cbrt(m[i] / (3.0 * prm.m_star)) * a;
-    int k = cut_bin(R, Rmin, Rmax, lmin, lmax, nb);
-    double vr = sqrt(bsum[k] / (double)bcnt[k]);
+    const double vr = bvr[bin[i]];
     // Eq. routi2 (P3T_CUT_HILL_VRAN) or Eq. routi (the other two); Eq. rsearch
     const double ro = prm.cutoff_mode == P3T_CUT_HILL_VRAN
                           ? fmax(prm.rcut0 * rhill, prm.rcut1 * vr * prm.dt_soft)
@@ -686,8 +682,9 @@ int p3t_run_cutoffs(p3t_ctx *c, p3t_particles *p, cudaStream_t s) {
   int64_t *boff = c->pos;
   int64_t *d_n = &c->counters[18];
   k_set_i64<<<1, 1, 0, s>>>(d_n, n);
+  int32_t *bin = c->flag;  // the bins of k_cut_u2, read by k_cut_final (N int32)
   k_cut_u2<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, p->z, p->vx, p->vy, p->vz, mu,
-                                          c->box_bits, nb, u2, c->keys, c->idx, bcnt);
+                                          c->box_bits, nb, u2, c->keys, c->idx, bin, bcnt);
   int rc = p3t_radix_sort(&c->keys, &c->idx, &c->keys_alt, &c->idx_alt, d_n, c->cap, 0, 16,
                           c->radix_hist, c->radix_hist_cap, s);
   if (rc) return rc;
@@ -695,8 +692,8 @@ int p3t_run_cutoffs(p3t_ctx *c, p3t_particles *p, cudaStream_t s) {
   k_cut_binsum<<<(unsigned)p3t_grid((int64_t)nb * 32, kBlock, (int64_t)c->num_sms * 4), kBlock, 0,
                  s>>>(nb, boff, c->idx, u2, bsum);
   k_cut_final<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, p->z, p->vx, p->vy,
-                                             p->vz, p->m, c->prm, c->box_bits, nb,
-                                             bsum, bcnt, p->r_out, p->r_search);
+                                             p->vz, p->m, c->prm, c->box_bits, bin, bsum,
+                                             p->r_out, p->r_search);
   if (c->prm.cutoff_mode == P3T_CUT_SHARED)
     k_cut_shared<<<(unsigned)g, kBlock, 0, s>>>(n, c->box_bits, p->r_out, p->r_search);
   // init, range, n, u2, offsets, bin sums, final (+ shared); the sort counts itself
