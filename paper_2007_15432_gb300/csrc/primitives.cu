@@ -168,37 +168,51 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 
+// The grids are sized for the capacity; the tiles actually holding keys
+// (from the count on the device) are dealt grid-stride, so a short sort (a
+// few thousand cluster members in a buffer sized for every particle) costs
+// little more than its launches.  hist rows keep the capacity's stride.
+__device__ __forceinline__ int64_t radix_tiles(const int64_t *d_n) {
+  return (*d_n + kSortTile - 1) / kSortTile;
+}
+
 __global__ void radix_upsweep(const uint64_t *keys, const int64_t *d_n,
                               int shift, uint32_t *hist, int ntiles) {
   __shared__ uint32_t h[kRadix];
-  h[threadIdx.x] = 0;
-  __syncthreads();
   const int64_t n = *d_n;
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  const int64_t used = radix_tiles(d_n);
   const int lane = threadIdx.x & 31;
-  for (int k = 0; k < kSortItems; ++k) {
-    const int64_t e = base + k * kSortThreads + threadIdx.x;
-    const uint32_t d = e < n ? (uint32_t)((keys[e] >> shift) & (kRadix - 1)) : kRadix;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);  // one atomic per digit and warp
-    if (d < kRadix && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
+  for (int64_t tile = blockIdx.x; tile < used; tile += gridDim.x) {
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = tile * kSortTile;
+    for (int k = 0; k < kSortItems; ++k) {
+      const int64_t e = base + k * kSortThreads + threadIdx.x;
+      const uint32_t d = e < n ? (uint32_t)((keys[e] >> shift) & (kRadix - 1)) : kRadix;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);  // one atomic per digit and warp
+      if (d < kRadix && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + tile] = h[threadIdx.x];
+    __syncthreads();
   }
-  __syncthreads();
-  hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
 // exclusive scan of each digit's row of tile counts (one block per digit);
 // the row total goes to the last slot of the digit's totals
 __global__ void __launch_bounds__(kRadix) radix_row_scan(uint32_t *hist, int ntiles,
-                                                         uint32_t *digit_total) {
+                                                         uint32_t *digit_total,
+                                                         const int64_t *d_n) {
   __shared__ int64_t sh[33];
   uint32_t *row = hist + (int64_t)blockIdx.x * ntiles;
+  const int used = (int)radix_tiles(d_n);
   int64_t carry = 0;
-  for (int base = 0; base < ntiles; base += kRadix) {
+  for (int base = 0; base < used; base += kRadix) {
     const int i = base + threadIdx.x;
-    const int64_t v = i < ntiles ? row[i] : 0;
+    const int64_t v = i < used ? row[i] : 0;
     int64_t ex;
     const int64_t tot = block_excl_scan(v, &ex, sh);
-    if (i < ntiles) row[i] = (uint32_t)(carry + ex);
+    if (i < used) row[i] = (uint32_t)(carry + ex);
     carry += tot;
   }
   if (threadIdx.x == 0) digit_total[blockIdx.x] = (uint32_t)carry;
@@ -219,72 +233,75 @@ radix_downsweep(const uint64_t *keys, const int32_t *vals, uint64_t *okeys,
   __shared__ uint64_t s_key[kSortTile];
   __shared__ int32_t s_val[kSortTile];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  s_run[t] = 0;
-  {
-    int64_t ex;
-    block_excl_scan((int64_t)digit_total[t], &ex, sh);   // digit bases
-    s_gbase[t] = (uint32_t)ex + hist[(int64_t)t * ntiles + blockIdx.x];
-  }
   const int64_t n = *d_n;
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  const uint32_t lt = (1u << lane) - 1u;
-  uint64_t key[kSortItems];
-  int32_t val[kSortItems];
-  uint32_t dig[kSortItems], rk[kSortItems];
-#pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
-#pragma unroll
-    for (int k = 0; k < kSortThreads / 32; ++k) s_warp[k][t] = 0;
+  const int64_t used = radix_tiles(d_n);
+  if (blockIdx.x >= used) return;  // no tile of this sort for this block
+  int64_t dbase;
+  block_excl_scan((int64_t)digit_total[t], &dbase, sh);   // digit bases
+  for (int64_t tile = blockIdx.x; tile < used; tile += gridDim.x) {
     __syncthreads();
-    const int64_t e = base + r * kSortThreads + t;
-    const bool valid = e < n;
-    key[r] = 0;
-    val[r] = 0;
-    uint32_t d = kRadix;  // invalid lanes form their own group
-    if (valid) {
-      key[r] = keys[e];
-      val[r] = vals[e];
-      d = (uint32_t)((key[r] >> shift) & (kRadix - 1));
-    }
-    dig[r] = d;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    if (valid && lane == __ffs(peers) - 1) s_warp[w][d] = __popc(peers);
-    __syncthreads();
-    {
-      uint32_t run = s_run[t];
+    s_run[t] = 0;
+    s_gbase[t] = (uint32_t)dbase + hist[(int64_t)t * ntiles + tile];
+    const int64_t base = tile * kSortTile;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint64_t key[kSortItems];
+    int32_t val[kSortItems];
+    uint32_t dig[kSortItems], rk[kSortItems];
 #pragma unroll
-      for (int k = 0; k < kSortThreads / 32; ++k) {
-        uint32_t c = s_warp[k][t];
-        s_warp[k][t] = run;
-        run += c;
+    for (int r = 0; r < kSortItems; ++r) {
+#pragma unroll
+      for (int k = 0; k < kSortThreads / 32; ++k) s_warp[k][t] = 0;
+      __syncthreads();
+      const int64_t e = base + r * kSortThreads + t;
+      const bool valid = e < n;
+      key[r] = 0;
+      val[r] = 0;
+      uint32_t d = kRadix;  // invalid lanes form their own group
+      if (valid) {
+        key[r] = keys[e];
+        val[r] = vals[e];
+        d = (uint32_t)((key[r] >> shift) & (kRadix - 1));
       }
-      s_run[t] = run;
-    }
-    __syncthreads();
-    rk[r] = valid ? s_warp[w][d] + __popc(peers & lt) : 0;  // rank within the tile's digit
-    __syncthreads();
-  }
-  {
-    int64_t ex;
-    block_excl_scan((int64_t)s_run[t], &ex, sh);
-    s_lbase[t] = (uint32_t)ex;
-  }
-  __syncthreads();
+      dig[r] = d;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      if (valid && lane == __ffs(peers) - 1) s_warp[w][d] = __popc(peers);
+      __syncthreads();
+      {
+        uint32_t run = s_run[t];
 #pragma unroll
-  for (int r = 0; r < kSortItems; ++r)
-    if (dig[r] < kRadix) {
-      const uint32_t pos = s_lbase[dig[r]] + rk[r];
-      s_key[pos] = key[r];
-      s_val[pos] = val[r];
+        for (int k = 0; k < kSortThreads / 32; ++k) {
+          uint32_t c = s_warp[k][t];
+          s_warp[k][t] = run;
+          run += c;
+        }
+        s_run[t] = run;
+      }
+      __syncthreads();
+      rk[r] = valid ? s_warp[w][d] + __popc(peers & lt) : 0;  // rank within the tile's digit
+      __syncthreads();
     }
-  __syncthreads();
-  const int64_t tn = n - base < kSortTile ? n - base : kSortTile;
-  for (int i = t; i < tn; i += kSortThreads) {
-    const uint64_t k = s_key[i];
-    const uint32_t d = (uint32_t)((k >> shift) & (kRadix - 1));
-    const uint32_t dst = s_gbase[d] + ((uint32_t)i - s_lbase[d]);
-    okeys[dst] = k;
-    ovals[dst] = s_val[i];
+    {
+      int64_t ex;
+      block_excl_scan((int64_t)s_run[t], &ex, sh);
+      s_lbase[t] = (uint32_t)ex;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r)
+      if (dig[r] < kRadix) {
+        const uint32_t pos = s_lbase[dig[r]] + rk[r];
+        s_key[pos] = key[r];
+        s_val[pos] = val[r];
+      }
+    __syncthreads();
+    const int64_t tn = n - base < kSortTile ? n - base : kSortTile;
+    for (int i = t; i < tn; i += kSortThreads) {
+      const uint64_t k = s_key[i];
+      const uint32_t d = (uint32_t)((k >> shift) & (kRadix - 1));
+      const uint32_t dst = s_gbase[d] + ((uint32_t)i - s_lbase[d]);
+      okeys[dst] = k;
+      ovals[dst] = s_val[i];
+    }
   }
 }
 
@@ -322,7 +339,7 @@ int p3t_radix_sort(uint64_t **keys, int32_t **vals, uint64_t **keys_alt,
   for (int shift = begin_bit; shift < end_bit; shift += kRadixBits) {
     radix_upsweep<<<(unsigned)ntiles, kSortThreads, 0, s>>>(*keys, d_n, shift,
                                                             hist, (int)ntiles);
-    radix_row_scan<<<kRadix, kRadix, 0, s>>>(hist, (int)ntiles, digit_total);
+    radix_row_scan<<<kRadix, kRadix, 0, s>>>(hist, (int)ntiles, digit_total, d_n);
     radix_downsweep<<<(unsigned)ntiles, kSortThreads, 0, s>>>(
         *keys, *vals, *keys_alt, *vals_alt, d_n, shift, hist, (int)ntiles, digit_total);
     p3t_note_launches(3);
