@@ -147,7 +147,11 @@ __global__ void __launch_bounds__(kDW * 32, MIXED ? P3T_DIRECT_MINB_MIXED : 1)
   __shared__ Q4<T> sA[kDW][32];                     // x_hi, y_hi, z_hi, m
   __shared__ Q4<T> sB[kDW][32];                     // x_lo, y_lo, z_lo, 1 / r_out
   __shared__ Q4<T> sL[VJP ? kDW : 1][VJP ? 32 : 1];  // lam
-  __shared__ double red[kDW][NC][kDTB];
+  // the 8 warps' sums: FP64, or (MIXED) float-float pairs added with FP32
+  // instructions only (an FP64 instruction costs 64 FP32 issue slots here)
+  __shared__ double red[MIXED ? 1 : kDW][NC][MIXED ? 1 : kDTB];
+  __shared__ float red_h[MIXED ? kDW : 1][NC][MIXED ? kDTB : 1];
+  __shared__ float red_l[MIXED ? kDW : 1][NC][MIXED ? kDTB : 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const T g = (T)gamma, i1mg = (T)(1.0 / (1.0 - gamma));
 
@@ -224,16 +228,30 @@ __global__ void __launch_bounds__(kDW * 32, MIXED ? P3T_DIRECT_MINB_MIXED : 1)
 #pragma unroll
   for (int t = 0; t < kDT; ++t)
 #pragma unroll
-    for (int c = 0; c < NC; ++c)
-      red[warp][c][t * 32 + lane] =
-          MIXED ? (double)fh[t][c] + (double)fl[t][c] : dd[t][c];
+    for (int c = 0; c < NC; ++c) {
+      if constexpr (MIXED) {
+        red_h[warp][c][t * 32 + lane] = fh[t][c];
+        red_l[warp][c][t * 32 + lane] = fl[t][c];
+      } else {
+        red[warp][c][t * 32 + lane] = dd[t][c];
+      }
+    }
   __syncthreads();
   for (int e = threadIdx.x; e < NC * kDTB; e += kDW * 32) {
     const int c = e / kDTB, tt = e - c * kDTB;
     const int64_t k = (int64_t)blockIdx.x * kDTB + tt;
     if (k >= n) continue;
     double s = 0.0;
-    for (int w = 0; w < kDW; ++w) s += red[w][c][tt];
+    if constexpr (MIXED) {
+      float h = red_h[0][c][tt], l = red_l[0][c][tt];
+      for (int w = 1; w < kDW; ++w) {
+        two_sum_acc(h, l, red_h[w][c][tt]);
+        l += red_l[w][c][tt];
+      }
+      s = (double)h + (double)l;
+    } else {
+      for (int w = 0; w < kDW; ++w) s += red[w][c][tt];
+    }
     if (gridDim.y == 1) {
       double *o = c == 0 ? out.o[0] : (c == 1 ? out.o[1] : (c == 2 ? out.o[2] : out.o[3]));
       o[k] = (out.add ? o[k] : 0.0) + out.scale * s;

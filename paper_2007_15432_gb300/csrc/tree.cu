@@ -61,11 +61,16 @@ __device__ __forceinline__ int cut_bin(double R, double Rmin, double Rmax,
 }
 
 // |u|^2 and the radial bin of every particle (kept for k_cut_final); bin
-// counts (integer atomics); (bin, index) pairs for a stable sort by bin
+// counts (integer atomics, first into the block's shared histogram);
+// (bin, index) pairs for a stable sort by bin
+constexpr int kMaxBins = 4096;
 __global__ void k_cut_u2(int64_t n, const double *x, const double *y, const double *z,
                          const double *vx, const double *vy, const double *vz, double mu,
                          const unsigned long long *bits, int nb, double *u2, uint64_t *key,
                          int32_t *idx, int32_t *bin, unsigned long long *bcnt) {
+  __shared__ uint32_t h[kMaxBins];
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) h[k] = 0;
+  __syncthreads();
   const double Rmin = ord_double(bits[0]), Rmax = ord_double(bits[1]);
   const double lmin = log(Rmin), lmax = log(Rmax);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -81,15 +86,48 @@ __global__ void k_cut_u2(int64_t n, const double *x, const double *y, const doub
     key[i] = (uint64_t)k;
     idx[i] = (int32_t)i;
     bin[i] = k;
-    atomicAdd(&bcnt[k], 1ull);
+    atomicAdd(&h[k], 1u);
   }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nb; k += blockDim.x)
+    if (h[k]) atomicAdd(&bcnt[k], (unsigned long long)h[k]);
 }
 
-// exclusive offsets of the bins (one thread: at most 4096 bins)
+// exclusive offsets of the bins (at most 4096): one block, chunks of its
+// size scanned with warp shuffles and carried
 __global__ void k_cut_offsets(int nb, const unsigned long long *bcnt, int64_t *boff) {
-  int64_t o = 0;
-  for (int k = 0; k < nb; ++k) { boff[k] = o; o += (int64_t)bcnt[k]; }
-  boff[nb] = o;
+  __shared__ int64_t wsum[32];
+  __shared__ int64_t carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += blockDim.x) {
+    const int k = base + threadIdx.x;
+    const int64_t v = k < nb ? (int64_t)bcnt[k] : 0;
+    int64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      const int64_t w0 = lane < nw ? wsum[lane] : 0;
+      int64_t y = w0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) y += t;
+      }
+      if (lane < nw) wsum[lane] = y - w0;
+    }
+    __syncthreads();
+    const int64_t ex = carry + wsum[warp] + (x - v);
+    if (k < nb) boff[k] = ex;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = ex + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) boff[nb] = carry;
 }
 
 // v_ran of each bin, sqrt(sum |u|^2 / count), the sum by one warp per bin
@@ -688,7 +726,7 @@ int p3t_run_cutoffs(p3t_ctx *c, p3t_particles *p, cudaStream_t s) {
   int rc = p3t_radix_sort(&c->keys, &c->idx, &c->keys_alt, &c->idx_alt, d_n, c->cap, 0, 16,
                           c->radix_hist, c->radix_hist_cap, s);
   if (rc) return rc;
-  k_cut_offsets<<<1, 1, 0, s>>>(nb, bcnt, boff);
+  k_cut_offsets<<<1, 1024, 0, s>>>(nb, bcnt, boff);
   k_cut_binsum<<<(unsigned)p3t_grid((int64_t)nb * 32, kBlock, (int64_t)c->num_sms * 4), kBlock, 0,
                  s>>>(nb, boff, c->idx, u2, bsum);
   k_cut_final<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, p->z, p->vx, p->vy,
