@@ -841,11 +841,18 @@ __global__ void __launch_bounds__(NT) k_hermite_block(
   const bool coll = prm.f_radius > 0.0 && p.r_phys != nullptr;
   unsigned long long steps = 0;
   bool underflow = false;
-  for (;;) {
-    if (tid == 0) C.cluster = atomicAdd(reinterpret_cast<unsigned long long *>(cursor), 1ull);
-    __syncthreads();
-    const int64_t c = C.cluster;
-    __syncthreads();
+  for (int64_t k = blockIdx.x;; k += gridDim.x) {
+    // clusters of up to 128 members are handed out by a cursor (a long
+    // encounter keeps its block while the others move on); the rare larger
+    // ones are dealt statically, so that this kernel's few blocks do not take
+    // a cursor step for every small cluster
+    int64_t c = k;
+    if constexpr (!BIG) {
+      if (tid == 0) C.cluster = atomicAdd(reinterpret_cast<unsigned long long *>(cursor), 1ull);
+      __syncthreads();
+      c = C.cluster;
+      __syncthreads();
+    }
     if (c >= ncl) break;
     const int64_t off = cl_off[c];
     const int nc = (int)(cl_off[c + 1] - off);
