@@ -70,8 +70,9 @@ def parse():
                     help="time one gradient of the 32-step soft KDK rollout at N=1e4")
     ap.add_argument("--adjoint-n", type=int, default=10_000)
     ap.add_argument("--ensemble", action="store_true",
-                    help="the batched ensemble of 256 independent disks: one CUDA graph per "
-                         "step vs the same disks stepped one after another")
+                    help="the ensemble of 256 independent disks: batched in one context "
+                         "(one launch sequence per step) vs per-disk contexts in one CUDA "
+                         "graph vs per-disk contexts one after another")
     ap.add_argument("--cutoff-sweep", action="store_true",
                     help="compare the cut-off schemes (shared / individual / individual with "
                          "random velocity) over R~cut,0 on the mass-spectrum ring; one JSON "
@@ -260,7 +261,7 @@ def run_ours(args):
     st = P.State.from_numpy(s, device=dev, r_phys=disks.physical_radius(s["m"]))
     ss = P.SoftStep(prm, st, device=local)
     stream = torch.cuda.current_stream(dev)
-    ss.init(update_cutoffs=True)            # row a1 at init, then after merges
+    ss.init(update_cutoffs=True)            # cut-off radii at init, then after merges
     torch.cuda.synchronize(dev)
     ss.status()
 
@@ -312,7 +313,7 @@ def run_ours(args):
     m_start = float(st.m.sum().item())
 
     energy = torch.zeros(2, 4, dtype=torch.float64, device=dev)
-    P.p3t_energy(ss.ctx, st, energy[0], stream)   # row a10, outside the timed region
+    P.p3t_energy(ss.ctx, st, energy[0], stream)   # energy, outside the timed region
     e_disp[0] = e_disp[1] = 0.0
     merged[0] = 0
     counts_all.zero_()
@@ -523,10 +524,14 @@ def run_cutoff_sweep(args):
 def run_ensemble(args):
     """256 independent disks (sizes round(exp U(ln 512, ln 16384)), seeds
     4000 + d; even disks equal-mass rings, odd disks power-law wide disks), no
-    collisions.  Group sizes per disk-size class from the autotuner.  One
-    ensemble soft step = one replay of a captured CUDA graph (disks forked
-    over 16 streams); compared with the same kernels issued disk after disk
-    on one stream.  Value: pair interactions of all disks per second."""
+    collisions.  Three ways to step them, each timed over the same K steps:
+    batched (one context, every disk a segment of one particle set, so one
+    launch sequence per step for all disks; group size from the batched
+    autotuner; replayed as a captured CUDA graph), per-disk contexts in a
+    captured graph (disks forked over 16 streams; group sizes per disk-size
+    class from the per-disk autotuner) and the per-disk kernels issued disk
+    after disk on one stream.  Value: pair interactions of all disks per
+    second of the batched step."""
     import torch
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
@@ -536,6 +541,36 @@ def run_ensemble(args):
     from paper_2007_15432_gb300 import p3t as P
     ds = disks.ensemble_disks()
     base = P.Params(theta=0.5, precision=P.P3T_MIXED, eta=0.01, eta0=0.001)
+    K, W = args.steps, args.warmup
+
+    def timed(run, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            run()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / 1e3
+
+    # batched
+    ens = EN.Ensemble(ds, [base] * len(ds), batched=True)
+    ens.init()
+    t0 = time.perf_counter()
+    gs_b = ens.autotune_batched()
+    t_tune_b = time.perf_counter() - t0
+    l0 = P.p3t_launch_count()
+    ens.step_sequential()
+    launches_b = P.p3t_launch_count() - l0
+    ens.capture()
+    for _ in range(W):
+        ens.step_graph()
+    torch.cuda.synchronize(dev)
+    t_b = timed(ens.step_graph, K)
+    ens.status()
+    inter_b = ens.interactions()
+    ens.close()
+
+    # per-disk contexts
     t0 = time.perf_counter()
     tune = EN.autotune(ds, base)
     t_tune = time.perf_counter() - t0
@@ -544,20 +579,11 @@ def run_ensemble(args):
         p = P.Params(**{f[0]: getattr(base, f[0]) for f in P.Params._fields_})
         p.group_size = tune[EN.size_class(len(d["m"]))]
         params.append(p)
-
-    def timed(run, k):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        inter = 0
-        e0.record()
-        for _ in range(k):
-            run()
-        e1.record()
-        torch.cuda.synchronize(dev)
-        return e0.elapsed_time(e1) / 1e3
-
-    K, W = args.steps, args.warmup
     ens = EN.Ensemble(ds, params)
     ens.init()
+    l0 = P.p3t_launch_count()
+    ens.step_sequential()
+    launches_d = P.p3t_launch_count() - l0
     ens.capture()
     for _ in range(W):
         ens.step_graph()
@@ -565,25 +591,28 @@ def run_ensemble(args):
     t_graph = timed(ens.step_graph, K)
     ens.status()
     inter = ens.interactions()
-    ens.close()
-    seq = EN.Ensemble(ds, params)
-    seq.init()
     for _ in range(W):
-        seq.step_sequential()
+        ens.step_sequential()
     torch.cuda.synchronize(dev)
-    t_seq = timed(seq.step_sequential, K)
-    seq.status()
-    inter_seq = seq.interactions()
-    seq.close()
+    t_seq = timed(ens.step_sequential, K)
+    ens.status()
+    inter_seq = ens.interactions()
+    ens.close()
     line = dict(metric="ensemble soft step: pair-interactions/s of all disks", study="ensemble",
-                value=inter / (t_graph / K), unit=UNIT, n_gpus=1, steps=K, warmup=W,
-                ms_per_step=1e3 * t_graph / K, higher_is_better=True,
+                value=inter_b / (t_b / K), unit=UNIT, n_gpus=1, steps=K, warmup=W,
+                ms_per_step=1e3 * t_b / K, higher_is_better=True,
+                gpu_launches=launches_b * K,
+                batched=dict(group_size=gs_b, autotune_s=t_tune_b, launches_per_step=launches_b),
+                per_disk_graph=dict(value=inter / (t_graph / K), ms_per_step=1e3 * t_graph / K,
+                                    launches_per_step=launches_d, streams=16,
+                                    group_size_by_log2_n={str(k): v
+                                                          for k, v in sorted(tune.items())},
+                                    autotune_s=t_tune),
                 sequential=dict(value=inter_seq / (t_seq / K), ms_per_step=1e3 * t_seq / K),
-                speedup=(t_seq / K) / (t_graph / K), dtype="f32/f64", data="synthetic (seeded disks)",
+                speedup_vs_per_disk_graph=t_graph / t_b, speedup_vs_sequential=t_seq / t_b,
+                dtype="f32/f64", data="synthetic (seeded disks)",
                 config=dict(workload="ensemble of 256 disks, sizes round(exp U(ln 512, ln 16384))",
-                            n_total=int(sum(len(d["m"]) for d in ds)), streams=16,
-                            group_size_by_log2_n={str(k): v for k, v in sorted(tune.items())},
-                            autotune_s=t_tune))
+                            n_total=int(sum(len(d["m"]) for d in ds))))
     print(json.dumps(line), flush=True)
     return 0
 

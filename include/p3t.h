@@ -138,7 +138,30 @@ int p3t_set_params(p3t_ctx *ctx, const p3t_params *p);
  * themselves, which allocates and is then not capturable. */
 int p3t_reserve(p3t_ctx *ctx, int64_t n);
 
-/* Row a1 -- cut-off and search radii, Eq. routi2 and Eq. rsearch:
+/* Batched ensemble: the particles of the following calls form nseg
+ * independent systems (disks) stored one after another, system d being
+ * [seg_off[d], seg_off[d + 1]) (host array of nseg + 1 offsets, seg_off[0]
+ * = 0, strictly increasing, copied; the sum below 2^31).  With nseg > 1
+ * every stage keeps the systems apart exactly as if each had a context of
+ * its own, and each system gets the same bits as it would alone: the cut-off
+ * radii use each system's own radial bins (Sec. 2.1.3; the bins of all
+ * systems together at most 4096, else P3T_ERR_INVALID from the cut-off
+ * calls), each system gets its own root cube, key grid and octree (one tree
+ * per system in the shared node arrays; the root of system d is node d), the
+ * walk of a target group starts at its system's root, so no force,
+ * neighbour or cluster links two systems (Sec. 2.3: clusters are
+ * independent).  One group size, leaf size and parameter set for all.  The
+ * particle count of later calls must equal seg_off[nseg] (else
+ * P3T_ERR_INVALID); p3t_energy, p3t_merge, p3t_soft_force_direct and
+ * p3t_soft_force_vjp return P3T_ERR_INVALID while nseg > 1.  nseg = 1
+ * restores the single system.  Returns P3T_ERR_INVALID for bad offsets or
+ * nseg outside [1, 4096] (the context keeps its previous segments) and
+ * P3T_ERR_CUDA when an allocation fails (the context is then a single
+ * system).  Synchronises the device and allocates: call it before any graph
+ * capture; it drops the context's tree. */
+int p3t_set_segments(p3t_ctx *ctx, int64_t nseg, const int64_t *seg_off);
+
+/* Cut-off and search radii, Eq. routi2 and Eq. rsearch:
  *   r_out,i    = max(R~cut,0 r_Hill,i, R~cut,1 v_ran,i dt_soft),
  *   r_Hill,i   = (m_i / 3M_*)^(1/3) a_i, a_i the osculating semi-major axis
  *                (a_i = |x_i| for an unbound orbit),
@@ -148,7 +171,7 @@ int p3t_reserve(p3t_ctx *ctx, int64_t n);
  * p->r_search. */
 int p3t_cutoffs(p3t_ctx *ctx, p3t_particles *p, void *stream);
 
-/* Row a1 without a context and without any allocation.  The paper has no
+/* Cut-off and search radii without a context and without any allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
  * cudaMalloc -- an application that owns all device memory through its own
  * pool and forbids other allocations (a plugin host, a framework with a fixed
@@ -175,7 +198,7 @@ int p3t_cutoffs(p3t_ctx *ctx, p3t_particles *p, void *stream);
  *    P3T_ERR_CUDA (the lookup or a launch failed). */
 int p3t_cutoffs_noalloc(const p3t_params *prm, p3t_particles *p, void *stream);
 
-/* Rows a2-a3 -- Morton keys on the 21-bit grid of the cubic bounding box,
+/* Morton keys on the 21-bit grid of the cubic bounding box,
  * stable sort by (key, index), octree (split while > leaf_size particles and
  * level < 21), per node mass, centre of mass, traceless quadrupole
  * Q_ab = sum m (3 d_a d_b - d^2 delta_ab), quantised tight box and search
@@ -185,7 +208,7 @@ int p3t_cutoffs_noalloc(const p3t_params *prm, p3t_particles *p, void *stream);
 int p3t_build_tree(p3t_ctx *ctx, p3t_particles *p, int update_cutoffs,
                    void *stream);
 
-/* Row a4 -- soft acceleration, Eq. softforce:
+/* Soft acceleration, Eq. softforce:
  *   a_i = -sum_j G m_j K(r_ij / r_out,ij) r_ij / r_ij^3,
  *   r_out,ij = max(r_out,i, r_out,j) (Eq. rout2), K the changeover of
  *   Sec. 2.1.1 (zero below gamma, one above 1),
@@ -201,7 +224,7 @@ int p3t_build_tree(p3t_ctx *ctx, p3t_particles *p, int update_cutoffs,
 int p3t_soft_force(p3t_ctx *ctx, const p3t_particles *p, double *ax, double *ay,
                    double *az, uint64_t *counts, void *stream);
 
-/* Rows a5-a6 -- neighbour lists and clusters, Sec. 2.3:
+/* Neighbour lists and clusters, Sec. 2.3:
  * a candidate j of i stays a neighbour iff r_ij < r_search,ij and either its
  * closest approach under linear motion over [0, dt_soft] (Eq. rsearch1 with
  * t_min) is at most R~s,2 r_out,ij, or v_ij < R~s,3 a_ij dt_soft / 2 with
@@ -218,7 +241,7 @@ int p3t_neighbours(p3t_ctx *ctx, const p3t_particles *p, int64_t *nb_off,
                    int32_t *nb_idx, int64_t nb_cap, p3t_clusters *out,
                    void *stream);
 
-/* Rows a8-a9 -- hard part over [0, dt] (procedure step 5, Eq. hardforce):
+/* Hard part over [0, dt] (procedure step 5, Eq. hardforce):
  * every cluster of >= 2 members is integrated with the fourth-order Hermite
  * predictor-corrector and block individual time steps (dt / 2^k, k <= 40;
  * Aarseth step with eta, first step eta0 |a|/|j|), under the star and the
@@ -237,22 +260,22 @@ int p3t_neighbours(p3t_ctx *ctx, const p3t_particles *p, int64_t *nb_off,
 int p3t_hard_step(p3t_ctx *ctx, p3t_particles *p, const p3t_clusters *cl,
                   double dt, uint64_t *n_steps, void *stream);
 
-/* Row a9 for every particle -- the Kepler drift of p3t_hard_step applied to
+/* The Kepler drift of p3t_hard_step applied to
  * all particles of p by dt (mu = G M_*), with no cluster integrated: the
  * drift of a rollout whose particles are all treated as isolated (the
- * row-f2 adjoint's forward map).  Positions and velocities updated in place;
+ * adjoint's forward map).  Positions and velocities updated in place;
  * a drift whose Newton iteration does not converge is reported as
  * P3T_ERR_TIMEOUT by p3t_status. */
 int p3t_kepler_drift(p3t_ctx *ctx, p3t_particles *p, double dt, void *stream);
 
-/* Row a7 -- soft kick (procedure steps 3 and 8): v += a * h, h usually
+/* Soft kick (procedure steps 3 and 8): v += a * h, h usually
  * dt_soft / 2.  ax, ay, az: n doubles each, caller order.  Members of a
  * composite formed by the last p3t_hard_step (f_radius > 0) are kicked with
  * the composite's mass-weighted mean acceleration (Sec. 2.4.1). */
 int p3t_kick(p3t_ctx *ctx, p3t_particles *p, const double *ax, const double *ay,
              const double *az, double h, void *stream);
 
-/* Procedure step 9 for collisions (Sec. 2.4.1; row f4 beyond the soft step):
+/* Procedure step 9 for collisions (Sec. 2.4.1, beyond the soft step):
  * replaces every composite formed by the last p3t_hard_step by one particle
  * at the lowest index of its members, with mass sum m_l, physical radius
  * (sum R_l^3)^(1/3) (one density for all bodies) and the members' common
@@ -269,7 +292,7 @@ int p3t_kick(p3t_ctx *ctx, p3t_particles *p, const double *ax, const double *ay,
 int p3t_merge(p3t_ctx *ctx, p3t_particles *p, int32_t *new_index, double *e_disp,
               int64_t *n_merged, void *stream);
 
-/* Row a6 at theta = 0 (and the forward force of the row-f2 adjoint) -- the
+/* The soft force at theta = 0 (and the forward force of the adjoint) -- the
  * soft force of Eq. softforce summed directly over all pairs, which is what
  * the tree walk gives at theta = 0:
  *   a_i = -G sum_{j != i} m_j K(r_ij / r_out,ij) r_ij / r_ij^3,
@@ -281,7 +304,7 @@ int p3t_merge(p3t_ctx *ctx, p3t_particles *p, int32_t *new_index, double *e_disp
 int p3t_soft_force_direct(p3t_ctx *ctx, const p3t_particles *p, double *ax, double *ay,
                           double *az, void *stream);
 
-/* Row f2 (adjoint of the soft kick-drift-kick; the paper has no counterpart:
+/* Adjoint of the soft kick-drift-kick (the paper has no counterpart:
  * a gradient of a trajectory with respect to its initial state) -- the
  * vector-Jacobian product of the soft force of Eq. softforce with the cut-off
  * radii held fixed, taken for the direct sum over all pairs (the force the
@@ -299,15 +322,15 @@ int p3t_soft_force_vjp(p3t_ctx *ctx, const p3t_particles *p, double h, const dou
                        const double *ly, const double *lz, double *gx, double *gy, double *gz,
                        double *gm, void *stream);
 
-/* Row f2 -- the adjoint of the Kepler drift of every particle of p by dt
- * (row a9's map, mu = G M_*): on entry lx..lvz hold the adjoint of the state
+/* The adjoint of the Kepler drift of every particle of p by dt
+ * (the drift's map, mu = G M_*): on entry lx..lvz hold the adjoint of the state
  * after the drift, on return the adjoint of the state before it (Phi^T lam,
  * Phi the state-transition matrix at the state p holds, which is the state
  * BEFORE the drift).  Device arrays, n each, caller order. */
 int p3t_kepler_vjp(p3t_ctx *ctx, const p3t_particles *p, double dt, double *lx, double *ly,
                    double *lz, double *lvx, double *lvy, double *lvz, void *stream);
 
-/* Row a10 -- total energy (Eqs. soft and hard; W + (1 - W) = 1 makes it the
+/* Total energy (Eqs. soft and hard; W + (1 - W) = 1 makes it the
  * Newtonian energy): out = device double[4] {E, kinetic, star potential,
  * pair potential}.  The pair sum is direct O(n^2), in FP64 for P3T_FP64 and
  * as FP32 terms on float-float relative coordinates with float-float sums for

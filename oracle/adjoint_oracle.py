@@ -1,4 +1,4 @@
-"""Plain FP64 CPU oracle of the adjoint of the soft kick-drift-kick (row f2).
+"""Plain FP64 CPU oracle of the adjoint of the soft kick-drift-kick.
 
 TEST INFRASTRUCTURE ONLY: used by ``tests/`` to check the GPU adjoint.  It
 shares no code with the CUDA path.

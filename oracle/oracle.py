@@ -147,7 +147,7 @@ def num_threads() -> int:
 
 
 def cutoffs(s: dict, p: Params):
-    """Row a1.  Returns (r_out, r_search, v_ran, bin)."""
+    """Cut-off and search radii.  Returns (r_out, r_search, v_ran, bin)."""
     n = len(s["m"])
     ro, rs, vr = np.empty(n), np.empty(n), np.empty(n)
     b = np.empty(n, dtype=np.int32)
@@ -186,7 +186,7 @@ class SoftResult:
 
 def tree_soft(s: dict, r_out, r_search, p: Params, targets=None,
               cand_cap: int | None = None) -> SoftResult:
-    """Rows a2-a4: tree soft force, interaction counts and neighbour candidates."""
+    """Tree soft force, interaction counts and neighbour candidates."""
     n = len(s["m"])
     ax, ay, az = np.zeros(n), np.zeros(n), np.zeros(n)
     counts = np.zeros(2, dtype=np.uint64)
@@ -241,7 +241,7 @@ def _csr_call(fn, n, pre, post):
 
 
 def neighbours_from_candidates(s: dict, r_out, r_search, p: Params, cand_i, cand_j):
-    """Row a5: exact neighbour predicate on the walk's candidates -> CSR."""
+    """Exact neighbour predicate on the walk's candidates -> CSR."""
     n = len(s["m"])
     cp = p.c()
     ci = np.ascontiguousarray(cand_i, dtype=np.int32)
@@ -252,7 +252,7 @@ def neighbours_from_candidates(s: dict, r_out, r_search, p: Params, cand_i, cand
 
 
 def neighbours_brute(s: dict, r_out, r_search, p: Params):
-    """Row a5 by brute force over all ordered pairs (small N only)."""
+    """The neighbour predicate by brute force over all ordered pairs (small N only)."""
     n = len(s["m"])
     cp = p.c()
     pre = [n] + [_f64(s[k]) for k in ("x", "y", "z", "vx", "vy", "vz", "m")] + [
@@ -276,7 +276,7 @@ class Clusters:
 
 
 def clusters(n: int, nb_off, nb_idx) -> Clusters:
-    """Row a6: the paper's min-label propagation, then compaction."""
+    """Neighbour clusters: the paper's min-label propagation, then compaction."""
     label = np.empty(n, dtype=np.int32)
     singles = np.empty(max(n, 1), dtype=np.int32)
     cl_off = np.zeros(max(n, 1) + 1, dtype=np.int64)
@@ -310,7 +310,7 @@ def _vptr(a):
 def hermite_cluster(s: dict, r_out, p: Params, members, dt: float, r_phys=None,
                     with_sets: bool = False):
     """Integrates the members of one cluster in place; returns (status, steps),
-    or (status, steps, roots, e_disp) with ``with_sets`` (row f4: ``roots`` the
+    or (status, steps, roots, e_disp) with ``with_sets`` (collisions: ``roots`` the
     lowest member of each member's composite, cluster-local; ``e_disp`` the
     dissipated energy).  ``r_phys`` (physical radii, caller order) switches the
     collision test on when ``p.f_radius > 0``."""
@@ -337,8 +337,8 @@ def kepler_drift(s: dict, dt: float, mu: float, idx=None) -> int:
 
 def hard_step(s: dict, r_out, p: Params, cl: Clusters, dt: float, r_phys=None,
               with_sets: bool = False):
-    """Rows a8 + a9 in place; returns (status, hermite particle-steps), or with
-    ``with_sets`` also (comp_root, e_hard): row f4's composites (lowest member's
+    """Hard step and Kepler drift in place; returns (status, hermite particle-steps), or with
+    ``with_sets`` also (comp_root, e_hard): the collision composites (lowest member's
     caller index, -1 outside composites) and the collisions' dissipation."""
     ns = C.c_int64(0)
     eh = C.c_double(0.0)
@@ -358,7 +358,7 @@ def hard_step(s: dict, r_out, p: Params, cl: Clusters, dt: float, r_phys=None,
 
 
 def kick_composites(s: dict, acc, h: float, comp_root):
-    """Row f4: kick with composite members given their composite's mass-weighted
+    """Collisions: kick with composite members given their composite's mass-weighted
     mean soft acceleration; returns the dissipated energy."""
     n = len(s["m"])
     return lib().or_kick_composites(n, s["vx"], s["vy"], s["vz"], _f64(acc[:, 0]),
@@ -367,7 +367,7 @@ def kick_composites(s: dict, acc, h: float, comp_root):
 
 
 def merge(s: dict, r_phys, r_out, r_search, comp_root):
-    """Row f4 (procedure step 9): replaces every composite by one particle.
+    """Collisions (procedure step 9): replaces every composite by one particle.
     Returns (new state dict, r_phys, r_out, r_search, new_index)."""
     n = len(s["m"])
     a = {k: np.array(s[k], dtype=np.float64, copy=True) for k in ("x", "y", "z", "vx", "vy", "vz", "m")}
@@ -380,7 +380,7 @@ def merge(s: dict, r_phys, r_out, r_search, comp_root):
 
 
 def energy(s: dict, G: float = 1.0, m_star: float = 1.0):
-    """Row a10: (E, kinetic, star potential, pair potential)."""
+    """Total energy: (E, kinetic, star potential, pair potential)."""
     out = np.empty(4)
     lib().or_energy(len(s["m"]), *[_f64(s[k]) for k in ("x", "y", "z", "vx", "vy", "vz", "m")],
                     float(G), float(m_star), out)
@@ -393,7 +393,7 @@ def soft_step(s: dict, r_out, r_search, p: Params, acc, cl: Clusters, r_phys=Non
     ``acc`` and ``cl`` are the soft acceleration and the clusters from the
     previous force evaluation.  Returns (acc, clusters, info) of the new
     evaluation, ready for the next step.  With ``r_phys`` and ``p.f_radius >
-    0`` colliding particles merge (row f4): the arrays of ``s`` are then
+    0`` colliding particles merge (Sec. 2.4.1): the arrays of ``s`` are then
     replaced by shorter ones, and info carries the new ``r_phys``, ``r_out``,
     ``r_search`` (recomputed for all particles, step 9), ``new_index`` and the
     dissipated energies ``e_hard``, ``e_soft``.

@@ -56,7 +56,7 @@ double or_changeover_dKdy(double y, double gamma) {
 }
 
 /* ========================================================================= */
-/* Row a1: cut-off and search radii.                                          */
+/* Cut-off and search radii.                                                  */
 /* r_Hill,i = (m_i / 3M_*)^(1/3) a_i (Sec. 2.1.1), a_i the osculating         */
 /* semi-major axis; r_out,i = max(R~cut,0 r_Hill,i, R~cut,1 v_ran,i dt)       */
 /* (Eq. routi2); r_search,i = R~s,0 r_out,i + R~s,1 v_ran,i dt (Eq. rsearch). */
@@ -160,7 +160,7 @@ int or_direct_soft(int64_t n, const double *x, const double *y, const double *z,
 }
 
 /* ========================================================================= */
-/* Rows a2-a4: the Barnes-Hut tree (Sec. 2.1.2 uses FDPS's tree; the discrete */
+/* The Barnes-Hut tree (Sec. 2.1.2 uses FDPS's tree; the discrete            */
 /* definitions below are reading C4).                                         */
 /*  * root cube: bounding box of the positions, made cubic (side L = largest  */
 /*    extent), corner at the per-axis minimum;                                */
@@ -601,7 +601,7 @@ int or_tree_soft(int64_t n, const double *x, const double *y, const double *z,
 }
 
 /* ========================================================================= */
-/* Row a5: neighbour predicate, Sec. 2.3.                                    */
+/* Neighbour predicate, Sec. 2.3.                                            */
 /* Candidates: r_ij < r_search,ij = max(r_search,i, r_search,j) (Eq. rsearch  */
 /* and the individual-cut-off rule after it).  A candidate is dropped when    */
 /* its closest approach under linear motion over [0, dt] exceeds             */
@@ -710,7 +710,7 @@ int64_t or_neighbours_brute(int64_t n, const double *x, const double *y,
 }
 
 /* ========================================================================= */
-/* Row a6: neighbour clusters, Sec. 2.3 steps i-iii: every particle starts    */
+/* Neighbour clusters, Sec. 2.3 steps i-iii: every particle starts           */
 /* with its own index as cluster index; each particle takes the minimum of    */
 /* its own and its neighbours' indices; repeat until nothing changes.  Then   */
 /* compaction: isolated particles ascending; clusters of >= 2 members ordered */
@@ -759,7 +759,7 @@ int64_t or_clusters(int64_t n, const int64_t *nb_off, const int32_t *nb_idx,
 }
 
 /* ========================================================================= */
-/* Row a7: soft velocity kick v += a_soft * h, h = dt/2 (procedure steps 3    */
+/* Soft velocity kick v += a_soft * h, h = dt/2 (procedure steps 3           */
 /* and 8, Eq. HamiltonSol).                                                   */
 /* ========================================================================= */
 void or_kick(int64_t n, double *vx, double *vy, double *vz, const double *ax,
@@ -770,7 +770,7 @@ void or_kick(int64_t n, double *vx, double *vy, double *vz, const double *ax,
 }
 
 /* ========================================================================= */
-/* Row a8: hard force and jerk on member k of a cluster (Eq. hardforce):      */
+/* Hard force and jerk on member k of a cluster (Eq. hardforce):             */
 /*   a_k = -G M_* x_k / |x_k|^3 - sum_{j != k} G m_j (1 - K(y)) r / r^3,      */
 /* r = x_k - x_j, y = r / r_out,kj (reading C8: all other cluster members).   */
 /* The jerk is the time derivative, including dK/dt = K'(y) (r.v)/(r r_out).  */
@@ -986,7 +986,7 @@ static double set_energy(int64_t nc, const unsigned char *chg, const int64_t *se
 /* All members are predicted to each block time; the active ones are        */
 /* evaluated from the predicted state and then corrected together.           */
 /*                                                                           */
-/* Perfect accretion (row f4, Sec. 2.4.1), when RP (physical radii) is given */
+/* Perfect accretion (Sec. 2.4.1), when RP (physical radii) is given         */
 /* and f_radius > 0.  Readings:                                              */
 /*  - detection: at every force evaluation (the initial one and each block   */
 /*    time), each evaluated member k records its lowest-index partner j      */
@@ -1183,7 +1183,7 @@ int or_hermite_cluster(int64_t nc, const int32_t *members, double *X, double *Y,
 }
 
 /* ========================================================================= */
-/* Row a9: Kepler drift of isolated particles (Sec. 2.1.2: "solving the       */
+/* Kepler drift of isolated particles (Sec. 2.1.2: "solving the              */
 /* Kepler equation with Newton-Raphson"; reading C9: mu = G M_*, no indirect  */
 /* term).  Gauss f and g functions written with the change of eccentric      */
 /* anomaly x = E - E0 (elliptic) or hyperbolic anomaly (hyperbolic):          */
@@ -1315,7 +1315,7 @@ int or_hard_step(int64_t n, double *x, double *y, double *z, double *vx,
 }
 
 /* ========================================================================= */
-/* Row f4: second kick of composites and the merge (Sec. 2.4.1).              */
+/* Second kick of composites and the merge (Sec. 2.4.1).                     */
 /* After the soft force of procedure step 7, the members of a composite are  */
 /* kicked with the mass-weighted mean of their soft accelerations,           */
 /*   a_c = sum_l m_l a_l / sum_l m_l (ascending l),                           */
@@ -1408,7 +1408,7 @@ int64_t or_merge(int64_t n, double *x, double *y, double *z, double *vx, double 
 }
 
 /* ========================================================================= */
-/* Row a10: total energy.  H_soft + H_hard (Eqs. soft, hard) with             */
+/* Total energy.  H_soft + H_hard (Eqs. soft, hard) with                    */
 /* W + (1 - W) = 1 is the Newtonian energy                                    */
 /*   E = sum m v^2 / 2 - sum G M_* m / r - sum_{i<j} G m_i m_j / r_ij.        */
 /* out = {E, kinetic, star potential, pair potential}.                       */

@@ -45,7 +45,7 @@ typedef struct {
 double or_changeover_K(double y, double gamma);
 double or_changeover_dKdy(double y, double gamma);
 
-/* ---- row a1: cut-off and search radii (Eqs. routi2, rsearch) ------------- */
+/* ---- cut-off and search radii (Eqs. routi2, rsearch) --------------------- */
 int or_cutoffs(int64_t n, const double *x, const double *y, const double *z,
                const double *vx, const double *vy, const double *vz,
                const double *m, const or_params *p,
@@ -56,7 +56,7 @@ int or_direct_soft(int64_t n, const double *x, const double *y, const double *z,
                    const double *m, const double *r_out, const or_params *p,
                    double *ax, double *ay, double *az);
 
-/* ---- rows a2-a4: Morton keys, octree, tree walk (Sec. 2.1.2, Eq. softforce) */
+/* ---- Morton keys, octree, tree walk (Sec. 2.1.2, Eq. softforce) ---------- */
 int or_morton_keys(int64_t n, const double *x, const double *y, const double *z,
                    uint64_t *key, double box_out[4]);
 int or_tree_soft(int64_t n, const double *x, const double *y, const double *z,
@@ -73,7 +73,7 @@ void or_node_moments(int64_t n, const double *x, const double *y,
 void or_multipole_acc(const double mom[10], double G, double px, double py,
                       double pz, double acc[3]);
 
-/* ---- row a5: neighbour filter (Eqs. rsearch, rsearch1, t_min) ------------ */
+/* ---- neighbour filter (Eqs. rsearch, rsearch1, t_min) -------------------- */
 int or_neighbour_pair(int64_t i, int64_t j, const double *x, const double *y,
                       const double *z, const double *vx, const double *vy,
                       const double *vz, const double *m, const double *r_out,
@@ -91,16 +91,16 @@ int64_t or_neighbours_brute(int64_t n, const double *x, const double *y,
                             const or_params *p, int64_t *nb_off,
                             int32_t *nb_idx, int64_t nb_cap);
 
-/* ---- row a6: neighbour clusters (Sec. 2.3, steps i-iii) ------------------- */
+/* ---- neighbour clusters (Sec. 2.3, steps i-iii) --------------------------- */
 int64_t or_clusters(int64_t n, const int64_t *nb_off, const int32_t *nb_idx,
                     int32_t *label, int64_t *n_single, int32_t *singles,
                     int64_t *n_clusters, int64_t *cl_off, int32_t *cl_mem);
 
-/* ---- row a7: soft kick (procedure steps 3 and 8) -------------------------- */
+/* ---- soft kick (procedure steps 3 and 8) ---------------------------------- */
 void or_kick(int64_t n, double *vx, double *vy, double *vz, const double *ax,
              const double *ay, const double *az, double h);
 
-/* ---- row a8: Hermite-4 hard step of one neighbour cluster ----------------- */
+/* ---- Hermite-4 hard step of one neighbour cluster ------------------------- */
 void or_hard_acc_jerk(int64_t nc, const double *x, const double *y,
                       const double *z, const double *vx, const double *vy,
                       const double *vz, const double *m, const double *r_out,
@@ -112,12 +112,12 @@ int or_hermite_cluster(int64_t nc, const int32_t *members, double *x, double *y,
                        const or_params *p, double dt, int64_t *n_steps,
                        int32_t *root_out, double *e_disp);
 
-/* ---- row a9: Kepler drift of isolated particles --------------------------- */
+/* ---- Kepler drift of isolated particles ----------------------------------- */
 int or_kepler_drift(int64_t n, const int32_t *idx, double *x, double *y,
                     double *z, double *vx, double *vy, double *vz, double dt,
                     double mu);
 
-/* ---- rows a8+a9 together: the hard part of one soft step ------------------ */
+/* ---- Hermite step and Kepler drift together: the hard part of a soft step - */
 /* r_phys: physical radii (NULL or f_radius == 0: no collisions); comp_root:   */
 /* n entries (or NULL), lowest member of each particle's composite or -1;     */
 /* e_hard: energy dissipated by the collisions.                               */
@@ -128,7 +128,7 @@ int or_hard_step(int64_t n, double *x, double *y, double *z, double *vx,
                  const int64_t *cl_off, const int32_t *cl_mem,
                  int64_t *n_hermite_steps, int32_t *comp_root, double *e_hard);
 
-/* ---- row f4: composite kick and merge (Sec. 2.4.1, procedure step 9) ------ */
+/* ---- composite kick and merge (Sec. 2.4.1, procedure step 9) -------------- */
 double or_kick_composites(int64_t n, double *vx, double *vy, double *vz,
                           const double *ax, const double *ay, const double *az,
                           double h, const double *m, const int32_t *comp_root);
@@ -136,7 +136,7 @@ int64_t or_merge(int64_t n, double *x, double *y, double *z, double *vx, double 
                  double *vz, double *m, double *r_phys, double *r_out,
                  double *r_search, const int32_t *comp_root, int32_t *new_index);
 
-/* ---- row a10: total energy (Eqs. soft + hard with W + (1-W) = 1) ---------- */
+/* ---- total energy (Eqs. soft + hard with W + (1-W) = 1) ------------------ */
 void or_energy(int64_t n, const double *x, const double *y, const double *z,
                const double *vx, const double *vy, const double *vz,
                const double *m, double G, double m_star, double out[4]);

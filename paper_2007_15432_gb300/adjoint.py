@@ -146,7 +146,7 @@ def soft_kdk(x0, v0, m, r_out, runner: SoftKDK):
 
 
 def cutoffs(params: P.Params, x0, v0, m, device: int = 0):
-    """Cut-off radii of the initial state (row a1), to be held fixed."""
+    """Cut-off radii of the initial state, to be held fixed."""
     n = m.numel()
     ro = torch.zeros(n, dtype=torch.float64, device=m.device)
     rs = torch.zeros(n, dtype=torch.float64, device=m.device)

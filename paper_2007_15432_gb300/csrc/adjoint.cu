@@ -1,4 +1,4 @@
-// Row f2: the vector-Jacobian product of the Kepler drift of every particle
+// Adjoint: the vector-Jacobian product of the Kepler drift of every particle
 // (the drift of a particle with no neighbours, Sec. 2.1.2) for the adjoint
 // of the soft kick-drift-kick (the soft force's VJP is in direct.cu).
 //

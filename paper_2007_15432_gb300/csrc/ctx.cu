@@ -52,6 +52,11 @@ bool particles_ok(const p3t_particles *p) {
          p->r_search;
 }
 
+// with segments set, the particle count must be the segments' total
+bool segments_ok(const p3t_ctx *c, const p3t_particles *p) {
+  return c->nseg == 1 || p->n == c->seg_off_h[c->nseg];
+}
+
 template <typename T> void dfree(T *&ptr) {
   if (ptr) cudaFree((void *)ptr);
   ptr = nullptr;
@@ -89,14 +94,15 @@ void free_particle_buffers(p3t_ctx *c) {
   c->have_tree = c->have_cand = false;
 }
 
-int64_t node_bound(int64_t n, int leaf) {
+int64_t node_bound(int64_t n, int leaf, int64_t nseg) {
   // internal nodes hold > leaf particles: at most n / (leaf + 1) per level
-  // below the root, 21 levels; leaves are disjoint non-empty sets: at most n
-  return n + (int64_t)P3T_BITS * (n / (leaf + 1) + 1) + 64;
+  // below the roots, 21 levels, plus one root per segment and level;
+  // leaves are disjoint non-empty sets: at most n
+  return n + (int64_t)P3T_BITS * (n / (leaf + 1) + nseg) + 64;
 }
 
 int reserve(p3t_ctx *c, int64_t n, int64_t cand_cap) {
-  const int64_t want_nodes = node_bound(n, c->prm.leaf_size);
+  const int64_t want_nodes = node_bound(n, c->prm.leaf_size, c->nseg);
   if (n <= c->cap && want_nodes <= c->node_cap && cand_cap <= c->cand_cap) return P3T_OK;
   cudaDeviceSynchronize();
   free_particle_buffers(c);
@@ -207,6 +213,8 @@ void p3t_destroy(p3t_ctx *c) {
   cudaDeviceSynchronize();
   free_particle_buffers(c);
   dfree(c->status); dfree(c->box); dfree(c->box_bits); dfree(c->counters);
+  dfree(c->seg_off); dfree(c->seg_nb); dfree(c->seg_base); dfree(c->seg_l);
+  delete[] c->seg_off_h;
   dfree(c->cl_counts); dfree(c->hsteps); dfree(c->hcursor); dfree(c->epart);
   dfree(c->coll_ctr);
   dfree(c->bh_table);
@@ -235,8 +243,44 @@ int p3t_reserve(p3t_ctx *c, int64_t n) {
   return ensure(c, n);
 }
 
+int p3t_set_segments(p3t_ctx *c, int64_t nseg, const int64_t *seg_off) {
+  if (!c || nseg < 1 || nseg > P3T_MAX_SEGMENTS || !seg_off || seg_off[0] != 0)
+    return P3T_ERR_INVALID;
+  for (int64_t d = 0; d < nseg; ++d)
+    if (seg_off[d + 1] <= seg_off[d]) return P3T_ERR_INVALID;  // no empty segment
+  if (seg_off[nseg] >= ((int64_t)1 << 31)) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  cudaDeviceSynchronize();
+  dfree(c->seg_off); dfree(c->seg_nb); dfree(c->seg_base); dfree(c->seg_l);
+  dfree(c->box); dfree(c->box_bits);
+  delete[] c->seg_off_h;
+  c->seg_off_h = nullptr;
+  c->nseg = 1;
+  const int64_t S = nseg;
+  bool ok = dalloc(c->box, 5 * S) && dalloc(c->box_bits, 6 * S);
+  if (ok && nseg > 1) {
+    ok = dalloc(c->seg_off, S + 1) && dalloc(c->seg_nb, S) && dalloc(c->seg_base, S) &&
+         dalloc(c->seg_l, 2 * S);
+    if (ok)
+      ok = cudaMemcpy(c->seg_off, seg_off, sizeof(int64_t) * (S + 1),
+                      cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok) {
+      c->seg_off_h = new (std::nothrow) int64_t[S + 1];
+      ok = c->seg_off_h != nullptr;
+      if (ok) for (int64_t d = 0; d <= S; ++d) c->seg_off_h[d] = seg_off[d];
+    }
+  }
+  if (!ok) {
+    cudaGetLastError();
+    return P3T_ERR_CUDA;
+  }
+  c->nseg = nseg;
+  c->have_tree = c->have_cand = false;
+  return P3T_OK;
+}
+
 int p3t_cutoffs(p3t_ctx *c, p3t_particles *p, void *stream) {
-  if (!c || !particles_ok(p)) return P3T_ERR_INVALID;
+  if (!c || !particles_ok(p) || !segments_ok(c, p)) return P3T_ERR_INVALID;
   DeviceGuard g(c->device);
   int rc = ensure(c, p->n);
   if (rc) return rc;
@@ -244,7 +288,7 @@ int p3t_cutoffs(p3t_ctx *c, p3t_particles *p, void *stream) {
 }
 
 int p3t_build_tree(p3t_ctx *c, p3t_particles *p, int update_cutoffs, void *stream) {
-  if (!c || !particles_ok(p)) return P3T_ERR_INVALID;
+  if (!c || !particles_ok(p) || !segments_ok(c, p)) return P3T_ERR_INVALID;
   DeviceGuard g(c->device);
   int rc = ensure(c, p->n);
   if (rc) return rc;
@@ -268,7 +312,7 @@ int p3t_build_tree(p3t_ctx *c, p3t_particles *p, int update_cutoffs, void *strea
 
 int p3t_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax, double *ay,
                    double *az, uint64_t *counts, void *stream) {
-  if (!c || !particles_ok(p)) return P3T_ERR_INVALID;
+  if (!c || !particles_ok(p) || !segments_ok(c, p)) return P3T_ERR_INVALID;
   if (p->n == 0) return P3T_OK;
   if (!ax || !ay || !az || !c->have_tree || p->n != c->last_n) return P3T_ERR_INVALID;
   DeviceGuard g(c->device);
@@ -324,7 +368,7 @@ int p3t_kick(p3t_ctx *c, p3t_particles *p, const double *ax, const double *ay,
 
 int p3t_merge(p3t_ctx *c, p3t_particles *p, int32_t *new_index, double *e_disp,
               int64_t *n_merged, void *stream) {
-  if (!c || !particles_ok(p)) return P3T_ERR_INVALID;
+  if (!c || !particles_ok(p) || c->nseg > 1) return P3T_ERR_INVALID;
   DeviceGuard g(c->device);
   if (p->n > c->cap) return P3T_ERR_INVALID;
   const int64_t n0 = p->n;
@@ -356,7 +400,7 @@ int p3t_kepler_drift(p3t_ctx *c, p3t_particles *p, double dt, void *stream) {
 
 int p3t_soft_force_direct(p3t_ctx *c, const p3t_particles *p, double *ax, double *ay,
                           double *az, void *stream) {
-  if (!c || !particles_ok(p)) return P3T_ERR_INVALID;
+  if (!c || !particles_ok(p) || c->nseg > 1) return P3T_ERR_INVALID;
   if (p->n > 0 && (!ax || !ay || !az)) return P3T_ERR_INVALID;
   DeviceGuard g(c->device);
   int rc = direct_scratch(c, p->n);
@@ -367,7 +411,7 @@ int p3t_soft_force_direct(p3t_ctx *c, const p3t_particles *p, double *ax, double
 int p3t_soft_force_vjp(p3t_ctx *c, const p3t_particles *p, double h, const double *lx,
                        const double *ly, const double *lz, double *gx, double *gy, double *gz,
                        double *gm, void *stream) {
-  if (!c || !particles_ok(p)) return P3T_ERR_INVALID;
+  if (!c || !particles_ok(p) || c->nseg > 1) return P3T_ERR_INVALID;
   if (p->n > 0 && (!lx || !ly || !lz || !gx || !gy || !gz || !gm)) return P3T_ERR_INVALID;
   DeviceGuard g(c->device);
   int rc = direct_scratch(c, p->n);
@@ -384,7 +428,7 @@ int p3t_kepler_vjp(p3t_ctx *c, const p3t_particles *p, double dt, double *lx, do
 }
 
 int p3t_energy(p3t_ctx *c, const p3t_particles *p, double *out, void *stream) {
-  if (!c || !particles_ok(p) || !out) return P3T_ERR_INVALID;
+  if (!c || !particles_ok(p) || !out || c->nseg > 1) return P3T_ERR_INVALID;
   DeviceGuard g(c->device);
   int rc = ensure(c, p->n);
   if (rc) return rc;

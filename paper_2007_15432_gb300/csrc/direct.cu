@@ -1,5 +1,5 @@
 // All-pairs sums of the soft force of Eq. softforce (the tree at theta = 0)
-// and of its vector-Jacobian product (row f2), cut-off radii held fixed:
+// and of its vector-Jacobian product (the adjoint), cut-off radii held fixed:
 //   a_k = -G sum_j m_j K(r_kj / r_out,kj) r_kj / r_kj^3,
 //   g_k += s sum_j J(r_kj) (m_k lam_j - m_j lam_k),  gm_k += s sum_j phi_kj lam_j . r_kj,
 // J = phi I + psi r r^T, phi = K / r^3, psi = K'(y) / (r_out r^4) - 3 K / r^5.

@@ -1,4 +1,4 @@
-// Rows a7-a10 of the soft step: kick, Hermite-4 hard step of the neighbour
+// Soft step: kick, Hermite-4 hard step of the neighbour
 // clusters, Kepler drift of isolated particles, energy.
 //
 // Compiled with -fmad=false.  The Hermite force, predictor, corrector and
@@ -12,8 +12,8 @@ namespace {
 constexpr int kBlock = 256;
 constexpr int64_t kHermiteIterLimit = 1 << 24;  // block steps per cluster
 
-// ---- row a7: soft kick (procedure steps 3 and 8) ----------------------------
-// Members of a composite formed by the last hard step (row f4, Sec. 2.4.1;
+// ---- soft kick (procedure steps 3 and 8) ------------------------------------
+// Members of a composite formed by the last hard step (Sec. 2.4.1;
 // slot[i] >= 0, its entry in ent) are kicked with the composite's mass-
 // weighted mean acceleration sum_l m_l a_l / sum_l m_l (ascending l); the
 // composite's lowest member records the dissipation sum_l m_l |h (a_l -
@@ -54,7 +54,7 @@ __global__ void k_kick(int64_t n, double *vx, double *vy, double *vz,
   }
 }
 
-// ---- row a9: Kepler drift, universal variables ------------------------------
+// ---- Kepler drift, universal variables --------------------------------------
 // Stumpff functions C(z) = sum (-z)^k / (2k+2)!, S(z) = sum (-z)^k / (2k+3)!,
 // as nested series for |z| < 1 (4 terms below |z| = 1e-3, 6 below 1e-2, 10
 // above; truncation below 1e-19 of the result in each band) and in closed
@@ -209,7 +209,7 @@ __global__ void k_kepler_all(p3t_particles p, double dt, KepConst K, DevStatus *
   }
 }
 
-// ---- row a8 (+ f4): Hermite-4 with block steps, one block per cluster ------
+// ---- Hermite-4 with block steps (+ collisions), one block per cluster ------
 // Clusters of up to 32 members (nearly all) run one warp each, so that the
 // FP64 instructions of their few work items are not spread over idle lanes
 // of several warps; clusters of 33 to 128 members run one 128-thread block
@@ -220,7 +220,7 @@ __global__ void k_kepler_all(p3t_particles p, double dt, KepConst K, DevStatus *
 // ascending index, of terms computed in parallel (state in shared memory) or,
 // above 128 members, by one thread per member (state in a global workspace).
 //
-// Perfect accretion (row f4, Sec. 2.4.1; on when f_radius > 0 and physical
+// Perfect accretion (Sec. 2.4.1; on when f_radius > 0 and physical
 // radii are given): at every force evaluation each evaluated member records
 // the lowest-index member outside its composite that it touches, r < f (R_k
 // + R_j).  After the correction the touching members (with the composites
@@ -320,7 +320,7 @@ struct BigView {
   __device__ int32_t &chg(int k) const { return I(5, k); }
 };
 
-// composites handed to the kick and the merge (row f4)
+// composites handed to the kick and the merge (Sec. 2.4.1)
 struct CollOut {
   unsigned long long *ctr;  // (records << 32) | entries
   int4 *ent;                // {particle, lowest member of its composite, lo, hi}
@@ -875,7 +875,7 @@ __global__ void k_zero_i64_three(int64_t *p) { p[0] = 0; p[1] = 0; p[2] = 0; }
 
 __global__ void k_zero_u64(unsigned long long *p) { *p = 0ull; }
 
-// ---- row a10: energy --------------------------------------------------------
+// ---- energy ----------------------------------------------------------------
 __device__ __forceinline__ void two_sum_f(float &hi, float &lo, float b) {
   const float s = hi + b;
   const float bb = s - hi;
@@ -982,7 +982,7 @@ __global__ void k_energy_final(const double *part, int64_t nblocks, double *out)
 }
 
 
-// ---- row f4: the merge after the second kick (procedure step 9) ------------
+// ---- the merge after the second kick (procedure step 9) --------------------
 // One block: every composite's lowest member gets the summed mass and the
 // radius of the summed volume; the dissipation totals are summed in a fixed
 // order (clusters by label, composites by lowest member) so that they do not
@@ -1147,7 +1147,7 @@ int p3t_run_kepler_drift(p3t_ctx *c, p3t_particles *p, double dt, cudaStream_t s
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 
-// Procedure step 9 for composites (row f4).  Synchronises the stream: the
+// Procedure step 9 for composites (Sec. 2.4.1).  Synchronises the stream: the
 // caller needs the new particle count on the host.
 int p3t_run_merge(p3t_ctx *c, p3t_particles *p, int32_t *new_index, double *e_disp,
                   int64_t *n_merged, cudaStream_t s) {

@@ -1,4 +1,4 @@
-// Rows a5-a6 of the soft step: neighbour lists and neighbour clusters
+// Soft step: neighbour lists and neighbour clusters
 // (Sec. 2.3).  Compiled with -fmad=false: the neighbour predicate is decided
 // in FP64 with a fixed evaluation order so that membership is bit-exact.
 #include "p3t_internal.cuh"
@@ -181,7 +181,7 @@ int p3t_run_neighbours(p3t_ctx *c, const p3t_particles *p, int64_t *nb_off,
   const int64_t gc = p3t_grid(c->cand_cap, kBlock, maxb);
   int64_t *cnt = c->counters;
   int rc;
-  // ---- row a5 ----
+  // ---- neighbour lists ----
   P3T_CUDA_TRY(cudaMemsetAsync(c->deg, 0, sizeof(int32_t) * (n + 1), s));
   P3T_CUDA_TRY(cudaMemsetAsync(c->fill, 0, sizeof(int32_t) * (n + 1), s));
   k_nb_filter<<<(unsigned)gc, kBlock, 0, s>>>(&cnt[9], c->cand_i, c->cand_j, c->idx, *p,
@@ -192,7 +192,7 @@ int p3t_run_neighbours(p3t_ctx *c, const p3t_particles *p, int64_t *nb_off,
   k_nb_fill<<<(unsigned)gc, kBlock, 0, s>>>(&cnt[9], c->cand_i, c->cand_j, c->idx,
                                             c->cand_keep, nb_off, c->fill, nb_idx, c->status);
   k_nb_sort_rows<<<(unsigned)g, kBlock, 0, s>>>(n, nb_off, nb_idx, c->status);
-  // ---- row a6 ----
+  // ---- neighbour clusters ----
   k_zero_i64<<<1, 32, 0, s>>>(c->cl_counts, 4);
   k_uf_init<<<(unsigned)g, kBlock, 0, s>>>(n, c->parent, c->csize);
   k_uf_union<<<(unsigned)g, kBlock, 0, s>>>(n, nb_off, nb_idx, c->parent, c->status);

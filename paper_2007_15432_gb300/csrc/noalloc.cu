@@ -1,4 +1,4 @@
-// p3t_cutoffs_noalloc: the cut-off and search radii (row a1) for callers that
+// p3t_cutoffs_noalloc: the cut-off and search radii for callers that
 // cannot allocate device memory.
 //
 // Some callers of this library cannot call cudaMalloc: an application that

@@ -10,6 +10,31 @@
 #define P3T_QMAX (1 << P3T_BITS)
 #define P3T_KMAX 40           // deepest Hermite block level: dt / 2^40
 #define P3T_NSM_BLOCKS 8      // resident blocks per SM assumed for grid sizing
+#define P3T_MAX_SEGMENTS 4096 // independent systems sharing one context
+
+// ---- segments: the segment of a position, its range --------------------------
+struct SegView {
+  const int64_t *off;  // nseg + 1 offsets (unused when nseg == 1)
+  int nseg;
+  int64_t n;
+};
+__device__ __forceinline__ int seg_of(const SegView &v, int64_t i) {
+  int lo = 0, hi = v.nseg - 1;  // largest d with off[d] <= i
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (v.off[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ int64_t seg_lo(const SegView &v, int d) {
+  return v.nseg == 1 ? 0 : v.off[d];
+}
+__device__ __forceinline__ int64_t seg_hi(const SegView &v, int d) {
+  return v.nseg == 1 ? v.n : v.off[d + 1];
+}
+__device__ __forceinline__ int seg_at(const SegView &v, int64_t i) {
+  return v.nseg == 1 ? 0 : seg_of(v, i);
+}
 
 // ---- device-side status (sticky first error + requested size) ------------
 struct DevStatus {
@@ -68,6 +93,14 @@ struct p3t_ctx {
   int64_t node_cap = 0;   // node capacity
   int64_t cand_cap = 0;   // neighbour-candidate capacity (pairs)
   int64_t walk_warps = 0; // resident warps of the walk kernel
+  // independent particle systems sharing the arrays (segments): nseg > 1 when
+  // set by p3t_set_segments; one segment is [0, n) and reads no table
+  int64_t nseg = 1;
+  int64_t *seg_off = nullptr;      // device, nseg + 1 offsets
+  int64_t *seg_off_h = nullptr;    // host copy
+  int32_t *seg_nb = nullptr;       // device, radial bins of each segment (cut-offs)
+  int32_t *seg_base = nullptr;     //   and the first global bin of each
+  double *seg_l = nullptr;         //   log R_min, log R_max of each (2 nseg)
   unsigned long long *scan_state = nullptr;  // the single-pass scan's tile words
   int64_t scan_words = 0;
   double *dpart = nullptr; // partial sums of the all-pairs kernels (allocated

@@ -1,4 +1,4 @@
-// Rows a1-a3 of the soft step: cut-off radii, Morton keys and sort, octree
+// Soft step: cut-off radii, Morton keys and sort, octree
 // with monopole + quadrupole moments.  Compiled with -fmad=false: the keys
 // and the integer grid geometry must be bit-identical on every IEEE machine.
 #include <math.h>
@@ -20,33 +20,97 @@ __device__ __forceinline__ double ord_double(unsigned long long b) {
 }
 
 // =========================================================================
-// Row a1: cut-off radii (Eq. routi2, Eq. rsearch).  Random velocity
+// Cut-off radii (Eq. routi2, Eq. rsearch).  Random velocity
 // u = v - sqrt(G M_* / |x|) phi_hat (phi_hat: cylindrical azimuth),
 // v_ran = rms |u| over radial bins uniform in ln R_cyl.
 // =========================================================================
-__global__ void k_cut_init(unsigned long long *bits, double *bsum,
+// per segment d: bits[4d] min R, bits[4d + 1] max R, bits[4d + 2], [4d + 3]
+// the largest r_out and r_search (shared scheme)
+__global__ void k_cut_init(unsigned long long *bits, int nseg, double *bsum,
                            unsigned long long *bcnt, int nb) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t == 0) { bits[0] = ~0ull; bits[1] = 0ull; bits[2] = 0ull; bits[3] = 0ull; }
+  for (int d = t; d < nseg; d += gridDim.x * blockDim.x) {
+    bits[4 * d] = ~0ull; bits[4 * d + 1] = 0ull; bits[4 * d + 2] = 0ull; bits[4 * d + 3] = 0ull;
+  }
   for (int k = t; k < nb; k += gridDim.x * blockDim.x) { bsum[k] = 0.0; bcnt[k] = 0ull; }
 }
 
-__global__ void k_cut_range(int64_t n, const double *x, const double *y,
+// a block's slice of its segment: blocks [d * slices, (d + 1) * slices) take
+// segment d in contiguous slices
+__device__ __forceinline__ void seg_slice(const SegView &sv, int slices, int &d, int64_t &a,
+                                          int64_t &b) {
+  d = (int)(blockIdx.x / slices);
+  const int sl = (int)(blockIdx.x % slices);
+  const int64_t s0 = seg_lo(sv, d), len = seg_hi(sv, d) - s0;
+  a = s0 + len * sl / slices;
+  b = s0 + len * (sl + 1) / slices;
+}
+
+__global__ void k_cut_range(SegView sv, int slices, const double *x, const double *y,
                             unsigned long long *bits) {
+  int d;
+  int64_t a, b;
+  seg_slice(sv, slices, d, a, b);
   unsigned long long lo = ~0ull, hi = 0ull;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    unsigned long long b = ord_bits(sqrt(x[i] * x[i] + y[i] * y[i]));
-    lo = b < lo ? b : lo;
-    hi = b > hi ? b : hi;
+  for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+    unsigned long long v = ord_bits(sqrt(x[i] * x[i] + y[i] * y[i]));
+    lo = v < lo ? v : lo;
+    hi = v > hi ? v : hi;
   }
   for (int o = 16; o > 0; o >>= 1) {
-    unsigned long long a = __shfl_xor_sync(0xffffffffu, lo, o);
+    unsigned long long u = __shfl_xor_sync(0xffffffffu, lo, o);
     unsigned long long c = __shfl_xor_sync(0xffffffffu, hi, o);
-    lo = a < lo ? a : lo;
+    lo = u < lo ? u : lo;
     hi = c > hi ? c : hi;
   }
-  if ((threadIdx.x & 31) == 0) { atomicMin(&bits[0], lo); atomicMax(&bits[1], hi); }
+  if ((threadIdx.x & 31) == 0) { atomicMin(&bits[4 * d], lo); atomicMax(&bits[4 * d + 1], hi); }
+}
+
+// radial bins of each segment (several segments): their number (as for a
+// single system), first global bin and log R range
+__global__ void k_cut_segbins(SegView sv, int vran_bins, const unsigned long long *bits,
+                              int32_t *seg_nb, int32_t *seg_base, double *seg_l) {
+  __shared__ int wsum[32];
+  __shared__ int carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < sv.nseg; base += blockDim.x) {
+    const int d = base + threadIdx.x;
+    int nb = 0;
+    if (d < sv.nseg) {
+      nb = vran_bins;
+      if (nb <= 0) {
+        const int64_t t = (seg_hi(sv, d) - seg_lo(sv, d)) / 1000;
+        nb = (int)(t < 1 ? 1 : (t > 1024 ? 1024 : t));
+      }
+      seg_nb[d] = nb;
+      seg_l[2 * d] = log(ord_double(bits[4 * d]));
+      seg_l[2 * d + 1] = log(ord_double(bits[4 * d + 1]));
+    }
+    int x = nb;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      const int w0 = lane < nw ? wsum[lane] : 0;
+      int y = w0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) y += t;
+      }
+      if (lane < nw) wsum[lane] = y - w0;
+    }
+    __syncthreads();
+    const int ex = carry + wsum[warp] + (x - nb);
+    if (d < sv.nseg) seg_base[d] = ex;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = ex + nb;
+    __syncthreads();
+  }
 }
 
 __device__ __forceinline__ int cut_bin(double R, double Rmin, double Rmax,
@@ -64,15 +128,18 @@ __device__ __forceinline__ int cut_bin(double R, double Rmin, double Rmax,
 // counts (integer atomics, first into the block's shared histogram);
 // (bin, index) pairs for a stable sort by bin
 constexpr int kMaxBins = 4096;
-__global__ void k_cut_u2(int64_t n, const double *x, const double *y, const double *z,
+__global__ void k_cut_u2(SegView sv, const double *x, const double *y, const double *z,
                          const double *vx, const double *vy, const double *vz, double mu,
-                         const unsigned long long *bits, int nb, double *u2, uint64_t *key,
-                         int32_t *idx, int32_t *bin, unsigned long long *bcnt) {
+                         const unsigned long long *bits, int nb, const int32_t *seg_nb,
+                         const int32_t *seg_base, const double *seg_l, double *u2,
+                         uint64_t *key, int32_t *idx, int32_t *bin, unsigned long long *bcnt) {
   __shared__ uint32_t h[kMaxBins];
   for (int k = threadIdx.x; k < nb; k += blockDim.x) h[k] = 0;
   __syncthreads();
-  const double Rmin = ord_double(bits[0]), Rmax = ord_double(bits[1]);
-  const double lmin = log(Rmin), lmax = log(Rmax);
+  const int64_t n = sv.n;
+  // one segment: its range here; several: per particle below
+  const double Rmin0 = ord_double(bits[0]), Rmax0 = ord_double(bits[1]);
+  const double lmin0 = log(Rmin0), lmax0 = log(Rmax0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     double R = sqrt(x[i] * x[i] + y[i] * y[i]);
@@ -82,7 +149,14 @@ __global__ void k_cut_u2(int64_t n, const double *x, const double *y, const doub
     if (R > 0.0) { px = -y[i] / R; py = x[i] / R; }
     double ux = vx[i] - vk * px, uy = vy[i] - vk * py, uz = vz[i];
     u2[i] = ux * ux + uy * uy + uz * uz;
-    const int k = cut_bin(R, Rmin, Rmax, lmin, lmax, nb);
+    int k;
+    if (sv.nseg == 1) {
+      k = cut_bin(R, Rmin0, Rmax0, lmin0, lmax0, nb);
+    } else {
+      const int d = seg_of(sv, i);
+      k = seg_base[d] + cut_bin(R, ord_double(bits[4 * d]), ord_double(bits[4 * d + 1]),
+                                seg_l[2 * d], seg_l[2 * d + 1], seg_nb[d]);
+    }
     key[i] = (uint64_t)k;
     idx[i] = (int32_t)i;
     bin[i] = k;
@@ -146,12 +220,13 @@ __global__ void k_cut_binsum(int nb, const int64_t *boff, const int32_t *sorted_
   }
 }
 
-__global__ void k_cut_final(int64_t n, const double *x, const double *y,
+__global__ void k_cut_final(SegView sv, const double *x, const double *y,
                             const double *z, const double *vx, const double *vy,
                             const double *vz, const double *m, p3t_params prm,
                             unsigned long long *bits, const int32_t *bin,
                             const double *bvr, double *r_out, double *r_search) {
   const double mu = prm.G * prm.m_star;
+  const int64_t n = sv.n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     double r = sqrt(x[i] * x[i] + y[i] * y[i] + z[i] * z[i]);
@@ -169,27 +244,27 @@ __global__ void k_cut_final(int64_t n, const double *x, const double *y,
     r_search[i] = rs;
     if (prm.cutoff_mode == P3T_CUT_SHARED) {
       // non-negative doubles order like their bit patterns
-      atomicMax(&bits[2], (unsigned long long)__double_as_longlong(ro));
-      atomicMax(&bits[3], (unsigned long long)__double_as_longlong(rs));
+      const int d = seg_at(sv, i);
+      atomicMax(&bits[4 * d + 2], (unsigned long long)__double_as_longlong(ro));
+      atomicMax(&bits[4 * d + 3], (unsigned long long)__double_as_longlong(rs));
     }
   }
 }
 
 // shared cut-off (Eq. rout1): every particle gets the largest r_out and the
 // largest search radius
-__global__ void k_cut_shared(int64_t n, const unsigned long long *bits, double *r_out,
+__global__ void k_cut_shared(SegView sv, const unsigned long long *bits, double *r_out,
                              double *r_search) {
-  const double ro = __longlong_as_double((long long)bits[2]);
-  const double rs = __longlong_as_double((long long)bits[3]);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sv.n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    r_out[i] = ro;
-    r_search[i] = rs;
+    const int d = seg_at(sv, i);
+    r_out[i] = __longlong_as_double((long long)bits[4 * d + 2]);
+    r_search[i] = __longlong_as_double((long long)bits[4 * d + 3]);
   }
 }
 
 // =========================================================================
-// Rows a2-a3: keys, sort, octree, moments.
+// Keys, sort, octree, moments.
 // =========================================================================
 __global__ void k_set_i64(int64_t *dst, int64_t v) { *dst = v; }
 
@@ -199,18 +274,22 @@ __global__ void k_clamp_nodes(int64_t *cnt, int64_t node_cap, DevStatus *st) {
   if (nn > node_cap) dev_fail(st, P3T_ERR_CAPACITY, 10, nn);
   cnt[3] = nn < node_cap ? nn : node_cap;
 }
-__global__ void k_box_init(unsigned long long *bits) {
-  if (threadIdx.x < 3) { bits[threadIdx.x] = ~0ull; bits[3 + threadIdx.x] = 0ull; }
+__global__ void k_box_init(unsigned long long *bits, int nseg) {
+  for (int d = threadIdx.x; d < nseg; d += blockDim.x)
+    for (int a = 0; a < 3; ++a) { bits[6 * d + a] = ~0ull; bits[6 * d + 3 + a] = 0ull; }
 }
 
-// min / max of the positions: warp and block reductions, then six atomics
-// per block (launched with a few blocks per SM)
-__global__ void k_box(int64_t n, const double *x, const double *y,
-                      const double *z, unsigned long long *bits) {
+// min / max of the positions of each segment: warp and block reductions over
+// a block's slice of its segment, then six atomics per block
+__global__ void k_box(SegView sv, int slices, const double *x, const double *y,
+                      const double *z, unsigned long long *bits6) {
   __shared__ unsigned long long red[6][kBlock / 32];
+  int d;
+  int64_t sa, sb;
+  seg_slice(sv, slices, d, sa, sb);
+  unsigned long long *bits = bits6 + 6 * d;
   unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = sa + threadIdx.x; i < sb; i += blockDim.x) {
     unsigned long long b[3] = {ord_bits(x[i]), ord_bits(y[i]), ord_bits(z[i])};
 #pragma unroll
     for (int a = 0; a < 3; ++a) { lo[a] = b[a] < lo[a] ? b[a] : lo[a]; hi[a] = b[a] > hi[a] ? b[a] : hi[a]; }
@@ -235,14 +314,19 @@ __global__ void k_box(int64_t n, const double *x, const double *y,
   }
 }
 
-// root cube: corner at the per-axis minimum, side = largest extent
-__global__ void k_box_final(const unsigned long long *bits, double *box) {
-  double lo[3], hi[3];
-  for (int a = 0; a < 3; ++a) { lo[a] = ord_double(bits[a]); hi[a] = ord_double(bits[3 + a]); }
-  double L = fmax(hi[0] - lo[0], fmax(hi[1] - lo[1], hi[2] - lo[2]));
-  if (!(L > 0.0)) L = 1.0;
-  box[0] = lo[0]; box[1] = lo[1]; box[2] = lo[2]; box[3] = L;
-  box[4] = (double)P3T_QMAX / L;  // quantisation scale S
+// root cube of each segment: corner at the per-axis minimum, side = largest
+// extent; box[5 d ..]: corner, side L, quantisation scale S
+__global__ void k_box_final(const unsigned long long *bits6, double *box5, int nseg) {
+  for (int d = threadIdx.x; d < nseg; d += blockDim.x) {
+    const unsigned long long *bits = bits6 + 6 * d;
+    double *box = box5 + 5 * d;
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) { lo[a] = ord_double(bits[a]); hi[a] = ord_double(bits[3 + a]); }
+    double L = fmax(hi[0] - lo[0], fmax(hi[1] - lo[1], hi[2] - lo[2]));
+    if (!(L > 0.0)) L = 1.0;
+    box[0] = lo[0]; box[1] = lo[1]; box[2] = lo[2]; box[3] = L;
+    box[4] = (double)P3T_QMAX / L;  // quantisation scale S
+  }
 }
 
 __device__ __forceinline__ uint64_t spread3(uint64_t v) {
@@ -272,16 +356,30 @@ __device__ __forceinline__ uint64_t quantise(double v, double lo, double S) {
   return (uint64_t)f;
 }
 
-__global__ void k_keys(int64_t n, const double *x, const double *y,
-                       const double *z, const double *box, uint64_t *keys,
-                       int32_t *idx) {
-  const double x0 = box[0], y0 = box[1], z0 = box[2], S = box[4];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+// Morton key of each particle on its segment's grid.  rekey = 0: slot s holds
+// particle s (idx[s] = s); rekey = 1: slot s holds particle idx[s] (the keys
+// of an order already sorted)
+__global__ void k_keys(SegView sv, const double *x, const double *y,
+                       const double *z, const double *box5, uint64_t *keys,
+                       int32_t *idx, int rekey) {
+  const int64_t n = sv.n;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = rekey ? (int64_t)idx[s] : s;
+    const double *box = box5 + 5 * seg_at(sv, i);
+    const double x0 = box[0], y0 = box[1], z0 = box[2], S = box[4];
     uint64_t qx = quantise(x[i], x0, S), qy = quantise(y[i], y0, S), qz = quantise(z[i], z0, S);
-    keys[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
-    idx[i] = (int32_t)i;
+    keys[s] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+    if (!rekey) idx[s] = (int32_t)s;
   }
+}
+
+// the segment of the particle in each slot, as the key of a stable sort
+// that brings each segment's particles together in key order
+__global__ void k_segkey(SegView sv, const int32_t *idx, uint64_t *keys) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < sv.n;
+       s += (int64_t)gridDim.x * blockDim.x)
+    keys[s] = (uint64_t)seg_of(sv, idx[s]);
 }
 
 // gather sorted copies (FP64 and the float-float packing of the mixed path)
@@ -317,26 +415,32 @@ __device__ __forceinline__ int lcp_levels(uint64_t a, uint64_t b) {
   return (__clzll((long long)d) - 1) / 3;
 }
 
-__global__ void k_lcp(int64_t n, const uint64_t *keys, int leaf, int32_t *wlcp,
+// (each segment's particles are a contiguous sorted run with a tree of its
+// own: a segment's first particle shares no level with its predecessor)
+__global__ void k_lcp(SegView sv, const uint64_t *keys, int leaf, int32_t *wlcp,
                       int8_t *lp) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sv.n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    const int d = seg_at(sv, i);
+    const int64_t s0 = seg_lo(sv, d), s1 = seg_hi(sv, d);
     const uint64_t k = keys[i];
-    lp[i] = (int8_t)(i == 0 ? -1 : lcp_levels(keys[i - 1], k));
-    if (i + leaf < n) wlcp[i] = lcp_levels(k, keys[i + leaf]);
+    lp[i] = (int8_t)(i == s0 ? -1 : lcp_levels(keys[i - 1], k));
+    if (i + leaf < s1) wlcp[i] = lcp_levels(k, keys[i + leaf]);
   }
 }
 
 // Leaf level of each particle and the number of nodes it starts.  The cell of
 // i at level l holds more than `leaf` particles iff some window of leaf + 1
 // consecutive sorted particles containing i shares the level-l prefix.
-__global__ void k_levels(int64_t n, int leaf, const int32_t *wlcp,
+__global__ void k_levels(SegView sv, int leaf, const int32_t *wlcp,
                          const int8_t *lp, int8_t *lv, int32_t *ncount) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sv.n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    const int d = seg_at(sv, i);
+    const int64_t s0 = seg_lo(sv, d), s1 = seg_hi(sv, d);
     int D = -1;
-    int64_t a0 = i - leaf > 0 ? i - leaf : 0;
-    int64_t a1 = i < n - 1 - leaf ? i : n - 1 - leaf;
+    int64_t a0 = i - leaf > s0 ? i - leaf : s0;
+    int64_t a1 = i < s1 - 1 - leaf ? i : s1 - 1 - leaf;
     for (int64_t a = a0; a <= a1; ++a) D = max(D, (int)wlcp[a]);
     int L = min(D + 1, P3T_BITS);
     lv[i] = (int8_t)L;
@@ -344,7 +448,7 @@ __global__ void k_levels(int64_t n, int leaf, const int32_t *wlcp,
   }
 }
 
-// first index e > i (or n) whose key leaves i's level-l cell
+// first index e > i (or the segment's end n) whose key leaves i's level-l cell
 __device__ __forceinline__ int64_t cell_end(const uint64_t *keys, int64_t n,
                                             int64_t i, int l) {
   if (l == 0) return n;
@@ -357,20 +461,21 @@ __device__ __forceinline__ int64_t cell_end(const uint64_t *keys, int64_t n,
   return lo;
 }
 
-__global__ void k_nodes_pre(int64_t n, const uint64_t *keys, const int8_t *lp,
+__global__ void k_nodes_pre(SegView sv, const uint64_t *keys, const int8_t *lp,
                             const int8_t *lv, const int64_t *nstart,
                             const int64_t *d_nnode, int64_t node_cap,
                             int32_t *pre_first, int32_t *pre_count,
                             int32_t *pre_level, uint64_t *lvl_keys,
                             int32_t *bfs2pre, DevStatus *st) {
   if (*d_nnode > node_cap || st->code != 0) return;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sv.n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s1 = seg_hi(sv, seg_at(sv, i));
     const int l0 = (int)lp[i] + 1, L = (int)lv[i];
     int64_t id = nstart[i];
     for (int l = l0; l <= L; ++l, ++id) {
       pre_first[id] = (int32_t)i;
-      pre_count[id] = (int32_t)(cell_end(keys, n, i, l) - i);
+      pre_count[id] = (int32_t)(cell_end(keys, s1, i, l) - i);
       pre_level[id] = l;
       lvl_keys[id] = (uint64_t)l;
       bfs2pre[id] = (int32_t)id;
@@ -518,14 +623,14 @@ __device__ __forceinline__ void finish_node(TreeNode *nd, Mom64 *m64, Mom32 *m32
 __global__ void k_moments_leaf(
     const int64_t *d_nleaf, const int32_t *leaf_list, TreeNode *node, Mom64 *m64, Mom32 *m32,
     double *nrs, const double *sx, const double *sy, const double *sz, const double *sm,
-    const double *srs, const int32_t *sq, const double *box) {
+    const double *srs, const int32_t *sq, const double *box, SegView sv) {
   const int64_t nleaf = *d_nleaf;
-  const double u = ldexp(box[3], -P3T_BITS);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nleaf;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = leaf_list[t];
     TreeNode *nd = &node[b];
     const int32_t f = nd->first, c = nd->count;
+    const double u = ldexp(box[5 * seg_at(sv, f) + 3], -P3T_BITS);
     const double rx = sx[f], ry = sy[f], rz = sz[f];
     double M = 0.0, D[3] = {0, 0, 0}, S[6] = {0, 0, 0, 0, 0, 0}, rs = 0.0;
     int32_t lo[3] = {P3T_QMAX, P3T_QMAX, P3T_QMAX}, hi[3] = {-1, -1, -1};
@@ -583,21 +688,40 @@ __global__ void k_level_offsets(const int64_t *d_nnode, int64_t node_cap, const 
 // small enough that its time is the latency of one warp's FP64 instruction
 // stream (one FP64 warp instruction per 64 cycles of a sub-partition), so a
 // node's children are spread over L lanes (L = 8, 4, 2 or 1, the largest that
-// keeps the level within about one warp per sub-partition), each lane summing
-// the children k = sub, sub + L, ..., and the L partial sums are added by
-// shuffles.  The loop runs in warp-uniform chunks so that every lane reaches
-// every shuffle; groups past the level's end or at leaves contribute nothing.
+// keeps the level within about one warp per sub-partition), lane sub holding
+// the child slots sub, sub + L, ... of the node's eight.  Each child's terms
+// are rounded on their own and the eight slots (zero where there is no child)
+// are added in one fixed pairwise tree, slots s and s + 4, then s + 2, then
+// s + 1: in registers while the stride is a multiple of L, by shuffles below
+// it.  The sums are therefore the same bits for every L, so a node's moments
+// do not depend on how many nodes share its level (a tree built alone or
+// beside other systems' trees).  The loop runs in warp-uniform chunks so that
+// every lane reaches every shuffle; groups past the level's end or at leaves
+// contribute nothing.
 __device__ __forceinline__ double shfl_down_group(double v, int o) {
   return __shfl_xor_sync(0xffffffffu, v, o);
 }
 
-__device__ void moments_level(int level, const int64_t *lvl_start, TreeNode *node, Mom64 *m64,
-                              Mom32 *m32, double *nrs, double u, int64_t warp_target) {
-  const int64_t b0 = lvl_start[level], b1 = lvl_start[level + 1];
-  const int64_t nn = b1 - b0;
-  if (nn <= 0) return;
-  int L = 8;
-  while (L > 1 && nn * L > 32 * warp_target) L >>= 1;
+// the fixed pairwise tree over slots: J = 8 / L slots in this lane's
+// registers, then the shuffles between the L lanes of the group
+template <int L, int NQ>
+__device__ __forceinline__ void slot_tree(double (&v)[8 / L][NQ]) {
+#pragma unroll
+  for (int S = 4; S >= L; S >>= 1)
+#pragma unroll
+    for (int j = 0; j < S / L; ++j)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) v[j][q] += v[j + S / L][q];
+#pragma unroll
+  for (int o = L >> 1; o > 0; o >>= 1)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[0][q] += shfl_down_group(v[0][q], o);
+}
+
+template <int L>
+__device__ void moments_level_L(int64_t b0, int64_t nn, TreeNode *node, Mom64 *m64, Mom32 *m32,
+                                double *nrs, const double *box, const SegView &sv) {
+  constexpr int J = 8 / L;
   const int lane = threadIdx.x & 31, sub = lane & (L - 1);
   const int per_warp = 32 / L;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -608,22 +732,27 @@ __device__ void moments_level(int level, const int64_t *lvl_start, TreeNode *nod
     const int64_t b = b0 + (valid ? gi : 0);
     TreeNode *pn = &node[b];
     const int32_t c0 = valid ? pn->child0 : 0, nch = valid ? pn->nchild : 0;
-    double PM = 0.0, P[3] = {0, 0, 0}, prs = 0.0;
+    double prs = 0.0;
     int32_t plo[3] = {P3T_QMAX, P3T_QMAX, P3T_QMAX}, phi[3] = {-1, -1, -1};
-    for (int k = sub; k < nch; k += L) {
-      const Mom64 &cm = m64[c0 + k];
-      PM += cm.M;
-      P[0] = __fma_rn(cm.M, cm.cx, P[0]);
-      P[1] = __fma_rn(cm.M, cm.cy, P[1]);
-      P[2] = __fma_rn(cm.M, cm.cz, P[2]);
-      prs = fmax(prs, nrs[c0 + k]);
-      const TreeNode &cn = node[c0 + k];
-      for (int a = 0; a < 3; ++a) { plo[a] = min(plo[a], cn.qlo[a]); phi[a] = max(phi[a], cn.qhi[a]); }
+    double t[J][4];  // M, M cx, M cy, M cz
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int k = sub + j * L;
+      t[j][0] = t[j][1] = t[j][2] = t[j][3] = 0.0;
+      if (k < nch) {
+        const Mom64 &cm = m64[c0 + k];
+        t[j][0] = cm.M;
+        t[j][1] = cm.M * cm.cx;
+        t[j][2] = cm.M * cm.cy;
+        t[j][3] = cm.M * cm.cz;
+        prs = fmax(prs, nrs[c0 + k]);
+        const TreeNode &cn = node[c0 + k];
+        for (int a = 0; a < 3; ++a) { plo[a] = min(plo[a], cn.qlo[a]); phi[a] = max(phi[a], cn.qhi[a]); }
+      }
     }
+    slot_tree<L, 4>(t);
     for (int o = L >> 1; o > 0; o >>= 1) {
-      PM += shfl_down_group(PM, o);
       for (int a = 0; a < 3; ++a) {
-        P[a] += shfl_down_group(P[a], o);
         plo[a] = min(plo[a], __shfl_xor_sync(0xffffffffu, plo[a], o));
         phi[a] = max(phi[a], __shfl_xor_sync(0xffffffffu, phi[a], o));
       }
@@ -631,30 +760,52 @@ __device__ void moments_level(int level, const int64_t *lvl_start, TreeNode *nod
     }
     Mom64 pm = {};
     if (nch > 0) {
-      const double iM = 1.0 / PM;
-      pm.M = PM; pm.cx = P[0] * iM; pm.cy = P[1] * iM; pm.cz = P[2] * iM;
+      const double iM = 1.0 / t[0][0];
+      pm.M = t[0][0]; pm.cx = t[0][1] * iM; pm.cy = t[0][2] * iM; pm.cz = t[0][3] * iM;
     }
-    double Q[6] = {0, 0, 0, 0, 0, 0};  // xx, yy, zz, xy, xz, yz
-    for (int k = sub; k < nch; k += L) {
-      const Mom64 &cm = m64[c0 + k];
-      const double dx = cm.cx - pm.cx, dy = cm.cy - pm.cy, dz = cm.cz - pm.cz;
-      const double d2 = __fma_rn(dx, dx, __fma_rn(dy, dy, dz * dz));
-      const double tx = 3.0 * dx, ty = 3.0 * dy;
-      Q[0] += __fma_rn(cm.M, __fma_rn(tx, dx, -d2), cm.qxx);
-      Q[1] += __fma_rn(cm.M, __fma_rn(ty, dy, -d2), cm.qyy);
-      Q[2] += __fma_rn(cm.M, __fma_rn(3.0 * dz, dz, -d2), cm.qzz);
-      Q[3] += __fma_rn(cm.M, tx * dy, cm.qxy);
-      Q[4] += __fma_rn(cm.M, tx * dz, cm.qxz);
-      Q[5] += __fma_rn(cm.M, ty * dz, cm.qyz);
+    double Q[J][6];  // xx, yy, zz, xy, xz, yz
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int k = sub + j * L;
+      for (int q = 0; q < 6; ++q) Q[j][q] = 0.0;
+      if (k < nch) {
+        const Mom64 &cm = m64[c0 + k];
+        const double dx = cm.cx - pm.cx, dy = cm.cy - pm.cy, dz = cm.cz - pm.cz;
+        const double d2 = __fma_rn(dx, dx, __fma_rn(dy, dy, dz * dz));
+        const double tx = 3.0 * dx, ty = 3.0 * dy;
+        Q[j][0] = __fma_rn(cm.M, __fma_rn(tx, dx, -d2), cm.qxx);
+        Q[j][1] = __fma_rn(cm.M, __fma_rn(ty, dy, -d2), cm.qyy);
+        Q[j][2] = __fma_rn(cm.M, __fma_rn(3.0 * dz, dz, -d2), cm.qzz);
+        Q[j][3] = __fma_rn(cm.M, tx * dy, cm.qxy);
+        Q[j][4] = __fma_rn(cm.M, tx * dz, cm.qxz);
+        Q[j][5] = __fma_rn(cm.M, ty * dz, cm.qyz);
+      }
     }
-    for (int o = L >> 1; o > 0; o >>= 1)
-      for (int q = 0; q < 6; ++q) Q[q] += shfl_down_group(Q[q], o);
+    slot_tree<L, 6>(Q);
     if (valid && nch > 0 && sub == 0) {
-      pm.qxx = Q[0]; pm.qyy = Q[1]; pm.qzz = Q[2]; pm.qxy = Q[3]; pm.qxz = Q[4]; pm.qyz = Q[5];
+      pm.qxx = Q[0][0]; pm.qyy = Q[0][1]; pm.qzz = Q[0][2];
+      pm.qxy = Q[0][3]; pm.qxz = Q[0][4]; pm.qyz = Q[0][5];
       for (int a = 0; a < 3; ++a) { pn->qlo[a] = plo[a]; pn->qhi[a] = phi[a]; }
       nrs[b] = prs;
-      finish_node(pn, m64, m32, prs, u, b, pm);
+      finish_node(pn, m64, m32, prs, ldexp(box[5 * seg_at(sv, pn->first) + 3], -P3T_BITS), b,
+                  pm);
     }
+  }
+}
+
+__device__ void moments_level(int level, const int64_t *lvl_start, TreeNode *node, Mom64 *m64,
+                              Mom32 *m32, double *nrs, const double *box, const SegView &sv,
+                              int64_t warp_target) {
+  const int64_t b0 = lvl_start[level], b1 = lvl_start[level + 1];
+  const int64_t nn = b1 - b0;
+  if (nn <= 0) return;
+  int L = 8;
+  while (L > 1 && nn * L > 32 * warp_target) L >>= 1;
+  switch (L) {
+    case 8: moments_level_L<8>(b0, nn, node, m64, m32, nrs, box, sv); break;
+    case 4: moments_level_L<4>(b0, nn, node, m64, m32, nrs, box, sv); break;
+    case 2: moments_level_L<2>(b0, nn, node, m64, m32, nrs, box, sv); break;
+    default: moments_level_L<1>(b0, nn, node, m64, m32, nrs, box, sv); break;
   }
 }
 
@@ -665,10 +816,9 @@ constexpr int kDeepLevel = 12;
 // (a block barrier between levels)
 __global__ void k_moments_level(int level_hi, int level_lo, const int64_t *lvl_start,
                                 TreeNode *node, Mom64 *m64, Mom32 *m32, double *nrs,
-                                const double *box, int64_t warp_target) {
-  const double u = ldexp(box[3], -P3T_BITS);
+                                const double *box, SegView sv, int64_t warp_target) {
   for (int l = level_hi; l >= level_lo; --l) {
-    moments_level(l, lvl_start, node, m64, m32, nrs, u, warp_target);
+    moments_level(l, lvl_start, node, m64, m32, nrs, box, sv, warp_target);
     if (l > level_lo) {
       __threadfence_block();
       __syncthreads();
@@ -702,17 +852,35 @@ __global__ void k_tree_stats(const int64_t *d_nnode, int64_t node_cap,
 // counters layout (int64): [0] n, [1] nodes, [2] leaves, [3] nodes clamped to
 // the capacity, [4..7] tree stats, [8] candidates, [9] candidates clamped,
 // [10] neighbour entries, [11] cluster members, [12] walk group cursor
+// radial bins of a system of n particles (Sec. 2.1.3 reading C3)
+static int cut_bins(int vran_bins, int64_t n) {
+  int nb = vran_bins;
+  if (nb <= 0) { int64_t t = n / 1000; nb = (int)(t < 1 ? 1 : (t > 1024 ? 1024 : t)); }
+  return nb;
+}
+
 int p3t_run_cutoffs(p3t_ctx *c, p3t_particles *p, cudaStream_t s) {
   const int64_t n = p->n;
   if (n == 0) return P3T_OK;
-  int nb = c->prm.vran_bins;
-  if (nb <= 0) { int64_t t = n / 1000; nb = (int)(t < 1 ? 1 : (t > 1024 ? 1024 : t)); }
-  if (nb > 4096) return P3T_ERR_INVALID;
+  const SegView sv{c->seg_off, (int)c->nseg, n};
+  int64_t nbt = 0;  // bins of all segments
+  if (c->nseg == 1) {
+    nbt = cut_bins(c->prm.vran_bins, n);
+  } else {
+    for (int64_t d = 0; d < c->nseg; ++d)
+      nbt += cut_bins(c->prm.vran_bins, c->seg_off_h[d + 1] - c->seg_off_h[d]);
+  }
+  if (nbt > kMaxBins) return P3T_ERR_INVALID;
+  const int nb = (int)nbt;
   double *bsum = c->epart;  // reuse: >= 4096 doubles
   unsigned long long *bcnt = reinterpret_cast<unsigned long long *>(c->epart + 4096);
   const int64_t g = p3t_grid(n, kBlock, (int64_t)c->num_sms * P3T_NSM_BLOCKS);
-  k_cut_init<<<4, kBlock, 0, s>>>(c->box_bits, bsum, bcnt, nb);
-  k_cut_range<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, c->box_bits);
+  k_cut_init<<<4, kBlock, 0, s>>>(c->box_bits, (int)c->nseg, bsum, bcnt, nb);
+  const int rsl = c->nseg == 1 ? (int)g : (int)((g + c->nseg - 1) / c->nseg);
+  k_cut_range<<<(unsigned)(rsl * c->nseg), kBlock, 0, s>>>(sv, rsl, p->x, p->y, c->box_bits);
+  if (c->nseg > 1)
+    k_cut_segbins<<<1, 1024, 0, s>>>(sv, c->prm.vran_bins, c->box_bits, c->seg_nb,
+                                     c->seg_base, c->seg_l);
   const double mu = c->prm.G * c->prm.m_star;
   // per-bin sums in a fixed order (particles grouped by bin with the stable
   // radix sort, then one warp per bin): the radii do not depend on timing
@@ -721,21 +889,23 @@ int p3t_run_cutoffs(p3t_ctx *c, p3t_particles *p, cudaStream_t s) {
   int64_t *d_n = &c->counters[18];
   k_set_i64<<<1, 1, 0, s>>>(d_n, n);
   int32_t *bin = c->flag;  // the bins of k_cut_u2, read by k_cut_final (N int32)
-  k_cut_u2<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, p->z, p->vx, p->vy, p->vz, mu,
-                                          c->box_bits, nb, u2, c->keys, c->idx, bin, bcnt);
+  k_cut_u2<<<(unsigned)g, kBlock, 0, s>>>(sv, p->x, p->y, p->z, p->vx, p->vy, p->vz, mu,
+                                          c->box_bits, nb, c->seg_nb, c->seg_base, c->seg_l,
+                                          u2, c->keys, c->idx, bin, bcnt);
   int rc = p3t_radix_sort(&c->keys, &c->idx, &c->keys_alt, &c->idx_alt, d_n, c->cap, 0, 16,
                           c->radix_hist, c->radix_hist_cap, s);
   if (rc) return rc;
   k_cut_offsets<<<1, 1024, 0, s>>>(nb, bcnt, boff);
   k_cut_binsum<<<(unsigned)p3t_grid((int64_t)nb * 32, kBlock, (int64_t)c->num_sms * 4), kBlock, 0,
                  s>>>(nb, boff, c->idx, u2, bsum);
-  k_cut_final<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, p->z, p->vx, p->vy,
+  k_cut_final<<<(unsigned)g, kBlock, 0, s>>>(sv, p->x, p->y, p->z, p->vx, p->vy,
                                              p->vz, p->m, c->prm, c->box_bits, bin, bsum,
                                              p->r_out, p->r_search);
   if (c->prm.cutoff_mode == P3T_CUT_SHARED)
-    k_cut_shared<<<(unsigned)g, kBlock, 0, s>>>(n, c->box_bits, p->r_out, p->r_search);
-  // init, range, n, u2, offsets, bin sums, final (+ shared); the sort counts itself
-  p3t_note_launches(c->prm.cutoff_mode == P3T_CUT_SHARED ? 8 : 7);
+    k_cut_shared<<<(unsigned)g, kBlock, 0, s>>>(sv, c->box_bits, p->r_out, p->r_search);
+  // init, range, n, u2, offsets, bin sums, final (+ shared, + segment bins);
+  // the sort counts itself
+  p3t_note_launches(7 + (c->prm.cutoff_mode == P3T_CUT_SHARED) + (c->nseg > 1));
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 
@@ -746,26 +916,42 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   const int64_t g = p3t_grid(n, kBlock, maxb);
   int64_t *cnt = c->counters;
   int rc;
+  const int nseg = (int)c->nseg;
+  const SegView sv{c->seg_off, nseg, n};
+  // one root cube per segment: a few blocks per SM in all, in slices of the
+  // segments
+  const int bsl = nseg >= 2 * c->num_sms ? 1 : 2 * c->num_sms / nseg;
+  k_box_init<<<1, 256, 0, s>>>(c->box_bits, nseg);
+  k_box<<<(unsigned)(bsl * nseg), kBlock, 0, s>>>(sv, bsl, p->x, p->y, p->z, c->box_bits);
+  k_box_final<<<1, 256, 0, s>>>(c->box_bits, c->box, nseg);
+  k_keys<<<(unsigned)g, kBlock, 0, s>>>(sv, p->x, p->y, p->z, c->box, c->keys, c->idx, 0);
   // n on the device for the count-driven primitives
-  k_box_init<<<1, 32, 0, s>>>(c->box_bits);
-  k_box<<<(unsigned)p3t_grid(n, kBlock, (int64_t)c->num_sms * 2), kBlock, 0, s>>>(
-      n, p->x, p->y, p->z, c->box_bits);
-  k_box_final<<<1, 1, 0, s>>>(c->box_bits, c->box);
-  k_keys<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, p->z, c->box, c->keys, c->idx);
   k_set_i64<<<1, 1, 0, s>>>(&cnt[0], n);
   rc = p3t_radix_sort(&c->keys, &c->idx, &c->keys_alt, &c->idx_alt, &cnt[0], c->cap,
                       0, 64, c->radix_hist, c->radix_hist_cap, s);
   if (rc) return rc;
+  if (nseg > 1) {
+    // stable sort by segment (the most significant digit of (segment, key)),
+    // then the keys of the new order
+    int sbits = 0;
+    while ((1 << sbits) < nseg) ++sbits;
+    k_segkey<<<(unsigned)g, kBlock, 0, s>>>(sv, c->idx, c->keys);
+    rc = p3t_radix_sort(&c->keys, &c->idx, &c->keys_alt, &c->idx_alt, &cnt[0], c->cap,
+                        0, sbits, c->radix_hist, c->radix_hist_cap, s);
+    if (rc) return rc;
+    k_keys<<<(unsigned)g, kBlock, 0, s>>>(sv, p->x, p->y, p->z, c->box, c->keys, c->idx, 1);
+    p3t_note_launches(2);
+  }
   k_gather<<<(unsigned)g, kBlock, 0, s>>>(n, c->idx, c->keys, p->x, p->y, p->z, p->m,
                                           p->r_out, p->r_search, c->sx, c->sy, c->sz,
                                           c->sm, c->sro, c->srs, c->sq, c->spA, c->spB,
                                           c->srs32, c->sml);
-  k_lcp<<<(unsigned)g, kBlock, 0, s>>>(n, c->keys, leaf, c->wlcp, c->lp);
-  k_levels<<<(unsigned)g, kBlock, 0, s>>>(n, leaf, c->wlcp, c->lp, c->lv, c->ncount);
+  k_lcp<<<(unsigned)g, kBlock, 0, s>>>(sv, c->keys, leaf, c->wlcp, c->lp);
+  k_levels<<<(unsigned)g, kBlock, 0, s>>>(sv, leaf, c->wlcp, c->lp, c->lv, c->ncount);
   rc = p3t_scan_i32_to_i64(c->ncount, c->nstart, &cnt[0], c->cap, &cnt[1], c->scan_state, c->scan_words, c->status, s);
   if (rc) return rc;
   k_clamp_nodes<<<1, 1, 0, s>>>(cnt, c->node_cap, c->status);
-  k_nodes_pre<<<(unsigned)g, kBlock, 0, s>>>(n, c->keys, c->lp, c->lv, c->nstart, &cnt[1],
+  k_nodes_pre<<<(unsigned)g, kBlock, 0, s>>>(sv, c->keys, c->lp, c->lv, c->nstart, &cnt[1],
                                              c->node_cap, c->pre_first, c->pre_count,
                                              c->pre_level, c->lvl_keys, c->bfs2pre, c->status);
   rc = p3t_radix_sort(&c->lvl_keys, &c->bfs2pre, &c->lvl_keys_alt, &c->bfs2pre_alt, &cnt[3],
@@ -785,7 +971,7 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
                                               c->leaf_pos, c->pre2bfs, c->leaf_list);
   k_moments_leaf<<<(unsigned)p3t_grid(c->node_cap, 128, maxb), 128, 0, s>>>(
       &cnt[2], c->leaf_list, c->node, c->mom64, c->mom32, c->nrs, c->sx, c->sy, c->sz, c->sm,
-      c->srs, c->sq, c->box);
+      c->srs, c->sq, c->box, sv);
   {
     // internal nodes, level by level, deepest first
     int64_t *lvl_start = c->counters + 32;  // [P3T_BITS + 2]
@@ -793,11 +979,12 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
     // the deep levels (empty or nearly so in a disk) in one single-block
     // launch, then one launch a level at about one warp per sub-partition
     k_moments_level<<<1, 128, 0, s>>>(P3T_BITS - 1, kDeepLevel, lvl_start, c->node, c->mom64,
-                                      c->mom32, c->nrs, c->box, 4);
+                                      c->mom32, c->nrs, c->box, sv, 4);
     const int64_t wt = (int64_t)c->num_sms * 4;
     for (int l = kDeepLevel - 1; l >= 0; --l)
       k_moments_level<<<(unsigned)c->num_sms, 128, 0, s>>>(l, l, lvl_start, c->node, c->mom64,
-                                                           c->mom32, c->nrs, c->box, wt);
+                                                           c->mom32, c->nrs, c->box, sv,
+                                                           wt);
   }
   k_group_flags<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->node, c->bfs2pre,
                                                 c->prm.group_size, c->group_flag);

@@ -1,4 +1,4 @@
-// Row a4 of the soft step: the changeover tree walk (Eq. softforce).
+// Soft step: the changeover tree walk (Eq. softforce).
 //
 // One warp per target group (the highest tree node holding <= group_size
 // particles, or a leaf), 32 targets per walk (larger groups are taken 32
@@ -53,6 +53,7 @@ struct WalkArgs {
   int64_t refine_cap;
   const int64_t *d_nrefine;        // refine count clamped to the capacity
   const int32_t *leaf_of;          // sorted index -> its leaf (BFS id)
+  SegView seg;                     // segments: the root of segment d is node d
   double G, gamma;
   float inv1mg_f, mgi_f;           // 1 / (1 - gamma), -gamma / (1 - gamma)
   float refine_cf;                 // refine when sum|term| > refine_cf * |a|
@@ -426,14 +427,17 @@ __device__ __forceinline__ void write_result<false>(const WalkArgs &a, Target<fa
 // hands full batches of 32 accepted nodes / leaf members to the evaluator.
 // Returns false when the walk had to stop (capacity or round bound).
 template <class Ev>
-__device__ bool traverse(const WalkArgs &a, const GroupBox &gb, int32_t *stack,
+__device__ bool traverse(const WalkArgs &a, const GroupBox &gb, int32_t first, int32_t *stack,
                          int32_t *pp, int32_t *nd, int32_t *big,
                          const int64_t *s_bh, int64_t round_limit, Ev &ev) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   int top = 1, npl = 0, nnd = 0, nbig = 0;
   int64_t rounds = 0;
-  if (lane == 0) stack[0] = 0;
+  // sorted order keeps each segment contiguous, and segment d's root (level
+  // 0, d-th in key order) is BFS node d: start at the root of the segment
+  // that holds sorted particle `first`
+  if (lane == 0) stack[0] = seg_at(a.seg, first);
   __syncwarp();
   while (top > 0) {
     if (++rounds > round_limit) {
@@ -737,7 +741,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_walk(const WalkArgs a) {
       t.load(a, tb + (lane - rep * k), rep < nrep, rep < nrep ? rep : 0, nrep);
       if constexpr (MIXED) far_box(t, s_box[w]);
       GroupEval<MIXED> ev{a, t, s_stage[w], s_box[w], npp, npn};
-      ok = traverse(a, gb, stack, s_pp[w], s_nd[w], s_big[w], s_bh, round_limit, ev);
+      ok = traverse(a, gb, gfirst, stack, s_pp[w], s_nd[w], s_big[w], s_bh, round_limit, ev);
       if (ok) {
         t.reduce(k);
         write_result<MIXED>(a, t);
@@ -783,7 +787,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_refine(const WalkArgs a) {
     gb.load(a.node[a.leaf_of[ti]]);
     const float4 A = a.spA[ti], B = a.spB[ti];
     RefineEval ev{a, A.x, A.y, A.z, B.x, B.y, B.z, B.w, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    if (!traverse(a, gb, stack, s_pp[w], s_nd[w], s_big[w], s_bh, round_limit, ev)) break;
+    if (!traverse(a, gb, ti, stack, s_pp[w], s_nd[w], s_big[w], s_bh,
+                  round_limit, ev))
+      break;
     // the target itself is in the list: its own term is skipped (r = 0)
     for (int o = 16; o > 0; o >>= 1) {
       ev.ax = ff_add(ev.ax, ff_shfl_xor(ev.ax, o));
@@ -844,6 +850,7 @@ int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
   a.refine_cap = c->cap;
   a.d_nrefine = &c->counters[14];
   a.leaf_of = c->leaf_of;
+  a.seg = SegView{c->seg_off, (int)c->nseg, p->n};
   a.refine_cf = 32.0f;
   a.G = c->prm.G;
   a.gamma = c->prm.gamma;

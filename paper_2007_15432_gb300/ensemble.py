@@ -3,12 +3,24 @@
 Every disk is an independent P3T system (the paper's clusters and soft steps
 never couple two disks).  The particles of all disks live in one set of
 float64 SoA arrays, disk d occupying [offset_d, offset_d + n_d) (the
-descriptor table), and each disk has its own libp3t context working on views
-of those arrays.  One ensemble soft step (kick, hard part, tree, soft force,
-neighbours, kick for every disk) is recorded once into a CUDA graph that forks
-the disks over a pool of streams and joins them again; replaying the graph
-runs the whole ensemble with one launch from the host.  ``step_sequential``
-issues the same kernels disk after disk on one stream, for comparison.
+descriptor table).  Two ways to step them:
+
+  * batched (``batched=True``): one libp3t context holds every disk as a
+    segment of one particle set (``p3t_set_segments``): each kernel of the
+    soft step runs once over all disks, each disk keeping its own radial bins,
+    root cube, octree and walk roots, so one ensemble step costs the launches
+    of one soft step whatever the number of disks.  One parameter set for all
+    disks (``autotune_batched`` picks its group size).
+  * per-disk contexts (``batched=False``): each disk has its own context on
+    views of the shared arrays, with parameters of its own (``autotune`` picks
+    a group size per disk-size class).
+
+Either way one ensemble soft step (kick, hard part, tree, soft force,
+neighbours, kick) is recorded once into a CUDA graph (per-disk contexts forked
+over a pool of streams and joined again); replaying the graph runs the whole
+ensemble with one launch from the host.  ``step_sequential`` issues the same
+kernels without the graph (per-disk: disk after disk on one stream).  Both
+ways give every disk the bits it gets when stepped alone.
 
 Collisions are off in the ensemble: the merge after a collision needs the
 new particle count on the host, which a captured graph cannot give.
@@ -39,15 +51,22 @@ def size_class(n: int) -> int:
     return int(np.floor(np.log2(max(n, 1))))
 
 
+def _fields(p: P.Params) -> tuple:
+    return tuple(getattr(p, f[0]) for f in P.Params._fields_)
+
+
 class Ensemble:
-    """Independent disks with per-disk parameters; see the module docstring."""
+    """Independent disks; see the module docstring.  ``params``: one
+    parameter set per disk (all equal when ``batched``)."""
 
     def __init__(self, disks: list[dict], params: list[P.Params], device: int = 0,
-                 n_streams: int = 16):
+                 n_streams: int = 16, batched: bool = False):
         if any(p.f_radius > 0.0 for p in params):
             raise ValueError("collisions are not supported in a captured ensemble step")
+        if len(params) != len(disks):
+            raise ValueError("one parameter set per disk")
         self.device = torch.device("cuda", device)
-        self.params = params
+        self.batched = bool(batched)
         self.table = descriptor_table([len(d["m"]) for d in disks])
         self.n_total = int(self.table[:, 1].sum())
         self.arrays = {k: torch.as_tensor(np.concatenate([d[k] for d in disks]),
@@ -55,10 +74,23 @@ class Ensemble:
                        for k in _KEYS}
         for k in ("r_out", "r_search"):
             self.arrays[k] = torch.zeros(self.n_total, dtype=torch.float64, device=self.device)
-        self.states = [P.State(*[self.arrays[k][o:o + n] for k in _KEYS + ("r_out", "r_search")])
-                       for o, n in self.table]
-        self.steps = [P.SoftStep(p, st, device=device, nb_cap=8 * len(st.m) + 1024)
-                      for p, st in zip(params, self.states)]
+        keys = _KEYS + ("r_out", "r_search")
+        self.states = [P.State(*[self.arrays[k][o:o + n] for k in keys]) for o, n in self.table]
+        if self.batched:
+            if any(_fields(p) != _fields(params[0]) for p in params):
+                raise ValueError("a batched ensemble takes one parameter set for all disks")
+            whole = P.State(*[self.arrays[k] for k in keys])
+            seg_off = np.concatenate([[0], np.cumsum(self.table[:, 1])]).astype(np.int64)
+            self.params = [params[0]]
+            self.units = [whole]
+            self.steps = [P.SoftStep(params[0], whole, device=device,
+                                     nb_cap=8 * self.n_total + 1024, seg_off=seg_off)]
+            n_streams = 1
+        else:
+            self.params = list(params)
+            self.units = self.states
+            self.steps = [P.SoftStep(p, st, device=device, nb_cap=8 * len(st.m) + 1024)
+                          for p, st in zip(params, self.states)]
         self.streams = [torch.cuda.Stream(self.device) for _ in range(n_streams)]
         self.graph = None
 
@@ -81,7 +113,8 @@ class Ensemble:
 
     # ---- one soft step ---------------------------------------------------------
     def _step_disk(self, d: int, stream):
-        ss, st, prm = self.steps[d], self.states[d], self.params[d]
+        """Soft step of unit d (one disk, or every disk when batched)."""
+        ss, st, prm = self.steps[d], self.units[d], self.params[d]
         h = 0.5 * prm.dt_soft
         P.p3t_kick(ss.ctx, st, ss.acc, h, stream)
         P.p3t_hard_step(ss.ctx, st, ss.cl, prm.dt_soft, ss.hsteps, stream)
@@ -91,7 +124,8 @@ class Ensemble:
         P.p3t_kick(ss.ctx, st, ss.acc, h, stream)
 
     def step_sequential(self):
-        """Every disk's soft step, one disk after the other on the current stream."""
+        """The ensemble's soft step without the graph, on the current stream
+        (per-disk contexts: one disk after the other)."""
         s = torch.cuda.current_stream(self.device)
         for d in range(len(self.steps)):
             self._step_disk(d, s)
@@ -121,6 +155,38 @@ class Ensemble:
     def step_graph(self):
         """One ensemble step by replaying the captured graph."""
         self.graph.replay()
+
+    def autotune_batched(self, candidates=(16, 32, 48, 64), reps: int = 3) -> int:
+        """Group size of a batched ensemble: the candidate with the shortest
+        tree build + soft force over all disks (CUDA events, best of
+        ``reps``), after ``init``.  Sets it, recomputes force, neighbours and
+        clusters with it (drops a captured graph) and returns it."""
+        if not self.batched:
+            raise ValueError("autotune_batched is for a batched ensemble")
+        ss, st = self.steps[0], self.units[0]
+        best = None
+        for gs in candidates:
+            prm = P.Params(**{f[0]: getattr(self.params[0], f[0]) for f in P.Params._fields_})
+            prm.group_size = int(gs)
+            P.p3t_set_params(ss.ctx, prm)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            times = []
+            for _ in range(reps):
+                e0.record()
+                P.p3t_build_tree(ss.ctx, st, False)
+                P.p3t_soft_force(ss.ctx, st, ss.acc, ss.counts)
+                e1.record()
+                torch.cuda.synchronize(self.device)
+                times.append(e0.elapsed_time(e1))
+            ss.status()
+            if best is None or min(times) < best[0]:
+                best = (min(times), prm)
+        self.params[0] = ss.params = best[1]
+        P.p3t_set_params(ss.ctx, best[1])
+        ss.force()
+        torch.cuda.synchronize(self.device)
+        self.graph = None
+        return int(best[1].group_size)
 
     # ---- results -----------------------------------------------------------------
     def interactions(self) -> int:

@@ -15,6 +15,7 @@ import ctypes as C
 import os
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -74,6 +75,7 @@ _sig = {
     "p3t_destroy": (None, [_CTX]),
     "p3t_set_params": (C.c_int, [_CTX, C.POINTER(Params)]),
     "p3t_reserve": (C.c_int, [_CTX, C.c_int64]),
+    "p3t_set_segments": (C.c_int, [_CTX, C.c_int64, C.POINTER(C.c_int64)]),
     "p3t_cutoffs": (C.c_int, [_CTX, C.POINTER(Particles), _vp]),
     "p3t_build_tree": (C.c_int, [_CTX, C.POINTER(Particles), C.c_int, _vp]),
     "p3t_soft_force": (C.c_int, [_CTX, C.POINTER(Particles), _vp, _vp, _vp, _vp, _vp]),
@@ -201,6 +203,17 @@ def p3t_reserve(ctx, n: int) -> None:
     _check(_lib.p3t_reserve(ctx, int(n)), "p3t_reserve")
 
 
+def p3t_set_segments(ctx, seg_off) -> None:
+    """The particles form len(seg_off) - 1 independent systems, system d
+    being [seg_off[d], seg_off[d + 1]) (host offsets, seg_off[0] = 0)."""
+    off = np.ascontiguousarray(np.asarray(seg_off, dtype=np.int64))
+    if off.ndim != 1 or off.size < 2:
+        raise ValueError("seg_off needs nseg + 1 >= 2 offsets")
+    _check(_lib.p3t_set_segments(ctx, off.size - 1,
+                                 off.ctypes.data_as(C.POINTER(C.c_int64))),
+           "p3t_set_segments")
+
+
 def p3t_cutoffs(ctx, st: State, stream=None) -> None:
     p = st.particles()
     _check(_lib.p3t_cutoffs(ctx, C.byref(p), _stream(stream)), "p3t_cutoffs")
@@ -245,7 +258,7 @@ def p3t_hard_step(ctx, st: State, cl: Clusters, dt: float, n_steps: torch.Tensor
 
 
 def p3t_kepler_drift(ctx, st: State, dt: float, stream=None) -> None:
-    """Every particle on its Kepler orbit about the star by dt (row a9 for all)."""
+    """Every particle on its Kepler orbit about the star by dt (the isolated particles' drift for all)."""
     p = st.particles()
     _check(_lib.p3t_kepler_drift(ctx, C.byref(p), float(dt), _stream(stream)),
            "p3t_kepler_drift")
@@ -349,11 +362,14 @@ class SoftStep:
     energy {hard part, kick}.
     """
 
-    def __init__(self, params: Params, st: State, device: int = 0, nb_cap: int | None = None):
+    def __init__(self, params: Params, st: State, device: int = 0, nb_cap: int | None = None,
+                 seg_off=None):
         self.params = params
         self.st = st
         self.n = len(st.m)
         self.ctx = p3t_create(params, device)
+        if seg_off is not None:
+            p3t_set_segments(self.ctx, seg_off)
         p3t_reserve(self.ctx, self.n)
         dev = st.m.device
         self.acc = torch.zeros(3, self.n, dtype=torch.float64, device=dev)

@@ -55,7 +55,7 @@ def test_binding_imports_and_mirrors_names():
 
 
 def test_ensemble_descriptor_table():
-    """Row f1 host logic: disks laid end to end in the shared arrays."""
+    """Ensemble host logic: disks laid end to end in the shared arrays."""
     from paper_2007_15432_gb300 import ensemble as EN
     t = EN.descriptor_table([5, 0, 3, 7])
     assert t.tolist() == [[0, 5], [5, 0], [5, 3], [8, 7]]

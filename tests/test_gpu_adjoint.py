@@ -1,4 +1,4 @@
-"""Row f2: the adjoint of the soft kick-drift-kick on the GPU, through the C ABI.
+"""The adjoint of the soft kick-drift-kick on the GPU, through the C ABI.
 
 * the soft-force VJP (FP64 and FP32 pair arithmetic) against the oracle's
   autograd VJP of the direct sum, element by element;
@@ -142,7 +142,7 @@ def test_kepler_vjp_matches_oracle(mods, dt):
 
 
 def test_kepler_drift_all_matches_oracle_and_hard_step(mods):
-    """p3t_kepler_drift: row a9's drift for every particle, the same bits as
+    """p3t_kepler_drift: the isolated particles' drift for every particle, the same bits as
     p3t_hard_step with every particle single, and the oracle's drift."""
     AD, P = mods
     from oracle import oracle as O

@@ -1,4 +1,4 @@
-"""Row f4 (perfect accretion, Sec. 2.4.1): GPU path vs the oracle through the
+"""Perfect accretion (Sec. 2.4.1): GPU path vs the oracle through the
 C ABI.
 
 Bars: after the hard step, positions and velocities of cluster members

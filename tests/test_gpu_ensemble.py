@@ -1,4 +1,4 @@
-"""Row f1: the batched ensemble.  A captured-graph ensemble step must give
+"""The ensemble with per-disk contexts.  A captured-graph ensemble step must give
 exactly the bits of the same disks stepped one after another and of each disk
 stepped alone (the same kernels on the same data); the autotuner picks one of
 its candidates per size class."""

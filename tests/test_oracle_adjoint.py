@@ -1,4 +1,4 @@
-"""Pins of the adjoint oracle (row f2: gradient of the soft kick-drift-kick).
+"""Pins of the adjoint oracle (gradient of the soft kick-drift-kick).
 
 The oracle states the forward map in plain PyTorch and differentiates it with
 torch.autograd.  Its forward is pinned to the C oracle's direct soft sum and

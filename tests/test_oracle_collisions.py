@@ -1,4 +1,4 @@
-"""Pins of the oracle's perfect-accretion collisions (row f4, Sec. 2.4.1).
+"""Pins of the oracle's perfect-accretion collisions (Sec. 2.4.1).
 
 Pinned against physics the procedure must respect: momentum conservation and
 uniform centre-of-mass motion of an isolated colliding pair, the energy

@@ -1,4 +1,4 @@
-"""Pins of the oracle's cut-off radii (row a1; Eqs. routi2, rsearch)."""
+"""Pins of the oracle's cut-off radii (Eqs. routi2, rsearch)."""
 import numpy as np
 
 from paper_2007_15432_gb300 import disks

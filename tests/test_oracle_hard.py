@@ -1,5 +1,5 @@
-"""Pins of the oracle's hard part: Kepler drift (row a9), Hermite-4 block
-steps (row a8) and the hard force/jerk, plus the energy (row a10).
+"""Pins of the oracle's hard part: Kepler drift, Hermite-4 block
+steps and the hard force/jerk, plus the energy.
 
 Pinned against closed forms (circular orbits, whole periods, conserved
 energy and angular momentum), an independent high-order numerical

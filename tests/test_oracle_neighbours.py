@@ -1,4 +1,4 @@
-"""Pins of the oracle's neighbour predicate and clusters (rows a5, a6).
+"""Pins of the oracle's neighbour predicate and clusters.
 
 Neighbour lists from the tree walk's candidates must equal brute force over
 all pairs; the closest-approach clause is checked against dense sampling of

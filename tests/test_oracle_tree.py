@@ -1,4 +1,4 @@
-"""Pins of the oracle's Morton keys, octree walk and soft force (rows a2-a4).
+"""Pins of the oracle's Morton keys, octree walk and soft force.
 
 Pinned against: a bit-by-bit interleave written out in Python (keys), the
 O(N^2) direct changeover sum (theta = 0 must reduce to it), plain Newtonian
