@@ -15,7 +15,13 @@
 // coordinate (x_i,hi - x_j,hi) + (x_i,lo - x_j,lo) carries the accuracy of an
 // FP64 subtraction rounded to FP32, with no FP64 instruction per pair.  Pair
 // and quadrupole terms are FP32; each batch's FP32 sum is folded into a
-// float-float accumulator.  FP64 path: everything in FP64.
+// float-float accumulator.  The mixed evaluators take the entries of a batch
+// two at a time with packed FP32 pair instructions (add/sub/mul/fma.f32x2:
+// one issue for two lanes' worth of FP32 work per thread), the batch staged
+// so that one 16-byte shared load gives one coordinate of both entries;
+// replicas split a batch by pairs, and each pair slot keeps its own partial
+// sum (even and odd entries) until the batch is folded.  FP64 path:
+// everything in FP64.
 #include "p3t_internal.cuh"
 
 namespace {
@@ -90,11 +96,52 @@ __device__ __forceinline__ void two_sum(float &hi, float &lo, float b) {
   lo += err;
 }
 
+#ifndef P3T_PAIR_UNROLL
+#define P3T_PAIR_UNROLL 1  // pair slots in flight per loop iteration
+#endif
+constexpr int kPairUnroll = P3T_PAIR_UNROLL;
+
+// ---- packed FP32 pairs ----------------------------------------------------------
+// a pair of floats in one 64-bit register (low half: the first value); the
+// .f32x2 instructions round each half as the scalar instruction would
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2_pk(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float f2_lo(f2 v) {
+  return __uint_as_float((unsigned)(v & 0xffffffffull));
+}
+__device__ __forceinline__ float f2_hi(f2 v) { return __uint_as_float((unsigned)(v >> 32)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2 f2_dup(float a) { return f2_pk(a, a); }
+
 // ---- per-target state (one lane per target) ---------------------------------
 template <bool MIXED> struct Target;
 
 template <> struct Target<true> {
-  float xh, yh, zh, xl, yl, zl, inv_ro, rs2;  // rs2: r_search^2 with the FP32 margin
+  f2 X, Y, Z, XL, YL, ZL;              // (hi, hi) and (lo, lo) of each coordinate
+  float inv_ro, rs2;                   // rs2: r_search^2 with the FP32 margin
   float ahx, ahy, ahz, alx, aly, alz;  // float-float accumulators
   float tabs;                          // sum of term magnitudes (conditioning)
   int32_t self;
@@ -109,10 +156,15 @@ template <> struct Target<true> {
     tabs = 0.f;
     if (v) {
       const float4 A = a.spA[ti], B = a.spB[ti];
-      xh = A.x; yh = A.y; zh = A.z; xl = B.x; yl = B.y; zl = B.z; inv_ro = B.w;
+      X = f2_dup(A.x); Y = f2_dup(A.y); Z = f2_dup(A.z);
+      XL = f2_dup(B.x); YL = f2_dup(B.y); ZL = f2_dup(B.z);
+      inv_ro = B.w;
       rs2 = a.srs32[ti];
     } else {  // far away: no force, no candidate
-      xh = yh = zh = 3.0e30f; xl = yl = zl = 0.f; inv_ro = 0.f; rs2 = 0.f;
+      X = Y = Z = f2_dup(3.0e30f);
+      XL = YL = ZL = 0ull;
+      inv_ro = 0.f;
+      rs2 = 0.f;
     }
   }
   __device__ void fold(float bx, float by, float bz) {
@@ -179,43 +231,74 @@ __device__ __forceinline__ void record_candidate(const WalkArgs &a, int32_t i,
 
 // per-warp staging area for one batch of 32 entries
 constexpr int kStageBytes = 32 * 96;
-struct StagePP32 { float4 A[32]; float4 B[32]; float rs[32]; int32_t idx[32]; };
+// mixed p-p batch by entry pairs (2p, 2p + 1): each 16-byte word holds one
+// component of both entries, e.g. axy[p] = (x_2p, x_2p+1, y_2p, y_2p+1) of
+// the hi parts; azw: z and mass; bxy, bzw: lo parts and 1 / r_out
+struct StagePP32 {
+  ulonglong2 axy[16], azw[16], bxy[16], bzw[16];
+  float rs[32];
+  int32_t idx[32];
+};
+// mixed node batch by pairs: centre hi / lo, -M, and the quadrupole
+// (q0xy: xx, yy; q0zw: zz, xy; q1xy: xz, yz)
+struct StageND32 {
+  ulonglong2 hxy[16], hzw[16], lxy[16], lzw[16], q0xy[16], q0zw[16], q1xy[16];
+};
 struct StagePP64 { double x[32], y[32], z[32], m[32], ro[32], rs[32]; int32_t idx[32]; };
 static_assert(sizeof(StagePP32) <= kStageBytes && sizeof(StagePP64) <= kStageBytes &&
-              sizeof(Mom32) * 32 <= kStageBytes && sizeof(Mom64) * 32 <= kStageBytes,
+              sizeof(StageND32) <= kStageBytes && sizeof(Mom64) * 32 <= kStageBytes,
               "stage area");
 
+// entry s of a pair-staged batch: component c (0..3) of word w
+__device__ __forceinline__ void stage_put(ulonglong2 *w, int s, float v0, float v1) {
+  float *f = reinterpret_cast<float *>(&w[s >> 1]);
+  f[s & 1] = v0;
+  f[2 + (s & 1)] = v1;
+}
+
 // ---- particle-particle batch ----------------------------------------------
-// one changeover pair term in FP32 on float-float relative coordinates.  r^2
-// is kept above 1e-30 for the reciprocal square root: a coincident pair (the
-// target itself) has y = 0 < gamma, K = 0 and so adds nothing, and f is
-// formed as ((m K) r^-1) r^-2 so that no factor overflows.  The candidate test
-// compares r^2 with max(r_search^2) (squared and widened in the gather);
-// far-away dummy targets never pass it.
-__device__ __forceinline__ void pp_term(const WalkArgs &a, Target<true> &t,
-                                        const float4 A, const float4 B, float rs2s,
-                                        const int32_t *idx, float &bx, float &by, float &bz,
-                                        unsigned &npp) {
-    const float dx = (t.xh - A.x) + (t.xl - B.x);
-    const float dy = (t.yh - A.y) + (t.yl - B.y);
-    const float dz = (t.zh - A.z) + (t.zl - B.z);
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
-    const float r = r2 * rinv;
-    const float y = r * fminf(t.inv_ro, B.w);
-    const float x = __saturatef(fmaf(y, a.inv1mg_f, a.mgi_f));
-    const float x2 = x * x;
-    const float K = (x2 * x2) * fmaf(fmaf(fmaf(-20.f, x, 70.f), x, -84.f), x, 35.f);
-    const float f = ((A.w * K) * rinv) * (rinv * rinv);
-    bx = fmaf(-f, dx, bx);
-    by = fmaf(-f, dy, by);
-    bz = fmaf(-f, dz, bz);
-    t.tabs = fmaf(f, r, t.tabs);
-    if (r2 < fmaxf(t.rs2, rs2s)) {
-      const int32_t j = *idx;
-      if (j != t.self) record_candidate(a, t.self, j);
-      else --npp;  // the target itself is not a pair
-    }
+// Changeover pair terms in FP32 on float-float relative coordinates, for the
+// two entries of pair slot p at once.  r^2 is kept above 1e-30 for the
+// reciprocal square root: a coincident pair (the target itself) has y = 0 <
+// gamma, K = 0 and so adds nothing, and f is formed as ((m K) r^-1) r^-2 so
+// that no factor overflows.  The candidate test compares r^2 with
+// max(r_search^2) (squared and widened in the gather); far-away dummy targets
+// and the massless dummy entry that pads an odd batch never pass it.  The
+// batch sums are kept negated (B = -sum f dx), which is exact.
+__device__ __forceinline__ void pp_pair(const WalkArgs &a, Target<true> &t,
+                                        const StagePP32 &S, int p, f2 &BX, f2 &BY, f2 &BZ,
+                                        f2 &TB, unsigned &npp) {
+  const ulonglong2 axy = S.axy[p], azw = S.azw[p], bxy = S.bxy[p], bzw = S.bzw[p];
+  const f2 dx = add2(sub2(t.X, axy.x), sub2(t.XL, bxy.x));
+  const f2 dy = add2(sub2(t.Y, axy.y), sub2(t.YL, bxy.y));
+  const f2 dz = add2(sub2(t.Z, azw.x), sub2(t.ZL, bzw.x));
+  const f2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+  const float r2a = f2_lo(r2), r2b = f2_hi(r2);
+  const f2 rinv = f2_pk(rsqrtf(fmaxf(r2a, 1e-30f)), rsqrtf(fmaxf(r2b, 1e-30f)));
+  const f2 r = mul2(r2, rinv);
+  const float ya = f2_lo(r) * fminf(t.inv_ro, f2_lo(bzw.y));
+  const float yb = f2_hi(r) * fminf(t.inv_ro, f2_hi(bzw.y));
+  const f2 x = f2_pk(__saturatef(fmaf(ya, a.inv1mg_f, a.mgi_f)),
+                     __saturatef(fmaf(yb, a.inv1mg_f, a.mgi_f)));
+  const f2 x2 = mul2(x, x);
+  const f2 poly = fma2(fma2(fma2(f2_dup(-20.f), x, f2_dup(70.f)), x, f2_dup(-84.f)), x,
+                       f2_dup(35.f));
+  const f2 K = mul2(mul2(x2, x2), poly);
+  const f2 f = mul2(mul2(mul2(azw.y, K), rinv), mul2(rinv, rinv));
+  BX = fma2(f, dx, BX);
+  BY = fma2(f, dy, BY);
+  BZ = fma2(f, dz, BZ);
+  TB = fma2(f, r, TB);
+  if (r2a < fmaxf(t.rs2, S.rs[2 * p])) {
+    const int32_t j = S.idx[2 * p];
+    if (j != t.self) record_candidate(a, t.self, j);
+    else --npp;  // the target itself is not a pair
+  }
+  if (r2b < fmaxf(t.rs2, S.rs[2 * p + 1])) {
+    const int32_t j = S.idx[2 * p + 1];
+    if (j != t.self) record_candidate(a, t.self, j);
+    else --npp;
+  }
 }
 
 // The targets' bounding box of one walk (float), the largest max(r_search^2,
@@ -243,21 +326,29 @@ __device__ __forceinline__ bool far_from(const FarBox &b, const float4 A, const 
   return d2 > 0.f && d2 >= R2;
 }
 
-// a pair term with K = 1 and no candidate test (the source is far, see above):
-// the same operations as pp_term's K = 1 case, so the same bits
-__device__ __forceinline__ void pp_term_far(Target<true> &t, const float4 A, const float4 B,
-                                            float &bx, float &by, float &bz) {
-    const float dx = (t.xh - A.x) + (t.xl - B.x);
-    const float dy = (t.yh - A.y) + (t.yl - B.y);
-    const float dz = (t.zh - A.z) + (t.zl - B.z);
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float rinv = rsqrtf(r2);
-    const float r = r2 * rinv;
-    const float f = (A.w * rinv) * (rinv * rinv);
-    bx = fmaf(-f, dx, bx);
-    by = fmaf(-f, dy, by);
-    bz = fmaf(-f, dz, bz);
-    t.tabs = fmaf(f, r, t.tabs);
+// pair terms with K = 1 and no candidate test (the batch is far, see above):
+// the same operations as pp_pair's K = 1 case, so the same bits
+__device__ __forceinline__ void pp_pair_far(Target<true> &t, const StagePP32 &S, int p, f2 &BX,
+                                            f2 &BY, f2 &BZ, f2 &TB) {
+  const ulonglong2 axy = S.axy[p], azw = S.azw[p], bxy = S.bxy[p], bzw = S.bzw[p];
+  const f2 dx = add2(sub2(t.X, axy.x), sub2(t.XL, bxy.x));
+  const f2 dy = add2(sub2(t.Y, axy.y), sub2(t.YL, bxy.y));
+  const f2 dz = add2(sub2(t.Z, azw.x), sub2(t.ZL, bzw.x));
+  const f2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+  const f2 rinv = f2_pk(rsqrtf(f2_lo(r2)), rsqrtf(f2_hi(r2)));
+  const f2 r = mul2(r2, rinv);
+  const f2 f = mul2(mul2(azw.y, rinv), mul2(rinv, rinv));
+  BX = fma2(f, dx, BX);
+  BY = fma2(f, dy, BY);
+  BZ = fma2(f, dz, BZ);
+  TB = fma2(f, r, TB);
+}
+
+// the batch sums of the even and odd slots into the target: the force sums
+// negated back (B = -sum), the magnitude sum as it is
+__device__ __forceinline__ void fold_pairs(Target<true> &t, f2 BX, f2 BY, f2 BZ, f2 TB) {
+  t.fold(-(f2_lo(BX) + f2_hi(BX)), -(f2_lo(BY) + f2_hi(BY)), -(f2_lo(BZ) + f2_hi(BZ)));
+  t.tabs += f2_lo(TB) + f2_hi(TB);
 }
 
 __device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<true> &t, const int32_t *list,
@@ -266,30 +357,37 @@ __device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<true> &t, cons
   StagePP32 &S = *reinterpret_cast<StagePP32 *>(stage);
   const int lane = threadIdx.x & 31;
   bool near = false;
+  float4 A = make_float4(1.0e18f, 1.0e18f, 1.0e18f, 0.f), B = make_float4(0.f, 0.f, 0.f, 0.f);
+  float rs = 0.f;
+  int32_t j = -1;
   if (lane < nsrc) {
-    const int32_t j = list[lane];
-    const float4 A = __ldg(&a.spA[j]), B = __ldg(&a.spB[j]);
-    const float rs = __ldg(&a.srs32[j]);
-    S.A[lane] = A;
-    S.B[lane] = B;
-    S.rs[lane] = rs;
-    S.idx[lane] = j;
+    j = list[lane];
+    A = __ldg(&a.spA[j]);
+    B = __ldg(&a.spB[j]);
+    rs = __ldg(&a.srs32[j]);
     near = !far_from(box, A, B, rs);
   }
+  // lanes past the batch stage a massless dummy far from everything
+  stage_put(S.axy, lane, A.x, A.y);
+  stage_put(S.azw, lane, A.z, A.w);
+  stage_put(S.bxy, lane, B.x, B.y);
+  stage_put(S.bzw, lane, B.z, B.w);
+  S.rs[lane] = rs;
+  S.idx[lane] = j;
   const bool any_near = __any_sync(0xffffffffu, near);
   __syncwarp();
-  float bx = 0.f, by = 0.f, bz = 0.f;
+  f2 BX = 0ull, BY = 0ull, BZ = 0ull, TB = 0ull;
   npp += (t.valid && t.rep == 0) ? (unsigned)nsrc : 0u;
+  const int np = (nsrc + 1) >> 1;
   if (any_near) {
-#pragma unroll 2
-    for (int s = t.rep; s < nsrc; s += t.nrep)
-      pp_term(a, t, S.A[s], S.B[s], S.rs[s], &S.idx[s], bx, by, bz, npp);
+#pragma unroll kPairUnroll
+    for (int p = t.rep; p < np; p += t.nrep) pp_pair(a, t, S, p, BX, BY, BZ, TB, npp);
   } else {
-#pragma unroll 2
-    for (int s = t.rep; s < nsrc; s += t.nrep) pp_term_far(t, S.A[s], S.B[s], bx, by, bz);
+#pragma unroll kPairUnroll
+    for (int p = t.rep; p < np; p += t.nrep) pp_pair_far(t, S, p, BX, BY, BZ, TB);
   }
   __syncwarp();
-  t.fold(bx, by, bz);
+  fold_pairs(t, BX, BY, BZ, TB);
 }
 
 __device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<false> &t, const int32_t *list,
@@ -327,46 +425,62 @@ __device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<false> &t, con
 }
 
 // ---- particle-node batch (monopole + traceless quadrupole) ---------------
-// a += -M r/r^3 + Q.r/r^5 - (5/2)(r.Q.r) r/r^7, r = x_i - com
-__device__ __forceinline__ void node_term(Target<true> &t, const float4 hi, const float4 lo,
-                                          const float4 q0, const float4 q1, float &bx,
-                                          float &by, float &bz) {
-    const float dx = (t.xh - hi.x) + (t.xl - lo.x);
-    const float dy = (t.yh - hi.y) + (t.yl - lo.y);
-    const float dz = (t.zh - hi.z) + (t.zl - lo.z);
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
-    const float rinv2 = rinv * rinv;
-    const float rinv3 = rinv2 * rinv;
-    const float rinv5 = rinv3 * rinv2;
-    const float qx = fmaf(q0.x, dx, fmaf(q0.w, dy, q1.x * dz));
-    const float qy = fmaf(q0.w, dx, fmaf(q0.y, dy, q1.y * dz));
-    const float qz = fmaf(q1.x, dx, fmaf(q1.y, dy, q0.z * dz));
-    const float rqr = fmaf(dx, qx, fmaf(dy, qy, dz * qz));
-    const float c = fmaf(-2.5f * rqr, rinv5 * rinv2, -hi.w * rinv3);
-    bx = fmaf(c, dx, fmaf(qx, rinv5, bx));
-    by = fmaf(c, dy, fmaf(qy, rinv5, by));
-    bz = fmaf(c, dz, fmaf(qz, rinv5, bz));
-    t.tabs = fmaf(hi.w, rinv2, t.tabs);
+// a += -M r/r^3 + Q.r/r^5 - (5/2)(r.Q.r) r/r^7, r = x_i - com, for the two
+// nodes of pair slot p (the stage holds -M)
+__device__ __forceinline__ void node_pair(Target<true> &t, const StageND32 &S, int p, f2 &BX,
+                                          f2 &BY, f2 &BZ, f2 &TB) {
+  const ulonglong2 hxy = S.hxy[p], hzw = S.hzw[p], lxy = S.lxy[p], lzw = S.lzw[p];
+  const ulonglong2 q0xy = S.q0xy[p], q0zw = S.q0zw[p], q1xy = S.q1xy[p];
+  const f2 dx = add2(sub2(t.X, hxy.x), sub2(t.XL, lxy.x));
+  const f2 dy = add2(sub2(t.Y, hxy.y), sub2(t.YL, lxy.y));
+  const f2 dz = add2(sub2(t.Z, hzw.x), sub2(t.ZL, lzw.x));
+  const f2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+  const f2 rinv = f2_pk(rsqrtf(fmaxf(f2_lo(r2), 1e-30f)), rsqrtf(fmaxf(f2_hi(r2), 1e-30f)));
+  const f2 rinv2 = mul2(rinv, rinv);
+  const f2 rinv3 = mul2(rinv2, rinv);
+  const f2 rinv5 = mul2(rinv3, rinv2);
+  // q0xy = (xx, yy), q0zw = (zz, xy), q1xy = (xz, yz)
+  const f2 qx = fma2(q0xy.x, dx, fma2(q0zw.y, dy, mul2(q1xy.x, dz)));
+  const f2 qy = fma2(q0zw.y, dx, fma2(q0xy.y, dy, mul2(q1xy.y, dz)));
+  const f2 qz = fma2(q1xy.x, dx, fma2(q1xy.y, dy, mul2(q0zw.x, dz)));
+  const f2 rqr = fma2(dx, qx, fma2(dy, qy, mul2(dz, qz)));
+  const f2 c = fma2(mul2(f2_dup(-2.5f), rqr), mul2(rinv5, rinv2), mul2(hzw.y, rinv3));
+  BX = fma2(c, dx, fma2(qx, rinv5, BX));
+  BY = fma2(c, dy, fma2(qy, rinv5, BY));
+  BZ = fma2(c, dz, fma2(qz, rinv5, BZ));
+  TB = fma2(hzw.y, rinv2, TB);  // -M / r^2
 }
 
 __device__ __forceinline__ void eval_nodes(const WalkArgs &a, Target<true> &t,
                                            const int32_t *list, int nnd, void *stage,
                                            unsigned &npn) {
-  Mom32 *S = reinterpret_cast<Mom32 *>(stage);
+  StageND32 &S = *reinterpret_cast<StageND32 *>(stage);
   const int lane = threadIdx.x & 31;
+  // lanes past the batch stage a massless, quadrupole-free dummy far away
+  float4 hi = make_float4(1.0e18f, 1.0e18f, 1.0e18f, 0.f), lo = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 q0 = lo, q1 = lo;
   if (lane < nnd) {
     const Mom32 *m = &a.mom32[list[lane]];
-    S[lane].hi = __ldg(&m->hi); S[lane].lo = __ldg(&m->lo);
-    S[lane].q0 = __ldg(&m->q0); S[lane].q1 = __ldg(&m->q1);
+    hi = __ldg(&m->hi); lo = __ldg(&m->lo);
+    q0 = __ldg(&m->q0); q1 = __ldg(&m->q1);
   }
+  stage_put(S.hxy, lane, hi.x, hi.y);
+  stage_put(S.hzw, lane, hi.z, -hi.w);
+  stage_put(S.lxy, lane, lo.x, lo.y);
+  stage_put(S.lzw, lane, lo.z, lo.w);
+  stage_put(S.q0xy, lane, q0.x, q0.y);
+  stage_put(S.q0zw, lane, q0.z, q0.w);
+  stage_put(S.q1xy, lane, q1.x, q1.y);
   __syncwarp();
-  float bx = 0.f, by = 0.f, bz = 0.f;
+  f2 BX = 0ull, BY = 0ull, BZ = 0ull, TB = 0ull;
   npn += (t.valid && t.rep == 0) ? (unsigned)nnd : 0u;
-#pragma unroll 2
-  for (int s = t.rep; s < nnd; s += t.nrep) node_term(t, S[s].hi, S[s].lo, S[s].q0, S[s].q1, bx, by, bz);
+  const int np = (nnd + 1) >> 1;
+#pragma unroll kPairUnroll
+  for (int p = t.rep; p < np; p += t.nrep) node_pair(t, S, p, BX, BY, BZ, TB);
   __syncwarp();
-  t.fold(bx, by, bz);
+  // force sums as they are; the magnitude sum was of -M / r^2
+  t.fold(f2_lo(BX) + f2_hi(BX), f2_lo(BY) + f2_hi(BY), f2_lo(BZ) + f2_hi(BZ));
+  t.tabs -= f2_lo(TB) + f2_hi(TB);
 }
 
 __device__ __forceinline__ void eval_nodes(const WalkArgs &a, Target<false> &t,
@@ -576,7 +690,8 @@ template <bool MIXED> struct GroupEval {
 
 // the walk's FarBox from its (valid) targets, written by lane 0
 __device__ __forceinline__ void far_box(const Target<true> &t, FarBox &b) {
-  const float x = t.xh + t.xl, y = t.yh + t.yl, z = t.zh + t.zl;
+  const float x = f2_lo(t.X) + f2_lo(t.XL), y = f2_lo(t.Y) + f2_lo(t.YL),
+              z = f2_lo(t.Z) + f2_lo(t.ZL);
   const float inf = __int_as_float(0x7f800000);
   float lo0 = t.valid ? x : inf, lo1 = t.valid ? y : inf, lo2 = t.valid ? z : inf;
   float hi0 = t.valid ? x : -inf, hi1 = t.valid ? y : -inf, hi2 = t.valid ? z : -inf;
@@ -706,8 +821,13 @@ struct RefineEval {
   }
 };
 
+#ifndef P3T_WALK_MINB_MIXED
+#define P3T_WALK_MINB_MIXED 6  // resident blocks per SM asked of the mixed walk
+#endif
+
 template <bool MIXED>
-__global__ void __launch_bounds__(kWarps * 32) k_walk(const WalkArgs a) {
+__global__ void __launch_bounds__(kWarps * 32, MIXED ? P3T_WALK_MINB_MIXED : 1)
+    k_walk(const WalkArgs a) {
   __shared__ int32_t s_pp[kWarps][kPPCap];
   __shared__ int32_t s_nd[kWarps][kNDCap];
   __shared__ int32_t s_big[kWarps][kBigCap];
@@ -826,8 +946,9 @@ __global__ void k_walk_post(int64_t *cnt, int64_t cand_cap, int64_t refine_cap,
 
 }  // namespace
 
-// 7 blocks of 4 warps: 72 registers and 30.5 KB of shared memory a block fit 7
-int p3t_walk_blocks_per_sm() { return 7; }
+// blocks of 4 warps resident per SM: the mixed walk is compiled for 6 (80
+// registers; 30.5 KB of shared memory a block)
+int p3t_walk_blocks_per_sm() { return P3T_WALK_MINB_MIXED; }
 
 int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
                        double *ay, double *az, uint64_t *counts,
@@ -881,7 +1002,7 @@ int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 
-// persistent walk warps for a context of up to n particles: 7 blocks per SM,
+// persistent walk warps for a context of up to n particles: 6 blocks per SM,
 // fewer for small systems (a block for every 256 particles: a group walk
 // takes a warp, and a group holds tens of particles)
 int64_t p3t_walk_warps(int num_sms, int64_t n) {
