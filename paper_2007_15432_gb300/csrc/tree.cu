@@ -113,12 +113,25 @@ __global__ void k_cut_segbins(SegView sv, int vran_bins, const unsigned long lon
   }
 }
 
+// bin of ln R among nb bins uniform on [lmin, lmax]: floor(nb (ln R - lmin) /
+// (lmax - lmin)) clamped to [0, nb - 1], decided in FP64.  An FP32 estimate
+// decides it first when no integer lies within its error bound of the
+// estimate (logf and the roundings to FP32 stay within 2e-6 absolute on ln R
+// and on each bound); otherwise the FP64 expression is evaluated.
 __device__ __forceinline__ int cut_bin(double R, double Rmin, double Rmax,
                                        double lmin, double lmax, int nb) {
   int k = 0;
   if (Rmax > Rmin && R > Rmin) {
-    double t = (log(R) - lmin) / (lmax - lmin);
-    double f = floor(t * (double)nb);
+    const float lminf = (float)lmin, span = (float)lmax - lminf;
+    const float tf = (logf((float)R) - lminf) / span * (float)nb;
+    const float margin = 8e-6f * (float)nb / span + 1e-3f;
+    double f;
+    if (span > 0.0f && margin < 0.25f && floorf(tf - margin) == floorf(tf + margin)) {
+      f = (double)floorf(tf);
+    } else {
+      double t = (log(R) - lmin) / (lmax - lmin);
+      f = floor(t * (double)nb);
+    }
     k = f < 0.0 ? 0 : (f > (double)(nb - 1) ? nb - 1 : (int)f);
   }
   return k;
@@ -140,13 +153,19 @@ __global__ void k_cut_u2(SegView sv, const double *x, const double *y, const dou
   // one segment: its range here; several: per particle below
   const double Rmin0 = ord_double(bits[0]), Rmax0 = ord_double(bits[1]);
   const double lmin0 = log(Rmin0), lmax0 = log(Rmax0);
+  const double smu = sqrt(mu);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double R = sqrt(x[i] * x[i] + y[i] * y[i]);
-    double r = sqrt(x[i] * x[i] + y[i] * y[i] + z[i] * z[i]);
-    double vk = sqrt(mu / r);
+    const double R2 = x[i] * x[i] + y[i] * y[i];
+    const double R = sqrt(R2);
+    const double r = sqrt(R2 + z[i] * z[i]);
+    const double vk = smu * rsqrt(r);  // sqrt(mu / r)
     double px = 0.0, py = 0.0;
-    if (R > 0.0) { px = -y[i] / R; py = x[i] / R; }
+    if (R > 0.0) {
+      const double iR = rsqrt(R2);
+      px = -y[i] * iR;
+      py = x[i] * iR;
+    }
     double ux = vx[i] - vk * px, uy = vy[i] - vk * py, uz = vz[i];
     u2[i] = ux * ux + uy * uy + uz * uz;
     int k;
@@ -220,20 +239,36 @@ __global__ void k_cut_binsum(int nb, const int64_t *boff, const int32_t *sorted_
   }
 }
 
+// x^(1/3) for x >= 0: the inverse cube root z = x^(-1/3) by Newton's method
+// on f(z) = z^-3 - x, z <- z (4 - x z^3) / 3 (quadratic convergence), from an
+// FP32 seed (relative error ~1e-7) in two steps, then x^(1/3) = x z^2; inputs
+// outside the FP32 seed's normal range take cbrt
+__device__ __forceinline__ double cbrt_pos(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return cbrt(x);
+  double z = (double)rcbrtf((float)x);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double z3 = z * z * z;
+    z = z * (4.0 - x * z3) * (1.0 / 3.0);
+  }
+  return x * z * z;
+}
+
 __global__ void k_cut_final(SegView sv, const double *x, const double *y,
                             const double *z, const double *vx, const double *vy,
                             const double *vz, const double *m, p3t_params prm,
                             unsigned long long *bits, const int32_t *bin,
                             const double *bvr, double *r_out, double *r_search) {
-  const double mu = prm.G * prm.m_star;
+  const double imu = 1.0 / (prm.G * prm.m_star), i3ms = 1.0 / (3.0 * prm.m_star);
   const int64_t n = sv.n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double r = sqrt(x[i] * x[i] + y[i] * y[i] + z[i] * z[i]);
+    const double r2 = x[i] * x[i] + y[i] * y[i] + z[i] * z[i];
+    const double ir = rsqrt(r2);
     double v2 = vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i];
-    double alpha = 2.0 / r - v2 / mu;  // 1/a, vis-viva
-    double a = alpha > 0.0 ? 1.0 / alpha : r;
-    double rhill = cbrt(m[i] / (3.0 * prm.m_star)) * a;
+    double alpha = 2.0 * ir - v2 * imu;  // 1/a, vis-viva
+    double a = alpha > 0.0 ? 1.0 / alpha : r2 * ir;
+    double rhill = cbrt_pos(m[i] * i3ms) * a;
     const double vr = bvr[bin[i]];
     // Eq. routi2 (P3T_CUT_HILL_VRAN) or Eq. routi (the other two); Eq. rsearch
     const double ro = prm.cutoff_mode == P3T_CUT_HILL_VRAN
