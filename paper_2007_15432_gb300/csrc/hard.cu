@@ -232,6 +232,12 @@ __global__ void k_kepler_all(p3t_particles p, double dt, KepConst K, DevStatus *
 // for the neighbours).  One thread does this bookkeeping in a fixed order;
 // collisions are rare.
 constexpr int kHMax = 128;  // largest cluster kept in shared memory
+// largest cluster integrated by one warp; larger ones take a block of four
+// warps, whose pair terms then run on four sub-partitions' FP64 pipes
+#ifndef P3T_HWARP_MAX
+#define P3T_HWARP_MAX 8
+#endif
+constexpr int kHWarpMax = P3T_HWARP_MAX;
 constexpr int32_t kNone = 0x7fffffff;  // no collision partner
 
 template <int KM>
@@ -240,7 +246,11 @@ struct HSmall {  // a cluster of <= KM members
   double p[3][KM], pv[3][KM];
   double a1[3][KM], j1[3][KM], a2e[3][KM], a3[3][KM];
   double m[KM], iro[KM], rp[KM];
-  double T[KM + 1][6];  // one batch: B members x (nc + 1) terms, at most KM + 1
+  // one batch of pair terms: B = NT / (nc + 1) members x (nc + 1) terms, at
+  // most NT (a batch is one pass of the block's threads), and at least the
+  // nc + 1 terms of one member
+  static constexpr int kT = KM + 1 > 32 ? KM + 1 : 32;
+  double T[kT][6];
   int64_t t[KM];
   int32_t lvl[KM], act[KM], set[KM], nset[KM], partner[KM], chg[KM];
 };
@@ -835,6 +845,7 @@ __global__ void __launch_bounds__(NT) k_hermite_block(
     int64_t *cursor, HBig big, CollOut co, DevStatus *st) {
   __shared__ HCtl C;
   extern __shared__ __align__(16) unsigned char hsm[];
+  static_assert(BIG || HSmall<KM>::kT >= NT, "a batch of pair terms must fit HSmall::T");
   HSmall<KM> *Sm = reinterpret_cast<HSmall<KM> *>(hsm);
   const int tid = threadIdx.x;
   const int64_t ncl = *d_ncl;
@@ -1106,15 +1117,17 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
   P3T_CUDA_TRY(cudaStreamWaitEvent(c->aux[1], c->ev_fork, 0));
   const int64_t ncl_max = (n / 2) > 0 ? n / 2 : 1;
   const int64_t nbig = c->num_sms < 32 ? c->num_sms : 32;
-  // clusters of 2..32 members: a warp each (stream aux[0]); 33..128: a
-  // 128-thread block each, then > 128 (stream aux[1])
-  k_hermite_block<32, 32, false><<<(unsigned)p3t_grid(ncl_max * 32, 32, (int64_t)c->num_sms * 16),
-                                   32, sizeof(HSmall<32>), c->aux[0]>>>(
-      &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, 2, 32, steps, c->hcursor, big, co,
-      c->status);
+  // clusters of 2..kHWarpMax members: a warp each (stream aux[0]); up to
+  // 128: a 128-thread block each, then > 128 (stream aux[1])
+  k_hermite_block<32, kHWarpMax, false><<<(unsigned)p3t_grid(ncl_max * 32, 32,
+                                                             (int64_t)c->num_sms * 16),
+                                          32, sizeof(HSmall<kHWarpMax>), c->aux[0]>>>(
+      &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, 2, kHWarpMax, steps, c->hcursor,
+      big, co, c->status);
   k_hermite_block<128, kHMax, false><<<(unsigned)p3t_grid(ncl_max * 128, 128, (int64_t)c->num_sms * 2),
                                        128, sizeof(HSmall<kHMax>), c->aux[1]>>>(
-      &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, 33, kHMax, steps, c->hcursor + 1,
+      &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, kHWarpMax + 1, kHMax, steps,
+      c->hcursor + 1,
       big, co, c->status);
   k_hermite_block<128, 1, true><<<(unsigned)p3t_grid(ncl_max, 1, nbig), 128, 0, c->aux[1]>>>(
       &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, kHMax + 1, 0x7fffffff, steps,
