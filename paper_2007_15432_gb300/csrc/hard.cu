@@ -356,12 +356,46 @@ __device__ __forceinline__ int ilogb_fast(double x) {
   return (e > 0 && e < 0x7ff) ? e - 1023 : ilogb(x);
 }
 
+// Conversions by integer operations.  On this part a conversion between FP64
+// and FP32 or from an integer to FP64 takes the FP64 pipe like an FP64
+// multiply (about 64 cycles of a sub-partition); along the serial block steps
+// of a close encounter these sit on the critical path, so where the result is
+// a normal number they are done on the bits instead, with the same results.
+// (float)(a 2^k), rounded to nearest even, for a 2^k in FP32's normal range
+__device__ __forceinline__ float d2f_scaled(double a, int k) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+  const int ed = (int)((b >> 52) & 0x7ff);
+  const int ef = ed - 1023 + k + 127;
+  if (ed == 0 || ed == 0x7ff || ef <= 0 || ef >= 255) return (float)ldexp_fast(a, k);
+  const unsigned long long m = b & 0xfffffffffffffull;
+  unsigned r = ((unsigned)ef << 23) | (unsigned)(m >> 29);
+  const unsigned long long rem = m & 0x1fffffffull, half = 0x10000000ull;
+  if (rem > half || (rem == half && (r & 1u))) ++r;  // a carry into the exponent is right
+  return __uint_as_float(r | ((unsigned)(b >> 32) & 0x80000000u));
+}
+// (double)f, exact
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const int ef = (int)((u >> 23) & 0xff);
+  if (ef == 0 || ef == 0xff) return (double)f;
+  return __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32 |
+                                          (unsigned long long)(ef - 127 + 1023) << 52 |
+                                          (unsigned long long)(u & 0x7fffffu) << 29));
+}
+// (double)x for 0 <= x < 2^53, exact
+__device__ __forceinline__ double i2d_exact(int64_t x) {
+  if (x <= 0) return (double)x;
+  const int e = 63 - __clzll(x);
+  return __longlong_as_double((long long)((unsigned long long)(e + 1023) << 52 |
+                                          (((unsigned long long)x << (52 - e)) &
+                                           0xfffffffffffffull)));
+}
+
 // The step estimates only choose a power-of-two step: formed in FP32 from
 // components scaled by an exact power of two 2^k (j by s, a2 by s^2, a3 by
 // s^3, s = 2^e close to the step) so that nothing overflows FP32.
 __device__ __forceinline__ float norm3f(double a, double b, double c, int k) {
-  const float x = (float)ldexp_fast(a, k), y = (float)ldexp_fast(b, k),
-              z = (float)ldexp_fast(c, k);
+  const float x = d2f_scaled(a, k), y = d2f_scaled(b, k), z = d2f_scaled(c, k);
   return sqrtf(x * x + y * y + z * z);
 }
 
@@ -409,7 +443,7 @@ __device__ __forceinline__ int first_level(const V &S, int k, const p3t_params &
   const int e = ilogb_fast(dt);
   const float an = norm3f(S.a(0, k), S.a(1, k), S.a(2, k), 0);
   const float jn = norm3f(S.j(0, k), S.j(1, k), S.j(2, k), e);
-  const double dtd = jn > 0.0f ? ldexp_fast((double)((float)prm.eta0 * an / jn), e) : dt;
+  const double dtd = jn > 0.0f ? ldexp_fast(f2d_exact((float)prm.eta0 * an / jn), e) : dt;
   return quantise_level(dtd, dt, 0, t, underflow);
 }
 
@@ -712,6 +746,14 @@ __device__ void integrate_cluster(const V &S, HCtl &C, double (*Tb)[6], int64_t 
   const double unit = ldexp(dt, -P3T_KMAX);
   const double idt = 1.0 / dt;
   const double i1mg = 1.0 / (1.0 - prm.gamma);
+  // a step of level l is D = unit 2^(40 - l) exactly, so D^n = RN(unit^n)
+  // 2^(n (40 - l)) and RN(D^n c) = RN(unit^n c) 2^(n (40 - l)) with unit^n
+  // formed by the same successive products: the corrector's powers of D and
+  // of 1/D are these constants shifted in the exponent (the same bits as the
+  // products, no FP64 instruction)
+  const double u2 = unit * unit, u3 = u2 * unit, u4 = u3 * unit, u5 = u4 * unit;
+  const double c3u = u3 * (1.0 / 6.0), c4u = u4 * (1.0 / 24.0), c5u = u5 * (1.0 / 120.0);
+  const double idt2 = idt * idt, idt3 = idt2 * idt;
   for (int k = item; k < nc; k += NT) {
     const int32_t i = cl_mem[off + k];
     S.x(0, k) = p.x[i]; S.x(1, k) = p.y[i]; S.x(2, k) = p.z[i];
@@ -775,11 +817,13 @@ __device__ void integrate_cluster(const V &S, HCtl &C, double (*Tb)[6], int64_t 
     // predict every member (component items)
     for (int i = item; i < nc * 3; i += NT) {
       const int k = i / 3, q = i - 3 * k;
-      const double D = (double)(tn - S.t(k)) * unit;
+      const double D = i2d_exact(tn - S.t(k)) * unit;
       const double jq = S.j(q, k), aq = S.a(q, k), vq = S.v(q, k);
       // Horner form, fused: x + D (v + D (a/2 + D j/6)), v + D (a + D j/2)
-      S.p(q, k) = __fma_rn(__fma_rn(__fma_rn(jq * (1.0 / 6.0), D, aq * 0.5), D, vq), D, S.x(q, k));
-      S.pv(q, k) = __fma_rn(__fma_rn(jq * 0.5, D, aq), D, vq);
+      // (the halvings exact, as exponent shifts)
+      S.p(q, k) = __fma_rn(__fma_rn(__fma_rn(jq * (1.0 / 6.0), D, ldexp_fast(aq, -1)), D, vq),
+                           D, S.x(q, k));
+      S.pv(q, k) = __fma_rn(__fma_rn(ldexp_fast(jq, -1), D, aq), D, vq);
     }
     __syncthreads();
     nact = build_list<NT>(S, C, nc, [&](int k) { return S.t(k) + (T >> S.lvl(k)) == tn; });
@@ -788,18 +832,18 @@ __device__ void integrate_cluster(const V &S, HCtl &C, double (*Tb)[6], int64_t 
     for (int i = item; i < nact * 3; i += NT) {
       const int b = i / 3, q = i - 3 * b;
       const int k = S.act(b);
-      const double D = (double)(T >> S.lvl(k)) * unit;
-      const double D2 = D * D, D3 = D2 * D, D4 = D3 * D, D5 = D4 * D;
+      const int lv = S.lvl(k), sh = P3T_KMAX - lv;
+      const double D = ldexp_fast(unit, sh);
       // 1 / D = 2^lvl (1 / dt) exactly (D = dt 2^-lvl): a product, not a division
-      const double iD = idt * __longlong_as_double((long long)(1023 + S.lvl(k)) << 52);
-      const double iD2 = iD * iD, iD3 = iD2 * iD;
+      const double iD2 = ldexp_fast(idt2, 2 * lv), iD3 = ldexp_fast(idt3, 3 * lv);
       const double da = S.a(q, k) - S.a1(q, k);
       const double j0 = S.j(q, k), j1 = S.j1(q, k);
       const double A2 = __fma_rn(-D, __fma_rn(2.0, j1, 4.0 * j0), -6.0 * da) * iD2;
       const double A3 = __fma_rn(6.0 * D, j0 + j1, 12.0 * da) * iD3;
       S.a2e(q, k) = __fma_rn(D, A3, A2);
       S.a3(q, k) = A3;
-      const double c3 = D3 * (1.0 / 6.0), c4 = D4 * (1.0 / 24.0), c5 = D5 * (1.0 / 120.0);
+      const double c3 = ldexp_fast(c3u, 3 * sh), c4 = ldexp_fast(c4u, 4 * sh),
+                   c5 = ldexp_fast(c5u, 5 * sh);
       S.x(q, k) = __fma_rn(A3, c5, __fma_rn(A2, c4, S.p(q, k)));
       S.v(q, k) = __fma_rn(A3, c4, __fma_rn(A2, c3, S.pv(q, k)));
       S.a(q, k) = S.a1(q, k);
@@ -809,7 +853,7 @@ __device__ void integrate_cluster(const V &S, HCtl &C, double (*Tb)[6], int64_t 
     // new steps of the active members
     for (int b = item; b < nact; b += NT) {
       const int k = S.act(b);
-      const double D = (double)(T >> S.lvl(k)) * unit;
+      const double D = ldexp_fast(unit, P3T_KMAX - S.lvl(k));
       const int e = ilogb_fast(D);  // dt = sqrt(eta num_s / den_s) s
       const float an = norm3f(S.a(0, k), S.a(1, k), S.a(2, k), 0);
       const float jn = norm3f(S.j(0, k), S.j(1, k), S.j(2, k), e);
@@ -817,7 +861,7 @@ __device__ void integrate_cluster(const V &S, HCtl &C, double (*Tb)[6], int64_t 
       const float a3n = norm3f(S.a3(0, k), S.a3(1, k), S.a3(2, k), 3 * e);
       const float num = an * a2n + jn * jn, den = jn * a3n + a2n * a2n;
       const double dtd =
-          den > 0.0f ? ldexp_fast((double)sqrtf((float)prm.eta * num / den), e) : dt;
+          den > 0.0f ? ldexp_fast(f2d_exact(sqrtf((float)prm.eta * num / den)), e) : dt;
       S.t(k) = tn;
       S.lvl(k) = quantise_level(dtd, dt, S.lvl(k), tn, underflow);
       if (S.partner(k) != kNone) C.any = 1;
