@@ -258,7 +258,9 @@ def run_ours(args):
     prm = P.Params(theta=0.5, precision=prec, eta=0.01, eta0=0.001, group_size=args.group_size,
                    f_radius=args.f_radius)
     from paper_2007_15432_gb300 import disks
-    st = P.State.from_numpy(s, device=dev, r_phys=disks.physical_radius(s["m"]))
+    # one (10, n) device tensor holds the state (the end-to-end leg moves it
+    # in one copy each way)
+    st, stbuf = P.State.from_numpy_packed(s, device=dev, r_phys=disks.physical_radius(s["m"]))
     ss = P.SoftStep(prm, st, device=local)
     stream = torch.cuda.current_stream(dev)
     ss.init(update_cutoffs=True)            # cut-off radii at init, then after merges
@@ -349,10 +351,10 @@ def run_ours(args):
     flops_per_launch = (FLOP_PP * c[:, 0, 0] + FLOP_PN * c[:, 0, 1]).mean()
 
     # ---- end to end through the C ABI with host buffers --------------------
-    keys = ("x", "y", "z", "vx", "vy", "vz", "m", "r_out", "r_search", "r_phys")
-    n0 = len(st.m)
-    host = {k: getattr(st, k).cpu().pin_memory() for k in keys}
-    host_out = {k: torch.empty_like(host[k]).pin_memory() for k in keys}
+    # the state's (10, n) block: x, y, z, vx, vy, vz, m, r_out, r_search,
+    # r_phys (rows shortened by merges keep their storage; the block moves whole)
+    host = stbuf.cpu().pin_memory()
+    host_out = torch.empty_like(host).pin_memory()
     E = max(1, args.e2e_steps)
     e2e_counts = torch.zeros(E, 2, 2, dtype=torch.int64, device=dev)
     h2d = d2h = 0
@@ -360,18 +362,13 @@ def run_ours(args):
     barrier(dist)
     t0 = time.perf_counter()
     for k in range(E):
-        n = len(st.m)
-        for key in keys:
-            getattr(st, key).copy_(host[key][:n], non_blocking=True)
-        h2d += 8 * n * len(keys)
+        stbuf.copy_(host, non_blocking=True)
+        h2d += host.numel() * host.element_size()
         step(None, counts=e2e_counts[k])
-        n = len(st.m)
-        for key in keys:
-            host_out[key][:n].copy_(getattr(st, key), non_blocking=True)
-        d2h += 8 * n * len(keys)
+        host_out.copy_(stbuf, non_blocking=True)
+        d2h += host_out.numel() * host_out.element_size()
         torch.cuda.synchronize(dev)
-        for key in keys:   # the result is the next step's input
-            host[key], host_out[key] = host_out[key], host[key]
+        host, host_out = host_out, host   # the result is the next step's input
     t_e2e = time.perf_counter() - t0
     e2e_inter = float(e2e_counts.sum().item())
     h2d //= E

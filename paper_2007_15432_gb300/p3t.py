@@ -155,6 +155,23 @@ class State:
         return State(t(s["x"]), t(s["y"]), t(s["z"]), t(s["vx"]), t(s["vy"]), t(s["vz"]),
                      t(s["m"]), ro, rs, t(r_phys) if r_phys is not None else None)
 
+    @staticmethod
+    def from_numpy_packed(s: dict, device="cuda", r_out=None, r_search=None, r_phys=None):
+        """Like ``from_numpy``, with the arrays the rows of one (k, n) tensor
+        (x, y, z, vx, vy, vz, m, r_out, r_search[, r_phys]), returned as well,
+        so that the whole state moves between host and device in one copy.
+        After a merge the rows are shortened views of the same storage."""
+        n = len(s["m"])
+        cols = [s[k] for k in ("x", "y", "z", "vx", "vy", "vz", "m")]
+        cols.append(r_out if r_out is not None else np.zeros(n))
+        cols.append(r_search if r_search is not None else np.zeros(n))
+        if r_phys is not None:
+            cols.append(r_phys)
+        buf = torch.as_tensor(np.stack([np.asarray(c, dtype=np.float64) for c in cols]),
+                              dtype=torch.float64).to(device).contiguous()
+        rows = list(buf.unbind(0))
+        return State(*rows[:9], rows[9] if r_phys is not None else None), buf
+
     def _arrays(self):
         return _KEYS + (("r_phys",) if self.r_phys is not None else ())
 
