@@ -147,11 +147,9 @@ struct p3t_ctx {
   double *nrs = nullptr;                   // max r_search per node
   int32_t *node_done = nullptr;            // bottom-up arrival counters
   int32_t *leaf_list = nullptr;            // leaves (BFS ids) in key order
-  int32_t *leaf_of = nullptr;              // sorted particle -> its target group (BFS id)
   int32_t *group_list = nullptr;           // target groups (BFS ids) in key order
   int32_t *group_flag = nullptr;
   int64_t *group_pos = nullptr;
-  int32_t *refine = nullptr;               // targets redone in FP64 (mixed path)
   int32_t *leaf_flag = nullptr;
   int64_t *leaf_pos = nullptr;
   int64_t *bh_table = nullptr;             // Barnes-Hut thresholds per level

@@ -614,16 +614,12 @@ __global__ void k_group_flags(const int64_t *d_nnode, int64_t node_cap,
 // group list in key order, and every member's group
 __global__ void k_group_list(const int64_t *d_nnode, int64_t node_cap,
                              const int32_t *group_flag, const int64_t *group_pos,
-                             const int32_t *pre2bfs, const TreeNode *node,
-                             int32_t *group_list, int32_t *group_of) {
+                             const int32_t *pre2bfs, int32_t *group_list) {
   const int64_t nn = min(*d_nnode, node_cap);
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nn;
        p += (int64_t)gridDim.x * blockDim.x) {
     if (!group_flag[p]) continue;
-    const int32_t b = pre2bfs[p];
-    group_list[group_pos[p]] = b;
-    const TreeNode &nd = node[b];
-    for (int32_t i = nd.first; i < nd.first + nd.count; ++i) group_of[i] = b;
+    group_list[group_pos[p]] = pre2bfs[p];
   }
 }
 
@@ -1027,8 +1023,7 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
                            c->scan_state, c->scan_words, c->status, s);
   if (rc) return rc;
   k_group_list<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->group_flag,
-                                               c->group_pos, c->pre2bfs, c->node,
-                                               c->group_list, c->leaf_of);
+                                               c->group_pos, c->pre2bfs, c->group_list);
   // own kernels here (the scans and sorts count themselves): box 3, keys, n,
   // gather, lcp, levels, clamp, nodes_pre, pre2bfs, nodes_bfs, parents,
   // leaf_list, moments (leaves, level offsets, 21 levels), group_flags,

@@ -54,11 +54,6 @@ struct WalkArgs {
   unsigned long long *counts;  // [2] n_pp, n_pnode (may be null)
   int64_t *cursor;
   DevStatus *st;
-  int32_t *refine;                 // targets whose FP32 sum is ill-conditioned
-  unsigned long long *refine_count;
-  int64_t refine_cap;
-  const int64_t *d_nrefine;        // refine count clamped to the capacity
-  const int32_t *leaf_of;          // sorted index -> its leaf (BFS id)
   SegView seg;                     // segments: the root of segment d is node d
   double G, gamma;
   float inv1mg_f, mgi_f;           // 1 / (1 - gamma), -gamma / (1 - gamma)
@@ -509,34 +504,34 @@ __device__ __forceinline__ void eval_nodes(const WalkArgs &a, Target<false> &t,
   __syncwarp();
 }
 
+// writes the target's acceleration; returns whether the target is to be
+// redone in float-float (mixed path)
 template <bool MIXED>
-__device__ __forceinline__ void write_result(const WalkArgs &a, Target<MIXED> &t);
+__device__ __forceinline__ bool write_result(const WalkArgs &a, Target<MIXED> &t);
 
 template <>
-__device__ __forceinline__ void write_result<true>(const WalkArgs &a, Target<true> &t) {
-  if (!t.valid || t.rep != 0) return;
+__device__ __forceinline__ bool write_result<true>(const WalkArgs &a, Target<true> &t) {
+  if (!t.valid || t.rep != 0) return false;
   const double x = (double)t.ahx + (double)t.alx;
   const double y = (double)t.ahy + (double)t.aly;
   const double z = (double)t.ahz + (double)t.alz;
   const int32_t i = a.idx[t.self];
   a.ax[i] = a.G * x; a.ay[i] = a.G * y; a.az[i] = a.G * z;
   // FP32 terms carry ~1e-7 relative error each; where they cancel to a sum
-  // much smaller than their magnitudes the target is redone in FP64
+  // much smaller than their magnitudes the target is redone in float-float
   const float amag = sqrtf((float)(x * x + y * y + z * z));
-  if (t.tabs > a.refine_cf * amag) {
-    const unsigned long long slot = atomicAdd(a.refine_count, 1ull);
-    if (slot < (unsigned long long)a.refine_cap) a.refine[slot] = t.self;
-  }
+  return t.tabs > a.refine_cf * amag;
 }
 
 template <>
-__device__ __forceinline__ void write_result<false>(const WalkArgs &a, Target<false> &t) {
-  if (!t.valid || t.rep != 0) return;
+__device__ __forceinline__ bool write_result<false>(const WalkArgs &a, Target<false> &t) {
+  if (!t.valid || t.rep != 0) return false;
   const int32_t i = a.idx[t.self];
   a.ax[i] = a.G * t.ax; a.ay[i] = a.G * t.ay; a.az[i] = a.G * t.az;
+  return false;
 }
 
-// ---- the traversal, shared by the group walk and the FP64 refinement --------
+// ---- the traversal, shared by the group walk and the float-float redo ------
 // Pops up to 32 nodes per round, decides opening on the integer grid, and
 // hands full batches of 32 accepted nodes / leaf members to the evaluator.
 // Returns false when the walk had to stop (capacity or round bound).
@@ -821,6 +816,32 @@ struct RefineEval {
   }
 };
 
+// Float-float redo of one target whose FP32 sum is ill-conditioned, by the
+// whole warp right after its group's walk: the same group box (so the same
+// interaction list), every lane on the entries, the lanes' float-float sums
+// added by shuffles
+__device__ bool refine_one(const WalkArgs &a, const GroupBox &gb, int32_t ti, int32_t *stack,
+                           int32_t *pp, int32_t *nd, int32_t *big, const int64_t *s_bh,
+                           int64_t round_limit) {
+  const int lane = threadIdx.x & 31;
+  const float4 A = a.spA[ti], B = a.spB[ti];
+  RefineEval ev{a, A.x, A.y, A.z, B.x, B.y, B.z, B.w, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  if (!traverse(a, gb, ti, stack, pp, nd, big, s_bh, round_limit, ev)) return false;
+  // the target itself is in the list: its own term is skipped (r = 0)
+  for (int o = 16; o > 0; o >>= 1) {
+    ev.ax = ff_add(ev.ax, ff_shfl_xor(ev.ax, o));
+    ev.ay = ff_add(ev.ay, ff_shfl_xor(ev.ay, o));
+    ev.az = ff_add(ev.az, ff_shfl_xor(ev.az, o));
+  }
+  if (lane == 0) {
+    const int32_t i = a.idx[ti];
+    a.ax[i] = a.G * ((double)ev.ax.h + (double)ev.ax.l);
+    a.ay[i] = a.G * ((double)ev.ay.h + (double)ev.ay.l);
+    a.az[i] = a.G * ((double)ev.az.h + (double)ev.az.l);
+  }
+  return true;
+}
+
 #ifndef P3T_WALK_MINB_MIXED
 #define P3T_WALK_MINB_MIXED 6  // resident blocks per SM asked of the mixed walk
 #endif
@@ -864,7 +885,17 @@ __global__ void __launch_bounds__(kWarps * 32, MIXED ? P3T_WALK_MINB_MIXED : 1)
       ok = traverse(a, gb, gfirst, stack, s_pp[w], s_nd[w], s_big[w], s_bh, round_limit, ev);
       if (ok) {
         t.reduce(k);
-        write_result<MIXED>(a, t);
+        const bool redo = write_result<MIXED>(a, t);
+        if constexpr (MIXED) {
+          // the chunk's ill-conditioned targets, one at a time with all lanes
+          unsigned todo = __ballot_sync(0xffffffffu, redo);
+          while (todo && ok) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1;
+            ok = refine_one(a, gb, __shfl_sync(0xffffffffu, t.self, l), stack, s_pp[w],
+                            s_nd[w], s_big[w], s_bh, round_limit);
+          }
+        }
       }
     }
     if (!ok) break;
@@ -884,64 +915,19 @@ __global__ void __launch_bounds__(kWarps * 32, MIXED ? P3T_WALK_MINB_MIXED : 1)
   }
 }
 
-// Float-float redo of the targets the mixed walk flagged: one warp per
-// target, the same group box (so the same interaction list), every lane on
-// the entries
-__global__ void __launch_bounds__(kWarps * 32) k_refine(const WalkArgs a) {
-  __shared__ int32_t s_pp[kWarps][kPPCap];
-  __shared__ int32_t s_nd[kWarps][kNDCap];
-  __shared__ int32_t s_big[kWarps][kBigCap];
-  __shared__ int64_t s_bh[P3T_BITS + 1];
-  if (threadIdx.x <= P3T_BITS) s_bh[threadIdx.x] = a.bh[threadIdx.x];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int32_t *stack = a.stack + ((int64_t)blockIdx.x * kWarps + w) * a.stack_cap;
-  const int64_t nref = *a.d_nrefine;
-  const int64_t round_limit = *a.d_nnode + 2;
-  const int64_t warp = (int64_t)blockIdx.x * kWarps + w;
-  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
-  for (int64_t q = warp; q < nref; q += nwarps) {
-    if (*(volatile int32_t *)&a.st->code != 0) break;
-    const int32_t ti = a.refine[q];
-    GroupBox gb;
-    gb.load(a.node[a.leaf_of[ti]]);
-    const float4 A = a.spA[ti], B = a.spB[ti];
-    RefineEval ev{a, A.x, A.y, A.z, B.x, B.y, B.z, B.w, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    if (!traverse(a, gb, ti, stack, s_pp[w], s_nd[w], s_big[w], s_bh,
-                  round_limit, ev))
-      break;
-    // the target itself is in the list: its own term is skipped (r = 0)
-    for (int o = 16; o > 0; o >>= 1) {
-      ev.ax = ff_add(ev.ax, ff_shfl_xor(ev.ax, o));
-      ev.ay = ff_add(ev.ay, ff_shfl_xor(ev.ay, o));
-      ev.az = ff_add(ev.az, ff_shfl_xor(ev.az, o));
-    }
-    if (lane == 0) {
-      const int32_t i = a.idx[ti];
-      a.ax[i] = a.G * ((double)ev.ax.h + (double)ev.ax.l);
-      a.ay[i] = a.G * ((double)ev.ay.h + (double)ev.ay.l);
-      a.az[i] = a.G * ((double)ev.az.h + (double)ev.az.l);
-    }
-  }
-}
-
 __global__ void k_walk_prep(int64_t *cursor, unsigned long long *cand_count,
-                            unsigned long long *counts, unsigned long long *refine_count) {
+                            unsigned long long *counts) {
   *cursor = 0;
   *cand_count = 0ull;
-  *refine_count = 0ull;
   if (counts) { counts[0] = 0ull; counts[1] = 0ull; }
 }
 
 // candidates found -> device status (for growth on the host) and clamped count
-__global__ void k_walk_post(int64_t *cnt, int64_t cand_cap, int64_t refine_cap,
-                            DevStatus *st) {
+__global__ void k_walk_post(int64_t *cnt, int64_t cand_cap, DevStatus *st) {
   const int64_t nc = cnt[8];
   st->cand_need = nc;
   if (nc > cand_cap) dev_fail(st, P3T_ERR_CAPACITY, 42, nc);
   cnt[9] = nc < cand_cap ? nc : cand_cap;
-  const int64_t nr = cnt[13];
-  cnt[14] = nr < refine_cap ? nr : refine_cap;
 }
 
 }  // namespace
@@ -966,11 +952,6 @@ int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
   a.counts = reinterpret_cast<unsigned long long *>(counts);
   a.cursor = &c->counters[12];
   a.st = c->status;
-  a.refine = c->refine;
-  a.refine_count = reinterpret_cast<unsigned long long *>(&c->counters[13]);
-  a.refine_cap = c->cap;
-  a.d_nrefine = &c->counters[14];
-  a.leaf_of = c->leaf_of;
   a.seg = SegView{c->seg_off, (int)c->nseg, p->n};
   a.refine_cf = 32.0f;
   a.G = c->prm.G;
@@ -985,7 +966,7 @@ int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
     X = ceil(X);
     a.bh[l] = X < big ? (int64_t)X : (int64_t)4611686018427387904LL;
   }
-  k_walk_prep<<<1, 1, 0, s>>>(a.cursor, a.cand_count, a.counts, a.refine_count);
+  k_walk_prep<<<1, 1, 0, s>>>(a.cursor, a.cand_count, a.counts);
   const unsigned blocks = (unsigned)(c->walk_warps / kWarps);
   if (c->prm.precision == P3T_MIXED) {
     // one target per lane (or several lanes per target): two targets per
@@ -995,9 +976,8 @@ int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
   } else {
     k_walk<false><<<blocks, kWarps * 32, 0, s>>>(a);
   }
-  k_walk_post<<<1, 1, 0, s>>>(c->counters, c->cand_cap, c->cap, c->status);
-  if (c->prm.precision == P3T_MIXED) k_refine<<<blocks, kWarps * 32, 0, s>>>(a);
-  p3t_note_launches(c->prm.precision == P3T_MIXED ? 4 : 3);
+  k_walk_post<<<1, 1, 0, s>>>(c->counters, c->cand_cap, c->status);
+  p3t_note_launches(3);
   (void)p;
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
