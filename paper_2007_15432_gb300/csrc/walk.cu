@@ -750,8 +750,8 @@ __device__ __forceinline__ FF ff_rsqrt(FF r2) {
   const float d = ((1.0f - t.h) - t.l);
   return ff_fast(y, 0.5f * y * d);
 }
-__device__ __forceinline__ FF ff_shfl_xor(FF a, int o) {
-  return {__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o)};
+__device__ __forceinline__ FF ff_shfl(FF a, int src) {
+  return {__shfl_sync(0xffffffffu, a.h, src), __shfl_sync(0xffffffffu, a.l, src)};
 }
 
 // one target, all 32 lanes, float-float (the refinement of ill-conditioned
@@ -762,6 +762,7 @@ struct RefineEval {
   const WalkArgs &a;
   float xh, yh, zh, xl, yl, zl, inv_ro;
   FF ax, ay, az;
+  int s0, ds;  // this lane's entries of a batch: s0, s0 + ds, ...
   __device__ void term(FF dx, FF dy, FF dz, FF m, float k_inv_ro, bool pp, const float4 q0,
                        const float4 q1) {
     const FF r2 = ff_add(ff_add(ff_mul(dx, dx), ff_mul(dy, dy)), ff_mul(dz, dz));
@@ -795,7 +796,7 @@ struct RefineEval {
   }
   __device__ void pp(const int32_t *list, int n) {
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int s = threadIdx.x & 31; s < n; s += 32) {
+    for (int s = s0; s < n; s += ds) {
       const int32_t j = list[s];
       const float4 A = __ldg(&a.spA[j]), B = __ldg(&a.spB[j]);
       const FF dx = ff_add({xh, xl}, {-A.x, -B.x});
@@ -805,7 +806,7 @@ struct RefineEval {
     }
   }
   __device__ void nodes(const int32_t *list, int n) {
-    for (int s = threadIdx.x & 31; s < n; s += 32) {
+    for (int s = s0; s < n; s += ds) {
       const Mom32 *m = &a.mom32[list[s]];
       const float4 hi = __ldg(&m->hi), lo = __ldg(&m->lo);
       const FF dx = ff_add({xh, xl}, {-hi.x, -lo.x});
@@ -816,24 +817,40 @@ struct RefineEval {
   }
 };
 
-// Float-float redo of one target whose FP32 sum is ill-conditioned, by the
-// whole warp right after its group's walk: the same group box (so the same
-// interaction list), every lane on the entries, the lanes' float-float sums
-// added by shuffles
-__device__ bool refine_one(const WalkArgs &a, const GroupBox &gb, int32_t ti, int32_t *stack,
-                           int32_t *pp, int32_t *nd, int32_t *big, const int64_t *s_bh,
-                           int64_t round_limit) {
+// Float-float redo of the ill-conditioned targets of one walk (lanes with
+// `redo` set), right after it: the same group box, hence the same interaction
+// list, walked once for all of them.  With k such targets each takes
+// floor(32 / k) lanes that split every batch (lane j + q k takes entries q,
+// q + 32 / k, ... for target j); the lanes' float-float sums are added in
+// replica order.
+__device__ bool refine_group(const WalkArgs &a, const GroupBox &gb, bool redo, int32_t self,
+                             int32_t first, int32_t *stack, int32_t *pp, int32_t *nd,
+                             int32_t *big, const int64_t *s_bh, int64_t round_limit) {
   const int lane = threadIdx.x & 31;
+  const unsigned todo = __ballot_sync(0xffffffffu, redo);
+  const int k = __popc(todo);
+  if (k == 0) return true;
+  const int nrep = 32 / k, rep = lane / k, j = lane - rep * k;
+  // lane of the j-th flagged target
+  unsigned m = todo;
+  for (int q = 0; q < j; ++q) m &= m - 1;
+  const int32_t ti = __shfl_sync(0xffffffffu, self, __ffs(m) - 1);
+  const bool valid = rep < nrep;
   const float4 A = a.spA[ti], B = a.spB[ti];
-  RefineEval ev{a, A.x, A.y, A.z, B.x, B.y, B.z, B.w, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-  if (!traverse(a, gb, ti, stack, pp, nd, big, s_bh, round_limit, ev)) return false;
-  // the target itself is in the list: its own term is skipped (r = 0)
-  for (int o = 16; o > 0; o >>= 1) {
-    ev.ax = ff_add(ev.ax, ff_shfl_xor(ev.ax, o));
-    ev.ay = ff_add(ev.ay, ff_shfl_xor(ev.ay, o));
-    ev.az = ff_add(ev.az, ff_shfl_xor(ev.az, o));
+  RefineEval ev{a, A.x, A.y, A.z, B.x, B.y, B.z, B.w, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f},
+                valid ? rep : 32, nrep};
+  if (!traverse(a, gb, first, stack, pp, nd, big, s_bh, round_limit, ev)) return false;
+  // a target's own entry is skipped (r = 0)
+  for (int q = 1; q < nrep; ++q) {
+    const int src = lane < k ? lane + q * k : lane;
+    const FF bx = ff_shfl(ev.ax, src), by = ff_shfl(ev.ay, src), bz = ff_shfl(ev.az, src);
+    if (lane < k) {
+      ev.ax = ff_add(ev.ax, bx);
+      ev.ay = ff_add(ev.ay, by);
+      ev.az = ff_add(ev.az, bz);
+    }
   }
-  if (lane == 0) {
+  if (lane < k) {
     const int32_t i = a.idx[ti];
     a.ax[i] = a.G * ((double)ev.ax.h + (double)ev.ax.l);
     a.ay[i] = a.G * ((double)ev.ay.h + (double)ev.ay.l);
@@ -886,16 +903,9 @@ __global__ void __launch_bounds__(kWarps * 32, MIXED ? P3T_WALK_MINB_MIXED : 1)
       if (ok) {
         t.reduce(k);
         const bool redo = write_result<MIXED>(a, t);
-        if constexpr (MIXED) {
-          // the chunk's ill-conditioned targets, one at a time with all lanes
-          unsigned todo = __ballot_sync(0xffffffffu, redo);
-          while (todo && ok) {
-            const int l = __ffs(todo) - 1;
-            todo &= todo - 1;
-            ok = refine_one(a, gb, __shfl_sync(0xffffffffu, t.self, l), stack, s_pp[w],
-                            s_nd[w], s_big[w], s_bh, round_limit);
-          }
-        }
+        if constexpr (MIXED)
+          ok = refine_group(a, gb, redo, t.self, gfirst, stack, s_pp[w], s_nd[w], s_big[w],
+                            s_bh, round_limit);
       }
     }
     if (!ok) break;
