@@ -4,12 +4,14 @@
 // particles, or a leaf), 32 targets per walk (larger groups are taken 32
 // targets at a time).  A walk of k < 32 targets gives each target r =
 // floor(32 / k) lanes, each of which takes every r-th entry of a batch; the
-// r partial sums are added at the end, so that lanes are not left idle.  The walk pops up to 32 nodes at a
-// time from a per-warp stack, decides opening for all of them at once on the
-// integer grid, and compacts accepted nodes, opened leaves and children with
-// warp ballots / scans into shared-memory lists.  Each batch of 32 list
-// entries is staged into shared memory once (one coalesced load per lane)
-// and then read by every lane as a broadcast.
+// r partial sums are added at the end, so that lanes are not left idle.  The
+// walk pops up to 32 nodes at a time from a per-warp stack, decides opening
+// for all of them at once on the integer grid, and compacts accepted nodes,
+// opened leaves and children with warp ballots / scans into shared-memory
+// lists.  Each batch of 32 list entries is staged into shared memory once
+// (one coalesced load per lane) and then read by every lane as a broadcast.
+// Targets whose FP32 sum is ill-conditioned are redone in float-float right
+// after their walk, all of them on one more traversal of the same list.
 //
 // Mixed path: positions are float-float (hi + lo) pairs, so a relative
 // coordinate (x_i,hi - x_j,hi) + (x_i,lo - x_j,lo) carries the accuracy of an
