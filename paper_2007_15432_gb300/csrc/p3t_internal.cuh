@@ -13,6 +13,41 @@
 #define P3T_MAX_SEGMENTS 4096 // independent systems sharing one context
 
 // ---- segments: the segment of a position, its range --------------------------
+// ---- float-float arithmetic (pairs hi + lo of floats, ~2^-44 relative) ------
+// Dekker's and Knuth's error-free transformations with fmaf for the product
+// error: FP32 instructions only, which on this part cost 1/64 of an FP64 one.
+struct FF {
+  float h, l;
+};
+__device__ __forceinline__ FF ff_fast(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  const float e = (a.h - (s - bb)) + (b.h - bb) + (a.l + b.l);
+  return ff_fast(s, e);
+}
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+  return ff_fast(p, e);
+}
+__device__ __forceinline__ FF ff_mulf(FF a, float b) {
+  const float p = a.h * b;
+  const float e = fmaf(a.l, b, fmaf(a.h, b, -p));
+  return ff_fast(p, e);
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return {-a.h, -a.l}; }
+// a / b: the FP32 quotient and one correction from the float-float residual
+__device__ __forceinline__ FF ff_div(FF a, FF b) {
+  const float q1 = a.h / b.h;
+  const FF r = ff_add(a, ff_neg(ff_mulf(b, q1)));
+  return ff_fast(q1, r.h / b.h);
+}
+
 struct SegView {
   const int64_t *off;  // nseg + 1 offsets (unused when nseg == 1)
   int nseg;

@@ -715,33 +715,6 @@ __device__ __forceinline__ void far_box(const Target<true> &t, FarBox &b) {
   __syncwarp();
 }
 
-// ---- float-float arithmetic (pairs hi + lo of floats, ~2^-44 relative) ------
-// Dekker's and Knuth's error-free transformations with fmaf for the product
-// error: FP32 instructions only, which on this part cost 1/64 of an FP64 one.
-struct FF {
-  float h, l;
-};
-__device__ __forceinline__ FF ff_fast(float a, float b) {  // |a| >= |b|
-  const float s = a + b;
-  return {s, b - (s - a)};
-}
-__device__ __forceinline__ FF ff_add(FF a, FF b) {
-  const float s = a.h + b.h;
-  const float bb = s - a.h;
-  const float e = (a.h - (s - bb)) + (b.h - bb) + (a.l + b.l);
-  return ff_fast(s, e);
-}
-__device__ __forceinline__ FF ff_mul(FF a, FF b) {
-  const float p = a.h * b.h;
-  float e = fmaf(a.h, b.h, -p);
-  e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
-  return ff_fast(p, e);
-}
-__device__ __forceinline__ FF ff_mulf(FF a, float b) {
-  const float p = a.h * b;
-  const float e = fmaf(a.l, b, fmaf(a.h, b, -p));
-  return ff_fast(p, e);
-}
 // 1 / sqrt(r2): the FP32 estimate and one Newton step y (3 - r2 y^2) / 2 with
 // the residual 1 - r2 y^2 formed in float-float
 __device__ __forceinline__ FF ff_rsqrt(FF r2) {
