@@ -705,14 +705,11 @@ __device__ __forceinline__ int64_t max_bits(int64_t a, double v) {
   return b > a ? b : a;
 }
 
-__global__ void k_moments_leaf32(
-    const int64_t *d_nleaf, const int32_t *leaf_list, TreeNode *node, Mom32 *m32, double *nrs,
-    const float4 *spA, const float4 *spB, const float *sml, const double *srs,
-    const int32_t *sq, const double *box, SegView sv) {
-  const int64_t nleaf = *d_nleaf;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nleaf;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = leaf_list[t];
+__device__ __forceinline__ void leaf_moments32(
+    int64_t b, TreeNode *node, Mom32 *m32, double *nrs, const float4 *spA, const float4 *spB,
+    const float *sml, const double *srs, const int32_t *sq, const double *box,
+    const SegView &sv) {
+  {
     TreeNode *nd = &node[b];
     const int32_t f = nd->first, c = nd->count;
     const double u = ldexp(box[5 * seg_at(sv, f) + 3], -P3T_BITS);
@@ -755,6 +752,121 @@ __global__ void k_moments_leaf32(
     const double rq = ceil(rs / u) + 1.0;
     nd->R = rq < 8388608.0 ? (int32_t)rq : 8388608;
     m32[b] = o;
+  }
+}
+
+// One internal node of the mixed path from its children's Mom32 records, by
+// one thread, the eight child slots added in the fixed pairwise tree ((s0 +
+// s4) + (s2 + s6)) + ((s1 + s5) + (s3 + s7)) (zero past the last child).  The
+// children were written by other threads of the same launch: read through L2.
+template <int NQ, class T, class F, class A>
+__device__ __forceinline__ void tree8_acc(F slot, A add, T (&r)[NQ]) {
+  T a[NQ], b[NQ], c[NQ], d[NQ];
+  slot(0, a); slot(4, b);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) a[q] = add(a[q], b[q]);
+  slot(2, b); slot(6, c);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) { b[q] = add(b[q], c[q]); a[q] = add(a[q], b[q]); }
+  slot(1, b); slot(5, c);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) b[q] = add(b[q], c[q]);
+  slot(3, c); slot(7, d);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) { c[q] = add(c[q], d[q]); b[q] = add(b[q], c[q]); r[q] = add(a[q], b[q]); }
+}
+
+__device__ __forceinline__ Mom32 ldcg_mom32(const Mom32 *m) {
+  Mom32 o;
+  o.hi = __ldcg(&m->hi); o.lo = __ldcg(&m->lo); o.q0 = __ldcg(&m->q0); o.q1 = __ldcg(&m->q1);
+  return o;
+}
+
+__device__ void node_moments32(int64_t b, TreeNode *node, Mom32 *m32, double *nrs,
+                               const double *box, const SegView &sv) {
+  TreeNode *pn = &node[b];
+  const int32_t c0 = pn->child0, nch = pn->nchild;
+  int64_t rsb = 0;
+  int32_t plo[3] = {P3T_QMAX, P3T_QMAX, P3T_QMAX}, phi[3] = {-1, -1, -1};
+  for (int k = 0; k < nch; ++k) {
+    rsb = max_bits(rsb, __ldcg(&nrs[c0 + k]));
+    const TreeNode *cn = &node[c0 + k];
+    for (int a = 0; a < 3; ++a) {
+      plo[a] = min(plo[a], __ldcg(&cn->qlo[a]));
+      phi[a] = max(phi[a], __ldcg(&cn->qhi[a]));
+    }
+  }
+  FF P[4];
+  tree8_acc<4>([&](int k, FF (&t)[4]) {
+    for (int q = 0; q < 4; ++q) t[q] = FF{0.f, 0.f};
+    if (k < nch) {
+      const Mom32 cm = ldcg_mom32(&m32[c0 + k]);
+      const FF M = ff_fast(cm.hi.w, cm.lo.w);
+      t[0] = M;
+      t[1] = ff_mul(M, ff_fast(cm.hi.x, cm.lo.x));
+      t[2] = ff_mul(M, ff_fast(cm.hi.y, cm.lo.y));
+      t[3] = ff_mul(M, ff_fast(cm.hi.z, cm.lo.z));
+    }
+  }, [](FF x, FF y) { return ff_add(x, y); }, P);
+  const FF pc[3] = {ff_div(P[1], P[0]), ff_div(P[2], P[0]), ff_div(P[3], P[0])};
+  float Q[6];
+  tree8_acc<6>([&](int k, float (&t)[6]) {
+    for (int q = 0; q < 6; ++q) t[q] = 0.f;
+    if (k < nch) {
+      const Mom32 cm = ldcg_mom32(&m32[c0 + k]);
+      const float M = cm.hi.w;
+      const float dx = ff_add(ff_fast(cm.hi.x, cm.lo.x), ff_neg(pc[0])).h;
+      const float dy = ff_add(ff_fast(cm.hi.y, cm.lo.y), ff_neg(pc[1])).h;
+      const float dz = ff_add(ff_fast(cm.hi.z, cm.lo.z), ff_neg(pc[2])).h;
+      const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      const float tx = 3.f * dx, ty = 3.f * dy;
+      t[0] = fmaf(M, fmaf(tx, dx, -d2), cm.q0.x);
+      t[1] = fmaf(M, fmaf(ty, dy, -d2), cm.q0.y);
+      t[2] = fmaf(M, fmaf(3.f * dz, dz, -d2), cm.q0.z);
+      t[3] = fmaf(M, tx * dy, cm.q0.w);
+      t[4] = fmaf(M, tx * dz, cm.q1.x);
+      t[5] = fmaf(M, ty * dz, cm.q1.y);
+    }
+  }, [](float x, float y) { return x + y; }, Q);
+  Mom32 o;
+  o.hi = make_float4(pc[0].h, pc[1].h, pc[2].h, P[0].h);
+  o.lo = make_float4(pc[0].l, pc[1].l, pc[2].l, P[0].l);
+  o.q0 = make_float4(Q[0], Q[1], Q[2], Q[3]);
+  o.q1 = make_float4(Q[4], Q[5], 0.f, 0.f);
+  for (int a = 0; a < 3; ++a) { pn->qlo[a] = plo[a]; pn->qhi[a] = phi[a]; }
+  const double rs = __longlong_as_double(rsb);
+  nrs[b] = rs;
+  const double rq = ceil(rs / ldexp(box[5 * seg_at(sv, pn->first) + 3], -P3T_BITS)) + 1.0;
+  pn->R = rq < 8388608.0 ? (int32_t)rq : 8388608;
+  m32[b] = o;
+}
+
+// All moments of the mixed path in one launch, bottom-up: a thread per leaf
+// computes the leaf, then counts itself at its parent (node_done, zeroed by
+// k_nodes_bfs); the child that completes the count computes the parent from
+// all its children and climbs on.  Nothing waits, and a node's result does
+// not depend on which child arrives last.  (In FP32 and float-float a node
+// costs a few thousand cycles of latency, so the climb's serial tail at the
+// top levels is short; the FP64 path keeps its level launches.)
+__global__ void k_moments_up32(
+    const int64_t *d_nleaf, const int32_t *leaf_list, TreeNode *node, Mom32 *m32, double *nrs,
+    const float4 *spA, const float4 *spB, const float *sml, const double *srs,
+    const int32_t *sq, const double *box, SegView sv, int32_t *node_done) {
+  const int64_t nleaf = *d_nleaf;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nleaf;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = leaf_list[t];
+    leaf_moments32(b, node, m32, nrs, spA, spB, sml, srs, sq, box, sv);
+    for (;;) {
+      const int32_t p = node[b].parent;
+      if (p < 0) break;
+      __threadfence();  // this node's record before the count
+      const int done = atomicAdd(&node_done[p], 1) + 1;
+      if (done < node[p].nchild) break;
+      __threadfence();  // the siblings' records after their counts
+      node_moments32(p, node, m32, nrs, box, sv);
+      b = p;
+    }
   }
 }
 
@@ -906,155 +1018,17 @@ __device__ void moments_level(int level, const int64_t *lvl_start, TreeNode *nod
   }
 }
 
-// Mixed path: internal nodes from their children's Mom32 records, M and the
-// centre of mass in float-float, the quadrupole with its parallel-axis shift
-// in FP32; the same lanes per node and the same fixed pairwise slot tree as
-// the FP64 path (float-float sums added by the same rule), so a node's
-// moments do not depend on how many nodes share its level.
-template <int L, int NQ>
-__device__ __forceinline__ void slot_tree_ff(FF (&v)[8 / L][NQ]) {
-#pragma unroll
-  for (int S = 4; S >= L; S >>= 1)
-#pragma unroll
-    for (int j = 0; j < S / L; ++j)
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) v[j][q] = ff_add(v[j][q], v[j + S / L][q]);
-#pragma unroll
-  for (int o = L >> 1; o > 0; o >>= 1)
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      const FF w{__shfl_xor_sync(0xffffffffu, v[0][q].h, o),
-                 __shfl_xor_sync(0xffffffffu, v[0][q].l, o)};
-      v[0][q] = ff_add(v[0][q], w);
-    }
-}
-template <int L, int NQ>
-__device__ __forceinline__ void slot_tree_f(float (&v)[8 / L][NQ]) {
-#pragma unroll
-  for (int S = 4; S >= L; S >>= 1)
-#pragma unroll
-    for (int j = 0; j < S / L; ++j)
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) v[j][q] += v[j + S / L][q];
-#pragma unroll
-  for (int o = L >> 1; o > 0; o >>= 1)
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) v[0][q] += __shfl_xor_sync(0xffffffffu, v[0][q], o);
-}
-
-template <int L>
-__device__ void moments_level32_L(int64_t b0, int64_t nn, TreeNode *node, Mom32 *m32,
-                                  double *nrs, const double *box, const SegView &sv) {
-  constexpr int J = 8 / L;
-  const int lane = threadIdx.x & 31, sub = lane & (L - 1);
-  const int per_warp = 32 / L;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t wb = warp * per_warp; wb < nn; wb += nwarps * per_warp) {
-    const int64_t gi = wb + lane / L;
-    const bool valid = gi < nn;
-    const int64_t b = b0 + (valid ? gi : 0);
-    TreeNode *pn = &node[b];
-    const int32_t c0 = valid ? pn->child0 : 0, nch = valid ? pn->nchild : 0;
-    int64_t rsb = 0;
-    int32_t plo[3] = {P3T_QMAX, P3T_QMAX, P3T_QMAX}, phi[3] = {-1, -1, -1};
-    FF t[J][4];  // M, M cx, M cy, M cz
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-      const int k = sub + j * L;
-      for (int q = 0; q < 4; ++q) t[j][q] = FF{0.f, 0.f};
-      if (k < nch) {
-        const Mom32 &cm = m32[c0 + k];
-        const FF M = ff_fast(cm.hi.w, cm.lo.w);
-        t[j][0] = M;
-        t[j][1] = ff_mul(M, ff_fast(cm.hi.x, cm.lo.x));
-        t[j][2] = ff_mul(M, ff_fast(cm.hi.y, cm.lo.y));
-        t[j][3] = ff_mul(M, ff_fast(cm.hi.z, cm.lo.z));
-        rsb = max_bits(rsb, nrs[c0 + k]);
-        const TreeNode &cn = node[c0 + k];
-        for (int a = 0; a < 3; ++a) { plo[a] = min(plo[a], cn.qlo[a]); phi[a] = max(phi[a], cn.qhi[a]); }
-      }
-    }
-    slot_tree_ff<L, 4>(t);
-    for (int o = L >> 1; o > 0; o >>= 1) {
-      for (int a = 0; a < 3; ++a) {
-        plo[a] = min(plo[a], __shfl_xor_sync(0xffffffffu, plo[a], o));
-        phi[a] = max(phi[a], __shfl_xor_sync(0xffffffffu, phi[a], o));
-      }
-      const long long ob = __shfl_xor_sync(0xffffffffu, (long long)rsb, o);
-      rsb = ob > rsb ? ob : rsb;
-    }
-    FF pc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    if (nch > 0)
-      for (int a = 0; a < 3; ++a) pc[a] = ff_div(t[0][a + 1], t[0][0]);
-    float Q[J][6];  // xx, yy, zz, xy, xz, yz
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-      const int k = sub + j * L;
-      for (int q = 0; q < 6; ++q) Q[j][q] = 0.f;
-      if (k < nch) {
-        const Mom32 &cm = m32[c0 + k];
-        const float M = cm.hi.w;
-        const float dx = ff_add(ff_fast(cm.hi.x, cm.lo.x), ff_neg(pc[0])).h;
-        const float dy = ff_add(ff_fast(cm.hi.y, cm.lo.y), ff_neg(pc[1])).h;
-        const float dz = ff_add(ff_fast(cm.hi.z, cm.lo.z), ff_neg(pc[2])).h;
-        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float tx = 3.f * dx, ty = 3.f * dy;
-        Q[j][0] = fmaf(M, fmaf(tx, dx, -d2), cm.q0.x);
-        Q[j][1] = fmaf(M, fmaf(ty, dy, -d2), cm.q0.y);
-        Q[j][2] = fmaf(M, fmaf(3.f * dz, dz, -d2), cm.q0.z);
-        Q[j][3] = fmaf(M, tx * dy, cm.q0.w);
-        Q[j][4] = fmaf(M, tx * dz, cm.q1.x);
-        Q[j][5] = fmaf(M, ty * dz, cm.q1.y);
-      }
-    }
-    slot_tree_f<L, 6>(Q);
-    if (valid && nch > 0 && sub == 0) {
-      Mom32 o;
-      o.hi = make_float4(pc[0].h, pc[1].h, pc[2].h, t[0][0].h);
-      o.lo = make_float4(pc[0].l, pc[1].l, pc[2].l, t[0][0].l);
-      o.q0 = make_float4(Q[0][0], Q[0][1], Q[0][2], Q[0][3]);
-      o.q1 = make_float4(Q[0][4], Q[0][5], 0.f, 0.f);
-      for (int a = 0; a < 3; ++a) { pn->qlo[a] = plo[a]; pn->qhi[a] = phi[a]; }
-      const double rs = __longlong_as_double(rsb);
-      nrs[b] = rs;
-      const double rq = ceil(rs / ldexp(box[5 * seg_at(sv, pn->first) + 3], -P3T_BITS)) + 1.0;
-      pn->R = rq < 8388608.0 ? (int32_t)rq : 8388608;
-      m32[b] = o;
-    }
-  }
-}
-
-__device__ void moments_level32(int level, const int64_t *lvl_start, TreeNode *node, Mom32 *m32,
-                                double *nrs, const double *box, const SegView &sv,
-                                int64_t warp_target) {
-  const int64_t b0 = lvl_start[level], b1 = lvl_start[level + 1];
-  const int64_t nn = b1 - b0;
-  if (nn <= 0) return;
-  int L = 8;
-  while (L > 1 && nn * L > 32 * warp_target) L >>= 1;
-  switch (L) {
-    case 8: moments_level32_L<8>(b0, nn, node, m32, nrs, box, sv); break;
-    case 4: moments_level32_L<4>(b0, nn, node, m32, nrs, box, sv); break;
-    case 2: moments_level32_L<2>(b0, nn, node, m32, nrs, box, sv); break;
-    default: moments_level32_L<1>(b0, nn, node, m32, nrs, box, sv); break;
-  }
-}
-
 // levels kDeepLevel and deeper share one single-block launch
 constexpr int kDeepLevel = 12;
 
+
 // levels level_hi down to level_lo; several levels only with a single block
 // (a block barrier between levels)
-template <bool MIXED>
 __global__ void k_moments_level(int level_hi, int level_lo, const int64_t *lvl_start,
                                 TreeNode *node, Mom64 *m64, Mom32 *m32, double *nrs,
                                 const double *box, SegView sv, int64_t warp_target) {
   for (int l = level_hi; l >= level_lo; --l) {
-    if constexpr (MIXED)
-      moments_level32(l, lvl_start, node, m32, nrs, box, sv, warp_target);
-    else
-      moments_level(l, lvl_start, node, m64, m32, nrs, box, sv, warp_target);
+    moments_level(l, lvl_start, node, m64, m32, nrs, box, sv, warp_target);
     if (l > level_lo) {
       __threadfence_block();
       __syncthreads();
@@ -1205,28 +1179,27 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   if (rc) return rc;
   k_leaf_list<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->leaf_flag,
                                               c->leaf_pos, c->pre2bfs, c->leaf_list);
-  const bool mixed = c->prm.precision == P3T_MIXED;
-  if (mixed)
-    k_moments_leaf32<<<(unsigned)p3t_grid(c->node_cap, 128, maxb), 128, 0, s>>>(
+  if (c->prm.precision == P3T_MIXED) {
+    k_moments_up32<<<(unsigned)p3t_grid(c->node_cap, 128, maxb), 128, 0, s>>>(
         &cnt[2], c->leaf_list, c->node, c->mom32, c->nrs, c->spA, c->spB, c->sml, c->srs,
-        c->sq, c->box, sv);
-  else
+        c->sq, c->box, sv, c->node_done);
+    p3t_note_launches(1);
+  } else {
     k_moments_leaf<<<(unsigned)p3t_grid(c->node_cap, 128, maxb), 128, 0, s>>>(
         &cnt[2], c->leaf_list, c->node, c->mom64, c->mom32, c->nrs, c->sx, c->sy, c->sz, c->sm,
         c->srs, c->sq, c->box, sv);
-  {
     // internal nodes, level by level, deepest first
     int64_t *lvl_start = c->counters + 32;  // [P3T_BITS + 2]
     k_level_offsets<<<1, 32, 0, s>>>(&cnt[3], c->node_cap, c->node, lvl_start);
     // the deep levels (empty or nearly so in a disk) in one single-block
     // launch, then one launch a level at about one warp per sub-partition
-    auto level = mixed ? k_moments_level<true> : k_moments_level<false>;
-    level<<<1, 128, 0, s>>>(P3T_BITS - 1, kDeepLevel, lvl_start, c->node, c->mom64, c->mom32,
-                            c->nrs, c->box, sv, 4);
+    k_moments_level<<<1, 128, 0, s>>>(P3T_BITS - 1, kDeepLevel, lvl_start, c->node, c->mom64,
+                                      c->mom32, c->nrs, c->box, sv, 4);
     const int64_t wt = (int64_t)c->num_sms * 4;
     for (int l = kDeepLevel - 1; l >= 0; --l)
-      level<<<(unsigned)c->num_sms, 128, 0, s>>>(l, l, lvl_start, c->node, c->mom64, c->mom32,
-                                                 c->nrs, c->box, sv, wt);
+      k_moments_level<<<(unsigned)c->num_sms, 128, 0, s>>>(l, l, lvl_start, c->node, c->mom64,
+                                                           c->mom32, c->nrs, c->box, sv, wt);
+    p3t_note_launches(3 + kDeepLevel);  // leaves, level offsets, deep levels, one a level
   }
   k_group_flags<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->node, c->bfs2pre,
                                                 c->prm.group_size, c->group_flag);
@@ -1235,11 +1208,10 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   if (rc) return rc;
   k_group_list<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->group_flag,
                                                c->group_pos, c->pre2bfs, c->group_list);
-  // own kernels here (the scans and sorts count themselves): box 3, keys, n,
-  // gather, lcp, levels, clamp, nodes_pre, pre2bfs, nodes_bfs, parents,
-  // leaf_list, moments (leaves, level offsets, 21 levels), group_flags,
-  // group_list
-  p3t_note_launches(18 + 1 + kDeepLevel);
+  // own kernels here (the scans, sorts and moments count themselves): box 3,
+  // keys, n, gather, lcp, levels, clamp, nodes_pre, pre2bfs, nodes_bfs,
+  // parents, leaf_list, group_flags, group_list
+  p3t_note_launches(16);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 
