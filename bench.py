@@ -46,8 +46,8 @@ FLOP_PP, FLOP_PN = 30.0, 70.0
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one k_walk launch on the N = 10^6 wide disk,
 # group size 64, from a single-pass ncu capture of this kernel
-# (dram__bytes_read.sum 80.11 MB + dram__bytes_write.sum 17.46 MB)
-WALK_TRAFFIC_1E6 = 97.57e6
+# (dram__bytes_read.sum 80.07 MB + dram__bytes_write.sum 17.48 MB)
+WALK_TRAFFIC_1E6 = 97.55e6
 
 
 def parse():
