@@ -483,14 +483,25 @@ __global__ void k_levels(SegView sv, int leaf, const int32_t *wlcp,
   }
 }
 
-// first index e > i (or the segment's end n) whose key leaves i's level-l cell
-__device__ __forceinline__ int64_t cell_end(const uint64_t *keys, int64_t n,
-                                            int64_t i, int l) {
-  if (l == 0) return n;
-  const uint64_t ki = keys[i];
-  int64_t lo = i + 1, hi = n;  // answer in [lo, hi]
+// first index e >= start (or the segment's end n) whose key leaves the
+// level-l cell of key ki, given that every index below start is inside (the
+// cell's members are contiguous in key order): a galloping search from start,
+// so the cost grows with the log of the distance, not of n
+__device__ __forceinline__ int64_t cell_end_from(const uint64_t *keys, int64_t n, uint64_t ki,
+                                                 int l, int64_t start) {
+  if (l == 0 || start >= n) return n;
+  if (lcp_levels(ki, keys[start]) < l) return start;
+  int64_t lo = start, hi, step = 1;  // keys[lo] inside
+  for (;;) {
+    hi = lo + step;
+    if (hi >= n) { hi = n; break; }
+    if (lcp_levels(ki, keys[hi]) < l) break;
+    lo = hi;
+    step <<= 1;
+  }
+  ++lo;  // the answer lies in [lo, hi]
   while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
+    const int64_t mid = (lo + hi) >> 1;
     if (lcp_levels(ki, keys[mid]) >= l) lo = mid + 1; else hi = mid;
   }
   return lo;
@@ -507,10 +518,15 @@ __global__ void k_nodes_pre(SegView sv, const uint64_t *keys, const int8_t *lp,
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s1 = seg_hi(sv, seg_at(sv, i));
     const int l0 = (int)lp[i] + 1, L = (int)lv[i];
-    int64_t id = nstart[i];
-    for (int l = l0; l <= L; ++l, ++id) {
+    if (L < l0) continue;
+    const uint64_t ki = keys[i];
+    // deepest cell first: each enclosing cell ends at or after the one inside
+    int64_t e = i + 1;
+    for (int l = L; l >= l0; --l) {
+      e = cell_end_from(keys, s1, ki, l, e);
+      const int64_t id = nstart[i] + (l - l0);
       pre_first[id] = (int32_t)i;
-      pre_count[id] = (int32_t)(cell_end(keys, s1, i, l) - i);
+      pre_count[id] = (int32_t)(e - i);
       pre_level[id] = l;
       lvl_keys[id] = (uint64_t)l;
       bfs2pre[id] = (int32_t)id;
