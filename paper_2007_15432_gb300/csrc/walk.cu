@@ -715,16 +715,6 @@ __device__ __forceinline__ void far_box(const Target<true> &t, FarBox &b) {
   __syncwarp();
 }
 
-// 1 / sqrt(r2): the FP32 estimate and one Newton step y (3 - r2 y^2) / 2 with
-// the residual 1 - r2 y^2 formed in float-float
-__device__ __forceinline__ FF ff_rsqrt(FF r2) {
-  const float y = rsqrtf(r2.h);
-  const float p = y * y;
-  const FF yy{p, fmaf(y, y, -p)};
-  const FF t = ff_mul(r2, yy);
-  const float d = ((1.0f - t.h) - t.l);
-  return ff_fast(y, 0.5f * y * d);
-}
 __device__ __forceinline__ FF ff_shfl(FF a, int src) {
   return {__shfl_sync(0xffffffffu, a.h, src), __shfl_sync(0xffffffffu, a.l, src)};
 }

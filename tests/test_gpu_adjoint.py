@@ -141,19 +141,21 @@ def test_kepler_vjp_matches_oracle(mods, dt):
     assert np.array_equal(X.cpu().numpy(), x) and np.array_equal(V.cpu().numpy(), v)
 
 
-def test_kepler_drift_all_matches_oracle_and_hard_step(mods):
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("dt", [0.3, 1.0 / 64.0])
+def test_kepler_drift_all_matches_oracle_and_hard_step(mods, precision, dt):
     """p3t_kepler_drift: the isolated particles' drift for every particle, the same bits as
-    p3t_hard_step with every particle single, and the oracle's drift."""
+    p3t_hard_step with every particle single, and the oracle's drift (in both precisions:
+    the mixed path's float-float drift takes the short arcs)."""
     AD, P = mods
     from oracle import oracle as O
     s = disks.disk(3000, 0.5, 2.0, 0.3, 0.1, 1e-10, 23)
-    dt = 0.3
     ref = {k: s[k].copy() for k in s}
     O.kepler_drift(ref, dt, 1.0)
     st = P.State.from_numpy(s, device="cuda")
     st2 = P.State.from_numpy(s, device="cuda")
     n = len(s["m"])
-    ctx = P.p3t_create(P.Params(), 0)
+    ctx = P.p3t_create(P.Params(precision=precision), 0)
     try:
         P.p3t_kepler_drift(ctx, st, dt)
         i32 = dict(dtype=torch.int32, device="cuda")

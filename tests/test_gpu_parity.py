@@ -196,12 +196,14 @@ def _cluster_struct(P3T, ocl, n):
     return cl, t
 
 
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("eta", [0.1, 0.01])
-def test_hard_step_matches_oracle(P3T, eta):
+def test_hard_step_matches_oracle(P3T, eta, precision):
     """Hermite clusters + Kepler singles over one soft step, from the oracle's
-    clusters (config-1 workload with planted pairs and triples)."""
+    clusters (config-1 workload with planted pairs and triples).  The mixed
+    path drifts the singles in float-float (the Hermite part is FP64 in both)."""
     s = disks.equal_mass_narrow(n=1000, seed=1001)
-    P = P3T.Params(theta=0.0, eta=eta, eta0=eta / 10)
+    P = P3T.Params(theta=0.0, eta=eta, eta0=eta / 10, precision=precision)
     op = oracle_params(P)
     ro, rs, _, _ = O.cutoffs(s, op)
     ref = O.tree_soft(s, ro, rs, op)
@@ -230,13 +232,16 @@ def test_hard_step_matches_oracle(P3T, eta):
     P3T.p3t_destroy(ctx)
 
 
-def test_kepler_long_and_unbound(P3T):
-    rng = np.random.default_rng(5)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_kepler_long_and_unbound(P3T, precision):
+    """Eccentric, inclined, unbound orbits, a short and a long arc; the mixed
+    path's float-float drift takes the short bound arcs and hands the rest to
+    the FP64 solver."""
     n = 64
     s = disks.disk(n, 0.5, 3.0, 0.3, 0.2, 1e-10, seed=7)
     s["vx"][:8] *= 1.6      # a few unbound orbits
     s["vy"][:8] *= 1.6
-    P = P3T.Params()
+    P = P3T.Params(precision=precision)
     op = oracle_params(P)
     st, ctx = _setup(P3T, s, P, np.full(n, 1e-9), np.full(n, 1e-9))
     ocl = O.Clusters(np.arange(n, dtype=np.int32), np.arange(n, dtype=np.int32),
@@ -250,6 +255,9 @@ def test_kepler_long_and_unbound(P3T):
         pos = np.stack([g["x"], g["y"], g["z"]], 1)
         ref = np.stack([s["x"], s["y"], s["z"]], 1)
         assert rel_err(pos, ref).max() < 1e-12
+        vel = np.stack([g["vx"], g["vy"], g["vz"]], 1)
+        vref = np.stack([s["vx"], s["vy"], s["vz"]], 1)
+        assert rel_err(vel, vref).max() < 1e-12
     P3T.p3t_destroy(ctx)
 
 
