@@ -130,7 +130,10 @@ int p3t_create(p3t_ctx **ctx, const p3t_params *p, int device);
 /* Frees everything the context owns (synchronises its device first). */
 void p3t_destroy(p3t_ctx *ctx);
 
-/* Replaces the parameters (host call; takes effect for work enqueued after). */
+/* Replaces the parameters (host call; takes effect for work enqueued after).
+ * A change of leaf_size, group_size or precision drops the tree (its sorted
+ * copies and moments are those of one precision): p3t_build_tree again
+ * before the next p3t_soft_force or p3t_neighbours. */
 int p3t_set_params(p3t_ctx *ctx, const p3t_params *p);
 
 /* Sizes every internal buffer for up to n particles (allocates, so call it

@@ -229,8 +229,10 @@ void p3t_destroy(p3t_ctx *c) {
 
 int p3t_set_params(p3t_ctx *c, const p3t_params *p) {
   if (!c || !params_ok(p)) return P3T_ERR_INVALID;
+  // the tree holds the sorted copies and moments of one precision only
   const bool leaf_changed = p->leaf_size != c->prm.leaf_size ||
-                            p->group_size != c->prm.group_size;
+                            p->group_size != c->prm.group_size ||
+                            p->precision != c->prm.precision;
   c->prm = *p;
   if (leaf_changed) c->have_tree = c->have_cand = false;
   return P3T_OK;

@@ -417,7 +417,9 @@ __global__ void k_segkey(SegView sv, const int32_t *idx, uint64_t *keys) {
     keys[s] = (uint64_t)seg_of(sv, idx[s]);
 }
 
-// gather sorted copies (FP64 and the float-float packing of the mixed path)
+// gather sorted copies: the FP64 arrays the FP64 path reads, or the
+// float-float packing the mixed path reads (each path writes only its own)
+template <bool MIXED>
 __global__ void k_gather(int64_t n, const int32_t *idx, const uint64_t *keys,
                          const double *x, const double *y, const double *z,
                          const double *m, const double *ro, const double *rs,
@@ -428,11 +430,15 @@ __global__ void k_gather(int64_t n, const int32_t *idx, const uint64_t *keys,
        s += (int64_t)gridDim.x * blockDim.x) {
     const int32_t i = idx[s];
     const double X = x[i], Y = y[i], Z = z[i], M = m[i], RO = ro[i], RS = rs[i];
-    sx[s] = X; sy[s] = Y; sz[s] = Z; sm[s] = M; sro[s] = RO; srs[s] = RS;
+    srs[s] = RS;
     const uint64_t k = keys[s];
     sq[3 * s + 0] = (int32_t)compact3(k >> 2);
     sq[3 * s + 1] = (int32_t)compact3(k >> 1);
     sq[3 * s + 2] = (int32_t)compact3(k);
+    if constexpr (!MIXED) {
+      sx[s] = X; sy[s] = Y; sz[s] = Z; sm[s] = M; sro[s] = RO;
+      continue;
+    }
     const float xh = (float)X, yh = (float)Y, zh = (float)Z;
     const float mh = (float)M;
     spA[s] = make_float4(xh, yh, zh, mh);
@@ -1168,7 +1174,8 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
     k_keys<<<(unsigned)g, kBlock, 0, s>>>(sv, p->x, p->y, p->z, c->box, c->keys, c->idx, 1);
     p3t_note_launches(2);
   }
-  k_gather<<<(unsigned)g, kBlock, 0, s>>>(n, c->idx, c->keys, p->x, p->y, p->z, p->m,
+  auto gather = c->prm.precision == P3T_MIXED ? k_gather<true> : k_gather<false>;
+  gather<<<(unsigned)g, kBlock, 0, s>>>(n, c->idx, c->keys, p->x, p->y, p->z, p->m,
                                           p->r_out, p->r_search, c->sx, c->sy, c->sz,
                                           c->sm, c->sro, c->srs, c->sq, c->spA, c->spB,
                                           c->srs32, c->sml);
