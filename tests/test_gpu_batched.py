@@ -97,13 +97,15 @@ def test_batched_graph_equals_sequential(mods):
         assert np.array_equal(out[0][k], out[1][k]), k
 
 
-def test_batched_cutoffs_per_disk(mods):
-    """Cut-off radii alone: each disk's bins
-    come from its own radial range and particle count."""
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_batched_cutoffs_per_disk(mods, mode):
+    """Cut-off radii alone, in the three cut-off schemes: each disk's bins come
+    from its own radial range and particle count, and the shared scheme's
+    maximum is each disk's own."""
     EN, P = mods
     ds = [disks.equal_mass_ring(n=3000, seed=5), disks.wide_power_law(n=20000, seed=6),
           disks.equal_mass_ring(n=7, seed=7)]
-    prm = P.Params(theta=0.5)
+    prm = P.Params(theta=0.5, cutoff_mode=mode)
     cat = {k: np.concatenate([d[k] for d in ds]) for k in ds[0]}
     off = np.concatenate([[0], np.cumsum([len(d["m"]) for d in ds])])
     st = P.State.from_numpy(cat)
