@@ -364,3 +364,37 @@ def test_runs_are_bit_reproducible(P3T):
         ss.close()
     for k in out[0]:
         assert np.array_equal(out[0][k], out[1][k]), k
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_empty_system_every_call(P3T, precision):
+    """N = 0 through every compute call of the ABI: each returns OK and
+    leaves the (empty) state alone; the energy is zero and nothing merges."""
+    s = {k: np.zeros(0) for k in ("x", "y", "z", "vx", "vy", "vz", "m")}
+    P = P3T.Params(precision=precision, f_radius=1.0)
+    st = P3T.State.from_numpy(s, r_phys=np.zeros(0))
+    ctx = P3T.p3t_create(P, 0)
+    try:
+        f64 = dict(dtype=torch.float64, device="cuda")
+        P3T.p3t_cutoffs(ctx, st)
+        P3T.p3t_build_tree(ctx, st, True)
+        acc = torch.zeros(3, 0, **f64)
+        P3T.p3t_soft_force(ctx, st, acc)
+        nb_off = torch.full((1,), 7, dtype=torch.int64, device="cuda")
+        nb_idx = torch.zeros(1, dtype=torch.int32, device="cuda")
+        cl = P3T.p3t_neighbours(ctx, st, nb_off, nb_idx)
+        P3T.p3t_hard_step(ctx, st, cl, P.dt_soft)
+        P3T.p3t_kick(ctx, st, acc, 0.5 * P.dt_soft)
+        P3T.p3t_kepler_drift(ctx, st, P.dt_soft)
+        P3T.p3t_soft_force_direct(ctx, st, acc)
+        out = torch.full((4,), 1.0, **f64)
+        P3T.p3t_energy(ctx, st, out)
+        nm, eh, es = P3T.p3t_merge(ctx, st)
+        torch.cuda.synchronize()
+        assert P3T.p3t_status(ctx)[0] == P3T.P3T_OK
+        assert int(nb_off[0].item()) == 0
+        assert torch.all(out == 0.0)
+        assert nm == 0 and eh == 0.0 and es == 0.0
+        assert len(st.m) == 0
+    finally:
+        P3T.p3t_destroy(ctx)
