@@ -96,6 +96,55 @@ __device__ __forceinline__ void pair_term(T rx, T ry, T rz, const Q4<T> &A, T ir
   }
 }
 
+// The mixed kernels' pair term for a lane's two targets at once, one per half
+// of each packed FP32 pair (f32x2 instructions round each half as the scalar
+// one would), the source's values duplicated into both halves.  Branch-free:
+// the changeover variable u = clamp((y - gamma) / (1 - gamma), 0, 1) gives K =
+// 0 below gamma, 1 beyond r_out and the polynomial between (35 - 84 + 70 - 20
+// = 1 exactly), and r^2 is kept above 1e-18 so that the target itself (r = 0,
+// y = 0, K = 0) and far-away dummy targets add exact zeros without an inf.
+// (Any real pair that close has y <= gamma: K = K' = 0 as well.)
+struct PairConst2 {
+  f2 g, i1mg, c35, c84, c70, c20, one, three, c140i;
+};
+template <bool VJP>
+__device__ __forceinline__ void pair_term2(f2 rx, f2 ry, f2 rz, const Q4<float> &A, float iroj,
+                                           const Q4<float> &L, f2 mk, f2 irok, f2 lxk, f2 lyk,
+                                           f2 lzk, const PairConst2 &k, f2 *acc) {
+  f2 r2 = fma2(rx, rx, fma2(ry, ry, mul2(rz, rz)));
+  r2 = f2_pk(fmaxf(f2_lo(r2), 1e-18f), fmaxf(f2_hi(r2), 1e-18f));
+  const f2 ir = f2_pk(rsqrtf(f2_lo(r2)), rsqrtf(f2_hi(r2)));
+  const f2 irout = f2_pk(fminf(f2_lo(irok), iroj), fminf(f2_hi(irok), iroj));
+  const f2 yv = mul2(mul2(r2, ir), irout);
+  const f2 t = mul2(sub2(yv, k.g), k.i1mg);
+  const f2 u = f2_pk(__saturatef(f2_lo(t)), __saturatef(f2_hi(t)));
+  const f2 u2 = mul2(u, u), u3 = mul2(u2, u);
+  const f2 poly = fma2(fma2(fma2(sub2(0ull, k.c20), u, k.c70), u, sub2(0ull, k.c84)), u, k.c35);
+  const f2 K = mul2(mul2(u2, u2), poly);
+  const f2 ir2 = mul2(ir, ir);
+  const f2 phi = mul2(mul2(K, ir2), ir);
+  if constexpr (!VJP) {
+    const f2 w = mul2(f2_dup(A.w), phi);  // m_j K / r^3
+    acc[0] = fma2(w, rx, acc[0]);
+    acc[1] = fma2(w, ry, acc[1]);
+    acc[2] = fma2(w, rz, acc[2]);
+  } else {
+    const f2 v = sub2(k.one, u);
+    const f2 dKr = mul2(mul2(mul2(k.c140i, u3), mul2(mul2(v, v), v)), irout);
+    const f2 psi = mul2(mul2(ir2, ir2), sub2(dKr, mul2(mul2(k.three, K), ir)));
+    const f2 mA = f2_dup(A.w);
+    const f2 wx = sub2(mul2(mk, f2_dup(L.x)), mul2(mA, lxk));
+    const f2 wy = sub2(mul2(mk, f2_dup(L.y)), mul2(mA, lyk));
+    const f2 wz = sub2(mul2(mk, f2_dup(L.z)), mul2(mA, lzk));
+    const f2 prw = mul2(psi, fma2(rx, wx, fma2(ry, wy, mul2(rz, wz))));
+    acc[0] = add2(acc[0], fma2(phi, wx, mul2(prw, rx)));
+    acc[1] = add2(acc[1], fma2(phi, wy, mul2(prw, ry)));
+    acc[2] = add2(acc[2], fma2(phi, wz, mul2(prw, rz)));
+    acc[3] = fma2(phi, fma2(f2_dup(L.x), rx, fma2(f2_dup(L.y), ry, mul2(f2_dup(L.z), rz))),
+                  acc[3]);
+  }
+}
+
 // outputs: with one split, the block writes out_c[k] = (add ? out_c[k] : 0)
 // + scale * sum itself; with several, the sums go to part
 struct DOut {
@@ -172,6 +221,19 @@ __global__ void __launch_bounds__(kDW * 32, MIXED ? P3T_DIRECT_MINB_MIXED : 1)
       }
     }
   }
+  struct TP {
+    f2 xh, yh, zh, xl, yl, zl, m, iro, lx, ly, lz;
+  } P{};
+  PairConst2 kc{};
+  if constexpr (MIXED) {
+    P = TP{f2_pk(txh[0], txh[1]), f2_pk(tyh[0], tyh[1]), f2_pk(tzh[0], tzh[1]),
+           f2_pk(txl[0], txl[1]), f2_pk(tyl[0], tyl[1]), f2_pk(tzl[0], tzl[1]),
+           f2_pk(tm[0], tm[1]), f2_pk(tiro[0], tiro[1]), f2_pk(tlx[0], tlx[1]),
+           f2_pk(tly[0], tly[1]), f2_pk(tlz[0], tlz[1])};
+    kc = PairConst2{f2_dup((float)g), f2_dup((float)i1mg), f2_dup(35.f), f2_dup(84.f),
+                    f2_dup(70.f), f2_dup(20.f), f2_dup(1.f), f2_dup(3.f),
+                    f2_dup((float)(140.0 * (1.0 / (1.0 - gamma))))};
+  }
   float fh[kDT][NC], fl[kDT][NC];  // MIXED running sums (float-float)
   double dd[kDT][NC];              // FP64 running sums
 #pragma unroll
@@ -200,21 +262,39 @@ __global__ void __launch_bounds__(kDW * 32, MIXED ? P3T_DIRECT_MINB_MIXED : 1)
     for (int t = 0; t < kDT; ++t)
 #pragma unroll
       for (int c = 0; c < NC; ++c) acc[t][c] = 0;
-#pragma unroll 4
-    for (int q = 0; q < lim; ++q) {
-      const Q4<T> A = sA[warp][q], B = sB[warp][q];
-      Q4<T> L{0, 0, 0, 0};
-      if constexpr (VJP) L = sL[warp][q];
+    if constexpr (MIXED) {
+      // the lane's two targets as the halves of packed pairs
+      static_assert(kDT == 2, "two targets per lane");
+      f2 a2[NC];
 #pragma unroll
-      for (int t = 0; t < kDT; ++t) {
-        T rx = txh[t] - A.x, ry = tyh[t] - A.y, rz = tzh[t] - A.z;
-        if constexpr (MIXED) {
-          rx += txl[t] - B.x;
-          ry += tyl[t] - B.y;
-          rz += tzl[t] - B.z;
+      for (int c = 0; c < NC; ++c) a2[c] = 0ull;
+#pragma unroll 2
+      for (int q = 0; q < lim; ++q) {
+        const Q4<T> A = sA[warp][q], B = sB[warp][q];
+        Q4<T> L{0, 0, 0, 0};
+        if constexpr (VJP) L = sL[warp][q];
+        const f2 rx = add2(sub2(P.xh, f2_dup(A.x)), sub2(P.xl, f2_dup(B.x)));
+        const f2 ry = add2(sub2(P.yh, f2_dup(A.y)), sub2(P.yl, f2_dup(B.y)));
+        const f2 rz = add2(sub2(P.zh, f2_dup(A.z)), sub2(P.zl, f2_dup(B.z)));
+        pair_term2<VJP>(rx, ry, rz, A, B.w, L, P.m, P.iro, P.lx, P.ly, P.lz, kc, a2);
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        acc[0][c] = f2_lo(a2[c]);
+        acc[1][c] = f2_hi(a2[c]);
+      }
+    } else {
+#pragma unroll 4
+      for (int q = 0; q < lim; ++q) {
+        const Q4<T> A = sA[warp][q], B = sB[warp][q];
+        Q4<T> L{0, 0, 0, 0};
+        if constexpr (VJP) L = sL[warp][q];
+#pragma unroll
+        for (int t = 0; t < kDT; ++t) {
+          T rx = txh[t] - A.x, ry = tyh[t] - A.y, rz = tzh[t] - A.z;
+          pair_term<T, VJP>(rx, ry, rz, A, B.w, L, tm[t], tiro[t], tlx[t], tly[t], tlz[t], g,
+                            i1mg, acc[t]);
         }
-        pair_term<T, VJP>(rx, ry, rz, A, B.w, L, tm[t], tiro[t], tlx[t], tly[t], tlz[t], g, i1mg,
-                          acc[t]);
       }
     }
 #pragma unroll

@@ -59,6 +59,41 @@ __device__ __forceinline__ FF ff_rsqrt(FF r2) {
   return ff_fast(y, 0.5f * y * d);
 }
 
+// ---- packed FP32 pairs ----------------------------------------------------------
+// a pair of floats in one 64-bit register (low half: the first value); the
+// .f32x2 instructions round each half as the scalar instruction would
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2_pk(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float f2_lo(f2 v) {
+  return __uint_as_float((unsigned)(v & 0xffffffffull));
+}
+__device__ __forceinline__ float f2_hi(f2 v) { return __uint_as_float((unsigned)(v >> 32)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2 f2_dup(float a) { return f2_pk(a, a); }
+
 struct SegView {
   const int64_t *off;  // nseg + 1 offsets (unused when nseg == 1)
   int nseg;
