@@ -185,6 +185,53 @@ __device__ bool kepler_uv(double X[3], double V[3], double dt, const KepConst &K
   return ok;
 }
 
+__device__ __forceinline__ double ldexp_fast(double x, int k) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e > 0 && e < 0x7ff && e + k > 0 && e + k < 0x7ff)
+    return __longlong_as_double(b + ((long long)k << 52));
+  return ldexp(x, k);
+}
+__device__ __forceinline__ int ilogb_fast(double x) {
+  const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+  return (e > 0 && e < 0x7ff) ? e - 1023 : ilogb(x);
+}
+
+// Conversions by integer operations.  On this part a conversion between FP64
+// and FP32 or from an integer to FP64 takes the FP64 pipe like an FP64
+// multiply (about 64 cycles of a sub-partition); along the serial block steps
+// of a close encounter these sit on the critical path, so where the result is
+// a normal number they are done on the bits instead, with the same results.
+// (float)(a 2^k), rounded to nearest even, for a 2^k in FP32's normal range
+__device__ __forceinline__ float d2f_scaled(double a, int k) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+  const int ed = (int)((b >> 52) & 0x7ff);
+  const int ef = ed - 1023 + k + 127;
+  if (ed == 0 || ed == 0x7ff || ef <= 0 || ef >= 255) return (float)ldexp_fast(a, k);
+  const unsigned long long m = b & 0xfffffffffffffull;
+  unsigned r = ((unsigned)ef << 23) | (unsigned)(m >> 29);
+  const unsigned long long rem = m & 0x1fffffffull, half = 0x10000000ull;
+  if (rem > half || (rem == half && (r & 1u))) ++r;  // a carry into the exponent is right
+  return __uint_as_float(r | ((unsigned)(b >> 32) & 0x80000000u));
+}
+// (double)f, exact
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const int ef = (int)((u >> 23) & 0xff);
+  if (ef == 0 || ef == 0xff) return (double)f;
+  return __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32 |
+                                          (unsigned long long)(ef - 127 + 1023) << 52 |
+                                          (unsigned long long)(u & 0x7fffffu) << 29));
+}
+// (double)x for 0 <= x < 2^53, exact
+__device__ __forceinline__ double i2d_exact(int64_t x) {
+  if (x <= 0) return (double)x;
+  const int e = 63 - __clzll(x);
+  return __longlong_as_double((long long)((unsigned long long)(e + 1023) << 52 |
+                                          (((unsigned long long)x << (52 - e)) &
+                                           0xfffffffffffffull)));
+}
+
 // Mixed path: the same drift in float-float arithmetic (FP32 instructions,
 // ~2^-47 relative per operation) for bound orbits whose Stumpff argument
 // stays below 1e-2 (a soft step is a small fraction of an orbit): the same
@@ -198,10 +245,13 @@ __device__ bool kepler_uv(double X[3], double V[3], double dt, const KepConst &K
 struct KepFF {
   FF sq, isq, imu;
 };
+// x = hi + lo with hi = (float)x and lo = (float)(x - hi) (the difference
+// exact); the conversions on the bits, one FP64 subtraction
 __device__ __forceinline__ FF ff_split(double x) {
-  const float h = (float)x;
-  return {h, (float)(x - (double)h)};
+  const float h = d2f_scaled(x, 0);
+  return {h, d2f_scaled(x - f2d_exact(h), 0)};
 }
+__device__ __forceinline__ double ff_to_double(FF a) { return f2d_exact(a.h) + f2d_exact(a.l); }
 __device__ __forceinline__ FF ff_sub(FF a, FF b) { return ff_add(a, ff_neg(b)); }
 __device__ __forceinline__ FF ff_c(float h, float l) { return {h, l}; }
 // the Stumpff series' coefficients as float-float constants
@@ -274,8 +324,8 @@ __device__ bool kepler_ff(double X[3], double V[3], double dt, const KepFF &K) {
   const FF gd = ff_sub(ff_c(1.0f, 0.0f), ff_mul(ff_mul(chi2, ir), C));
   for (int a = 0; a < 3; ++a) {
     const FF nv = ff_add(ff_mul(fd, x[a]), ff_mul(gd, v[a]));
-    X[a] = (double)nx[a].h + (double)nx[a].l;
-    V[a] = (double)nv.h + (double)nv.l;
+    X[a] = ff_to_double(nx[a]);
+    V[a] = ff_to_double(nv);
   }
   return true;
 }
@@ -453,53 +503,6 @@ struct CollOut {
 // operations when x (and the result) are normal -- the same values as ldexp
 // and ilogb, without an FP64 instruction (one costs 64 cycles of a
 // sub-partition's FP64 pipe on this part) -- and by ldexp / ilogb otherwise.
-__device__ __forceinline__ double ldexp_fast(double x, int k) {
-  const long long b = __double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7ff);
-  if (e > 0 && e < 0x7ff && e + k > 0 && e + k < 0x7ff)
-    return __longlong_as_double(b + ((long long)k << 52));
-  return ldexp(x, k);
-}
-__device__ __forceinline__ int ilogb_fast(double x) {
-  const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
-  return (e > 0 && e < 0x7ff) ? e - 1023 : ilogb(x);
-}
-
-// Conversions by integer operations.  On this part a conversion between FP64
-// and FP32 or from an integer to FP64 takes the FP64 pipe like an FP64
-// multiply (about 64 cycles of a sub-partition); along the serial block steps
-// of a close encounter these sit on the critical path, so where the result is
-// a normal number they are done on the bits instead, with the same results.
-// (float)(a 2^k), rounded to nearest even, for a 2^k in FP32's normal range
-__device__ __forceinline__ float d2f_scaled(double a, int k) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(a);
-  const int ed = (int)((b >> 52) & 0x7ff);
-  const int ef = ed - 1023 + k + 127;
-  if (ed == 0 || ed == 0x7ff || ef <= 0 || ef >= 255) return (float)ldexp_fast(a, k);
-  const unsigned long long m = b & 0xfffffffffffffull;
-  unsigned r = ((unsigned)ef << 23) | (unsigned)(m >> 29);
-  const unsigned long long rem = m & 0x1fffffffull, half = 0x10000000ull;
-  if (rem > half || (rem == half && (r & 1u))) ++r;  // a carry into the exponent is right
-  return __uint_as_float(r | ((unsigned)(b >> 32) & 0x80000000u));
-}
-// (double)f, exact
-__device__ __forceinline__ double f2d_exact(float f) {
-  const unsigned u = __float_as_uint(f);
-  const int ef = (int)((u >> 23) & 0xff);
-  if (ef == 0 || ef == 0xff) return (double)f;
-  return __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32 |
-                                          (unsigned long long)(ef - 127 + 1023) << 52 |
-                                          (unsigned long long)(u & 0x7fffffu) << 29));
-}
-// (double)x for 0 <= x < 2^53, exact
-__device__ __forceinline__ double i2d_exact(int64_t x) {
-  if (x <= 0) return (double)x;
-  const int e = 63 - __clzll(x);
-  return __longlong_as_double((long long)((unsigned long long)(e + 1023) << 52 |
-                                          (((unsigned long long)x << (52 - e)) &
-                                           0xfffffffffffffull)));
-}
-
 // The step estimates only choose a power-of-two step: formed in FP32 from
 // components scaled by an exact power of two 2^k (j by s, a2 by s^2, a3 by
 // s^3, s = 2^e close to the step) so that nothing overflows FP32.
