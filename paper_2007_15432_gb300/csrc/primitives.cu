@@ -186,9 +186,16 @@ __global__ void radix_upsweep(const uint64_t *keys, const int64_t *d_n,
     h[threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = tile * kSortTile;
+    // every load of the tile issued before the first is used
+    uint32_t dig[kSortItems];
+#pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
       const int64_t e = base + k * kSortThreads + threadIdx.x;
-      const uint32_t d = e < n ? (uint32_t)((keys[e] >> shift) & (kRadix - 1)) : kRadix;
+      dig[k] = e < n ? (uint32_t)((__ldg(&keys[e]) >> shift) & (kRadix - 1)) : kRadix;
+    }
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+      const uint32_t d = dig[k];
       const uint32_t peers = __match_any_sync(0xffffffffu, d);  // one atomic per digit and warp
       if (d < kRadix && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
     }
@@ -247,6 +254,18 @@ radix_downsweep(const uint64_t *keys, const int32_t *vals, uint64_t *okeys,
     uint64_t key[kSortItems];
     int32_t val[kSortItems];
     uint32_t dig[kSortItems], rk[kSortItems];
+    // the tile's loads all issued up front: the ranking rounds below are
+    // separated by block barriers, which no load can be moved across
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+      const int64_t e = base + r * kSortThreads + t;
+      key[r] = 0;
+      val[r] = 0;
+      if (e < n) {
+        key[r] = __ldg(&keys[e]);
+        val[r] = __ldg(&vals[e]);
+      }
+    }
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
 #pragma unroll
@@ -254,14 +273,8 @@ radix_downsweep(const uint64_t *keys, const int32_t *vals, uint64_t *okeys,
       __syncthreads();
       const int64_t e = base + r * kSortThreads + t;
       const bool valid = e < n;
-      key[r] = 0;
-      val[r] = 0;
-      uint32_t d = kRadix;  // invalid lanes form their own group
-      if (valid) {
-        key[r] = keys[e];
-        val[r] = vals[e];
-        d = (uint32_t)((key[r] >> shift) & (kRadix - 1));
-      }
+      // invalid lanes form their own group
+      const uint32_t d = valid ? (uint32_t)((key[r] >> shift) & (kRadix - 1)) : kRadix;
       dig[r] = d;
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
       if (valid && lane == __ffs(peers) - 1) s_warp[w][d] = __popc(peers);
