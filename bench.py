@@ -284,15 +284,20 @@ def run_ours(args):
         P.p3t_hard_step(ss.ctx, st, ss.cl, prm.dt_soft,
                         hsteps_all[k:k + 1] if k is not None else ss.hsteps, stream)
         if e: e[1].record(stream)
+        # composites formed by this hard step (synchronises): the merge after
+        # the second kick rebuilds the neighbour lists, so the force before
+        # it builds none
+        pending = ss.collisions and P.p3t_collisions_pending(ss.ctx, stream) > 0
         P.p3t_build_tree(ss.ctx, st, False, stream)
         if e: e[2].record(stream)
         P.p3t_soft_force(ss.ctx, st, ss.acc, cnt[0], stream)
         if e: e[3].record(stream)
-        ss.cl = P.p3t_neighbours(ss.ctx, st, ss.nb_off, ss.nb_idx, stream)
+        if not pending:
+            ss.cl = P.p3t_neighbours(ss.ctx, st, ss.nb_off, ss.nb_idx, stream)
         if e: e[4].record(stream)
         P.p3t_kick(ss.ctx, st, ss.acc, h, stream)
         if e: e[5].record(stream)
-        if ss.collisions:
+        if pending:
             # procedure step 9: merge (synchronises), then new radii and force
             nm, eh, es = P.p3t_merge(ss.ctx, st, None, stream)
             e_disp[0] += eh
@@ -305,6 +310,8 @@ def run_ours(args):
                 P.p3t_build_tree(ss.ctx, st, False, stream)
                 P.p3t_soft_force(ss.ctx, st, ss.acc, cnt[1], stream)
                 ss.cl = P.p3t_neighbours(ss.ctx, st, ss.nb_off, ss.nb_idx, stream)
+            else:
+                raise RuntimeError("composites pending but nothing merged")
         if e: e[6].record(stream)
 
     for _ in range(W):

@@ -295,6 +295,16 @@ int p3t_kick(p3t_ctx *ctx, p3t_particles *p, const double *ax, const double *ay,
 int p3t_merge(p3t_ctx *ctx, p3t_particles *p, int32_t *new_index, double *e_disp,
               int64_t *n_merged, void *stream);
 
+/* Whether the last p3t_hard_step formed composites that p3t_merge has not
+ * yet merged (Sec. 2.4.1): *n_clusters (host) receives the number of
+ * clusters in which composites formed, 0 when the step had no collision (or
+ * f_radius = 0).  Synchronises `stream`;
+ * not capturable.  A caller that learns of pending merges right after the
+ * hard step may leave out the neighbour lists of the force that precedes
+ * the merge (procedure step 7): the recomputation after the merge
+ * (procedure step 9) replaces them before any hard step reads them. */
+int p3t_collisions_pending(p3t_ctx *ctx, int64_t *n_clusters, void *stream);
+
 /* The soft force at theta = 0 (and the forward force of the adjoint) -- the
  * soft force of Eq. softforce summed directly over all pairs, which is what
  * the tree walk gives at theta = 0:

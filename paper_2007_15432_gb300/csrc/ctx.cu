@@ -378,6 +378,18 @@ int p3t_merge(p3t_ctx *c, p3t_particles *p, int32_t *new_index, double *e_disp,
   return rc;
 }
 
+int p3t_collisions_pending(p3t_ctx *c, int64_t *n_clusters, void *stream) {
+  if (!c || !n_clusters) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  const cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long ctr = 0;  // (records << 32) | entries
+  if (cudaMemcpyAsync(&ctr, c->coll_ctr, sizeof(ctr), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return P3T_ERR_CUDA;
+  *n_clusters = (int64_t)(ctr >> 32);
+  return P3T_OK;
+}
+
 // the all-pairs kernels' scratch: the packed particles in hw (sized by
 // ensure) and the partial sums, one allocation of fixed size made on the
 // first call (a graph captured after one eager call allocates nothing)

@@ -86,6 +86,7 @@ _sig = {
     "p3t_kepler_drift": (C.c_int, [_CTX, C.POINTER(Particles), C.c_double, _vp]),
     "p3t_kick": (C.c_int, [_CTX, C.POINTER(Particles), _vp, _vp, _vp, C.c_double, _vp]),
     "p3t_energy": (C.c_int, [_CTX, C.POINTER(Particles), _vp, _vp]),
+    "p3t_collisions_pending": (C.c_int, [_CTX, C.POINTER(C.c_int64), _vp]),
     "p3t_merge": (C.c_int, [_CTX, C.POINTER(Particles), _vp, C.POINTER(C.c_double),
                             C.POINTER(C.c_int64), _vp]),
     "p3t_soft_force_direct": (C.c_int, [_CTX, C.POINTER(Particles), _vp, _vp, _vp, _vp]),
@@ -292,6 +293,15 @@ def p3t_energy(ctx, st: State, out: torch.Tensor, stream=None) -> None:
     _check(_lib.p3t_energy(ctx, C.byref(p), _ptr(out), _stream(stream)), "p3t_energy")
 
 
+def p3t_collisions_pending(ctx, stream=None) -> int:
+    """Clusters of the last hard step in which composites formed that are not
+    yet merged (0: no collision).  Synchronises."""
+    n = C.c_int64(0)
+    _check(_lib.p3t_collisions_pending(ctx, C.byref(n), _stream(stream)),
+           "p3t_collisions_pending")
+    return n.value
+
+
 def p3t_merge(ctx, st: State, new_index: torch.Tensor | None = None, stream=None):
     """Procedure step 9 for collisions: merges the composites of the last hard
     step, shortens the tensors of ``st`` to the new count in place and returns
@@ -375,7 +385,9 @@ class SoftStep:
     lists and clusters; each ``step()`` then runs kick, hard step, tree,
     force, neighbours, kick and, with collisions on (``f_radius > 0`` and
     ``st.r_phys``), the merge followed by new cut-off radii, force and
-    neighbours when particles merged.  ``e_disp`` accumulates the dissipated
+    neighbours when particles merged (a step whose hard part formed
+    composites skips the neighbour lists of its first force: the merge
+    replaces them).  ``e_disp`` accumulates the dissipated
     energy {hard part, kick}.
     """
 
@@ -440,10 +452,16 @@ class SoftStep:
         h = 0.5 * self.params.dt_soft
         p3t_kick(self.ctx, self.st, self.acc, h, stream)
         p3t_hard_step(self.ctx, self.st, self.cl, self.params.dt_soft, self.hsteps, stream)
-        self.force(stream)
+        # composites formed in this hard step: the merge after the second kick
+        # recomputes the neighbour lists, so the force before it needs none
+        pending = self.collisions and p3t_collisions_pending(self.ctx, stream) > 0
+        p3t_build_tree(self.ctx, self.st, False, stream)
+        p3t_soft_force(self.ctx, self.st, self.acc, self.counts, stream)
+        if not pending:
+            self.cl = p3t_neighbours(self.ctx, self.st, self.nb_off, self.nb_idx, stream)
         p3t_kick(self.ctx, self.st, self.acc, h, stream)
-        if self.collisions:
-            self.merge(stream)
+        if pending and self.merge(stream) == 0:
+            raise P3TError(P3T_ERR_INVALID, "composites pending but nothing merged")
 
     def status(self):
         rc, req = p3t_status(self.ctx)

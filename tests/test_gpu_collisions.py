@@ -79,6 +79,9 @@ def test_collision_hard_kick_merge_match_oracle(P3T, name):
     rc, hsteps, comp, e_hard = O.hard_step(so, ro, op, ocl, P.dt_soft, rp, with_sets=True)
     assert rc == 0
     assert (comp >= 0).sum() >= 4
+    # one pending record per cluster that holds composites
+    lab = ocl.label[comp >= 0]
+    assert P3T.p3t_collisions_pending(ctx) == len(np.unique(lab))
     assert int(steps.item()) == hsteps
     g = st.numpy()
     for keys in (("x", "y", "z"), ("vx", "vy", "vz")):
@@ -111,7 +114,8 @@ def test_collision_hard_kick_merge_match_oracle(P3T, name):
     assert np.all(np.abs(g["r_phys"] - rp2) <= 4 * np.spacing(rp2))
     assert eh == pytest.approx(e_hard, rel=1e-12, abs=1e-30)
     assert es == pytest.approx(e_soft, rel=1e-12, abs=1e-40)
-    # the list is consumed: a second merge finds nothing
+    # the list is consumed: nothing pending, a second merge finds nothing
+    assert P3T.p3t_collisions_pending(ctx) == 0
     assert P3T.p3t_merge(ctx, st)[0] == 0
     P3T.p3t_destroy(ctx)
 
@@ -135,6 +139,7 @@ def test_collisions_without_contact_change_nothing(P3T):
         cl, keep = _cluster_struct(P3T, ocl)
         P3T.p3t_hard_step(ctx, st, cl, P.dt_soft)
         ni = torch.empty(n, dtype=torch.int32, device="cuda")
+        assert P3T.p3t_collisions_pending(ctx) == 0
         nm, eh, es = P3T.p3t_merge(ctx, st, ni)
         assert P3T.p3t_status(ctx)[0] == 0
         assert nm == 0 and eh == 0.0 and es == 0.0
