@@ -42,10 +42,6 @@ __device__ __forceinline__ D6 operator*(double s, const D6 &a) {
   for (int i = 0; i < 6; ++i) r.d[i] = s * a.d[i];
   return r;
 }
-__device__ __forceinline__ D6 operator+(double s, const D6 &a) {
-  D6 r = a; r.v = s + a.v;
-  return r;
-}
 __device__ __forceinline__ D6 operator/(const D6 &a, const D6 &b) {
   D6 r; r.v = a.v / b.v;
   const double ib = 1.0 / b.v;

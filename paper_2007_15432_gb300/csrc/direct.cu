@@ -21,6 +21,8 @@
 // instruction runs inside the pair loop.
 #include <math.h>
 
+#include <type_traits>
+
 #include "p3t_internal.cuh"
 
 namespace {
@@ -46,7 +48,6 @@ struct DT<true> {
   using T = float;
 };
 
-__device__ __forceinline__ float rsq(float a) { return rsqrtf(a); }
 __device__ __forceinline__ double rsq(double a) { return 1.0 / sqrt(a); }
 
 // hi + lo += p without losing the rounding error of the addition (TwoSum)
@@ -62,6 +63,8 @@ template <typename T, bool VJP>
 __device__ __forceinline__ void pair_term(T rx, T ry, T rz, const Q4<T> &A, T iroj,
                                           const Q4<T> &L, T mk, T irok, T lxk, T lyk, T lzk,
                                           T g, T i1mg, T *acc) {
+  // the FP64 path's term (the mixed path uses pair_term2)
+  static_assert(std::is_same<T, double>::value, "FP64 pair term");
   const T r2 = rx * rx + ry * ry + rz * rz;
   const T ir = rsq(r2);
   const T irout = irok < iroj ? irok : iroj;  // 1 / max(r_out,k, r_out,j)
