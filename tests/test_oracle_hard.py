@@ -8,7 +8,7 @@ scheme, a finite-difference jerk, and numerically integrated W(y).
 """
 import numpy as np
 import pytest
-from scipy.integrate import quad, solve_ivp
+from scipy.integrate import solve_ivp
 
 from paper_2007_15432_gb300 import disks
 
@@ -152,11 +152,17 @@ def test_hermite_two_body_inside_inner_cutoff(orc):
 
 
 def _W(y, g, orc):
-    """W(y) = y int_y^inf K(s)/s^2 ds, integrated numerically from the oracle's K."""
+    """W(y) = y int_y^inf K(s)/s^2 ds, integrated numerically from the oracle's K:
+    beyond 1 the integrand is 1/s^2 (integral 1); on [max(y, g), 1] K is a
+    polynomial, so K/s^2 is analytic there with its one pole at s = 0, and a
+    64-point Gauss-Legendre rule is exact to rounding."""
     if y >= 1.0:
         return 1.0
-    val, _ = quad(lambda t: orc.changeover_K(t, g) / t**2, max(y, g), 1.0, epsabs=1e-15, epsrel=1e-14, limit=200)
-    return y * (val + 1.0)
+    a = max(y, g)
+    xs, ws = np.polynomial.legendre.leggauss(64)
+    t = 0.5 * (1.0 - a) * xs + 0.5 * (1.0 + a)
+    f = np.array([orc.changeover_K(v, g) for v in t]) / t**2
+    return y * (0.5 * (1.0 - a) * np.dot(ws, f) + 1.0)
 
 
 def test_hermite_conserves_hard_energy_through_changeover(orc):
