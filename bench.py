@@ -400,7 +400,7 @@ def run_ours(args):
     achieved = flops_per_launch / walk_s / 1e12
     line = dict(
         metric=METRIC, value=tot_inter / tot_elapsed, unit=UNIT, n_gpus=world, steps=K,
-        warmup=W, ms_per_step=1e3 * elapsed / K, higher_is_better=True, scaling="weak",
+        warmup=W, ms_per_step=1e3 * tot_elapsed / K, higher_is_better=True, scaling="weak",
         vs_baseline=None, dtype="f32/f64" if prec == P.P3T_MIXED else "f64",
         data="synthetic (seeded disk)",
         config=dict(workload=workload_name(args.n), n=args.n, group_size=args.group_size,
