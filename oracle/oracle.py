@@ -114,13 +114,18 @@ def lib():
         L.or_hard_acc_jerk.argtypes = ([C.c_int64] + [_dp] * 8 + [_P, C.c_int64, _dp, _dp])
         L.or_hermite_cluster.restype = C.c_int
         L.or_hermite_cluster.argtypes = ([C.c_int64, _i32p] + [_dp] * 8 + [
-            _vp, _P, C.c_double, C.POINTER(C.c_int64), _vp, C.POINTER(C.c_double)])
+            _vp, _P, C.c_double, C.POINTER(C.c_int64), _vp, C.POINTER(C.c_double), _vp])
         L.or_kepler_drift.restype = C.c_int
         L.or_kepler_drift.argtypes = [C.c_int64, _vp] + [_dp] * 6 + [C.c_double, C.c_double]
         L.or_hard_step.restype = C.c_int
         L.or_hard_step.argtypes = ([C.c_int64] + [_dp] * 8 + [
             _vp, _P, C.c_double, C.c_int64, _i32p, C.c_int64, _i64p, _i32p,
-            C.POINTER(C.c_int64), _i32p, C.POINTER(C.c_double)])
+            C.POINTER(C.c_int64), _i32p, C.POINTER(C.c_double), _vp])
+        L.or_bh_threshold.restype = C.c_int64
+        L.or_bh_threshold.argtypes = [C.c_double, C.c_int]
+        L.or_mac_open.restype = C.c_int
+        L.or_mac_open.argtypes = [C.c_double, C.c_int, _i64p, _i64p, _i64p, C.c_int64,
+                                  _i64p, _i64p, C.c_int64]
         L.or_kick_composites.restype = C.c_double
         L.or_kick_composites.argtypes = [C.c_int64] + [_dp] * 6 + [C.c_double, _dp, _i32p]
         L.or_merge.restype = C.c_int64
@@ -216,6 +221,21 @@ def tree_soft(s: dict, r_out, r_search, p: Params, targets=None,
                            depth=int(stats[2]), max_leaf=int(stats[3])))
 
 
+def bh_threshold(theta: float, level: int) -> int:
+    """ceil((2^(22-level))^2 / theta^2) in exact arithmetic (half cell units)."""
+    return int(lib().or_bh_threshold(float(theta), int(level)))
+
+
+def mac_open(theta: float, level: int, node_c2, node_qlo, node_qhi, node_R: int,
+             grp_qlo, grp_qhi, grp_R: int) -> bool:
+    """The tree's node-opening test (reading C4) for grid boxes given directly."""
+    def a(v):
+        return np.ascontiguousarray(v, dtype=np.int64)
+    return bool(lib().or_mac_open(float(theta), int(level), a(node_c2), a(node_qlo),
+                                  a(node_qhi), int(node_R), a(grp_qlo), a(grp_qhi),
+                                  int(grp_R)))
+
+
 def node_moments(x, y, z, m):
     out = np.empty(10)
     lib().or_node_moments(len(m), _f64(x), _f64(y), _f64(z), _f64(m), out)
@@ -308,24 +328,26 @@ def _vptr(a):
 
 
 def hermite_cluster(s: dict, r_out, p: Params, members, dt: float, r_phys=None,
-                    with_sets: bool = False):
+                    with_sets: bool = False, member_steps: bool = False):
     """Integrates the members of one cluster in place; returns (status, steps),
     or (status, steps, roots, e_disp) with ``with_sets`` (collisions: ``roots`` the
     lowest member of each member's composite, cluster-local; ``e_disp`` the
-    dissipated energy).  ``r_phys`` (physical radii, caller order) switches the
+    dissipated energy), with the corrector steps of each member appended when
+    ``member_steps``.  ``r_phys`` (physical radii, caller order) switches the
     collision test on when ``p.f_radius > 0``."""
     mem = np.ascontiguousarray(members, dtype=np.int32)
     ns = C.c_int64(0)
     ed = C.c_double(0.0)
     roots = np.empty(len(mem), dtype=np.int32)
+    ms = np.zeros(len(mem), dtype=np.int32)
     rp = None if r_phys is None else _f64(r_phys)
     cp = p.c()
     st = lib().or_hermite_cluster(len(mem), mem, s["x"], s["y"], s["z"], s["vx"], s["vy"],
                                   s["vz"], _f64(s["m"]), _f64(r_out), _vptr(rp), C.byref(cp),
-                                  float(dt), C.byref(ns), roots.ctypes.data, C.byref(ed))
-    if with_sets:
-        return st, ns.value, roots, ed.value
-    return st, ns.value
+                                  float(dt), C.byref(ns), roots.ctypes.data, C.byref(ed),
+                                  ms.ctypes.data)
+    out = (st, ns.value, roots, ed.value) if with_sets else (st, ns.value)
+    return out + (ms,) if member_steps else out
 
 
 def kepler_drift(s: dict, dt: float, mu: float, idx=None) -> int:
@@ -336,14 +358,16 @@ def kepler_drift(s: dict, dt: float, mu: float, idx=None) -> int:
 
 
 def hard_step(s: dict, r_out, p: Params, cl: Clusters, dt: float, r_phys=None,
-              with_sets: bool = False):
+              with_sets: bool = False, member_steps: bool = False):
     """Hard step and Kepler drift in place; returns (status, hermite particle-steps), or with
     ``with_sets`` also (comp_root, e_hard): the collision composites (lowest member's
-    caller index, -1 outside composites) and the collisions' dissipation."""
+    caller index, -1 outside composites) and the collisions' dissipation; with
+    ``member_steps`` also the corrector steps of every particle (0 for singles)."""
     ns = C.c_int64(0)
     eh = C.c_double(0.0)
     n = len(s["m"])
     comp = np.empty(n, dtype=np.int32)
+    msteps = np.zeros(max(n, 1), dtype=np.int32)
     rp = None if r_phys is None else _f64(r_phys)
     cp = p.c()
     st = lib().or_hard_step(n, s["x"], s["y"], s["z"], s["vx"], s["vy"], s["vz"],
@@ -351,10 +375,9 @@ def hard_step(s: dict, r_out, p: Params, cl: Clusters, dt: float, r_phys=None,
                             len(cl.singles), np.ascontiguousarray(cl.singles, dtype=np.int32),
                             len(cl.cl_off) - 1, np.ascontiguousarray(cl.cl_off, dtype=np.int64),
                             np.ascontiguousarray(cl.cl_mem, dtype=np.int32), C.byref(ns),
-                            comp, C.byref(eh))
-    if with_sets:
-        return st, ns.value, comp, eh.value
-    return st, ns.value
+                            comp, C.byref(eh), msteps.ctypes.data)
+    out = (st, ns.value, comp, eh.value) if with_sets else (st, ns.value)
+    return out + (msteps[:n],) if member_steps else out
 
 
 def kick_composites(s: dict, acc, h: float, comp_root):

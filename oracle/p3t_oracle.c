@@ -164,11 +164,10 @@ int or_direct_soft(int64_t n, const double *x, const double *y, const double *z,
 /* definitions below are reading C4).                                         */
 /*  * root cube: bounding box of the positions, made cubic (side L = largest  */
 /*    extent), corner at the per-axis minimum;                                */
-/*  * each axis quantised to q = floor((v - lo) S) in [0, 2^21), with the    */
-/*    scale S = 2^21 / L formed once (unit u = L / 2^21); bits interleaved    */
-/*    (x highest) into a 63-bit Morton key; particles ordered by (key,        */
-/*    caller index).  q is the cell of v up to ~1e-9 u, well inside the two- */
-/*    cell margin of the reach test below;                                    */
+/*  * each axis quantised to its cell q = floor(d / u), d = v - lo (rounded   */
+/*    to FP64), u = L / 2^21 (exact), the quotient taken exactly: the largest */
+/*    q with q u <= d, clamped to [0, 2^21); bits interleaved (x highest)     */
+/*    into a 63-bit Morton key; particles ordered by (key, caller index);     */
 /*  * a node is a key prefix at level l holding > 0 particles; a node is      */
 /*    split while it holds more than leaf_size particles and l < 21;          */
 /*  * target groups: a node is a group iff it holds <= group_size particles  */
@@ -194,8 +193,13 @@ static uint64_t spread3(uint64_t v) {
   return r;
 }
 
-static int64_t quantise(double v, double lo, double S) {
-  int64_t q = (int64_t)floor((v - lo) * S);
+static int64_t quantise(double v, double lo, double L) {
+  const double u = ldexp(L, -OR_BITS);
+  const double d = v - lo;
+  int64_t q = (int64_t)floor(d / u);
+  /* the rounded quotient can reach the next integer from below: keep q u <= d */
+  /* (the fused q u - d is rounded once, so its sign is that of the exact one) */
+  if (fma((double)q, u, -d) > 0.0) --q;
   if (q < 0) q = 0;
   if (q > OR_QMAX - 1) q = OR_QMAX - 1;
   return q;
@@ -219,11 +223,10 @@ int or_morton_keys(int64_t n, const double *x, const double *y, const double *z,
                    uint64_t *key, double box_out[4]) {
   double box[4];
   root_box(n, x, y, z, box);
-  const double S = (double)OR_QMAX / box[3];
   for (int64_t i = 0; i < n; ++i) {
-    uint64_t qx = (uint64_t)quantise(x[i], box[0], S);
-    uint64_t qy = (uint64_t)quantise(y[i], box[1], S);
-    uint64_t qz = (uint64_t)quantise(z[i], box[2], S);
+    uint64_t qx = (uint64_t)quantise(x[i], box[0], box[3]);
+    uint64_t qy = (uint64_t)quantise(y[i], box[1], box[3]);
+    uint64_t qz = (uint64_t)quantise(z[i], box[2], box[3]);
     key[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
   }
   if (box_out) memcpy(box_out, box, sizeof(box));
@@ -373,9 +376,9 @@ static void tree_build(or_tree *T, int64_t n, const double *x, const double *y,
     T->ord[s] = i; T->key[s] = kv[s].key;
     T->x[s] = x[i]; T->y[s] = y[i]; T->z[s] = z[i]; T->m[s] = m[i];
     T->ro[s] = ro[i]; T->rs[s] = rs[i];
-    T->qx[s] = quantise(x[i], T->box[0], (double)OR_QMAX / T->box[3]);
-    T->qy[s] = quantise(y[i], T->box[1], (double)OR_QMAX / T->box[3]);
-    T->qz[s] = quantise(z[i], T->box[2], (double)OR_QMAX / T->box[3]);
+    T->qx[s] = quantise(x[i], T->box[0], T->box[3]);
+    T->qy[s] = quantise(y[i], T->box[1], T->box[3]);
+    T->qz[s] = quantise(z[i], T->box[2], T->box[3]);
   }
   free(kv); free(key);
   /* breadth-first: children of a node are appended contiguously */
@@ -415,18 +418,45 @@ static void tree_free(or_tree *T) {
   free(T->node); free(T->parent);
 }
 
-/* Barnes-Hut thresholds per level (reading C4): open iff d^2 < T[l] with    */
-/* T[l] = ceil((2^(22-l))^2 / theta^2) in half units; theta = 0 opens all.    */
-static void bh_thresholds(double theta, int64_t T[OR_BITS + 1]) {
-  const double big = 4611686018427387904.0; /* 2^62 */
-  double th2 = theta * theta;
-  for (int l = 0; l <= OR_BITS; ++l) {
-    double X = th2 > 0.0 ? ldexp(1.0, 2 * (OR_BITS + 1 - l)) / th2 : big;
-    X = ceil(X);
-    T[l] = X < big ? (int64_t)X : (int64_t)4611686018427387904LL;
+/* Barnes-Hut thresholds per level (reading C4): open iff d^2 < T[l], T[l]   */
+/* the smallest integer >= side^2 / theta^2, side = 2^(22-l) half units, so  */
+/* that d^2 < T[l] is exactly side^2 > theta^2 d^2 for the integer d^2.       */
+/* Exact integer arithmetic: theta = M 2^E with M an odd integer (frexp), so  */
+/* side^2 / theta^2 = 2^K / M^2 with K = 2(22 - l) - 2E, and T = ceil(2^K /   */
+/* M^2) by long division (M^2 < 2^106, held in 128 bits).  T is capped at     */
+/* 2^62, above every d^2 on the grid; theta = 0 opens every node.            */
+#define OR_TCAP ((int64_t)1 << 62)
+static int64_t bh_threshold(double theta, int level) {
+  if (!(theta > 0.0)) return OR_TCAP;
+  int e;
+  double fr = frexp(theta, &e);              /* theta = fr 2^e, 1/2 <= fr < 1 */
+  uint64_t M = (uint64_t)ldexp(fr, 53);      /* theta = M 2^(e - 53) exactly   */
+  int E = e - 53;
+  while ((M & 1u) == 0) { M >>= 1; ++E; }
+  const unsigned __int128 D = (unsigned __int128)M * M;
+  const int K = 2 * (OR_BITS + 1 - level) - 2 * E;
+  if (K < 0) return 1;                       /* 0 < side^2 / theta^2 < 1 */
+  unsigned __int128 r = 0;
+  int64_t q = 0;
+  for (int b = K; b >= 0; --b) {             /* the bits of 2^K, highest first */
+    r = (r << 1) | (unsigned __int128)(b == K);
+    int bit = 0;
+    if (r >= D) { r -= D; bit = 1; }
+    q = 2 * q + bit;
+    if (q >= OR_TCAP) return OR_TCAP;
   }
+  if (r != 0) ++q;
+  return q < OR_TCAP ? q : OR_TCAP;
 }
 
+static void bh_thresholds(double theta, int64_t T[OR_BITS + 1]) {
+  for (int l = 0; l <= OR_BITS; ++l) T[l] = bh_threshold(theta, l);
+}
+
+/* The opening test of a node for a target group, on the grid (reading C4), */
+/* exported for the tests: cells [gq_lo, gq_hi] of the group, the node's     */
+/* level, cell centre c2 (half units), cells [nq_lo, nq_hi] and the reaches  */
+/* R of both.  Returns 1 when the node is opened.                             */
 /* Opening decision for node nd seen from target group g (reading C4). */
 static int mac_open(const or_node *g, const or_node *nd, const int64_t *bh) {
   int64_t d2 = 0, g2 = 0;
@@ -444,6 +474,24 @@ static int mac_open(const or_node *g, const or_node *nd, const int64_t *bh) {
   int64_t R = g->R > nd->R ? g->R : nd->R;
   return g2 < R * R;
 }
+
+int or_mac_open(double theta, int level, const int64_t node_c2[3],
+                const int64_t node_qlo[3], const int64_t node_qhi[3], int64_t node_R,
+                const int64_t grp_qlo[3], const int64_t grp_qhi[3], int64_t grp_R) {
+  or_node g, nd;
+  memset(&g, 0, sizeof(g));
+  memset(&nd, 0, sizeof(nd));
+  for (int a = 0; a < 3; ++a) {
+    g.qlo[a] = grp_qlo[a]; g.qhi[a] = grp_qhi[a];
+    nd.qlo[a] = node_qlo[a]; nd.qhi[a] = node_qhi[a]; nd.c2[a] = node_c2[a];
+  }
+  g.R = grp_R; nd.R = node_R; nd.level = level;
+  int64_t bh[OR_BITS + 1];
+  bh_thresholds(theta, bh);
+  return mac_open(&g, &nd, bh);
+}
+
+int64_t or_bh_threshold(double theta, int level) { return bh_threshold(theta, level); }
 
 typedef struct {
   int32_t *ci, *cj;
@@ -773,61 +821,69 @@ void or_kick(int64_t n, double *vx, double *vy, double *vz, const double *ax,
 /* Hard force and jerk on member k of a cluster (Eq. hardforce):             */
 /*   a_k = -G M_* x_k / |x_k|^3 - sum_{j != k} G m_j (1 - K(y)) r / r^3,      */
 /* r = x_k - x_j, y = r / r_out,kj (reading C8: all other cluster members).   */
-/* The jerk is the time derivative, including dK/dt = K'(y) (r.v)/(r r_out).  */
+/* The jerk is the time derivative along the relative velocity u:            */
+/*   d/dt [(1 - K) r / r^3] = (1 - K) [u / r^3 - 3 (r.u) r / r^5]             */
+/*                            - K'(y) (r.u) / (r r_out,kj) r / r^3.           */
+/* Written as printed, term by term; member sets (composites, Sec. 2.4.1):   */
+/* with set given, the other members of k's own composite (set[j] ==          */
+/* set[k]) are left out, and with RP given *partner receives the lowest-     */
+/* index member j outside k's composite that touches k, r_kj < f (R_p,k +    */
+/* R_p,j), at the positions the force is evaluated at (or -1).                */
 /* ========================================================================= */
+static void hard_acc_jerk_sets(int64_t nc, const double *x, const double *y,
+                               const double *z, const double *vx, const double *vy,
+                               const double *vz, const double *m, const double *r_out,
+                               const double *RP, const int64_t *set, const or_params *p,
+                               int64_t k, double acc[3], double jerk[3], int64_t *partner) {
+  double ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0;
+  if (partner) *partner = -1;
+  {
+    /* the central star: -G M_* x / r^3 and its derivative */
+    double r2 = x[k] * x[k] + y[k] * y[k] + z[k] * z[k];
+    double r = sqrt(r2);
+    double r3 = r2 * r, r5 = r3 * r2;
+    double rv = x[k] * vx[k] + y[k] * vy[k] + z[k] * vz[k];
+    double GM = p->G * p->m_star;
+    ax -= GM * x[k] / r3; ay -= GM * y[k] / r3; az -= GM * z[k] / r3;
+    jx -= GM * (vx[k] / r3 - 3.0 * rv * x[k] / r5);
+    jy -= GM * (vy[k] / r3 - 3.0 * rv * y[k] / r5);
+    jz -= GM * (vz[k] / r3 - 3.0 * rv * z[k] / r5);
+  }
+  for (int64_t j = 0; j < nc; ++j) {
+    if (j == k || (set && set[j] == set[k])) continue;
+    double rx = x[k] - x[j], ry = y[k] - y[j], rz = z[k] - z[j];
+    double ux = vx[k] - vx[j], uy = vy[k] - vy[j], uz = vz[k] - vz[j];
+    double r2 = rx * rx + ry * ry + rz * rz;
+    if (RP && partner && *partner < 0) {
+      double sr = p->f_radius * (RP[k] + RP[j]);
+      if (r2 < sr * sr) *partner = j;
+    }
+    if (r2 == 0.0) continue;
+    double r = sqrt(r2);
+    double ro = dmax(r_out[k], r_out[j]);
+    double yv = r / ro;
+    double w = 1.0 - or_changeover_K(yv, p->gamma);
+    if (w == 0.0) continue;
+    double dK = or_changeover_dKdy(yv, p->gamma);
+    double r3 = r2 * r, r5 = r3 * r2;
+    double rv = rx * ux + ry * uy + rz * uz;
+    double Gm = p->G * m[j];
+    ax -= Gm * w * rx / r3; ay -= Gm * w * ry / r3; az -= Gm * w * rz / r3;
+    double dw = dK * rv / (r * ro); /* -d(1 - K)/dt */
+    jx -= Gm * (w * (ux / r3 - 3.0 * rv * rx / r5) - dw * rx / r3);
+    jy -= Gm * (w * (uy / r3 - 3.0 * rv * ry / r5) - dw * ry / r3);
+    jz -= Gm * (w * (uz / r3 - 3.0 * rv * rz / r5) - dw * rz / r3);
+  }
+  acc[0] = ax; acc[1] = ay; acc[2] = az;
+  jerk[0] = jx; jerk[1] = jy; jerk[2] = jz;
+}
+
 void or_hard_acc_jerk(int64_t nc, const double *x, const double *y,
                       const double *z, const double *vx, const double *vy,
                       const double *vz, const double *m, const double *r_out,
                       const or_params *p, int64_t k, double acc[3],
                       double jerk[3]) {
-  /* evaluated with one reciprocal square root per pair and reciprocal
-   * factors (1/r, 1/r_out, 1/(1-gamma)); the formulas are those above */
-  const double i1mg = 1.0 / (1.0 - p->gamma);
-  double ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0;
-  {
-    double r2 = fma(x[k], x[k], fma(y[k], y[k], z[k] * z[k]));
-    double rinv = 1.0 / sqrt(r2);
-    double rinv2 = rinv * rinv;
-    double f = p->G * p->m_star * (rinv2 * rinv);
-    double rv = fma(x[k], vx[k], fma(y[k], vy[k], z[k] * vz[k]));
-    ax -= f * x[k]; ay -= f * y[k]; az -= f * z[k];
-    double c = 3.0 * rv * rinv2;
-    jx -= f * fma(-c, x[k], vx[k]);
-    jy -= f * fma(-c, y[k], vy[k]);
-    jz -= f * fma(-c, z[k], vz[k]);
-  }
-  const double irok = 1.0 / r_out[k];
-  for (int64_t j = 0; j < nc; ++j) {
-    if (j == k) continue;
-    double rx = x[k] - x[j], ry = y[k] - y[j], rz = z[k] - z[j];
-    double ux = vx[k] - vx[j], uy = vy[k] - vy[j], uz = vz[k] - vz[j];
-    double r2 = fma(rx, rx, fma(ry, ry, rz * rz));
-    if (r2 == 0.0) continue;
-    double rinv = 1.0 / sqrt(r2);
-    double r = r2 * rinv;
-    double irot = dmin(irok, 1.0 / r_out[j]); /* = 1 / max(r_out,k, r_out,j) */
-    double yv = r * irot;
-    if (yv >= 1.0) continue;
-    double w = 1.0, dK = 0.0;
-    if (yv > p->gamma) {
-      double xs = (yv - p->gamma) * i1mg;
-      double x2 = xs * xs, x3 = x2 * xs, x4 = x2 * x2, u = 1.0 - xs;
-      w = 1.0 - x4 * (35.0 - 84.0 * xs + 70.0 * x2 - 20.0 * x3);
-      dK = 140.0 * x3 * (u * u * u) * i1mg;
-    }
-    double rinv2 = rinv * rinv;
-    double g3 = p->G * m[j] * (rinv2 * rinv);
-    double f = g3 * w;
-    double rv = fma(rx, ux, fma(ry, uy, rz * uz));
-    ax -= f * rx; ay -= f * ry; az -= f * rz;
-    /* d/dt [w r / r^3] = w v / r^3 - (3 w (r.v)/r^2 + K'(y) (r.v)/(r r_out)) r / r^3 */
-    double c = fma(dK * rv * rinv, irot, 3.0 * w * rv * rinv2);
-    jx -= g3 * fma(-c, rx, w * ux);
-    jy -= g3 * fma(-c, ry, w * uy);
-    jz -= g3 * fma(-c, rz, w * uz);
-  }
-  acc[0] = ax; acc[1] = ay; acc[2] = az;
-  jerk[0] = jx; jerk[1] = jy; jerk[2] = jz;
+  hard_acc_jerk_sets(nc, x, y, z, vx, vy, vz, m, r_out, NULL, NULL, p, k, acc, jerk, NULL);
 }
 
 /* Block time-step quantisation (reading C7): the largest dt_soft / 2^k not   */
@@ -848,77 +904,14 @@ static int quantise_level(double dt_des, double dt_soft, int prev_level,
   return lvl;
 }
 
-/* The step estimates only set a power-of-two step, so they are formed in
- * single precision.  Each derivative is first scaled by an exact power of two
- * s^k, s = 2^e close to the step, so that every term of the estimate has the
- * size of an acceleration squared and nothing overflows FP32. */
-static float norm3f(const double *v, int k) {
-  float a = (float)ldexp(v[0], k), b = (float)ldexp(v[1], k), c = (float)ldexp(v[2], k);
-  return sqrtf(a * a + b * b + c * c);
+static double norm3(const double *v) {
+  return sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
 }
 
-/* Hard force and jerk of member k when some members form composites (row   */
-/* f4, Sec. 2.4.1): a member's hard force leaves out the other members of    */
-/* its own composite (set[j] == set[k]).  With RP given, *partner receives   */
-/* the lowest-index member j outside k's composite that touches k, i.e.      */
-/*   r_kj < f (R_p,k + R_p,j),                                               */
-/* at the positions the force is evaluated at (or -1).  Otherwise the terms  */
-/* and their order are those of or_hard_acc_jerk.                             */
-static void hard_acc_jerk_sets(int64_t nc, const double *x, const double *y,
-                               const double *z, const double *vx, const double *vy,
-                               const double *vz, const double *m, const double *r_out,
-                               const double *RP, const int64_t *set, const or_params *p,
-                               int64_t k, double acc[3], double jerk[3], int64_t *partner) {
-  const double i1mg = 1.0 / (1.0 - p->gamma);
-  double ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0;
-  if (partner) *partner = -1;
-  {
-    double r2 = fma(x[k], x[k], fma(y[k], y[k], z[k] * z[k]));
-    double rinv = 1.0 / sqrt(r2);
-    double rinv2 = rinv * rinv;
-    double f = p->G * p->m_star * (rinv2 * rinv);
-    double rv = fma(x[k], vx[k], fma(y[k], vy[k], z[k] * vz[k]));
-    ax -= f * x[k]; ay -= f * y[k]; az -= f * z[k];
-    double c = 3.0 * rv * rinv2;
-    jx -= f * fma(-c, x[k], vx[k]);
-    jy -= f * fma(-c, y[k], vy[k]);
-    jz -= f * fma(-c, z[k], vz[k]);
-  }
-  const double irok = 1.0 / r_out[k];
-  for (int64_t j = 0; j < nc; ++j) {
-    if (j == k || set[j] == set[k]) continue;
-    double rx = x[k] - x[j], ry = y[k] - y[j], rz = z[k] - z[j];
-    double ux = vx[k] - vx[j], uy = vy[k] - vy[j], uz = vz[k] - vz[j];
-    double r2 = fma(rx, rx, fma(ry, ry, rz * rz));
-    if (RP && partner && *partner < 0) {
-      double sr = p->f_radius * (RP[k] + RP[j]);
-      if (r2 < sr * sr) *partner = j;
-    }
-    if (r2 == 0.0) continue;
-    double rinv = 1.0 / sqrt(r2);
-    double r = r2 * rinv;
-    double irot = dmin(irok, 1.0 / r_out[j]);
-    double yv = r * irot;
-    if (yv >= 1.0) continue;
-    double w = 1.0, dK = 0.0;
-    if (yv > p->gamma) {
-      double xs = (yv - p->gamma) * i1mg;
-      double x2 = xs * xs, x3 = x2 * xs, x4 = x2 * x2, u = 1.0 - xs;
-      w = 1.0 - x4 * (35.0 - 84.0 * xs + 70.0 * x2 - 20.0 * x3);
-      dK = 140.0 * x3 * (u * u * u) * i1mg;
-    }
-    double rinv2 = rinv * rinv;
-    double g3 = p->G * m[j] * (rinv2 * rinv);
-    double f = g3 * w;
-    double rv = fma(rx, ux, fma(ry, uy, rz * uz));
-    ax -= f * rx; ay -= f * ry; az -= f * rz;
-    double c = fma(dK * rv * rinv, irot, 3.0 * w * rv * rinv2);
-    jx -= g3 * fma(-c, rx, w * ux);
-    jy -= g3 * fma(-c, ry, w * uy);
-    jz -= g3 * fma(-c, rz, w * uz);
-  }
-  acc[0] = ax; acc[1] = ay; acc[2] = az;
-  jerk[0] = jx; jerk[1] = jy; jerk[2] = jz;
+/* First step of a member (Sec. 3.1): eta0 |a| / |j|. */
+static double first_step(const double *a, const double *j, double eta0, double dt) {
+  double jn = norm3(j);
+  return jn > 0.0 ? eta0 * norm3(a) / jn : dt;
 }
 
 /* The hard acceleration (and jerk) of a composite is the mass-weighted mean  */
@@ -974,15 +967,13 @@ static double set_energy(int64_t nc, const unsigned char *chg, const int64_t *se
 /* Fourth-order Hermite with block individual time steps over [0, dt] for one */
 /* cluster (Sec. 2.1.2, Makino 1991; Aarseth time steps).  Reading C7:        */
 /*  predictor  x_p = x + v D + a D^2/2 + j D^3/6, v_p = v + a D + j D^2/2;    */
-/*             (Horner form with fused multiply-adds, as are the corrector's */
-/*             sums and the pair term's dot products)                        */
 /*  corrector  a2 = (-6(a0-a1) - D(4 j0 + 2 j1))/D^2,                        */
 /*             a3 = (12(a0-a1) + 6 D (j0 + j1))/D^3,                          */
 /*             x = x_p + a2 D^4/24 + a3 D^5/120, v = v_p + a2 D^3/6 + a3 D^4/24;*/
 /*  new step   sqrt(eta (|a||a2'| + |j|^2)/(|j||a3| + |a2'|^2)), a2' = a2+D a3;*/
 /*  first step eta0 |a|/|j| (each hard step starts afresh, so every member's   */
-/*  first step of the hard step uses eta0).  Both estimates are formed in FP32  */
-/*  (they are quantised to dt / 2^k); state, forces and corrector are FP64.    */
+/*  first step of the hard step uses eta0).  Everything in FP64, each formula  */
+/*  evaluated as written, left to right.                                      */
 /* All members are predicted to each block time; the active ones are        */
 /* evaluated from the predicted state and then corrected together.           */
 /*                                                                           */
@@ -1004,12 +995,15 @@ static double set_energy(int64_t nc, const unsigned char *chg, const int64_t *se
 /*    of the affected members (kinetic, star potential, pair potential with  */
 /*    the cluster) from before to after the replacement.                     */
 /* root_out (nc entries, or NULL) receives for each member the lowest member */
-/* of its composite (itself if none); *e_disp the dissipated energy.         */
+/* of its composite (itself if none); *e_disp the dissipated energy;         */
+/* msteps (nc entries, or NULL) the number of corrector steps of each member.*/
 int or_hermite_cluster(int64_t nc, const int32_t *members, double *X, double *Y,
                        double *Z, double *VX, double *VY, double *VZ,
                        const double *M, const double *RO, const double *RPall,
                        const or_params *p, double dt, int64_t *n_steps,
-                       int32_t *root_out, double *e_disp) {
+                       int32_t *root_out, double *e_disp, int32_t *msteps) {
+  if (msteps)
+    for (int64_t k = 0; k < nc; ++k) msteps[k] = 0;
   const int64_t T = ((int64_t)1) << OR_KMAX;
   const double unit = ldexp(dt, -OR_KMAX);
   const int coll = RPall != NULL && p->f_radius > 0.0;
@@ -1040,18 +1034,17 @@ int or_hermite_cluster(int64_t nc, const int32_t *members, double *X, double *Y,
     hard_acc_jerk_sets(nc, x, y, z, vx, vy, vz, m, ro, RP, set, p, k, a + 3 * k, jk + 3 * k,
                        &partner[k]);
   for (int64_t k = 0; k < nc; ++k) {
-    /* eta0 |a| / |j| = (eta0 |a| / |j s|) s, s = 2^e */
-    int e = ilogb(dt);
-    float an = norm3f(a + 3 * k, 0), jn = norm3f(jk + 3 * k, e);
-    double dtd = jn > 0.0f ? ldexp((double)((float)p->eta0 * an / jn), e) : dt;
     t[k] = 0;
-    lvl[k] = quantise_level(dtd, dt, 0, 0, &underflow);
+    lvl[k] = quantise_level(first_step(a + 3 * k, jk + 3 * k, p->eta0, dt), dt, 0, 0,
+                            &underflow);
   }
   /* at t = 0 the block-time state is the initial state */
   memcpy(px, x, sizeof(double) * nc * 6);
   int64_t steps = 0, blocks = 0, tn = 0;
   int timeout = 0;
   for (;;) {
+    /* a step below dt / 2^40 ends the cluster's integration (an error) */
+    if (underflow) break;
     /* ---- collisions found by this evaluation (all members at tn) ---- */
     int any = 0;
     for (int64_t k = 0; k < nc; ++k) any |= partner[k] >= 0;
@@ -1102,12 +1095,11 @@ int or_hermite_cluster(int64_t nc, const int32_t *members, double *X, double *Y,
       average_sets(nc, set, chg, m, a, jk);
       for (int64_t k = 0; k < nc; ++k) {
         if (!chg[k]) continue;
-        int e = ilogb(dt);
-        float an = norm3f(a + 3 * k, 0), jn = norm3f(jk + 3 * k, e);
-        double dtd = jn > 0.0f ? ldexp((double)((float)p->eta0 * an / jn), e) : dt;
-        lvl[k] = quantise_level(dtd, dt, 0, tn, &underflow);
+        lvl[k] = quantise_level(first_step(a + 3 * k, jk + 3 * k, p->eta0, dt), dt, 0, tn,
+                                &underflow);
       }
       for (int64_t k = 0; k < nc; ++k) partner[k] = -1;
+      if (underflow) break;
     }
     /* ---- next block time ---- */
     if (++blocks > OR_BLOCK_LIMIT) { timeout = 1; break; }
@@ -1120,16 +1112,16 @@ int or_hermite_cluster(int64_t nc, const int32_t *members, double *X, double *Y,
     for (int64_t k = 0; k < nc; ++k) if (t[k] < tmin) tmin = t[k];
     if (tmin >= T) break;
     for (int64_t k = 0; k < nc; ++k) {
+      /* predictor to the block time (reading C7) */
       double D = (double)(tn - t[k]) * unit;
       const double *ak = a + 3 * k, *jj = jk + 3 * k;
-      /* Horner form with fused multiply-adds: x + D (v + D (a/2 + D j/6)),
-       * v + D (a + D j/2) */
-      px[k] = fma(fma(fma(jj[0] * (1.0 / 6.0), D, ak[0] * 0.5), D, vx[k]), D, x[k]);
-      py[k] = fma(fma(fma(jj[1] * (1.0 / 6.0), D, ak[1] * 0.5), D, vy[k]), D, y[k]);
-      pz[k] = fma(fma(fma(jj[2] * (1.0 / 6.0), D, ak[2] * 0.5), D, vz[k]), D, z[k]);
-      pvx[k] = fma(fma(jj[0] * 0.5, D, ak[0]), D, vx[k]);
-      pvy[k] = fma(fma(jj[1] * 0.5, D, ak[1]), D, vy[k]);
-      pvz[k] = fma(fma(jj[2] * 0.5, D, ak[2]), D, vz[k]);
+      double D2 = D * D, D3 = D2 * D;
+      px[k] = x[k] + vx[k] * D + ak[0] * D2 / 2.0 + jj[0] * D3 / 6.0;
+      py[k] = y[k] + vy[k] * D + ak[1] * D2 / 2.0 + jj[1] * D3 / 6.0;
+      pz[k] = z[k] + vz[k] * D + ak[2] * D2 / 2.0 + jj[2] * D3 / 6.0;
+      pvx[k] = vx[k] + ak[0] * D + jj[0] * D2 / 2.0;
+      pvy[k] = vy[k] + ak[1] * D + jj[1] * D2 / 2.0;
+      pvz[k] = vz[k] + ak[2] * D + jj[2] * D2 / 2.0;
       act[k] = (t[k] + (T >> lvl[k]) == tn);
     }
     for (int64_t k = 0; k < nc; ++k)
@@ -1139,34 +1131,32 @@ int or_hermite_cluster(int64_t nc, const int32_t *members, double *X, double *Y,
     average_sets(nc, set, act, m, a1, j1);
     for (int64_t k = 0; k < nc; ++k) {
       if (!act[k]) continue;
+      /* corrector (Makino & Aarseth 1992, reading C7) */
       double D = (double)(T >> lvl[k]) * unit;
       double D2 = D * D, D3 = D2 * D, D4 = D3 * D, D5 = D4 * D;
-      double iD = 1.0 / D, iD2 = iD * iD, iD3 = iD2 * iD;
       double A2[3], A3[3], A2e[3];
       for (int c = 0; c < 3; ++c) {
-        double da = a[3 * k + c] - a1[3 * k + c];
-        A2[c] = fma(-D, fma(2.0, j1[3 * k + c], 4.0 * jk[3 * k + c]), -6.0 * da) * iD2;
-        A3[c] = fma(6.0 * D, jk[3 * k + c] + j1[3 * k + c], 12.0 * da) * iD3;
-        A2e[c] = fma(D, A3[c], A2[c]);
+        double a0 = a[3 * k + c], a1c = a1[3 * k + c];
+        double j0 = jk[3 * k + c], j1c = j1[3 * k + c];
+        A2[c] = (-6.0 * (a0 - a1c) - D * (4.0 * j0 + 2.0 * j1c)) / D2;
+        A3[c] = (12.0 * (a0 - a1c) + 6.0 * D * (j0 + j1c)) / D3;
+        A2e[c] = A2[c] + D * A3[c];  /* second derivative at the end of the step */
       }
-      /* x_p + a2 D^4/24 + a3 D^5/120, v_p + a2 D^3/6 + a3 D^4/24, fused */
-      const double c3 = D3 * (1.0 / 6.0), c4 = D4 * (1.0 / 24.0), c5 = D5 * (1.0 / 120.0);
-      x[k] = fma(A3[0], c5, fma(A2[0], c4, px[k]));
-      y[k] = fma(A3[1], c5, fma(A2[1], c4, py[k]));
-      z[k] = fma(A3[2], c5, fma(A2[2], c4, pz[k]));
-      vx[k] = fma(A3[0], c4, fma(A2[0], c3, pvx[k]));
-      vy[k] = fma(A3[1], c4, fma(A2[1], c3, pvy[k]));
-      vz[k] = fma(A3[2], c4, fma(A2[2], c3, pvz[k]));
+      x[k] = px[k] + A2[0] * D4 / 24.0 + A3[0] * D5 / 120.0;
+      y[k] = py[k] + A2[1] * D4 / 24.0 + A3[1] * D5 / 120.0;
+      z[k] = pz[k] + A2[2] * D4 / 24.0 + A3[2] * D5 / 120.0;
+      vx[k] = pvx[k] + A2[0] * D3 / 6.0 + A3[0] * D4 / 24.0;
+      vy[k] = pvy[k] + A2[1] * D3 / 6.0 + A3[1] * D4 / 24.0;
+      vz[k] = pvz[k] + A2[2] * D3 / 6.0 + A3[2] * D4 / 24.0;
       for (int c = 0; c < 3; ++c) { a[3 * k + c] = a1[3 * k + c]; jk[3 * k + c] = j1[3 * k + c]; }
-      /* Aarseth step with j, a2, a3 scaled by s, s^2, s^3 (s = 2^e ~ D):
-       * dt = sqrt(eta num_s / den_s) s */
-      int e = ilogb(D);
-      float an = norm3f(a + 3 * k, 0), jn = norm3f(jk + 3 * k, e);
-      float a2n = norm3f(A2e, 2 * e), a3n = norm3f(A3, 3 * e);
-      float num = an * a2n + jn * jn, den = jn * a3n + a2n * a2n;
-      double dtd = den > 0.0f ? ldexp((double)sqrtf((float)p->eta * num / den), e) : dt;
+      /* Aarseth step sqrt(eta (|a| |a2'| + |j|^2) / (|j| |a3| + |a2'|^2)) */
+      double an = norm3(a + 3 * k), jn = norm3(jk + 3 * k);
+      double a2n = norm3(A2e), a3n = norm3(A3);
+      double num = an * a2n + jn * jn, den = jn * a3n + a2n * a2n;
+      double dtd = den > 0.0 ? sqrt(p->eta * num / den) : dt;
       t[k] = tn;
       lvl[k] = quantise_level(dtd, dt, lvl[k], tn, &underflow);
+      if (msteps) ++msteps[k];
       ++steps;
     }
   }
@@ -1278,10 +1268,13 @@ int or_hard_step(int64_t n, double *x, double *y, double *z, double *vx,
                  const double *RP, const or_params *p, double dt, int64_t n_single,
                  const int32_t *singles, int64_t n_clusters,
                  const int64_t *cl_off, const int32_t *cl_mem,
-                 int64_t *n_hermite_steps, int32_t *comp_root, double *e_hard) {
+                 int64_t *n_hermite_steps, int32_t *comp_root, double *e_hard,
+                 int32_t *member_steps) {
   int err = or_kepler_drift(n_single, singles, x, y, z, vx, vy, vz, dt, p->G * p->m_star);
   if (comp_root)
     for (int64_t i = 0; i < n; ++i) comp_root[i] = -1;
+  if (member_steps)
+    for (int64_t i = 0; i < n; ++i) member_steps[i] = 0;
   double *ec = (double *)calloc(n_clusters > 0 ? n_clusters : 1, sizeof(double));
   int64_t steps = 0;
   int herr = 0;
@@ -1290,10 +1283,12 @@ int or_hard_step(int64_t n, double *x, double *y, double *z, double *vx,
     int64_t ns = 0;
     const int64_t nc = cl_off[c + 1] - cl_off[c];
     const int32_t *mem = cl_mem + cl_off[c];
-    int32_t *root = (int32_t *)malloc(sizeof(int32_t) * 2 * nc);
-    int32_t *cnt = root + nc;
+    int32_t *root = (int32_t *)malloc(sizeof(int32_t) * 3 * nc);
+    int32_t *cnt = root + nc, *ms = cnt + nc;
     int e = or_hermite_cluster(nc, mem, x, y, z, vx, vy, vz, m, r_out, RP, p, dt, &ns, root,
-                               &ec[c]);
+                               &ec[c], ms);
+    if (member_steps)
+      for (int64_t k = 0; k < nc; ++k) member_steps[mem[k]] = ms[k];
     if (comp_root) {
       /* members of composites of two or more: the caller index of the lowest */
       for (int64_t k = 0; k < nc; ++k) cnt[k] = 0;

@@ -66,6 +66,14 @@ int or_tree_soft(int64_t n, const double *x, const double *y, const double *z,
                  int64_t cand_cap, int32_t *cand_i, int32_t *cand_j,
                  int64_t *n_cand, int64_t tree_stats[4]);
 
+/* the Barnes-Hut threshold of a level, ceil((2^(22-level))^2 / theta^2)     */
+/* (half cell units, exact), and the node-opening test of reading C4 for a  */
+/* group and a node given by their grid boxes (1: open)                     */
+int64_t or_bh_threshold(double theta, int level);
+int or_mac_open(double theta, int level, const int64_t node_c2[3],
+                const int64_t node_qlo[3], const int64_t node_qhi[3], int64_t node_R,
+                const int64_t grp_qlo[3], const int64_t grp_qhi[3], int64_t grp_R);
+
 /* multipole moments of a particle set and their field at a point (Barnes-Hut
  * node term, monopole + traceless quadrupole) */
 void or_node_moments(int64_t n, const double *x, const double *y,
@@ -110,7 +118,7 @@ int or_hermite_cluster(int64_t nc, const int32_t *members, double *x, double *y,
                        double *z, double *vx, double *vy, double *vz,
                        const double *m, const double *r_out, const double *r_phys,
                        const or_params *p, double dt, int64_t *n_steps,
-                       int32_t *root_out, double *e_disp);
+                       int32_t *root_out, double *e_disp, int32_t *member_steps);
 
 /* ---- Kepler drift of isolated particles ----------------------------------- */
 int or_kepler_drift(int64_t n, const int32_t *idx, double *x, double *y,
@@ -120,13 +128,15 @@ int or_kepler_drift(int64_t n, const int32_t *idx, double *x, double *y,
 /* ---- Hermite step and Kepler drift together: the hard part of a soft step - */
 /* r_phys: physical radii (NULL or f_radius == 0: no collisions); comp_root:   */
 /* n entries (or NULL), lowest member of each particle's composite or -1;     */
-/* e_hard: energy dissipated by the collisions.                               */
+/* e_hard: energy dissipated by the collisions; member_steps: n entries (or  */
+/* NULL), the corrector steps each cluster member took (0 for singles).      */
 int or_hard_step(int64_t n, double *x, double *y, double *z, double *vx,
                  double *vy, double *vz, const double *m, const double *r_out,
                  const double *r_phys, const or_params *p, double dt,
                  int64_t n_single, const int32_t *singles, int64_t n_clusters,
                  const int64_t *cl_off, const int32_t *cl_mem,
-                 int64_t *n_hermite_steps, int32_t *comp_root, double *e_hard);
+                 int64_t *n_hermite_steps, int32_t *comp_root, double *e_hard,
+                 int32_t *member_steps);
 
 /* ---- composite kick and merge (Sec. 2.4.1, procedure step 9) -------------- */
 double or_kick_composites(int64_t n, double *vx, double *vy, double *vz,

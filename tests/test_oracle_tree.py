@@ -1,11 +1,16 @@
 """Pins of the oracle's Morton keys, octree walk and soft force.
 
-Pinned against: a bit-by-bit interleave written out in Python (keys), the
+Pinned against: a bit-by-bit interleave of the exact cell (rational
+arithmetic) written out in Python (keys), the Barnes-Hut and reach opening
+tests evaluated in exact rational arithmetic, the
 O(N^2) direct changeover sum (theta = 0 must reduce to it), plain Newtonian
 direct summation (r_out -> 0), Newton's third law, the convergence order of
 the quadrupole expansion, and brute-force candidate pairs (the cut-off
 opening rule must reach every pair within the search radius).
 """
+import math
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -17,6 +22,22 @@ def _small(n=600, seed=11):
     return s
 
 
+def _interleave(q):
+    k = 0
+    for b in range(20, -1, -1):          # most significant level first
+        for a in range(3):
+            k = (k << 1) | ((q[a] >> b) & 1)
+    return k
+
+
+def _exact_cell(v, lo, L):
+    """floor((v - lo) / u), u = L / 2^21, with v - lo rounded to FP64 and the
+    quotient taken in exact rational arithmetic; clamped to [0, 2^21)."""
+    d = Fraction(float(np.float64(v) - np.float64(lo)))
+    q = math.floor(d / (Fraction(float(L)) / 2**21))
+    return min(max(q, 0), 2**21 - 1)
+
+
 def test_morton_keys_bitwise(orc):
     rng = np.random.default_rng(3)
     s = {k: rng.uniform(-2, 3, 40) for k in ("x", "y", "z")}
@@ -25,22 +46,103 @@ def test_morton_keys_bitwise(orc):
     lo = np.array([s["x"].min(), s["y"].min(), s["z"].min()])
     L = max(s["x"].max() - lo[0], s["y"].max() - lo[1], s["z"].max() - lo[2])
     assert np.allclose(box, [*lo, L], rtol=0, atol=0)
-    S = 2.0**21 / L
     for i in range(40):
-        q = []
-        for a, c in enumerate(("x", "y", "z")):
-            t = int(np.floor((s[c][i] - lo[a]) * S))
-            q.append(min(max(t, 0), 2**21 - 1))
-            # the position lies in its cell [q u, (q + 1) u) up to far less
-            # than the two-cell margin of the cut-off reach test
-            u = L / 2**21
-            off = (s[c][i] - lo[a]) / u - q[-1]
-            assert -1e-6 < off < 1 + 1e-6
-        k = 0
-        for b in range(20, -1, -1):          # most significant level first
-            for a in range(3):
-                k = (k << 1) | ((q[a] >> b) & 1)
-        assert int(key[i]) == k
+        q = [_exact_cell(s[c][i], lo[a], L) for a, c in enumerate(("x", "y", "z"))]
+        assert int(key[i]) == _interleave(q)
+
+
+def test_morton_keys_on_cell_boundaries(orc):
+    """Coordinates on cell boundaries and one ulp either side: the cell is the
+    exact floor of (v - lo) / u, also where the rounded quotient reaches the
+    next integer from below (such cases are checked to occur)."""
+    rng = np.random.default_rng(17)
+    n = 600
+    x = np.empty(n)
+    x[0], x[1] = -1.3, 1.7371234567   # the box: lo = x[0], L = x[1] - x[0] (the widest axis)
+    u = (x[1] - x[0]) / 2**21
+    ks = rng.integers(1, 2**21 - 1, (n - 2) // 3)
+    base = x[0] + ks * u
+    x[2:2 + len(ks)] = np.nextafter(base, -np.inf)
+    x[2 + len(ks):2 + 2 * len(ks)] = base
+    x[2 + 2 * len(ks):2 + 3 * len(ks)] = np.nextafter(base, np.inf)
+    x[2 + 3 * len(ks):] = 0.1
+    s = {"x": x, "y": np.zeros(n), "z": np.zeros(n)}
+    key, box = orc.morton_keys(s)
+    lo, L = box[0], box[3]
+    naive_differs = 0
+    for i in range(n):
+        q = _exact_cell(x[i], lo, L)
+        naive = min(max(math.floor((x[i] - lo) / (L / 2**21)), 0), 2**21 - 1)
+        naive_differs += naive != q
+        assert int(key[i]) == _interleave([q, 0, 0]), i
+    assert naive_differs > 10
+
+
+def test_bh_threshold_exact(orc):
+    """The Barnes-Hut threshold ceil(side^2 / theta^2) of every level equals
+    the exact rational value, for the paper's theta and for random theta
+    (where a rounded FP64 quotient is off in about one case in a thousand)."""
+    rng = np.random.default_rng(23)
+    thetas = [0.1, 0.5, 1.0, 0.3, 0.7] + list(rng.uniform(0.05, 1.5, 300))
+    for th in thetas:
+        for lvl in range(22):
+            side2 = Fraction(4) ** (22 - lvl)
+            want = math.ceil(side2 / Fraction(float(th)) ** 2)
+            assert orc.bh_threshold(th, lvl) == min(want, 2**62), (th, lvl)
+    assert orc.bh_threshold(0.0, 5) == 2**62        # theta = 0 opens every node
+
+
+@pytest.mark.parametrize("theta", [0.1, 0.5, 1.0])
+def test_mac_barnes_hut_exact(orc, theta):
+    """The node-opening test against side^2 > theta^2 d^2 in exact rational
+    arithmetic: node cell side s (half units 2s), the node's cell centre, the
+    group's cell box, d the point-box distance; boxes are built at squared
+    distances just below, at and just above side^2 / theta^2 along random
+    directions.  The reach term is switched off (R = 0, far-apart boxes)."""
+    rng = np.random.default_rng(int(theta * 100) + 1)
+    checked = opened = 0
+    for lvl in (3, 8, 12, 17, 21):
+        side = 2 ** (22 - lvl)                      # half cell units
+        thr = Fraction(side) ** 2 / Fraction(theta) ** 2
+        for _ in range(40):
+            # a group box of a few cells, and a node centre at a chosen distance
+            glo = rng.integers(2**19, 2**20, 3)
+            ghi = glo + rng.integers(0, 8, 3)
+            lo2, hi2 = 2 * glo, 2 * ghi + 2            # the group's box in half units
+            dirn = rng.normal(size=3)
+            dirn = np.abs(dirn) / np.linalg.norm(dirn)
+            target = float(thr) * rng.choice([0.999, 1.0, 1.001])
+            dvec = np.floor(dirn * math.sqrt(target)).astype(np.int64)
+            for bump in (0, 1):
+                dv = dvec + bump
+                c2 = hi2 + dv                          # centre beyond the box's upper faces
+                node_q = (c2 // 2 - 1, c2 // 2)        # node cells far from the group
+                d2 = int((dv * dv).sum())
+                want = Fraction(side) ** 2 > Fraction(theta) ** 2 * d2
+                got = orc.mac_open(theta, lvl, c2, node_q[0], node_q[1], 0, glo, ghi, 0)
+                assert got == want, (lvl, d2, float(thr))
+                checked += 1
+                opened += got
+    assert 0 < opened < checked
+
+
+def test_mac_reach_term_exact(orc):
+    """The cut-off reach term: per-axis gap g (grid cells less two, never
+    negative) between the node's and the group's cell boxes, open iff
+    g^2 < max(R_group, R_node)^2; theta large so that Barnes-Hut never opens."""
+    rng = np.random.default_rng(31)
+    for _ in range(300):
+        glo = rng.integers(0, 2**20, 3)
+        ghi = glo + rng.integers(0, 50, 3)
+        gap = rng.integers(0, 60, 3)
+        nlo = ghi + 2 + gap
+        nhi = nlo + rng.integers(0, 50, 3)
+        Rg, Rn = (int(v) for v in rng.integers(0, 120, 2))
+        lvl = 21
+        c2 = nlo + nhi + 1                              # any centre: theta makes BH close
+        g2 = int((gap * gap).sum())
+        want = g2 < max(Rg, Rn) ** 2
+        assert orc.mac_open(1e6, lvl, c2, nlo, nhi, Rn, glo, ghi, Rg) == want
 
 
 @pytest.mark.parametrize("group_size", [0, 32, 64])
