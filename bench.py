@@ -64,8 +64,9 @@ def parse():
                     help="collision radius factor f (0: no collisions)")
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-targets", type=int, default=16384,
-                    help="targets of the CPU oracle's timed walk sample")
+    ap.add_argument("--cpu-steps", type=int, default=8,
+                    help="most whole oracle soft steps timed for the CPU baseline "
+                         "(stops after ~20 s of stepping)")
     ap.add_argument("--adjoint", action="store_true",
                     help="time one gradient of the 32-step soft KDK rollout at N=1e4")
     ap.add_argument("--adjoint-n", type=int, default=10_000)
@@ -181,34 +182,44 @@ def allsum(dist, v):
 
 
 # ------------------------------------------------------------- CPU oracle ----
-def oracle_step_estimate(s, n_targets, seed=7, group_size=64):
-    """The CPU oracle on a bounded sample of the same workload.
-
-    Timed: the full tree build at N (keys, sort, octree, moments), the walk for
-    a random sample of targets (scaled to all N), and the Kepler drift of all
-    particles.  Returns (interactions per step, seconds per step, info)."""
+def oracle_steps(s, k_steps, warmup=0, group_size=64, f_radius=1.0, budget_s=None):
+    """The CPU oracle stepping the same workload: after the initial force
+    (untimed), whole soft steps (kick, Hermite clusters + Kepler drift with
+    collisions, cut-offs held, tree build, tree walk, neighbour filter,
+    clusters, kick, and the merge with new radii, tree, walk and neighbours
+    when bodies collided); `warmup` steps untimed, then up to k_steps timed
+    ones, stopping early once budget_s seconds of timed stepping have passed
+    (at least one step).  Returns (pair interactions, seconds, timed steps,
+    info)."""
     from oracle import oracle as O
-    p = O.Params(theta=0.5, group_size=group_size)
+    from paper_2007_15432_gb300 import disks
+    s = disks.copy_state(s)
+    rp = disks.physical_radius(s["m"])
+    p = O.Params(theta=0.5, eta=0.01, eta0=0.001, group_size=group_size, f_radius=f_radius)
     ro, rs, _, _ = O.cutoffs(s, p)
-    n = len(s["m"])
-    rng = np.random.default_rng(seed)
-    tg = rng.choice(n, size=min(n_targets, n), replace=False)
-    t0 = time.perf_counter()
-    O.tree_soft(s, ro, rs, p, targets=np.array([0]), cand_cap=1 << 20)
-    t_tree = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    res = O.tree_soft(s, ro, rs, p, targets=tg, cand_cap=1 << 22)
-    t_walk = time.perf_counter() - t0 - t_tree
-    scale = n / len(tg)
-    inter = (res.n_pp + res.n_pnode) * scale
-    sk = {k: np.array(s[k], copy=True) for k in ("x", "y", "z", "vx", "vy", "vz", "m")}
-    t0 = time.perf_counter()
-    O.kepler_drift(sk, 1.0 / 64, 1.0)
-    t_kep = time.perf_counter() - t0
-    step = t_tree + max(t_walk, 0.0) * scale + t_kep
-    info = dict(t_tree_s=t_tree, t_walk_sample_s=t_walk, t_kepler_s=t_kep,
-                sample_targets=len(tg), threads=O.num_threads())
-    return inter, step, info
+    acc, cl, _ = O.initial_force(s, ro, rs, p)
+    inter, secs, done = 0, 0.0, 0
+    for k in range(warmup + k_steps):
+        t0 = time.perf_counter()
+        acc, cl, info = O.soft_step(s, ro, rs, p, acc, cl, r_phys=rp)
+        dt = time.perf_counter() - t0
+        if info["merged"]:
+            rp, ro, rs = info["r_phys"], info["r_out"], info["r_search"]
+        if k < warmup:
+            continue
+        secs += dt
+        inter += info["n_pp"] + info["n_pnode"]
+        done += 1
+        if budget_s is not None and secs >= budget_s:
+            break
+    return inter, secs, done, dict(threads=O.num_threads())
+
+
+def _oracle_sample_text(n, done):
+    return (f"{done} whole oracle soft steps of the N={n} workload (kick, Hermite clusters "
+            "and Kepler drift with collisions, tree build, tree walk, neighbour filter, "
+            "clusters, kick, merges with new radii/force/neighbours), each timed; "
+            "initial force untimed")
 
 
 def run_reference(args):
@@ -218,26 +229,22 @@ def run_reference(args):
     s = workload(args.n)
     from oracle import oracle as O
     O.build()
-    times, inter = [], 0.0
-    for k in range(args.warmup + args.steps):
-        i, t, info = oracle_step_estimate(s, args.cpu_targets, seed=100 + k,
-                                          group_size=args.group_size)
-        if k >= args.warmup:
-            times.append(t)
-            inter += i
-    tot = float(np.sum(times))
-    value = inter / tot
-    sample = (f"per step: oracle tree build at N={args.n}, walk of {info['sample_targets']} "
-              f"random targets scaled by N/targets, Kepler drift of all N")
-    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
-                warmup=args.warmup, ms_per_step=1e3 * tot / args.steps, higher_is_better=True,
+    t_wall = time.perf_counter()
+    # warm-up steps are stepped but not timed; then args.steps timed steps
+    inter_t, secs_t, done_t, info = oracle_steps(s, args.steps, warmup=args.warmup,
+                                                 group_size=args.group_size,
+                                                 f_radius=args.f_radius)
+    value = inter_t / secs_t
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=done_t,
+                warmup=args.warmup, ms_per_step=1e3 * secs_t / done_t, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                 impl="reference",
                 config=dict(workload=workload_name(args.n), n=args.n, group_size=args.group_size,
                             precision="fp64 (CPU oracle)"),
                 cpu_baseline=dict(value=value, unit=UNIT, cores=info["threads"], kind="oracle",
-                                  sample=sample),
-                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+                                  sample=_oracle_sample_text(args.n, done_t)),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0),
+                wall_s=time.perf_counter() - t_wall)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -391,12 +398,11 @@ def run_ours(args):
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        i_cpu, t_cpu, info = oracle_step_estimate(workload(args.n), args.cpu_targets,
-                                                   group_size=args.group_size)
+        i_cpu, t_cpu, done, info = oracle_steps(workload(args.n), args.cpu_steps,
+                                                group_size=args.group_size,
+                                                f_radius=args.f_radius, budget_s=20.0)
         cpu = dict(value=i_cpu / t_cpu, unit=UNIT, cores=info["threads"], kind="oracle",
-                   sample=(f"oracle tree build at N={args.n} + walk of {info['sample_targets']} "
-                           f"random targets scaled by N/targets + Kepler drift of all N; "
-                           f"{t_cpu:.2f} s per estimated step"))
+                   sample=_oracle_sample_text(args.n, done) + f"; {t_cpu / done:.2f} s per step")
     achieved = flops_per_launch / walk_s / 1e12
     line = dict(
         metric=METRIC, value=tot_inter / tot_elapsed, unit=UNIT, n_gpus=world, steps=K,

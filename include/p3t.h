@@ -181,12 +181,14 @@ int p3t_cutoffs(p3t_ctx *ctx, p3t_particles *p, void *stream);
  * memory budget), or a latency-critical loop where the synchronisation
  * cudaMalloc and cudaFree may imply would stall other work.  Such callers
  * cannot create a context (p3t_create allocates) but can call this.
- *  - Same results as p3t_cutoffs for the same parameters and particles (the
- *    radial-bin sums are accumulated in a different order: a few ulp).
+ *  - Same results as p3t_cutoffs for the same parameters and particles to a
+ *    few ulp: the radial-bin sums of |u|^2 are exact 128-bit fixed-point sums
+ *    of terms cut to multiples of 2^-88 (|u|^2 below 2^40), so every run gives
+ *    the same bits, but not p3t_cutoffs' FP64 sums.
  *  - Runs on the CURRENT CUDA device; all particle pointers must be on it.
  *    p and *p are host memory; the arrays they point to are device memory
  *    owned by the caller (inputs x..m are read, r_out and r_search written).
- *  - Scratch: a fixed 65,552-byte array in device memory that every GPU
+ *  - Scratch: a fixed 98,320-byte array in device memory that every GPU
  *    loading the library holds until the process exits; at most 4096 radial
  *    bins (prm->vran_bins > 4096 returns P3T_ERR_INVALID; the automatic choice
  *    is at most 1024).  Each call clears what it uses before use.
@@ -358,6 +360,29 @@ int p3t_energy(p3t_ctx *ctx, const p3t_particles *p, double *out, void *stream);
 int p3t_copy_clusters(p3t_ctx *ctx, const p3t_clusters *cl, int64_t n,
                       int32_t *label, int32_t *singles, int64_t *cl_off,
                       int32_t *cl_mem, int64_t *counts, void *stream);
+
+/* Limits of the bounded device loops and a per-member record of the
+ * Hermite block steps (the paper has no counterpart: diagnostics).
+ *  - hermite_block_limit: block times one cluster may take in one
+ *    p3t_hard_step; a cluster that needs more stops where it is and
+ *    P3T_ERR_TIMEOUT is recorded.  0 selects the default, 2^24.
+ *  - scan_poll_limit: polls a tile of the library's single-pass scans makes
+ *    for its predecessors' sums before it gives up (P3T_ERR_TIMEOUT; the
+ *    scan's result is then invalid).  0 selects the default, 2^22.
+ *  - hermite_steps: NULL, or a device int32[n] (caller order) into which
+ *    every later p3t_hard_step writes, for each member of a cluster of >= 2,
+ *    the number of corrector steps the member took; entries of isolated
+ *    particles are left as they are.  It must stay valid while it is set and
+ *    hold n entries for every later hard step.
+ * Host call, no device work; takes effect for work enqueued after it and
+ * holds until the next call.  P3T_ERR_INVALID for a NULL argument or a
+ * negative limit. */
+typedef struct {
+  int64_t hermite_block_limit;
+  int64_t scan_poll_limit;
+  int32_t *hermite_steps;
+} p3t_diag;
+int p3t_set_diag(p3t_ctx *ctx, const p3t_diag *d);
 
 /* Synchronises the context's device, returns the first device-side error
  * recorded since the last call (or 0) and clears it.  *required (may be NULL)

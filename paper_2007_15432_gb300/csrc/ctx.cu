@@ -466,6 +466,14 @@ int p3t_copy_clusters(p3t_ctx *c, const p3t_clusters *cl, int64_t n, int32_t *la
   return P3T_OK;
 }
 
+int p3t_set_diag(p3t_ctx *c, const p3t_diag *d) {
+  if (!c || !d || d->hermite_block_limit < 0 || d->scan_poll_limit < 0) return P3T_ERR_INVALID;
+  c->hermite_limit = d->hermite_block_limit > 0 ? d->hermite_block_limit : (int64_t)1 << 24;
+  c->poll_limit = d->scan_poll_limit > 0 ? d->scan_poll_limit : (int64_t)1 << 22;
+  c->hermite_rec = d->hermite_steps;
+  return P3T_OK;
+}
+
 int p3t_status(p3t_ctx *c, int64_t *required) {
   if (!c) return P3T_ERR_INVALID;
   DeviceGuard g(c->device);

@@ -10,7 +10,6 @@
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int64_t kHermiteIterLimit = 1 << 24;  // block steps per cluster
 
 // ---- soft kick (procedure steps 3 and 8) ------------------------------------
 // Members of a composite formed by the last hard step (Sec. 2.4.1;
@@ -421,7 +420,7 @@ struct HCtl {  // per-block control, shared memory
   int64_t red[2][4];
   int32_t wcount[4];
   int64_t cluster;
-  int nact, any, ncomp;
+  int nact, any, ncomp, stop;
   double edisp;
 };
 
@@ -851,9 +850,11 @@ __device__ void integrate_cluster(const V &S, HCtl &C, double (*Tb)[6], int64_t 
                                   const int32_t *cl_mem, const p3t_particles &p,
                                   const p3t_params &prm, double dt, bool coll,
                                   const CollOut &co, unsigned long long &steps,
-                                  bool &underflow, DevStatus *st) {
+                                  bool &underflow, DevStatus *st, int64_t iter_limit,
+                                  int32_t *rec) {
   const int tid = threadIdx.x;
   const int item = (tid & 31) * (NT / 32) + (tid >> 5);  // consecutive items -> different warps
+  bool uf = false;  // a step of this cluster fell below dt / 2^40
   const int64_t T = ((int64_t)1) << P3T_KMAX;
   const double unit = ldexp(dt, -P3T_KMAX);
   const double idt = 1.0 / dt;
@@ -876,8 +877,9 @@ __device__ void integrate_cluster(const V &S, HCtl &C, double (*Tb)[6], int64_t 
     S.rp(k) = coll ? p.r_phys[i] : 0.0;
     S.set(k) = k;
     S.partner(k) = kNone;
+    if (rec) rec[i] = 0;
   }
-  if (tid == 0) { C.any = 0; C.ncomp = 0; C.edisp = 0.0; }
+  if (tid == 0) { C.any = 0; C.ncomp = 0; C.stop = 0; C.edisp = 0.0; }
   __syncthreads();
   // initial forces of every member (the block-time state is the initial
   // state), first steps
@@ -886,12 +888,17 @@ __device__ void integrate_cluster(const V &S, HCtl &C, double (*Tb)[6], int64_t 
   for (int k = item; k < nc; k += NT) {
     for (int q = 0; q < 3; ++q) { S.a(q, k) = S.a1(q, k); S.j(q, k) = S.j1(q, k); }
     S.t(k) = 0;
-    S.lvl(k) = first_level(S, k, prm, dt, 0, underflow);
+    S.lvl(k) = first_level(S, k, prm, dt, 0, uf);
     if (S.partner(k) != kNone) C.any = 1;
   }
+  if (uf) C.stop = 1;
   __syncthreads();
   int64_t tn = 0, iter = 0;
   for (;;) {
+    // a step below dt / 2^40 ends the cluster's integration (the error is
+    // recorded when the block finishes): every thread reads the flag after
+    // the barrier that follows its last write
+    if (C.stop) break;
     if (C.any) {
       // collisions found by the last evaluation: every member's state at tn
       for (int k = item; k < nc; k += NT)
@@ -905,12 +912,14 @@ __device__ void integrate_cluster(const V &S, HCtl &C, double (*Tb)[6], int64_t 
       for (int b = item; b < nact; b += NT) {
         const int k = S.act(b);
         for (int q = 0; q < 3; ++q) { S.a(q, k) = S.a1(q, k); S.j(q, k) = S.j1(q, k); }
-        S.lvl(k) = first_level(S, k, prm, dt, tn, underflow);
+        S.lvl(k) = first_level(S, k, prm, dt, tn, uf);
       }
       for (int k = item; k < nc; k += NT) S.partner(k) = kNone;
+      if (uf) C.stop = 1;
       __syncthreads();
       if (tid == 0) C.any = 0;
       __syncthreads();
+      if (C.stop) break;
     }
     int64_t e_min = T, t_min = T;
     for (int k = tid; k < nc; k += NT) {
@@ -922,7 +931,7 @@ __device__ void integrate_cluster(const V &S, HCtl &C, double (*Tb)[6], int64_t 
     tn = e_min;
     const int64_t tmin = t_min;
     if (tmin >= T) break;
-    if (++iter > kHermiteIterLimit) {
+    if (++iter > iter_limit) {
       if (tid == 0) dev_fail(st, P3T_ERR_TIMEOUT, 61, 0);
       break;
     }
@@ -975,9 +984,11 @@ __device__ void integrate_cluster(const V &S, HCtl &C, double (*Tb)[6], int64_t 
       const double dtd =
           den > 0.0f ? ldexp_fast(f2d_exact(sqrtf((float)prm.eta * num / den)), e) : dt;
       S.t(k) = tn;
-      S.lvl(k) = quantise_level(dtd, dt, S.lvl(k), tn, underflow);
+      S.lvl(k) = quantise_level(dtd, dt, S.lvl(k), tn, uf);
       if (S.partner(k) != kNone) C.any = 1;
+      if (rec) rec[cl_mem[off + k]] += 1;
     }
+    if (uf) C.stop = 1;
     if (tid == 0) steps += (unsigned long long)nact;
     __syncthreads();
   }
@@ -987,6 +998,7 @@ __device__ void integrate_cluster(const V &S, HCtl &C, double (*Tb)[6], int64_t 
     p.vx[i] = S.v(0, k); p.vy[i] = S.v(1, k); p.vz[i] = S.v(2, k);
   }
   if (tid == 0 && C.ncomp) emit_composites(S, C, nc, off, cl_mem, co, st);
+  if (uf) underflow = true;
   __syncthreads();
 }
 
@@ -998,7 +1010,7 @@ template <int NT, int KM, bool BIG>
 __global__ void __launch_bounds__(NT) k_hermite_block(
     const int64_t *d_ncl, const int64_t *cl_off, const int32_t *cl_mem, p3t_particles p,
     p3t_params prm, double dt, int nc_lo, int nc_hi, unsigned long long *steps_out,
-    int64_t *cursor, HBig big, CollOut co, DevStatus *st) {
+    int64_t *cursor, HBig big, CollOut co, DevStatus *st, int64_t iter_limit, int32_t *rec) {
   __shared__ HCtl C;
   extern __shared__ __align__(16) unsigned char hsm[];
   static_assert(BIG || HSmall<KM>::kT >= NT, "a batch of pair terms must fit HSmall::T");
@@ -1027,11 +1039,11 @@ __global__ void __launch_bounds__(NT) k_hermite_block(
     if constexpr (BIG) {
       const BigView S{big.d, big.t, big.i, big.cap, off};
       integrate_cluster<NT>(S, C, nullptr, off, nc, cl_mem, p, prm, dt, coll, co, steps,
-                            underflow, st);
+                            underflow, st, iter_limit, rec);
     } else {
       const SmallView<KM> S{Sm};
       integrate_cluster<NT>(S, C, Sm->T, off, nc, cl_mem, p, prm, dt, coll, co, steps,
-                            underflow, st);
+                            underflow, st, iter_limit, rec);
     }
   }
   if (underflow) dev_fail(st, P3T_ERR_DT_UNDERFLOW, 62, 0);
@@ -1279,15 +1291,15 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
                                                              (int64_t)c->num_sms * 16),
                                           32, sizeof(HSmall<kHWarpMax>), c->aux[0]>>>(
       &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, 2, kHWarpMax, steps, c->hcursor,
-      big, co, c->status);
+      big, co, c->status, c->hermite_limit, c->hermite_rec);
   k_hermite_block<128, kHMax, false><<<(unsigned)p3t_grid(ncl_max * 128, 128, (int64_t)c->num_sms * 2),
                                        128, sizeof(HSmall<kHMax>), c->aux[1]>>>(
       &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, kHWarpMax + 1, kHMax, steps,
       c->hcursor + 1,
-      big, co, c->status);
+      big, co, c->status, c->hermite_limit, c->hermite_rec);
   k_hermite_block<128, 1, true><<<(unsigned)p3t_grid(ncl_max, 1, nbig), 128, 0, c->aux[1]>>>(
       &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, kHMax + 1, 0x7fffffff, steps,
-      c->hcursor + 2, big, co, c->status);
+      c->hcursor + 2, big, co, c->status, c->hermite_limit, c->hermite_rec);
   KepConst kc;
   kc.mu = mu;
   kc.sq = sqrt(mu);
@@ -1352,7 +1364,7 @@ int p3t_run_merge(p3t_ctx *c, p3t_particles *p, int32_t *new_index, double *e_di
                                   p->r_phys, sorted_h, sorted_s, out);
   const unsigned g = (unsigned)p3t_grid(n, kBlock, maxb);
   k_merge_keep<<<g, kBlock, 0, s>>>(n, c->coll_slot, co.ent, keep);
-  int rc = p3t_scan_i32_to_i64(keep, pos, d_n, n, d_total, c->scan_state, c->scan_words, c->status, s);
+  int rc = p3t_scan_i32_to_i64(keep, pos, d_n, n, d_total, c->scan_state, c->scan_words, c->status, c->poll_limit, s);
   if (rc) return rc;
   k_merge_gather<<<g, kBlock, 0, s>>>(n, keep, pos, *p, scr, ni);
   double *dst[10] = {p->x, p->y, p->z, p->vx, p->vy, p->vz, p->m, p->r_out, p->r_search,

@@ -186,7 +186,7 @@ int p3t_run_neighbours(p3t_ctx *c, const p3t_particles *p, int64_t *nb_off,
   P3T_CUDA_TRY(cudaMemsetAsync(c->fill, 0, sizeof(int32_t) * (n + 1), s));
   k_nb_filter<<<(unsigned)gc, kBlock, 0, s>>>(&cnt[9], c->cand_i, c->cand_j, c->idx, *p,
                                               c->prm, c->cand_keep, c->deg, c->status);
-  rc = p3t_scan_i32_to_i64(c->deg, nb_off, &cnt[0], c->cap, nb_off + n, c->scan_state, c->scan_words, c->status, s);
+  rc = p3t_scan_i32_to_i64(c->deg, nb_off, &cnt[0], c->cap, nb_off + n, c->scan_state, c->scan_words, c->status, c->poll_limit, s);
   if (rc) return rc;
   k_nb_check<<<1, 1, 0, s>>>(nb_off + n, nb_cap, c->status);
   k_nb_fill<<<(unsigned)gc, kBlock, 0, s>>>(&cnt[9], c->cand_i, c->cand_j, c->idx,
@@ -203,7 +203,7 @@ int p3t_run_neighbours(p3t_ctx *c, const p3t_particles *p, int64_t *nb_off,
     int64_t *tot = q == 0 ? &c->cl_counts[0] : q == 1 ? &c->cl_counts[1]
                  : q == 2 ? &c->cl_counts[2] : &cnt[11];
     rc = p3t_scan_i32_to_i64(c->flag + q * n, c->pos + q * n, &cnt[0], c->cap, tot,
-                             c->scan_state, c->scan_words, c->status, s);
+                             c->scan_state, c->scan_words, c->status, c->poll_limit, s);
     if (rc) return rc;
   }
   k_cl_scatter<<<(unsigned)g, kBlock, 0, s>>>(n, c->label, c->flag, c->pos, c->singles,

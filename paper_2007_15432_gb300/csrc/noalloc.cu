@@ -16,6 +16,11 @@
 // it keeps the contents of the last call; each call clears the part it uses
 // before use.  Calls that overlap on the GPU (on different streams without an
 // ordering between them) race on the scratch and must not be issued.
+//
+// The bin sums of |u|^2 are exact sums of fixed-point terms: each term is cut
+// to a multiple of 2^-88 (|u|^2 < 2^40 assumed; a larger term saturates) and
+// added as a 128-bit integer, so the order in which threads add them does not
+// matter and every run gives the same bits.
 #include <math.h>
 
 #include <mutex>
@@ -25,13 +30,15 @@
 namespace {
 
 constexpr int kMaxBins = 4096;           // largest vran_bins this entry point accepts
-constexpr int kScratchWords = 2 + 2 * kMaxBins;  // range bits, bin sums, bin counts
+// range bits, 128-bit bin sums (low and high words), bin counts
+constexpr int kScratchWords = 2 + 3 * kMaxBins;
+constexpr int kSharedBins = 2048;        // bins summed per block in shared memory first
 constexpr int kMaxDevices = 64;
 constexpr int kBlock = 256;
 
 }  // namespace
 
-// 8 + 2 * 4096 * 8 = 65,552 bytes per device
+// 16 + 3 * 4096 * 8 = 98,320 bytes per device
 static __device__ __align__(256) unsigned long long p3t_noalloc_scratch[kScratchWords];
 
 namespace {
@@ -70,14 +77,16 @@ __device__ __forceinline__ double nz_ord_double(unsigned long long b) {
   return __longlong_as_double((long long)b);
 }
 
-// scratch layout: [0] min and [1] max of R_cyl (ordered bits),
-// [2, 2 + nb) bin sums of |u|^2 (double bits), [2 + kMaxBins, ...) bin counts
+// scratch layout: [0] min and [1] max of R_cyl (ordered bits), then per bin
+// the low words [2, 2 + nb) and high words [2 + kMaxBins, ...) of the
+// fixed-point sums of |u|^2, and the counts [2 + 2 kMaxBins, ...)
 __global__ void nz_clear(unsigned long long *sc, int nb) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t == 0) { sc[0] = ~0ull; sc[1] = 0ull; }
   for (int k = t; k < nb; k += gridDim.x * blockDim.x) {
-    sc[2 + k] = 0ull;  // +0.0
+    sc[2 + k] = 0ull;
     sc[2 + kMaxBins + k] = 0ull;
+    sc[2 + 2 * kMaxBins + k] = 0ull;
   }
 }
 
@@ -110,15 +119,41 @@ __device__ __forceinline__ int nz_bin(double R, double Rmin, double Rmax,
   return k;
 }
 
+// t >= 0 as a 128-bit count of 2^-88 (truncated; saturated at 2^128 - 1):
+// the high word is floor(t 2^24), the low word the next 64 bits (both
+// products by powers of two and the fraction t 2^24 - hi are exact)
+__device__ __forceinline__ void nz_fixed(double t, unsigned long long &lo,
+                                         unsigned long long &hi) {
+  const double a = t * 16777216.0;  // t 2^(88 - 64)
+  if (!(a < 18446744073709551616.0)) { lo = hi = ~0ull; return; }
+  const double h = floor(a);
+  hi = (unsigned long long)h;
+  lo = (unsigned long long)((a - h) * 18446744073709551616.0);
+}
+
+// (lo, hi) += (a_lo, a_hi) with atomics: the carry out of the low word is
+// known from its old value, so the 128-bit total is exact in any order
+__device__ __forceinline__ void nz_add128(unsigned long long *lo, unsigned long long *hi,
+                                          unsigned long long a_lo, unsigned long long a_hi) {
+  const unsigned long long old = atomicAdd(lo, a_lo);
+  const unsigned long long carry = old + a_lo < old ? 1ull : 0ull;
+  if (a_hi + carry) atomicAdd(hi, a_hi + carry);
+}
+
 // random velocity u = v - sqrt(G M_* / |x|) phi_hat, |u|^2 summed per bin
+// (per block in shared memory first when the bins fit)
 __global__ void nz_bins(int64_t n, const double *x, const double *y,
                         const double *z, const double *vx, const double *vy,
                         const double *vz, double mu, int nb,
                         unsigned long long *sc) {
-  extern __shared__ double s_sum[];
-  unsigned int *s_cnt = reinterpret_cast<unsigned int *>(s_sum + nb);
-  for (int k = threadIdx.x; k < nb; k += blockDim.x) { s_sum[k] = 0.0; s_cnt[k] = 0u; }
-  __syncthreads();
+  extern __shared__ unsigned long long s_w[];
+  const bool shared = nb <= kSharedBins;
+  unsigned long long *s_lo = s_w, *s_hi = s_w + nb, *s_cnt = s_w + 2 * nb;
+  if (shared) {
+    for (int k = threadIdx.x; k < 3 * nb; k += blockDim.x) s_w[k] = 0ull;
+    __syncthreads();
+  }
+  unsigned long long *g_lo = sc + 2, *g_hi = sc + 2 + kMaxBins, *g_cnt = sc + 2 + 2 * kMaxBins;
   const double Rmin = nz_ord_double(sc[0]), Rmax = nz_ord_double(sc[1]);
   const double lmin = log(Rmin), lmax = log(Rmax);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -130,15 +165,22 @@ __global__ void nz_bins(int64_t n, const double *x, const double *y,
     if (R > 0.0) { px = -y[i] / R; py = x[i] / R; }
     const double ux = vx[i] - vk * px, uy = vy[i] - vk * py, uz = vz[i];
     const int k = nz_bin(R, Rmin, Rmax, lmin, lmax, nb);
-    atomicAdd(&s_sum[k], ux * ux + uy * uy + uz * uz);
-    atomicAdd(&s_cnt[k], 1u);
+    unsigned long long lo, hi;
+    nz_fixed(ux * ux + uy * uy + uz * uz, lo, hi);
+    if (shared) {
+      nz_add128(&s_lo[k], &s_hi[k], lo, hi);
+      atomicAdd(&s_cnt[k], 1ull);
+    } else {
+      nz_add128(&g_lo[k], &g_hi[k], lo, hi);
+      atomicAdd(&g_cnt[k], 1ull);
+    }
   }
+  if (!shared) return;
   __syncthreads();
-  double *gsum = reinterpret_cast<double *>(sc + 2);
   for (int k = threadIdx.x; k < nb; k += blockDim.x) {
     if (s_cnt[k]) {
-      atomicAdd(&gsum[k], s_sum[k]);
-      atomicAdd(&sc[2 + kMaxBins + k], (unsigned long long)s_cnt[k]);
+      nz_add128(&g_lo[k], &g_hi[k], s_lo[k], s_hi[k]);
+      atomicAdd(&g_cnt[k], s_cnt[k]);
     }
   }
 }
@@ -152,7 +194,6 @@ __global__ void nz_final(int64_t n, const double *x, const double *y,
   const double mu = prm.G * prm.m_star;
   const double Rmin = nz_ord_double(sc[0]), Rmax = nz_ord_double(sc[1]);
   const double lmin = log(Rmin), lmax = log(Rmax);
-  const double *gsum = reinterpret_cast<const double *>(sc + 2);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double R = sqrt(x[i] * x[i] + y[i] * y[i]);
@@ -162,7 +203,10 @@ __global__ void nz_final(int64_t n, const double *x, const double *y,
     const double a = alpha > 0.0 ? 1.0 / alpha : r;
     const double rhill = cbrt(m[i] / (3.0 * prm.m_star)) * a;
     const int k = nz_bin(R, Rmin, Rmax, lmin, lmax, nb);
-    const double vr = sqrt(gsum[k] / (double)sc[2 + kMaxBins + k]);
+    // the bin's 128-bit sum to FP64: hi 2^-24 + lo 2^-88
+    const double sum = (double)sc[2 + kMaxBins + k] * 5.9604644775390625e-08 +
+                       (double)sc[2 + k] * 3.2311742677852644e-27;
+    const double vr = sqrt(sum / (double)sc[2 + 2 * kMaxBins + k]);
     const double ro = prm.cutoff_mode == P3T_CUT_HILL_VRAN
                           ? fmax(prm.rcut0 * rhill, prm.rcut1 * vr * prm.dt_soft)
                           : prm.rcut0 * rhill;
@@ -207,8 +251,9 @@ extern "C" int p3t_cutoffs_noalloc(const p3t_params *prm, p3t_particles *p,
   const double mu = prm->G * prm->m_star;
   nz_clear<<<4, kBlock, 0, s>>>(sc, nb);
   nz_range<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, sc);
-  nz_bins<<<(unsigned)g, kBlock, nb * (sizeof(double) + sizeof(unsigned)), s>>>(
-      n, p->x, p->y, p->z, p->vx, p->vy, p->vz, mu, nb, sc);
+  const size_t smem = nb <= kSharedBins ? 3 * sizeof(unsigned long long) * nb : 0;
+  nz_bins<<<(unsigned)g, kBlock, smem, s>>>(n, p->x, p->y, p->z, p->vx, p->vy, p->vz, mu,
+                                            nb, sc);
   nz_final<<<(unsigned)g, kBlock, 0, s>>>(n, p->x, p->y, p->z, p->vx, p->vy, p->vz,
                                           p->m, *prm, nb, sc, p->r_out, p->r_search);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;

@@ -189,6 +189,11 @@ struct p3t_ctx {
   int32_t *dcnt = nullptr; // their per-tile arrival counters (zero between calls)
   int64_t dcnt_cap = 0;
   int64_t stack_cap = 0;  // walk stack entries per warp
+  // limits of the bounded device loops and the per-member Hermite step
+  // record (p3t_set_diag)
+  int64_t hermite_limit = (int64_t)1 << 24;  // block times per cluster and hard step
+  int64_t poll_limit = (int64_t)1 << 22;     // polls of a waiting scan tile
+  int32_t *hermite_rec = nullptr;            // caller's int32[n] or null
   int64_t last_n = -1;    // n of the last tree build
   bool have_tree = false;
   bool have_cand = false;
@@ -298,9 +303,12 @@ static inline int64_t p3t_grid(int64_t n, int block, int64_t max_blocks) {
 // decoupled look-back).  state: p3t_scan_state_words(n_cap) words, zero
 // before the first call (the scan leaves them zero).
 int64_t p3t_scan_state_words(int64_t n_cap);
+// poll_limit: polls a tile makes for its predecessors' sums before it gives
+// up (P3T_ERR_TIMEOUT recorded, the silent tiles counted as zero).
 int p3t_scan_i32_to_i64(const int32_t *in, int64_t *out, const int64_t *d_n,
                         int64_t n_cap, int64_t *d_total, unsigned long long *state,
-                        int64_t state_words, DevStatus *st, cudaStream_t s);
+                        int64_t state_words, DevStatus *st, int64_t poll_limit,
+                        cudaStream_t s);
 // Stable LSD radix sort of (key, val) on bits [begin_bit, end_bit), n from
 // device memory (at most n_cap).  Ping-pongs between the two buffers; on
 // return *keys / *vals point at the sorted data.

@@ -51,11 +51,9 @@ constexpr int kScanPer = 8;
 constexpr int kScanTile = kScanThreads * kScanPer;
 constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagInc = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
-constexpr int kScanPollLimit = 1 << 22;
-
 __global__ void __launch_bounds__(kScanThreads)
 scan_onepass(const int32_t *in, int64_t *out, const int64_t *d_n, int64_t *d_total,
-             unsigned long long *state, DevStatus *st) {
+             unsigned long long *state, DevStatus *st, int64_t poll_limit) {
   __shared__ int64_t sh[33];
   // the tile: first its int32 inputs, then its int64 outputs (staged so that
   // both the loads and the stores are coalesced)
@@ -101,12 +99,12 @@ scan_onepass(const int32_t *in, int64_t *out, const int64_t *d_n, int64_t *d_tot
           __stcg(&ts[tile], kFlagAgg | (unsigned long long)agg);
         }
         int64_t p = tile - 1;  // the window's first (nearest) predecessor
-        int polls = 0;
+        int64_t polls = 0;
         for (;;) {
           const int64_t q = p - lane;
           unsigned long long w = q >= 0 ? __ldcv(&ts[q]) : kFlagInc;
           while (__any_sync(0xffffffffu, (w >> 62) == 0)) {
-            if (++polls > kScanPollLimit) {
+            if (++polls > poll_limit) {
               if (lane == 0) dev_fail(st, P3T_ERR_TIMEOUT, 70, 0);
               w = (w >> 62) == 0 ? kFlagAgg : w;  // count the silent tile as zero
               break;
@@ -326,11 +324,13 @@ int64_t p3t_scan_state_words(int64_t n_cap) {
 
 int p3t_scan_i32_to_i64(const int32_t *in, int64_t *out, const int64_t *d_n,
                         int64_t n_cap, int64_t *d_total, unsigned long long *state,
-                        int64_t state_words, DevStatus *st, cudaStream_t s) {
+                        int64_t state_words, DevStatus *st, int64_t poll_limit,
+                        cudaStream_t s) {
   int64_t G = (n_cap + kScanTile - 1) / kScanTile;
   if (G < 1) G = 1;
   if (G + 2 > state_words) return P3T_ERR_CAPACITY;
-  scan_onepass<<<(unsigned)G, kScanThreads, 0, s>>>(in, out, d_n, d_total, state, st);
+  scan_onepass<<<(unsigned)G, kScanThreads, 0, s>>>(in, out, d_n, d_total, state, st,
+                                                    poll_limit);
   p3t_note_launches(1);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }

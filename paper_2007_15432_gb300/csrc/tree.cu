@@ -383,9 +383,17 @@ __device__ __forceinline__ uint32_t compact3(uint64_t v) {
   return (uint32_t)v;
 }
 
-// cell index floor((v - lo) S), S = 2^21 / L formed once per build
-__device__ __forceinline__ uint64_t quantise(double v, double lo, double S) {
-  double f = floor((v - lo) * S);
+// cell index of v: floor(d / u) of d = v - lo (rounded) and the cell side
+// u = L / 2^21, the quotient taken exactly (the largest q with q u <= d),
+// clamped to [0, 2^21).  The estimate floor(d S), with the scale S = 2^21 / L
+// formed once per build, is within ~1e-9 cells of d / u, so it is off by at
+// most one cell and only beside a cell boundary; two fused multiply-adds,
+// each rounded once and so with the sign of the exact q u - d, settle it.
+__device__ __forceinline__ uint64_t quantise(double v, double lo, double S, double u) {
+  const double d = v - lo;
+  double f = floor(d * S);
+  if (__fma_rn(f, u, -d) > 0.0) f -= 1.0;
+  else if (__fma_rn(f + 1.0, u, -d) <= 0.0) f += 1.0;
   if (f < 0.0) f = 0.0;
   if (f > (double)(P3T_QMAX - 1)) f = (double)(P3T_QMAX - 1);
   return (uint64_t)f;
@@ -403,7 +411,9 @@ __global__ void k_keys(SegView sv, const double *x, const double *y,
     const int64_t i = rekey ? (int64_t)idx[s] : s;
     const double *box = box5 + 5 * seg_at(sv, i);
     const double x0 = box[0], y0 = box[1], z0 = box[2], S = box[4];
-    uint64_t qx = quantise(x[i], x0, S), qy = quantise(y[i], y0, S), qz = quantise(z[i], z0, S);
+    const double u = box[3] * (1.0 / (double)P3T_QMAX);  // exact: a power-of-two scaling
+    uint64_t qx = quantise(x[i], x0, S, u), qy = quantise(y[i], y0, S, u),
+             qz = quantise(z[i], z0, S, u);
     keys[s] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
     if (!rekey) idx[s] = (int32_t)s;
   }
@@ -1181,7 +1191,7 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
                                           c->srs32, c->sml);
   k_lcp<<<(unsigned)g, kBlock, 0, s>>>(sv, c->keys, leaf, c->wlcp, c->lp);
   k_levels<<<(unsigned)g, kBlock, 0, s>>>(sv, leaf, c->wlcp, c->lp, c->lv, c->ncount);
-  rc = p3t_scan_i32_to_i64(c->ncount, c->nstart, &cnt[0], c->cap, &cnt[1], c->scan_state, c->scan_words, c->status, s);
+  rc = p3t_scan_i32_to_i64(c->ncount, c->nstart, &cnt[0], c->cap, &cnt[1], c->scan_state, c->scan_words, c->status, c->poll_limit, s);
   if (rc) return rc;
   k_clamp_nodes<<<1, 1, 0, s>>>(cnt, c->node_cap, c->status);
   k_nodes_pre<<<(unsigned)g, kBlock, 0, s>>>(sv, c->keys, c->lp, c->lv, c->nstart, &cnt[1],
@@ -1198,7 +1208,7 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
                                               c->leaf_flag, c->node_done, c->status);
   k_parents<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->node);
   rc = p3t_scan_i32_to_i64(c->leaf_flag, c->leaf_pos, &cnt[3], c->node_cap, &cnt[2],
-                           c->scan_state, c->scan_words, c->status, s);
+                           c->scan_state, c->scan_words, c->status, c->poll_limit, s);
   if (rc) return rc;
   k_leaf_list<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->leaf_flag,
                                               c->leaf_pos, c->pre2bfs, c->leaf_list);
@@ -1227,7 +1237,7 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   k_group_flags<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->node, c->bfs2pre,
                                                 c->prm.group_size, c->group_flag);
   rc = p3t_scan_i32_to_i64(c->group_flag, c->group_pos, &cnt[3], c->node_cap, &cnt[15],
-                           c->scan_state, c->scan_words, c->status, s);
+                           c->scan_state, c->scan_words, c->status, c->poll_limit, s);
   if (rc) return rc;
   k_group_list<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->group_flag,
                                                c->group_pos, c->pre2bfs, c->group_list);

@@ -871,6 +871,46 @@ __global__ void k_walk_post(int64_t *cnt, int64_t cand_cap, DevStatus *st) {
   cnt[9] = nc < cand_cap ? nc : cand_cap;
 }
 
+// T M^2 >= 2^K for T < 2^49, M < 2^53, K >= 0: the product formed exactly in
+// three 64-bit limbs and compared with the power of two
+bool prod_sq_ge_pow2(uint64_t T, uint64_t M, int K) {
+  const unsigned __int128 a = (unsigned __int128)T * M;  // < 2^102
+  const unsigned __int128 p0 = (unsigned __int128)(uint64_t)a * M;
+  const unsigned __int128 p1 = (unsigned __int128)(uint64_t)(a >> 64) * M;
+  const unsigned __int128 mid = (p0 >> 64) + (unsigned __int128)(uint64_t)p1;
+  const uint64_t w[3] = {(uint64_t)p0, (uint64_t)mid,
+                         (uint64_t)(p1 >> 64) + (uint64_t)(mid >> 64)};
+  if (K >= 192) return false;
+  for (int q = 2; q > K / 64; --q)
+    if (w[q]) return true;
+  return (w[K / 64] >> (K % 64)) != 0;
+}
+
+// Barnes-Hut threshold of a level: the smallest integer T with T theta^2 >=
+// side^2, side = 2^(22 - l) half cells, so that the integer test d^2 < T is
+// exactly side^2 > theta^2 d^2.  theta = M 2^E with M odd, so the condition
+// is T M^2 >= 2^K, K = 2 (22 - l) - 2E.  The FP64 quotient side^2 / theta^2
+// gives T to within one, and the exact product settles it.  Thresholds
+// beyond 2^47 (above every squared distance on the grid, < 3 * 2^44) are
+// clamped to 2^47; theta = 0 opens every node.
+int64_t bh_threshold(double theta, int level) {
+  const int64_t cap = (int64_t)1 << 47;
+  if (!(theta > 0.0)) return cap;
+  int e;
+  uint64_t M = (uint64_t)ldexp(frexp(theta, &e), 53);
+  int E = e - 53;
+  while (!(M & 1u)) { M >>= 1; ++E; }
+  const int K = 2 * (P3T_BITS + 1 - level) - 2 * E;
+  if (K < 0) return 1;
+  const double X = ldexp(1.0, 2 * (P3T_BITS + 1 - level)) / (theta * theta);
+  if (X > (double)cap + 4.0) return cap;
+  uint64_t T = (uint64_t)ceil(X);
+  if (T < 1) T = 1;
+  while (T > 1 && prod_sq_ge_pow2(T - 1, M, K)) --T;
+  while (!prod_sq_ge_pow2(T, M, K)) ++T;
+  return (int64_t)T < cap ? (int64_t)T : cap;
+}
+
 }  // namespace
 
 // blocks of 4 warps resident per SM: the mixed walk is compiled for 6 (80
@@ -900,13 +940,7 @@ int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
   a.inv1mg_f = (float)(1.0 / (1.0 - c->prm.gamma));
   a.mgi_f = (float)(-c->prm.gamma / (1.0 - c->prm.gamma));
   // Barnes-Hut thresholds per level, ceil((2^(22-l))^2 / theta^2) (half units)
-  const double big = 4611686018427387904.0;
-  const double th2 = c->prm.theta * c->prm.theta;
-  for (int l = 0; l <= P3T_BITS; ++l) {
-    double X = th2 > 0.0 ? ldexp(1.0, 2 * (P3T_BITS + 1 - l)) / th2 : big;
-    X = ceil(X);
-    a.bh[l] = X < big ? (int64_t)X : (int64_t)4611686018427387904LL;
-  }
+  for (int l = 0; l <= P3T_BITS; ++l) a.bh[l] = bh_threshold(c->prm.theta, l);
   k_walk_prep<<<1, 1, 0, s>>>(a.cursor, a.cand_count, a.counts);
   const unsigned blocks = (unsigned)(c->walk_warps / kWarps);
   if (c->prm.precision == P3T_MIXED) {

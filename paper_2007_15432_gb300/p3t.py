@@ -64,6 +64,14 @@ class Particles(C.Structure):
         "x", "y", "z", "vx", "vy", "vz", "m", "r_out", "r_search", "r_phys")]
 
 
+class Diag(C.Structure):
+    """``p3t_diag``: limits of the bounded device loops (0: default) and the
+    optional per-member Hermite step record (device int32 pointer)."""
+
+    _fields_ = [("hermite_block_limit", C.c_int64), ("scan_poll_limit", C.c_int64),
+                ("hermite_steps", C.c_void_p)]
+
+
 class Clusters(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("label", "singles", "cl_off", "cl_mem", "counts")]
 
@@ -93,6 +101,7 @@ _sig = {
     "p3t_soft_force_vjp": (C.c_int, [_CTX, C.POINTER(Particles), C.c_double] + [_vp] * 8),
     "p3t_kepler_vjp": (C.c_int, [_CTX, C.POINTER(Particles), C.c_double] + [_vp] * 7),
     "p3t_status": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
+    "p3t_set_diag": (C.c_int, [_CTX, C.POINTER(Diag)]),
     "p3t_tree_stats": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
     "p3t_strerror": (C.c_char_p, [C.c_int]),
     "p3t_launch_count": (C.c_int64, []),
@@ -341,6 +350,19 @@ def p3t_kepler_vjp(ctx, st: State, dt: float, lam_x: torch.Tensor, lam_v: torch.
     _check(_lib.p3t_kepler_vjp(ctx, C.byref(p), float(dt), _ptr(lam_x[0]), _ptr(lam_x[1]),
                                _ptr(lam_x[2]), _ptr(lam_v[0]), _ptr(lam_v[1]), _ptr(lam_v[2]),
                                _stream(stream)), "p3t_kepler_vjp")
+
+
+def p3t_set_diag(ctx, hermite_block_limit: int = 0, scan_poll_limit: int = 0,
+                 hermite_steps: torch.Tensor | None = None) -> None:
+    """Loop limits (0: the defaults 2^24 block times, 2^22 polls) and, with
+    ``hermite_steps`` (int32 CUDA tensor of n), the per-member corrector step
+    record of later hard steps."""
+    if hermite_steps is not None and (hermite_steps.dtype != torch.int32
+                                      or not hermite_steps.is_cuda):
+        raise TypeError("hermite_steps must be an int32 CUDA tensor")
+    d = Diag(int(hermite_block_limit), int(scan_poll_limit),
+             hermite_steps.data_ptr() if hermite_steps is not None else None)
+    _check(_lib.p3t_set_diag(ctx, C.byref(d)), "p3t_set_diag")
 
 
 def p3t_status(ctx) -> tuple[int, int]:

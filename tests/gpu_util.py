@@ -22,3 +22,27 @@ def oracle_params(P, **kw):
                                     "precision", "vran_bins", "group_size", "cutoff_mode")}
     d.update(kw)
     return O.Params(**d)
+
+
+def hermite_report(g, o, members, g_steps, o_steps):
+    """Cluster members after a hard step, GPU state g against the oracle's o
+    (state dicts): a member is "flipped" when its number of corrector steps
+    differs between the two (the block-step schedules parted: the GPU forms
+    its step estimates in its own arithmetic).  Returns the counts and the
+    largest relative position / velocity error of flipped and unflipped
+    members."""
+    members = np.asarray(members)
+    pos = np.stack([g["x"], g["y"], g["z"]], 1)[members]
+    pref = np.stack([o["x"], o["y"], o["z"]], 1)[members]
+    vel = np.stack([g["vx"], g["vy"], g["vz"]], 1)[members]
+    vref = np.stack([o["vx"], o["vy"], o["vz"]], 1)[members]
+    ep, ev = rel_err(pos, pref), rel_err(vel, vref)
+    flip = np.asarray(g_steps)[members] != np.asarray(o_steps)[members]
+
+    def mx(e, sel):
+        return float(e[sel].max()) if sel.any() else 0.0
+    return dict(members=int(len(members)), flipped=int(flip.sum()),
+                pos_unflipped=mx(ep, ~flip), vel_unflipped=mx(ev, ~flip),
+                pos_flipped=mx(ep, flip), vel_flipped=mx(ev, flip),
+                steps_gpu=int(np.asarray(g_steps)[members].sum()),
+                steps_oracle=int(np.asarray(o_steps)[members].sum()))

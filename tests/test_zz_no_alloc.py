@@ -7,13 +7,15 @@ This entry point computes the same radii as p3t_cutoffs with its scratch in a
 fixed device array.  The test calls it through the C ABI twice in a row, on
 different inputs with different bin counts (so stale scratch from the first
 call would show), and compares each result with p3t_cutoffs through a
-context, to the tolerance the cut-off parity test uses (1e-13 relative).
-The file name makes pytest collect it last.
+context and with the CPU oracle, to the tolerance the cut-off parity test
+uses (1e-13 relative); a repeated call on the same input gives the same bits
+(order-independent bin sums).  The file name makes pytest collect it last.
 """
 import numpy as np
 import pytest
 import torch
 
+from oracle import oracle as O
 from paper_2007_15432_gb300 import disks
 
 pytestmark = pytest.mark.gpu
@@ -40,11 +42,18 @@ def test_noalloc_cutoffs_match_context_path():
         got.r_search.fill_(-1.0)
         P.p3t_cutoffs_noalloc(prm, got)
         torch.cuda.synchronize()
-        for k in ("r_out", "r_search"):
+        o_ro, o_rs, _, _ = O.cutoffs(s, O.Params())
+        for k, o in (("r_out", o_ro), ("r_search", o_rs)):
             a = getattr(got, k).cpu().numpy()
             b = getattr(ref, k).cpu().numpy()
             assert np.all(a > 0)
             assert np.max(np.abs(a - b) / b) < 1e-13, k
+            assert np.max(np.abs(a - o) / o) < 1e-13, k
+        again = P.State.from_numpy(s)
+        P.p3t_cutoffs_noalloc(prm, again)
+        torch.cuda.synchronize()
+        for k in ("r_out", "r_search"):
+            assert torch.equal(getattr(again, k), getattr(got, k)), k
 
 
 def test_noalloc_rejects_too_many_bins():
