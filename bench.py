@@ -44,6 +44,9 @@ FLOP_PP, FLOP_PN = 30.0, 70.0
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 (FMA)
 # x 2.07 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP64 peak likewise: 152 SMs x 2 FP64 FMA lanes x 2 x 2.07 GHz (a dependent-
+# free DFMA stream was measured at 1.25 TFLOP/s on this part)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one k_walk launch on the N = 10^6 wide disk,
 # group size 64, from a single-pass ncu capture of this kernel
 # (dram__bytes_read.sum 80.07 MB + dram__bytes_write.sum 17.48 MB)
@@ -74,6 +77,9 @@ def parse():
                     help="the ensemble of 256 independent disks: batched in one context "
                          "(one launch sequence per step) vs per-disk contexts in one CUDA "
                          "graph vs per-disk contexts one after another")
+    ap.add_argument("--precision-study", action="store_true",
+                    help="FP64 vs mixed path over 64 soft steps of the N=1e5 ring, with the "
+                         "per-particle force error against the oracle (max, p99)")
     ap.add_argument("--cutoff-sweep", action="store_true",
                     help="compare the cut-off schemes (shared / individual / individual with "
                          "random velocity) over R~cut,0 on the mass-spectrum ring; one JSON "
@@ -404,6 +410,7 @@ def run_ours(args):
         cpu = dict(value=i_cpu / t_cpu, unit=UNIT, cores=info["threads"], kind="oracle",
                    sample=_oracle_sample_text(args.n, done) + f"; {t_cpu / done:.2f} s per step")
     achieved = flops_per_launch / walk_s / 1e12
+    peak = FP32_PEAK_TFLOPS if prec == P.P3T_MIXED else FP64_PEAK_TFLOPS
     line = dict(
         metric=METRIC, value=tot_inter / tot_elapsed, unit=UNIT, n_gpus=world, steps=K,
         warmup=W, ms_per_step=1e3 * tot_elapsed / K, higher_is_better=True, scaling="weak",
@@ -424,11 +431,13 @@ def run_ours(args):
         phases_ms=dict(kick_and_hard=phase[0], tree=phase[1], soft_force=phase[2],
                        neighbours_clusters=phase[3], kick=phase[4],
                        merge_and_recompute=phase[5]),
-        roofline=dict(kernel="k_walk (mixed) + float-float refinement", bound="alu",
-                      achieved=achieved, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
-                      frac=achieved / FP32_PEAK_TFLOPS,
-                      traffic=WALK_TRAFFIC_1E6 if (args.n == 1_000_000 and args.group_size == 64)
-                      else None, traffic_kernel="k_walk"),
+        roofline=dict(kernel=("k_walk (mixed) + float-float refinement" if prec == P.P3T_MIXED
+                              else "k_walk (fp64)"),
+                      bound="alu", pipe="fp32" if prec == P.P3T_MIXED else "fp64",
+                      achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                      traffic=WALK_TRAFFIC_1E6 if (args.n == 1_000_000 and args.group_size == 64
+                                                   and prec == P.P3T_MIXED) else None,
+                      traffic_kernel="k_walk"),
         e2e=dict(value=tot_e2e_inter / tot_e2e_t, unit=UNIT, h2d_bytes_per_step=h2d,
                  d2h_bytes_per_step=d2h),
         gpu_launches=int(launches),
@@ -527,6 +536,80 @@ def run_cutoff_sweep(args):
                     line["note"] = "steps not timed: largest cluster above 600 members"
                 print(json.dumps(line), flush=True)
                 ss.close()
+    return 0
+
+
+# -------------------------------------------------------- FP64 vs mixed ------
+def run_precision_study(args):
+    """The N = 1e5 equal-mass ring (0.9-1.1 au, m = 1e-11, e/i rms
+    0.01/0.005, seed 1002), theta = 0.5, monopole + quadrupole, leaf 16,
+    target groups of up to 64, dt = 1/64: 64 soft steps in the plain FP64
+    path and in the mixed path, each from the same initial state.  Reported
+    per path: time per soft step and pair interactions per second, and the
+    per-particle relative error of the soft force against the FP64 oracle
+    (same tree rules) on the initial state and on the state after the 64
+    steps: max, p99, median and max(|a - a_ref|) / rms|a_ref|."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    from paper_2007_15432_gb300 import build, disks
+    build.build()
+    from paper_2007_15432_gb300 import p3t as P
+    from oracle import oracle as O
+    n, K = args.n if args.n != 1_000_000 else 100_000, 64
+    s0 = disks.equal_mass_ring(n=n, seed=1002)
+
+    def force_err(st, ctx, op):
+        acc = torch.zeros(3, len(st.m), dtype=torch.float64, device=dev)
+        P.p3t_build_tree(ctx, st, False, stream)
+        P.p3t_soft_force(ctx, st, acc, None, stream)
+        torch.cuda.synchronize(dev)
+        g = st.numpy()
+        ref = O.tree_soft(g, g["r_out"], g["r_search"], op).acc
+        a = acc.cpu().numpy().T
+        e = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        rms = float(np.sqrt((ref * ref).sum(1).mean()))
+        return dict(max=float(e.max()), p99=float(np.percentile(e, 99)),
+                    median=float(np.median(e)),
+                    max_over_rms=float(np.linalg.norm(a - ref, axis=1).max() / rms))
+
+    out = {}
+    for name, prec in (("fp64", P.P3T_FP64), ("mixed", P.P3T_MIXED)):
+        prm = P.Params(theta=0.5, precision=prec, eta=0.01, eta0=0.001, group_size=64)
+        op = O.Params(theta=0.5, eta=0.01, eta0=0.001, group_size=64)
+        st = P.State.from_numpy(s0, device=dev)
+        ss = P.SoftStep(prm, st, device=0)
+        ss.init(update_cutoffs=True)
+        ss.status()
+        err0 = force_err(st, ss.ctx, op)
+        ss.force(stream)                       # the step's force again (tree of this state)
+        counts = torch.zeros(K, 2, dtype=torch.int64, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        E = torch.zeros(2, 4, dtype=torch.float64, device=dev)
+        P.p3t_energy(ss.ctx, st, E[0], stream)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for k in range(K):
+            ss.counts = counts[k]
+            ss.step(stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ss.status()
+        P.p3t_energy(ss.ctx, st, E[1], stream)
+        t = e0.elapsed_time(e1) / 1e3
+        errK = force_err(st, ss.ctx, op)
+        Ev = E.cpu().numpy()
+        out[name] = dict(ms_per_step=1e3 * t / K, value=float(counts.sum().item()) / t,
+                         force_error_initial=err0, force_error_after_64=errK,
+                         energy_error=abs(Ev[1, 0] / Ev[0, 0] - 1.0))
+        ss.close()
+    line = dict(study="precision", metric="soft step: FP64 vs mixed path, force error vs the "
+                "FP64 oracle", unit=UNIT, n=n, steps=K,
+                config=dict(workload=f"equal-mass ring N={n}, 0.9-1.1 au, m=1e-11, e/i rms "
+                            "0.01/0.005, theta=0.5, leaf 16, groups of <= 64, dt=1/64, eta=0.01"),
+                data="synthetic (seeded ring)", **out)
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -721,6 +804,8 @@ def main():
         return run_ensemble(args)
     if args.cutoff_sweep:
         return run_cutoff_sweep(args)
+    if args.precision_study:
+        return run_precision_study(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
