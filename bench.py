@@ -649,7 +649,7 @@ def run_ensemble(args):
     ens = EN.Ensemble(ds, [base] * len(ds), batched=True)
     ens.init()
     t0 = time.perf_counter()
-    gs_b = ens.autotune_batched()
+    tune_b = ens.autotune_batched()
     t_tune_b = time.perf_counter() - t0
     l0 = P.p3t_launch_count()
     ens.step_sequential()
@@ -695,7 +695,7 @@ def run_ensemble(args):
                 value=inter_b / (t_b / K), unit=UNIT, n_gpus=1, steps=K, warmup=W,
                 ms_per_step=1e3 * t_b / K, higher_is_better=True,
                 gpu_launches=launches_b * K,
-                batched=dict(group_size=gs_b, autotune_s=t_tune_b, launches_per_step=launches_b),
+                batched=dict(tuned=tune_b, autotune_s=t_tune_b, launches_per_step=launches_b),
                 per_disk_graph=dict(value=inter / (t_graph / K), ms_per_step=1e3 * t_graph / K,
                                     launches_per_step=launches_d, streams=16,
                                     group_size_by_log2_n={str(k): v

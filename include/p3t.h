@@ -384,6 +384,21 @@ typedef struct {
 } p3t_diag;
 int p3t_set_diag(p3t_ctx *ctx, const p3t_diag *d);
 
+/* Launch shapes that change speed but not results (the paper has no
+ * counterpart: tuning knobs, e.g. for an autotuner).
+ *  - hermite_warp_max: clusters of 2..hermite_warp_max members are integrated
+ *    by one warp each, larger ones (up to 128) by a block of four warps;
+ *    2..32, 0 selects the default 8.
+ *  - walk_blocks_per_sm: blocks of the soft-force walk per SM, 1..6 (the
+ *    kernel is compiled for 6 resident), 0 selects as many as fit.
+ * Host call, no device work; takes effect for work enqueued after it.
+ * P3T_ERR_INVALID for a NULL argument or a value out of range. */
+typedef struct {
+  int32_t hermite_warp_max;
+  int32_t walk_blocks_per_sm;
+} p3t_tuning;
+int p3t_set_tuning(p3t_ctx *ctx, const p3t_tuning *t);
+
 /* Synchronises the context's device, returns the first device-side error
  * recorded since the last call (or 0) and clears it.  *required (may be NULL)
  * receives the buffer size a P3T_ERR_CAPACITY asked for.  Not capturable. */

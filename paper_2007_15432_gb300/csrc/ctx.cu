@@ -9,6 +9,7 @@
 #include "p3t_internal.cuh"
 
 int64_t p3t_walk_warps(int num_sms, int64_t n);
+int p3t_walk_blocks_per_sm();
 
 static std::atomic<long long> g_launches{0};
 void p3t_note_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -471,6 +472,17 @@ int p3t_set_diag(p3t_ctx *c, const p3t_diag *d) {
   c->hermite_limit = d->hermite_block_limit > 0 ? d->hermite_block_limit : (int64_t)1 << 24;
   c->poll_limit = d->scan_poll_limit > 0 ? d->scan_poll_limit : (int64_t)1 << 22;
   c->hermite_rec = d->hermite_steps;
+  return P3T_OK;
+}
+
+int p3t_set_tuning(p3t_ctx *c, const p3t_tuning *t) {
+  if (!c || !t) return P3T_ERR_INVALID;
+  if (t->hermite_warp_max != 0 && (t->hermite_warp_max < 2 || t->hermite_warp_max > 32))
+    return P3T_ERR_INVALID;
+  if (t->walk_blocks_per_sm < 0 || t->walk_blocks_per_sm > p3t_walk_blocks_per_sm())
+    return P3T_ERR_INVALID;
+  c->hwarp_max = t->hermite_warp_max ? t->hermite_warp_max : 8;
+  c->walk_bps = t->walk_blocks_per_sm;
   return P3T_OK;
 }
 

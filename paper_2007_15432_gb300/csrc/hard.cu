@@ -390,12 +390,11 @@ __global__ void k_kepler_all(p3t_particles p, double dt, KepConst K, DevStatus *
 // for the neighbours).  One thread does this bookkeeping in a fixed order;
 // collisions are rare.
 constexpr int kHMax = 128;  // largest cluster kept in shared memory
-// largest cluster integrated by one warp; larger ones take a block of four
-// warps, whose pair terms then run on four sub-partitions' FP64 pipes
-#ifndef P3T_HWARP_MAX
-#define P3T_HWARP_MAX 8
-#endif
-constexpr int kHWarpMax = P3T_HWARP_MAX;
+// the largest cluster integrated by one warp is a launch-shape choice
+// (p3t_set_tuning; 8 by default): larger ones take a block of four warps,
+// whose pair terms then run on four sub-partitions' FP64 pipes.  The one-warp
+// kernel is compiled for clusters of up to 8, 16 and 32 members (its shared
+// memory grows with the bound, so the smallest that fits is launched).
 constexpr int32_t kNone = 0x7fffffff;  // no collision partner
 
 template <int KM>
@@ -1285,16 +1284,25 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
   P3T_CUDA_TRY(cudaStreamWaitEvent(c->aux[1], c->ev_fork, 0));
   const int64_t ncl_max = (n / 2) > 0 ? n / 2 : 1;
   const int64_t nbig = c->num_sms < 32 ? c->num_sms : 32;
-  // clusters of 2..kHWarpMax members: a warp each (stream aux[0]); up to
-  // 128: a 128-thread block each, then > 128 (stream aux[1])
-  k_hermite_block<32, kHWarpMax, false><<<(unsigned)p3t_grid(ncl_max * 32, 32,
-                                                             (int64_t)c->num_sms * 16),
-                                          32, sizeof(HSmall<kHWarpMax>), c->aux[0]>>>(
-      &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, 2, kHWarpMax, steps, c->hcursor,
-      big, co, c->status, c->hermite_limit, c->hermite_rec);
+  // clusters of 2..hw members: a warp each (stream aux[0]); up to 128: a
+  // 128-thread block each, then > 128 (stream aux[1])
+  const int hw = c->hwarp_max;
+  const unsigned gw = (unsigned)p3t_grid(ncl_max * 32, 32, (int64_t)c->num_sms * 16);
+  if (hw <= 8)
+    k_hermite_block<32, 8, false><<<gw, 32, sizeof(HSmall<8>), c->aux[0]>>>(
+        &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, 2, hw, steps, c->hcursor,
+        big, co, c->status, c->hermite_limit, c->hermite_rec);
+  else if (hw <= 16)
+    k_hermite_block<32, 16, false><<<gw, 32, sizeof(HSmall<16>), c->aux[0]>>>(
+        &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, 2, hw, steps, c->hcursor,
+        big, co, c->status, c->hermite_limit, c->hermite_rec);
+  else
+    k_hermite_block<32, 32, false><<<gw, 32, sizeof(HSmall<32>), c->aux[0]>>>(
+        &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, 2, hw, steps, c->hcursor,
+        big, co, c->status, c->hermite_limit, c->hermite_rec);
   k_hermite_block<128, kHMax, false><<<(unsigned)p3t_grid(ncl_max * 128, 128, (int64_t)c->num_sms * 2),
                                        128, sizeof(HSmall<kHMax>), c->aux[1]>>>(
-      &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, kHWarpMax + 1, kHMax, steps,
+      &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, hw + 1, kHMax, steps,
       c->hcursor + 1,
       big, co, c->status, c->hermite_limit, c->hermite_rec);
   k_hermite_block<128, 1, true><<<(unsigned)p3t_grid(ncl_max, 1, nbig), 128, 0, c->aux[1]>>>(

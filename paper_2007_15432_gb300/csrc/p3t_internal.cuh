@@ -194,6 +194,10 @@ struct p3t_ctx {
   int64_t hermite_limit = (int64_t)1 << 24;  // block times per cluster and hard step
   int64_t poll_limit = (int64_t)1 << 22;     // polls of a waiting scan tile
   int32_t *hermite_rec = nullptr;            // caller's int32[n] or null
+  // launch shapes (p3t_set_tuning): largest cluster integrated by one warp,
+  // walk blocks per SM
+  int hwarp_max = 8;
+  int walk_bps = 0;  // 0: as many as fit
   int64_t last_n = -1;    // n of the last tree build
   bool have_tree = false;
   bool have_cand = false;

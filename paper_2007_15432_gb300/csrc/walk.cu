@@ -942,7 +942,9 @@ int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
   // Barnes-Hut thresholds per level, ceil((2^(22-l))^2 / theta^2) (half units)
   for (int l = 0; l <= P3T_BITS; ++l) a.bh[l] = bh_threshold(c->prm.theta, l);
   k_walk_prep<<<1, 1, 0, s>>>(a.cursor, a.cand_count, a.counts);
-  const unsigned blocks = (unsigned)(c->walk_warps / kWarps);
+  unsigned blocks = (unsigned)(c->walk_warps / kWarps);
+  if (c->walk_bps > 0 && (int64_t)c->num_sms * c->walk_bps < (int64_t)blocks)
+    blocks = (unsigned)(c->num_sms * c->walk_bps);
   if (c->prm.precision == P3T_MIXED) {
     // one target per lane (or several lanes per target): two targets per
     // lane (a 64-target group walked once) was measured slower than two

@@ -10,7 +10,8 @@ descriptor table).  Two ways to step them:
     soft step runs once over all disks, each disk keeping its own radial bins,
     root cube, octree and walk roots, so one ensemble step costs the launches
     of one soft step whatever the number of disks.  One parameter set for all
-    disks (``autotune_batched`` picks its group size).
+    disks (``autotune_batched`` picks its group size, Hermite warp split
+    and walk grid).
   * per-disk contexts (``batched=False``): each disk has its own context on
     views of the shared arrays, with parameters of its own (``autotune`` picks
     a group size per disk-size class).
@@ -156,37 +157,65 @@ class Ensemble:
         """One ensemble step by replaying the captured graph."""
         self.graph.replay()
 
-    def autotune_batched(self, candidates=(16, 32, 48, 64), reps: int = 3) -> int:
-        """Group size of a batched ensemble: the candidate with the shortest
-        tree build + soft force over all disks (CUDA events, best of
-        ``reps``), after ``init``.  Sets it, recomputes force, neighbours and
-        clusters with it (drops a captured graph) and returns it."""
+    def autotune_batched(self, group_sizes=(32, 48, 64), warp_max=(4, 8, 16, 32),
+                         walk_blocks=(4, 6), reps: int = 2) -> dict:
+        """Launch shapes of a batched ensemble, after ``init``: every
+        combination of the walk's group size, the largest Hermite cluster
+        integrated by one warp and the walk's blocks per SM is timed on whole
+        ensemble soft steps (CUDA events, best of ``reps``), each from the
+        same snapshot of the state (restored afterwards, with the force,
+        neighbours and clusters of the chosen group size).  Group size
+        changes the interaction lists (the method's target groups), the other
+        two only the launch.  Sets and returns the fastest
+        {group_size, hermite_warp_max, walk_blocks_per_sm, ms}; drops a
+        captured graph."""
         if not self.batched:
             raise ValueError("autotune_batched is for a batched ensemble")
-        ss, st = self.steps[0], self.units[0]
-        best = None
-        for gs in candidates:
+        ss = self.steps[0]
+        snap = {k: v.clone() for k, v in self.arrays.items()}
+        stream = torch.cuda.current_stream(self.device)
+
+        def restore():
+            for k, v in self.arrays.items():
+                v.copy_(snap[k])
+
+        def params_with(gs):
             prm = P.Params(**{f[0]: getattr(self.params[0], f[0]) for f in P.Params._fields_})
             prm.group_size = int(gs)
+            return prm
+
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = None
+        for gs in group_sizes:
+            prm = params_with(gs)
             P.p3t_set_params(ss.ctx, prm)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            times = []
-            for _ in range(reps):
-                e0.record()
-                P.p3t_build_tree(ss.ctx, st, False)
-                P.p3t_soft_force(ss.ctx, st, ss.acc, ss.counts)
-                e1.record()
-                torch.cuda.synchronize(self.device)
-                times.append(e0.elapsed_time(e1))
-            ss.status()
-            if best is None or min(times) < best[0]:
-                best = (min(times), prm)
-        self.params[0] = ss.params = best[1]
-        P.p3t_set_params(ss.ctx, best[1])
-        ss.force()
+            self.params[0] = ss.params = prm
+            for hw in warp_max:
+                for wb in walk_blocks:
+                    P.p3t_set_tuning(ss.ctx, hw, wb)
+                    times = []
+                    for _ in range(reps):
+                        restore()
+                        ss.force(stream)
+                        e0.record(stream)
+                        self._step_disk(0, stream)
+                        e1.record(stream)
+                        torch.cuda.synchronize(self.device)
+                        times.append(e0.elapsed_time(e1))
+                    ss.status()
+                    t = min(times)
+                    if best is None or t < best["ms"]:
+                        best = dict(group_size=int(gs), hermite_warp_max=int(hw),
+                                    walk_blocks_per_sm=int(wb), ms=float(t))
+        prm = params_with(best["group_size"])
+        P.p3t_set_params(ss.ctx, prm)
+        self.params[0] = ss.params = prm
+        P.p3t_set_tuning(ss.ctx, best["hermite_warp_max"], best["walk_blocks_per_sm"])
+        restore()
+        ss.force(stream)
         torch.cuda.synchronize(self.device)
         self.graph = None
-        return int(best[1].group_size)
+        return best
 
     # ---- results -----------------------------------------------------------------
     def interactions(self) -> int:

@@ -72,6 +72,12 @@ class Diag(C.Structure):
                 ("hermite_steps", C.c_void_p)]
 
 
+class Tuning(C.Structure):
+    """``p3t_tuning``: launch shapes (0: default)."""
+
+    _fields_ = [("hermite_warp_max", C.c_int32), ("walk_blocks_per_sm", C.c_int32)]
+
+
 class Clusters(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("label", "singles", "cl_off", "cl_mem", "counts")]
 
@@ -102,6 +108,7 @@ _sig = {
     "p3t_kepler_vjp": (C.c_int, [_CTX, C.POINTER(Particles), C.c_double] + [_vp] * 7),
     "p3t_status": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
     "p3t_set_diag": (C.c_int, [_CTX, C.POINTER(Diag)]),
+    "p3t_set_tuning": (C.c_int, [_CTX, C.POINTER(Tuning)]),
     "p3t_tree_stats": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
     "p3t_strerror": (C.c_char_p, [C.c_int]),
     "p3t_launch_count": (C.c_int64, []),
@@ -363,6 +370,13 @@ def p3t_set_diag(ctx, hermite_block_limit: int = 0, scan_poll_limit: int = 0,
     d = Diag(int(hermite_block_limit), int(scan_poll_limit),
              hermite_steps.data_ptr() if hermite_steps is not None else None)
     _check(_lib.p3t_set_diag(ctx, C.byref(d)), "p3t_set_diag")
+
+
+def p3t_set_tuning(ctx, hermite_warp_max: int = 0, walk_blocks_per_sm: int = 0) -> None:
+    """Launch shapes (speed only): one-warp Hermite clusters up to
+    ``hermite_warp_max`` members, walk blocks per SM (0: defaults)."""
+    t = Tuning(int(hermite_warp_max), int(walk_blocks_per_sm))
+    _check(_lib.p3t_set_tuning(ctx, C.byref(t)), "p3t_set_tuning")
 
 
 def p3t_status(ctx) -> tuple[int, int]:

@@ -136,8 +136,14 @@ def test_batched_autotune_and_single_segment(mods):
     prm = _params(P, 1)
     ens = EN.Ensemble(ds, [prm] * len(ds), batched=True)
     ens.init()
-    gs = ens.autotune_batched(candidates=(16, 64), reps=1)
-    assert gs in (16, 64)
+    snap = ens.numpy()
+    best = ens.autotune_batched(group_sizes=(16, 64), warp_max=(4, 32), walk_blocks=(2, 6),
+                                reps=1)
+    assert best["group_size"] in (16, 64) and best["hermite_warp_max"] in (4, 32)
+    assert best["walk_blocks_per_sm"] in (2, 6) and best["ms"] > 0
+    # the tuner leaves the state as it found it
+    after = ens.numpy()
+    assert all(np.array_equal(snap[k], after[k]) for k in snap)
     ens.capture()
     ens.step_graph()
     torch.cuda.synchronize()
