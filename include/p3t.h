@@ -337,6 +337,22 @@ int p3t_soft_force_vjp(p3t_ctx *ctx, const p3t_particles *p, double h, const dou
                        const double *ly, const double *lz, double *gx, double *gy, double *gz,
                        double *gm, void *stream);
 
+/* Adjoint of the tree soft force (the paper has no counterpart): the
+ * vector-Jacobian product of Eq. softforce as p3t_soft_force evaluates it
+ * with the tree, the interaction lists (which nodes are accepted and which
+ * leaves are opened for each target group) and the cut-off radii held fixed:
+ * a second walk of the context's tree meets the lists of the forward walk.
+ * With L = sum_i lam_i . a_i, ADDS h dL/dx_i to (gx, gy, gz) and h dL/dm_i
+ * to gm; node terms reach the particles through the node's mass, centre of
+ * mass and quadrupole.  Requires a P3T_FP64 context whose tree was built
+ * from p (p3t_build_tree; else P3T_ERR_INVALID).  lx, ly, lz, gx..gm:
+ * device, n each, caller order.  FP64 arithmetic; contributions reach the
+ * sums through atomic additions, so the last bits can differ between runs.
+ * The first call allocates a per-node buffer (call it before any capture). */
+int p3t_soft_force_vjp_tree(p3t_ctx *ctx, const p3t_particles *p, double h, const double *lx,
+                            const double *ly, const double *lz, double *gx, double *gy,
+                            double *gz, double *gm, void *stream);
+
 /* The adjoint of the Kepler drift of every particle of p by dt
  * (the drift's map, mu = G M_*): on entry lx..lvz hold the adjoint of the state
  * after the drift, on return the adjoint of the state before it (Phi^T lam,

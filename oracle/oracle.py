@@ -121,6 +121,8 @@ def lib():
         L.or_hard_step.argtypes = ([C.c_int64] + [_dp] * 8 + [
             _vp, _P, C.c_double, C.c_int64, _i32p, C.c_int64, _i64p, _i32p,
             C.POINTER(C.c_int64), _i32p, C.POINTER(C.c_double), _vp])
+        L.or_tree_lists.argtypes = ([C.c_int64] + [_dp] * 6 + [_P, _i64p, _i64p] +
+                                    [_vp] * 7)
         L.or_bh_threshold.restype = C.c_int64
         L.or_bh_threshold.argtypes = [C.c_double, C.c_int]
         L.or_mac_open.restype = C.c_int
@@ -234,6 +236,40 @@ def mac_open(theta: float, level: int, node_c2, node_qlo, node_qhi, node_R: int,
     return bool(lib().or_mac_open(float(theta), int(level), a(node_c2), a(node_qlo),
                                   a(node_qhi), int(node_R), a(grp_qlo), a(grp_qhi),
                                   int(grp_R)))
+
+
+def tree_lists(s: dict, r_out, r_search, p: Params) -> dict:
+    """The tree walk's interaction lists (same tree, groups and opening rules
+    as ``tree_soft``): ``ord`` (sorted position -> caller index), each node's
+    member range in sorted order (``node_first``, ``node_count``), the target
+    groups (``group_node``, ``group_off`` into the list) and the list in walk
+    order: ``rec_kind`` 0 for an accepted node, 1 for an opened leaf, with
+    its node id in ``rec_node``."""
+    n = len(s["m"])
+    caps = np.array([4 * n + 64, 2 * n + 8, 64 * n + 1024], dtype=np.int64)
+    for _ in range(3):
+        sizes = np.zeros(3, dtype=np.int64)
+        out = dict(ord=np.empty(max(n, 1), dtype=np.int64),
+                   node_first=np.empty(caps[0], dtype=np.int64),
+                   node_count=np.empty(caps[0], dtype=np.int64),
+                   group_node=np.empty(caps[1], dtype=np.int64),
+                   group_off=np.empty(caps[1] + 1, dtype=np.int64),
+                   rec_kind=np.empty(caps[2], dtype=np.int32),
+                   rec_node=np.empty(caps[2], dtype=np.int32))
+        cp = p.c()
+        lib().or_tree_lists(n, *[_f64(s[k]) for k in ("x", "y", "z", "m")], _f64(r_out),
+                            _f64(r_search), C.byref(cp), caps, sizes,
+                            *[out[k].ctypes.data for k in ("ord", "node_first", "node_count",
+                                                           "group_node", "group_off",
+                                                           "rec_kind", "rec_node")])
+        if np.all(sizes <= caps):
+            nn, ng, nr = (int(v) for v in sizes)
+            return dict(ord=out["ord"][:n], node_first=out["node_first"][:nn],
+                        node_count=out["node_count"][:nn], group_node=out["group_node"][:ng],
+                        group_off=out["group_off"][:ng + 1], rec_kind=out["rec_kind"][:nr],
+                        rec_node=out["rec_node"][:nr])
+        caps = np.maximum(caps, sizes)
+    raise RuntimeError("tree list capacity did not converge")
 
 
 def node_moments(x, y, z, m):

@@ -516,6 +516,7 @@ typedef struct {
   uint64_t npp, npn;
   cand_buf *cb;
   const int64_t *bh;
+  cand_buf *rec;    /* or NULL: the group's list as (kind, node): 0 accepted node, 1 opened leaf */
 } walk_ctx;
 
 static void walk(walk_ctx *w, int64_t k) {
@@ -523,6 +524,7 @@ static void walk(walk_ctx *w, int64_t k) {
   const or_node *nd = &T->node[k];
   const or_node *g = w->g;
   if (!mac_open(g, nd, w->bh)) {
+    if (w->rec) cand_push(w->rec, 0, (int32_t)k);
     double mom[10] = {nd->M, nd->com[0], nd->com[1], nd->com[2], nd->Q[0],
                       nd->Q[1], nd->Q[2], nd->Q[3], nd->Q[4], nd->Q[5]};
     for (int64_t s = g->first; s < g->first + g->count; ++s) {
@@ -536,6 +538,7 @@ static void walk(walk_ctx *w, int64_t k) {
     return;
   }
   if (nd->nchild == 0) {
+    if (w->rec) cand_push(w->rec, 1, (int32_t)k);
     for (int64_t s = g->first; s < g->first + g->count; ++s) {
       if (!w->is_target[s]) continue;
       double *acc = w->acc[s - g->first];
@@ -613,7 +616,7 @@ int or_tree_soft(int64_t n, const double *x, const double *y, const double *z,
         a = big;
       }
       memset(a, 0, sizeof(double) * 3 * g->count);
-      walk_ctx w = {&T, p, g, is_target, a, 0, 0, &cbs[tid], bh};
+      walk_ctx w = {&T, p, g, is_target, a, 0, 0, &cbs[tid], bh, NULL};
       walk(&w, 0);
       for (int64_t s = g->first; s < g->first + g->count; ++s) {
         if (!is_target[s]) continue;
@@ -644,6 +647,52 @@ int or_tree_soft(int64_t n, const double *x, const double *y, const double *z,
         tree_stats[3] = T.node[k].count;
   }
   free(leaves); free(is_target); free(inv);
+  tree_free(&T);
+  return 0;
+}
+
+/* The interaction lists of the tree walk (the same tree, groups and opening */
+/* decisions as or_tree_soft), for the adjoint's oracle: the sorted order   */
+/* ord (sorted position -> caller index), every node's member range         */
+/* [first, first + count) in sorted order, the target groups (their node)   */
+/* and per group its list, in walk order, of accepted nodes (kind 0, whose  */
+/* monopole + quadrupole act on the group's particles) and opened leaves    */
+/* (kind 1, whose particles act as pairs on every other particle of the     */
+/* group).  sizes = {nodes, groups, list entries}; arrays beyond their caps  */
+/* (caps, same order) are left unfilled and the caller asks again.          */
+int or_tree_lists(int64_t n, const double *x, const double *y, const double *z,
+                  const double *m, const double *r_out, const double *r_search,
+                  const or_params *p, const int64_t caps[3], int64_t sizes[3],
+                  int64_t *ord, int64_t *node_first, int64_t *node_count,
+                  int64_t *group_node, int64_t *group_off, int32_t *rec_kind,
+                  int32_t *rec_node) {
+  sizes[0] = sizes[1] = sizes[2] = 0;
+  if (n <= 0) return 0;
+  or_tree T;
+  tree_build(&T, n, x, y, z, m, r_out, r_search, p->leaf_size);
+  unsigned char *none = (unsigned char *)calloc(n, 1);
+  int64_t bh[OR_BITS + 1];
+  bh_thresholds(p->theta, bh);
+  const int64_t gs = p->group_size;
+  cand_buf rec = {0, 0, 0, 0};
+  int64_t ngroup = 0;
+  sizes[0] = T.nnode;
+  for (int64_t k = 0; k < T.nnode; ++k) {
+    if (k < caps[0]) { node_first[k] = T.node[k].first; node_count[k] = T.node[k].count; }
+    int small = T.node[k].count <= gs || T.node[k].nchild == 0;
+    int top = k == 0 || T.node[T.parent[k]].count > gs;
+    if (!(small && top)) continue;
+    if (ngroup < caps[1]) { group_node[ngroup] = k; group_off[ngroup] = rec.n; }
+    walk_ctx w = {&T, p, &T.node[k], none, NULL, 0, 0, NULL, bh, &rec};
+    walk(&w, 0);
+    ++ngroup;
+  }
+  if (ngroup < caps[1] + 1 && group_off) group_off[ngroup] = rec.n;
+  for (int64_t q = 0; q < rec.n && q < caps[2]; ++q) { rec_kind[q] = rec.ci[q]; rec_node[q] = rec.cj[q]; }
+  for (int64_t s2 = 0; s2 < n && ord; ++s2) ord[s2] = T.ord[s2];
+  sizes[1] = ngroup;
+  sizes[2] = rec.n;
+  free(rec.ci); free(rec.cj); free(none);
   tree_free(&T);
   return 0;
 }

@@ -74,6 +74,15 @@ int or_mac_open(double theta, int level, const int64_t node_c2[3],
                 const int64_t node_qlo[3], const int64_t node_qhi[3], int64_t node_R,
                 const int64_t grp_qlo[3], const int64_t grp_qhi[3], int64_t grp_R);
 
+/* the walk's interaction lists: groups, their accepted nodes (kind 0) and  */
+/* opened leaves (kind 1) in walk order, node member ranges, sorted order    */
+int or_tree_lists(int64_t n, const double *x, const double *y, const double *z,
+                  const double *m, const double *r_out, const double *r_search,
+                  const or_params *p, const int64_t caps[3], int64_t sizes[3],
+                  int64_t *ord, int64_t *node_first, int64_t *node_count,
+                  int64_t *group_node, int64_t *group_off, int32_t *rec_kind,
+                  int32_t *rec_node);
+
 /* multipole moments of a particle set and their field at a point (Barnes-Hut
  * node term, monopole + traceless quadrupole) */
 void or_node_moments(int64_t n, const double *x, const double *y,

@@ -3,11 +3,16 @@
 A rollout of ``steps`` soft steps of the paper's procedure (kick h = dt/2,
 drift by dt, new soft force, kick h) in the form where every particle drifts
 on its Kepler orbit about the star (the drift the paper gives an isolated
-particle, Sec. 2.1.2) and the soft force of Eq. softforce is summed directly
-over all pairs (``p3t_soft_force_direct``, what the tree gives at theta = 0),
-with the cut-off radii frozen at the values the caller passes.  Gradients of
-a loss of the final state with respect to the initial positions, velocities
-and masses come from a reverse sweep through libp3t's kernels:
+particle, Sec. 2.1.2) and the soft force of Eq. softforce is either summed
+directly over all pairs (``force="direct"``: ``p3t_soft_force_direct``, what
+the tree gives at theta = 0) or evaluated by the tree walk (``force="tree"``:
+``p3t_build_tree`` + ``p3t_soft_force``, FP64), with the cut-off (and, for
+the tree, search) radii frozen at the values the caller passes.  The tree's
+adjoint holds its interaction lists fixed: the reverse sweep rebuilds the
+tree at each recomputed state and ``p3t_soft_force_vjp_tree`` walks it again.
+Gradients of a loss of the final state with respect to the initial
+positions, velocities and masses come from a reverse sweep through libp3t's
+kernels:
 
   * the second kick of step k-1 and the first kick of step k act at the same
     positions x_k with the same velocity adjoint, so the sweep takes one
@@ -29,18 +34,23 @@ from . import p3t as P
 class SoftKDK:
     """Forward and reverse sweeps of an n-particle soft KDK rollout on one GPU.
 
-    ``params``: the method's parameters (theta is not used: the force is the
-    direct sum, whose VJP the reverse sweep takes); collisions must be off.
-    ``precision`` of the params selects FP64 or FP32 pair arithmetic for both
-    the soft force and its VJP."""
+    ``params``: the method's parameters (theta and the group size matter for
+    the tree force only); collisions must be off.  With the direct force
+    ``precision`` selects FP64 or FP32 pair arithmetic for both the soft
+    force and its VJP; the tree force and its VJP run in FP64."""
 
     def __init__(self, params: P.Params, n: int, steps: int, checkpoint: int = 8,
-                 device: int = 0):
+                 device: int = 0, force: str = "direct"):
         if params.f_radius > 0.0:
             raise ValueError("the adjoint rollout has no collisions (f_radius must be 0)")
         if steps < 1 or checkpoint < 1:
             raise ValueError("steps and checkpoint must be >= 1")
+        if force not in ("direct", "tree"):
+            raise ValueError("force is 'direct' or 'tree'")
+        self.force = force
         self.params = P.Params(**{f[0]: getattr(params, f[0]) for f in P.Params._fields_})
+        if force == "tree":
+            self.params.precision = P.P3T_FP64   # the tree's adjoint is FP64
         self.n, self.steps, self.checkpoint = int(n), int(steps), int(checkpoint)
         self.dev = torch.device("cuda", device)
         self.ctx = P.p3t_create(self.params, device)
@@ -65,7 +75,19 @@ class SoftKDK:
         return P.State(X[0], X[1], X[2], V[0], V[1], V[2], m, r_out, self._rs)
 
     def _force(self, st: P.State):
-        P.p3t_soft_force_direct(self.ctx, st, self.acc)
+        if self.force == "tree":
+            P.p3t_build_tree(self.ctx, st, False)
+            P.p3t_soft_force(self.ctx, st, self.acc)
+        else:
+            P.p3t_soft_force_direct(self.ctx, st, self.acc)
+
+    def _vjp(self, st: P.State, h, lv, lx, gm):
+        """h lam^T da/d(x, m) of the soft force at st, added to (lx, gm)."""
+        if self.force == "tree":
+            P.p3t_build_tree(self.ctx, st, False)
+            P.p3t_soft_force_vjp_tree(self.ctx, st, h, lv, lx, gm)
+        else:
+            P.p3t_soft_force_vjp(self.ctx, st, h, lv, lx, gm)
 
     def _run(self, X, V, m, r_out, k0: int, k1: int, keep=None, have_force=False):
         """Steps k0..k1-1 in place on (X, V); with ``keep`` a list, appends
@@ -84,8 +106,13 @@ class SoftKDK:
             P.p3t_kick(self.ctx, st, self.acc, h)
 
     # ---- sweeps --------------------------------------------------------------
-    def forward(self, x0, v0, m, r_out):
-        """Returns (x_N, v_N, tape); the tape holds the checkpoints."""
+    def forward(self, x0, v0, m, r_out, r_search=None):
+        """Returns (x_N, v_N, tape); the tape holds the checkpoints.  The tree
+        force needs the frozen search radii as well (``r_search``)."""
+        if self.force == "tree":
+            if r_search is None:
+                raise ValueError("the tree force needs r_search")
+            self._rs = r_search.detach().contiguous()
         for t, shape in ((x0, (3, self.n)), (v0, (3, self.n)), (m, (self.n,)),
                          (r_out, (self.n,))):
             if tuple(t.shape) != shape or t.dtype != torch.float64 or t.device != self.dev:
@@ -107,7 +134,7 @@ class SoftKDK:
         lv = lam_v.detach().clone().contiguous()
         gm = torch.zeros(self.n, dtype=torch.float64, device=self.dev)
         st = self._state(tape["xN"], tape["vN"], m, r_out)
-        P.p3t_soft_force_vjp(self.ctx, st, h, lv, lx, gm)
+        self._vjp(st, h, lv, lx, gm)
         for k0, Xc, Vc in reversed(tape["checkpoints"]):
             k1 = min(self.steps, k0 + self.checkpoint)
             keep = []
@@ -116,7 +143,7 @@ class SoftKDK:
                 Xk, Vk = keep[k - k0]
                 st = self._state(Xk, Vk, m, r_out)
                 P.p3t_kepler_vjp(self.ctx, st, dt, lx, lv)
-                P.p3t_soft_force_vjp(self.ctx, st, h if k == 0 else dt, lv, lx, gm)
+                self._vjp(st, h if k == 0 else dt, lv, lx, gm)
         return lx, lv, gm
 
     def status(self):
@@ -127,8 +154,8 @@ class SoftKDK:
 
 class _KDK(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, x0, v0, m, r_out, runner):
-        xN, vN, tape = runner.forward(x0, v0, m, r_out)
+    def forward(ctx, x0, v0, m, r_out, runner, r_search):
+        xN, vN, tape = runner.forward(x0, v0, m, r_out, r_search)
         ctx.runner, ctx.tape = runner, tape
         return xN, vN
 
@@ -137,16 +164,17 @@ class _KDK(torch.autograd.Function):
         r = ctx.runner
         z = torch.zeros(3, r.n, dtype=torch.float64, device=r.dev)
         gx0, gv0, gm = r.backward(ctx.tape, z if gx is None else gx, z if gv is None else gv)
-        return gx0, gv0, gm, None, None
+        return gx0, gv0, gm, None, None, None
 
 
-def soft_kdk(x0, v0, m, r_out, runner: SoftKDK):
-    """(x_N, v_N) of the rollout, differentiable in x0, v0 and m (r_out frozen)."""
-    return _KDK.apply(x0, v0, m, r_out, runner)
+def soft_kdk(x0, v0, m, r_out, runner: SoftKDK, r_search=None):
+    """(x_N, v_N) of the rollout, differentiable in x0, v0 and m (radii frozen)."""
+    return _KDK.apply(x0, v0, m, r_out, runner, r_search)
 
 
-def cutoffs(params: P.Params, x0, v0, m, device: int = 0):
-    """Cut-off radii of the initial state, to be held fixed."""
+def cutoffs(params: P.Params, x0, v0, m, device: int = 0, with_search: bool = False):
+    """Cut-off radii of the initial state, to be held fixed (and the search
+    radii as well with ``with_search``: the tree force needs both)."""
     n = m.numel()
     ro = torch.zeros(n, dtype=torch.float64, device=m.device)
     rs = torch.zeros(n, dtype=torch.float64, device=m.device)
@@ -158,4 +186,4 @@ def cutoffs(params: P.Params, x0, v0, m, device: int = 0):
         torch.cuda.synchronize(m.device)
     finally:
         P.p3t_destroy(ctx)
-    return ro
+    return (ro, rs) if with_search else ro

@@ -89,6 +89,8 @@ void free_particle_buffers(p3t_ctx *c) {
   dfree(c->hw); dfree(c->ht); dfree(c->hl);
   dfree(c->coll_ent); dfree(c->coll_rec); dfree(c->coll_rec_e); dfree(c->coll_esoft);
   dfree(c->coll_slot); dfree(c->scan_state);
+  dfree(c->nadj);
+  c->nadj_cap = 0;
   c->scan_words = 0;
   c->cap = 0;
   c->have_tree = c->have_cand = false;
@@ -431,6 +433,21 @@ int p3t_soft_force_vjp(p3t_ctx *c, const p3t_particles *p, double h, const doubl
   int rc = direct_scratch(c, p->n);
   if (rc) return rc;
   return p3t_run_soft_force_vjp(c, p, h, lx, ly, lz, gx, gy, gz, gm, (cudaStream_t)stream);
+}
+
+int p3t_soft_force_vjp_tree(p3t_ctx *c, const p3t_particles *p, double h, const double *lx,
+                            const double *ly, const double *lz, double *gx, double *gy,
+                            double *gz, double *gm, void *stream) {
+  if (!c || !particles_ok(p) || !segments_ok(c, p)) return P3T_ERR_INVALID;
+  if (p->n == 0) return P3T_OK;
+  if (!lx || !ly || !lz || !gx || !gy || !gz || !gm) return P3T_ERR_INVALID;
+  if (c->prm.precision != P3T_FP64 || !c->have_tree || p->n != c->last_n) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  if (c->nadj_cap < c->node_cap) {
+    if (!dalloc(c->nadj, 10 * c->node_cap)) return P3T_ERR_CUDA;
+    c->nadj_cap = c->node_cap;
+  }
+  return p3t_run_soft_force_vjp_tree(c, p, h, lx, ly, lz, gx, gy, gz, gm, (cudaStream_t)stream);
 }
 
 int p3t_kepler_vjp(p3t_ctx *c, const p3t_particles *p, double dt, double *lx, double *ly,

@@ -279,6 +279,11 @@ struct p3t_ctx {
   // energy
   double *epart = nullptr;                 // per-block partial sums
 
+  // adjoint of the tree walk: per node dL/dc, dL/dM, dL/dQ (allocated on
+  // the first call, node_cap entries of 10)
+  double *nadj = nullptr;
+  int64_t nadj_cap = 0;
+
   // auxiliary streams and events for work that can overlap inside a call
   cudaStream_t aux[2] = {nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
@@ -349,3 +354,7 @@ int p3t_run_soft_force_vjp(p3t_ctx *c, const p3t_particles *p, double h, const d
                            double *gz, double *gm, cudaStream_t s);
 int p3t_run_kepler_vjp(p3t_ctx *c, const p3t_particles *p, double dt, double *lx, double *ly,
                        double *lz, double *lvx, double *lvy, double *lvz, cudaStream_t s);
+int p3t_run_soft_force_vjp_tree(p3t_ctx *c, const p3t_particles *p, double s,
+                                const double *lx, const double *ly, const double *lz,
+                                double *gx, double *gy, double *gz, double *gm,
+                                cudaStream_t st);

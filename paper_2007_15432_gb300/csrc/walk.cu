@@ -856,6 +856,228 @@ __global__ void __launch_bounds__(kWarps * 32, MIXED ? P3T_WALK_MINB_MIXED : 1)
   }
 }
 
+// ---- adjoint of the tree walk (FP64 path) -----------------------------------
+// The vector-Jacobian product of the soft force of Eq. softforce as the tree
+// gives it, with the tree and the interaction lists held fixed: a second walk
+// of the same tree from the same group boxes meets the same lists.  With
+// L = sum_i lam_i . a_i (lam_i = s times the caller's velocity adjoint):
+//   p-p term a_i += -G m_j K(y) r / r^3, r = x_i - x_j, y = r / r_out,ij:
+//     dL/dx_i += J lam_i, dL/dx_j -= J lam_i, dL/dm_j += lam_i . (-G K r / r^3),
+//     J = -G m_j (phi I + psi r r^T), phi = K / r^3,
+//     psi = K'(y) / (r_out,ij r^4) - 3 K / r^5;
+//   node term a_i += G [-M r / r^3 + Q r / r^5 - (5/2) (r.Q.r) r / r^7],
+//     r = x_i - c: dL/dx_i += g, dL/dc -= g, with g = grad_r (lam_i . a),
+//     and dL/dM, dL/dQ accumulated per node;
+// the node adjoints then reach the member particles through M = sum m_k,
+// c = sum m_k x_k / M, Q = sum m_k (3 d d^T - d^2 I), d = x_k - c (the
+// derivative of Q through c vanishes, as sum m_k d_k = 0).  One warp per
+// target group, one lane per target (lanes past the group idle); the
+// contributions of a walk's targets to one source or node are added by a
+// warp reduction and then to the global sums by FP64 atomics (their order
+// follows the walks' order, so the last bits can differ from run to run).
+struct VjpOut {
+  const double *lx, *ly, *lz;  // velocity adjoints, caller order
+  double s;                    // scale (the kick's time step)
+  double *gx, *gy, *gz, *gm;   // accumulated position and mass adjoints, caller order
+  double *nadj;                // per node: dL/dc (3), dL/dM, dL/dQ (xx yy zz xy xz yz)
+};
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+struct VjpEval {
+  const WalkArgs &a;
+  const VjpOut &o;
+  void *stage;
+  bool valid;
+  int32_t self;            // sorted index of the lane's target
+  double x, y, z, ro;      // target
+  double lx, ly, lz;       // s lam
+  double gx, gy, gz;       // dL/dx of the target, this walk
+  __device__ void nodes(const int32_t *list, int n) {
+    Mom64 *S = reinterpret_cast<Mom64 *>(stage);
+    int32_t *ids = reinterpret_cast<int32_t *>(S + 32);
+    const int lane = threadIdx.x & 31;
+    if (lane < n) {
+      S[lane] = a.mom64[list[lane]];
+      ids[lane] = list[lane];
+    }
+    __syncwarp();
+    for (int q = 0; q < n; ++q) {
+      const Mom64 &m = S[q];
+      double c[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+      if (valid) {
+        const double rx = x - m.cx, ry = y - m.cy, rz = z - m.cz;
+        const double r2 = rx * rx + ry * ry + rz * rz;
+        const double ri = 1.0 / sqrt(r2);
+        const double ri2 = ri * ri, ri3 = ri2 * ri, ri5 = ri3 * ri2, ri7 = ri5 * ri2,
+                     ri9 = ri7 * ri2;
+        const double qx = m.qxx * rx + m.qxy * ry + m.qxz * rz;
+        const double qy = m.qxy * rx + m.qyy * ry + m.qyz * rz;
+        const double qz = m.qxz * rx + m.qyz * ry + m.qzz * rz;
+        const double q2 = rx * qx + ry * qy + rz * qz;           // r.Q.r
+        const double lr = lx * rx + ly * ry + lz * rz;           // lam.r
+        const double lq = lx * qx + ly * qy + lz * qz;           // lam.Q r
+        const double Ql_x = m.qxx * lx + m.qxy * ly + m.qxz * lz;  // Q lam
+        const double Ql_y = m.qxy * lx + m.qyy * ly + m.qyz * lz;
+        const double Ql_z = m.qxz * lx + m.qyz * ly + m.qzz * lz;
+        const double G = a.G;
+        // g = grad_r lam.a (a the node term)
+        const double cr = G * (3.0 * m.M * lr * ri5 - 5.0 * lq * ri7 + 17.5 * q2 * lr * ri9);
+        const double cl = G * (-m.M * ri3 - 2.5 * q2 * ri7);
+        const double cQ = G * ri5, cQr = -5.0 * G * lr * ri7;
+        const double g0 = cl * lx + cr * rx + cQ * Ql_x + cQr * qx;
+        const double g1 = cl * ly + cr * ry + cQ * Ql_y + cQr * qy;
+        const double g2 = cl * lz + cr * rz + cQ * Ql_z + cQr * qz;
+        gx += g0; gy += g1; gz += g2;
+        c[0] = -g0; c[1] = -g1; c[2] = -g2;
+        c[3] = -G * lr * ri3;
+        // d(lam.a)/dQ per stored component (an off-diagonal one stands for ab and ba)
+        const double u = G * ri5, v = -2.5 * G * lr * ri7;
+        c[4] = u * lx * rx + v * rx * rx;
+        c[5] = u * ly * ry + v * ry * ry;
+        c[6] = u * lz * rz + v * rz * rz;
+        c[7] = u * (lx * ry + ly * rx) + 2.0 * v * rx * ry;
+        c[8] = u * (lx * rz + lz * rx) + 2.0 * v * rx * rz;
+        c[9] = u * (ly * rz + lz * ry) + 2.0 * v * ry * rz;
+      }
+      for (int k = 0; k < 10; ++k) c[k] = warp_sum_d(c[k]);
+      if (lane == 0)
+        for (int k = 0; k < 10; ++k) atomicAdd(&o.nadj[10 * (int64_t)ids[q] + k], c[k]);
+    }
+    __syncwarp();
+  }
+  __device__ void pp(const int32_t *list, int n) {
+    double *S = reinterpret_cast<double *>(stage);  // x, y, z, m, ro of 32 sources
+    int32_t *ids = reinterpret_cast<int32_t *>(S + 5 * 32);
+    const int lane = threadIdx.x & 31;
+    if (lane < n) {
+      const int32_t j = list[lane];
+      S[lane] = a.sx[j]; S[32 + lane] = a.sy[j]; S[64 + lane] = a.sz[j];
+      S[96 + lane] = a.sm[j]; S[128 + lane] = a.sro[j];
+      ids[lane] = j;
+    }
+    __syncwarp();
+    const double i1mg = 1.0 / (1.0 - a.gamma);
+    for (int q = 0; q < n; ++q) {
+      double c[4] = {0, 0, 0, 0};
+      if (valid && ids[q] != self) {
+        const double rx = x - S[q], ry = y - S[32 + q], rz = z - S[64 + q];
+        const double mj = S[96 + q];
+        const double r2 = rx * rx + ry * ry + rz * rz;
+        const double r = sqrt(r2);
+        const double roij = fmax(ro, S[128 + q]);
+        const double yv = r / roij;
+        double K = 0.0, dK = 0.0;
+        if (yv >= 1.0) {
+          K = 1.0;
+        } else if (yv > a.gamma) {
+          const double xs = (yv - a.gamma) * i1mg;
+          const double x2 = xs * xs, x3 = x2 * xs, us = 1.0 - xs;
+          K = x2 * x2 * (35.0 - 84.0 * xs + 70.0 * x2 - 20.0 * x3);
+          dK = 140.0 * x3 * us * us * us * i1mg;
+        }
+        if (K != 0.0 || dK != 0.0) {
+          const double r3 = r2 * r, r4 = r2 * r2, r5 = r4 * r;
+          const double phi = K / r3, psi = dK / (roij * r4) - 3.0 * K / r5;
+          const double lr = lx * rx + ly * ry + lz * rz;
+          const double f = -a.G * mj;
+          const double j0 = f * (phi * lx + psi * lr * rx);
+          const double j1 = f * (phi * ly + psi * lr * ry);
+          const double j2 = f * (phi * lz + psi * lr * rz);
+          gx += j0; gy += j1; gz += j2;
+          c[0] = -j0; c[1] = -j1; c[2] = -j2;
+          c[3] = -a.G * phi * lr;
+        }
+      }
+      for (int k = 0; k < 4; ++k) c[k] = warp_sum_d(c[k]);
+      if (lane == 0) {
+        const int32_t i = a.idx[ids[q]];
+        atomicAdd(&o.gx[i], c[0]); atomicAdd(&o.gy[i], c[1]); atomicAdd(&o.gz[i], c[2]);
+        atomicAdd(&o.gm[i], c[3]);
+      }
+    }
+    __syncwarp();
+  }
+};
+
+__global__ void __launch_bounds__(kWarps * 32) k_walk_vjp(const WalkArgs a, const VjpOut o) {
+  __shared__ int32_t s_pp[kWarps][kPPCap];
+  __shared__ int32_t s_nd[kWarps][kNDCap];
+  __shared__ int32_t s_big[kWarps][kBigCap];
+  // a batch of 32 FP64 moments (or sources) and their 32 ids
+  __shared__ __align__(16) unsigned char s_stage[kWarps][32 * sizeof(Mom64) + 32 * 4];
+  __shared__ int64_t s_bh[P3T_BITS + 1];
+  if (threadIdx.x <= P3T_BITS) s_bh[threadIdx.x] = a.bh[threadIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t *stack = a.stack + ((int64_t)blockIdx.x * kWarps + w) * a.stack_cap;
+  const int64_t ngroup = *a.d_nleaf;
+  const int64_t round_limit = *a.d_nnode + 2;
+  for (;;) {
+    int64_t g = 0;
+    if (lane == 0) g = atomicAdd(reinterpret_cast<unsigned long long *>(a.cursor), 1ull);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= ngroup) break;
+    if (*(volatile int32_t *)&a.st->code != 0) break;
+    const TreeNode &G = a.node[a.leaf_list[g]];
+    GroupBox gb;
+    gb.load(G);
+    bool ok = true;
+    for (int32_t tb = G.first; tb < G.first + G.count && ok; tb += 32) {
+      const bool valid = tb + lane < G.first + G.count;
+      VjpEval ev{a, o, s_stage[w], valid, tb + lane, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0};
+      if (valid) {
+        const int32_t t = tb + lane, i = a.idx[t];
+        ev.x = a.sx[t]; ev.y = a.sy[t]; ev.z = a.sz[t]; ev.ro = a.sro[t];
+        ev.lx = o.s * o.lx[i]; ev.ly = o.s * o.ly[i]; ev.lz = o.s * o.lz[i];
+      }
+      ok = traverse(a, gb, G.first, stack, s_pp[w], s_nd[w], s_big[w], s_bh, round_limit, ev);
+      if (ok && valid) {
+        const int32_t i = a.idx[tb + lane];
+        atomicAdd(&o.gx[i], ev.gx); atomicAdd(&o.gy[i], ev.gy); atomicAdd(&o.gz[i], ev.gz);
+      }
+    }
+    if (!ok) break;
+  }
+}
+
+// node adjoints to the member particles: each particle climbs from its leaf
+// to the root (fixed order)
+__global__ void k_node_adjoint(const int64_t *d_nleaf, const int32_t *leaf_list,
+                               const TreeNode *node, const Mom64 *mom, const double *nadj,
+                               const double *sx, const double *sy, const double *sz,
+                               const double *sm, const int32_t *idx, double *gx, double *gy,
+                               double *gz, double *gm) {
+  const int64_t nleaf = *d_nleaf;
+  for (int64_t b = blockIdx.x; b < nleaf; b += gridDim.x) {
+    const TreeNode &L = node[leaf_list[b]];
+    for (int32_t k = L.first + threadIdx.x; k < L.first + L.count; k += blockDim.x) {
+      const double xk = sx[k], yk = sy[k], zk = sz[k], mk = sm[k];
+      double ax = 0.0, ay = 0.0, az = 0.0, am = 0.0;
+      for (int32_t n = leaf_list[b]; n >= 0; n = node[n].parent) {
+        const double *A = nadj + 10 * (int64_t)n;
+        const Mom64 &M = mom[n];
+        const double dx = xk - M.cx, dy = yk - M.cy, dz = zk - M.cz;
+        const double d2 = dx * dx + dy * dy + dz * dz;
+        const double tr = A[4] + A[5] + A[6];
+        // dQ/dx_k and dQ/dm_k with the stored components (xx yy zz xy xz yz)
+        ax += mk / M.M * A[0] + mk * (6.0 * A[4] * dx - 2.0 * tr * dx + 3.0 * (A[7] * dy + A[8] * dz));
+        ay += mk / M.M * A[1] + mk * (6.0 * A[5] * dy - 2.0 * tr * dy + 3.0 * (A[7] * dx + A[9] * dz));
+        az += mk / M.M * A[2] + mk * (6.0 * A[6] * dz - 2.0 * tr * dz + 3.0 * (A[8] * dx + A[9] * dy));
+        am += A[3] + (A[0] * dx + A[1] * dy + A[2] * dz) / M.M +
+              A[4] * (3.0 * dx * dx - d2) + A[5] * (3.0 * dy * dy - d2) +
+              A[6] * (3.0 * dz * dz - d2) +
+              3.0 * (A[7] * dx * dy + A[8] * dx * dz + A[9] * dy * dz);
+      }
+      const int32_t i = idx[k];
+      gx[i] += ax; gy[i] += ay; gz[i] += az; gm[i] += am;
+    }
+  }
+}
+
 __global__ void k_walk_prep(int64_t *cursor, unsigned long long *cand_count,
                             unsigned long long *counts) {
   *cursor = 0;
@@ -916,6 +1138,48 @@ int64_t bh_threshold(double theta, int level) {
 // blocks of 4 warps resident per SM: the mixed walk is compiled for 6 (80
 // registers; 30.5 KB of shared memory a block)
 int p3t_walk_blocks_per_sm() { return P3T_WALK_MINB_MIXED; }
+
+// the walk's arguments for the tree of context c built from particles p
+static WalkArgs walk_args(p3t_ctx *c, const p3t_particles *p) {
+  WalkArgs a;
+  a.node = c->node; a.mom64 = c->mom64; a.mom32 = c->mom32;
+  a.leaf_list = c->group_list; a.d_nleaf = &c->counters[15]; a.d_nnode = &c->counters[3];
+  a.sx = c->sx; a.sy = c->sy; a.sz = c->sz; a.sm = c->sm; a.sro = c->sro; a.srs = c->srs;
+  a.spA = c->spA; a.spB = c->spB; a.srs32 = c->srs32; a.sml = c->sml;
+  a.idx = c->idx;
+  a.ax = a.ay = a.az = nullptr;
+  a.stack = c->walk_stack; a.stack_cap = c->stack_cap;
+  a.cand_i = c->cand_i; a.cand_j = c->cand_j; a.cand_cap = c->cand_cap;
+  a.cand_count = reinterpret_cast<unsigned long long *>(&c->counters[8]);
+  a.counts = nullptr;
+  a.cursor = &c->counters[12];
+  a.st = c->status;
+  a.seg = SegView{c->seg_off, (int)c->nseg, p->n};
+  a.refine_cf = 32.0f;
+  a.G = c->prm.G;
+  a.gamma = c->prm.gamma;
+  a.inv1mg_f = (float)(1.0 / (1.0 - c->prm.gamma));
+  a.mgi_f = (float)(-c->prm.gamma / (1.0 - c->prm.gamma));
+  for (int l = 0; l <= P3T_BITS; ++l) a.bh[l] = bh_threshold(c->prm.theta, l);
+  return a;
+}
+
+int p3t_run_soft_force_vjp_tree(p3t_ctx *c, const p3t_particles *p, double s,
+                                const double *lx, const double *ly, const double *lz,
+                                double *gx, double *gy, double *gz, double *gm,
+                                cudaStream_t st) {
+  WalkArgs a = walk_args(c, p);
+  VjpOut o{lx, ly, lz, s, gx, gy, gz, gm, c->nadj};
+  P3T_CUDA_TRY(cudaMemsetAsync(c->nadj, 0, sizeof(double) * 10 * c->node_cap, st));
+  P3T_CUDA_TRY(cudaMemsetAsync(a.cursor, 0, sizeof(int64_t), st));
+  const unsigned blocks = (unsigned)(c->walk_warps / kWarps);
+  k_walk_vjp<<<blocks, kWarps * 32, 0, st>>>(a, o);
+  k_node_adjoint<<<(unsigned)(c->num_sms * 8), 128, 0, st>>>(
+      &c->counters[2], c->leaf_list, c->node, c->mom64, c->nadj, c->sx, c->sy, c->sz, c->sm,
+      c->idx, gx, gy, gz, gm);
+  p3t_note_launches(3);
+  return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
+}
 
 int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
                        double *ay, double *az, uint64_t *counts,

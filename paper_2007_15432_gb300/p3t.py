@@ -106,6 +106,7 @@ _sig = {
     "p3t_soft_force_direct": (C.c_int, [_CTX, C.POINTER(Particles), _vp, _vp, _vp, _vp]),
     "p3t_soft_force_vjp": (C.c_int, [_CTX, C.POINTER(Particles), C.c_double] + [_vp] * 8),
     "p3t_kepler_vjp": (C.c_int, [_CTX, C.POINTER(Particles), C.c_double] + [_vp] * 7),
+    "p3t_soft_force_vjp_tree": (C.c_int, [_CTX, C.POINTER(Particles), C.c_double] + [_vp] * 8),
     "p3t_status": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
     "p3t_set_diag": (C.c_int, [_CTX, C.POINTER(Diag)]),
     "p3t_set_tuning": (C.c_int, [_CTX, C.POINTER(Tuning)]),
@@ -347,6 +348,16 @@ def p3t_soft_force_vjp(ctx, st: State, h: float, lam: torch.Tensor, gx: torch.Te
     _check(_lib.p3t_soft_force_vjp(ctx, C.byref(p), float(h), _ptr(lam[0]), _ptr(lam[1]),
                                    _ptr(lam[2]), _ptr(gx[0]), _ptr(gx[1]), _ptr(gx[2]), _ptr(gm),
                                    _stream(stream)), "p3t_soft_force_vjp")
+
+
+def p3t_soft_force_vjp_tree(ctx, st: State, h: float, lam: torch.Tensor, gx: torch.Tensor,
+                            gm: torch.Tensor, stream=None) -> None:
+    """Adds h * lam^T da/dx and h * lam^T da/dm for the TREE soft force of the
+    context's tree (built from st, FP64 context), lists held fixed."""
+    p = st.particles()
+    _check(_lib.p3t_soft_force_vjp_tree(ctx, C.byref(p), float(h), _ptr(lam[0]), _ptr(lam[1]),
+                                        _ptr(lam[2]), _ptr(gx[0]), _ptr(gx[1]), _ptr(gx[2]),
+                                        _ptr(gm), _stream(stream)), "p3t_soft_force_vjp_tree")
 
 
 def p3t_kepler_vjp(ctx, st: State, dt: float, lam_x: torch.Tensor, lam_v: torch.Tensor,

@@ -173,3 +173,60 @@ def test_changeover_derivative_term_matters_at_these_sizes():
     w = m[:, None, None] * lam[None, :, :] - m[None, :, None] * lam[:, None, :]
     g_phi = (phi[:, :, None] * w).sum(1)
     assert torch.max(torch.abs(g - g_phi)) > 1e-3 * torch.max(torch.abs(g))
+
+
+def test_tree_force_from_lists_equals_oracle_walk(orc):
+    """The adjoint oracle's tree force, rebuilt from the walk's exported
+    interaction lists with the node moments taken from the member particles,
+    equals the C oracle's tree walk (same pairs, same nodes, force <= 1e-13)."""
+    from oracle import adjoint_oracle as AO
+    s = disks.adjoint_disk(3000)
+    for gs in (0, 64):
+        p = orc.Params(theta=0.5, group_size=gs)
+        ro, rs, _, _ = orc.cutoffs(s, p)
+        L = orc.tree_lists(s, ro, rs, p)
+        ref = orc.tree_soft(s, ro, rs, p)
+        x = torch.tensor(np.stack([s["x"], s["y"], s["z"]], 1))
+        a = AO.tree_force(x, torch.tensor(s["m"]), torch.tensor(ro), L).numpy()
+        tp, sp, tn, nd = AO.list_pairs(L)
+        assert len(tp) == ref.n_pp and len(tn) == ref.n_pnode
+        err = np.linalg.norm(a - ref.acc, axis=1) / np.linalg.norm(ref.acc, axis=1)
+        assert err.max() < 1e-13
+
+
+def test_tree_force_gradient_central_differences(orc):
+    """torch.autograd through the tree force with the lists held fixed
+    against central differences in positions and masses."""
+    from oracle import adjoint_oracle as AO
+    s = disks.adjoint_disk(600)
+    p = orc.Params(theta=0.5, group_size=32)
+    ro, rs, _, _ = orc.cutoffs(s, p)
+    L = orc.tree_lists(s, ro, rs, p)
+    x0 = torch.tensor(np.stack([s["x"], s["y"], s["z"]], 1))
+    m0 = torch.tensor(s["m"])
+    lam = torch.tensor(np.random.default_rng(5).normal(size=(600, 3)))
+    x = x0.clone().requires_grad_(True)
+    m = m0.clone().requires_grad_(True)
+    (AO.tree_force(x, m, torch.tensor(ro), L) * lam).sum().backward()
+
+    def f(xx, mm):
+        return float((AO.tree_force(xx, mm, torch.tensor(ro), L) * lam).sum())
+    # rounding noise of a central difference of the sum: ~ eps sum|terms| / h
+    scale = float((AO.tree_force(x0, m0, torch.tensor(ro), L) * lam).abs().sum())
+    rng = np.random.default_rng(6)
+    for i in rng.choice(600, 4, replace=False):
+        for c in range(3):
+            h = 1e-7 * abs(float(x0[i, c]))
+            xp, xm = x0.clone(), x0.clone()
+            xp[i, c] += h
+            xm[i, c] -= h
+            fd = (f(xp, m0) - f(xm, m0)) / (2 * h)
+            noise = 64 * 2.2e-16 * scale / h
+            assert abs(fd - float(x.grad[i, c])) <= 1e-6 * abs(float(x.grad[i, c])) + noise
+        h = 1e-4 * float(m0[i])
+        mp, mm_ = m0.clone(), m0.clone()
+        mp[i] += h
+        mm_[i] -= h
+        fd = (f(x0, mp) - f(x0, mm_)) / (2 * h)
+        noise = 64 * 2.2e-16 * scale / h
+        assert abs(fd - float(m.grad[i])) <= 1e-6 * abs(float(m.grad[i])) + noise
