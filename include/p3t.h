@@ -353,6 +353,25 @@ int p3t_soft_force_vjp_tree(p3t_ctx *ctx, const p3t_particles *p, double h, cons
                             const double *ly, const double *lz, double *gx, double *gy,
                             double *gz, double *gm, void *stream);
 
+/* Adjoint of the hard part of a soft step (the paper has no counterpart;
+ * procedure step 5 with the neighbour clusters and the block schedule held
+ * fixed): on entry lx..lvz hold the adjoint of the state after
+ * p3t_hard_step(ctx, p, cl, dt), on return the adjoint of the state p holds
+ * (the state BEFORE the hard step), and h-independent mass terms dL/dm of
+ * the cluster members are ADDED to gm.  Isolated particles: the Kepler
+ * drift's adjoint (as p3t_kepler_vjp); members of clusters of >= 2: the
+ * derivative of the Hermite-4 block-step integration through forward-mode
+ * tangents (one per member state component and mass), each integration in
+ * plain FP64 with its step decisions taken on the values, so with the
+ * schedule fixed.  Clusters of more than 16 members are not handled
+ * (P3T_ERR_CAPACITY recorded).  No collisions (f_radius must be 0, else
+ * P3T_ERR_INVALID).  cl: the clusters the forward hard step used.  Device
+ * arrays, n each, caller order.  The first call allocates a buffer (call it
+ * before any capture). */
+int p3t_hard_step_vjp(p3t_ctx *ctx, const p3t_particles *p, const p3t_clusters *cl, double dt,
+                      double *lx, double *ly, double *lz, double *lvx, double *lvy, double *lvz,
+                      double *gm, void *stream);
+
 /* The adjoint of the Kepler drift of every particle of p by dt
  * (the drift's map, mu = G M_*): on entry lx..lvz hold the adjoint of the state
  * after the drift, on return the adjoint of the state before it (Phi^T lam,

@@ -21,9 +21,14 @@ states the forward:
   * one step = kick, drift, kick; loss = sum |x_final - x_target|^2;
   * the tree form of the soft force (``tree_force``): the same sum over the
     interactions the tree walk evaluates, its lists (from the C oracle) held
-    fixed, node moments from the member particles.
+    fixed, node moments from the member particles;
+  * the paper's hard part (``hermite_cluster``, ``rollout_p3t``): neighbour
+    clusters integrated by the Hermite scheme of the C oracle written in
+    PyTorch, its block schedule decided on detached values.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 import torch
@@ -177,6 +182,169 @@ def rollout_tree(x0, v0, m, r_out, r_search, steps, params, dt=1.0 / 64):
         v = v + h * a
         x, v = kepler_drift(x, v, dt, params.G * params.m_star)
         a = force(x)
+        v = v + h * a
+    return x, v
+
+
+def _level(dt_des, dt, prev, t, kmax=40):
+    """Block level: the largest dt / 2^l not above dt_des (l <= 40), at most
+    twice the previous step, commensurate with the time t (units dt/2^40)."""
+    lvl = 0
+    while lvl < kmax and math.ldexp(dt, -lvl) > dt_des:
+        lvl += 1
+    if math.ldexp(dt, -lvl) > dt_des:
+        raise ValueError("Hermite step below dt / 2^40")
+    lvl = max(lvl, prev - 1)
+    while lvl < kmax and t % (1 << (kmax - lvl)) != 0:
+        lvl += 1
+    return lvl
+
+
+def _norm(u):
+    """|u| of a (3,) tensor as a number (a step decision: no gradient)."""
+    u = u.detach()
+    return float(torch.sqrt((u * u).sum()))
+
+
+def _hard_acc_jerk(x, v, m, ro, k, G, m_star, gamma):
+    """Hard force and jerk of member k (Eq. hardforce): the star and the
+    (1 - K) part of every other member, jerk with dK/dt; x, v: lists of (3,)
+    tensors; the sum over members in ascending order."""
+    r2 = x[k][0] * x[k][0] + x[k][1] * x[k][1] + x[k][2] * x[k][2]
+    r = torch.sqrt(r2)
+    r3 = r2 * r
+    r5 = r3 * r2
+    rv = x[k][0] * v[k][0] + x[k][1] * v[k][1] + x[k][2] * v[k][2]
+    GM = G * m_star
+    a = -(GM * x[k] / r3)
+    j = -(GM * (v[k] / r3 - 3.0 * rv * x[k] / r5))
+    for q in range(len(x)):
+        if q == k:
+            continue
+        rr, uu = x[k] - x[q], v[k] - v[q]
+        r2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2]
+        if float(r2.detach()) == 0.0:
+            continue
+        r = torch.sqrt(r2)
+        roij = max(float(ro[k]), float(ro[q]))
+        y = r / roij
+        yv = float(y.detach())
+        if yv >= 1.0:
+            continue
+        if yv > gamma:
+            xs = (y - gamma) / (1.0 - gamma)
+            x2 = xs * xs
+            x3, x4, us = x2 * xs, x2 * x2, 1.0 - xs
+            w = 1.0 - x4 * (35.0 - 84.0 * xs + 70.0 * x2 - 20.0 * x3)
+            dK = 140.0 * xs * xs * xs * us * us * us / (1.0 - gamma)
+        else:
+            w, dK = 1.0, 0.0
+        rv = rr[0] * uu[0] + rr[1] * uu[1] + rr[2] * uu[2]
+        r3 = r2 * r
+        r5 = r3 * r2
+        dw = dK * rv / (r * roij)
+        Gm = G * m[q]
+        a = a - Gm * w * rr / r3
+        j = j - Gm * (w * (uu / r3 - 3.0 * rv * rr / r5) - dw * rr / r3)
+    return a, j
+
+
+def hermite_cluster(x0, v0, m, ro, dt, eta, eta0, G=1.0, m_star=1.0, gamma=0.1):
+    """Fourth-order Hermite with block individual steps over [0, dt] for one
+    cluster (Sec. 2.1.2; the predictor to the jerk, the Makino & Aarseth
+    corrector, the Aarseth step, the first step eta0 |a|/|j|), differentiable
+    in (x0, v0, m): the step decisions are taken on detached values, so the
+    gradient is that of the integration with its schedule fixed.  x0, v0:
+    (nc, 3); m: (nc,); ro: cut-off radii (numbers)."""
+    nc = x0.shape[0]
+    T, unit = 1 << 40, math.ldexp(dt, -40)
+    x = [x0[k] for k in range(nc)]
+    v = [v0[k] for k in range(nc)]
+    aj = [_hard_acc_jerk(x, v, m, ro, k, G, m_star, gamma) for k in range(nc)]
+    a = [q[0] for q in aj]
+    jk = [q[1] for q in aj]
+    t = [0] * nc
+    lvl = []
+    for k in range(nc):
+        jn = _norm(jk[k])
+        d0 = eta0 * _norm(a[k]) / jn if jn > 0 else dt
+        lvl.append(_level(d0, dt, 0, 0))
+    while min(t) < T:
+        tn = min(t[k] + (T >> lvl[k]) for k in range(nc))
+        px, pv, act = [], [], []
+        for k in range(nc):
+            D = (tn - t[k]) * unit
+            D2 = D * D
+            D3 = D2 * D
+            px.append(x[k] + v[k] * D + a[k] * D2 / 2.0 + jk[k] * D3 / 6.0)
+            pv.append(v[k] + a[k] * D + jk[k] * D2 / 2.0)
+            act.append(t[k] + (T >> lvl[k]) == tn)
+        new = {k: _hard_acc_jerk(px, pv, m, ro, k, G, m_star, gamma) for k in range(nc) if act[k]}
+        for k in range(nc):
+            if not act[k]:
+                continue
+            a1, j1 = new[k]
+            D = (T >> lvl[k]) * unit
+            D2 = D * D
+            D3 = D2 * D
+            D4 = D3 * D
+            D5 = D4 * D
+            da = a[k] - a1
+            A2 = (-6.0 * da - D * (4.0 * jk[k] + 2.0 * j1)) / D2
+            A3 = (12.0 * da + 6.0 * D * (jk[k] + j1)) / D3
+            A2e = A2 + D * A3
+            x[k] = px[k] + A2 * D4 / 24.0 + A3 * D5 / 120.0
+            v[k] = pv[k] + A2 * D3 / 6.0 + A3 * D4 / 24.0
+            a[k], jk[k] = a1, j1
+            an, jn, a2n, a3n = _norm(a1), _norm(j1), _norm(A2e), _norm(A3)
+            num, den = an * a2n + jn * jn, jn * a3n + a2n * a2n
+            t[k] = tn
+            lvl[k] = _level(math.sqrt(eta * num / den) if den > 0 else dt, dt, lvl[k], tn)
+    return torch.stack(x), torch.stack(v)
+
+
+def rollout_p3t(x0, v0, m, r_out, r_search, steps, params, dt=1.0 / 64):
+    """The rollout with the paper's hard part: the tree force (lists from the
+    C oracle, held fixed), kick, then every neighbour cluster (from the C
+    oracle's neighbour search at the force evaluation, held fixed)
+    integrated by ``hermite_cluster`` and every isolated particle by the
+    Kepler drift, then the force and the kick; ``params``: the oracle's
+    parameter block."""
+    from oracle import oracle as O
+    G, mu = params.G, params.G * params.m_star
+    ro_np, rs_np = r_out.numpy(), r_search.numpy()
+
+    def state(x, v):
+        xd, vd = x.detach().numpy(), v.detach().numpy()
+        return {"x": xd[:, 0].copy(), "y": xd[:, 1].copy(), "z": xd[:, 2].copy(),
+                "vx": vd[:, 0].copy(), "vy": vd[:, 1].copy(), "vz": vd[:, 2].copy(),
+                "m": m.detach().numpy().copy()}
+
+    def force_and_clusters(x, v):
+        s = state(x, v)
+        L = O.tree_lists(s, ro_np, rs_np, params)
+        res = O.tree_soft(s, ro_np, rs_np, params)
+        off, idx = O.neighbours_from_candidates(s, ro_np, rs_np, params, res.cand_i, res.cand_j)
+        cl = O.clusters(len(ro_np), off, idx)
+        return tree_force(x, m, r_out, L, G, params.gamma), cl
+
+    h = 0.5 * dt
+    x, v = x0, v0
+    a, cl = force_and_clusters(x, v)
+    for _ in range(steps):
+        v = v + h * a
+        sing = torch.as_tensor(cl.singles, dtype=torch.long)
+        xs, vs = kepler_drift(x[sing], v[sing], dt, mu)
+        xn = torch.zeros_like(x).index_copy(0, sing, xs)
+        vn = torch.zeros_like(v).index_copy(0, sing, vs)
+        for c in range(len(cl.cl_off) - 1):
+            mem = torch.as_tensor(cl.cl_mem[cl.cl_off[c]:cl.cl_off[c + 1]], dtype=torch.long)
+            xc, vc = hermite_cluster(x[mem], v[mem], m[mem], ro_np[mem.numpy()], dt, params.eta,
+                                     params.eta0, G, params.m_star, params.gamma)
+            xn = xn.index_copy(0, mem, xc)
+            vn = vn.index_copy(0, mem, vc)
+        x, v = xn, vn
+        a, cl = force_and_clusters(x, v)
         v = v + h * a
     return x, v
 

@@ -18,7 +18,10 @@ kernels:
     positions x_k with the same velocity adjoint, so the sweep takes one
     soft-force VJP per step (scale dt; h at x_0 and at x_N);
   * the drift's adjoint is Phi^T lam with Phi the Kepler state-transition
-    matrix at the state before the drift (``p3t_kepler_vjp``);
+    matrix at the state before the drift (``p3t_kepler_vjp``), or, with
+    ``hard="p3t"`` (the paper's hard part: neighbour clusters integrated by
+    Hermite, isolated particles by Kepler), the hard step's adjoint with the
+    clusters and block schedule of the forward sweep (``p3t_hard_step_vjp``);
   * states are checkpointed every ``checkpoint`` steps; the backward pass
     recomputes each segment forward from its checkpoint.
 
@@ -40,14 +43,17 @@ class SoftKDK:
     force and its VJP; the tree force and its VJP run in FP64."""
 
     def __init__(self, params: P.Params, n: int, steps: int, checkpoint: int = 8,
-                 device: int = 0, force: str = "direct"):
+                 device: int = 0, force: str = "direct", hard: str = "kepler"):
         if params.f_radius > 0.0:
             raise ValueError("the adjoint rollout has no collisions (f_radius must be 0)")
         if steps < 1 or checkpoint < 1:
             raise ValueError("steps and checkpoint must be >= 1")
         if force not in ("direct", "tree"):
             raise ValueError("force is 'direct' or 'tree'")
-        self.force = force
+        if hard not in ("kepler", "p3t") or (hard == "p3t" and force != "tree"):
+            raise ValueError("hard is 'kepler' or 'p3t' (the latter with the tree force, "
+                             "whose walk gives the neighbour candidates)")
+        self.force, self.hard = force, hard
         self.params = P.Params(**{f[0]: getattr(params, f[0]) for f in P.Params._fields_})
         if force == "tree":
             self.params.precision = P.P3T_FP64   # the tree's adjoint is FP64
@@ -58,6 +64,10 @@ class SoftKDK:
         f64 = dict(dtype=torch.float64, device=self.dev)
         self.acc = torch.zeros(3, self.n, **f64)
         self._rs = torch.zeros(self.n, **f64)
+        if hard == "p3t":
+            self.nb_off = torch.zeros(self.n + 1, dtype=torch.int64, device=self.dev)
+            self.nb_idx = torch.zeros(8 * self.n + 1024, dtype=torch.int32, device=self.dev)
+        self.cl = None      # clusters for the next hard step (views or a copy)
 
     def close(self):
         if self.ctx:
@@ -78,8 +88,22 @@ class SoftKDK:
         if self.force == "tree":
             P.p3t_build_tree(self.ctx, st, False)
             P.p3t_soft_force(self.ctx, st, self.acc)
+            if self.hard == "p3t":   # neighbour clusters of this force (procedure step 7)
+                self.cl = P.p3t_neighbours(self.ctx, st, self.nb_off, self.nb_idx)
         else:
             P.p3t_soft_force_direct(self.ctx, st, self.acc)
+
+    def _copy_clusters(self):
+        """A copy of the current clusters (tensors and a view on them)."""
+        t = P.p3t_copy_clusters(self.ctx, self.cl, self.n)
+        return t, P.Clusters(*[t[k].data_ptr() for k in ("label", "singles", "cl_off",
+                                                          "cl_mem", "counts")])
+
+    def _drift(self, st: P.State):
+        if self.hard == "p3t":
+            P.p3t_hard_step(self.ctx, st, self.cl, self.params.dt_soft)
+        else:
+            P.p3t_kepler_drift(self.ctx, st, self.params.dt_soft)
 
     def _vjp(self, st: P.State, h, lv, lx, gm):
         """h lam^T da/d(x, m) of the soft force at st, added to (lx, gm)."""
@@ -100,8 +124,9 @@ class SoftKDK:
         for _ in range(k0, k1):
             P.p3t_kick(self.ctx, st, self.acc, h)
             if keep is not None:
-                keep.append((X.clone(), V.clone()))
-            P.p3t_kepler_drift(self.ctx, st, self.params.dt_soft)
+                keep.append((X.clone(), V.clone(),
+                             self._copy_clusters() if self.hard == "p3t" else None))
+            self._drift(st)
             self._force(st)
             P.p3t_kick(self.ctx, st, self.acc, h)
 
@@ -121,9 +146,14 @@ class SoftKDK:
         m, r_out = m.detach().contiguous(), r_out.detach().contiguous()
         cps = []
         for k0 in range(0, self.steps, self.checkpoint):
-            cps.append((k0, X.clone(), V.clone()))
+            if k0 == 0 and self.hard == "p3t":
+                self._force(self._state(X, V, m, r_out))
+            # the clusters in force at a checkpoint come from the force before
+            # it (the neighbour search saw the velocities before that kick)
+            cl = self._copy_clusters() if self.hard == "p3t" else None
+            cps.append((k0, X.clone(), V.clone(), cl))
             self._run(X, V, m, r_out, k0, min(self.steps, k0 + self.checkpoint),
-                      have_force=k0 > 0)
+                      have_force=k0 > 0 or self.hard == "p3t")
         return X, V, dict(checkpoints=cps, m=m, r_out=r_out, xN=X.clone(), vN=V.clone())
 
     def backward(self, tape, lam_x, lam_v):
@@ -135,14 +165,25 @@ class SoftKDK:
         gm = torch.zeros(self.n, dtype=torch.float64, device=self.dev)
         st = self._state(tape["xN"], tape["vN"], m, r_out)
         self._vjp(st, h, lv, lx, gm)
-        for k0, Xc, Vc in reversed(tape["checkpoints"]):
+        for k0, Xc, Vc, clc in reversed(tape["checkpoints"]):
             k1 = min(self.steps, k0 + self.checkpoint)
             keep = []
-            self._run(Xc.clone(), Vc.clone(), m, r_out, k0, k1, keep)
+            if clc is not None:
+                # the checkpoint's force and clusters, as in the forward sweep
+                X, V = Xc.clone(), Vc.clone()
+                P.p3t_build_tree(self.ctx, self._state(X, V, m, r_out), False)
+                P.p3t_soft_force(self.ctx, self._state(X, V, m, r_out), self.acc)
+                self.cl = clc[1]
+                self._run(X, V, m, r_out, k0, k1, keep, have_force=True)
+            else:
+                self._run(Xc.clone(), Vc.clone(), m, r_out, k0, k1, keep)
             for k in range(k1 - 1, k0 - 1, -1):
-                Xk, Vk = keep[k - k0]
+                Xk, Vk, clk = keep[k - k0]
                 st = self._state(Xk, Vk, m, r_out)
-                P.p3t_kepler_vjp(self.ctx, st, dt, lx, lv)
+                if clk is not None:
+                    P.p3t_hard_step_vjp(self.ctx, st, clk[1], dt, lx, lv, gm)
+                else:
+                    P.p3t_kepler_vjp(self.ctx, st, dt, lx, lv)
                 self._vjp(st, h if k == 0 else dt, lv, lx, gm)
         return lx, lv, gm
 

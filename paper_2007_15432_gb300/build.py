@@ -21,8 +21,8 @@ OBJDIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libp3t.so")
 
 SOURCES = ["primitives.cu", "tree.cu", "walk.cu", "neighbours.cu", "hard.cu", "ctx.cu",
-           "noalloc.cu", "adjoint.cu", "direct.cu"]
-NO_FMA = {"tree.cu", "neighbours.cu", "hard.cu", "ctx.cu", "noalloc.cu"}
+           "noalloc.cu", "adjoint.cu", "direct.cu", "hermite_adj.cu"]
+NO_FMA = {"tree.cu", "neighbours.cu", "hard.cu", "ctx.cu", "noalloc.cu", "hermite_adj.cu"}
 # FP32 subnormals flushed to zero (the all-pairs kernels' FP32 operands are
 # far from 2^-126; rsqrtf then needs no subnormal handling)
 FTZ = {"direct.cu"}

@@ -91,6 +91,8 @@ void free_particle_buffers(p3t_ctx *c) {
   dfree(c->coll_slot); dfree(c->scan_state);
   dfree(c->nadj);
   c->nadj_cap = 0;
+  dfree(c->hadj);
+  c->hadj_cap = 0;
   c->scan_words = 0;
   c->cap = 0;
   c->have_tree = c->have_cand = false;
@@ -448,6 +450,24 @@ int p3t_soft_force_vjp_tree(p3t_ctx *c, const p3t_particles *p, double h, const 
     c->nadj_cap = c->node_cap;
   }
   return p3t_run_soft_force_vjp_tree(c, p, h, lx, ly, lz, gx, gy, gz, gm, (cudaStream_t)stream);
+}
+
+int p3t_hard_step_vjp(p3t_ctx *c, const p3t_particles *p, const p3t_clusters *cl, double dt,
+                      double *lx, double *ly, double *lz, double *lvx, double *lvy, double *lvz,
+                      double *gm, void *stream) {
+  if (!c || !particles_ok(p) || !cl || !(dt > 0.0) || c->prm.f_radius > 0.0)
+    return P3T_ERR_INVALID;
+  if (p->n == 0) return P3T_OK;
+  if (!cl->cl_off || !cl->cl_mem || !cl->counts || !lx || !ly || !lz || !lvx || !lvy || !lvz ||
+      !gm)
+    return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  if (c->hadj_cap < p->n) {
+    if (!dalloc(c->hadj, 6 * p->n)) return P3T_ERR_CUDA;
+    c->hadj_cap = p->n;
+  }
+  return p3t_run_hard_step_vjp(c, p, cl, dt, lx, ly, lz, lvx, lvy, lvz, gm,
+                               (cudaStream_t)stream);
 }
 
 int p3t_kepler_vjp(p3t_ctx *c, const p3t_particles *p, double dt, double *lx, double *ly,

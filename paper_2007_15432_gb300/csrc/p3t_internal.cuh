@@ -283,6 +283,10 @@ struct p3t_ctx {
   // the first call, node_cap entries of 10)
   double *nadj = nullptr;
   int64_t nadj_cap = 0;
+  // adjoint of the hard part: the cluster members' adjoints (6 per member,
+  // allocated on the first call, cap entries)
+  double *hadj = nullptr;
+  int64_t hadj_cap = 0;
 
   // auxiliary streams and events for work that can overlap inside a call
   cudaStream_t aux[2] = {nullptr, nullptr};
@@ -354,6 +358,9 @@ int p3t_run_soft_force_vjp(p3t_ctx *c, const p3t_particles *p, double h, const d
                            double *gz, double *gm, cudaStream_t s);
 int p3t_run_kepler_vjp(p3t_ctx *c, const p3t_particles *p, double dt, double *lx, double *ly,
                        double *lz, double *lvx, double *lvy, double *lvz, cudaStream_t s);
+int p3t_run_hard_step_vjp(p3t_ctx *c, const p3t_particles *p, const p3t_clusters *cl, double dt,
+                          double *lx, double *ly, double *lz, double *lvx, double *lvy,
+                          double *lvz, double *gm, cudaStream_t s);
 int p3t_run_soft_force_vjp_tree(p3t_ctx *c, const p3t_particles *p, double s,
                                 const double *lx, const double *ly, const double *lz,
                                 double *gx, double *gy, double *gz, double *gm,

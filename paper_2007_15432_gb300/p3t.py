@@ -107,6 +107,8 @@ _sig = {
     "p3t_soft_force_vjp": (C.c_int, [_CTX, C.POINTER(Particles), C.c_double] + [_vp] * 8),
     "p3t_kepler_vjp": (C.c_int, [_CTX, C.POINTER(Particles), C.c_double] + [_vp] * 7),
     "p3t_soft_force_vjp_tree": (C.c_int, [_CTX, C.POINTER(Particles), C.c_double] + [_vp] * 8),
+    "p3t_hard_step_vjp": (C.c_int, [_CTX, C.POINTER(Particles), C.POINTER(Clusters), C.c_double]
+                          + [_vp] * 8),
     "p3t_status": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
     "p3t_set_diag": (C.c_int, [_CTX, C.POINTER(Diag)]),
     "p3t_set_tuning": (C.c_int, [_CTX, C.POINTER(Tuning)]),
@@ -358,6 +360,18 @@ def p3t_soft_force_vjp_tree(ctx, st: State, h: float, lam: torch.Tensor, gx: tor
     _check(_lib.p3t_soft_force_vjp_tree(ctx, C.byref(p), float(h), _ptr(lam[0]), _ptr(lam[1]),
                                         _ptr(lam[2]), _ptr(gx[0]), _ptr(gx[1]), _ptr(gx[2]),
                                         _ptr(gm), _stream(stream)), "p3t_soft_force_vjp_tree")
+
+
+def p3t_hard_step_vjp(ctx, st: State, cl: Clusters, dt: float, lam_x: torch.Tensor,
+                      lam_v: torch.Tensor, gm: torch.Tensor, stream=None) -> None:
+    """In place: the adjoints (lam_x, lam_v), each (3, n), of the state after
+    the hard step become those of the state st before it (clusters cl and
+    the block schedule fixed); cluster members' mass terms added to gm."""
+    p = st.particles()
+    _check(_lib.p3t_hard_step_vjp(ctx, C.byref(p), C.byref(cl), float(dt), _ptr(lam_x[0]),
+                                  _ptr(lam_x[1]), _ptr(lam_x[2]), _ptr(lam_v[0]), _ptr(lam_v[1]),
+                                  _ptr(lam_v[2]), _ptr(gm), _stream(stream)),
+           "p3t_hard_step_vjp")
 
 
 def p3t_kepler_vjp(ctx, st: State, dt: float, lam_x: torch.Tensor, lam_v: torch.Tensor,
