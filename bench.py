@@ -73,6 +73,10 @@ def parse():
     ap.add_argument("--adjoint", action="store_true",
                     help="time one gradient of the 32-step soft KDK rollout at N=1e4")
     ap.add_argument("--adjoint-n", type=int, default=10_000)
+    ap.add_argument("--adjoint-form", default="direct", choices=["direct", "p3t"],
+                    help="direct: all-pairs soft force (FP32 pairs) and Kepler drift of every "
+                         "particle; p3t: tree soft force and the paper's hard part (Hermite "
+                         "clusters, Kepler singles), FP64")
     ap.add_argument("--ensemble", action="store_true",
                     help="the ensemble of 256 independent disks: batched in one context "
                          "(one launch sequence per step) vs per-disk contexts in one CUDA "
@@ -731,14 +735,20 @@ def run_adjoint(args):
     X0 = torch.tensor(np.stack([s["x"], s["y"], s["z"]]), device=dev)
     V0 = torch.tensor(np.stack([s["vx"], s["vy"], s["vz"]]), device=dev)
     M = torch.tensor(s["m"], device=dev)
-    RO = AD.cutoffs(P.Params(), X0, V0, M)
-    run = AD.SoftKDK(P.Params(precision=P.P3T_MIXED), n, steps, ck)
-    TGT = run.forward(X0, V0, M, RO)[0] + torch.tensor(disks.target_offsets(n), device=dev)
+    p3t = args.adjoint_form == "p3t"
+    if p3t:
+        prm = P.Params(theta=0.5, precision=P.P3T_FP64, group_size=64)
+        RO, RS = AD.cutoffs(prm, X0, V0, M, with_search=True)
+        run = AD.SoftKDK(prm, n, steps, ck, force="tree", hard="p3t")
+    else:
+        RO, RS = AD.cutoffs(P.Params(), X0, V0, M), None
+        run = AD.SoftKDK(P.Params(precision=P.P3T_MIXED), n, steps, ck)
+    TGT = run.forward(X0, V0, M, RO, RS)[0] + torch.tensor(disks.target_offsets(n), device=dev)
 
     def grad():
         x0, v0, m = X0.clone().requires_grad_(True), V0.clone().requires_grad_(True), \
             M.clone().requires_grad_(True)
-        xN, _ = AD.soft_kdk(x0, v0, m, RO, run)
+        xN, _ = AD.soft_kdk(x0, v0, m, RO, run, RS)
         ((xN - TGT) ** 2).sum().backward()
         return x0.grad, v0.grad, m.grad
 
@@ -755,10 +765,26 @@ def run_adjoint(args):
     t = e[0].elapsed_time(e[1]) / 1e3 / K
     # phases of one gradient
     e[0].record()
-    xN, vN, tape = run.forward(X0, V0, M, RO)
+    xN, vN, tape = run.forward(X0, V0, M, RO, RS)
     e[1].record()
     run.backward(tape, 2.0 * (xN - TGT), torch.zeros_like(vN))
     e[2].record()
+    torch.cuda.synchronize(dev)
+    t_fwd, t_bwd = e[0].elapsed_time(e[1]) / 1e3, e[1].elapsed_time(e[2]) / 1e3
+    if p3t:
+        run.status()
+        line = dict(metric="adjoint of 32 soft KDK steps at N=1e4 (tree force, Hermite clusters):"
+                    " gradient time", study="adjoint", form="p3t", value=1e3 * t,
+                    unit="ms per gradient", n_gpus=1, steps=K, warmup=W, ms_per_step=1e3 * t,
+                    higher_is_better=False,
+                    phases_ms=dict(forward=1e3 * t_fwd, backward=1e3 * t_bwd),
+                    dtype="f64", data="synthetic (seeded ring)",
+                    config=dict(workload=f"equal-mass ring N={n}, 0.95-1.05 au, m=1e-10, 32 KDK "
+                                "steps, checkpoint 8, theta=0.5, groups of <= 64", n=n,
+                                steps_per_gradient=steps, checkpoint=ck))
+        run.close()
+        print(json.dumps(line), flush=True)
+        return 0
     lp = torch.zeros(3, n, dtype=torch.float64, device=dev)
     lxx = torch.zeros(3, n, dtype=torch.float64, device=dev)
     gm = torch.zeros(n, dtype=torch.float64, device=dev)
@@ -770,7 +796,6 @@ def run_adjoint(args):
     e4.record()
     torch.cuda.synchronize(dev)
     run.status()
-    t_fwd, t_bwd = e[0].elapsed_time(e[1]) / 1e3, e[1].elapsed_time(e[2]) / 1e3
     t_vjp = e[3].elapsed_time(e4) / 1e3 / 10
     segs = (steps + ck - 1) // ck
     forces = (steps + 1) + (steps + segs)  # forward sweep + recomputation
