@@ -307,6 +307,18 @@ int p3t_merge(p3t_ctx *ctx, p3t_particles *p, int32_t *new_index, double *e_disp
  * (procedure step 9) replaces them before any hard step reads them. */
 int p3t_collisions_pending(p3t_ctx *ctx, int64_t *n_clusters, void *stream);
 
+/* The same count without synchronising the stream (Sec. 2.4.1, procedure
+ * steps 7 and 9).  p3t_collisions_pending_async queues on `stream` a copy of
+ * the count into host memory that the context owns and returns at once; work
+ * queued after it (the tree and the soft force, which do not depend on it)
+ * runs on.  p3t_collisions_pending_wait blocks until that copy alone has
+ * landed and stores the count in *n_clusters (host).  One wait per queued
+ * copy: P3T_ERR_INVALID when none is queued (the wait consumes it), and a
+ * second _async before the wait replaces the first.  Neither is capturable
+ * into a graph whose replay the caller does not wait for. */
+int p3t_collisions_pending_async(p3t_ctx *ctx, void *stream);
+int p3t_collisions_pending_wait(p3t_ctx *ctx, int64_t *n_clusters);
+
 /* The soft force at theta = 0 (and the forward force of the adjoint) -- the
  * soft force of Eq. softforce summed directly over all pairs, which is what
  * the tree walk gives at theta = 0:

@@ -197,7 +197,10 @@ int p3t_create(p3t_ctx **ctx, const p3t_params *p, int device) {
   for (int q = 0; q < 2 && ok; ++q)
     ok = cudaStreamCreateWithFlags(&c->aux[q], cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->ev_join[q], cudaEventDisableTiming) == cudaSuccess;
-  if (ok) ok = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  if (ok) ok = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&c->ev_coll, cudaEventDisableTiming) == cudaSuccess &&
+               cudaHostAlloc(reinterpret_cast<void **>(&c->coll_pin), sizeof(unsigned long long),
+                             cudaHostAllocDefault) == cudaSuccess;
   if (ok) ok = cudaMemset(c->status, 0, sizeof(DevStatus)) == cudaSuccess &&
                cudaMemset(c->counters, 0, 64 * sizeof(int64_t)) == cudaSuccess &&
                cudaMemset(c->coll_ctr, 0, sizeof(unsigned long long)) == cudaSuccess &&
@@ -228,6 +231,8 @@ void p3t_destroy(p3t_ctx *c) {
     if (c->ev_join[q]) cudaEventDestroy(c->ev_join[q]);
   }
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_coll) cudaEventDestroy(c->ev_coll);
+  if (c->coll_pin) cudaFreeHost(c->coll_pin);
   cudaGetLastError();
   delete c;
 }
@@ -392,6 +397,27 @@ int p3t_collisions_pending(p3t_ctx *c, int64_t *n_clusters, void *stream) {
       cudaStreamSynchronize(s) != cudaSuccess)
     return P3T_ERR_CUDA;
   *n_clusters = (int64_t)(ctr >> 32);
+  return P3T_OK;
+}
+
+int p3t_collisions_pending_async(p3t_ctx *c, void *stream) {
+  if (!c) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  const cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(c->coll_pin, c->coll_ctr, sizeof(unsigned long long),
+                      cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaEventRecord(c->ev_coll, s) != cudaSuccess)
+    return P3T_ERR_CUDA;
+  c->coll_queued = true;
+  return P3T_OK;
+}
+
+int p3t_collisions_pending_wait(p3t_ctx *c, int64_t *n_clusters) {
+  if (!c || !n_clusters || !c->coll_queued) return P3T_ERR_INVALID;
+  DeviceGuard g(c->device);
+  c->coll_queued = false;
+  if (cudaEventSynchronize(c->ev_coll) != cudaSuccess) return P3T_ERR_CUDA;
+  *n_clusters = (int64_t)(*c->coll_pin >> 32);
   return P3T_OK;
 }
 

@@ -291,6 +291,11 @@ struct p3t_ctx {
   // auxiliary streams and events for work that can overlap inside a call
   cudaStream_t aux[2] = {nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+  // the pending-collision count read without a stream synchronisation:
+  // pinned host word, the event after its copy, and whether a copy is queued
+  unsigned long long *coll_pin = nullptr;
+  cudaEvent_t ev_coll = nullptr;
+  bool coll_queued = false;
 };
 
 // ---- helpers -------------------------------------------------------------

@@ -101,6 +101,8 @@ _sig = {
     "p3t_kick": (C.c_int, [_CTX, C.POINTER(Particles), _vp, _vp, _vp, C.c_double, _vp]),
     "p3t_energy": (C.c_int, [_CTX, C.POINTER(Particles), _vp, _vp]),
     "p3t_collisions_pending": (C.c_int, [_CTX, C.POINTER(C.c_int64), _vp]),
+    "p3t_collisions_pending_async": (C.c_int, [_CTX, _vp]),
+    "p3t_collisions_pending_wait": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
     "p3t_merge": (C.c_int, [_CTX, C.POINTER(Particles), _vp, C.POINTER(C.c_double),
                             C.POINTER(C.c_int64), _vp]),
     "p3t_soft_force_direct": (C.c_int, [_CTX, C.POINTER(Particles), _vp, _vp, _vp, _vp]),
@@ -321,6 +323,20 @@ def p3t_collisions_pending(ctx, stream=None) -> int:
     return n.value
 
 
+def p3t_collisions_pending_async(ctx, stream=None) -> None:
+    """Queues a copy of the pending-collision count; returns at once."""
+    _check(_lib.p3t_collisions_pending_async(ctx, _stream(stream)),
+           "p3t_collisions_pending_async")
+
+
+def p3t_collisions_pending_wait(ctx) -> int:
+    """The count of the last queued copy, once it has landed (waits for that
+    copy only, not for the work queued after it)."""
+    n = C.c_int64(0)
+    _check(_lib.p3t_collisions_pending_wait(ctx, C.byref(n)), "p3t_collisions_pending_wait")
+    return n.value
+
+
 def p3t_merge(ctx, st: State, new_index: torch.Tensor | None = None, stream=None):
     """Procedure step 9 for collisions: merges the composites of the last hard
     step, shortens the tensors of ``st`` to the new count in place and returns
@@ -514,10 +530,13 @@ class SoftStep:
         p3t_kick(self.ctx, self.st, self.acc, h, stream)
         p3t_hard_step(self.ctx, self.st, self.cl, self.params.dt_soft, self.hsteps, stream)
         # composites formed in this hard step: the merge after the second kick
-        # recomputes the neighbour lists, so the force before it needs none
-        pending = self.collisions and p3t_collisions_pending(self.ctx, stream) > 0
+        # recomputes the neighbour lists, so the force before it needs none.
+        # The count is read while the tree and the force run.
+        if self.collisions:
+            p3t_collisions_pending_async(self.ctx, stream)
         p3t_build_tree(self.ctx, self.st, False, stream)
         p3t_soft_force(self.ctx, self.st, self.acc, self.counts, stream)
+        pending = self.collisions and p3t_collisions_pending_wait(self.ctx) > 0
         if not pending:
             self.cl = p3t_neighbours(self.ctx, self.st, self.nb_off, self.nb_idx, stream)
         p3t_kick(self.ctx, self.st, self.acc, h, stream)

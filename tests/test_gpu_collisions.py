@@ -87,6 +87,15 @@ def test_collision_hard_kick_merge_match_oracle(P3T, name):
     # one pending record per cluster that holds composites
     lab = ocl.label[comp >= 0]
     assert P3T.p3t_collisions_pending(ctx) == len(np.unique(lab))
+    # the same count through the queued copy, with other work queued behind
+    # it; a wait with no copy queued is an error
+    P3T.p3t_collisions_pending_async(ctx)
+    junk = torch.zeros(1 << 20, dtype=torch.float64, device="cuda")
+    for _ in range(8):
+        junk.add_(1.0)
+    assert P3T.p3t_collisions_pending_wait(ctx) == len(np.unique(lab))
+    with pytest.raises(P3T.P3TError):
+        P3T.p3t_collisions_pending_wait(ctx)
     g = st.numpy()
     rep = hermite_report(g, so, ocl.cl_mem, rec.cpu().numpy(), msteps)
     print("hermite with collisions", name, rep)
@@ -123,6 +132,8 @@ def test_collision_hard_kick_merge_match_oracle(P3T, name):
     assert es == pytest.approx(e_soft, rel=1e-12, abs=1e-40)
     # the list is consumed: nothing pending, a second merge finds nothing
     assert P3T.p3t_collisions_pending(ctx) == 0
+    P3T.p3t_collisions_pending_async(ctx)
+    assert P3T.p3t_collisions_pending_wait(ctx) == 0
     assert P3T.p3t_merge(ctx, st)[0] == 0
     P3T.p3t_destroy(ctx)
 
