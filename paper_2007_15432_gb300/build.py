@@ -38,7 +38,8 @@ def _nvcc():
 
 def _deps():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, "p3t_internal.cuh"), os.path.join(INCLUDE, "p3t.h")]
+    files += [os.path.join(CSRC, "p3t_internal.cuh"), os.path.join(CSRC, "exact_conv.cuh"),
+              os.path.join(INCLUDE, "p3t.h")]
     return max(os.path.getmtime(f) for f in files)
 
 

@@ -73,6 +73,7 @@ void free_particle_buffers(p3t_ctx *c) {
   dfree(c->keys); dfree(c->keys_alt); dfree(c->idx); dfree(c->idx_alt);
   dfree(c->radix_hist);
   dfree(c->sx); dfree(c->sy); dfree(c->sz); dfree(c->sm); dfree(c->sro); dfree(c->srs);
+  dfree(c->pack);
   dfree(c->sq); dfree(c->spA); dfree(c->spB); dfree(c->srs32); dfree(c->sml);
   dfree(c->lp); dfree(c->lv); dfree(c->wlcp); dfree(c->ncount); dfree(c->nstart);
   dfree(c->pre_first); dfree(c->pre_count); dfree(c->pre_level);
@@ -121,6 +122,7 @@ int reserve(p3t_ctx *c, int64_t n, int64_t cand_cap) {
   ok &= dalloc(c->keys, N) && dalloc(c->keys_alt, N) && dalloc(c->idx, N) && dalloc(c->idx_alt, N);
   ok &= dalloc(c->radix_hist, c->radix_hist_cap);
   ok &= dalloc(c->sx, N) && dalloc(c->sy, N) && dalloc(c->sz, N) && dalloc(c->sm, N);
+  ok &= dalloc(c->pack, 6 * N);
   ok &= dalloc(c->sro, N) && dalloc(c->srs, N) && dalloc(c->sq, 3 * N);
   ok &= dalloc(c->spA, N) && dalloc(c->spB, N) && dalloc(c->srs32, N) &&
         dalloc(c->sml, N);

@@ -216,6 +216,7 @@ struct p3t_ctx {
 
   // sorted particles (FP64 and mixed packings)
   double *sx = nullptr, *sy = nullptr, *sz = nullptr, *sm = nullptr;
+  double *pack = nullptr;  // (x, y, z, m, r_out, r_search) per particle, caller order
   double *sro = nullptr, *srs = nullptr;
   int32_t *sq = nullptr;                   // 3 * cap quantised coordinates
   float4 *spA = nullptr, *spB = nullptr;   // {x_hi,y_hi,z_hi,m}, {x_lo,y_lo,z_lo,1/r_out}

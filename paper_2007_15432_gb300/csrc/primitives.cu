@@ -179,7 +179,6 @@ __global__ void radix_upsweep(const uint64_t *keys, const int64_t *d_n,
   __shared__ uint32_t h[kRadix];
   const int64_t n = *d_n;
   const int64_t used = radix_tiles(d_n);
-  const int lane = threadIdx.x & 31;
   for (int64_t tile = blockIdx.x; tile < used; tile += gridDim.x) {
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -191,12 +190,11 @@ __global__ void radix_upsweep(const uint64_t *keys, const int64_t *d_n,
       const int64_t e = base + k * kSortThreads + threadIdx.x;
       dig[k] = e < n ? (uint32_t)((__ldg(&keys[e]) >> shift) & (kRadix - 1)) : kRadix;
     }
+    // plain shared atomics: on this part a warp's same-address atomics cost
+    // less than matching the lanes' digits first
 #pragma unroll
-    for (int k = 0; k < kSortItems; ++k) {
-      const uint32_t d = dig[k];
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);  // one atomic per digit and warp
-      if (d < kRadix && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
-    }
+    for (int k = 0; k < kSortItems; ++k)
+      if (dig[k] < kRadix) atomicAdd(&h[dig[k]], 1u);
     __syncthreads();
     hist[(int64_t)threadIdx.x * ntiles + tile] = h[threadIdx.x];
     __syncthreads();

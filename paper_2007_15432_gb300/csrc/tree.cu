@@ -4,6 +4,7 @@
 #include <math.h>
 
 #include "p3t_internal.cuh"
+#include "exact_conv.cuh"
 
 namespace {
 
@@ -383,39 +384,32 @@ __device__ __forceinline__ uint32_t compact3(uint64_t v) {
   return (uint32_t)v;
 }
 
-// cell index of v: floor(d / u) of d = v - lo (rounded) and the cell side
-// u = L / 2^21, the quotient taken exactly (the largest q with q u <= d),
-// clamped to [0, 2^21).  The estimate floor(d S), with the scale S = 2^21 / L
-// formed once per build, is within ~1e-9 cells of d / u, so it is off by at
-// most one cell and only beside a cell boundary; two fused multiply-adds,
-// each rounded once and so with the sign of the exact q u - d, settle it.
-__device__ __forceinline__ uint64_t quantise(double v, double lo, double S, double u) {
-  const double d = v - lo;
-  double f = floor(d * S);
-  if (__fma_rn(f, u, -d) > 0.0) f -= 1.0;
-  else if (__fma_rn(f + 1.0, u, -d) <= 0.0) f += 1.0;
-  if (f < 0.0) f = 0.0;
-  if (f > (double)(P3T_QMAX - 1)) f = (double)(P3T_QMAX - 1);
-  return (uint64_t)f;
-}
-
 // Morton key of each particle on its segment's grid.  rekey = 0: slot s holds
-// particle s (idx[s] = s); rekey = 1: slot s holds particle idx[s] (the keys
-// of an order already sorted)
+// particle s (idx[s] = s), and the particle's record (x, y, z, m, r_out,
+// r_search) is packed for the gather (one 48-byte read per particle there in
+// place of six scattered 8-byte ones); rekey = 1: slot s holds particle idx[s]
+// (the keys of an order already sorted)
 __global__ void k_keys(SegView sv, const double *x, const double *y,
-                       const double *z, const double *box5, uint64_t *keys,
-                       int32_t *idx, int rekey) {
+                       const double *z, const double *m, const double *ro,
+                       const double *rs, const double *box5, uint64_t *keys,
+                       int32_t *idx, double *pack, int rekey) {
   const int64_t n = sv.n;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
        s += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = rekey ? (int64_t)idx[s] : s;
     const double *box = box5 + 5 * seg_at(sv, i);
-    const double x0 = box[0], y0 = box[1], z0 = box[2], S = box[4];
-    const double u = box[3] * (1.0 / (double)P3T_QMAX);  // exact: a power-of-two scaling
-    uint64_t qx = quantise(x[i], x0, S, u), qy = quantise(y[i], y0, S, u),
-             qz = quantise(z[i], z0, S, u);
+    const CellScale cs = cell_scale(box[3]);
+    const double X = x[i], Y = y[i], Z = z[i];
+    const uint64_t qx = quantise(X, box[0], cs), qy = quantise(Y, box[1], cs),
+                   qz = quantise(Z, box[2], cs);
     keys[s] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
-    if (!rekey) idx[s] = (int32_t)s;
+    if (!rekey) {
+      idx[s] = (int32_t)s;
+      double2 *o = reinterpret_cast<double2 *>(pack + 6 * s);
+      o[0] = make_double2(X, Y);
+      o[1] = make_double2(Z, m[s]);
+      o[2] = make_double2(ro[s], rs[s]);
+    }
   }
 }
 
@@ -431,15 +425,15 @@ __global__ void k_segkey(SegView sv, const int32_t *idx, uint64_t *keys) {
 // float-float packing the mixed path reads (each path writes only its own)
 template <bool MIXED>
 __global__ void k_gather(int64_t n, const int32_t *idx, const uint64_t *keys,
-                         const double *x, const double *y, const double *z,
-                         const double *m, const double *ro, const double *rs,
-                         double *sx, double *sy, double *sz, double *sm,
+                         const double *pack, double *sx, double *sy, double *sz, double *sm,
                          double *sro, double *srs, int32_t *sq, float4 *spA,
                          float4 *spB, float *srs32, float *sml) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
        s += (int64_t)gridDim.x * blockDim.x) {
     const int32_t i = idx[s];
-    const double X = x[i], Y = y[i], Z = z[i], M = m[i], RO = ro[i], RS = rs[i];
+    const double2 *rec = reinterpret_cast<const double2 *>(pack + 6 * (int64_t)i);
+    const double2 r0 = rec[0], r1 = rec[1], r2 = rec[2];
+    const double X = r0.x, Y = r0.y, Z = r1.x, M = r1.y, RO = r2.x, RS = r2.y;
     srs[s] = RS;
     const uint64_t k = keys[s];
     sq[3 * s + 0] = (int32_t)compact3(k >> 2);
@@ -449,13 +443,17 @@ __global__ void k_gather(int64_t n, const int32_t *idx, const uint64_t *keys,
       sx[s] = X; sy[s] = Y; sz[s] = Z; sm[s] = M; sro[s] = RO;
       continue;
     }
-    const float xh = (float)X, yh = (float)Y, zh = (float)Z;
-    const float mh = (float)M;
+    float xh, xl, yh, yl, zh, zl, mh, ml, roh, rol, r2h, r2l;
+    split_f32(X, xh, xl);
+    split_f32(Y, yh, yl);
+    split_f32(Z, zh, zl);
+    split_f32(M, mh, ml);
+    split_f32(RO, roh, rol);
+    split_f32(RS * RS, r2h, r2l);
     spA[s] = make_float4(xh, yh, zh, mh);
-    sml[s] = (float)(M - (double)mh);
-    spB[s] = make_float4((float)(X - (double)xh), (float)(Y - (double)yh),
-                         (float)(Z - (double)zh), 1.0f / (float)RO);  // FP32 path only
-    srs32[s] = (float)(RS * RS) * 1.00001f;  // walk's candidate test: r^2 vs r_search^2, widened
+    sml[s] = ml;
+    spB[s] = make_float4(xl, yl, zl, 1.0f / roh);  // FP32 path only
+    srs32[s] = r2h * 1.00001f;  // walk's candidate test: r^2 vs r_search^2, widened
   }
 }
 
@@ -1166,7 +1164,8 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   k_box_init<<<1, 256, 0, s>>>(c->box_bits, nseg);
   k_box<<<(unsigned)(bsl * nseg), kBlock, 0, s>>>(sv, bsl, p->x, p->y, p->z, c->box_bits);
   k_box_final<<<1, 256, 0, s>>>(c->box_bits, c->box, nseg);
-  k_keys<<<(unsigned)g, kBlock, 0, s>>>(sv, p->x, p->y, p->z, c->box, c->keys, c->idx, 0);
+  k_keys<<<(unsigned)g, kBlock, 0, s>>>(sv, p->x, p->y, p->z, p->m, p->r_out, p->r_search,
+                                        c->box, c->keys, c->idx, c->pack, 0);
   // n on the device for the count-driven primitives
   k_set_i64<<<1, 1, 0, s>>>(&cnt[0], n);
   rc = p3t_radix_sort(&c->keys, &c->idx, &c->keys_alt, &c->idx_alt, &cnt[0], c->cap,
@@ -1181,12 +1180,12 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
     rc = p3t_radix_sort(&c->keys, &c->idx, &c->keys_alt, &c->idx_alt, &cnt[0], c->cap,
                         0, sbits, c->radix_hist, c->radix_hist_cap, s);
     if (rc) return rc;
-    k_keys<<<(unsigned)g, kBlock, 0, s>>>(sv, p->x, p->y, p->z, c->box, c->keys, c->idx, 1);
+    k_keys<<<(unsigned)g, kBlock, 0, s>>>(sv, p->x, p->y, p->z, p->m, p->r_out, p->r_search,
+                                          c->box, c->keys, c->idx, c->pack, 1);
     p3t_note_launches(2);
   }
   auto gather = c->prm.precision == P3T_MIXED ? k_gather<true> : k_gather<false>;
-  gather<<<(unsigned)g, kBlock, 0, s>>>(n, c->idx, c->keys, p->x, p->y, p->z, p->m,
-                                          p->r_out, p->r_search, c->sx, c->sy, c->sz,
+  gather<<<(unsigned)g, kBlock, 0, s>>>(n, c->idx, c->keys, c->pack, c->sx, c->sy, c->sz,
                                           c->sm, c->sro, c->srs, c->sq, c->spA, c->spB,
                                           c->srs32, c->sml);
   k_lcp<<<(unsigned)g, kBlock, 0, s>>>(sv, c->keys, leaf, c->wlcp, c->lp);

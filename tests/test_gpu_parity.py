@@ -6,6 +6,8 @@ neighbour lists and cluster labels bit-exact (given the same r_out / r_search
 arrays); kick bit-exact; Kepler <= 1e-12 and Hermite members <= 1e-11
 relative after one soft step, with the block-schedule flips counted.
 """
+from fractions import Fraction
+
 import numpy as np
 import pytest
 import torch
@@ -385,6 +387,53 @@ def test_tiny_and_single_leaf_systems(P3T, n):
         assert np.all(acc == 0.0)
     assert P3T.p3t_tree_stats(ctx) == ref.tree
     P3T.p3t_destroy(ctx)
+
+
+def test_keys_on_cell_boundaries(P3T):
+    """Particles placed on coarse cell boundaries of the 21-bit grid (multiples
+    of 2^15 cells along x or y) and one ulp either side: the key kernel's cell
+    is the exact floor of (v - lo) / u like the oracle's, so the tree shape,
+    interaction counts and forces agree; a cell off by one would move these
+    particles into other level-6 cells."""
+    s = disks.equal_mass_narrow(n=3000, seed=29, planted=False)
+    rng = np.random.default_rng(31)
+    lo = [s[a].min() for a in ("x", "y", "z")]
+    L = max(s[a].max() - s[a].min() for a in ("x", "y", "z"))
+    u = L / 2**21
+    naive_differs = 0
+    slot = 0
+    for a, ax in enumerate(("x", "y")):
+        span = (s[ax].max() - lo[a]) / u
+        ks = rng.integers(1, int(span // 2**15), 200) * 2**15
+        base = lo[a] + ks * u
+        for v in (np.nextafter(base, -np.inf), base, np.nextafter(base, np.inf)):
+            # any particle but the ones holding this axis' extremes
+            keep_ext = [np.argmin(s[ax]), np.argmax(s[ax])]
+            idx = np.setdiff1d(np.arange(3000), keep_ext)[slot:slot + len(v)]
+            s[ax][idx] = v
+            slot += len(v)
+            d = v - lo[a]   # rounded as the key kernel rounds it
+            exact = np.array([int(Fraction(float(w)) // Fraction(u)) for w in d])
+            naive = np.floor(d / u).astype(np.int64)
+            naive_differs += int(np.sum(naive != exact))
+    # the box is unchanged: the extremes were left in place
+    assert [s[a].min() for a in ("x", "y", "z")] == lo
+    assert max(s[a].max() - s[a].min() for a in ("x", "y", "z")) == L
+    # Hill cut-offs: the moved particles keep their ring velocities, which the
+    # random-velocity term would turn into very large search radii
+    P = P3T.Params(theta=0.5, cutoff_mode=P3T.P3T_CUT_HILL)
+    op = oracle_params(P)
+    ro, rs, _, _ = O.cutoffs(s, op)
+    ref = O.tree_soft(s, ro, rs, op)
+    for prec, bar in ((0, 1e-12), (1, 1e-5)):
+        P.precision = prec
+        st, ctx = _setup(P3T, s, P, ro, rs)
+        acc, counts = _force(P3T, ctx, st)
+        assert P3T.p3t_tree_stats(ctx) == ref.tree
+        assert counts[0] == ref.n_pp and counts[1] == ref.n_pnode
+        assert rel_err(acc, ref.acc).max() <= bar
+        P3T.p3t_destroy(ctx)
+    print("boundary particles whose naive FP64 cell differs from the exact one:", naive_differs)
 
 
 def test_coincident_particles_level21_leaf(P3T):
