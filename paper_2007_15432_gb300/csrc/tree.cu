@@ -497,54 +497,88 @@ __global__ void k_levels(SegView sv, int leaf, const int32_t *wlcp,
   }
 }
 
-// first index e >= start (or the segment's end n) whose key leaves the
-// level-l cell of key ki, given that every index below start is inside (the
-// cell's members are contiguous in key order): a galloping search from start,
-// so the cost grows with the log of the distance, not of n
-__device__ __forceinline__ int64_t cell_end_from(const uint64_t *keys, int64_t n, uint64_t ki,
-                                                 int l, int64_t start) {
-  if (l == 0 || start >= n) return n;
-  if (lcp_levels(ki, keys[start]) < l) return start;
-  int64_t lo = start, hi, step = 1;  // keys[lo] inside
-  for (;;) {
-    hi = lo + step;
-    if (hi >= n) { hi = n; break; }
-    if (lcp_levels(ki, keys[hi]) < l) break;
-    lo = hi;
-    step <<= 1;
-  }
-  ++lo;  // the answer lies in [lo, hi]
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (lcp_levels(ki, keys[mid]) >= l) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
-__global__ void k_nodes_pre(SegView sv, const uint64_t *keys, const int8_t *lp,
-                            const int8_t *lv, const int64_t *nstart,
-                            const int64_t *d_nnode, int64_t node_cap,
-                            int32_t *pre_first, int32_t *pre_count,
-                            int32_t *pre_level, uint64_t *lvl_keys,
+// The nodes a particle starts (levels lp + 1 .. lv, deepest last in preorder):
+// their first particle and level, and the identity order for the level sort;
+// the member counts come from k_node_counts
+__global__ void k_nodes_pre(SegView sv, const int8_t *lp, const int8_t *lv,
+                            const int64_t *nstart, const int64_t *d_nnode, int64_t node_cap,
+                            int32_t *pre_first, int32_t *pre_level, uint64_t *lvl_keys,
                             int32_t *bfs2pre, DevStatus *st) {
   if (*d_nnode > node_cap || st->code != 0) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sv.n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t s1 = seg_hi(sv, seg_at(sv, i));
     const int l0 = (int)lp[i] + 1, L = (int)lv[i];
-    if (L < l0) continue;
-    const uint64_t ki = keys[i];
-    // deepest cell first: each enclosing cell ends at or after the one inside
-    int64_t e = i + 1;
-    for (int l = L; l >= l0; --l) {
-      e = cell_end_from(keys, s1, ki, l, e);
+    for (int l = l0; l <= L; ++l) {
       const int64_t id = nstart[i] + (l - l0);
       pre_first[id] = (int32_t)i;
-      pre_count[id] = (int32_t)(e - i);
       pre_level[id] = l;
       lvl_keys[id] = (uint64_t)l;
       bfs2pre[id] = (int32_t)id;
     }
+  }
+}
+
+// Members of each node: the node's cell (level l, first particle i) ends at
+// the first sorted key at or above kend = (prefix of key i at level l, plus
+// one) shifted back, or at the segment's end -- a lower bound found with 8
+// independent probes a round: galloping from i (probe steps 1..8, then 8x
+// larger each round), then narrowing the last interval ninefold a round.  A
+// node's search is its own thread's: the longest chain (the root) is about a
+// dozen rounds, not one search per level in a row.
+__global__ void k_node_counts(SegView sv, const uint64_t *keys, const int64_t *d_nnode,
+                              int64_t node_cap, const int32_t *pre_first,
+                              const int32_t *pre_level, int32_t *pre_count, DevStatus *st) {
+  if (*d_nnode > node_cap || st->code != 0) return;
+  const int64_t nn = *d_nnode;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nn;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = pre_first[b];
+    const int l = pre_level[b];
+    const int64_t s1 = seg_hi(sv, seg_at(sv, i));
+    int64_t end = s1;
+    if (l > 0) {
+      const int sh = 3 * (P3T_BITS - l);
+      const uint64_t kend = ((keys[i] >> sh) + 1) << sh;
+      // invariant: keys[lo] < kend; the answer lies in (lo, hi]
+      int64_t lo = i, hi = s1, step = 1;
+      for (;;) {  // gallop
+        uint64_t kp[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int64_t q = lo + (m + 1) * step;
+          kp[m] = q < s1 ? __ldg(&keys[q]) : ~0ull;
+        }
+        int f = 8;
+#pragma unroll
+        for (int m = 7; m >= 0; --m)
+          if (kp[m] >= kend) f = m;
+        if (f < 8) {
+          hi = lo + (f + 1) * step < s1 ? lo + (f + 1) * step : s1;
+          lo += f * step;
+          break;
+        }
+        lo += 8 * step;
+        step *= 8;
+      }
+      while (hi - lo > 1) {  // narrow (lo, hi]
+        const int64_t w = (hi - lo + 8) / 9;
+        uint64_t kp[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int64_t q = lo + (m + 1) * w;
+          kp[m] = q < hi ? __ldg(&keys[q]) : ~0ull;
+        }
+        int f = 8;
+#pragma unroll
+        for (int m = 7; m >= 0; --m)
+          if (kp[m] >= kend) f = m;
+        const int64_t nhi = lo + (f + 1) * w;
+        if (nhi < hi) hi = nhi;
+        lo += f * w;
+      }
+      end = hi;
+    }
+    pre_count[b] = (int32_t)(end - i);
   }
 }
 
@@ -1193,9 +1227,11 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   rc = p3t_scan_i32_to_i64(c->ncount, c->nstart, &cnt[0], c->cap, &cnt[1], c->scan_state, c->scan_words, c->status, c->poll_limit, s);
   if (rc) return rc;
   k_clamp_nodes<<<1, 1, 0, s>>>(cnt, c->node_cap, c->status);
-  k_nodes_pre<<<(unsigned)g, kBlock, 0, s>>>(sv, c->keys, c->lp, c->lv, c->nstart, &cnt[1],
-                                             c->node_cap, c->pre_first, c->pre_count,
-                                             c->pre_level, c->lvl_keys, c->bfs2pre, c->status);
+  k_nodes_pre<<<(unsigned)g, kBlock, 0, s>>>(sv, c->lp, c->lv, c->nstart, &cnt[1], c->node_cap,
+                                             c->pre_first, c->pre_level, c->lvl_keys,
+                                             c->bfs2pre, c->status);
+  k_node_counts<<<(unsigned)p3t_grid(c->node_cap, kBlock, maxb), kBlock, 0, s>>>(
+      sv, c->keys, &cnt[1], c->node_cap, c->pre_first, c->pre_level, c->pre_count, c->status);
   rc = p3t_radix_sort(&c->lvl_keys, &c->bfs2pre, &c->lvl_keys_alt, &c->bfs2pre_alt, &cnt[3],
                       c->node_cap, 0, 8, c->radix_hist, c->radix_hist_cap, s);
   if (rc) return rc;
@@ -1241,9 +1277,9 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   k_group_list<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->group_flag,
                                                c->group_pos, c->pre2bfs, c->group_list);
   // own kernels here (the scans, sorts and moments count themselves): box 3,
-  // keys, n, gather, lcp, levels, clamp, nodes_pre, pre2bfs, nodes_bfs,
-  // parents, leaf_list, group_flags, group_list
-  p3t_note_launches(16);
+  // keys, n, gather, lcp, levels, clamp, nodes_pre, node_counts, pre2bfs,
+  // nodes_bfs, parents, leaf_list, group_flags, group_list
+  p3t_note_launches(17);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 
