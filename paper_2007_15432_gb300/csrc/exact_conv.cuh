@@ -29,6 +29,23 @@ __device__ __forceinline__ CellScale cell_scale(double L) {
   const uint64_t Mu = (b & 0xfffffffffffffull) | (1ull << 52);
   return {Mu, (int)((b >> 52) & 0x7ff), 1.0f / (float)(uint32_t)(Mu >> 21)};
 }
+// floor(Md 2^k / Mu) and its remainder for 0 <= k <= 22 (a quotient below
+// 2^23): the FP32 estimate is within 3 of the quotient, and the remainder
+// Md 2^k - q Mu, below 2^55 in magnitude, is exact modulo 2^64
+__device__ __forceinline__ int32_t floor_div_cells(uint64_t Md, int k, const CellScale &cs,
+                                                   int64_t &r) {
+  int32_t q = (int32_t)((float)(uint32_t)(Md >> 21) * cs.rb * (float)(1u << k));
+  r = (int64_t)((Md << k) - (uint64_t)(uint32_t)q * cs.Mu);
+  const int64_t mu = (int64_t)cs.Mu;
+#pragma unroll
+  for (int it = 0; it < 4; ++it)
+    if (r < 0) { r += mu; --q; }
+#pragma unroll
+  for (int it = 0; it < 4; ++it)
+    if (r >= mu) { r -= mu; ++q; }
+  return q;
+}
+
 __device__ __forceinline__ uint64_t quantise(double v, double lo, CellScale cs) {
   const double d = v - lo;
   const uint64_t bd = (uint64_t)__double_as_longlong(d);
@@ -40,20 +57,37 @@ __device__ __forceinline__ uint64_t quantise(double v, double lo, CellScale cs) 
   const int k = ed - cs.eL + P3T_BITS;  // d / u = (Md / Mu) 2^k
   if (k < 0) return 0;                   // Md / Mu < 2: below one cell
   if (k > P3T_BITS + 1) return P3T_QMAX - 1;  // at least 2^22 cells: clamped
-  // estimate (relative error below 5 2^-24 + 2^-31 on a value below 2^23:
-  // within 3 of the quotient), then the exact remainder r = Md 2^k - q Mu
-  // brought into [0, Mu).  |r| < 4 Mu < 2^55, so the difference taken modulo
-  // 2^64 and read as a signed integer is r itself.
-  int32_t q = (int32_t)((float)(uint32_t)(Md >> 21) * cs.rb * (float)(1u << k));
-  int64_t r = (int64_t)((Md << k) - (uint64_t)(uint32_t)q * cs.Mu);
-  const int64_t mu = (int64_t)cs.Mu;
-#pragma unroll
-  for (int it = 0; it < 4; ++it)
-    if (r < 0) { r += mu; --q; }
-#pragma unroll
-  for (int it = 0; it < 4; ++it)
-    if (r >= mu) { r -= mu; ++q; }
+  int64_t r;
+  const int32_t q = floor_div_cells(Md, k, cs, r);
   return q < P3T_QMAX - 1 ? (uint64_t)(uint32_t)q : (uint64_t)(P3T_QMAX - 1);
+}
+
+// A node's search reach in grid cells, R = ceil(rs / u) + 1 with the FP64
+// quotient (rounded to nearest) as the definition has it, capped at 2^23.
+__device__ __noinline__ int32_t reach_cells_fp64(double rs, double L) {
+  const double rq = ceil(rs / ldexp(L, -P3T_BITS)) + 1.0;
+  return rq < 8388608.0 ? (int32_t)rq : 8388608;
+}
+// The same without FP64 arithmetic: the exact quotient is x = q + r / Mu
+// (floor_div_cells); its FP64 rounding stays at q exactly when the fraction
+// is at most half an ulp of x, 2^(floor(log2 q) - 53) (a tie rounds to the
+// even q), i.e. when r <= Mu / 2^(53 - floor(log2 q)); otherwise it lies in
+// (q, q + 1] and its ceiling is q + 1.  Outside 2^-900 < x < 2^21 (and for
+// rs that is zero, subnormal, negative or not finite) the FP64 expression.
+__device__ __forceinline__ int32_t reach_cells(double rs, double L, const CellScale &cs) {
+  const uint64_t bd = (uint64_t)__double_as_longlong(rs);
+  const int ed = (int)(bd >> 52);
+  if (ed == 0 || ed >= 0x7ff) return reach_cells_fp64(rs, L);
+  const int k = ed - cs.eL + P3T_BITS;
+  if (k > P3T_BITS || k < -900) return reach_cells_fp64(rs, L);
+  if (k < 0) return 2;  // 0 < x < 1: the rounded quotient is in (0, 1]
+  const uint64_t Md = (bd & 0xfffffffffffffull) | (1ull << 52);
+  int64_t r;
+  const int32_t q = floor_div_cells(Md, k, cs, r);
+  if (r == 0) return q + 1;
+  if (q == 0) return 2;
+  const int s = 53 - (31 - __clz(q));
+  return r <= (int64_t)(cs.Mu >> s) ? q + 1 : q + 2;
 }
 
 // x = hi + lo: hi = x rounded to FP32 and lo = (x - hi) rounded to FP32,

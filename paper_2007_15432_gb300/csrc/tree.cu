@@ -763,7 +763,8 @@ __global__ void k_moments_leaf(
 // carries ~2^-44 of the coordinates, the float-float redo's need), S and the
 // quadrupole are FP32 (the walk reads Q in FP32).  The search reach is the
 // largest r_search as a bit pattern (non-negative doubles order like their
-// bits), so the node's reach R is the FP64 path's.
+// bits), and R = ceil(rs / u) + 1 comes from integer operations (reach_cells:
+// the value of the FP64 expression the FP64 path evaluates).
 __device__ __forceinline__ int64_t max_bits(int64_t a, double v) {
   const int64_t b = __double_as_longlong(v);
   return b > a ? b : a;
@@ -776,7 +777,7 @@ __device__ __forceinline__ void leaf_moments32(
   {
     TreeNode *nd = &node[b];
     const int32_t f = nd->first, c = nd->count;
-    const double u = ldexp(box[5 * seg_at(sv, f) + 3], -P3T_BITS);
+    const double L = box[5 * seg_at(sv, f) + 3];
     const float4 A0 = spA[f], B0 = spB[f];
     FF M{0.f, 0.f}, D[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     float S[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -813,8 +814,7 @@ __device__ __forceinline__ void leaf_moments32(
     for (int a = 0; a < 3; ++a) { nd->qlo[a] = lo[a]; nd->qhi[a] = hi[a]; }
     const double rs = __longlong_as_double(rsb);
     nrs[b] = rs;
-    const double rq = ceil(rs / u) + 1.0;
-    nd->R = rq < 8388608.0 ? (int32_t)rq : 8388608;
+    nd->R = reach_cells(rs, L, cell_scale(L));
     m32[b] = o;
   }
 }
@@ -900,8 +900,8 @@ __device__ void node_moments32(int64_t b, TreeNode *node, Mom32 *m32, double *nr
   for (int a = 0; a < 3; ++a) { pn->qlo[a] = plo[a]; pn->qhi[a] = phi[a]; }
   const double rs = __longlong_as_double(rsb);
   nrs[b] = rs;
-  const double rq = ceil(rs / ldexp(box[5 * seg_at(sv, pn->first) + 3], -P3T_BITS)) + 1.0;
-  pn->R = rq < 8388608.0 ? (int32_t)rq : 8388608;
+  const double L = box[5 * seg_at(sv, pn->first) + 3];
+  pn->R = reach_cells(rs, L, cell_scale(L));
   m32[b] = o;
 }
 

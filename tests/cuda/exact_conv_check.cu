@@ -3,6 +3,7 @@
 // grid for coordinates read from a file (the test compares those with the
 // exact rational floor).
 //   exact_conv_check split <count> <seed>      -> prints mismatches
+//   exact_conv_check reach <count> <seed>      -> prints mismatches
 //   exact_conv_check cells <in.bin> <out.bin>  -> in: n, lo, L, v[n] (double)
 //                                                 out: q[n] (uint64)
 #include <cstdint>
@@ -52,6 +53,36 @@ __global__ void k_split(int64_t n, uint64_t seed, unsigned long long *bad, doubl
   }
 }
 
+// reach_cells against the FP64 expression, on radii of every magnitude and
+// radii within a few ulps of whole and half cells, for boxes of many sides
+__global__ void k_reach(int64_t n, uint64_t seed, unsigned long long *bad, double *first_bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t r = mix64(seed + (uint64_t)i);
+    const double L = ldexp(1.0 + (double)(mix64(r ^ 0x5555ull) >> 11) * 0x1p-53,
+                           (int)((r >> 50) % 40) - 20);
+    const double u = ldexp(L, -P3T_BITS);
+    double rs;
+    const int kind = (int)(r & 3);
+    if (kind == 0) {  // any magnitude up to beyond the cap
+      rs = ldexp(1.0 + (double)(mix64(r) >> 11) * 0x1p-53, (int)((r >> 8) % 64) - 40) * u;
+    } else if (kind == 1) {  // a whole number of cells, a few ulps either side
+      const double m = (double)(mix64(r) % 5000000ull);
+      rs = m * u;
+      for (int s = 0; s < (int)((r >> 20) % 4); ++s) rs = nextafter(rs, (r >> 24) & 1 ? 0.0 : 1e300);
+    } else if (kind == 2) {  // small multiples
+      rs = (double)(mix64(r) % 64ull) * u * (1.0 + ldexp((double)((int)((r >> 30) % 9) - 4), -52));
+    } else {  // the range edges
+      rs = ldexp(1.0, (int)((r >> 8) % 6) + 19) * u * (1.0 + ldexp((double)((int)((r >> 30) % 9) - 4), -52));
+    }
+    if (!(rs >= 0.0)) continue;
+    const int32_t got = reach_cells(rs, L, cell_scale(L));
+    const double rq = ceil(rs / u) + 1.0;
+    const int32_t want = rq < 8388608.0 ? (int32_t)rq : 8388608;
+    if (got != want && atomicAdd(bad, 1ull) == 0ull) *first_bad = rs / u;
+  }
+}
+
 __global__ void k_cells(int64_t n, double lo, double L, const double *v, uint64_t *q) {
   const CellScale cs = cell_scale(L);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -78,6 +109,25 @@ int main(int argc, char **argv) {
     CK(cudaMalloc(&fb, sizeof(*fb)));
     CK(cudaMemset(bad, 0, sizeof(*bad)));
     k_split<<<1024, 256>>>(n, seed, bad, fb);
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    unsigned long long hb = 0;
+    double hf = 0.0;
+    CK(cudaMemcpy(&hb, bad, sizeof(hb), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&hf, fb, sizeof(hf), cudaMemcpyDeviceToHost));
+    printf("{\"checked\": %lld, \"mismatches\": %llu, \"first\": %.17g}\n", (long long)n, hb,
+           hb ? hf : 0.0);
+    return 0;
+  }
+  if (argc == 4 && !strcmp(argv[1], "reach")) {
+    const int64_t n = atoll(argv[2]);
+    const uint64_t seed = strtoull(argv[3], nullptr, 10);
+    unsigned long long *bad;
+    double *fb;
+    CK(cudaMalloc(&bad, sizeof(*bad)));
+    CK(cudaMalloc(&fb, sizeof(*fb)));
+    CK(cudaMemset(bad, 0, sizeof(*bad)));
+    k_reach<<<1024, 256>>>(n, seed, bad, fb);
     CK(cudaGetLastError());
     CK(cudaDeviceSynchronize());
     unsigned long long hb = 0;

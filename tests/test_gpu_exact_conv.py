@@ -5,6 +5,9 @@ checked on the GPU by a small test program built from the same header:
     residual rounded to FP32), formed from integer operations, equals the
     hardware FP64 conversions bit for bit, on random bit patterns, the
     workloads' magnitudes, halfway mantissas and the edges of its range;
+  * a node's search reach ceil(rs / u) + 1 from integer operations equals
+    the FP64 expression it replaces, including radii a few ulps from whole
+    cells, where the rounded quotient and the exact one part;
   * the cell index on the 21-bit grid equals the exact rational floor of
     fl(v - lo) / (L / 2^21), clamped to [0, 2^21), on coordinates on cell
     boundaries, one and two ulps either side, and random ones (the tree's
@@ -42,6 +45,17 @@ def test_split_equals_hardware_conversions(checker, seed):
     import json
     res = json.loads(r.stdout)
     assert res["checked"] == 1 << 24
+    assert res["mismatches"] == 0, res
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_reach_equals_fp64_expression(checker, seed):
+    """A node's search reach ceil(rs / u) + 1 (FP64 quotient, capped at
+    2^23) from integer operations equals the FP64 expression."""
+    import json
+    r = subprocess.run([checker, "reach", str(1 << 24), str(seed)], check=True,
+                       capture_output=True, text=True)
+    res = json.loads(r.stdout)
     assert res["mismatches"] == 0, res
 
 
