@@ -304,12 +304,6 @@ __global__ void k_cut_shared(SegView sv, const unsigned long long *bits, double 
 // =========================================================================
 __global__ void k_set_i64(int64_t *dst, int64_t v) { *dst = v; }
 
-// node count clamped to the capacity (kernels index with the clamped value)
-__global__ void k_clamp_nodes(int64_t *cnt, int64_t node_cap, DevStatus *st) {
-  const int64_t nn = cnt[1];
-  if (nn > node_cap) dev_fail(st, P3T_ERR_CAPACITY, 10, nn);
-  cnt[3] = nn < node_cap ? nn : node_cap;
-}
 __global__ void k_box_init(unsigned long long *bits, int nseg) {
   for (int d = threadIdx.x; d < nseg; d += blockDim.x)
     for (int a = 0; a < 3; ++a) { bits[6 * d + a] = ~0ull; bits[6 * d + 3 + a] = 0ull; }
@@ -325,10 +319,24 @@ __global__ void k_box(SegView sv, int slices, const double *x, const double *y,
   seg_slice(sv, slices, d, sa, sb);
   unsigned long long *bits = bits6 + 6 * d;
   unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
-  for (int64_t i = sa + threadIdx.x; i < sb; i += blockDim.x) {
-    unsigned long long b[3] = {ord_bits(x[i]), ord_bits(y[i]), ord_bits(z[i])};
+  // four elements a trip, their loads issued before the first is used
+  for (int64_t i0 = sa + threadIdx.x; i0 < sb; i0 += 4 * (int64_t)blockDim.x) {
+    double v[4][3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) { lo[a] = b[a] < lo[a] ? b[a] : lo[a]; hi[a] = b[a] > hi[a] ? b[a] : hi[a]; }
+    for (int k = 0; k < 4; ++k) {
+      const int64_t i = i0 + k * (int64_t)blockDim.x;
+      if (i < sb) { v[k][0] = x[i]; v[k][1] = y[i]; v[k][2] = z[i]; }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (i0 + k * (int64_t)blockDim.x < sb) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const unsigned long long b = ord_bits(v[k][a]);
+          lo[a] = b < lo[a] ? b : lo[a];
+          hi[a] = b > hi[a] ? b : hi[a];
+        }
+      }
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -392,8 +400,9 @@ __device__ __forceinline__ uint32_t compact3(uint64_t v) {
 __global__ void k_keys(SegView sv, const double *x, const double *y,
                        const double *z, const double *m, const double *ro,
                        const double *rs, const double *box5, uint64_t *keys,
-                       int32_t *idx, double *pack, int rekey) {
+                       int32_t *idx, double *pack, int rekey, int64_t *d_n) {
   const int64_t n = sv.n;
+  if (d_n && blockIdx.x == 0 && threadIdx.x == 0) *d_n = n;  // for the count-driven primitives
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
        s += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = rekey ? (int64_t)idx[s] : s;
@@ -501,10 +510,17 @@ __global__ void k_levels(SegView sv, int leaf, const int32_t *wlcp,
 // their first particle and level, and the identity order for the level sort;
 // the member counts come from k_node_counts
 __global__ void k_nodes_pre(SegView sv, const int8_t *lp, const int8_t *lv,
-                            const int64_t *nstart, const int64_t *d_nnode, int64_t node_cap,
+                            const int64_t *nstart, int64_t *cnt, int64_t node_cap,
                             int32_t *pre_first, int32_t *pre_level, uint64_t *lvl_keys,
                             int32_t *bfs2pre, DevStatus *st) {
-  if (*d_nnode > node_cap || st->code != 0) return;
+  // the node count (cnt[1], from the scan) clamped to the capacity in cnt[3]:
+  // the later kernels index with the clamped value
+  const int64_t nn = cnt[1];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (nn > node_cap) dev_fail(st, P3T_ERR_CAPACITY, 10, nn);
+    cnt[3] = nn < node_cap ? nn : node_cap;
+  }
+  if (nn > node_cap || st->code != 0) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sv.n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int l0 = (int)lp[i] + 1, L = (int)lv[i];
@@ -1194,14 +1210,12 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   const SegView sv{c->seg_off, nseg, n};
   // one root cube per segment: a few blocks per SM in all, in slices of the
   // segments
-  const int bsl = nseg >= 2 * c->num_sms ? 1 : 2 * c->num_sms / nseg;
+  const int bsl = nseg >= 4 * c->num_sms ? 1 : 4 * c->num_sms / nseg;
   k_box_init<<<1, 256, 0, s>>>(c->box_bits, nseg);
   k_box<<<(unsigned)(bsl * nseg), kBlock, 0, s>>>(sv, bsl, p->x, p->y, p->z, c->box_bits);
   k_box_final<<<1, 256, 0, s>>>(c->box_bits, c->box, nseg);
   k_keys<<<(unsigned)g, kBlock, 0, s>>>(sv, p->x, p->y, p->z, p->m, p->r_out, p->r_search,
-                                        c->box, c->keys, c->idx, c->pack, 0);
-  // n on the device for the count-driven primitives
-  k_set_i64<<<1, 1, 0, s>>>(&cnt[0], n);
+                                        c->box, c->keys, c->idx, c->pack, 0, &cnt[0]);
   rc = p3t_radix_sort(&c->keys, &c->idx, &c->keys_alt, &c->idx_alt, &cnt[0], c->cap,
                       0, 64, c->radix_hist, c->radix_hist_cap, s);
   if (rc) return rc;
@@ -1215,7 +1229,7 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
                         0, sbits, c->radix_hist, c->radix_hist_cap, s);
     if (rc) return rc;
     k_keys<<<(unsigned)g, kBlock, 0, s>>>(sv, p->x, p->y, p->z, p->m, p->r_out, p->r_search,
-                                          c->box, c->keys, c->idx, c->pack, 1);
+                                          c->box, c->keys, c->idx, c->pack, 1, nullptr);
     p3t_note_launches(2);
   }
   auto gather = c->prm.precision == P3T_MIXED ? k_gather<true> : k_gather<false>;
@@ -1226,8 +1240,7 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   k_levels<<<(unsigned)g, kBlock, 0, s>>>(sv, leaf, c->wlcp, c->lp, c->lv, c->ncount);
   rc = p3t_scan_i32_to_i64(c->ncount, c->nstart, &cnt[0], c->cap, &cnt[1], c->scan_state, c->scan_words, c->status, c->poll_limit, s);
   if (rc) return rc;
-  k_clamp_nodes<<<1, 1, 0, s>>>(cnt, c->node_cap, c->status);
-  k_nodes_pre<<<(unsigned)g, kBlock, 0, s>>>(sv, c->lp, c->lv, c->nstart, &cnt[1], c->node_cap,
+  k_nodes_pre<<<(unsigned)g, kBlock, 0, s>>>(sv, c->lp, c->lv, c->nstart, cnt, c->node_cap,
                                              c->pre_first, c->pre_level, c->lvl_keys,
                                              c->bfs2pre, c->status);
   k_node_counts<<<(unsigned)p3t_grid(c->node_cap, kBlock, maxb), kBlock, 0, s>>>(
@@ -1277,9 +1290,9 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   k_group_list<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->group_flag,
                                                c->group_pos, c->pre2bfs, c->group_list);
   // own kernels here (the scans, sorts and moments count themselves): box 3,
-  // keys, n, gather, lcp, levels, clamp, nodes_pre, node_counts, pre2bfs,
-  // nodes_bfs, parents, leaf_list, group_flags, group_list
-  p3t_note_launches(17);
+  // keys, gather, lcp, levels, nodes_pre, node_counts, pre2bfs, nodes_bfs,
+  // parents, leaf_list, group_flags, group_list
+  p3t_note_launches(15);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 
