@@ -75,7 +75,7 @@ void free_particle_buffers(p3t_ctx *c) {
   dfree(c->sx); dfree(c->sy); dfree(c->sz); dfree(c->sm); dfree(c->sro); dfree(c->srs);
   dfree(c->pack);
   dfree(c->sq); dfree(c->spA); dfree(c->spB); dfree(c->srs32); dfree(c->sml);
-  dfree(c->lp); dfree(c->lv); dfree(c->wlcp); dfree(c->ncount); dfree(c->nstart);
+  dfree(c->lp); dfree(c->lv); dfree(c->ncount); dfree(c->nstart);
   dfree(c->pre_first); dfree(c->pre_count); dfree(c->pre_level);
   dfree(c->lvl_keys); dfree(c->lvl_keys_alt); dfree(c->bfs2pre); dfree(c->bfs2pre_alt);
   dfree(c->pre2bfs); dfree(c->node); dfree(c->mom64); dfree(c->mom32); dfree(c->nrs);
@@ -126,7 +126,7 @@ int reserve(p3t_ctx *c, int64_t n, int64_t cand_cap) {
   ok &= dalloc(c->sro, N) && dalloc(c->srs, N) && dalloc(c->sq, 3 * N);
   ok &= dalloc(c->spA, N) && dalloc(c->spB, N) && dalloc(c->srs32, N) &&
         dalloc(c->sml, N);
-  ok &= dalloc(c->lp, N) && dalloc(c->lv, N) && dalloc(c->wlcp, N) && dalloc(c->ncount, N);
+  ok &= dalloc(c->lp, N) && dalloc(c->lv, N) && dalloc(c->ncount, N);
   ok &= dalloc(c->nstart, N);
   ok &= dalloc(c->pre_first, NC) && dalloc(c->pre_count, NC) && dalloc(c->pre_level, NC);
   ok &= dalloc(c->lvl_keys, NC) && dalloc(c->lvl_keys_alt, NC);

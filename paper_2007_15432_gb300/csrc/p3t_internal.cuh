@@ -225,7 +225,6 @@ struct p3t_ctx {
 
   // tree build scratch (per particle)
   int8_t *lp = nullptr, *lv = nullptr;     // lcp with predecessor, leaf level
-  int32_t *wlcp = nullptr;                 // lcp(a, a + leaf)
   int32_t *ncount = nullptr;               // nodes started by particle
   int64_t *nstart = nullptr;               // exclusive scan of ncount
   // nodes (preorder scratch and breadth-first result)

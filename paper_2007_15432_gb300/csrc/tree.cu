@@ -473,36 +473,43 @@ __device__ __forceinline__ int lcp_levels(uint64_t a, uint64_t b) {
   return (__clzll((long long)d) - 1) / 3;
 }
 
-// (each segment's particles are a contiguous sorted run with a tree of its
-// own: a segment's first particle shares no level with its predecessor)
-__global__ void k_lcp(SegView sv, const uint64_t *keys, int leaf, int32_t *wlcp,
-                      int8_t *lp) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sv.n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int d = seg_at(sv, i);
-    const int64_t s0 = seg_lo(sv, d), s1 = seg_hi(sv, d);
-    const uint64_t k = keys[i];
-    lp[i] = (int8_t)(i == s0 ? -1 : lcp_levels(keys[i - 1], k));
-    if (i + leaf < s1) wlcp[i] = lcp_levels(k, keys[i + leaf]);
-  }
-}
-
-// Leaf level of each particle and the number of nodes it starts.  The cell of
-// i at level l holds more than `leaf` particles iff some window of leaf + 1
-// consecutive sorted particles containing i shares the level-l prefix.
-__global__ void k_levels(SegView sv, int leaf, const int32_t *wlcp,
-                         const int8_t *lp, int8_t *lv, int32_t *ncount) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sv.n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int d = seg_at(sv, i);
-    const int64_t s0 = seg_lo(sv, d), s1 = seg_hi(sv, d);
-    int D = -1;
-    int64_t a0 = i - leaf > s0 ? i - leaf : s0;
-    int64_t a1 = i < s1 - 1 - leaf ? i : s1 - 1 - leaf;
-    for (int64_t a = a0; a <= a1; ++a) D = max(D, (int)wlcp[a]);
-    int L = min(D + 1, P3T_BITS);
-    lv[i] = (int8_t)L;
-    ncount[i] = max(0, L - (int)lp[i]);
+// Each particle's common prefix with its predecessor (lp, levels; -1 at a
+// segment's first particle), its leaf level and the number of nodes it starts.
+// The cell of i at level l holds more than `leaf` particles iff some window
+// of leaf + 1 consecutive sorted particles containing i (within its segment)
+// shares the level-l prefix; the window prefixes w(a) = lcp(a, a + leaf) of a
+// block's tile and the `leaf` positions before it are formed once in shared
+// memory.  (Each segment's particles are a contiguous sorted run with a tree
+// of its own.)
+constexpr int kLevelTile = 256;  // = kBlock
+__global__ void __launch_bounds__(kLevelTile)
+k_lcp_levels(SegView sv, const uint64_t *keys, int leaf, int8_t *lp, int8_t *lv,
+             int32_t *ncount) {
+  __shared__ int8_t w[kLevelTile + 32];  // leaf <= 32
+  const int64_t n = sv.n;
+  for (int64_t t0 = (int64_t)blockIdx.x * kLevelTile; t0 < n;
+       t0 += (int64_t)gridDim.x * kLevelTile) {
+    __syncthreads();
+    for (int j = threadIdx.x; j < kLevelTile + leaf; j += kLevelTile) {
+      const int64_t a = t0 - leaf + j;
+      w[j] = (a >= 0 && a + leaf < n) ? (int8_t)lcp_levels(keys[a], keys[a + leaf]) : (int8_t)-1;
+    }
+    __syncthreads();
+    const int64_t i = t0 + threadIdx.x;
+    if (i < n) {
+      const int d = seg_at(sv, i);
+      const int64_t s0 = seg_lo(sv, d), s1 = seg_hi(sv, d);
+      const uint64_t k = keys[i];
+      const int p = i == s0 ? -1 : lcp_levels(keys[i - 1], k);
+      lp[i] = (int8_t)p;
+      int D = -1;
+      const int64_t a0 = i - leaf > s0 ? i - leaf : s0;
+      const int64_t a1 = i < s1 - 1 - leaf ? i : s1 - 1 - leaf;
+      for (int64_t a = a0; a <= a1; ++a) D = max(D, (int)w[a - (t0 - leaf)]);
+      const int L = min(D + 1, P3T_BITS);
+      lv[i] = (int8_t)L;
+      ncount[i] = max(0, L - p);
+    }
   }
 }
 
@@ -1236,8 +1243,8 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   gather<<<(unsigned)g, kBlock, 0, s>>>(n, c->idx, c->keys, c->pack, c->sx, c->sy, c->sz,
                                           c->sm, c->sro, c->srs, c->sq, c->spA, c->spB,
                                           c->srs32, c->sml);
-  k_lcp<<<(unsigned)g, kBlock, 0, s>>>(sv, c->keys, leaf, c->wlcp, c->lp);
-  k_levels<<<(unsigned)g, kBlock, 0, s>>>(sv, leaf, c->wlcp, c->lp, c->lv, c->ncount);
+  k_lcp_levels<<<(unsigned)p3t_grid(n, kLevelTile, maxb), kLevelTile, 0, s>>>(
+      sv, c->keys, leaf, c->lp, c->lv, c->ncount);
   rc = p3t_scan_i32_to_i64(c->ncount, c->nstart, &cnt[0], c->cap, &cnt[1], c->scan_state, c->scan_words, c->status, c->poll_limit, s);
   if (rc) return rc;
   k_nodes_pre<<<(unsigned)g, kBlock, 0, s>>>(sv, c->lp, c->lv, c->nstart, cnt, c->node_cap,
@@ -1290,9 +1297,9 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   k_group_list<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->group_flag,
                                                c->group_pos, c->pre2bfs, c->group_list);
   // own kernels here (the scans, sorts and moments count themselves): box 3,
-  // keys, gather, lcp, levels, nodes_pre, node_counts, pre2bfs, nodes_bfs,
+  // keys, gather, lcp_levels, nodes_pre, node_counts, pre2bfs, nodes_bfs,
   // parents, leaf_list, group_flags, group_list
-  p3t_note_launches(15);
+  p3t_note_launches(14);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 
