@@ -42,9 +42,10 @@ __device__ int64_t block_excl_scan(int64_t v, int64_t *excl, int64_t *sh) {
 // time and stops at the nearest one that holds an inclusive prefix), and
 // publishes its own inclusive prefix.  A word holds a flag in bits 63-62 (1:
 // the tile's own sum, 2: inclusive prefix) and the value in bits 61-0
-// (non-negative inputs).  The last block to finish (counter state[1]) clears
-// the words it used and both counters, so that the next call starts clean
-// with no host involvement.  A bounded number of polls: a predecessor that
+// (non-negative inputs).  The grid is sized for the capacity; only as many
+// blocks as the count has tiles take one, the rest return at once.  The last
+// block to finish (counter state[1]) clears the words it used and both
+// counters, so that the next call starts clean with no host involvement.  A bounded number of polls: a predecessor that
 // never publishes is reported (P3T_ERR_TIMEOUT) and counted as zero.
 constexpr int kScanThreads = 512;
 constexpr int kScanPer = 8;
@@ -62,10 +63,15 @@ scan_onepass(const int32_t *in, int64_t *out, const int64_t *d_n, int64_t *d_tot
   __shared__ unsigned long long s_tile;
   __shared__ int64_t s_prefix;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int64_t n = *d_n;
+  // the grid is sized for the capacity: only the first `used` blocks take
+  // tiles (and count themselves out below); the others return at once
+  const int64_t used = (n + kScanTile - 1) / kScanTile;
+  const int64_t takers = used < 1 ? 1 : (used < (int64_t)gridDim.x ? used : (int64_t)gridDim.x);
+  if ((int64_t)blockIdx.x >= takers) return;
   if (t == 0) s_tile = atomicAdd(&state[0], 1ull);
   __syncthreads();
   const int64_t tile = (int64_t)s_tile;
-  const int64_t n = *d_n;
   const int64_t base = tile * kScanTile;
   unsigned long long *ts = state + 2;
   if (base < n) {
@@ -148,12 +154,11 @@ scan_onepass(const int32_t *in, int64_t *out, const int64_t *d_n, int64_t *d_tot
   __syncthreads();
   if (t == 0) {
     __threadfence();
-    s_last = atomicAdd(&state[1], 1ull) == (unsigned long long)gridDim.x - 1;
+    s_last = atomicAdd(&state[1], 1ull) == (unsigned long long)takers - 1;
   }
   __syncthreads();
   if (s_last) {
     __threadfence();
-    const int64_t used = (n + kScanTile - 1) / kScanTile;
     for (int64_t k = t; k < used; k += kScanThreads) ts[k] = 0ull;
     if (t == 0) { state[0] = 0ull; state[1] = 0ull; }
   }
