@@ -226,6 +226,19 @@ __global__ void __launch_bounds__(kRadix) radix_row_scan(uint32_t *hist, int nti
   if (threadIdx.x == 0) digit_total[blockIdx.x] = (uint32_t)carry;
 }
 
+// The lanes of the warp whose (valid) digit equals this lane's: eight ballots,
+// one a bit of the digit (on this part cheaper than __match_any_sync); zero
+// for an invalid lane
+__device__ __forceinline__ uint32_t match_digit(uint32_t d, bool valid) {
+  uint32_t m = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+  for (int b = 0; b < kRadixBits; ++b) {
+    const uint32_t bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+    m &= ((d >> b) & 1u) ? bb : ~bb;
+  }
+  return valid ? m : 0u;
+}
+
 // Stable scatter of one tile: the tile's elements are ranked by (digit,
 // position), placed digit-ordered in shared memory, then written out so that
 // consecutive threads write consecutive addresses of one digit's run.
@@ -274,10 +287,10 @@ radix_downsweep(const uint64_t *keys, const int32_t *vals, uint64_t *okeys,
       __syncthreads();
       const int64_t e = base + r * kSortThreads + t;
       const bool valid = e < n;
-      // invalid lanes form their own group
+      // invalid lanes belong to no group
       const uint32_t d = valid ? (uint32_t)((key[r] >> shift) & (kRadix - 1)) : kRadix;
       dig[r] = d;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t peers = match_digit(d, valid);
       if (valid && lane == __ffs(peers) - 1) s_warp[w][d] = __popc(peers);
       __syncthreads();
       {
