@@ -302,6 +302,30 @@ struct p3t_ctx {
 // kernels launched by the library in this process (diagnostics)
 void p3t_note_launches(int64_t k);
 
+// ---- programmatic dependent launch ------------------------------------------
+// A kernel launched with pdl_launch may be scheduled while its predecessor on
+// the stream is still finishing (its blocks are dispatched as the
+// predecessor's last blocks exit, the launch latency hidden); it calls
+// pdl_wait() before anything else, which returns once the predecessor has
+// completed and its writes are visible.  Launched the ordinary way, pdl_wait()
+// returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 #define P3T_CUDA_TRY(x)                      \
   do {                                       \
     cudaError_t e_ = (x);                    \

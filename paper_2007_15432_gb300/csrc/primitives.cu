@@ -55,6 +55,7 @@ constexpr unsigned long long kValMask = (1ull << 62) - 1;
 __global__ void __launch_bounds__(kScanThreads)
 scan_onepass(const int32_t *in, int64_t *out, const int64_t *d_n, int64_t *d_total,
              unsigned long long *state, DevStatus *st, int64_t poll_limit) {
+  pdl_wait();
   __shared__ int64_t sh[33];
   // the tile: first its int32 inputs, then its int64 outputs (staged so that
   // both the loads and the stores are coalesced)
@@ -181,6 +182,7 @@ __device__ __forceinline__ int64_t radix_tiles(const int64_t *d_n) {
 
 __global__ void radix_upsweep(const uint64_t *keys, const int64_t *d_n,
                               int shift, uint32_t *hist, int ntiles) {
+  pdl_wait();
   __shared__ uint32_t h[kRadix];
   const int64_t n = *d_n;
   const int64_t used = radix_tiles(d_n);
@@ -211,6 +213,7 @@ __global__ void radix_upsweep(const uint64_t *keys, const int64_t *d_n,
 __global__ void __launch_bounds__(kRadix) radix_row_scan(uint32_t *hist, int ntiles,
                                                          uint32_t *digit_total,
                                                          const int64_t *d_n) {
+  pdl_wait();
   __shared__ int64_t sh[33];
   uint32_t *row = hist + (int64_t)blockIdx.x * ntiles;
   const int used = (int)radix_tiles(d_n);
@@ -246,6 +249,7 @@ __global__ void __launch_bounds__(kSortThreads)
 radix_downsweep(const uint64_t *keys, const int32_t *vals, uint64_t *okeys,
                 int32_t *ovals, const int64_t *d_n, int shift,
                 const uint32_t *hist, int ntiles, const uint32_t *digit_total) {
+  pdl_wait();
   __shared__ uint32_t s_warp[kSortThreads / 32][kRadix];
   __shared__ uint32_t s_run[kRadix];
   __shared__ uint32_t s_gbase[kRadix];  // first output index of the tile's digit d
@@ -345,7 +349,7 @@ int p3t_scan_i32_to_i64(const int32_t *in, int64_t *out, const int64_t *d_n,
   int64_t G = (n_cap + kScanTile - 1) / kScanTile;
   if (G < 1) G = 1;
   if (G + 2 > state_words) return P3T_ERR_CAPACITY;
-  scan_onepass<<<(unsigned)G, kScanThreads, 0, s>>>(in, out, d_n, d_total, state, st,
+  pdl_launch(scan_onepass, dim3((unsigned)G), dim3(kScanThreads), s, in, out, d_n, d_total, state, st,
                                                     poll_limit);
   p3t_note_launches(1);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
@@ -366,10 +370,10 @@ int p3t_radix_sort(uint64_t **keys, int32_t **vals, uint64_t **keys_alt,
   if (ntiles * kRadix + kRadix > hist_cap) return P3T_ERR_CAPACITY;
   uint32_t *digit_total = hist + ntiles * kRadix;
   for (int shift = begin_bit; shift < end_bit; shift += kRadixBits) {
-    radix_upsweep<<<(unsigned)ntiles, kSortThreads, 0, s>>>(*keys, d_n, shift,
+    pdl_launch(radix_upsweep, dim3((unsigned)ntiles), dim3(kSortThreads), s, *keys, d_n, shift,
                                                             hist, (int)ntiles);
-    radix_row_scan<<<kRadix, kRadix, 0, s>>>(hist, (int)ntiles, digit_total, d_n);
-    radix_downsweep<<<(unsigned)ntiles, kSortThreads, 0, s>>>(
+    pdl_launch(radix_row_scan, dim3(kRadix), dim3(kRadix), s, hist, (int)ntiles, digit_total, d_n);
+    pdl_launch(radix_downsweep, dim3((unsigned)ntiles), dim3(kSortThreads), s, 
         *keys, *vals, *keys_alt, *vals_alt, d_n, shift, hist, (int)ntiles, digit_total);
     p3t_note_launches(3);
     uint64_t *tk = *keys; *keys = *keys_alt; *keys_alt = tk;

@@ -29,6 +29,7 @@ __device__ __forceinline__ double ord_double(unsigned long long b) {
 // the largest r_out and r_search (shared scheme)
 __global__ void k_cut_init(unsigned long long *bits, int nseg, double *bsum,
                            unsigned long long *bcnt, int nb) {
+  pdl_wait();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   for (int d = t; d < nseg; d += gridDim.x * blockDim.x) {
     bits[4 * d] = ~0ull; bits[4 * d + 1] = 0ull; bits[4 * d + 2] = 0ull; bits[4 * d + 3] = 0ull;
@@ -49,6 +50,7 @@ __device__ __forceinline__ void seg_slice(const SegView &sv, int slices, int &d,
 
 __global__ void k_cut_range(SegView sv, int slices, const double *x, const double *y,
                             unsigned long long *bits) {
+  pdl_wait();
   int d;
   int64_t a, b;
   seg_slice(sv, slices, d, a, b);
@@ -71,6 +73,7 @@ __global__ void k_cut_range(SegView sv, int slices, const double *x, const doubl
 // single system), first global bin and log R range
 __global__ void k_cut_segbins(SegView sv, int vran_bins, const unsigned long long *bits,
                               int32_t *seg_nb, int32_t *seg_base, double *seg_l) {
+  pdl_wait();
   __shared__ int wsum[32];
   __shared__ int carry;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -147,6 +150,7 @@ __global__ void k_cut_u2(SegView sv, const double *x, const double *y, const dou
                          const unsigned long long *bits, int nb, const int32_t *seg_nb,
                          const int32_t *seg_base, const double *seg_l, double *u2,
                          uint64_t *key, int32_t *idx, int32_t *bin, unsigned long long *bcnt) {
+  pdl_wait();
   __shared__ uint32_t h[kMaxBins];
   for (int k = threadIdx.x; k < nb; k += blockDim.x) h[k] = 0;
   __syncthreads();
@@ -190,6 +194,7 @@ __global__ void k_cut_u2(SegView sv, const double *x, const double *y, const dou
 // exclusive offsets of the bins (at most 4096): one block, chunks of its
 // size scanned with warp shuffles and carried
 __global__ void k_cut_offsets(int nb, const unsigned long long *bcnt, int64_t *boff) {
+  pdl_wait();
   __shared__ int64_t wsum[32];
   __shared__ int64_t carry;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -229,6 +234,7 @@ __global__ void k_cut_offsets(int nb, const unsigned long long *bcnt, int64_t *b
 // shuffle tree: the same sum on every run)
 __global__ void k_cut_binsum(int nb, const int64_t *boff, const int32_t *sorted_idx,
                              const double *u2, double *bvr) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -260,6 +266,7 @@ __global__ void k_cut_final(SegView sv, const double *x, const double *y,
                             const double *vz, const double *m, p3t_params prm,
                             unsigned long long *bits, const int32_t *bin,
                             const double *bvr, double *r_out, double *r_search) {
+  pdl_wait();
   const double imu = 1.0 / (prm.G * prm.m_star), i3ms = 1.0 / (3.0 * prm.m_star);
   const int64_t n = sv.n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -291,6 +298,7 @@ __global__ void k_cut_final(SegView sv, const double *x, const double *y,
 // largest search radius
 __global__ void k_cut_shared(SegView sv, const unsigned long long *bits, double *r_out,
                              double *r_search) {
+  pdl_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sv.n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int d = seg_at(sv, i);
@@ -302,9 +310,11 @@ __global__ void k_cut_shared(SegView sv, const unsigned long long *bits, double 
 // =========================================================================
 // Keys, sort, octree, moments.
 // =========================================================================
-__global__ void k_set_i64(int64_t *dst, int64_t v) { *dst = v; }
+__global__ void k_set_i64(int64_t *dst, int64_t v) {
+  pdl_wait(); *dst = v; }
 
 __global__ void k_box_init(unsigned long long *bits, int nseg) {
+  pdl_wait();
   for (int d = threadIdx.x; d < nseg; d += blockDim.x)
     for (int a = 0; a < 3; ++a) { bits[6 * d + a] = ~0ull; bits[6 * d + 3 + a] = 0ull; }
 }
@@ -313,6 +323,7 @@ __global__ void k_box_init(unsigned long long *bits, int nseg) {
 // a block's slice of its segment, then six atomics per block
 __global__ void k_box(SegView sv, int slices, const double *x, const double *y,
                       const double *z, unsigned long long *bits6) {
+  pdl_wait();
   __shared__ unsigned long long red[6][kBlock / 32];
   int d;
   int64_t sa, sb;
@@ -361,6 +372,7 @@ __global__ void k_box(SegView sv, int slices, const double *x, const double *y,
 // root cube of each segment: corner at the per-axis minimum, side = largest
 // extent; box[5 d ..]: corner, side L, quantisation scale S
 __global__ void k_box_final(const unsigned long long *bits6, double *box5, int nseg) {
+  pdl_wait();
   for (int d = threadIdx.x; d < nseg; d += blockDim.x) {
     const unsigned long long *bits = bits6 + 6 * d;
     double *box = box5 + 5 * d;
@@ -401,6 +413,7 @@ __global__ void k_keys(SegView sv, const double *x, const double *y,
                        const double *z, const double *m, const double *ro,
                        const double *rs, const double *box5, uint64_t *keys,
                        int32_t *idx, double *pack, int rekey, int64_t *d_n) {
+  pdl_wait();
   const int64_t n = sv.n;
   if (d_n && blockIdx.x == 0 && threadIdx.x == 0) *d_n = n;  // for the count-driven primitives
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
@@ -425,6 +438,7 @@ __global__ void k_keys(SegView sv, const double *x, const double *y,
 // the segment of the particle in each slot, as the key of a stable sort
 // that brings each segment's particles together in key order
 __global__ void k_segkey(SegView sv, const int32_t *idx, uint64_t *keys) {
+  pdl_wait();
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < sv.n;
        s += (int64_t)gridDim.x * blockDim.x)
     keys[s] = (uint64_t)seg_of(sv, idx[s]);
@@ -437,6 +451,7 @@ __global__ void k_gather(int64_t n, const int32_t *idx, const uint64_t *keys,
                          const double *pack, double *sx, double *sy, double *sz, double *sm,
                          double *sro, double *srs, int32_t *sq, float4 *spA,
                          float4 *spB, float *srs32, float *sml) {
+  pdl_wait();
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
        s += (int64_t)gridDim.x * blockDim.x) {
     const int32_t i = idx[s];
@@ -485,6 +500,7 @@ constexpr int kLevelTile = 256;  // = kBlock
 __global__ void __launch_bounds__(kLevelTile)
 k_lcp_levels(SegView sv, const uint64_t *keys, int leaf, int8_t *lp, int8_t *lv,
              int32_t *ncount) {
+  pdl_wait();
   __shared__ int8_t w[kLevelTile + 32];  // leaf <= 32
   const int64_t n = sv.n;
   for (int64_t t0 = (int64_t)blockIdx.x * kLevelTile; t0 < n;
@@ -520,6 +536,7 @@ __global__ void k_nodes_pre(SegView sv, const int8_t *lp, const int8_t *lv,
                             const int64_t *nstart, int64_t *cnt, int64_t node_cap,
                             int32_t *pre_first, int32_t *pre_level, uint64_t *lvl_keys,
                             int32_t *bfs2pre, DevStatus *st) {
+  pdl_wait();
   // the node count (cnt[1], from the scan) clamped to the capacity in cnt[3]:
   // the later kernels index with the clamped value
   const int64_t nn = cnt[1];
@@ -551,6 +568,7 @@ __global__ void k_nodes_pre(SegView sv, const int8_t *lp, const int8_t *lv,
 __global__ void k_node_counts(SegView sv, const uint64_t *keys, const int64_t *d_nnode,
                               int64_t node_cap, const int32_t *pre_first,
                               const int32_t *pre_level, int32_t *pre_count, DevStatus *st) {
+  pdl_wait();
   if (*d_nnode > node_cap || st->code != 0) return;
   const int64_t nn = *d_nnode;
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nn;
@@ -607,6 +625,7 @@ __global__ void k_node_counts(SegView sv, const uint64_t *keys, const int64_t *d
 
 __global__ void k_pre2bfs(const int64_t *d_nnode, int64_t node_cap,
                           const int32_t *bfs2pre, int32_t *pre2bfs) {
+  pdl_wait();
   const int64_t nn = min(*d_nnode, node_cap);
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nn;
        b += (int64_t)gridDim.x * blockDim.x)
@@ -620,6 +639,7 @@ __global__ void k_nodes_bfs(const int64_t *d_nnode, int64_t node_cap,
                             const int8_t *lv, const int64_t *nstart,
                             const int32_t *sq, TreeNode *node,
                             int32_t *leaf_flag, int32_t *node_done, DevStatus *st) {
+  pdl_wait();
   const int64_t nn = min(*d_nnode, node_cap);
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nn;
        b += (int64_t)gridDim.x * blockDim.x) {
@@ -665,6 +685,7 @@ __global__ void k_nodes_bfs(const int64_t *d_nnode, int64_t node_cap,
 }
 
 __global__ void k_parents(const int64_t *d_nnode, int64_t node_cap, TreeNode *node) {
+  pdl_wait();
   const int64_t nn = min(*d_nnode, node_cap);
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nn;
        b += (int64_t)gridDim.x * blockDim.x) {
@@ -677,6 +698,7 @@ __global__ void k_parents(const int64_t *d_nnode, int64_t node_cap, TreeNode *no
 __global__ void k_leaf_list(const int64_t *d_nnode, int64_t node_cap,
                             const int32_t *leaf_flag, const int64_t *leaf_pos,
                             const int32_t *pre2bfs, int32_t *leaf_list) {
+  pdl_wait();
   const int64_t nn = min(*d_nnode, node_cap);
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nn;
        p += (int64_t)gridDim.x * blockDim.x)
@@ -688,6 +710,7 @@ __global__ void k_leaf_list(const int64_t *d_nnode, int64_t node_cap,
 __global__ void k_group_flags(const int64_t *d_nnode, int64_t node_cap,
                               const TreeNode *node, const int32_t *bfs2pre, int gs,
                               int32_t *group_flag) {
+  pdl_wait();
   const int64_t nn = min(*d_nnode, node_cap);
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nn;
        b += (int64_t)gridDim.x * blockDim.x) {
@@ -702,6 +725,7 @@ __global__ void k_group_flags(const int64_t *d_nnode, int64_t node_cap,
 __global__ void k_group_list(const int64_t *d_nnode, int64_t node_cap,
                              const int32_t *group_flag, const int64_t *group_pos,
                              const int32_t *pre2bfs, int32_t *group_list) {
+  pdl_wait();
   const int64_t nn = min(*d_nnode, node_cap);
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nn;
        p += (int64_t)gridDim.x * blockDim.x) {
@@ -742,6 +766,7 @@ __global__ void k_moments_leaf(
     const int64_t *d_nleaf, const int32_t *leaf_list, TreeNode *node, Mom64 *m64, Mom32 *m32,
     double *nrs, const double *sx, const double *sy, const double *sz, const double *sm,
     const double *srs, const int32_t *sq, const double *box, SegView sv) {
+  pdl_wait();
   const int64_t nleaf = *d_nleaf;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nleaf;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -939,6 +964,7 @@ __global__ void k_moments_up32(
     const int64_t *d_nleaf, const int32_t *leaf_list, TreeNode *node, Mom32 *m32, double *nrs,
     const float4 *spA, const float4 *spB, const float *sml, const double *srs,
     const int32_t *sq, const double *box, SegView sv, int32_t *node_done) {
+  pdl_wait();
   const int64_t nleaf = *d_nleaf;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nleaf;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -971,6 +997,7 @@ __device__ __forceinline__ int64_t level_begin(const TreeNode *node, int64_t nn,
 // ascend in breadth-first order): one thread per level
 __global__ void k_level_offsets(const int64_t *d_nnode, int64_t node_cap, const TreeNode *node,
                                 int64_t *lvl_start) {
+  pdl_wait();
   const int64_t nn = min(*d_nnode, node_cap);
   const int l = threadIdx.x;
   if (l <= P3T_BITS + 1) lvl_start[l] = l == P3T_BITS + 1 ? nn : level_begin(node, nn, l);
@@ -1114,6 +1141,7 @@ constexpr int kDeepLevel = 12;
 __global__ void k_moments_level(int level_hi, int level_lo, const int64_t *lvl_start,
                                 TreeNode *node, Mom64 *m64, Mom32 *m32, double *nrs,
                                 const double *box, SegView sv, int64_t warp_target) {
+  pdl_wait();
   for (int l = level_hi; l >= level_lo; --l) {
     moments_level(l, lvl_start, node, m64, m32, nrs, box, sv, warp_target);
     if (l > level_lo) {
@@ -1125,6 +1153,7 @@ __global__ void k_moments_level(int level_hi, int level_lo, const int64_t *lvl_s
 
 __global__ void k_tree_stats(const int64_t *d_nnode, int64_t node_cap,
                              const TreeNode *node, int64_t *stats) {
+  pdl_wait();
   const int64_t nn = min(*d_nnode, node_cap);
   unsigned long long depth = 0, maxleaf = 0, nleaf = 0;
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nn;
@@ -1218,10 +1247,10 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   // one root cube per segment: a few blocks per SM in all, in slices of the
   // segments
   const int bsl = nseg >= 4 * c->num_sms ? 1 : 4 * c->num_sms / nseg;
-  k_box_init<<<1, 256, 0, s>>>(c->box_bits, nseg);
-  k_box<<<(unsigned)(bsl * nseg), kBlock, 0, s>>>(sv, bsl, p->x, p->y, p->z, c->box_bits);
-  k_box_final<<<1, 256, 0, s>>>(c->box_bits, c->box, nseg);
-  k_keys<<<(unsigned)g, kBlock, 0, s>>>(sv, p->x, p->y, p->z, p->m, p->r_out, p->r_search,
+  pdl_launch(k_box_init, dim3(1), dim3(256), s, c->box_bits, nseg);
+  pdl_launch(k_box, dim3((unsigned)(bsl * nseg)), dim3(kBlock), s, sv, bsl, p->x, p->y, p->z, c->box_bits);
+  pdl_launch(k_box_final, dim3(1), dim3(256), s, c->box_bits, c->box, nseg);
+  pdl_launch(k_keys, dim3((unsigned)g), dim3(kBlock), s, sv, p->x, p->y, p->z, p->m, p->r_out, p->r_search,
                                         c->box, c->keys, c->idx, c->pack, 0, &cnt[0]);
   rc = p3t_radix_sort(&c->keys, &c->idx, &c->keys_alt, &c->idx_alt, &cnt[0], c->cap,
                       0, 64, c->radix_hist, c->radix_hist_cap, s);
@@ -1231,70 +1260,70 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
     // then the keys of the new order
     int sbits = 0;
     while ((1 << sbits) < nseg) ++sbits;
-    k_segkey<<<(unsigned)g, kBlock, 0, s>>>(sv, c->idx, c->keys);
+    pdl_launch(k_segkey, dim3((unsigned)g), dim3(kBlock), s, sv, c->idx, c->keys);
     rc = p3t_radix_sort(&c->keys, &c->idx, &c->keys_alt, &c->idx_alt, &cnt[0], c->cap,
                         0, sbits, c->radix_hist, c->radix_hist_cap, s);
     if (rc) return rc;
-    k_keys<<<(unsigned)g, kBlock, 0, s>>>(sv, p->x, p->y, p->z, p->m, p->r_out, p->r_search,
+    pdl_launch(k_keys, dim3((unsigned)g), dim3(kBlock), s, sv, p->x, p->y, p->z, p->m, p->r_out, p->r_search,
                                           c->box, c->keys, c->idx, c->pack, 1, nullptr);
     p3t_note_launches(2);
   }
   auto gather = c->prm.precision == P3T_MIXED ? k_gather<true> : k_gather<false>;
-  gather<<<(unsigned)g, kBlock, 0, s>>>(n, c->idx, c->keys, c->pack, c->sx, c->sy, c->sz,
+  pdl_launch(gather, dim3((unsigned)g), dim3(kBlock), s, n, c->idx, c->keys, c->pack, c->sx, c->sy, c->sz,
                                           c->sm, c->sro, c->srs, c->sq, c->spA, c->spB,
                                           c->srs32, c->sml);
-  k_lcp_levels<<<(unsigned)p3t_grid(n, kLevelTile, maxb), kLevelTile, 0, s>>>(
+  pdl_launch(k_lcp_levels, dim3((unsigned)p3t_grid(n, kLevelTile, maxb)), dim3(kLevelTile), s, 
       sv, c->keys, leaf, c->lp, c->lv, c->ncount);
   rc = p3t_scan_i32_to_i64(c->ncount, c->nstart, &cnt[0], c->cap, &cnt[1], c->scan_state, c->scan_words, c->status, c->poll_limit, s);
   if (rc) return rc;
-  k_nodes_pre<<<(unsigned)g, kBlock, 0, s>>>(sv, c->lp, c->lv, c->nstart, cnt, c->node_cap,
+  pdl_launch(k_nodes_pre, dim3((unsigned)g), dim3(kBlock), s, sv, c->lp, c->lv, c->nstart, cnt, c->node_cap,
                                              c->pre_first, c->pre_level, c->lvl_keys,
                                              c->bfs2pre, c->status);
-  k_node_counts<<<(unsigned)p3t_grid(c->node_cap, kBlock, maxb), kBlock, 0, s>>>(
+  pdl_launch(k_node_counts, dim3((unsigned)p3t_grid(c->node_cap, kBlock, maxb)), dim3(kBlock), s, 
       sv, c->keys, &cnt[1], c->node_cap, c->pre_first, c->pre_level, c->pre_count, c->status);
   rc = p3t_radix_sort(&c->lvl_keys, &c->bfs2pre, &c->lvl_keys_alt, &c->bfs2pre_alt, &cnt[3],
                       c->node_cap, 0, 8, c->radix_hist, c->radix_hist_cap, s);
   if (rc) return rc;
   const int64_t gn = p3t_grid(c->node_cap, kBlock, maxb);
-  k_pre2bfs<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->bfs2pre, c->pre2bfs);
-  k_nodes_bfs<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->bfs2pre, c->pre2bfs,
+  pdl_launch(k_pre2bfs, dim3((unsigned)gn), dim3(kBlock), s, &cnt[3], c->node_cap, c->bfs2pre, c->pre2bfs);
+  pdl_launch(k_nodes_bfs, dim3((unsigned)gn), dim3(kBlock), s, &cnt[3], c->node_cap, c->bfs2pre, c->pre2bfs,
                                               c->pre_first, c->pre_count, c->pre_level,
                                               c->lp, c->lv, c->nstart, c->sq, c->node,
                                               c->leaf_flag, c->node_done, c->status);
-  k_parents<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->node);
+  pdl_launch(k_parents, dim3((unsigned)gn), dim3(kBlock), s, &cnt[3], c->node_cap, c->node);
   rc = p3t_scan_i32_to_i64(c->leaf_flag, c->leaf_pos, &cnt[3], c->node_cap, &cnt[2],
                            c->scan_state, c->scan_words, c->status, c->poll_limit, s);
   if (rc) return rc;
-  k_leaf_list<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->leaf_flag,
+  pdl_launch(k_leaf_list, dim3((unsigned)gn), dim3(kBlock), s, &cnt[3], c->node_cap, c->leaf_flag,
                                               c->leaf_pos, c->pre2bfs, c->leaf_list);
   if (c->prm.precision == P3T_MIXED) {
-    k_moments_up32<<<(unsigned)p3t_grid(c->node_cap, 128, maxb), 128, 0, s>>>(
+    pdl_launch(k_moments_up32, dim3((unsigned)p3t_grid(c->node_cap, 128, maxb)), dim3(128), s, 
         &cnt[2], c->leaf_list, c->node, c->mom32, c->nrs, c->spA, c->spB, c->sml, c->srs,
         c->sq, c->box, sv, c->node_done);
     p3t_note_launches(1);
   } else {
-    k_moments_leaf<<<(unsigned)p3t_grid(c->node_cap, 128, maxb), 128, 0, s>>>(
+    pdl_launch(k_moments_leaf, dim3((unsigned)p3t_grid(c->node_cap, 128, maxb)), dim3(128), s, 
         &cnt[2], c->leaf_list, c->node, c->mom64, c->mom32, c->nrs, c->sx, c->sy, c->sz, c->sm,
         c->srs, c->sq, c->box, sv);
     // internal nodes, level by level, deepest first
     int64_t *lvl_start = c->counters + 32;  // [P3T_BITS + 2]
-    k_level_offsets<<<1, 32, 0, s>>>(&cnt[3], c->node_cap, c->node, lvl_start);
+    pdl_launch(k_level_offsets, dim3(1), dim3(32), s, &cnt[3], c->node_cap, c->node, lvl_start);
     // the deep levels (empty or nearly so in a disk) in one single-block
     // launch, then one launch a level at about one warp per sub-partition
-    k_moments_level<<<1, 128, 0, s>>>(P3T_BITS - 1, kDeepLevel, lvl_start, c->node, c->mom64,
+    pdl_launch(k_moments_level, dim3(1), dim3(128), s, P3T_BITS - 1, kDeepLevel, lvl_start, c->node, c->mom64,
                                       c->mom32, c->nrs, c->box, sv, 4);
     const int64_t wt = (int64_t)c->num_sms * 4;
     for (int l = kDeepLevel - 1; l >= 0; --l)
-      k_moments_level<<<(unsigned)c->num_sms, 128, 0, s>>>(l, l, lvl_start, c->node, c->mom64,
+      pdl_launch(k_moments_level, dim3((unsigned)c->num_sms), dim3(128), s, l, l, lvl_start, c->node, c->mom64,
                                                            c->mom32, c->nrs, c->box, sv, wt);
     p3t_note_launches(3 + kDeepLevel);  // leaves, level offsets, deep levels, one a level
   }
-  k_group_flags<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->node, c->bfs2pre,
+  pdl_launch(k_group_flags, dim3((unsigned)gn), dim3(kBlock), s, &cnt[3], c->node_cap, c->node, c->bfs2pre,
                                                 c->prm.group_size, c->group_flag);
   rc = p3t_scan_i32_to_i64(c->group_flag, c->group_pos, &cnt[3], c->node_cap, &cnt[15],
                            c->scan_state, c->scan_words, c->status, c->poll_limit, s);
   if (rc) return rc;
-  k_group_list<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->group_flag,
+  pdl_launch(k_group_list, dim3((unsigned)gn), dim3(kBlock), s, &cnt[3], c->node_cap, c->group_flag,
                                                c->group_pos, c->pre2bfs, c->group_list);
   // own kernels here (the scans, sorts and moments count themselves): box 3,
   // keys, gather, lcp_levels, nodes_pre, node_counts, pre2bfs, nodes_bfs,
