@@ -21,6 +21,7 @@ __global__ void k_kick(int64_t n, double *vx, double *vy, double *vz,
                        const double *ax, const double *ay, const double *az,
                        double h, const int32_t *slot, const int4 *ent, const double *m,
                        double *esoft) {
+  pdl_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t s = slot ? slot[i] : -1;
@@ -336,6 +337,7 @@ __device__ __forceinline__ KepFF kep_ff(const KepConst &K) {
 template <bool MIXED>
 __global__ void k_kepler(const int64_t *d_nsingle, const int32_t *singles,
                          p3t_particles p, double dt, KepConst K, DevStatus *st) {
+  pdl_wait();
   const int64_t ns = *d_nsingle;
   KepFF KF;
   if constexpr (MIXED) KF = kep_ff(K);
@@ -354,6 +356,7 @@ __global__ void k_kepler(const int64_t *d_nsingle, const int32_t *singles,
 // every particle of p (p3t_kepler_drift)
 template <bool MIXED>
 __global__ void k_kepler_all(p3t_particles p, double dt, KepConst K, DevStatus *st) {
+  pdl_wait();
   KepFF KF;
   if constexpr (MIXED) KF = kep_ff(K);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n;
@@ -1010,6 +1013,7 @@ __global__ void __launch_bounds__(NT) k_hermite_block(
     const int64_t *d_ncl, const int64_t *cl_off, const int32_t *cl_mem, p3t_particles p,
     p3t_params prm, double dt, int nc_lo, int nc_hi, unsigned long long *steps_out,
     int64_t *cursor, HBig big, CollOut co, DevStatus *st, int64_t iter_limit, int32_t *rec) {
+  pdl_wait();
   __shared__ HCtl C;
   extern __shared__ __align__(16) unsigned char hsm[];
   static_assert(BIG || HSmall<KM>::kT >= NT, "a batch of pair terms must fit HSmall::T");
@@ -1049,9 +1053,11 @@ __global__ void __launch_bounds__(NT) k_hermite_block(
   if (tid == 0 && steps_out && steps) atomicAdd(steps_out, steps);
 }
 
-__global__ void k_zero_i64_three(int64_t *p) { p[0] = 0; p[1] = 0; p[2] = 0; }
+__global__ void k_zero_i64_three(int64_t *p) {
+  pdl_wait(); p[0] = 0; p[1] = 0; p[2] = 0; }
 
-__global__ void k_zero_u64(unsigned long long *p) { *p = 0ull; }
+__global__ void k_zero_u64(unsigned long long *p) {
+  pdl_wait(); *p = 0ull; }
 
 // ---- energy ----------------------------------------------------------------
 __device__ __forceinline__ void two_sum_f(float &hi, float &lo, float b) {
@@ -1067,6 +1073,7 @@ constexpr int kETile = 256;
 template <bool MIXED>
 __global__ void __launch_bounds__(kETile) k_energy(p3t_particles p, p3t_params prm,
                                                    double *part) {
+  pdl_wait();
   __shared__ double s_x[kETile], s_y[kETile], s_z[kETile], s_m[kETile];
   __shared__ float4 s_h[kETile], s_l[kETile];
   __shared__ double s_red[3][kETile / 32];
@@ -1144,6 +1151,7 @@ __global__ void __launch_bounds__(kETile) k_energy(p3t_particles p, p3t_params p
 // the three sums over the block partials in block order (one warp each, a
 // fixed lane-strided order and shuffle tree): the same result on every run
 __global__ void k_energy_final(const double *part, int64_t nblocks, double *out) {
+  pdl_wait();
   const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ double sum[3];
   if (q < 3) {
@@ -1168,6 +1176,7 @@ __global__ void k_energy_final(const double *part, int64_t nblocks, double *out)
 __global__ void k_merge_sets(const int4 *ent, int64_t ne, const int4 *rec, const double *rec_e,
                              int64_t nrec, const double *esoft, double *m, double *rp,
                              double *sorted_h, double *sorted_s, double *out) {
+  pdl_wait();
   for (int64_t s = threadIdx.x; s < ne; s += blockDim.x) {
     const int4 e = ent[s];
     if (e.x != e.y) continue;
@@ -1201,6 +1210,7 @@ __global__ void k_merge_sets(const int4 *ent, int64_t ne, const int4 *rec, const
 }
 
 __global__ void k_merge_keep(int64_t n, const int32_t *slot, const int4 *ent, int32_t *keep) {
+  pdl_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t s = slot[i];
@@ -1211,6 +1221,7 @@ __global__ void k_merge_keep(int64_t n, const int32_t *slot, const int4 *ent, in
 // survivors to their new places in the scratch arrays (10 arrays of n)
 __global__ void k_merge_gather(int64_t n, const int32_t *keep, const int64_t *pos,
                                p3t_particles p, double *scr, int32_t *new_index) {
+  pdl_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (!keep[i]) {
@@ -1228,6 +1239,7 @@ __global__ void k_merge_gather(int64_t n, const int32_t *keep, const int64_t *po
 
 __global__ void k_merge_reset(const int4 *ent, int64_t ne, int32_t *slot,
                               unsigned long long *ctr) {
+  pdl_wait();
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ne;
        s += (int64_t)gridDim.x * blockDim.x)
     slot[ent[s].x] = -1;
@@ -1235,6 +1247,7 @@ __global__ void k_merge_reset(const int4 *ent, int64_t ne, int32_t *slot,
 }
 
 __global__ void k_iota(int64_t n, int32_t *a) {
+  pdl_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     a[i] = (int32_t)i;
@@ -1259,7 +1272,7 @@ int p3t_run_kick(p3t_ctx *c, p3t_particles *p, const double *ax,
   if (p->n == 0) return P3T_OK;
   const int64_t g = p3t_grid(p->n, kBlock, (int64_t)c->num_sms * P3T_NSM_BLOCKS);
   const bool coll = c->prm.f_radius > 0.0;
-  k_kick<<<(unsigned)g, kBlock, 0, s>>>(p->n, p->vx, p->vy, p->vz, ax, ay, az, h,
+  pdl_launch(k_kick, dim3((unsigned)g), dim3(kBlock), 0, s, p->n, p->vx, p->vy, p->vz, ax, ay, az, h,
                                         coll ? c->coll_slot : nullptr, c->coll_ent, p->m,
                                         c->coll_esoft);
   p3t_note_launches(1);
@@ -1275,8 +1288,8 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
   const CollOut co = coll_out(c);
   unsigned long long *steps = n_steps ? reinterpret_cast<unsigned long long *>(n_steps)
                                       : c->hsteps;
-  k_zero_u64<<<1, 1, 0, s>>>(steps);
-  k_zero_i64_three<<<1, 1, 0, s>>>(c->hcursor);
+  pdl_launch(k_zero_u64, dim3(1), dim3(1), 0, s, steps);
+  pdl_launch(k_zero_i64_three, dim3(1), dim3(1), 0, s, c->hcursor);
   // Kepler drift, small clusters and large clusters touch disjoint particles:
   // run them on three streams forked from and joined back to the caller's
   P3T_CUDA_TRY(cudaEventRecord(c->ev_fork, s));
@@ -1289,23 +1302,22 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
   const int hw = c->hwarp_max;
   const unsigned gw = (unsigned)p3t_grid(ncl_max * 32, 32, (int64_t)c->num_sms * 16);
   if (hw <= 8)
-    k_hermite_block<32, 8, false><<<gw, 32, sizeof(HSmall<8>), c->aux[0]>>>(
+    pdl_launch(k_hermite_block<32, 8, false>, dim3(gw), dim3(32), sizeof(HSmall<8>), c->aux[0], 
         &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, 2, hw, steps, c->hcursor,
         big, co, c->status, c->hermite_limit, c->hermite_rec);
   else if (hw <= 16)
-    k_hermite_block<32, 16, false><<<gw, 32, sizeof(HSmall<16>), c->aux[0]>>>(
+    pdl_launch(k_hermite_block<32, 16, false>, dim3(gw), dim3(32), sizeof(HSmall<16>), c->aux[0], 
         &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, 2, hw, steps, c->hcursor,
         big, co, c->status, c->hermite_limit, c->hermite_rec);
   else
-    k_hermite_block<32, 32, false><<<gw, 32, sizeof(HSmall<32>), c->aux[0]>>>(
+    pdl_launch(k_hermite_block<32, 32, false>, dim3(gw), dim3(32), sizeof(HSmall<32>), c->aux[0], 
         &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, 2, hw, steps, c->hcursor,
         big, co, c->status, c->hermite_limit, c->hermite_rec);
-  k_hermite_block<128, kHMax, false><<<(unsigned)p3t_grid(ncl_max * 128, 128, (int64_t)c->num_sms * 2),
-                                       128, sizeof(HSmall<kHMax>), c->aux[1]>>>(
+  pdl_launch(k_hermite_block<128, kHMax, false>, dim3((unsigned)p3t_grid(ncl_max * 128, 128, (int64_t)c->num_sms * 2)), dim3(128), sizeof(HSmall<kHMax>), c->aux[1], 
       &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, hw + 1, kHMax, steps,
       c->hcursor + 1,
       big, co, c->status, c->hermite_limit, c->hermite_rec);
-  k_hermite_block<128, 1, true><<<(unsigned)p3t_grid(ncl_max, 1, nbig), 128, 0, c->aux[1]>>>(
+  pdl_launch(k_hermite_block<128, 1, true>, dim3((unsigned)p3t_grid(ncl_max, 1, nbig)), dim3(128), 0, c->aux[1], 
       &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, kHMax + 1, 0x7fffffff, steps,
       c->hcursor + 2, big, co, c->status, c->hermite_limit, c->hermite_rec);
   KepConst kc;
@@ -1314,7 +1326,7 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
   kc.isq = 1.0 / kc.sq;
   kc.imu = 1.0 / mu;
   auto kep = c->prm.precision == P3T_MIXED ? k_kepler<true> : k_kepler<false>;
-  kep<<<(unsigned)p3t_grid(n, 128, maxb), 128, 0, s>>>(&cl->counts[0], cl->singles, *p, dt, kc,
+  pdl_launch(kep, dim3((unsigned)p3t_grid(n, 128, maxb)), dim3(128), 0, s, &cl->counts[0], cl->singles, *p, dt, kc,
                                                         c->status);
   P3T_CUDA_TRY(cudaEventRecord(c->ev_join[0], c->aux[0]));
   P3T_CUDA_TRY(cudaEventRecord(c->ev_join[1], c->aux[1]));
@@ -1332,7 +1344,7 @@ int p3t_run_kepler_drift(p3t_ctx *c, p3t_particles *p, double dt, cudaStream_t s
   kc.isq = 1.0 / kc.sq;
   kc.imu = 1.0 / kc.mu;
   auto kep = c->prm.precision == P3T_MIXED ? k_kepler_all<true> : k_kepler_all<false>;
-  kep<<<(unsigned)p3t_grid(p->n, 128, (int64_t)c->num_sms * P3T_NSM_BLOCKS), 128, 0, s>>>(
+  pdl_launch(kep, dim3((unsigned)p3t_grid(p->n, 128, (int64_t)c->num_sms * P3T_NSM_BLOCKS)), dim3(128), 0, s, 
       *p, dt, kc, c->status);
   p3t_note_launches(1);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
@@ -1355,7 +1367,7 @@ int p3t_run_merge(p3t_ctx *c, p3t_particles *p, int32_t *new_index, double *e_di
     if (e_disp) e_disp[0] = e_disp[1] = 0.0;
     if (n_merged) *n_merged = 0;
     if (new_index && n > 0) {
-      k_iota<<<(unsigned)p3t_grid(n, kBlock, maxb), kBlock, 0, s>>>(n, new_index);
+      pdl_launch(k_iota, dim3((unsigned)p3t_grid(n, kBlock, maxb)), dim3(kBlock), 0, s, n, new_index);
       p3t_note_launches(1);
     }
     return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
@@ -1368,20 +1380,20 @@ int p3t_run_merge(p3t_ctx *c, p3t_particles *p, int32_t *new_index, double *e_di
   int32_t *ni = new_index ? new_index : c->flag + c->cap;
   int64_t *d_n = c->counters + 16, *d_total = c->counters + 17;
   P3T_CUDA_TRY(cudaMemcpyAsync(d_n, &n, sizeof(n), cudaMemcpyHostToDevice, s));
-  k_merge_sets<<<1, 1024, 0, s>>>(co.ent, ne, co.rec, co.rec_e, nrec, c->coll_esoft, p->m,
+  pdl_launch(k_merge_sets, dim3(1), dim3(1024), 0, s, co.ent, ne, co.rec, co.rec_e, nrec, c->coll_esoft, p->m,
                                   p->r_phys, sorted_h, sorted_s, out);
   const unsigned g = (unsigned)p3t_grid(n, kBlock, maxb);
-  k_merge_keep<<<g, kBlock, 0, s>>>(n, c->coll_slot, co.ent, keep);
+  pdl_launch(k_merge_keep, dim3(g), dim3(kBlock), 0, s, n, c->coll_slot, co.ent, keep);
   int rc = p3t_scan_i32_to_i64(keep, pos, d_n, n, d_total, c->scan_state, c->scan_words, c->status, c->poll_limit, s);
   if (rc) return rc;
-  k_merge_gather<<<g, kBlock, 0, s>>>(n, keep, pos, *p, scr, ni);
+  pdl_launch(k_merge_gather, dim3(g), dim3(kBlock), 0, s, n, keep, pos, *p, scr, ni);
   double *dst[10] = {p->x, p->y, p->z, p->vx, p->vy, p->vz, p->m, p->r_out, p->r_search,
                      p->r_phys};
   for (int q = 0; q < 10; ++q)
     if (dst[q])
       P3T_CUDA_TRY(cudaMemcpyAsync(dst[q], scr + q * n, sizeof(double) * n,
                                    cudaMemcpyDeviceToDevice, s));
-  k_merge_reset<<<(unsigned)p3t_grid(ne, kBlock, maxb), kBlock, 0, s>>>(co.ent, ne, c->coll_slot,
+  pdl_launch(k_merge_reset, dim3((unsigned)p3t_grid(ne, kBlock, maxb)), dim3(kBlock), 0, s, co.ent, ne, c->coll_slot,
                                                                         c->coll_ctr);
   p3t_note_launches(5);
   double eo[2];
@@ -1400,11 +1412,11 @@ int p3t_run_energy(p3t_ctx *c, const p3t_particles *p, double *out, cudaStream_t
   double *part = c->hw;  // 3 g <= 33 cap doubles
   if (p->n > 0) {
     if (c->prm.precision == P3T_MIXED)
-      k_energy<true><<<(unsigned)g, kETile, 0, s>>>(*p, c->prm, part);
+      pdl_launch(k_energy<true>, dim3((unsigned)g), dim3(kETile), 0, s, *p, c->prm, part);
     else
-      k_energy<false><<<(unsigned)g, kETile, 0, s>>>(*p, c->prm, part);
+      pdl_launch(k_energy<false>, dim3((unsigned)g), dim3(kETile), 0, s, *p, c->prm, part);
   }
-  k_energy_final<<<1, 96, 0, s>>>(part, g, out);
+  pdl_launch(k_energy_final, dim3(1), dim3(96), 0, s, part, g, out);
   p3t_note_launches(p->n > 0 ? 2 : 1);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }

@@ -41,6 +41,7 @@ __global__ void k_nb_filter(const int64_t *d_ncand, const int32_t *cand_i,
                             const int32_t *cand_j, const int32_t *idx,
                             const p3t_particles p, const p3t_params prm,
                             int32_t *keep, int32_t *deg, const DevStatus *st) {
+  pdl_wait();
   if (st->code != 0) return;
   const int64_t nc = *d_ncand;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nc;
@@ -53,6 +54,7 @@ __global__ void k_nb_filter(const int64_t *d_ncand, const int32_t *cand_i,
 }
 
 __global__ void k_nb_check(const int64_t *nb_total, int64_t nb_cap, DevStatus *st) {
+  pdl_wait();
   if (*nb_total > nb_cap) dev_fail(st, P3T_ERR_CAPACITY, 50, *nb_total);
 }
 
@@ -60,6 +62,7 @@ __global__ void k_nb_fill(const int64_t *d_ncand, const int32_t *cand_i,
                           const int32_t *cand_j, const int32_t *idx,
                           const int32_t *keep, const int64_t *nb_off,
                           int32_t *fill, int32_t *nb_idx, const DevStatus *st) {
+  pdl_wait();
   if (st->code != 0) return;
   const int64_t nc = *d_ncand;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nc;
@@ -74,6 +77,7 @@ __global__ void k_nb_fill(const int64_t *d_ncand, const int32_t *cand_i,
 // rows are short (<n_b> << 1 in the paper's runs): insertion sort per row
 __global__ void k_nb_sort_rows(int64_t n, const int64_t *nb_off, int32_t *nb_idx,
                                const DevStatus *st) {
+  pdl_wait();
   if (st->code != 0) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -96,6 +100,7 @@ __device__ __forceinline__ int32_t uf_find(const int32_t *parent, int32_t x) {
 }
 
 __global__ void k_uf_init(int64_t n, int32_t *parent, int32_t *csize) {
+  pdl_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     parent[i] = (int32_t)i;
@@ -105,6 +110,7 @@ __global__ void k_uf_init(int64_t n, int32_t *parent, int32_t *csize) {
 
 __global__ void k_uf_union(int64_t n, const int64_t *nb_off, const int32_t *nb_idx,
                            int32_t *parent, DevStatus *st) {
+  pdl_wait();
   if (st->code != 0) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -126,6 +132,7 @@ __global__ void k_uf_union(int64_t n, const int64_t *nb_off, const int32_t *nb_i
 
 __global__ void k_uf_label(int64_t n, const int32_t *parent, int32_t *label,
                            int32_t *csize) {
+  pdl_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t r = uf_find(parent, (int32_t)i);
@@ -138,6 +145,7 @@ __global__ void k_uf_label(int64_t n, const int32_t *parent, int32_t *label,
 // [3n, 4n) members of clusters of >= 2
 __global__ void k_cl_flags(int64_t n, const int32_t *label, const int32_t *csize,
                            int32_t *flag, int64_t *counts) {
+  pdl_wait();
   unsigned long long mx = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -155,6 +163,7 @@ __global__ void k_cl_flags(int64_t n, const int32_t *label, const int32_t *csize
 __global__ void k_cl_scatter(int64_t n, const int32_t *label, const int32_t *flag,
                              const int64_t *pos, int32_t *singles, int64_t *cl_off,
                              uint64_t *mkeys, int32_t *mvals, const int64_t *counts) {
+  pdl_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (flag[i]) singles[pos[i]] = (int32_t)i;
@@ -168,6 +177,7 @@ __global__ void k_cl_scatter(int64_t n, const int32_t *label, const int32_t *fla
 }
 
 __global__ void k_zero_i64(int64_t *p, int k) {
+  pdl_wait();
   if (threadIdx.x < k) p[threadIdx.x] = 0;
 }
 
@@ -184,20 +194,20 @@ int p3t_run_neighbours(p3t_ctx *c, const p3t_particles *p, int64_t *nb_off,
   // ---- neighbour lists ----
   P3T_CUDA_TRY(cudaMemsetAsync(c->deg, 0, sizeof(int32_t) * (n + 1), s));
   P3T_CUDA_TRY(cudaMemsetAsync(c->fill, 0, sizeof(int32_t) * (n + 1), s));
-  k_nb_filter<<<(unsigned)gc, kBlock, 0, s>>>(&cnt[9], c->cand_i, c->cand_j, c->idx, *p,
+  pdl_launch(k_nb_filter, dim3((unsigned)gc), dim3(kBlock), 0, s, &cnt[9], c->cand_i, c->cand_j, c->idx, *p,
                                               c->prm, c->cand_keep, c->deg, c->status);
   rc = p3t_scan_i32_to_i64(c->deg, nb_off, &cnt[0], c->cap, nb_off + n, c->scan_state, c->scan_words, c->status, c->poll_limit, s);
   if (rc) return rc;
-  k_nb_check<<<1, 1, 0, s>>>(nb_off + n, nb_cap, c->status);
-  k_nb_fill<<<(unsigned)gc, kBlock, 0, s>>>(&cnt[9], c->cand_i, c->cand_j, c->idx,
+  pdl_launch(k_nb_check, dim3(1), dim3(1), 0, s, nb_off + n, nb_cap, c->status);
+  pdl_launch(k_nb_fill, dim3((unsigned)gc), dim3(kBlock), 0, s, &cnt[9], c->cand_i, c->cand_j, c->idx,
                                             c->cand_keep, nb_off, c->fill, nb_idx, c->status);
-  k_nb_sort_rows<<<(unsigned)g, kBlock, 0, s>>>(n, nb_off, nb_idx, c->status);
+  pdl_launch(k_nb_sort_rows, dim3((unsigned)g), dim3(kBlock), 0, s, n, nb_off, nb_idx, c->status);
   // ---- neighbour clusters ----
-  k_zero_i64<<<1, 32, 0, s>>>(c->cl_counts, 4);
-  k_uf_init<<<(unsigned)g, kBlock, 0, s>>>(n, c->parent, c->csize);
-  k_uf_union<<<(unsigned)g, kBlock, 0, s>>>(n, nb_off, nb_idx, c->parent, c->status);
-  k_uf_label<<<(unsigned)g, kBlock, 0, s>>>(n, c->parent, c->label, c->csize);
-  k_cl_flags<<<(unsigned)g, kBlock, 0, s>>>(n, c->label, c->csize, c->flag, c->cl_counts);
+  pdl_launch(k_zero_i64, dim3(1), dim3(32), 0, s, c->cl_counts, 4);
+  pdl_launch(k_uf_init, dim3((unsigned)g), dim3(kBlock), 0, s, n, c->parent, c->csize);
+  pdl_launch(k_uf_union, dim3((unsigned)g), dim3(kBlock), 0, s, n, nb_off, nb_idx, c->parent, c->status);
+  pdl_launch(k_uf_label, dim3((unsigned)g), dim3(kBlock), 0, s, n, c->parent, c->label, c->csize);
+  pdl_launch(k_cl_flags, dim3((unsigned)g), dim3(kBlock), 0, s, n, c->label, c->csize, c->flag, c->cl_counts);
   // four scans: isolated, roots, root sizes, members
   for (int q = 0; q < 4; ++q) {
     int64_t *tot = q == 0 ? &c->cl_counts[0] : q == 1 ? &c->cl_counts[1]
@@ -206,7 +216,7 @@ int p3t_run_neighbours(p3t_ctx *c, const p3t_particles *p, int64_t *nb_off,
                              c->scan_state, c->scan_words, c->status, c->poll_limit, s);
     if (rc) return rc;
   }
-  k_cl_scatter<<<(unsigned)g, kBlock, 0, s>>>(n, c->label, c->flag, c->pos, c->singles,
+  pdl_launch(k_cl_scatter, dim3((unsigned)g), dim3(kBlock), 0, s, n, c->label, c->flag, c->pos, c->singles,
                                               c->cl_off, c->mkeys, c->mvals, c->cl_counts);
   // filter, check, fill, sort_rows, zero, uf_init, uf_union, uf_label, flags, scatter
   p3t_note_launches(10);

@@ -349,7 +349,7 @@ int p3t_scan_i32_to_i64(const int32_t *in, int64_t *out, const int64_t *d_n,
   int64_t G = (n_cap + kScanTile - 1) / kScanTile;
   if (G < 1) G = 1;
   if (G + 2 > state_words) return P3T_ERR_CAPACITY;
-  pdl_launch(scan_onepass, dim3((unsigned)G), dim3(kScanThreads), s, in, out, d_n, d_total, state, st,
+  pdl_launch(scan_onepass, dim3((unsigned)G), dim3(kScanThreads), 0, s, in, out, d_n, d_total, state, st,
                                                     poll_limit);
   p3t_note_launches(1);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
@@ -370,10 +370,10 @@ int p3t_radix_sort(uint64_t **keys, int32_t **vals, uint64_t **keys_alt,
   if (ntiles * kRadix + kRadix > hist_cap) return P3T_ERR_CAPACITY;
   uint32_t *digit_total = hist + ntiles * kRadix;
   for (int shift = begin_bit; shift < end_bit; shift += kRadixBits) {
-    pdl_launch(radix_upsweep, dim3((unsigned)ntiles), dim3(kSortThreads), s, *keys, d_n, shift,
+    pdl_launch(radix_upsweep, dim3((unsigned)ntiles), dim3(kSortThreads), 0, s, *keys, d_n, shift,
                                                             hist, (int)ntiles);
-    pdl_launch(radix_row_scan, dim3(kRadix), dim3(kRadix), s, hist, (int)ntiles, digit_total, d_n);
-    pdl_launch(radix_downsweep, dim3((unsigned)ntiles), dim3(kSortThreads), s, 
+    pdl_launch(radix_row_scan, dim3(kRadix), dim3(kRadix), 0, s, hist, (int)ntiles, digit_total, d_n);
+    pdl_launch(radix_downsweep, dim3((unsigned)ntiles), dim3(kSortThreads), 0, s, 
         *keys, *vals, *keys_alt, *vals_alt, d_n, shift, hist, (int)ntiles, digit_total);
     p3t_note_launches(3);
     uint64_t *tk = *keys; *keys = *keys_alt; *keys_alt = tk;

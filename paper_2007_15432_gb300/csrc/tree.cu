@@ -1247,10 +1247,10 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   // one root cube per segment: a few blocks per SM in all, in slices of the
   // segments
   const int bsl = nseg >= 4 * c->num_sms ? 1 : 4 * c->num_sms / nseg;
-  pdl_launch(k_box_init, dim3(1), dim3(256), s, c->box_bits, nseg);
-  pdl_launch(k_box, dim3((unsigned)(bsl * nseg)), dim3(kBlock), s, sv, bsl, p->x, p->y, p->z, c->box_bits);
-  pdl_launch(k_box_final, dim3(1), dim3(256), s, c->box_bits, c->box, nseg);
-  pdl_launch(k_keys, dim3((unsigned)g), dim3(kBlock), s, sv, p->x, p->y, p->z, p->m, p->r_out, p->r_search,
+  pdl_launch(k_box_init, dim3(1), dim3(256), 0, s, c->box_bits, nseg);
+  pdl_launch(k_box, dim3((unsigned)(bsl * nseg)), dim3(kBlock), 0, s, sv, bsl, p->x, p->y, p->z, c->box_bits);
+  pdl_launch(k_box_final, dim3(1), dim3(256), 0, s, c->box_bits, c->box, nseg);
+  pdl_launch(k_keys, dim3((unsigned)g), dim3(kBlock), 0, s, sv, p->x, p->y, p->z, p->m, p->r_out, p->r_search,
                                         c->box, c->keys, c->idx, c->pack, 0, &cnt[0]);
   rc = p3t_radix_sort(&c->keys, &c->idx, &c->keys_alt, &c->idx_alt, &cnt[0], c->cap,
                       0, 64, c->radix_hist, c->radix_hist_cap, s);
@@ -1260,70 +1260,70 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
     // then the keys of the new order
     int sbits = 0;
     while ((1 << sbits) < nseg) ++sbits;
-    pdl_launch(k_segkey, dim3((unsigned)g), dim3(kBlock), s, sv, c->idx, c->keys);
+    pdl_launch(k_segkey, dim3((unsigned)g), dim3(kBlock), 0, s, sv, c->idx, c->keys);
     rc = p3t_radix_sort(&c->keys, &c->idx, &c->keys_alt, &c->idx_alt, &cnt[0], c->cap,
                         0, sbits, c->radix_hist, c->radix_hist_cap, s);
     if (rc) return rc;
-    pdl_launch(k_keys, dim3((unsigned)g), dim3(kBlock), s, sv, p->x, p->y, p->z, p->m, p->r_out, p->r_search,
+    pdl_launch(k_keys, dim3((unsigned)g), dim3(kBlock), 0, s, sv, p->x, p->y, p->z, p->m, p->r_out, p->r_search,
                                           c->box, c->keys, c->idx, c->pack, 1, nullptr);
     p3t_note_launches(2);
   }
   auto gather = c->prm.precision == P3T_MIXED ? k_gather<true> : k_gather<false>;
-  pdl_launch(gather, dim3((unsigned)g), dim3(kBlock), s, n, c->idx, c->keys, c->pack, c->sx, c->sy, c->sz,
+  pdl_launch(gather, dim3((unsigned)g), dim3(kBlock), 0, s, n, c->idx, c->keys, c->pack, c->sx, c->sy, c->sz,
                                           c->sm, c->sro, c->srs, c->sq, c->spA, c->spB,
                                           c->srs32, c->sml);
-  pdl_launch(k_lcp_levels, dim3((unsigned)p3t_grid(n, kLevelTile, maxb)), dim3(kLevelTile), s, 
+  pdl_launch(k_lcp_levels, dim3((unsigned)p3t_grid(n, kLevelTile, maxb)), dim3(kLevelTile), 0, s, 
       sv, c->keys, leaf, c->lp, c->lv, c->ncount);
   rc = p3t_scan_i32_to_i64(c->ncount, c->nstart, &cnt[0], c->cap, &cnt[1], c->scan_state, c->scan_words, c->status, c->poll_limit, s);
   if (rc) return rc;
-  pdl_launch(k_nodes_pre, dim3((unsigned)g), dim3(kBlock), s, sv, c->lp, c->lv, c->nstart, cnt, c->node_cap,
+  pdl_launch(k_nodes_pre, dim3((unsigned)g), dim3(kBlock), 0, s, sv, c->lp, c->lv, c->nstart, cnt, c->node_cap,
                                              c->pre_first, c->pre_level, c->lvl_keys,
                                              c->bfs2pre, c->status);
-  pdl_launch(k_node_counts, dim3((unsigned)p3t_grid(c->node_cap, kBlock, maxb)), dim3(kBlock), s, 
+  pdl_launch(k_node_counts, dim3((unsigned)p3t_grid(c->node_cap, kBlock, maxb)), dim3(kBlock), 0, s, 
       sv, c->keys, &cnt[1], c->node_cap, c->pre_first, c->pre_level, c->pre_count, c->status);
   rc = p3t_radix_sort(&c->lvl_keys, &c->bfs2pre, &c->lvl_keys_alt, &c->bfs2pre_alt, &cnt[3],
                       c->node_cap, 0, 8, c->radix_hist, c->radix_hist_cap, s);
   if (rc) return rc;
   const int64_t gn = p3t_grid(c->node_cap, kBlock, maxb);
-  pdl_launch(k_pre2bfs, dim3((unsigned)gn), dim3(kBlock), s, &cnt[3], c->node_cap, c->bfs2pre, c->pre2bfs);
-  pdl_launch(k_nodes_bfs, dim3((unsigned)gn), dim3(kBlock), s, &cnt[3], c->node_cap, c->bfs2pre, c->pre2bfs,
+  pdl_launch(k_pre2bfs, dim3((unsigned)gn), dim3(kBlock), 0, s, &cnt[3], c->node_cap, c->bfs2pre, c->pre2bfs);
+  pdl_launch(k_nodes_bfs, dim3((unsigned)gn), dim3(kBlock), 0, s, &cnt[3], c->node_cap, c->bfs2pre, c->pre2bfs,
                                               c->pre_first, c->pre_count, c->pre_level,
                                               c->lp, c->lv, c->nstart, c->sq, c->node,
                                               c->leaf_flag, c->node_done, c->status);
-  pdl_launch(k_parents, dim3((unsigned)gn), dim3(kBlock), s, &cnt[3], c->node_cap, c->node);
+  pdl_launch(k_parents, dim3((unsigned)gn), dim3(kBlock), 0, s, &cnt[3], c->node_cap, c->node);
   rc = p3t_scan_i32_to_i64(c->leaf_flag, c->leaf_pos, &cnt[3], c->node_cap, &cnt[2],
                            c->scan_state, c->scan_words, c->status, c->poll_limit, s);
   if (rc) return rc;
-  pdl_launch(k_leaf_list, dim3((unsigned)gn), dim3(kBlock), s, &cnt[3], c->node_cap, c->leaf_flag,
+  pdl_launch(k_leaf_list, dim3((unsigned)gn), dim3(kBlock), 0, s, &cnt[3], c->node_cap, c->leaf_flag,
                                               c->leaf_pos, c->pre2bfs, c->leaf_list);
   if (c->prm.precision == P3T_MIXED) {
-    pdl_launch(k_moments_up32, dim3((unsigned)p3t_grid(c->node_cap, 128, maxb)), dim3(128), s, 
+    pdl_launch(k_moments_up32, dim3((unsigned)p3t_grid(c->node_cap, 128, maxb)), dim3(128), 0, s, 
         &cnt[2], c->leaf_list, c->node, c->mom32, c->nrs, c->spA, c->spB, c->sml, c->srs,
         c->sq, c->box, sv, c->node_done);
     p3t_note_launches(1);
   } else {
-    pdl_launch(k_moments_leaf, dim3((unsigned)p3t_grid(c->node_cap, 128, maxb)), dim3(128), s, 
+    pdl_launch(k_moments_leaf, dim3((unsigned)p3t_grid(c->node_cap, 128, maxb)), dim3(128), 0, s, 
         &cnt[2], c->leaf_list, c->node, c->mom64, c->mom32, c->nrs, c->sx, c->sy, c->sz, c->sm,
         c->srs, c->sq, c->box, sv);
     // internal nodes, level by level, deepest first
     int64_t *lvl_start = c->counters + 32;  // [P3T_BITS + 2]
-    pdl_launch(k_level_offsets, dim3(1), dim3(32), s, &cnt[3], c->node_cap, c->node, lvl_start);
+    pdl_launch(k_level_offsets, dim3(1), dim3(32), 0, s, &cnt[3], c->node_cap, c->node, lvl_start);
     // the deep levels (empty or nearly so in a disk) in one single-block
     // launch, then one launch a level at about one warp per sub-partition
-    pdl_launch(k_moments_level, dim3(1), dim3(128), s, P3T_BITS - 1, kDeepLevel, lvl_start, c->node, c->mom64,
+    pdl_launch(k_moments_level, dim3(1), dim3(128), 0, s, P3T_BITS - 1, kDeepLevel, lvl_start, c->node, c->mom64,
                                       c->mom32, c->nrs, c->box, sv, 4);
     const int64_t wt = (int64_t)c->num_sms * 4;
     for (int l = kDeepLevel - 1; l >= 0; --l)
-      pdl_launch(k_moments_level, dim3((unsigned)c->num_sms), dim3(128), s, l, l, lvl_start, c->node, c->mom64,
+      pdl_launch(k_moments_level, dim3((unsigned)c->num_sms), dim3(128), 0, s, l, l, lvl_start, c->node, c->mom64,
                                                            c->mom32, c->nrs, c->box, sv, wt);
     p3t_note_launches(3 + kDeepLevel);  // leaves, level offsets, deep levels, one a level
   }
-  pdl_launch(k_group_flags, dim3((unsigned)gn), dim3(kBlock), s, &cnt[3], c->node_cap, c->node, c->bfs2pre,
+  pdl_launch(k_group_flags, dim3((unsigned)gn), dim3(kBlock), 0, s, &cnt[3], c->node_cap, c->node, c->bfs2pre,
                                                 c->prm.group_size, c->group_flag);
   rc = p3t_scan_i32_to_i64(c->group_flag, c->group_pos, &cnt[3], c->node_cap, &cnt[15],
                            c->scan_state, c->scan_words, c->status, c->poll_limit, s);
   if (rc) return rc;
-  pdl_launch(k_group_list, dim3((unsigned)gn), dim3(kBlock), s, &cnt[3], c->node_cap, c->group_flag,
+  pdl_launch(k_group_list, dim3((unsigned)gn), dim3(kBlock), 0, s, &cnt[3], c->node_cap, c->group_flag,
                                                c->group_pos, c->pre2bfs, c->group_list);
   // own kernels here (the scans, sorts and moments count themselves): box 3,
   // keys, gather, lcp_levels, nodes_pre, node_counts, pre2bfs, nodes_bfs,

@@ -797,6 +797,7 @@ __device__ bool refine_group(const WalkArgs &a, const GroupBox &gb, bool redo, i
 template <bool MIXED>
 __global__ void __launch_bounds__(kWarps * 32, MIXED ? P3T_WALK_MINB_MIXED : 1)
     k_walk(const WalkArgs a) {
+  pdl_wait();
   __shared__ int32_t s_pp[kWarps][kPPCap];
   __shared__ int32_t s_nd[kWarps][kNDCap];
   __shared__ int32_t s_big[kWarps][kBigCap];
@@ -1004,6 +1005,7 @@ struct VjpEval {
 };
 
 __global__ void __launch_bounds__(kWarps * 32) k_walk_vjp(const WalkArgs a, const VjpOut o) {
+  pdl_wait();
   __shared__ int32_t s_pp[kWarps][kPPCap];
   __shared__ int32_t s_nd[kWarps][kNDCap];
   __shared__ int32_t s_big[kWarps][kBigCap];
@@ -1051,6 +1053,7 @@ __global__ void k_node_adjoint(const int64_t *d_nleaf, const int32_t *leaf_list,
                                const double *sx, const double *sy, const double *sz,
                                const double *sm, const int32_t *idx, double *gx, double *gy,
                                double *gz, double *gm) {
+  pdl_wait();
   const int64_t nleaf = *d_nleaf;
   for (int64_t b = blockIdx.x; b < nleaf; b += gridDim.x) {
     const TreeNode &L = node[leaf_list[b]];
@@ -1080,6 +1083,7 @@ __global__ void k_node_adjoint(const int64_t *d_nleaf, const int32_t *leaf_list,
 
 __global__ void k_walk_prep(int64_t *cursor, unsigned long long *cand_count,
                             unsigned long long *counts) {
+  pdl_wait();
   *cursor = 0;
   *cand_count = 0ull;
   if (counts) { counts[0] = 0ull; counts[1] = 0ull; }
@@ -1087,6 +1091,7 @@ __global__ void k_walk_prep(int64_t *cursor, unsigned long long *cand_count,
 
 // candidates found -> device status (for growth on the host) and clamped count
 __global__ void k_walk_post(int64_t *cnt, int64_t cand_cap, DevStatus *st) {
+  pdl_wait();
   const int64_t nc = cnt[8];
   st->cand_need = nc;
   if (nc > cand_cap) dev_fail(st, P3T_ERR_CAPACITY, 42, nc);
@@ -1173,8 +1178,8 @@ int p3t_run_soft_force_vjp_tree(p3t_ctx *c, const p3t_particles *p, double s,
   P3T_CUDA_TRY(cudaMemsetAsync(c->nadj, 0, sizeof(double) * 10 * c->node_cap, st));
   P3T_CUDA_TRY(cudaMemsetAsync(a.cursor, 0, sizeof(int64_t), st));
   const unsigned blocks = (unsigned)(c->walk_warps / kWarps);
-  k_walk_vjp<<<blocks, kWarps * 32, 0, st>>>(a, o);
-  k_node_adjoint<<<(unsigned)(c->num_sms * 8), 128, 0, st>>>(
+  pdl_launch(k_walk_vjp, dim3(blocks), dim3(kWarps * 32), 0, st, a, o);
+  pdl_launch(k_node_adjoint, dim3((unsigned)(c->num_sms * 8)), dim3(128), 0, st, 
       &c->counters[2], c->leaf_list, c->node, c->mom64, c->nadj, c->sx, c->sy, c->sz, c->sm,
       c->idx, gx, gy, gz, gm);
   p3t_note_launches(3);
@@ -1205,7 +1210,7 @@ int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
   a.mgi_f = (float)(-c->prm.gamma / (1.0 - c->prm.gamma));
   // Barnes-Hut thresholds per level, ceil((2^(22-l))^2 / theta^2) (half units)
   for (int l = 0; l <= P3T_BITS; ++l) a.bh[l] = bh_threshold(c->prm.theta, l);
-  k_walk_prep<<<1, 1, 0, s>>>(a.cursor, a.cand_count, a.counts);
+  pdl_launch(k_walk_prep, dim3(1), dim3(1), 0, s, a.cursor, a.cand_count, a.counts);
   unsigned blocks = (unsigned)(c->walk_warps / kWarps);
   if (c->walk_bps > 0 && (int64_t)c->num_sms * c->walk_bps < (int64_t)blocks)
     blocks = (unsigned)(c->num_sms * c->walk_bps);
@@ -1213,11 +1218,11 @@ int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
     // one target per lane (or several lanes per target): two targets per
     // lane (a 64-target group walked once) was measured slower than two
     // walks of 32 (register pressure, longer chains)
-    k_walk<true><<<blocks, kWarps * 32, 0, s>>>(a);
+    pdl_launch(k_walk<true>, dim3(blocks), dim3(kWarps * 32), 0, s, a);
   } else {
-    k_walk<false><<<blocks, kWarps * 32, 0, s>>>(a);
+    pdl_launch(k_walk<false>, dim3(blocks), dim3(kWarps * 32), 0, s, a);
   }
-  k_walk_post<<<1, 1, 0, s>>>(c->counters, c->cand_cap, c->status);
+  pdl_launch(k_walk_post, dim3(1), dim3(1), 0, s, c->counters, c->cand_cap, c->status);
   p3t_note_launches(3);
   (void)p;
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
