@@ -151,6 +151,7 @@ __global__ void k_kepler_vjp(int64_t n, const double *x, const double *y, const 
                              const double *vx, const double *vy, const double *vz, double dt,
                              double mu, double *lx, double *ly, double *lz, double *lvx,
                              double *lvy, double *lvz) {
+  pdl_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     D6 X[3] = {dc(x[i]), dc(y[i]), dc(z[i])}, V[3] = {dc(vx[i]), dc(vy[i]), dc(vz[i])};
@@ -206,7 +207,7 @@ int p3t_run_kepler_vjp(p3t_ctx *c, const p3t_particles *p, double dt, double *lx
                        double *lz, double *lvx, double *lvy, double *lvz, cudaStream_t s) {
   const int64_t n = p->n;
   if (n == 0) return P3T_OK;
-  k_kepler_vjp<<<(unsigned)p3t_grid(n, 128, (int64_t)c->num_sms * P3T_NSM_BLOCKS), 128, 0, s>>>(
+  pdl_launch(k_kepler_vjp, dim3((unsigned)p3t_grid(n, 128, (int64_t)c->num_sms * P3T_NSM_BLOCKS)), dim3(128), 0, s, 
       n, p->x, p->y, p->z, p->vx, p->vy, p->vz, dt, c->prm.G * c->prm.m_star, lx, ly, lz, lvx,
       lvy, lvz);
   p3t_note_launches(1);

@@ -166,6 +166,7 @@ __global__ void k_direct_pack(int64_t n, const double *x, const double *y, const
                               const double *ly, const double *lz,
                               Q4<typename DT<MIXED>::T> *A, Q4<typename DT<MIXED>::T> *B,
                               Q4<typename DT<MIXED>::T> *L) {
+  pdl_wait();
   using T = typename DT<MIXED>::T;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
@@ -194,6 +195,7 @@ __global__ void __launch_bounds__(kDW * 32, MIXED ? P3T_DIRECT_MINB_MIXED : 1)
              const Q4<typename DT<MIXED>::T> *__restrict__ PB,
              const Q4<typename DT<MIXED>::T> *__restrict__ PL, double gamma, double *part,
              int32_t *tile_cnt, DOut out) {
+  pdl_wait();
   using T = typename DT<MIXED>::T;
   constexpr int NC = VJP ? 4 : 3;
   __shared__ Q4<T> sA[kDW][32];                     // x_hi, y_hi, z_hi, m
@@ -422,11 +424,11 @@ int launch_direct(p3t_ctx *c, const p3t_particles *p, const double *lx, const do
   using T = typename DT<MIXED>::T;
   Q4<T> *A = reinterpret_cast<Q4<T> *>(c->hw);  // 3 n packed 4-vectors <= 96 n bytes
   Q4<T> *B = A + n, *L = B + n;
-  k_direct_pack<MIXED, VJP><<<(unsigned)p3t_grid(n, 256, (int64_t)c->num_sms * 4), 256, 0, s>>>(
+  pdl_launch(k_direct_pack<MIXED, VJP>, dim3((unsigned)p3t_grid(n, 256, (int64_t)c->num_sms * 4)), dim3(256), 0, s, 
       n, p->x, p->y, p->z, p->m, p->r_out, lx, ly, lz, A, B, L);
   if (sp.nsplit > 1 && sp.tiles > c->dcnt_cap) return P3T_ERR_CAPACITY;
   const dim3 grid((unsigned)sp.tiles, (unsigned)sp.nsplit);
-  k_direct<MIXED, VJP><<<grid, kDW * 32, 0, s>>>(n, sp.chunk, A, B, L, c->prm.gamma, c->dpart,
+  pdl_launch(k_direct<MIXED, VJP>, dim3(grid), dim3(kDW * 32), 0, s, n, sp.chunk, A, B, L, c->prm.gamma, c->dpart,
                                                 c->dcnt, out);
   p3t_note_launches(2);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;

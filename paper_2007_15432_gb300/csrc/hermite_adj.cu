@@ -111,6 +111,7 @@ __global__ void k_hermite_tangent(const int64_t *counts, const int64_t *cl_off,
                                   double dt, const double *lx, const double *ly, const double *lz,
                                   const double *lvx, const double *lvy, const double *lvz,
                                   double *lin, double *gm, DevStatus *st) {
+  pdl_wait();
   const int64_t ncl = counts[1], nmem = counts[2];
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 7 * nmem;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -214,6 +215,7 @@ __global__ void k_hermite_tangent(const int64_t *counts, const int64_t *cl_off,
 __global__ void k_member_adjoint(const int64_t *counts, const int32_t *cl_mem, const double *lin,
                                  double *lx, double *ly, double *lz, double *lvx, double *lvy,
                                  double *lvz) {
+  pdl_wait();
   const int64_t nmem = counts[2];
   for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nmem;
        u += (int64_t)gridDim.x * blockDim.x) {
@@ -234,12 +236,12 @@ int p3t_run_hard_step_vjp(p3t_ctx *c, const p3t_particles *p, const p3t_clusters
   const int64_t n = p->n;
   if (n == 0) return P3T_OK;
   const int64_t maxb = (int64_t)c->num_sms * P3T_NSM_BLOCKS;
-  k_hermite_tangent<<<(unsigned)p3t_grid(7 * n, 128, maxb), 128, 0, s>>>(
+  pdl_launch(k_hermite_tangent, dim3((unsigned)p3t_grid(7 * n, 128, maxb)), dim3(128), 0, s, 
       cl->counts, cl->cl_off, cl->cl_mem, *p, c->prm, dt, lx, ly, lz, lvx, lvy, lvz, c->hadj, gm,
       c->status);
   int rc = p3t_run_kepler_vjp(c, p, dt, lx, ly, lz, lvx, lvy, lvz, s);
   if (rc) return rc;
-  k_member_adjoint<<<(unsigned)p3t_grid(n, 128, maxb), 128, 0, s>>>(cl->counts, cl->cl_mem,
+  pdl_launch(k_member_adjoint, dim3((unsigned)p3t_grid(n, 128, maxb)), dim3(128), 0, s, cl->counts, cl->cl_mem,
                                                                      c->hadj, lx, ly, lz, lvx,
                                                                      lvy, lvz);
   p3t_note_launches(2);

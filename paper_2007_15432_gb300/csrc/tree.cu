@@ -1201,11 +1201,11 @@ int p3t_run_cutoffs(p3t_ctx *c, p3t_particles *p, cudaStream_t s) {
   double *bsum = c->epart;  // reuse: >= 4096 doubles
   unsigned long long *bcnt = reinterpret_cast<unsigned long long *>(c->epart + 4096);
   const int64_t g = p3t_grid(n, kBlock, (int64_t)c->num_sms * P3T_NSM_BLOCKS);
-  k_cut_init<<<4, kBlock, 0, s>>>(c->box_bits, (int)c->nseg, bsum, bcnt, nb);
+  pdl_launch(k_cut_init, dim3(4), dim3(kBlock), 0, s, c->box_bits, (int)c->nseg, bsum, bcnt, nb);
   const int rsl = c->nseg == 1 ? (int)g : (int)((g + c->nseg - 1) / c->nseg);
-  k_cut_range<<<(unsigned)(rsl * c->nseg), kBlock, 0, s>>>(sv, rsl, p->x, p->y, c->box_bits);
+  pdl_launch(k_cut_range, dim3((unsigned)(rsl * c->nseg)), dim3(kBlock), 0, s, sv, rsl, p->x, p->y, c->box_bits);
   if (c->nseg > 1)
-    k_cut_segbins<<<1, 1024, 0, s>>>(sv, c->prm.vran_bins, c->box_bits, c->seg_nb,
+    pdl_launch(k_cut_segbins, dim3(1), dim3(1024), 0, s, sv, c->prm.vran_bins, c->box_bits, c->seg_nb,
                                      c->seg_base, c->seg_l);
   const double mu = c->prm.G * c->prm.m_star;
   // per-bin sums in a fixed order (particles grouped by bin with the stable
@@ -1213,22 +1213,21 @@ int p3t_run_cutoffs(p3t_ctx *c, p3t_particles *p, cudaStream_t s) {
   double *u2 = c->hw;
   int64_t *boff = c->pos;
   int64_t *d_n = &c->counters[18];
-  k_set_i64<<<1, 1, 0, s>>>(d_n, n);
+  pdl_launch(k_set_i64, dim3(1), dim3(1), 0, s, d_n, n);
   int32_t *bin = c->flag;  // the bins of k_cut_u2, read by k_cut_final (N int32)
-  k_cut_u2<<<(unsigned)g, kBlock, 0, s>>>(sv, p->x, p->y, p->z, p->vx, p->vy, p->vz, mu,
+  pdl_launch(k_cut_u2, dim3((unsigned)g), dim3(kBlock), 0, s, sv, p->x, p->y, p->z, p->vx, p->vy, p->vz, mu,
                                           c->box_bits, nb, c->seg_nb, c->seg_base, c->seg_l,
                                           u2, c->keys, c->idx, bin, bcnt);
   int rc = p3t_radix_sort(&c->keys, &c->idx, &c->keys_alt, &c->idx_alt, d_n, c->cap, 0, 16,
                           c->radix_hist, c->radix_hist_cap, s);
   if (rc) return rc;
-  k_cut_offsets<<<1, 1024, 0, s>>>(nb, bcnt, boff);
-  k_cut_binsum<<<(unsigned)p3t_grid((int64_t)nb * 32, kBlock, (int64_t)c->num_sms * 4), kBlock, 0,
-                 s>>>(nb, boff, c->idx, u2, bsum);
-  k_cut_final<<<(unsigned)g, kBlock, 0, s>>>(sv, p->x, p->y, p->z, p->vx, p->vy,
+  pdl_launch(k_cut_offsets, dim3(1), dim3(1024), 0, s, nb, bcnt, boff);
+  pdl_launch(k_cut_binsum, dim3((unsigned)p3t_grid((int64_t)nb * 32, kBlock, (int64_t)c->num_sms * 4)), dim3(kBlock), 0, s, nb, boff, c->idx, u2, bsum);
+  pdl_launch(k_cut_final, dim3((unsigned)g), dim3(kBlock), 0, s, sv, p->x, p->y, p->z, p->vx, p->vy,
                                              p->vz, p->m, c->prm, c->box_bits, bin, bsum,
                                              p->r_out, p->r_search);
   if (c->prm.cutoff_mode == P3T_CUT_SHARED)
-    k_cut_shared<<<(unsigned)g, kBlock, 0, s>>>(sv, c->box_bits, p->r_out, p->r_search);
+    pdl_launch(k_cut_shared, dim3((unsigned)g), dim3(kBlock), 0, s, sv, c->box_bits, p->r_out, p->r_search);
   // init, range, n, u2, offsets, bin sums, final (+ shared, + segment bins);
   // the sort counts itself
   p3t_note_launches(7 + (c->prm.cutoff_mode == P3T_CUT_SHARED) + (c->nseg > 1));
@@ -1337,7 +1336,7 @@ int p3t_run_tree_stats(p3t_ctx *c, cudaStream_t s) {
   int64_t *cnt = c->counters;
   P3T_CUDA_TRY(cudaMemsetAsync(&cnt[4], 0, 4 * sizeof(int64_t), s));
   const int64_t gn = p3t_grid(c->node_cap, kBlock, (int64_t)c->num_sms * P3T_NSM_BLOCKS);
-  k_tree_stats<<<(unsigned)gn, kBlock, 0, s>>>(&cnt[3], c->node_cap, c->node, &cnt[4]);
+  pdl_launch(k_tree_stats, dim3((unsigned)gn), dim3(kBlock), 0, s, &cnt[3], c->node_cap, c->node, &cnt[4]);
   p3t_note_launches(1);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
