@@ -50,7 +50,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one k_walk launch on the N = 10^6 wide disk,
 # group size 64, from a single-pass ncu capture of this kernel
 # (dram__bytes_read.sum 80.07 MB + dram__bytes_write.sum 17.48 MB)
-WALK_TRAFFIC_1E6 = 97.55e6
+WALK_TRAFFIC_1E6 = 95.62e6
 
 
 def parse():
