@@ -2,7 +2,8 @@
 //
 // One warp per target group (the highest tree node holding <= group_size
 // particles, or a leaf), 32 targets per walk (larger groups are taken 32
-// targets at a time).  A walk of k < 32 targets gives each target r =
+// targets at a time; the warps take a group's first 32 targets and its rest
+// as separate units of work, each walking with the whole group's box).  A walk of k < 32 targets gives each target r =
 // floor(32 / k) lanes, each of which takes every r-th entry of a batch; the
 // r partial sums are added at the end, so that lanes are not left idle.  The
 // walk pops up to 32 nodes at a time from a per-warp stack, decides opening
@@ -814,18 +815,25 @@ __global__ void __launch_bounds__(kWarps * 32, MIXED ? P3T_WALK_MINB_MIXED : 1)
   unsigned npp = 0, npn = 0;
 
   for (;;) {
-    int64_t g = 0;
-    if (lane == 0) g = atomicAdd(reinterpret_cast<unsigned long long *>(a.cursor), 1ull);
-    g = __shfl_sync(0xffffffffu, g, 0);
+    // work unit u: target group u / 2, its first 32 targets (u even) or the
+    // rest (u odd; empty for a group of at most 32): half-group units keep
+    // the warps' finishing times within one such unit of each other
+    int64_t u = 0;
+    if (lane == 0) u = atomicAdd(reinterpret_cast<unsigned long long *>(a.cursor), 1ull);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    const int64_t g = u >> 1;
     if (g >= nleaf) break;
     if (*(volatile int32_t *)&a.st->code != 0) break;
     const TreeNode &G = a.node[a.leaf_list[g]];
+    const int32_t gfirst = G.first, gcount = G.count;
+    const int32_t t0 = (u & 1) ? gfirst + 32 : gfirst;
+    const int32_t t1 = (u & 1) ? gfirst + gcount : min(gfirst + gcount, gfirst + 32);
+    if (t0 >= t1) continue;
     GroupBox gb;
     gb.load(G);
-    const int32_t gfirst = G.first, gcount = G.count;
     bool ok = true;
-    for (int32_t tb = gfirst; tb < gfirst + gcount && ok; tb += 32) {
-      const int k = min(32, gfirst + gcount - tb);
+    for (int32_t tb = t0; tb < t1 && ok; tb += 32) {
+      const int k = min(32, t1 - tb);
       const int nrep = 32 / k, rep = lane / k;
       Target<MIXED> t;
       t.load(a, tb + (lane - rep * k), rep < nrep, rep < nrep ? rep : 0, nrep);
