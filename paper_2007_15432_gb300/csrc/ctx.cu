@@ -83,7 +83,7 @@ void free_particle_buffers(p3t_ctx *c) {
   dfree(c->group_list); dfree(c->group_flag); dfree(c->group_pos);
   dfree(c->walk_stack); dfree(c->cand_i); dfree(c->cand_j); dfree(c->cand_keep);
   dfree(c->deg); dfree(c->fill); dfree(c->parent); dfree(c->label); dfree(c->csize);
-  dfree(c->flag); dfree(c->pos); dfree(c->singles); dfree(c->cl_off);
+  dfree(c->flag); dfree(c->pos); dfree(c->singles); dfree(c->cl_off); dfree(c->hlist);
   // cl_mem aliases one of the mvals buffers
   c->cl_mem = nullptr;
   dfree(c->mkeys); dfree(c->mkeys_alt); dfree(c->mvals); dfree(c->mvals_alt);
@@ -141,6 +141,8 @@ int reserve(p3t_ctx *c, int64_t n, int64_t cand_cap) {
   ok &= dalloc(c->parent, N) && dalloc(c->label, N) && dalloc(c->csize, N);
   ok &= dalloc(c->flag, 4 * N) && dalloc(c->pos, 4 * N);
   ok &= dalloc(c->singles, N) && dalloc(c->cl_off, N + 1);
+  c->hlist_cap = N / 2 + 1;  // clusters have at least two members
+  ok &= dalloc(c->hlist, 2 * c->hlist_cap);
   ok &= dalloc(c->mkeys, N) && dalloc(c->mkeys_alt, N) && dalloc(c->mvals, N) && dalloc(c->mvals_alt, N);
   ok &= dalloc(c->hw, 33 * N) && dalloc(c->ht, N) && dalloc(c->hl, 6 * N);
   ok &= dalloc(c->coll_ent, N) && dalloc(c->coll_rec, N / 2 + 1) && dalloc(c->coll_rec_e, N / 2 + 1);
@@ -193,7 +195,7 @@ int p3t_create(p3t_ctx **ctx, const p3t_params *p, int device) {
     return P3T_ERR_CUDA;
   }
   bool ok = dalloc(c->status, 1) && dalloc(c->box, 5) && dalloc(c->box_bits, 6) &&
-            dalloc(c->counters, 64) && dalloc(c->cl_counts, 4) && dalloc(c->hsteps, 1) && dalloc(c->hcursor, 3) &&
+            dalloc(c->counters, 64) && dalloc(c->cl_counts, 4) && dalloc(c->hsteps, 1) && dalloc(c->hcursor, 5) &&
             dalloc(c->coll_ctr, 1) &&
             dalloc(c->epart, 8192) && dalloc(c->bh_table, 32);
   for (int q = 0; q < 2 && ok; ++q)

@@ -1012,22 +1012,23 @@ template <int NT, int KM, bool BIG>
 __global__ void __launch_bounds__(NT) k_hermite_block(
     const int64_t *d_ncl, const int64_t *cl_off, const int32_t *cl_mem, p3t_particles p,
     p3t_params prm, double dt, int nc_lo, int nc_hi, unsigned long long *steps_out,
-    int64_t *cursor, HBig big, CollOut co, DevStatus *st, int64_t iter_limit, int32_t *rec) {
+    int64_t *cursor, const int32_t *list, const int64_t *d_nlist, HBig big, CollOut co,
+    DevStatus *st, int64_t iter_limit, int32_t *rec) {
   pdl_wait();
   __shared__ HCtl C;
   extern __shared__ __align__(16) unsigned char hsm[];
   static_assert(BIG || HSmall<KM>::kT >= NT, "a batch of pair terms must fit HSmall::T");
   HSmall<KM> *Sm = reinterpret_cast<HSmall<KM> *>(hsm);
   const int tid = threadIdx.x;
-  const int64_t ncl = *d_ncl;
+  // every cluster, or (list) the clusters of this kernel's sizes
+  const int64_t ncl = list ? *d_nlist : *d_ncl;
   const bool coll = prm.f_radius > 0.0 && p.r_phys != nullptr;
   unsigned long long steps = 0;
   bool underflow = false;
   for (int64_t k = blockIdx.x;; k += gridDim.x) {
     // clusters of up to 128 members are handed out by a cursor (a long
     // encounter keeps its block while the others move on); the rare larger
-    // ones are dealt statically, so that this kernel's few blocks do not take
-    // a cursor step for every small cluster
+    // ones are dealt statically
     int64_t c = k;
     if constexpr (!BIG) {
       if (tid == 0) C.cluster = atomicAdd(reinterpret_cast<unsigned long long *>(cursor), 1ull);
@@ -1036,6 +1037,7 @@ __global__ void __launch_bounds__(NT) k_hermite_block(
       __syncthreads();
     }
     if (c >= ncl) break;
+    if (list) c = list[c];
     const int64_t off = cl_off[c];
     const int nc = (int)(cl_off[c + 1] - off);
     if (nc < nc_lo || nc > nc_hi) continue;
@@ -1053,8 +1055,26 @@ __global__ void __launch_bounds__(NT) k_hermite_block(
   if (tid == 0 && steps_out && steps) atomicAdd(steps_out, steps);
 }
 
-__global__ void k_zero_i64_three(int64_t *p) {
-  pdl_wait(); p[0] = 0; p[1] = 0; p[2] = 0; }
+__global__ void k_zero_i64_five(int64_t *p) {
+  pdl_wait(); p[0] = 0; p[1] = 0; p[2] = 0; p[3] = 0; p[4] = 0; }
+
+// the clusters of more than hw members: up to kHMax into list[0..), larger
+// ones into list[cap..); their numbers into n[0], n[1] (zeroed before).  The
+// order within a list is arrival order: each cluster is integrated on its own,
+// so the results do not depend on it.
+__global__ void k_cluster_classes(const int64_t *d_ncl, const int64_t *cl_off, int hw,
+                                  int64_t cap, int32_t *list, int64_t *n) {
+  pdl_wait();
+  const int64_t ncl = *d_ncl;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncl;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t nc = cl_off[c + 1] - cl_off[c];
+    if (nc <= hw) continue;
+    const int big = nc > kHMax ? 1 : 0;
+    const int64_t slot = (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(&n[big]), 1ull);
+    if (slot < cap) list[big * cap + slot] = (int32_t)c;
+  }
+}
 
 __global__ void k_zero_u64(unsigned long long *p) {
   pdl_wait(); *p = 0ull; }
@@ -1289,7 +1309,12 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
   unsigned long long *steps = n_steps ? reinterpret_cast<unsigned long long *>(n_steps)
                                       : c->hsteps;
   pdl_launch(k_zero_u64, dim3(1), dim3(1), 0, s, steps);
-  pdl_launch(k_zero_i64_three, dim3(1), dim3(1), 0, s, c->hcursor);
+  pdl_launch(k_zero_i64_five, dim3(1), dim3(1), 0, s, c->hcursor);
+  // the clusters of the four-warp and workspace kernels, listed once so that
+  // those kernels do not step through every small cluster
+  const int hw = c->hwarp_max;
+  pdl_launch(k_cluster_classes, dim3((unsigned)p3t_grid(n / 2 + 1, kBlock, maxb)), dim3(kBlock), 0,
+             s, &cl->counts[1], cl->cl_off, hw, c->hlist_cap, c->hlist, c->hcursor + 3);
   // Kepler drift, small clusters and large clusters touch disjoint particles:
   // run them on three streams forked from and joined back to the caller's
   P3T_CUDA_TRY(cudaEventRecord(c->ev_fork, s));
@@ -1299,27 +1324,30 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
   const int64_t nbig = c->num_sms < 32 ? c->num_sms : 32;
   // clusters of 2..hw members: a warp each (stream aux[0]); up to 128: a
   // 128-thread block each, then > 128 (stream aux[1])
-  const int hw = c->hwarp_max;
   const unsigned gw = (unsigned)p3t_grid(ncl_max * 32, 32, (int64_t)c->num_sms * 16);
   if (hw <= 8)
     pdl_launch(k_hermite_block<32, 8, false>, dim3(gw), dim3(32), sizeof(HSmall<8>), c->aux[0], 
         &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, 2, hw, steps, c->hcursor,
-        big, co, c->status, c->hermite_limit, c->hermite_rec);
+        (const int32_t *)nullptr, (const int64_t *)nullptr, big, co, c->status, c->hermite_limit,
+        c->hermite_rec);
   else if (hw <= 16)
     pdl_launch(k_hermite_block<32, 16, false>, dim3(gw), dim3(32), sizeof(HSmall<16>), c->aux[0], 
         &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, 2, hw, steps, c->hcursor,
-        big, co, c->status, c->hermite_limit, c->hermite_rec);
+        (const int32_t *)nullptr, (const int64_t *)nullptr, big, co, c->status, c->hermite_limit,
+        c->hermite_rec);
   else
     pdl_launch(k_hermite_block<32, 32, false>, dim3(gw), dim3(32), sizeof(HSmall<32>), c->aux[0], 
         &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, 2, hw, steps, c->hcursor,
-        big, co, c->status, c->hermite_limit, c->hermite_rec);
+        (const int32_t *)nullptr, (const int64_t *)nullptr, big, co, c->status, c->hermite_limit,
+        c->hermite_rec);
   pdl_launch(k_hermite_block<128, kHMax, false>, dim3((unsigned)p3t_grid(ncl_max * 128, 128, (int64_t)c->num_sms * 2)), dim3(128), sizeof(HSmall<kHMax>), c->aux[1], 
       &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, hw + 1, kHMax, steps,
-      c->hcursor + 1,
+      c->hcursor + 1, (const int32_t *)c->hlist, (const int64_t *)(c->hcursor + 3),
       big, co, c->status, c->hermite_limit, c->hermite_rec);
   pdl_launch(k_hermite_block<128, 1, true>, dim3((unsigned)p3t_grid(ncl_max, 1, nbig)), dim3(128), 0, c->aux[1], 
       &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, kHMax + 1, 0x7fffffff, steps,
-      c->hcursor + 2, big, co, c->status, c->hermite_limit, c->hermite_rec);
+      c->hcursor + 2, (const int32_t *)(c->hlist + c->hlist_cap),
+      (const int64_t *)(c->hcursor + 4), big, co, c->status, c->hermite_limit, c->hermite_rec);
   KepConst kc;
   kc.mu = mu;
   kc.sq = sqrt(mu);
@@ -1332,7 +1360,7 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
   P3T_CUDA_TRY(cudaEventRecord(c->ev_join[1], c->aux[1]));
   P3T_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[0], 0));
   P3T_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join[1], 0));
-  p3t_note_launches(6);
+  p3t_note_launches(7);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 

@@ -266,7 +266,11 @@ struct p3t_ctx {
   int64_t *ht = nullptr;                   // time in units of dt / 2^40
   int32_t *hl = nullptr;                   // 6 * cap: level, list, sets, partner, flags
   unsigned long long *hsteps = nullptr;    // device counter
-  int64_t *hcursor = nullptr;              // [3] cluster cursors of the three Hermite kernels
+  int64_t *hcursor = nullptr;              // [5] cluster cursors of the three Hermite kernels,
+                                           // then the lengths of the two lists below
+  int32_t *hlist = nullptr;                // clusters of the four-warp kernel, then (from
+                                           // hlist_cap on) those of the workspace kernel
+  int64_t hlist_cap = 0;
 
   // composites of colliding particles, from the hard step to the merge
   unsigned long long *coll_ctr = nullptr;  // (records << 32) | entries
