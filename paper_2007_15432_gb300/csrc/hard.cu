@@ -1322,9 +1322,11 @@ int p3t_run_hard_step(p3t_ctx *c, p3t_particles *p, const p3t_clusters *cl,
   P3T_CUDA_TRY(cudaStreamWaitEvent(c->aux[1], c->ev_fork, 0));
   const int64_t ncl_max = (n / 2) > 0 ? n / 2 : 1;
   const int64_t nbig = c->num_sms < 32 ? c->num_sms : 32;
-  // clusters of 2..hw members: a warp each (stream aux[0]); up to 128: a
+  // clusters of 2..hw members: a warp each (stream aux[0]), up to 32 such
+  // one-warp blocks an SM (the FP64 latency of their block steps, not the
+  // FP64 pipe, limits them: 16 an SM took 40 us more a step); up to 128: a
   // 128-thread block each, then > 128 (stream aux[1])
-  const unsigned gw = (unsigned)p3t_grid(ncl_max * 32, 32, (int64_t)c->num_sms * 16);
+  const unsigned gw = (unsigned)p3t_grid(ncl_max * 32, 32, (int64_t)c->num_sms * 32);
   if (hw <= 8)
     pdl_launch(k_hermite_block<32, 8, false>, dim3(gw), dim3(32), sizeof(HSmall<8>), c->aux[0], 
         &cl->counts[1], cl->cl_off, cl->cl_mem, *p, c->prm, dt, 2, hw, steps, c->hcursor,
