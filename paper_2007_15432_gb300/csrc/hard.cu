@@ -203,11 +203,17 @@ __device__ __forceinline__ int ilogb_fast(double x) {
 // of a close encounter these sit on the critical path, so where the result is
 // a normal number they are done on the bits instead, with the same results.
 // (float)(a 2^k), rounded to nearest even, for a 2^k in FP32's normal range
+// (the FP64 forms of the rare cases out of line: inlined, the compiler
+// predicates them into every call, and predicated-off FP64 instructions still
+// take the FP64 pipe)
+__device__ __noinline__ float d2f_scaled_fp64(double a, int k) { return (float)ldexp_fast(a, k); }
+__device__ __noinline__ double f2d_fp64(float f) { return (double)f; }
+__device__ __noinline__ double i2d_fp64(int64_t x) { return (double)x; }
 __device__ __forceinline__ float d2f_scaled(double a, int k) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(a);
   const int ed = (int)((b >> 52) & 0x7ff);
   const int ef = ed - 1023 + k + 127;
-  if (ed == 0 || ed == 0x7ff || ef <= 0 || ef >= 255) return (float)ldexp_fast(a, k);
+  if (ed == 0 || ed == 0x7ff || ef <= 0 || ef >= 255) return d2f_scaled_fp64(a, k);
   const unsigned long long m = b & 0xfffffffffffffull;
   unsigned r = ((unsigned)ef << 23) | (unsigned)(m >> 29);
   const unsigned long long rem = m & 0x1fffffffull, half = 0x10000000ull;
@@ -218,14 +224,14 @@ __device__ __forceinline__ float d2f_scaled(double a, int k) {
 __device__ __forceinline__ double f2d_exact(float f) {
   const unsigned u = __float_as_uint(f);
   const int ef = (int)((u >> 23) & 0xff);
-  if (ef == 0 || ef == 0xff) return (double)f;
+  if (ef == 0 || ef == 0xff) return f2d_fp64(f);
   return __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32 |
                                           (unsigned long long)(ef - 127 + 1023) << 52 |
                                           (unsigned long long)(u & 0x7fffffu) << 29));
 }
 // (double)x for 0 <= x < 2^53, exact
 __device__ __forceinline__ double i2d_exact(int64_t x) {
-  if (x <= 0) return (double)x;
+  if (x <= 0) return i2d_fp64(x);
   const int e = 63 - __clzll(x);
   return __longlong_as_double((long long)((unsigned long long)(e + 1023) << 52 |
                                           (((unsigned long long)x << (52 - e)) &
