@@ -79,8 +79,8 @@ void free_particle_buffers(p3t_ctx *c) {
   dfree(c->pre_first); dfree(c->pre_count); dfree(c->pre_level);
   dfree(c->lvl_keys); dfree(c->lvl_keys_alt); dfree(c->bfs2pre); dfree(c->bfs2pre_alt);
   dfree(c->pre2bfs); dfree(c->node); dfree(c->mom64); dfree(c->mom32); dfree(c->nrs);
-  dfree(c->node_done); dfree(c->leaf_list); dfree(c->leaf_flag); dfree(c->leaf_pos);
-  dfree(c->group_list); dfree(c->group_flag); dfree(c->group_pos);
+  dfree(c->node_done); dfree(c->leaf_list); dfree(c->node_flag); dfree(c->flag_pos);
+  dfree(c->group_list);
   dfree(c->walk_stack); dfree(c->cand_i); dfree(c->cand_j); dfree(c->cand_keep);
   dfree(c->deg); dfree(c->fill); dfree(c->parent); dfree(c->label); dfree(c->csize);
   dfree(c->flag); dfree(c->pos); dfree(c->singles); dfree(c->cl_off); dfree(c->hlist);
@@ -132,9 +132,9 @@ int reserve(p3t_ctx *c, int64_t n, int64_t cand_cap) {
   ok &= dalloc(c->lvl_keys, NC) && dalloc(c->lvl_keys_alt, NC);
   ok &= dalloc(c->bfs2pre, NC) && dalloc(c->bfs2pre_alt, NC) && dalloc(c->pre2bfs, NC);
   ok &= dalloc(c->node, NC) && dalloc(c->mom64, NC) && dalloc(c->mom32, NC) && dalloc(c->nrs, NC);
-  ok &= dalloc(c->node_done, NC) && dalloc(c->leaf_list, NC) && dalloc(c->leaf_flag, NC);
-  ok &= dalloc(c->leaf_pos, NC);
-  ok &= dalloc(c->group_list, NC) && dalloc(c->group_flag, NC) && dalloc(c->group_pos, NC);
+  ok &= dalloc(c->node_done, NC) && dalloc(c->leaf_list, NC) && dalloc(c->node_flag, NC);
+  ok &= dalloc(c->flag_pos, NC);
+  ok &= dalloc(c->group_list, NC);
   ok &= dalloc(c->walk_stack, c->walk_warps * c->stack_cap);
   ok &= dalloc(c->cand_i, cand_cap) && dalloc(c->cand_j, cand_cap) && dalloc(c->cand_keep, cand_cap);
   ok &= dalloc(c->deg, N + 1) && dalloc(c->fill, N + 1);

@@ -238,10 +238,8 @@ struct p3t_ctx {
   int32_t *node_done = nullptr;            // bottom-up arrival counters
   int32_t *leaf_list = nullptr;            // leaves (BFS ids) in key order
   int32_t *group_list = nullptr;           // target groups (BFS ids) in key order
-  int32_t *group_flag = nullptr;
-  int64_t *group_pos = nullptr;
-  int32_t *leaf_flag = nullptr;
-  int64_t *leaf_pos = nullptr;
+  int32_t *node_flag = nullptr;            // per preorder node: bit 0 leaf, bit 1 target group
+  int64_t *flag_pos = nullptr;             // their prefix counts (leaves bits 0-30, groups from 31)
   int64_t *bh_table = nullptr;             // Barnes-Hut thresholds per level
 
   // walk
@@ -355,6 +353,12 @@ int p3t_scan_i32_to_i64(const int32_t *in, int64_t *out, const int64_t *d_n,
                         int64_t n_cap, int64_t *d_total, unsigned long long *state,
                         int64_t state_words, DevStatus *st, int64_t poll_limit,
                         cudaStream_t s);
+// The same scan of inputs that each hold two 0/1 flags (bits 0 and 1): out
+// and *d_total hold the prefix count of flag 0 in bits 0-30 and that of flag
+// 1 from bit 31 up.
+int p3t_scan_flag_pairs(const int32_t *in, int64_t *out, const int64_t *d_n, int64_t n_cap,
+                        int64_t *d_total, unsigned long long *state, int64_t state_words,
+                        DevStatus *st, int64_t poll_limit, cudaStream_t s);
 // Stable LSD radix sort of (key, val) on bits [begin_bit, end_bit), n from
 // device memory (at most n_cap).  Ping-pongs between the two buffers; on
 // return *keys / *vals point at the sorted data.

@@ -46,12 +46,20 @@ __device__ int64_t block_excl_scan(int64_t v, int64_t *excl, int64_t *sh) {
 // blocks as the count has tiles take one, the rest return at once.  The last
 // block to finish (counter state[1]) clears the words it used and both
 // counters, so that the next call starts clean with no host involvement.  A bounded number of polls: a predecessor that
-// never publishes is reported (P3T_ERR_TIMEOUT) and counted as zero.
+// never publishes is reported (P3T_ERR_TIMEOUT) and counted as zero.  With
+// PAIRS, every input holds two 0/1 flags (bits 0 and 1) and counts as
+// flag0 + flag1 2^31, so that one scan gives both prefix counts (each below
+// 2^31) in one word.
 constexpr int kScanThreads = 512;
 constexpr int kScanPer = 8;
 constexpr int kScanTile = kScanThreads * kScanPer;
 constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagInc = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
+template <bool PAIRS>
+__device__ __forceinline__ int64_t scan_value(int32_t v) {
+  return PAIRS ? (int64_t)(v & 1) + ((int64_t)((v >> 1) & 1) << 31) : (int64_t)v;
+}
+template <bool PAIRS>
 __global__ void __launch_bounds__(kScanThreads)
 scan_onepass(const int32_t *in, int64_t *out, const int64_t *d_n, int64_t *d_total,
              unsigned long long *state, DevStatus *st, int64_t poll_limit) {
@@ -90,7 +98,7 @@ scan_onepass(const int32_t *in, int64_t *out, const int64_t *d_n, int64_t *d_tot
       v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
     }
 #pragma unroll
-    for (int i = 0; i < kScanPer; ++i) sum += v[i];
+    for (int i = 0; i < kScanPer; ++i) sum += scan_value<PAIRS>(v[i]);
     int64_t ex;
     const int64_t agg = block_excl_scan(sum, &ex, sh);
     if (warp == 0) {
@@ -139,7 +147,7 @@ scan_onepass(const int32_t *in, int64_t *out, const int64_t *d_n, int64_t *d_tot
 #pragma unroll
     for (int i = 0; i < kScanPer; ++i) {
       s_buf[t * kScanPer + i] = run;
-      run += v[i];
+      run += scan_value<PAIRS>(v[i]);
     }
     __syncthreads();
     for (int i = 0; i < kScanPer; ++i) {
@@ -349,8 +357,20 @@ int p3t_scan_i32_to_i64(const int32_t *in, int64_t *out, const int64_t *d_n,
   int64_t G = (n_cap + kScanTile - 1) / kScanTile;
   if (G < 1) G = 1;
   if (G + 2 > state_words) return P3T_ERR_CAPACITY;
-  pdl_launch(scan_onepass, dim3((unsigned)G), dim3(kScanThreads), 0, s, in, out, d_n, d_total, state, st,
-                                                    poll_limit);
+  pdl_launch(scan_onepass<false>, dim3((unsigned)G), dim3(kScanThreads), 0, s, in, out, d_n, d_total,
+             state, st, poll_limit);
+  p3t_note_launches(1);
+  return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
+}
+
+int p3t_scan_flag_pairs(const int32_t *in, int64_t *out, const int64_t *d_n, int64_t n_cap,
+                        int64_t *d_total, unsigned long long *state, int64_t state_words,
+                        DevStatus *st, int64_t poll_limit, cudaStream_t s) {
+  int64_t G = (n_cap + kScanTile - 1) / kScanTile;
+  if (G < 1) G = 1;
+  if (G + 2 > state_words) return P3T_ERR_CAPACITY;
+  pdl_launch(scan_onepass<true>, dim3((unsigned)G), dim3(kScanThreads), 0, s, in, out, d_n, d_total,
+             state, st, poll_limit);
   p3t_note_launches(1);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }

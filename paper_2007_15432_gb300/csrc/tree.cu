@@ -638,7 +638,7 @@ __global__ void k_nodes_bfs(const int64_t *d_nnode, int64_t node_cap,
                             const int32_t *pre_level, const int8_t *lp,
                             const int8_t *lv, const int64_t *nstart,
                             const int32_t *sq, TreeNode *node,
-                            int32_t *leaf_flag, int32_t *node_done, DevStatus *st) {
+                            int gs, int32_t *flags, int32_t *node_done, DevStatus *st) {
   pdl_wait();
   const int64_t nn = min(*d_nnode, node_cap);
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nn;
@@ -652,8 +652,6 @@ __global__ void k_nodes_bfs(const int64_t *d_nnode, int64_t node_cap,
     const int sh = P3T_BITS - l;
     for (int a = 0; a < 3; ++a) nd.c2[a] = (2 * (sq[3 * first + a] >> sh) + 1) << sh;
     const bool internal = l < (int)lv[first];
-    leaf_flag[pre] = internal ? 0 : 1;
-    node_done[b] = 0;
     if (internal && pre + 1 < nn) {
       nd.child0 = pre2bfs[pre + 1];
       const int64_t e = (int64_t)first + count;
@@ -670,10 +668,16 @@ __global__ void k_nodes_bfs(const int64_t *d_nnode, int64_t node_cap,
         }
       }
       nd.nchild = k;
+      node_done[b] = k;
     } else {
       nd.child0 = -1;
       nd.nchild = 0;
+      node_done[b] = 0;
     }
+    // bit 0: a leaf; bit 1: a target group without a parent (a root; the
+    // parents flag the others)
+    const bool small = count <= gs || nd.nchild == 0;
+    flags[pre] = (internal ? 0 : 1) | (l == 0 && small ? 2 : 0);
     // geometry (qlo, qhi, R) is filled bottom-up by k_moments and the parent
     // links by k_parents
     TreeNode *o = &node[b];
@@ -684,53 +688,49 @@ __global__ void k_nodes_bfs(const int64_t *d_nnode, int64_t node_cap,
   }
 }
 
-__global__ void k_parents(const int64_t *d_nnode, int64_t node_cap, TreeNode *node) {
+// parent links, and the target-group flag (bit 1 of the preorder flags) of
+// every child: a node holding <= gs particles (or a leaf) whose parent holds
+// more
+__global__ void k_parents(const int64_t *d_nnode, int64_t node_cap, TreeNode *node,
+                          const int32_t *bfs2pre, int gs, int32_t *flags) {
   pdl_wait();
   const int64_t nn = min(*d_nnode, node_cap);
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nn;
        b += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c0 = node[b].child0, nc = node[b].nchild;
     if (nc > 0 && (c0 <= b || (int64_t)c0 + nc > nn)) continue;  // inconsistent: skip
-    for (int k = 0; k < nc; ++k) node[c0 + k].parent = (int32_t)b;
+    const bool big = node[b].count > gs;
+    for (int k = 0; k < nc; ++k) {
+      TreeNode &cn = node[c0 + k];
+      cn.parent = (int32_t)b;
+      if (big && (cn.count <= gs || cn.nchild == 0)) flags[bfs2pre[c0 + k]] |= 2;
+    }
   }
 }
 
-__global__ void k_leaf_list(const int64_t *d_nnode, int64_t node_cap,
-                            const int32_t *leaf_flag, const int64_t *leaf_pos,
-                            const int32_t *pre2bfs, int32_t *leaf_list) {
+// the leaf list and the target-group list in key order from the flag-pair
+// scan (leaf positions in bits 0-30, group positions from bit 31), and both
+// counts from its total
+__global__ void k_lists(const int64_t *d_nnode, int64_t node_cap, const int32_t *flags,
+                        const int64_t *pos, const int32_t *pre2bfs, const int64_t *d_total,
+                        int32_t *leaf_list, int32_t *group_list, int64_t *d_nleaf,
+                        int64_t *d_ngroup) {
   pdl_wait();
   const int64_t nn = min(*d_nnode, node_cap);
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nn;
-       p += (int64_t)gridDim.x * blockDim.x)
-    if (leaf_flag[p]) leaf_list[leaf_pos[p]] = pre2bfs[p];
-}
-
-// target groups: a node holding <= gs particles (or a leaf) whose parent
-// holds more (or the root); flags indexed by preorder id for key order
-__global__ void k_group_flags(const int64_t *d_nnode, int64_t node_cap,
-                              const TreeNode *node, const int32_t *bfs2pre, int gs,
-                              int32_t *group_flag) {
-  pdl_wait();
-  const int64_t nn = min(*d_nnode, node_cap);
-  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nn;
-       b += (int64_t)gridDim.x * blockDim.x) {
-    const TreeNode &nd = node[b];
-    const bool small = nd.count <= gs || nd.nchild == 0;
-    const bool top = nd.parent < 0 || node[nd.parent].count > gs;
-    group_flag[bfs2pre[b]] = (small && top) ? 1 : 0;
+  constexpr int64_t kLow = (1ll << 31) - 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t t = *d_total;
+    *d_nleaf = t & kLow;
+    *d_ngroup = t >> 31;
   }
-}
-
-// group list in key order, and every member's group
-__global__ void k_group_list(const int64_t *d_nnode, int64_t node_cap,
-                             const int32_t *group_flag, const int64_t *group_pos,
-                             const int32_t *pre2bfs, int32_t *group_list) {
-  pdl_wait();
-  const int64_t nn = min(*d_nnode, node_cap);
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nn;
        p += (int64_t)gridDim.x * blockDim.x) {
-    if (!group_flag[p]) continue;
-    group_list[group_pos[p]] = pre2bfs[p];
+    const int32_t f = flags[p];
+    if (!f) continue;
+    const int64_t q = pos[p];
+    const int32_t b = pre2bfs[p];
+    if (f & 1) leaf_list[q & kLow] = b;
+    if (f & 2) group_list[q >> 31] = b;
   }
 }
 
@@ -818,13 +818,14 @@ __device__ __forceinline__ int64_t max_bits(int64_t a, double v) {
   return b > a ? b : a;
 }
 
-__device__ __forceinline__ void leaf_moments32(
+__device__ __forceinline__ int32_t leaf_moments32(
     int64_t b, TreeNode *node, Mom32 *m32, double *nrs, const float4 *spA, const float4 *spB,
     const float *sml, const double *srs, const int32_t *sq, const double *box,
     const SegView &sv) {
   {
     TreeNode *nd = &node[b];
-    const int32_t f = nd->first, c = nd->count;
+    const int4 r2 = reinterpret_cast<const int4 *>(nd)[2], r3 = reinterpret_cast<const int4 *>(nd)[3];
+    const int32_t f = r3.z, c = r3.w;
     const double L = box[5 * seg_at(sv, f) + 3];
     const float4 A0 = spA[f], B0 = spB[f];
     FF M{0.f, 0.f}, D[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
@@ -864,6 +865,7 @@ __device__ __forceinline__ void leaf_moments32(
     nrs[b] = rs;
     nd->R = reach_cells(rs, L, cell_scale(L));
     m32[b] = o;
+    return r2.w;
   }
 }
 
@@ -894,10 +896,12 @@ __device__ __forceinline__ Mom32 ldcg_mom32(const Mom32 *m) {
   return o;
 }
 
-__device__ void node_moments32(int64_t b, TreeNode *node, Mom32 *m32, double *nrs,
-                               const double *box, const SegView &sv) {
+__device__ int32_t node_moments32(int64_t b, TreeNode *node, Mom32 *m32, double *nrs,
+                                  const double *box, const SegView &sv) {
   TreeNode *pn = &node[b];
-  const int32_t c0 = pn->child0, nch = pn->nchild;
+  const int4 r2 = __ldcg(reinterpret_cast<const int4 *>(pn) + 2),
+             r3 = __ldcg(reinterpret_cast<const int4 *>(pn) + 3);
+  const int32_t c0 = r3.x, nch = r3.y;
   int64_t rsb = 0;
   int32_t plo[3] = {P3T_QMAX, P3T_QMAX, P3T_QMAX}, phi[3] = {-1, -1, -1};
   for (int k = 0; k < nch; ++k) {
@@ -948,15 +952,17 @@ __device__ void node_moments32(int64_t b, TreeNode *node, Mom32 *m32, double *nr
   for (int a = 0; a < 3; ++a) { pn->qlo[a] = plo[a]; pn->qhi[a] = phi[a]; }
   const double rs = __longlong_as_double(rsb);
   nrs[b] = rs;
-  const double L = box[5 * seg_at(sv, pn->first) + 3];
+  const double L = box[5 * seg_at(sv, r3.z) + 3];
   pn->R = reach_cells(rs, L, cell_scale(L));
   m32[b] = o;
+  return r2.w;
 }
 
 // All moments of the mixed path in one launch, bottom-up: a thread per leaf
-// computes the leaf, then counts itself at its parent (node_done, zeroed by
-// k_nodes_bfs); the child that completes the count computes the parent from
-// all its children and climbs on.  Nothing waits, and a node's result does
+// computes the leaf, then counts itself off at its parent (node_done, preset
+// to the number of children by k_nodes_bfs); the child that brings the count
+// to zero computes the parent from all its children and climbs on (each
+// node's record gives its parent in the same load as its children).  Nothing waits, and a node's result does
 // not depend on which child arrives last.  (In FP32 and float-float a node
 // costs a few thousand cycles of latency, so the climb's serial tail at the
 // top levels is short; the FP64 path keeps its level launches.)
@@ -968,17 +974,12 @@ __global__ void k_moments_up32(
   const int64_t nleaf = *d_nleaf;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nleaf;
        t += (int64_t)gridDim.x * blockDim.x) {
-    int64_t b = leaf_list[t];
-    leaf_moments32(b, node, m32, nrs, spA, spB, sml, srs, sq, box, sv);
-    for (;;) {
-      const int32_t p = node[b].parent;
-      if (p < 0) break;
+    int32_t p = leaf_moments32(leaf_list[t], node, m32, nrs, spA, spB, sml, srs, sq, box, sv);
+    while (p >= 0) {
       __threadfence();  // this node's record before the count
-      const int done = atomicAdd(&node_done[p], 1) + 1;
-      if (done < node[p].nchild) break;
+      if (atomicSub(&node_done[p], 1) != 1) break;  // siblings still to come
       __threadfence();  // the siblings' records after their counts
-      node_moments32(p, node, m32, nrs, box, sv);
-      b = p;
+      p = node_moments32(p, node, m32, nrs, box, sv);
     }
   }
 }
@@ -1288,13 +1289,16 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
   pdl_launch(k_nodes_bfs, dim3((unsigned)gn), dim3(kBlock), 0, s, &cnt[3], c->node_cap, c->bfs2pre, c->pre2bfs,
                                               c->pre_first, c->pre_count, c->pre_level,
                                               c->lp, c->lv, c->nstart, c->sq, c->node,
-                                              c->leaf_flag, c->node_done, c->status);
-  pdl_launch(k_parents, dim3((unsigned)gn), dim3(kBlock), 0, s, &cnt[3], c->node_cap, c->node);
-  rc = p3t_scan_i32_to_i64(c->leaf_flag, c->leaf_pos, &cnt[3], c->node_cap, &cnt[2],
+                                              c->prm.group_size, c->node_flag, c->node_done,
+                                              c->status);
+  pdl_launch(k_parents, dim3((unsigned)gn), dim3(kBlock), 0, s, &cnt[3], c->node_cap, c->node,
+             c->bfs2pre, c->prm.group_size, c->node_flag);
+  // leaves (bit 0) and target groups (bit 1) counted by one scan
+  rc = p3t_scan_flag_pairs(c->node_flag, c->flag_pos, &cnt[3], c->node_cap, &cnt[19],
                            c->scan_state, c->scan_words, c->status, c->poll_limit, s);
   if (rc) return rc;
-  pdl_launch(k_leaf_list, dim3((unsigned)gn), dim3(kBlock), 0, s, &cnt[3], c->node_cap, c->leaf_flag,
-                                              c->leaf_pos, c->pre2bfs, c->leaf_list);
+  pdl_launch(k_lists, dim3((unsigned)gn), dim3(kBlock), 0, s, &cnt[3], c->node_cap, c->node_flag,
+             c->flag_pos, c->pre2bfs, &cnt[19], c->leaf_list, c->group_list, &cnt[2], &cnt[15]);
   if (c->prm.precision == P3T_MIXED) {
     pdl_launch(k_moments_up32, dim3((unsigned)p3t_grid(c->node_cap, 128, maxb)), dim3(128), 0, s, 
         &cnt[2], c->leaf_list, c->node, c->mom32, c->nrs, c->spA, c->spB, c->sml, c->srs,
@@ -1317,17 +1321,10 @@ int p3t_run_build_tree(p3t_ctx *c, const p3t_particles *p, cudaStream_t s) {
                                                            c->mom32, c->nrs, c->box, sv, wt);
     p3t_note_launches(3 + kDeepLevel);  // leaves, level offsets, deep levels, one a level
   }
-  pdl_launch(k_group_flags, dim3((unsigned)gn), dim3(kBlock), 0, s, &cnt[3], c->node_cap, c->node, c->bfs2pre,
-                                                c->prm.group_size, c->group_flag);
-  rc = p3t_scan_i32_to_i64(c->group_flag, c->group_pos, &cnt[3], c->node_cap, &cnt[15],
-                           c->scan_state, c->scan_words, c->status, c->poll_limit, s);
-  if (rc) return rc;
-  pdl_launch(k_group_list, dim3((unsigned)gn), dim3(kBlock), 0, s, &cnt[3], c->node_cap, c->group_flag,
-                                               c->group_pos, c->pre2bfs, c->group_list);
   // own kernels here (the scans, sorts and moments count themselves): box 3,
   // keys, gather, lcp_levels, nodes_pre, node_counts, pre2bfs, nodes_bfs,
-  // parents, leaf_list, group_flags, group_list
-  p3t_note_launches(14);
+  // parents, lists
+  p3t_note_launches(12);
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
 
