@@ -874,20 +874,50 @@ __device__ __forceinline__ int32_t leaf_moments32(
 // s4) + (s2 + s6)) + ((s1 + s5) + (s3 + s7)) (zero past the last child).  The
 // children were written by other threads of the same launch: read through L2.
 template <int NQ, class T, class F, class A>
-__device__ __forceinline__ void tree8_acc(F slot, A add, T (&r)[NQ]) {
+__device__ __forceinline__ void tree8_acc(int nch, F slot, A add, T (&r)[NQ]) {
+  // the children fill slots 0 .. nch - 1; an empty slot is zero and adding
+  // zero to a (normalised) sum returns it, so empty slots and their additions
+  // are skipped: the same values as the full tree
   T a[NQ], b[NQ], c[NQ], d[NQ];
-  slot(0, a); slot(4, b);
+  slot(0, a);
+  if (nch > 4) {
+    slot(4, b);
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) a[q] = add(a[q], b[q]);
-  slot(2, b); slot(6, c);
+    for (int q = 0; q < NQ; ++q) a[q] = add(a[q], b[q]);
+  }
+  if (nch > 2) {
+    slot(2, b);
+    if (nch > 6) {
+      slot(6, c);
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) { b[q] = add(b[q], c[q]); a[q] = add(a[q], b[q]); }
-  slot(1, b); slot(5, c);
+      for (int q = 0; q < NQ; ++q) b[q] = add(b[q], c[q]);
+    }
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) b[q] = add(b[q], c[q]);
-  slot(3, c); slot(7, d);
+    for (int q = 0; q < NQ; ++q) a[q] = add(a[q], b[q]);
+  }
+  if (nch > 1) {
+    slot(1, b);
+    if (nch > 5) {
+      slot(5, c);
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) { c[q] = add(c[q], d[q]); b[q] = add(b[q], c[q]); r[q] = add(a[q], b[q]); }
+      for (int q = 0; q < NQ; ++q) b[q] = add(b[q], c[q]);
+    }
+    if (nch > 3) {
+      slot(3, c);
+      if (nch > 7) {
+        slot(7, d);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) c[q] = add(c[q], d[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) b[q] = add(b[q], c[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) r[q] = add(a[q], b[q]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) r[q] = a[q];
+  }
 }
 
 __device__ __forceinline__ Mom32 ldcg_mom32(const Mom32 *m) {
@@ -902,6 +932,7 @@ __device__ int32_t node_moments32(int64_t b, TreeNode *node, Mom32 *m32, double 
   const int4 r2 = __ldcg(reinterpret_cast<const int4 *>(pn) + 2),
              r3 = __ldcg(reinterpret_cast<const int4 *>(pn) + 3);
   const int32_t c0 = r3.x, nch = r3.y;
+  if (nch < 1 || nch > 8) return r2.w;  // only a node with children is completed
   int64_t rsb = 0;
   int32_t plo[3] = {P3T_QMAX, P3T_QMAX, P3T_QMAX}, phi[3] = {-1, -1, -1};
   for (int k = 0; k < nch; ++k) {
@@ -913,22 +944,18 @@ __device__ int32_t node_moments32(int64_t b, TreeNode *node, Mom32 *m32, double 
     }
   }
   FF P[4];
-  tree8_acc<4>([&](int k, FF (&t)[4]) {
-    for (int q = 0; q < 4; ++q) t[q] = FF{0.f, 0.f};
-    if (k < nch) {
-      const Mom32 cm = ldcg_mom32(&m32[c0 + k]);
-      const FF M = ff_fast(cm.hi.w, cm.lo.w);
-      t[0] = M;
-      t[1] = ff_mul(M, ff_fast(cm.hi.x, cm.lo.x));
-      t[2] = ff_mul(M, ff_fast(cm.hi.y, cm.lo.y));
-      t[3] = ff_mul(M, ff_fast(cm.hi.z, cm.lo.z));
-    }
+  tree8_acc<4>(nch, [&](int k, FF (&t)[4]) {
+    const float4 hi = __ldcg(&m32[c0 + k].hi), lo = __ldcg(&m32[c0 + k].lo);
+    const FF M = ff_fast(hi.w, lo.w);
+    t[0] = M;
+    t[1] = ff_mul(M, ff_fast(hi.x, lo.x));
+    t[2] = ff_mul(M, ff_fast(hi.y, lo.y));
+    t[3] = ff_mul(M, ff_fast(hi.z, lo.z));
   }, [](FF x, FF y) { return ff_add(x, y); }, P);
   const FF pc[3] = {ff_div(P[1], P[0]), ff_div(P[2], P[0]), ff_div(P[3], P[0])};
   float Q[6];
-  tree8_acc<6>([&](int k, float (&t)[6]) {
-    for (int q = 0; q < 6; ++q) t[q] = 0.f;
-    if (k < nch) {
+  tree8_acc<6>(nch, [&](int k, float (&t)[6]) {
+    {
       const Mom32 cm = ldcg_mom32(&m32[c0 + k]);
       const float M = cm.hi.w;
       const float dx = ff_add(ff_fast(cm.hi.x, cm.lo.x), ff_neg(pc[0])).h;
