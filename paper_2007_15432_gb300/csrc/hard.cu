@@ -121,6 +121,20 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
   return y;
 }
 
+// the same with its rounded fallback out of line (an inlined fallback is
+// predicated into every call, and predicated-off FP64 instructions still take
+// the FP64 pipe): the pair terms of the block steps
+__device__ __noinline__ double rsqrt_rounded(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ double rsqrt_nr_ool(double x) {
+  const float xf = (float)x;
+  if (!(xf > 1e-36f && xf < 1e36f)) return rsqrt_rounded(x);
+  double y = (double)rsqrtf(xf);
+  const double hx = 0.5 * x;
+  y = y * __fma_rn(-hx * y, y, 1.5);
+  y = y * __fma_rn(-hx * y, y, 1.5);
+  return y;
+}
+
 // Advances (X, V) by dt on the Kepler orbit about mu.  Universal anomaly chi
 // solves F(chi) = sig chi^2 C + (1 - alpha r0) chi^3 S + r0 chi - sqrt(mu) dt
 // = 0 (z = alpha chi^2, sig = r0 v_r0 / sqrt(mu)) by Newton-Raphson from the
@@ -595,7 +609,7 @@ __device__ __forceinline__ void hard_term(const V &S, int nc, int k, int j,
     hit = r2 < sr * sr;
   }
   if (r2 == 0.0) return;
-  const double rinv = 1.0 / sqrt(r2);
+  const double rinv = rsqrt_nr_ool(r2);
   const double r = r2 * rinv;
   const double irot = star ? 0.0 : (S.iro(k) < S.iro(js) ? S.iro(k) : S.iro(js));
   const double yv = r * irot;
