@@ -293,13 +293,15 @@ def run_ours(args):
     e_disp = [0.0, 0.0]
     merged = [0]
 
-    def step(k=None, counts=None):
+    def step(k=None, counts=None, out=None):
         e = ev[k] if k is not None else None
         cnt = counts if counts is not None else (counts_all[k] if k is not None else scratch_counts)
         if e: e[0].record(stream)
         P.p3t_kick(ss.ctx, st, ss.acc, h, stream)
         P.p3t_hard_step(ss.ctx, st, ss.cl, prm.dt_soft,
                         hsteps_all[k:k + 1] if k is not None else ss.hsteps, stream)
+        if out is not None:
+            out.after_hard(st, stream)   # rows the rest of the step leaves alone
         if e: e[1].record(stream)
         # composites formed by this hard step: the merge after the second
         # kick rebuilds the neighbour lists, so the force before it builds
@@ -319,6 +321,8 @@ def run_ours(args):
         if e: e[5].record(stream)
         if pending:
             # procedure step 9: merge (synchronises), then new radii and force
+            if out is not None:
+                out.fence(stream)
             nm, eh, es = P.p3t_merge(ss.ctx, st, None, stream)
             e_disp[0] += eh
             e_disp[1] += es
@@ -332,6 +336,8 @@ def run_ours(args):
                 ss.cl = P.p3t_neighbours(ss.ctx, st, ss.nb_off, ss.nb_idx, stream)
             else:
                 raise RuntimeError("composites pending but nothing merged")
+        if out is not None:
+            out.finish(st, stream, pending)
         if e: e[6].record(stream)
 
     for _ in range(W):
@@ -379,27 +385,30 @@ def run_ours(args):
 
     # ---- end to end through the C ABI with host buffers --------------------
     # the state's (10, n) block: x, y, z, vx, vy, vz, m, r_out, r_search,
-    # r_phys (rows shortened by merges keep their storage; the block moves whole)
+    # r_phys (rows shortened by merges keep their storage; the block moves in
+    # whole).  The result comes back row by row (StateCopyOut): the rows the
+    # second kick leaves alone cross the link while the tree and the force
+    # run, the velocities after the kick (every row again after a merge).
     host = stbuf.cpu().pin_memory()
     host_out = torch.empty_like(host).pin_memory()
+    out = P.StateCopyOut(host_out)
     E = max(1, args.e2e_steps)
     e2e_counts = torch.zeros(E, 2, 2, dtype=torch.int64, device=dev)
-    h2d = d2h = 0
+    h2d = 0
     torch.cuda.synchronize(dev)
     barrier(dist)
     t0 = time.perf_counter()
     for k in range(E):
         stbuf.copy_(host, non_blocking=True)
         h2d += host.numel() * host.element_size()
-        step(None, counts=e2e_counts[k])
-        host_out.copy_(stbuf, non_blocking=True)
-        d2h += host_out.numel() * host_out.element_size()
+        out.host = host_out
+        step(None, counts=e2e_counts[k], out=out)
         torch.cuda.synchronize(dev)
         host, host_out = host_out, host   # the result is the next step's input
     t_e2e = time.perf_counter() - t0
     e2e_inter = float(e2e_counts.sum().item())
     h2d //= E
-    d2h //= E
+    d2h = out.d2h_bytes // E
     ss.status()
 
     tot_elapsed = allmax(dist, elapsed)

@@ -215,6 +215,51 @@ class State:
         return {k: getattr(self, k).cpu().numpy() for k in self._arrays()}
 
 
+class StateCopyOut:
+    """Reads a State back into a pinned host block while a soft step runs.
+
+    ``host`` is a pinned float64 CPU tensor of shape (10, >= n) whose rows
+    receive x, y, z, vx, vy, vz, m, r_out, r_search, r_phys (columns 0..n-1).
+    After the hard step only the second kick (velocities) and a merge change
+    the state, so ``after_hard`` queues the other rows on a side stream, where
+    they cross the link while the tree and the force run; ``finish`` copies
+    the velocities, or, when the step merged particles, every row again.
+    ``fence`` (before a merge) keeps the merge from rewriting rows that are
+    still being read.  ``d2h_bytes`` counts the bytes copied.
+    """
+
+    LATE = (3, 4, 5)
+
+    def __init__(self, host: torch.Tensor):
+        if host.is_cuda or host.dtype != torch.float64 or host.dim() != 2 or host.shape[0] < 10:
+            raise TypeError("host must be a (10, n) float64 CPU tensor")
+        self.host = host
+        self.side = torch.cuda.Stream()
+        self.ev = torch.cuda.Event()
+        self.d2h_bytes = 0
+
+    def _copy(self, st: State, rows, stream) -> None:
+        names = st._arrays()
+        n = len(st.m)
+        with torch.cuda.stream(stream):
+            for r in rows:
+                if r < len(names):
+                    self.host[r, :n].copy_(getattr(st, names[r]), non_blocking=True)
+                    self.d2h_bytes += 8 * n
+
+    def after_hard(self, st: State, stream) -> None:
+        self.ev.record(stream)
+        self.side.wait_event(self.ev)
+        self._copy(st, [r for r in range(10) if r not in self.LATE], self.side)
+
+    def fence(self, stream) -> None:
+        stream.wait_stream(self.side)
+
+    def finish(self, st: State, stream, merged: bool) -> None:
+        stream.wait_stream(self.side)
+        self._copy(st, range(10) if merged else self.LATE, stream)
+
+
 # ---- functions with the C names ---------------------------------------------
 def p3t_strerror(code: int) -> str:
     return _lib.p3t_strerror(int(code)).decode()
@@ -525,10 +570,15 @@ class SoftStep:
             self.force(stream)
         return nm
 
-    def step(self, stream=None):
+    def step(self, stream=None, out: StateCopyOut | None = None):
+        """One soft step; with ``out``, the state after the step is also read
+        back into ``out.host`` (see StateCopyOut), overlapped with the step."""
         h = 0.5 * self.params.dt_soft
+        cs = stream if stream is not None else torch.cuda.current_stream()
         p3t_kick(self.ctx, self.st, self.acc, h, stream)
         p3t_hard_step(self.ctx, self.st, self.cl, self.params.dt_soft, self.hsteps, stream)
+        if out is not None:
+            out.after_hard(self.st, cs)
         # composites formed in this hard step: the merge after the second kick
         # recomputes the neighbour lists, so the force before it needs none.
         # The count is read while the tree and the force run.
@@ -540,8 +590,13 @@ class SoftStep:
         if not pending:
             self.cl = p3t_neighbours(self.ctx, self.st, self.nb_off, self.nb_idx, stream)
         p3t_kick(self.ctx, self.st, self.acc, h, stream)
-        if pending and self.merge(stream) == 0:
-            raise P3TError(P3T_ERR_INVALID, "composites pending but nothing merged")
+        if pending:
+            if out is not None:
+                out.fence(cs)
+            if self.merge(stream) == 0:
+                raise P3TError(P3T_ERR_INVALID, "composites pending but nothing merged")
+        if out is not None:
+            out.finish(self.st, cs, pending)
 
     def status(self):
         rc, req = p3t_status(self.ctx)

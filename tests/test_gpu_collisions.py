@@ -201,3 +201,40 @@ def test_whole_soft_steps_with_collisions(P3T):
         assert rel_err(_vec(g, keys), _vec(so, keys)).max() < 1e-11
     assert ss.e_disp[0] == pytest.approx(e_ref[0], rel=1e-10)
     ss.close()
+
+
+def test_state_copy_out_during_steps(P3T):
+    """SoftStep.step(out=StateCopyOut): the host block equals the state after
+    every step, in steps that merge (every row copied again) and in steps
+    that do not (positions, masses and radii read back while the tree and
+    the force run, the velocities after the kick)."""
+    s = disks.planted_impacts(disks.equal_mass_narrow(), [(100, 101), (500, 501)])
+    P = P3T.Params(theta=0.5, eta=0.01, eta0=0.001, f_radius=1.0)
+    op = oracle_params(P)
+    rp = disks.physical_radius(s["m"])
+    ro, rs, _, _ = O.cutoffs(s, op)
+    st, buf = P3T.State.from_numpy_packed(s, r_out=ro, r_search=rs, r_phys=rp)
+    ss = P3T.SoftStep(P, st)
+    ss.init(update_cutoffs=False)
+    host = torch.full(tuple(buf.shape), float("nan"), dtype=torch.float64).pin_memory()
+    out = P3T.StateCopyOut(host)
+    kinds = set()
+    for _ in range(3):
+        before = ss.merged
+        out.d2h_bytes = 0
+        ss.step(out=out)
+        torch.cuda.synchronize()
+        ss.status()
+        n = len(ss.st.m)
+        g = ss.st.numpy()
+        for r, k in enumerate(("x", "y", "z", "vx", "vy", "vz", "m", "r_out", "r_search",
+                               "r_phys")):
+            assert np.array_equal(host[r, :n].numpy(), g[k]), (k, ss.merged)
+        merged = ss.merged > before
+        kinds.add(merged)
+        # seven rows after the hard step (n before the merge), then three, or
+        # all ten after a merge
+        n_before = n + (ss.merged - before)
+        assert out.d2h_bytes == 8 * (7 * n_before + (10 * n if merged else 3 * n))
+    assert kinds == {True, False}
+    ss.close()
