@@ -59,6 +59,7 @@ struct WalkArgs {
   DevStatus *st;
   SegView seg;                     // segments: the root of segment d is node d
   double G, gamma;
+  double inv1mg;                   // 1 / (1 - gamma)
   float inv1mg_f, mgi_f;           // 1 / (1 - gamma), -gamma / (1 - gamma)
   float refine_cf;                 // refine when sum|term| > refine_cf * |a|
   int64_t bh[P3T_BITS + 1];
@@ -155,7 +156,7 @@ template <> struct Target<true> {
 };
 
 template <> struct Target<false> {
-  double x, y, z, ro, rs;
+  double x, y, z, iro, rs;  // iro = 1 / r_out
   double ax, ay, az;
   int32_t self;
   int rep, nrep;
@@ -167,9 +168,9 @@ template <> struct Target<false> {
     nrep = nr;
     ax = ay = az = 0.0;
     if (v) {
-      x = a.sx[ti]; y = a.sy[ti]; z = a.sz[ti]; ro = a.sro[ti]; rs = a.srs[ti];
+      x = a.sx[ti]; y = a.sy[ti]; z = a.sz[ti]; iro = 1.0 / a.sro[ti]; rs = a.srs[ti];
     } else {
-      x = y = z = 1.0e300; ro = 1.0; rs = 0.0;
+      x = y = z = 1.0e300; iro = 1.0; rs = 0.0;
     }
   }
   __device__ void reduce(int k) {
@@ -208,7 +209,7 @@ struct StagePP32 {
 struct StageND32 {
   ulonglong2 hxy[16], hzw[16], lxy[16], lzw[16], q0xy[16], q0zw[16], q1xy[16];
 };
-struct StagePP64 { double x[32], y[32], z[32], m[32], ro[32], rs[32]; int32_t idx[32]; };
+struct StagePP64 { double x[32], y[32], z[32], m[32], iro[32], rs[32]; int32_t idx[32]; };
 static_assert(sizeof(StagePP32) <= kStageBytes && sizeof(StagePP64) <= kStageBytes &&
               sizeof(StageND32) <= kStageBytes && sizeof(Mom64) * 32 <= kStageBytes,
               "stage area");
@@ -354,6 +355,24 @@ __device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<true> &t, cons
   fold_pairs(t, BX, BY, BZ, TB);
 }
 
+// 1 / sqrt(x) for the FP64 evaluators, x > 0: the FP32 estimate and two FP64
+// Newton-Raphson steps y (3 - x y^2) / 2 (the error squares each step, from
+// ~2^-23 to FP64 rounding) instead of a rounded square root and a division
+// (each a sequence of FP64 instructions at 1/64 of the FP32 rate); outside
+// the FP32 normal range the rounded form, out of line (inlined, its
+// instructions would be predicated into every pair and still take the FP64
+// pipe)
+__device__ __noinline__ double rsqrt64_rounded(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ double rsqrt64(double x) {
+  const float xf = (float)x;
+  if (!(xf > 1e-36f && xf < 1e36f)) return rsqrt64_rounded(x);
+  double y = (double)rsqrtf(xf);
+  const double hx = 0.5 * x;
+  y = y * __fma_rn(-hx * y, y, 1.5);
+  y = y * __fma_rn(-hx * y, y, 1.5);
+  return y;
+}
+
 __device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<false> &t, const int32_t *list,
                                         int nsrc, void *stage, const FarBox &, unsigned &npp) {
   StagePP64 &S = *reinterpret_cast<StagePP64 *>(stage);
@@ -361,7 +380,7 @@ __device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<false> &t, con
   if (lane < nsrc) {
     const int32_t j = list[lane];
     S.x[lane] = a.sx[j]; S.y[lane] = a.sy[j]; S.z[lane] = a.sz[j];
-    S.m[lane] = a.sm[j]; S.ro[lane] = a.sro[j]; S.rs[lane] = a.srs[j];
+    S.m[lane] = a.sm[j]; S.iro[lane] = 1.0 / a.sro[j]; S.rs[lane] = a.srs[j];
     S.idx[lane] = j;
   }
   __syncwarp();
@@ -369,10 +388,12 @@ __device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<false> &t, con
   for (int s = t.rep; s < nsrc; s += t.nrep) {
     const double dx = t.x - S.x[s], dy = t.y - S.y[s], dz = t.z - S.z[s];
     const double r2 = dx * dx + dy * dy + dz * dz;
-    const double rinv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
+    const double rinv = r2 > 0.0 ? rsqrt64(r2) : 0.0;
     const double r = r2 * rinv;
-    const double y = r / fmax(t.ro, S.ro[s]);
-    double x = (y - a.gamma) / (1.0 - a.gamma);
+    // y = r / max(r_out,i, r_out,j) as r min(1 / r_out): one reciprocal a
+    // staged source, not a division a pair
+    const double y = r * fmin(t.iro, S.iro[s]);
+    double x = (y - a.gamma) * a.inv1mg;
     x = x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x);
     const double x2 = x * x;
     const double K = (x2 * x2) * (((-20.0 * x + 70.0) * x - 84.0) * x + 35.0);
@@ -459,7 +480,7 @@ __device__ __forceinline__ void eval_nodes(const WalkArgs &a, Target<false> &t,
     const Mom64 &m = S[s];
     const double dx = t.x - m.cx, dy = t.y - m.cy, dz = t.z - m.cz;
     const double r2 = dx * dx + dy * dy + dz * dz;
-    const double rinv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
+    const double rinv = r2 > 0.0 ? rsqrt64(r2) : 0.0;
     const double rinv2 = rinv * rinv, rinv3 = rinv2 * rinv, rinv5 = rinv3 * rinv2;
     const double qx = m.qxx * dx + m.qxy * dy + m.qxz * dz;
     const double qy = m.qxy * dx + m.qyy * dy + m.qyz * dz;
@@ -1171,6 +1192,7 @@ static WalkArgs walk_args(p3t_ctx *c, const p3t_particles *p) {
   a.refine_cf = 32.0f;
   a.G = c->prm.G;
   a.gamma = c->prm.gamma;
+  a.inv1mg = 1.0 / (1.0 - c->prm.gamma);
   a.inv1mg_f = (float)(1.0 / (1.0 - c->prm.gamma));
   a.mgi_f = (float)(-c->prm.gamma / (1.0 - c->prm.gamma));
   for (int l = 0; l <= P3T_BITS; ++l) a.bh[l] = bh_threshold(c->prm.theta, l);
@@ -1214,6 +1236,7 @@ int p3t_run_soft_force(p3t_ctx *c, const p3t_particles *p, double *ax,
   a.refine_cf = 32.0f;
   a.G = c->prm.G;
   a.gamma = c->prm.gamma;
+  a.inv1mg = 1.0 / (1.0 - c->prm.gamma);
   a.inv1mg_f = (float)(1.0 / (1.0 - c->prm.gamma));
   a.mgi_f = (float)(-c->prm.gamma / (1.0 - c->prm.gamma));
   // Barnes-Hut thresholds per level, ceil((2^(22-l))^2 / theta^2) (half units)
