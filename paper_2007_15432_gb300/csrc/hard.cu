@@ -107,34 +107,6 @@ struct KepConst {
   double mu, sq, isq, imu;
 };
 
-// 1 / sqrt(x), x > 0: the FP32 estimate refined by two Newton-Raphson steps
-// y <- y (3 - x y^2) / 2 in FP64 (the error squares at each step, from ~2^-23
-// to below FP64 rounding), instead of a rounded square root and a division.
-// Outside the FP32 normal range the rounded forms are used.
-__device__ __forceinline__ double rsqrt_nr(double x) {
-  const float xf = (float)x;
-  if (!(xf > 1e-36f && xf < 1e36f)) return 1.0 / sqrt(x);
-  double y = (double)rsqrtf(xf);
-  const double hx = 0.5 * x;
-  y = y * __fma_rn(-hx * y, y, 1.5);
-  y = y * __fma_rn(-hx * y, y, 1.5);
-  return y;
-}
-
-// the same with its rounded fallback out of line (an inlined fallback is
-// predicated into every call, and predicated-off FP64 instructions still take
-// the FP64 pipe): the pair terms of the block steps
-__device__ __noinline__ double rsqrt_rounded(double x) { return 1.0 / sqrt(x); }
-__device__ __forceinline__ double rsqrt_nr_ool(double x) {
-  const float xf = (float)x;
-  if (!(xf > 1e-36f && xf < 1e36f)) return rsqrt_rounded(x);
-  double y = (double)rsqrtf(xf);
-  const double hx = 0.5 * x;
-  y = y * __fma_rn(-hx * y, y, 1.5);
-  y = y * __fma_rn(-hx * y, y, 1.5);
-  return y;
-}
-
 // Advances (X, V) by dt on the Kepler orbit about mu.  Universal anomaly chi
 // solves F(chi) = sig chi^2 C + (1 - alpha r0) chi^3 S + r0 chi - sqrt(mu) dt
 // = 0 (z = alpha chi^2, sig = r0 v_r0 / sqrt(mu)) by Newton-Raphson from the
@@ -146,7 +118,7 @@ __device__ bool kepler_uv(double X[3], double V[3], double dt, const KepConst &K
   const double r02 = __fma_rn(X[0], X[0], __fma_rn(X[1], X[1], X[2] * X[2]));
   const double v2 = __fma_rn(V[0], V[0], __fma_rn(V[1], V[1], V[2] * V[2]));
   const double rv = __fma_rn(X[0], V[0], __fma_rn(X[1], V[1], X[2] * V[2]));
-  const double ir0 = rsqrt_nr(r02);
+  const double ir0 = rsqrt(r02);
   const double r0 = r02 * ir0;
   const double alpha = __fma_rn(-v2, K.imu, 2.0 * ir0);
   const double sig = rv * K.isq;  // r0 v_r0 / sqrt(mu)
@@ -188,7 +160,7 @@ __device__ bool kepler_uv(double X[3], double V[3], double dt, const KepConst &K
   const double g = __fma_rn(-chi2 * chi, S * K.isq, dt);
   double nx[3];
   for (int a = 0; a < 3; ++a) nx[a] = __fma_rn(f, X[a], g * V[a]);
-  const double ir = rsqrt_nr(__fma_rn(nx[0], nx[0], __fma_rn(nx[1], nx[1], nx[2] * nx[2])));
+  const double ir = rsqrt(__fma_rn(nx[0], nx[0], __fma_rn(nx[1], nx[1], nx[2] * nx[2])));
   const double fd = K.sq * ir * ir0 * __fma_rn(z, S, -1.0) * chi;
   const double gd = __fma_rn(-chi2 * ir, C, 1.0);
   for (int a = 0; a < 3; ++a) {
@@ -609,7 +581,7 @@ __device__ __forceinline__ void hard_term(const V &S, int nc, int k, int j,
     hit = r2 < sr * sr;
   }
   if (r2 == 0.0) return;
-  const double rinv = rsqrt_nr_ool(r2);
+  const double rinv = rsqrt(r2);
   const double r = r2 * rinv;
   const double irot = star ? 0.0 : (S.iro(k) < S.iro(js) ? S.iro(k) : S.iro(js));
   const double yv = r * irot;

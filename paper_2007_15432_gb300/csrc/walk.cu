@@ -355,24 +355,6 @@ __device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<true> &t, cons
   fold_pairs(t, BX, BY, BZ, TB);
 }
 
-// 1 / sqrt(x) for the FP64 evaluators, x > 0: the FP32 estimate and two FP64
-// Newton-Raphson steps y (3 - x y^2) / 2 (the error squares each step, from
-// ~2^-23 to FP64 rounding) instead of a rounded square root and a division
-// (each a sequence of FP64 instructions at 1/64 of the FP32 rate); outside
-// the FP32 normal range the rounded form, out of line (inlined, its
-// instructions would be predicated into every pair and still take the FP64
-// pipe)
-__device__ __noinline__ double rsqrt64_rounded(double x) { return 1.0 / sqrt(x); }
-__device__ __forceinline__ double rsqrt64(double x) {
-  const float xf = (float)x;
-  if (!(xf > 1e-36f && xf < 1e36f)) return rsqrt64_rounded(x);
-  double y = (double)rsqrtf(xf);
-  const double hx = 0.5 * x;
-  y = y * __fma_rn(-hx * y, y, 1.5);
-  y = y * __fma_rn(-hx * y, y, 1.5);
-  return y;
-}
-
 __device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<false> &t, const int32_t *list,
                                         int nsrc, void *stage, const FarBox &, unsigned &npp) {
   StagePP64 &S = *reinterpret_cast<StagePP64 *>(stage);
@@ -388,7 +370,7 @@ __device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<false> &t, con
   for (int s = t.rep; s < nsrc; s += t.nrep) {
     const double dx = t.x - S.x[s], dy = t.y - S.y[s], dz = t.z - S.z[s];
     const double r2 = dx * dx + dy * dy + dz * dz;
-    const double rinv = r2 > 0.0 ? rsqrt64(r2) : 0.0;
+    const double rinv = r2 > 0.0 ? rsqrt(r2) : 0.0;
     const double r = r2 * rinv;
     // y = r / max(r_out,i, r_out,j) as r min(1 / r_out): one reciprocal a
     // staged source, not a division a pair
@@ -480,7 +462,7 @@ __device__ __forceinline__ void eval_nodes(const WalkArgs &a, Target<false> &t,
     const Mom64 &m = S[s];
     const double dx = t.x - m.cx, dy = t.y - m.cy, dz = t.z - m.cz;
     const double r2 = dx * dx + dy * dy + dz * dz;
-    const double rinv = r2 > 0.0 ? rsqrt64(r2) : 0.0;
+    const double rinv = r2 > 0.0 ? rsqrt(r2) : 0.0;
     const double rinv2 = rinv * rinv, rinv3 = rinv2 * rinv, rinv5 = rinv3 * rinv2;
     const double qx = m.qxx * dx + m.qxy * dy + m.qxz * dz;
     const double qy = m.qxy * dx + m.qyy * dy + m.qyz * dz;
