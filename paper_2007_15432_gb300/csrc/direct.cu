@@ -48,7 +48,7 @@ struct DT<true> {
   using T = float;
 };
 
-__device__ __forceinline__ double rsq(double a) { return 1.0 / sqrt(a); }
+__device__ __forceinline__ double rsq(double a) { return rsqrt(a); }
 
 // hi + lo += p without losing the rounding error of the addition (TwoSum)
 __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float p) {

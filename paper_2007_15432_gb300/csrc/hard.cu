@@ -1141,7 +1141,7 @@ __global__ void __launch_bounds__(kETile) k_energy(p3t_particles p, p3t_params p
       for (int q = 0; q < lim; ++q) {
         if (base + q == i) continue;
         const double dx = xi - s_x[q], dy = yi - s_y[q], dz = zi - s_z[q];
-        sd += s_m[q] / sqrt(dx * dx + dy * dy + dz * dz);
+        sd += s_m[q] * rsqrt(dx * dx + dy * dy + dz * dz);
       }
     }
   }

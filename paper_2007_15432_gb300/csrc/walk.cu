@@ -923,7 +923,7 @@ struct VjpEval {
       if (valid) {
         const double rx = x - m.cx, ry = y - m.cy, rz = z - m.cz;
         const double r2 = rx * rx + ry * ry + rz * rz;
-        const double ri = 1.0 / sqrt(r2);
+        const double ri = rsqrt(r2);
         const double ri2 = ri * ri, ri3 = ri2 * ri, ri5 = ri3 * ri2, ri7 = ri5 * ri2,
                      ri9 = ri7 * ri2;
         const double qx = m.qxx * rx + m.qxy * ry + m.qxz * rz;
