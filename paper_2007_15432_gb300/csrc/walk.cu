@@ -291,6 +291,28 @@ __device__ __forceinline__ bool far_from(const FarBox &b, const float4 A, const 
   return d2 > 0.f && d2 >= R2;
 }
 
+// The FP64 walk's counterpart: the targets' box in FP64 and the largest
+// max(r_search, r_out)^2 of its targets.  A source whose distance to the box
+// exceeds max(r_search, r_out) of the source and of every target by a
+// relative 1e-9 (far above the rounding of the pair's r and y) has y >= 1
+// (K = 1 exactly) and r^2 >= r_search,max^2 for every target: the far
+// evaluation below then gives the bits of the full one.
+struct FarBox64 {
+  double lo[3], hi[3], R2;
+};
+template <bool MIXED> struct BoxOf { using type = FarBox; };
+template <> struct BoxOf<false> { using type = FarBox64; };
+
+__device__ __forceinline__ bool far_from64(const FarBox64 &b, double x, double y, double z,
+                                           double ro, double rs) {
+  const double gx = fmax(fmax(b.lo[0] - x, x - b.hi[0]), 0.0);
+  const double gy = fmax(fmax(b.lo[1] - y, y - b.hi[1]), 0.0);
+  const double gz = fmax(fmax(b.lo[2] - z, z - b.hi[2]), 0.0);
+  const double d2 = gx * gx + gy * gy + gz * gz;
+  const double R2 = fmax(b.R2, fmax(rs * rs, ro * ro));
+  return d2 > 0.0 && d2 >= R2 * (1.0 + 1e-9);
+}
+
 // pair terms with K = 1 and no candidate test (the batch is far, see above):
 // the same operations as pp_pair's K = 1 case, so the same bits
 __device__ __forceinline__ void pp_pair_far(Target<true> &t, const StagePP32 &S, int p, f2 &BX,
@@ -356,17 +378,35 @@ __device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<true> &t, cons
 }
 
 __device__ __forceinline__ void eval_pp(const WalkArgs &a, Target<false> &t, const int32_t *list,
-                                        int nsrc, void *stage, const FarBox &, unsigned &npp) {
+                                        int nsrc, void *stage, const FarBox64 &box,
+                                        unsigned &npp) {
   StagePP64 &S = *reinterpret_cast<StagePP64 *>(stage);
   const int lane = threadIdx.x & 31;
+  bool near = false;
   if (lane < nsrc) {
     const int32_t j = list[lane];
-    S.x[lane] = a.sx[j]; S.y[lane] = a.sy[j]; S.z[lane] = a.sz[j];
-    S.m[lane] = a.sm[j]; S.iro[lane] = 1.0 / a.sro[j]; S.rs[lane] = a.srs[j];
+    const double x = a.sx[j], y = a.sy[j], z = a.sz[j], ro = a.sro[j], rs = a.srs[j];
+    S.x[lane] = x; S.y[lane] = y; S.z[lane] = z;
+    S.m[lane] = a.sm[j]; S.iro[lane] = 1.0 / ro; S.rs[lane] = rs;
     S.idx[lane] = j;
+    near = !far_from64(box, x, y, z, ro, rs);
   }
+  const bool any_near = __any_sync(0xffffffffu, near);
   __syncwarp();
   npp += (t.valid && t.rep == 0) ? (unsigned)nsrc : 0u;
+  if (!any_near) {
+    // K = 1 for every pair and no candidate: the full loop's operations with
+    // K = 1 (m K = m exactly)
+    for (int s = t.rep; s < nsrc; s += t.nrep) {
+      const double dx = t.x - S.x[s], dy = t.y - S.y[s], dz = t.z - S.z[s];
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      const double rinv = r2 > 0.0 ? rsqrt(r2) : 0.0;
+      const double f = S.m[s] * (rinv * rinv * rinv);
+      t.ax -= f * dx; t.ay -= f * dy; t.az -= f * dz;
+    }
+    __syncwarp();
+    return;
+  }
   for (int s = t.rep; s < nsrc; s += t.nrep) {
     const double dx = t.x - S.x[s], dy = t.y - S.y[s], dz = t.z - S.z[s];
     const double r2 = dx * dx + dy * dy + dz * dz;
@@ -649,7 +689,7 @@ template <bool MIXED> struct GroupEval {
   const WalkArgs &a;
   Target<MIXED> &t;
   void *stage;
-  const FarBox &box;
+  const typename BoxOf<MIXED>::type &box;
   unsigned &npp, &npn;
   __device__ void nodes(const int32_t *list, int n) { eval_nodes(a, t, list, n, stage, npn); }
   __device__ void pp(const int32_t *list, int n) { eval_pp(a, t, list, n, stage, box, npp); }
@@ -681,6 +721,31 @@ __device__ __forceinline__ void far_box(const Target<true> &t, FarBox &b) {
     b.hi[0] = hi0; b.hi[1] = hi1; b.hi[2] = hi2;
     b.R2 = R2;
     b.amax = am;
+  }
+  __syncwarp();
+}
+
+// the FP64 walk's FarBox64 from its (valid) targets, written by lane 0
+__device__ __forceinline__ void far_box64(const Target<false> &t, FarBox64 &b) {
+  const double inf = __longlong_as_double(0x7ff0000000000000ll);
+  double lo0 = t.valid ? t.x : inf, lo1 = t.valid ? t.y : inf, lo2 = t.valid ? t.z : inf;
+  double hi0 = t.valid ? t.x : -inf, hi1 = t.valid ? t.y : -inf, hi2 = t.valid ? t.z : -inf;
+  const double ro = 1.0 / t.iro;
+  double R2 = t.valid ? fmax(t.rs * t.rs, ro * ro) : 0.0;
+  for (int o = 16; o > 0; o >>= 1) {
+    lo0 = fmin(lo0, __shfl_xor_sync(0xffffffffu, lo0, o));
+    lo1 = fmin(lo1, __shfl_xor_sync(0xffffffffu, lo1, o));
+    lo2 = fmin(lo2, __shfl_xor_sync(0xffffffffu, lo2, o));
+    hi0 = fmax(hi0, __shfl_xor_sync(0xffffffffu, hi0, o));
+    hi1 = fmax(hi1, __shfl_xor_sync(0xffffffffu, hi1, o));
+    hi2 = fmax(hi2, __shfl_xor_sync(0xffffffffu, hi2, o));
+    R2 = fmax(R2, __shfl_xor_sync(0xffffffffu, R2, o));
+  }
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) {
+    b.lo[0] = lo0; b.lo[1] = lo1; b.lo[2] = lo2;
+    b.hi[0] = hi0; b.hi[1] = hi1; b.hi[2] = hi2;
+    b.R2 = R2;
   }
   __syncwarp();
 }
@@ -807,7 +872,7 @@ __global__ void __launch_bounds__(kWarps * 32, MIXED ? P3T_WALK_MINB_MIXED : 1)
   __shared__ int32_t s_big[kWarps][kBigCap];
   __shared__ __align__(16) unsigned char s_stage[kWarps][kStageBytes];
   __shared__ int64_t s_bh[P3T_BITS + 1];
-  __shared__ FarBox s_box[kWarps];
+  __shared__ typename BoxOf<MIXED>::type s_box[kWarps];
   if (threadIdx.x <= P3T_BITS) s_bh[threadIdx.x] = a.bh[threadIdx.x];
   __syncthreads();
 
@@ -840,7 +905,7 @@ __global__ void __launch_bounds__(kWarps * 32, MIXED ? P3T_WALK_MINB_MIXED : 1)
       const int nrep = 32 / k, rep = lane / k;
       Target<MIXED> t;
       t.load(a, tb + (lane - rep * k), rep < nrep, rep < nrep ? rep : 0, nrep);
-      if constexpr (MIXED) far_box(t, s_box[w]);
+      if constexpr (MIXED) far_box(t, s_box[w]); else far_box64(t, s_box[w]);
       GroupEval<MIXED> ev{a, t, s_stage[w], s_box[w], npp, npn};
       ok = traverse(a, gb, gfirst, stack, s_pp[w], s_nd[w], s_big[w], s_bh, round_limit, ev);
       if (ok) {
