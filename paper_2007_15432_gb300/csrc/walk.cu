@@ -557,8 +557,19 @@ __device__ bool traverse(const WalkArgs &a, const GroupBox &gb, int32_t first, i
   int64_t rounds = 0;
   // sorted order keeps each segment contiguous, and segment d's root (level
   // 0, d-th in key order) is BFS node d: start at the root of the segment
-  // that holds sorted particle `first`
-  if (lane == 0) stack[0] = seg_at(a.seg, first);
+  // that holds sorted particle `first`.  Every box inside the root cube lies
+  // within 2^21 half cells of its centre on each axis, so when the root's
+  // Barnes-Hut threshold exceeds 3 (2^21)^2 the root is opened for every
+  // group: its children then start the stack, where the first round would
+  // have pushed them
+  const int32_t root = seg_at(a.seg, first);
+  const int4 rc = __ldg(reinterpret_cast<const int4 *>(&a.node[root]) + 3);  // child0, nchild
+  if (s_bh[0] > (3ll << 42) && rc.y > 0) {
+    if (lane < rc.y) stack[lane] = rc.x + lane;
+    top = rc.y;
+  } else if (lane == 0) {
+    stack[0] = root;
+  }
   __syncwarp();
   while (top > 0) {
     if (++rounds > round_limit) {
