@@ -49,8 +49,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one k_walk launch on the N = 10^6 wide disk,
 # group size 64, from a single-pass ncu capture of this kernel
-# (dram__bytes_read.sum 79.07 MB + dram__bytes_write.sum 16.31 MB)
-WALK_TRAFFIC_1E6 = 95.39e6
+# (dram__bytes_read.sum 78.90 MB + dram__bytes_write.sum 16.13 MB)
+WALK_TRAFFIC_1E6 = 95.03e6
 
 
 def parse():
