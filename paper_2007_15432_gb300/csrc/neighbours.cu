@@ -151,29 +151,47 @@ __global__ void k_cl_flags(int64_t n, const int32_t *label, const int32_t *csize
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t sz = csize[label[i]];
     const bool root = label[i] == i && csize[i] >= 2;
-    flag[i] = sz == 1;
-    flag[n + i] = root;
-    flag[2 * n + i] = root ? csize[i] : 0;
-    flag[3 * n + i] = sz >= 2;
+    // two words a particle, each scanned as (bit 0) + (bits 1-31) 2^31:
+    // isolated and cluster member; cluster root and its size
+    flag[i] = (sz == 1 ? 1 : 0) | (sz >= 2 ? 2 : 0);
+    flag[n + i] = root ? 1 | (csize[i] << 1) : 0;
     if (root) mx = max(mx, (unsigned long long)csize[i]);
   }
   if (mx) atomicMax(reinterpret_cast<unsigned long long *>(&counts[3]), mx);
 }
 
+// the singles, each cluster's offset and the members (with their labels, for
+// the sort) from the two packed scans (counts in bits 0-30, the second sum
+// from bit 31), and the four totals: singles, clusters, members (counts[0..2])
+// and members again for the sort (*d_nmem)
 __global__ void k_cl_scatter(int64_t n, const int32_t *label, const int32_t *flag,
-                             const int64_t *pos, int32_t *singles, int64_t *cl_off,
-                             uint64_t *mkeys, int32_t *mvals, const int64_t *counts) {
+                             const int64_t *pos, const int64_t *d_tot, int32_t *singles,
+                             int64_t *cl_off, uint64_t *mkeys, int32_t *mvals, int64_t *counts,
+                             int64_t *d_nmem) {
   pdl_wait();
+  constexpr int64_t kLow = (1ll << 31) - 1;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    if (flag[i]) singles[pos[i]] = (int32_t)i;
-    if (flag[n + i]) cl_off[pos[n + i]] = pos[2 * n + i];
-    if (flag[3 * n + i]) {
-      mkeys[pos[3 * n + i]] = (uint64_t)label[i];
-      mvals[pos[3 * n + i]] = (int32_t)i;
+    const int32_t fa = flag[i], fb = flag[n + i];
+    if (fa & 1) singles[pos[i] & kLow] = (int32_t)i;
+    if (fb & 1) {
+      const int64_t q = pos[n + i];
+      cl_off[q & kLow] = q >> 31;
+    }
+    if (fa & 2) {
+      const int64_t q = pos[i] >> 31;
+      mkeys[q] = (uint64_t)label[i];
+      mvals[q] = (int32_t)i;
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) cl_off[counts[1]] = counts[2];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t ta = d_tot[0], tb = d_tot[1];
+    counts[0] = ta & kLow;
+    counts[1] = tb & kLow;
+    counts[2] = tb >> 31;
+    *d_nmem = ta >> 31;
+    cl_off[tb & kLow] = tb >> 31;
+  }
 }
 
 __global__ void k_zero_i64(int64_t *p, int k) {
@@ -208,16 +226,15 @@ int p3t_run_neighbours(p3t_ctx *c, const p3t_particles *p, int64_t *nb_off,
   pdl_launch(k_uf_union, dim3((unsigned)g), dim3(kBlock), 0, s, n, nb_off, nb_idx, c->parent, c->status);
   pdl_launch(k_uf_label, dim3((unsigned)g), dim3(kBlock), 0, s, n, c->parent, c->label, c->csize);
   pdl_launch(k_cl_flags, dim3((unsigned)g), dim3(kBlock), 0, s, n, c->label, c->csize, c->flag, c->cl_counts);
-  // four scans: isolated, roots, root sizes, members
-  for (int q = 0; q < 4; ++q) {
-    int64_t *tot = q == 0 ? &c->cl_counts[0] : q == 1 ? &c->cl_counts[1]
-                 : q == 2 ? &c->cl_counts[2] : &cnt[11];
-    rc = p3t_scan_i32_to_i64(c->flag + q * n, c->pos + q * n, &cnt[0], c->cap, tot,
+  // two packed scans: (isolated, members) and (roots, root sizes); their
+  // totals in cnt[21], cnt[22]
+  for (int q = 0; q < 2; ++q) {
+    rc = p3t_scan_flag_pairs(c->flag + q * n, c->pos + q * n, &cnt[0], c->cap, &cnt[21 + q],
                              c->scan_state, c->scan_words, c->status, c->poll_limit, s);
     if (rc) return rc;
   }
-  pdl_launch(k_cl_scatter, dim3((unsigned)g), dim3(kBlock), 0, s, n, c->label, c->flag, c->pos, c->singles,
-                                              c->cl_off, c->mkeys, c->mvals, c->cl_counts);
+  pdl_launch(k_cl_scatter, dim3((unsigned)g), dim3(kBlock), 0, s, n, c->label, c->flag, c->pos,
+             &cnt[21], c->singles, c->cl_off, c->mkeys, c->mvals, c->cl_counts, &cnt[11]);
   // filter, check, fill, sort_rows, zero, uf_init, uf_union, uf_label, flags, scatter
   p3t_note_launches(10);
   // members ordered by (label, index): stable sort of the ascending member list;

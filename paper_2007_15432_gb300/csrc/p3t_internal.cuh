@@ -353,9 +353,10 @@ int p3t_scan_i32_to_i64(const int32_t *in, int64_t *out, const int64_t *d_n,
                         int64_t n_cap, int64_t *d_total, unsigned long long *state,
                         int64_t state_words, DevStatus *st, int64_t poll_limit,
                         cudaStream_t s);
-// The same scan of inputs that each hold two 0/1 flags (bits 0 and 1): out
-// and *d_total hold the prefix count of flag 0 in bits 0-30 and that of flag
-// 1 from bit 31 up.
+// The same scan of inputs that each hold a 0/1 flag in bit 0 and a
+// non-negative value in bits 1-31: out and *d_total hold the prefix count of
+// the flag in bits 0-30 and the prefix sum of the values from bit 31 up (each
+// sum below 2^31).
 int p3t_scan_flag_pairs(const int32_t *in, int64_t *out, const int64_t *d_n, int64_t n_cap,
                         int64_t *d_total, unsigned long long *state, int64_t state_words,
                         DevStatus *st, int64_t poll_limit, cudaStream_t s);

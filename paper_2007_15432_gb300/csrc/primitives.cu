@@ -47,9 +47,9 @@ __device__ int64_t block_excl_scan(int64_t v, int64_t *excl, int64_t *sh) {
 // block to finish (counter state[1]) clears the words it used and both
 // counters, so that the next call starts clean with no host involvement.  A bounded number of polls: a predecessor that
 // never publishes is reported (P3T_ERR_TIMEOUT) and counted as zero.  With
-// PAIRS, every input holds two 0/1 flags (bits 0 and 1) and counts as
-// flag0 + flag1 2^31, so that one scan gives both prefix counts (each below
-// 2^31) in one word.
+// PAIRS, every input holds a 0/1 flag in bit 0 and a non-negative value in
+// bits 1-31 and counts as flag + value 2^31, so that one scan gives both
+// prefix sums (each below 2^31) in one word.
 constexpr int kScanThreads = 512;
 constexpr int kScanPer = 8;
 constexpr int kScanTile = kScanThreads * kScanPer;
@@ -57,7 +57,7 @@ constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagInc = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
 template <bool PAIRS>
 __device__ __forceinline__ int64_t scan_value(int32_t v) {
-  return PAIRS ? (int64_t)(v & 1) + ((int64_t)((v >> 1) & 1) << 31) : (int64_t)v;
+  return PAIRS ? (int64_t)(v & 1) + ((int64_t)((uint32_t)v >> 1) << 31) : (int64_t)v;
 }
 template <bool PAIRS>
 __global__ void __launch_bounds__(kScanThreads)
