@@ -194,6 +194,15 @@ __global__ void k_cl_scatter(int64_t n, const int32_t *label, const int32_t *fla
   }
 }
 
+// the first *d_n values of src into dst
+__global__ void k_copy_i32(const int64_t *d_n, const int32_t *src, int32_t *dst) {
+  pdl_wait();
+  const int64_t n = *d_n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
 __global__ void k_zero_i64(int64_t *p, int k) {
   pdl_wait();
   if (threadIdx.x < k) p[threadIdx.x] = 0;
@@ -237,17 +246,23 @@ int p3t_run_neighbours(p3t_ctx *c, const p3t_particles *p, int64_t *nb_off,
              &cnt[21], c->singles, c->cl_off, c->mkeys, c->mvals, c->cl_counts, &cnt[11]);
   // filter, check, fill, sort_rows, zero, uf_init, uf_union, uf_label, flags, scatter
   p3t_note_launches(10);
-  // members ordered by (label, index): stable sort of the ascending member list;
-  // an even number of 8-bit passes leaves the result in the buffer it started
-  // in, so the cluster views keep their addresses from step to step (a step
-  // captured in a CUDA graph reads the previous step's clusters there)
-  const int bits = n <= 65536 ? 16 : 32;
+  // members ordered by (label, index): stable sort of the ascending member
+  // list on the label's bits (labels are particle indices below n).  The
+  // sorted members must land in the buffer they started in, so that the
+  // cluster views keep their addresses from step to step (a step captured in
+  // a CUDA graph reads the previous step's clusters there): after an odd
+  // number of 8-bit passes they are copied back
+  const int bits = n <= 65536 ? 16 : (n <= (1 << 24) ? 24 : 32);
   uint64_t *k0 = c->mkeys, *k1 = c->mkeys_alt;
   int32_t *v0 = c->mvals, *v1 = c->mvals_alt;
   rc = p3t_radix_sort(&k0, &v0, &k1, &v1, &cnt[11], c->cap, 0, bits, c->radix_hist,
                       c->radix_hist_cap, s);
   if (rc) return rc;
-  c->cl_mem = v0;  // sorted payload buffer
-  c->mvals = v0; c->mvals_alt = v1; c->mkeys = k0; c->mkeys_alt = k1;
+  if (v0 != c->mvals) {
+    pdl_launch(k_copy_i32, dim3((unsigned)p3t_grid(n, kBlock, maxb)), dim3(kBlock), 0, s, &cnt[11],
+               v0, c->mvals);
+    p3t_note_launches(1);
+  }
+  c->cl_mem = c->mvals;  // sorted payload buffer
   return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
 }
